@@ -1,0 +1,196 @@
+"""CPU oracle for the p-bit Feynman-path sampler (arXiv 2007.07379).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline / reference leg of ``bench.py``; never by the product
+package.  It shares no code with the CUDA library.  ``oracle.c`` holds the
+plain C implementation (FP64 state vector, exact path sum, reference Gibbs
+sampler, Philox4x32-10); this module compiles it with gcc on first use and
+wraps it with ctypes.  ``mlp.py`` holds the FP64 numpy MLP reference.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+H, S, T, CNOT, CZ = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, OpenMP, -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC", "-shared",
+             _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            lib.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            lib.orc_philox4x32_10.restype = None
+            for name in ("orc_statevector", "orc_pathsum_exact", "orc_gf2_rank",
+                         "orc_colour", "orc_gibbs", "orc_violations", "orc_path_phase",
+                         "orc_thresholds"):
+                getattr(lib, name).restype = ctypes.c_int
+            lib.orc_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _gates(gates) -> np.ndarray:
+    g = np.ascontiguousarray(np.asarray(gates, dtype=np.int32).reshape(-1, 4))
+    return g
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one counter (4 x u32) under one key (2 x u32)."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib.orc_philox4x32_10(c.ctypes.data_as(u32p), k.ctypes.data_as(u32p), out.ctypes.data_as(u32p))
+    return out
+
+
+def statevector(n: int, d: int, gates, beta: int = 0) -> np.ndarray:
+    """FP64 state vector psi_alpha = U_{alpha,beta} (Eq. U), complex128[2^n]."""
+    lib = _load()
+    g = _gates(gates)
+    re = np.zeros(1 << n)
+    im = np.zeros(1 << n)
+    rc = lib.orc_statevector(n, d, _p(g), len(g), ctypes.c_uint32(beta), _p(re), _p(im))
+    if rc != 0:
+        raise ValueError(f"orc_statevector failed ({rc})")
+    return re + 1j * im
+
+
+def pathsum_exact(n: int, d: int, gates, beta: int = 0):
+    """Exact path sum: (cnt int64[2^n, 8], h); U_alpha = 2^{-h/2} sum_b cnt[alpha,b] w^b."""
+    lib = _load()
+    g = _gates(gates)
+    cnt = np.zeros((1 << n, 8), dtype=np.int64)
+    h = ctypes.c_int(0)
+    rc = lib.orc_pathsum_exact(n, d, _p(g), len(g), ctypes.c_uint32(beta), _p(cnt), ctypes.byref(h))
+    if rc != 0:
+        raise ValueError(f"orc_pathsum_exact failed ({rc})")
+    return cnt, h.value
+
+
+def phase_counts_to_complex(cnt: np.ndarray, h: int) -> np.ndarray:
+    """2^{-h/2} sum_b cnt[..., b] e^{i pi b / 4} in FP64."""
+    w = np.exp(1j * np.pi * np.arange(8) / 4.0)
+    return (cnt.astype(np.float64) @ w) * 2.0 ** (-h / 2.0)
+
+
+def gf2_rank(n: int, d: int, gates):
+    """(h, rank) of the GF(2) map from H outputs to the last layer."""
+    lib = _load()
+    g = _gates(gates)
+    h = ctypes.c_int(0)
+    r = ctypes.c_int(0)
+    rc = lib.orc_gf2_rank(n, d, _p(g), len(g), ctypes.byref(h), ctypes.byref(r))
+    if rc != 0:
+        raise ValueError(f"orc_gf2_rank failed ({rc})")
+    return h.value, r.value
+
+
+def thresholds(J: float) -> np.ndarray:
+    lib = _load()
+    thr = np.zeros(4, dtype=np.uint32)
+    rc = lib.orc_thresholds(ctypes.c_double(J), _p(thr))
+    if rc != 0:
+        raise ValueError("bad J")
+    return thr
+
+
+def colour(n: int, d: int, gates) -> np.ndarray:
+    """Colour class (0..3) of every p-bit, shape [d, n] (row k-1 = layer k)."""
+    lib = _load()
+    g = _gates(gates)
+    col = np.zeros((d, n), dtype=np.int32)
+    rc = lib.orc_colour(n, d, _p(g), len(g), _p(col))
+    if rc != 0:
+        raise ValueError("orc_colour failed")
+    return col
+
+
+def gibbs(n: int, d: int, gates, *, J: float, seed: int, chains: int, sweeps: int,
+          beta: int = 0, chain0: int = 0, sweep0: int = 0, burn_in: int = 0,
+          record_every: int = 1, state: np.ndarray | None = None, alphas=None):
+    """Reference Gibbs run.  Returns dict(state[chains, d] u32, cnt[bins, 8] u64,
+    valid, samples).  ``state=None`` starts from fresh valid paths (init=1)."""
+    lib = _load()
+    g = _gates(gates)
+    init = 1 if state is None else 0
+    st = np.zeros((chains, d), dtype=np.uint32) if state is None else \
+        np.ascontiguousarray(state, dtype=np.uint32).copy()
+    assert st.shape == (chains, d)
+    if alphas is None:
+        bins = 1 << n
+        al = None
+    else:
+        al = np.ascontiguousarray(alphas, dtype=np.uint32)
+        bins = len(al)
+    cnt = np.zeros((bins, 8), dtype=np.uint64)
+    valid = ctypes.c_uint64(0)
+    samples = ctypes.c_uint64(0)
+    rc = lib.orc_gibbs(n, d, _p(g), len(g), ctypes.c_uint32(beta), ctypes.c_double(J),
+                       ctypes.c_uint64(seed), ctypes.c_uint32(chain0), ctypes.c_uint32(chains),
+                       ctypes.c_uint32(sweep0), ctypes.c_uint32(sweeps), ctypes.c_uint32(burn_in),
+                       ctypes.c_uint32(record_every), init, _p(st),
+                       None if al is None else _p(al), 0 if al is None else len(al),
+                       _p(cnt), ctypes.byref(valid), ctypes.byref(samples))
+    if rc != 0:
+        raise ValueError(f"orc_gibbs failed ({rc})")
+    return {"state": st, "cnt": cnt, "valid": valid.value, "samples": samples.value}
+
+
+def violations(n: int, d: int, gates, state: np.ndarray, beta: int = 0) -> np.ndarray:
+    lib = _load()
+    g = _gates(gates)
+    st = np.ascontiguousarray(state, dtype=np.uint32)
+    out = np.zeros(st.shape[0], dtype=np.int32)
+    rc = lib.orc_violations(n, d, _p(g), len(g), ctypes.c_uint32(beta), ctypes.c_uint32(st.shape[0]),
+                            _p(st), _p(out))
+    if rc != 0:
+        raise ValueError("orc_violations failed")
+    return out
+
+
+def path_phase(n: int, d: int, gates, path, beta: int = 0) -> int:
+    lib = _load()
+    g = _gates(gates)
+    p = np.ascontiguousarray(path, dtype=np.uint32)
+    return lib.orc_path_phase(n, d, _p(g), len(g), ctypes.c_uint32(beta), _p(p))
+
+
+def num_threads() -> int:
+    return _load().orc_num_threads()
+
+
+def estimate_amplitudes(cnt: np.ndarray, valid: int, h: int) -> np.ndarray:
+    """Eq. U23 with uniform valid paths: psi_hat = 2^{h/2} sum_b cnt[.,b] w^b / valid."""
+    w = np.exp(1j * np.pi * np.arange(8) / 4.0)
+    return (cnt.astype(np.float64) @ w) * (2.0 ** (h / 2.0)) / max(valid, 1)

@@ -1,0 +1,177 @@
+"""Seeded synthetic inputs: random Clifford+T circuits and the five workloads.
+
+This module holds input generation only (no sampling, energy or phase
+arithmetic).  The CUDA path and the CPU oracle both take its gate lists.
+
+Generator (the paper names no circuit family; this is the stated reading):
+per layer, the qubits are visited in a seeded random order; each qubit not yet
+used in the layer draws a gate uniformly from {H, S, T, CNOT, CZ}; a 2-qubit
+draw takes a partner uniformly among the still-free qubits (CNOT control and
+target in random order); with no free partner the draw is redone among the
+1-qubit gates.  Every qubit is acted on once per layer.  Randomness is
+SplitMix64(seed).
+
+A gate is the row ``(op, layer, q0, q1)``: ``op`` in H=0, S=1, T=2, CNOT=3,
+CZ=4; ``layer`` in ``[0, d)`` maps the state after ``layer`` gate layers to
+the next; for CNOT ``q0`` is the control and ``q1`` the target; a 1-qubit gate
+has ``q1 = -1``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+H, S, T, CNOT, CZ = 0, 1, 2, 3, 4
+GATE_NAMES = {H: "H", S: "S", T: "T", CNOT: "CNOT", CZ: "CZ"}
+_MASK64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea, Flood 2014)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK64
+
+    def next(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+        return z ^ (z >> 31)
+
+    def below(self, m: int) -> int:
+        """Uniform integer in [0, m) by rejection."""
+        if m <= 0:
+            raise ValueError("m must be positive")
+        limit = (1 << 64) - ((1 << 64) % m)
+        while True:
+            x = self.next()
+            if x < limit:
+                return x % m
+
+
+def random_circuit(n: int, d: int, seed: int, one_gate_per_layer: bool = False) -> np.ndarray:
+    """Seeded random Clifford+T circuit, int32[n_gates, 4] rows (op, layer, q0, q1).
+
+    ``one_gate_per_layer`` is the alternative reading (a single random gate per
+    layer, the other qubits idle); the graded workloads never use it.
+    """
+    if not (1 <= n <= 32 and 1 <= d <= 64):
+        raise ValueError("need 1 <= n <= 32 and 1 <= d <= 64")
+    rng = SplitMix64(seed)
+    rows = []
+    for layer in range(d):
+        if one_gate_per_layer:
+            op = rng.below(5) if n >= 2 else rng.below(3)
+            q0 = rng.below(n)
+            if op in (CNOT, CZ):
+                q1 = rng.below(n - 1)
+                q1 = q1 + 1 if q1 >= q0 else q1
+                rows.append((op, layer, q0, q1))
+            else:
+                rows.append((op, layer, q0, -1))
+            continue
+        order = list(range(n))
+        for i in range(n - 1, 0, -1):  # Fisher-Yates
+            j = rng.below(i + 1)
+            order[i], order[j] = order[j], order[i]
+        free = [True] * n
+        for q in order:
+            if not free[q]:
+                continue
+            op = rng.below(5)
+            partners = [p for p in range(n) if free[p] and p != q]
+            if op in (CNOT, CZ) and not partners:
+                op = rng.below(3)
+            if op in (CNOT, CZ):
+                p = partners[rng.below(len(partners))]
+                a, b = (q, p) if rng.below(2) == 0 else (p, q)
+                rows.append((op, layer, a, b))
+                free[q] = free[p] = False
+            else:
+                rows.append((op, layer, q, -1))
+                free[q] = False
+    return np.asarray(rows, dtype=np.int32).reshape(-1, 4)
+
+
+def hadamard_chain(d: int) -> np.ndarray:
+    """n = 1, d Hadamard gates in series (Sec. 4, Fig. 3/4)."""
+    return np.asarray([(H, k, 0, -1) for k in range(d)], dtype=np.int32).reshape(-1, 4)
+
+
+def ghz(n: int) -> np.ndarray:
+    """H on qubit 0 then a CNOT ladder 0->1->...->n-1 (d = n layers)."""
+    rows = [(H, 0, 0, -1)] + [(CNOT, k, k - 1, k) for k in range(1, n)]
+    return np.asarray(rows, dtype=np.int32).reshape(-1, 4)
+
+
+def chains_for(n: int) -> int:
+    """Batched workload chain count: max(256, 2^ceil(n/2))."""
+    return max(256, 1 << ((n + 1) // 2))
+
+
+def default_J(n: int, d: int, gates) -> float:
+    """J = ln(M / ln 2), M = number of linked (non-H) p-bits: the stationary
+    fraction of valid paths, (1 + e^{-J})^{-M}, is then close to 1/2."""
+    h = int(np.sum(np.asarray(gates)[:, 0] == H))
+    M = max(n * d - h, 1)
+    return float(np.log(max(M / np.log(2.0), 1.0 + 1e-9)))
+
+
+@dataclass
+class Workload:
+    name: str
+    n: int
+    d: int
+    gates: np.ndarray
+    chains: int
+    sweeps: int
+    seed: int
+    J: float
+    alphas: np.ndarray | None = None
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_pbits(self) -> int:
+        return self.n * (self.d + 1)
+
+
+def tiny() -> Workload:
+    """n=3, d=4 (15 p-bits), 1024 chains x 1e4 sweeps, J = 4."""
+    g = random_circuit(3, 4, seed=0)
+    return Workload("tiny", 3, 4, g, chains=1024, sweeps=10_000, seed=0x5EED, J=4.0)
+
+
+def mid() -> Workload:
+    """n=12, d=20 (252 p-bits), 4096 chains x 1e5 sweeps, full 2^12 histogram."""
+    g = random_circuit(12, 20, seed=1000)
+    return Workload("mid", 12, 20, g, chains=4096, sweeps=100_000, seed=0x5EED + 1,
+                    J=default_J(12, 20, g))
+
+
+def batched(count: int = 256) -> list[Workload]:
+    """256 circuits, n ~ U[6,20], d ~ U[8,40], chains max(256, 2^ceil(n/2)), 1e4 sweeps."""
+    rng = SplitMix64(2000)
+    out = []
+    for i in range(count):
+        n = 6 + rng.below(15)
+        d = 8 + rng.below(33)
+        g = random_circuit(n, d, seed=2000 + i)
+        out.append(Workload(f"batched_{i}", n, d, g, chains=chains_for(n), sweeps=10_000,
+                            seed=0x5EED + i, J=default_J(n, d, g)))
+    return out
+
+
+def learned() -> Workload:
+    """n=16, d=24 circuit for the learned proposal (MLP hidden 256)."""
+    g = random_circuit(16, 24, seed=3000)
+    return Workload("learned", 16, 24, g, chains=4096, sweeps=10_000, seed=0x5EED + 3,
+                    J=default_J(16, 24, g), extra={"hidden": 256, "train_paths": 1_000_000})
+
+
+def large() -> Workload:
+    """n=24, d=32 (24*33 = 792 p-bits), 65536 chains, 64 output amplitudes alpha in 0..63."""
+    g = random_circuit(24, 32, seed=4000)
+    return Workload("large", 24, 32, g, chains=65536, sweeps=10_000, seed=0x5EED + 4,
+                    J=default_J(24, 32, g), alphas=np.arange(64, dtype=np.uint32))
