@@ -1,0 +1,198 @@
+/*
+ * pbits.h -- C ABI of the GB300 p-bit Feynman-path sampler.
+ *
+ * Method: arXiv 2007.07379, "Emulating Quantum Interference with Generalized
+ * Ising Machines".  A circuit of d gate layers on n qubits becomes a layered
+ * network of p-bits; a configuration s_1..s_d of the layers is a Feynman path
+ * beta -> s_1 -> ... -> s_d = alpha whose weight is the product of the layer
+ * matrix elements (Eq. U, Eq. path).  Paths are drawn by Gibbs sampling on the
+ * real part of the complex energy E = -ln U (Eq. UE), with zero matrix
+ * elements replaced by e^{-J} (Appendix), and each sampled valid path adds its
+ * phase exp(-i Im E) to the bin of its end state (Fig. 2, Steps 1-3).
+ *
+ * Conventions for every call:
+ *  - Returns a pb_status (0 = PB_OK, negative = error); nothing throws across
+ *    the ABI.  pb_strerror() names a code.
+ *  - Inputs are copied: the caller keeps ownership of every pointer it passes.
+ *  - Device memory is the caller's: pb_run_create() takes a device workspace
+ *    (pointer + byte count; size from pb_workspace_bytes()).  The library
+ *    performs no device allocation on these paths.
+ *  - Streams are CUDA stream handles cast to uintptr_t (0 = legacy default).
+ *  - pb_model and trained pb_mlp objects are immutable after creation and may
+ *    be shared; a pb_run belongs to one host thread at a time.
+ *  - Host arrays passed for results are caller-owned and sized as stated.
+ */
+#ifndef PBITS_H
+#define PBITS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PB_API __attribute__((visibility("default")))
+#else
+#define PB_API
+#endif
+
+typedef enum {
+  PB_OK = 0,
+  PB_EINVAL = -1,   /* malformed argument (bad gate, bad pointer, bad enum) */
+  PB_ERANGE = -2,   /* size out of range (n > 32, d > 64, buffer too small) */
+  PB_ENOMEM = -3,   /* host allocation failed                               */
+  PB_ECUDA = -4,    /* a CUDA runtime call failed                           */
+  PB_ETIMEOUT = -5, /* a device-side bounded wait expired (status word)     */
+  PB_ESTATE = -6    /* call not valid in the object's current state         */
+} pb_status;
+
+/* Gate kinds.  Matrices (rows = output, columns = input, Sec. 2):
+ *   H  = (1/sqrt2)[[1,1],[1,-1]]  (Eq. Had)
+ *   S  = diag(1, i), T = diag(1, e^{i pi/4})  (diagonal Rz family, Appendix,
+ *        with the global phase fixed so that <0|G|0> = 1)
+ *   CNOT: control q0, target q1, x_t -> x_t XOR x_c  (Appendix, "CNOT Gate")
+ *   CZ  = diag(1,1,1,-1) on (q0, q1)  (diagonal two-qubit gate, Appendix)   */
+typedef enum { PB_H = 0, PB_S = 1, PB_T = 2, PB_CNOT = 3, PB_CZ = 4 } pb_op;
+
+/* One gate: layer in [0, d) maps s_layer to s_{layer+1}; 1-qubit gates set
+ * q1 = -1.  Each qubit appears at most once per layer. */
+typedef struct {
+  int32_t op, layer, q0, q1;
+} pb_gate;
+
+typedef struct pb_model pb_model;
+typedef struct pb_run pb_run;
+typedef struct pb_mlp pb_mlp;
+
+/* ---- A1: compile (Eqs. UE, EB, ET2; Appendix) ---------------------------
+ * Builds the layered J-penalty network of a gate list: p-bit (k, q) is bit q
+ * of s_k, k = 1..d, s_0 = input_bits (clamped).  Every output bit of a non-H
+ * gate whose value differs from the gate's deterministic map of its inputs
+ * costs J; H outputs are free.  Computes the sweep's colour classes, the
+ * heat-bath thresholds floor(2^32 / (1 + e^{J v})), v = 0..3, h (H count),
+ * M = n d - h and the GF(2) rank of H outputs -> s_d.
+ *   n_qubits in [1, 32], n_layers in [1, 64], J >= 0 (finite).
+ *   Errors: PB_EINVAL (bad op, qubit, duplicate use in a layer, NULL),
+ *           PB_ERANGE (n or d out of range).  *out is NULL on error.
+ * Host only; the model is freed with pb_model_free(). */
+PB_API int pb_compile(int n_qubits, int n_layers, const pb_gate* gates,
+                      int n_gates, uint32_t input_bits, double J,
+                      pb_model** out);
+
+typedef struct {
+  int32_t n, d;        /* qubits, gate layers                          */
+  int32_t n_pbits;     /* n (d + 1), input layer included              */
+  int32_t h;           /* H gates = free p-bits of a valid path        */
+  int32_t M;           /* linked (non-H) p-bits                        */
+  int32_t rank;        /* GF(2) rank of the map H outputs -> s_d       */
+  double J;
+  uint32_t input_bits;
+  uint32_t thr[4];     /* heat-bath thresholds for |v| = 0..3         */
+  int32_t colour_size[4];
+} pb_model_info_t;
+
+PB_API int pb_model_info(const pb_model* m, pb_model_info_t* info);
+/* Colour class (0..3) of every p-bit, row-major [d][n] (row k-1 = layer k). */
+PB_API int pb_model_colours(const pb_model* m, int32_t* colour);
+PB_API void pb_model_free(pb_model* m);
+
+/* ---- runs ---------------------------------------------------------------
+ * A run holds the chains of one or more models ("batched" when more than
+ * one).  Chains are bit-sliced: 32 chains form a group and share one 32-bit
+ * word per p-bit (bit c = chain 32 g + c).  The random numbers of chain c at
+ * sweep t for p-bit p = (k-1) n + q are Philox4x32-10 outputs under key =
+ * seed at counter (c / 32, t, p | tag << 16, j / 4), word j % 4, j = 0..31:
+ * bit c % 32 of word j is bit 31-j of the chain's uniform u (tag 0 = sweep,
+ * tag 1 = initial H outputs).  A p-bit whose violation count changes by v
+ * when it goes 0 -> 1 is redrawn as [v < 0] XOR [u < thr[|v|]]  (heat-bath,
+ * Fig. 2 Steps 1-2).  One sweep visits the four colour classes in order. */
+enum { PB_GIBBS = 0, PB_LEARNED = 1 };
+
+typedef struct {
+  uint64_t seed;          /* Philox key                                        */
+  uint32_t chains;        /* >= 1 (any count; groups of 32, the last ragged)    */
+  uint32_t burn_in;       /* first recorded sweep (absolute index)             */
+  uint32_t record_every;  /* >= 1: record after sweep t when t >= burn_in and
+                             (t - burn_in) % record_every == 0                  */
+  uint32_t n_batches;     /* SE batches over chain groups (0 = automatic)      */
+  const uint32_t* alphas; /* bins to record; NULL = full 2^n histogram (n<=22)  */
+  int32_t n_alphas;
+  int32_t sampler;        /* PB_GIBBS or PB_LEARNED                            */
+  const pb_mlp* proposal; /* trained MLP for PB_LEARNED, else NULL             */
+  uint32_t mh_every;      /* PB_LEARNED: one suffix MH move every mh_every sweeps */
+} pb_run_cfg;
+
+/* Bytes of device workspace that pb_run_create() needs for these models. */
+PB_API int pb_workspace_bytes(pb_model* const* models, const pb_run_cfg* cfgs,
+                              int n_models, size_t* bytes);
+
+/* Lays out the caller's device workspace (>= pb_workspace_bytes, 256-byte
+ * aligned), uploads the tables, zeroes the counters and initialises every
+ * chain to a valid path with random H outputs (tag-1 stream).  Asynchronous
+ * on `stream`.  Errors: PB_EINVAL, PB_ERANGE (workspace too small), PB_ECUDA. */
+PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs,
+                         int n_models, void* d_workspace, size_t workspace_bytes,
+                         uintptr_t stream, pb_run** out);
+
+/* Enqueues n_sweeps further sweeps of every chain of every model (one
+ * launch; asynchronous).  Sweep indices continue from the previous call. */
+PB_API int pb_run_sweeps(pb_run* run, uint32_t n_sweeps);
+
+/* Waits for the run's stream; returns PB_OK, PB_ECUDA or the device status
+ * word (PB_ETIMEOUT when a bounded device wait expired). */
+PB_API int pb_run_wait(pb_run* run);
+
+/* Histogram of model `model` (synchronous): counts[bin*8 + b] = valid samples
+ * that ended in bin with phase w^b (w = e^{i pi/4}) summed over batches;
+ * bins = n_alphas or 2^n.  Any of the three pointers may be NULL. */
+PB_API int pb_run_histogram(const pb_run* run, int model, uint64_t* counts,
+                            uint64_t* valid_total, uint64_t* samples_total);
+
+/* Amplitude estimates (Eq. U23, uniform valid paths; computed on the device):
+ * psi[bin] = 2^{h/2} sum_b counts[bin][b] w^b / valid_total, and its standard
+ * error from batch means over chain groups (Eq. U26).  l2_normalize != 0
+ * divides by the L2 norm over the recorded bins (Fig. 2 Step 4).
+ * re, im, se: host arrays of `bins` doubles (se may be NULL). */
+PB_API int pb_run_amplitudes(const pb_run* run, int model, int l2_normalize,
+                             double* re, double* im, double* se);
+
+/* Chain words of model `model` (synchronous copy): layout
+ * [group][k-1][q] u32, groups = ceil(chains/32); `bytes` must be >=
+ * groups * d * n * 4. */
+PB_API int pb_run_get_state(const pb_run* run, int model, uint32_t* words,
+                            size_t bytes);
+PB_API int pb_run_set_state(pb_run* run, int model, const uint32_t* words,
+                            size_t bytes);
+
+typedef struct {
+  uint64_t sweeps_done;   /* sweeps enqueued so far (per chain)            */
+  double flips;           /* p-bit updates enqueued: chains * sweeps * n d */
+  double last_ms;         /* device time of the last pb_run_sweeps call    */
+  double flips_per_s;     /* flips of that call / its device time          */
+} pb_run_stats_t;
+PB_API int pb_run_stats(pb_run* run, pb_run_stats_t* stats);
+
+/* Checkpoint: chain words, counters and the sweep index of every model.
+ * bytes_needed is written when host_buf is NULL.  Restore puts them back;
+ * since the draws are counter-based the resumed run is bit-identical to an
+ * uninterrupted one. */
+PB_API int pb_run_checkpoint(const pb_run* run, void* host_buf, size_t bytes,
+                             size_t* bytes_needed);
+PB_API int pb_run_restore(pb_run* run, const void* host_buf, size_t bytes);
+PB_API void pb_run_free(pb_run* run);
+
+/* Test hook: fills out[i*4 .. i*4+3] with Philox4x32-10 of counters
+ * ctr[i*4..] under key (k0, k1) on the device (d_ctr, d_out are device
+ * pointers, count counters). */
+PB_API int pb_philox_fill(const uint32_t* d_ctr, uint32_t k0, uint32_t k1,
+                          uint32_t count, uint32_t* d_out, uintptr_t stream);
+
+PB_API const char* pb_strerror(int status);
+PB_API int pb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBITS_H */

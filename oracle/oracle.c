@@ -378,7 +378,7 @@ static int det_output(int op, int x) {
 typedef struct {
   int n, d, ng;
   const orc_gate* g;
-  int8_t* gate_of; /* [d][n]: index of the gate on (layer, qubit) or -1 */
+  int32_t* gate_of; /* [d][n]: index of the gate on (layer, qubit) or -1 */
 } orc_net;
 
 /* Number of violated output bits of layer L (s_L -> s_{L+1}). */
@@ -437,12 +437,12 @@ static int pbit_colour(const orc_net* net, int k, int q) {
 
 int orc_colour(int n, int d, const orc_gate* g, int ng, int32_t* colour) {
   if (check_circuit(n, d, g, ng) != 0) return -1;
-  orc_net net = {n, d, ng, g, (int8_t*)malloc((size_t)n * d)};
+  orc_net net = {n, d, ng, g, (int32_t*)malloc((size_t)n * d * sizeof(int32_t))};
   if (!net.gate_of) return -3;
-  memset(net.gate_of, -1, (size_t)n * d);
+  memset(net.gate_of, -1, (size_t)n * d * sizeof(int32_t));
   for (int i = 0; i < ng; ++i) {
-    net.gate_of[g[i].layer * n + g[i].q0] = (int8_t)i;
-    if (gate_arity(g[i].op) == 2) net.gate_of[g[i].layer * n + g[i].q1] = (int8_t)i;
+    net.gate_of[g[i].layer * n + g[i].q0] = i;
+    if (gate_arity(g[i].op) == 2) net.gate_of[g[i].layer * n + g[i].q1] = i;
   }
   for (int k = 1; k <= d; ++k)
     for (int q = 0; q < n; ++q) colour[(k - 1) * n + q] = pbit_colour(&net, k, q);
@@ -512,12 +512,12 @@ int orc_gibbs(int n, int d, const orc_gate* g, int ng, uint32_t beta, double J,
   if (!alphas && n > 24) return -2;
   uint32_t thr[4];
   if (orc_thresholds(J, thr) != 0) return -1;
-  orc_net net = {n, d, ng, g, (int8_t*)malloc((size_t)n * d)};
+  orc_net net = {n, d, ng, g, (int32_t*)malloc((size_t)n * d * sizeof(int32_t))};
   if (!net.gate_of) return -3;
-  memset(net.gate_of, -1, (size_t)n * d);
+  memset(net.gate_of, -1, (size_t)n * d * sizeof(int32_t));
   for (int i = 0; i < ng; ++i) {
-    net.gate_of[g[i].layer * n + g[i].q0] = (int8_t)i;
-    if (gate_arity(g[i].op) == 2) net.gate_of[g[i].layer * n + g[i].q1] = (int8_t)i;
+    net.gate_of[g[i].layer * n + g[i].q0] = i;
+    if (gate_arity(g[i].op) == 2) net.gate_of[g[i].layer * n + g[i].q1] = i;
   }
   const uint32_t nmask = (n == 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
   const uint64_t bins = alphas ? (uint64_t)n_alphas : (1ull << n);
@@ -616,12 +616,12 @@ int orc_gibbs(int n, int d, const orc_gate* g, int ng, uint32_t beta, double J,
 int orc_violations(int n, int d, const orc_gate* g, int ng, uint32_t beta,
                    uint32_t chains, const uint32_t* state, int32_t* viol) {
   if (check_circuit(n, d, g, ng) != 0) return -1;
-  orc_net net = {n, d, ng, g, (int8_t*)malloc((size_t)n * d)};
+  orc_net net = {n, d, ng, g, (int32_t*)malloc((size_t)n * d * sizeof(int32_t))};
   if (!net.gate_of) return -3;
-  memset(net.gate_of, -1, (size_t)n * d);
+  memset(net.gate_of, -1, (size_t)n * d * sizeof(int32_t));
   for (int i = 0; i < ng; ++i) {
-    net.gate_of[g[i].layer * n + g[i].q0] = (int8_t)i;
-    if (gate_arity(g[i].op) == 2) net.gate_of[g[i].layer * n + g[i].q1] = (int8_t)i;
+    net.gate_of[g[i].layer * n + g[i].q0] = i;
+    if (gate_arity(g[i].op) == 2) net.gate_of[g[i].layer * n + g[i].q1] = i;
   }
   uint32_t* s = (uint32_t*)calloc((size_t)d + 1, sizeof(uint32_t));
   const uint32_t nmask = (n == 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
@@ -641,7 +641,7 @@ int orc_path_phase(int n, int d, const orc_gate* g, int ng, uint32_t beta,
                    const uint32_t* s1_to_sd) {
   if (check_circuit(n, d, g, ng) != 0) return -2;
   uint32_t* s = (uint32_t*)calloc((size_t)d + 1, sizeof(uint32_t));
-  int8_t* gate_of = (int8_t*)malloc((size_t)n * d);
+  int32_t* gate_of = (int32_t*)malloc((size_t)n * d * sizeof(int32_t));
   memset(gate_of, -1, (size_t)n * d);
   orc_net net = {n, d, ng, g, gate_of};
   s[0] = beta;

@@ -1,0 +1,83 @@
+// Internal layout shared by the host compiler, the runtime and the kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "pbits.h"
+
+namespace pb {
+
+// Word indices in a chain group's shared-memory image: layer k word q sits
+// at k*n + q (k = 0 is the clamped input), followed by a zero word and an
+// all-ones word.
+__host__ __device__ inline int zero_idx(int n, int d) { return (d + 1) * n; }
+__host__ __device__ inline int ones_idx(int n, int d) { return (d + 1) * n + 1; }
+__host__ __device__ inline int n_words(int n, int d) { return (d + 1) * n + 2; }
+
+// One p-bit update (16 bytes).  Link i (i < m) demands the value
+// r_i = W[a[i]] ^ W[b[i]]; the p-bit's violation count changes by
+// v = sum_i (1 - 2 r_i) when it goes 0 -> 1.
+struct Desc {
+  uint16_t dst;   // word index of the p-bit (k*n + q)
+  uint8_t mflag;  // bits 0-1: m (links), bit 2: link 0 is the p-bit's own link
+  uint8_t pair;   // threshold pair: 0 (t0,t0) 1 (t1,t1) 2 (t2,t0) 3 (t3,t1)
+  uint16_t a[3];
+  uint16_t b[3];
+};
+static_assert(sizeof(Desc) == 16, "Desc must be 16 bytes");
+
+// Record term of one p-bit (16 bytes): violation word W[vd]^W[va]^W[vb]
+// (all ZERO when the p-bit has no own link) and phase term
+// w * (W[pa] & W[pb]) with w in {0, 1, 2, 4} units of pi/4.
+struct Rec {
+  uint16_t vd, va, vb;
+  uint16_t pa, pb;
+  uint16_t w;
+  uint16_t pad[2];
+};
+static_assert(sizeof(Rec) == 16, "Rec must be 16 bytes");
+
+// Per-model device header (in the workspace).
+struct ModelDev {
+  int32_t n, d, nw;        // qubits, layers, words per group image
+  int32_t h;
+  uint32_t beta;
+  uint32_t thr[4];
+  int32_t col_off[5];      // descriptor ranges per colour class
+  int32_t max_col;         // largest colour class
+};
+
+// Per-model run entry (device), one per model of a run.
+struct RunModelDev {
+  const ModelDev* model;
+  const Desc* desc;        // n*d, ordered by colour class
+  const Rec* rec;          // n*d
+  uint32_t* state;         // groups * d * n words
+  unsigned long long* hist;     // n_batches * bins * 8
+  unsigned long long* valid;    // n_batches
+  unsigned long long* samples;  // n_batches
+  const uint32_t* alpha_sorted; // n_alphas (sorted)
+  const int32_t* alpha_slot;    // original position of each sorted alpha
+  double* amp;             // bins * 3 (re, im, se) output of the amplitude kernel
+  int32_t n_alphas;        // 0 = full histogram
+  uint32_t bins;
+  uint32_t chains, groups, n_batches;
+  uint32_t burn_in, record_every;
+  uint32_t seed_lo, seed_hi;
+  uint32_t group_base;     // first flat group index of this model in a launch
+  uint32_t pad;
+};
+
+// Workspace header at offset 0.
+struct WsHeader {
+  uint32_t status;         // 0 = ok, else a pb_status code set by a kernel
+  uint32_t work_next;      // persistent scheduler counter
+  uint32_t sweep0;         // absolute index of the next sweep
+  uint32_t pad[61];
+};
+
+constexpr uint32_t kTagSweep = 0;
+constexpr uint32_t kTagInit = 1;
+constexpr uint32_t kTagMH = 2;
+
+}  // namespace pb

@@ -1,0 +1,773 @@
+// Host side of the C ABI: the circuit compiler (gate list -> p-bit tables),
+// workspace layout, run objects, CUDA-graph replay and result read-back.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "pb_internal.h"
+
+namespace pb {
+cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
+                        const uint32_t* const* d_init_tabs, size_t smem_bytes, WsHeader* hdr,
+                        cudaStream_t st);
+cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
+                          uint32_t n_sweeps, int threads, size_t smem_bytes, WsHeader* hdr,
+                          cudaStream_t st);
+cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
+                                     uint32_t n_work, uint32_t n_sweeps, int threads, int grid,
+                                     size_t smem_bytes, WsHeader* hdr, cudaStream_t st);
+cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
+                              cudaStream_t st);
+cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t count,
+                               uint32_t* out, cudaStream_t st);
+size_t sweep_smem_bytes(int n, int d, int threads);
+cudaError_t sweep_prepare();
+int sweep_max_blocks_per_sm(int threads, size_t smem);
+}  // namespace pb
+
+using namespace pb;
+
+// ---------------------------------------------------------------------------
+// Compiled model (host).
+struct pb_model {
+  int n = 0, d = 0;
+  uint32_t beta = 0;
+  double J = 0.0;
+  uint32_t thr[4] = {0, 0, 0, 0};
+  int h = 0, M = 0, rank = 0;
+  int col_off[5] = {0, 0, 0, 0, 0};
+  std::vector<int32_t> colour;  // [d][n]
+  std::vector<Desc> desc;       // colour-ordered
+  std::vector<Rec> rec;         // by p = (k-1) n + q
+  std::vector<uint32_t> init;   // by p: 0xFFFFFFFF = H output, else a | b << 16
+  std::vector<pb_gate> gates;
+};
+
+namespace {
+
+// Gate occupying (layer, qubit): kind and partner / role.
+struct Slot {
+  int op = -1;       // -1 identity wire
+  int partner = -1;  // other qubit of a 2-qubit gate
+  bool target = false;  // CNOT target
+};
+
+// GF(2) rank of the rows (bitsets over the H variables), by inserting each
+// row into an XOR basis keyed by its highest set bit.
+int gf2_rank_rows(const std::vector<std::vector<uint64_t>>& rows, int nbits) {
+  const int nw = (nbits + 63) / 64;
+  std::vector<std::vector<uint64_t>> basis(nbits);
+  std::vector<bool> have(nbits, false);
+  int rank = 0;
+  for (auto row : rows) {
+    row.resize(nw, 0);
+    for (int b = nbits - 1; b >= 0; --b) {
+      if (!((row[b >> 6] >> (b & 63)) & 1ull)) continue;
+      if (!have[b]) {
+        basis[b] = row;
+        have[b] = true;
+        ++rank;
+        break;
+      }
+      for (int w = 0; w < nw; ++w) row[w] ^= basis[b][w];
+    }
+  }
+  return rank;
+}
+
+}  // namespace
+
+extern "C" {
+
+PB_API int pb_version(void) { return 1; }
+
+PB_API const char* pb_strerror(int s) {
+  switch (s) {
+    case PB_OK: return "ok";
+    case PB_EINVAL: return "invalid argument";
+    case PB_ERANGE: return "size out of range";
+    case PB_ENOMEM: return "out of host memory";
+    case PB_ECUDA: return "CUDA runtime error";
+    case PB_ETIMEOUT: return "device wait timed out";
+    case PB_ESTATE: return "invalid state for this call";
+  }
+  return "unknown status";
+}
+
+PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t input_bits,
+                      double J, pb_model** out) {
+  if (!out) return PB_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n > 32 || d < 1 || d > 64) return PB_ERANGE;
+  if (n_gates < 0 || (n_gates > 0 && !gates)) return PB_EINVAL;
+  if (!(J >= 0.0) || !std::isfinite(J)) return PB_EINVAL;
+  if (n < 32 && (input_bits >> n) != 0) return PB_EINVAL;
+
+  std::vector<Slot> slot((size_t)d * n);
+  for (int i = 0; i < n_gates; ++i) {
+    const pb_gate& g = gates[i];
+    if (g.op < PB_H || g.op > PB_CZ || g.layer < 0 || g.layer >= d) return PB_EINVAL;
+    if (g.q0 < 0 || g.q0 >= n) return PB_EINVAL;
+    const bool two = g.op == PB_CNOT || g.op == PB_CZ;
+    if (two && (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0)) return PB_EINVAL;
+    Slot& s0 = slot[(size_t)g.layer * n + g.q0];
+    if (s0.op != -1) return PB_EINVAL;
+    s0.op = g.op;
+    if (two) {
+      Slot& s1 = slot[(size_t)g.layer * n + g.q1];
+      if (s1.op != -1) return PB_EINVAL;
+      s0.partner = g.q1;
+      s1.op = g.op;
+      s1.partner = g.q0;
+      s1.target = (g.op == PB_CNOT);
+    }
+  }
+
+  std::unique_ptr<pb_model> m(new (std::nothrow) pb_model);
+  if (!m) return PB_ENOMEM;
+  m->n = n;
+  m->d = d;
+  m->beta = input_bits;
+  m->J = J;
+  m->gates.assign(gates, gates + n_gates);
+  // Heat-bath thresholds: P(1) = 1 / (1 + e^{J v}) for a violation change v.
+  m->thr[0] = 0x80000000u;
+  for (int v = 1; v <= 3; ++v) {
+    double t = std::floor(4294967296.0 / (1.0 + std::exp(J * (double)v)));
+    m->thr[v] = (uint32_t)std::min(t, 4294967295.0);
+  }
+
+  const uint16_t Z = (uint16_t)zero_idx(n, d), O = (uint16_t)ones_idx(n, d);
+  auto at = [&](int layer, int q) -> const Slot& { return slot[(size_t)layer * n + q]; };
+  auto word = [&](int k, int q) -> uint16_t { return (uint16_t)(k * n + q); };
+
+  const int npb = n * d;
+  std::vector<Desc> by_p(npb);
+  m->rec.assign(npb, Rec{});
+  m->init.assign(npb, 0xFFFFFFFFu);
+  m->colour.assign(npb, 0);
+  for (int k = 1; k <= d; ++k) {
+    for (int q = 0; q < n; ++q) {
+      const int p = (k - 1) * n + q;
+      Desc D;
+      D.dst = word(k, q);
+      for (int l = 0; l < 3; ++l) { D.a[l] = Z; D.b[l] = Z; }
+      int m_links = 0;
+      bool own = false;
+      // own link: gate layer k-1 produces s_k
+      const Slot& prod = at(k - 1, q);
+      if (prod.op != PB_H) {
+        own = true;
+        D.a[m_links] = word(k - 1, q);
+        D.b[m_links] = (prod.op == PB_CNOT && prod.target) ? word(k - 1, prod.partner) : Z;
+        ++m_links;
+      }
+      bool tgt_next = false;
+      if (k < d) {
+        const Slot& cons = at(k, q);  // gate layer k consumes s_k
+        if (cons.op != PB_H) {        // the wire's next bit demands s_k[q]
+          D.a[m_links] = word(k + 1, q);
+          D.b[m_links] = (cons.op == PB_CNOT && cons.target) ? word(k, cons.partner) : Z;
+          ++m_links;
+        }
+        if (cons.op == PB_CNOT && !cons.target) {  // control: the target's next bit
+          D.a[m_links] = word(k + 1, cons.partner);
+          D.b[m_links] = word(k, cons.partner);
+          ++m_links;
+        }
+        tgt_next = cons.op == PB_CNOT && cons.target;
+      }
+      D.mflag = (uint8_t)(m_links | (own ? 4 : 0));
+      static const uint8_t pair_of_m[4] = {0, 1, 2, 3};
+      D.pair = pair_of_m[m_links];
+      by_p[p] = D;
+      m->colour[p] = 2 * ((k % 2) == 0) + (tgt_next ? 1 : 0);
+
+      Rec R{};
+      R.vd = R.va = R.vb = Z;
+      R.pa = R.pb = Z;
+      R.w = 0;
+      if (own) {
+        R.vd = D.dst;
+        R.va = D.a[0];
+        R.vb = D.b[0];
+        m->init[p] = (uint32_t)D.a[0] | ((uint32_t)D.b[0] << 16);
+      }
+      switch (prod.op) {
+        case PB_H: R.w = 4; R.pa = word(k - 1, q); R.pb = word(k, q); break;
+        case PB_S: R.w = 2; R.pa = word(k - 1, q); R.pb = O; break;
+        case PB_T: R.w = 1; R.pa = word(k - 1, q); R.pb = O; break;
+        case PB_CZ:
+          if (q < prod.partner) { R.w = 4; R.pa = word(k - 1, q); R.pb = word(k - 1, prod.partner); }
+          break;
+        default: break;
+      }
+      m->rec[p] = R;
+    }
+  }
+  // colour-ordered descriptors
+  for (int c = 0; c < 4; ++c) {
+    m->col_off[c] = (int)m->desc.size();
+    for (int p = 0; p < npb; ++p)
+      if (m->colour[p] == c) m->desc.push_back(by_p[p]);
+  }
+  m->col_off[4] = (int)m->desc.size();
+
+  // h, M and the GF(2) rank of H outputs -> s_d
+  int h = 0;
+  for (int i = 0; i < n_gates; ++i) h += gates[i].op == PB_H;
+  m->h = h;
+  m->M = npb - h;
+  {
+    std::vector<std::vector<uint64_t>> wire(n, std::vector<uint64_t>((h + 63) / 64 + 1, 0));
+    int var = 0;
+    for (int L = 0; L < d; ++L) {
+      std::vector<std::vector<uint64_t>> nxt = wire;
+      for (int q = 0; q < n; ++q) {
+        const Slot& s = at(L, q);
+        if (s.op == PB_H) {
+          std::fill(nxt[q].begin(), nxt[q].end(), 0);
+          nxt[q][var >> 6] |= 1ull << (var & 63);
+          ++var;
+        } else if (s.op == PB_CNOT && s.target) {
+          for (size_t w = 0; w < nxt[q].size(); ++w) nxt[q][w] = wire[q][w] ^ wire[s.partner][w];
+        }
+      }
+      wire.swap(nxt);
+    }
+    m->rank = h > 0 ? gf2_rank_rows(wire, h) : 0;
+  }
+  *out = m.release();
+  return PB_OK;
+}
+
+PB_API int pb_model_info(const pb_model* m, pb_model_info_t* info) {
+  if (!m || !info) return PB_EINVAL;
+  info->n = m->n;
+  info->d = m->d;
+  info->n_pbits = m->n * (m->d + 1);
+  info->h = m->h;
+  info->M = m->M;
+  info->rank = m->rank;
+  info->J = m->J;
+  info->input_bits = m->beta;
+  for (int i = 0; i < 4; ++i) {
+    info->thr[i] = m->thr[i];
+    info->colour_size[i] = m->col_off[i + 1] - m->col_off[i];
+  }
+  return PB_OK;
+}
+
+PB_API int pb_model_colours(const pb_model* m, int32_t* colour) {
+  if (!m || !colour) return PB_EINVAL;
+  std::memcpy(colour, m->colour.data(), m->colour.size() * sizeof(int32_t));
+  return PB_OK;
+}
+
+PB_API void pb_model_free(pb_model* m) { delete m; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Runs.
+namespace {
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
+
+struct ModelSlots {
+  size_t model_dev, desc, rec, init, state, hist, valid, samples, alpha_sorted, alpha_slot, amp;
+  uint32_t bins, groups, n_batches;
+};
+
+struct Layout {
+  size_t hdr = 0, rm = 0, init_ptrs = 0, work = 0, total = 0;
+  std::vector<ModelSlots> ms;
+};
+
+int check_cfg(const pb_model* m, const pb_run_cfg& c) {
+  if (!m) return PB_EINVAL;
+  if (c.chains == 0 || c.record_every == 0) return PB_EINVAL;
+  if (c.sampler != PB_GIBBS) return PB_EINVAL;  // the learned sampler has its own entry points
+  if (c.alphas == nullptr) {
+    if (c.n_alphas != 0) return PB_EINVAL;
+    if (m->n > 22) return PB_ERANGE;
+  } else {
+    if (c.n_alphas <= 0) return PB_EINVAL;
+    for (int i = 0; i < c.n_alphas; ++i)
+      if (m->n < 32 && (c.alphas[i] >> m->n) != 0) return PB_EINVAL;
+  }
+  return PB_OK;
+}
+
+uint32_t auto_batches(uint32_t groups, uint32_t bins) {
+  uint32_t b = std::min<uint32_t>(groups, 32);
+  // keep the per-batch histograms within 64 MiB
+  while (b > 1 && (uint64_t)b * bins * 64 > (64ull << 20)) b >>= 1;
+  return std::max<uint32_t>(b, 1);
+}
+
+int plan(pb_model* const* models, const pb_run_cfg* cfgs, int nm, Layout& L) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = align_up(off, 256);
+    size_t at = off;
+    off += std::max<size_t>(bytes, 1);
+    return at;
+  };
+  L.hdr = take(sizeof(WsHeader));
+  L.rm = take(sizeof(RunModelDev) * nm);
+  L.init_ptrs = take(sizeof(uint32_t*) * nm);
+  uint32_t total_groups = 0;
+  L.ms.resize(nm);
+  for (int i = 0; i < nm; ++i) {
+    const pb_model* m = models[i];
+    const pb_run_cfg& c = cfgs[i];
+    int rc = check_cfg(m, c);
+    if (rc != PB_OK) return rc;
+    ModelSlots& s = L.ms[i];
+    const size_t npb = (size_t)m->n * m->d;
+    s.groups = (c.chains + 31) / 32;
+    s.bins = c.alphas ? (uint32_t)c.n_alphas : (1u << m->n);
+    s.n_batches = c.n_batches ? std::min<uint32_t>(c.n_batches, s.groups) : auto_batches(s.groups, s.bins);
+    total_groups += s.groups;
+    s.model_dev = take(sizeof(ModelDev));
+    s.desc = take(npb * sizeof(Desc));
+    s.rec = take(npb * sizeof(Rec));
+    s.init = take(npb * sizeof(uint32_t));
+    s.state = take((size_t)s.groups * npb * 4);
+    s.hist = take((size_t)s.n_batches * s.bins * 8 * 8);
+    s.valid = take((size_t)s.n_batches * 8);
+    s.samples = take((size_t)s.n_batches * 8);
+    s.alpha_sorted = take((size_t)(c.alphas ? c.n_alphas : 0) * 4);
+    s.alpha_slot = take((size_t)(c.alphas ? c.n_alphas : 0) * 4);
+    s.amp = take((size_t)s.bins * 3 * 8);
+  }
+  L.work = take((size_t)total_groups * 4);
+  L.total = align_up(off, 256);
+  return PB_OK;
+}
+
+}  // namespace
+
+struct pb_run {
+  cudaStream_t st = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int nm = 0;
+  std::vector<std::shared_ptr<pb_model>> models;  // private copies
+  std::vector<pb_run_cfg> cfgs;
+  Layout L;
+  std::vector<RunModelDev> rm;
+  uint32_t total_groups = 0;
+  int threads = 32;
+  size_t smem = 0;
+  bool persistent = false;
+  int grid = 0;
+  uint64_t sweeps_done = 0;
+  double flips_per_sweep = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  double last_flips = 0.0;
+  std::map<uint32_t, cudaGraphExec_t> graphs;
+  WsHeader* hdr() const { return reinterpret_cast<WsHeader*>(ws + L.hdr); }
+  RunModelDev* d_rm() const { return reinterpret_cast<RunModelDev*>(ws + L.rm); }
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? PB_OK : PB_ECUDA; }
+
+// Launch shape: threads per CTA = the largest colour class rounded up to a
+// warp (one p-bit per thread per class), capped at 256; environment override
+// PB_THREADS; persistent scheduling for batched runs.
+void choose_shape(pb_run* r) {
+  int maxcol = 1;
+  int maxn = 1, maxd = 1;
+  for (auto& m : r->models) {
+    for (int c = 0; c < 4; ++c) maxcol = std::max(maxcol, m->col_off[c + 1] - m->col_off[c]);
+    maxn = std::max(maxn, m->n);
+    maxd = std::max(maxd, m->d);
+  }
+  int t = ((maxcol + 31) / 32) * 32;
+  t = std::max(32, std::min(256, t));
+  if (const char* e = std::getenv("PB_THREADS")) {
+    int v = std::atoi(e);
+    if (v >= 32 && v <= 1024 && v % 32 == 0) t = v;
+  }
+  r->threads = t;
+  size_t smem = 0;
+  for (auto& m : r->models) smem = std::max(smem, sweep_smem_bytes(m->n, m->d, t));
+  r->smem = smem;
+  r->persistent = r->nm > 1;
+  if (const char* e = std::getenv("PB_PERSISTENT")) r->persistent = std::atoi(e) != 0;
+  if (r->persistent) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = sweep_max_blocks_per_sm(t, smem);
+    r->grid = std::max(1, sms * std::max(1, per_sm));
+    r->grid = (int)std::min<uint32_t>((uint32_t)r->grid, r->total_groups);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+PB_API int pb_workspace_bytes(pb_model* const* models, const pb_run_cfg* cfgs, int n_models,
+                              size_t* bytes) {
+  if (!models || !cfgs || n_models < 1 || !bytes) return PB_EINVAL;
+  Layout L;
+  int rc = plan(models, cfgs, n_models, L);
+  if (rc != PB_OK) return rc;
+  *bytes = L.total;
+  return PB_OK;
+}
+
+PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_models,
+                         void* d_workspace, size_t workspace_bytes, uintptr_t stream,
+                         pb_run** out) {
+  if (!out) return PB_EINVAL;
+  *out = nullptr;
+  if (!models || !cfgs || n_models < 1 || !d_workspace) return PB_EINVAL;
+  if (((uintptr_t)d_workspace & 255u) != 0) return PB_EINVAL;
+  std::unique_ptr<pb_run> r(new (std::nothrow) pb_run);
+  if (!r) return PB_ENOMEM;
+  int rc = plan(models, cfgs, n_models, r->L);
+  if (rc != PB_OK) return rc;
+  if (workspace_bytes < r->L.total) return PB_ERANGE;
+  r->st = reinterpret_cast<cudaStream_t>(stream);
+  r->ws = static_cast<char*>(d_workspace);
+  r->ws_bytes = workspace_bytes;
+  r->nm = n_models;
+  r->cfgs.assign(cfgs, cfgs + n_models);
+  for (int i = 0; i < n_models; ++i) r->models.emplace_back(new pb_model(*models[i]));
+
+  cudaStream_t st = r->st;
+  char* ws = r->ws;
+  // Zero the header and every counter; tables are uploaded below.
+  cudaError_t e = cudaMemsetAsync(ws, 0, r->L.total, st);
+  if (e != cudaSuccess) return PB_ECUDA;
+
+  std::vector<const uint32_t*> init_ptrs(n_models);
+  std::vector<uint32_t> work;
+  std::vector<std::pair<double, uint32_t>> cost;
+  uint32_t base = 0;
+  r->rm.resize(n_models);
+  std::vector<std::vector<uint32_t>> sorted_alpha(n_models);
+  std::vector<std::vector<int32_t>> slot_alpha(n_models);
+  for (int i = 0; i < n_models; ++i) {
+    const pb_model& m = *r->models[i];
+    const pb_run_cfg& c = r->cfgs[i];
+    const ModelSlots& s = r->L.ms[i];
+    ModelDev md{};
+    md.n = m.n;
+    md.d = m.d;
+    md.nw = n_words(m.n, m.d);
+    md.h = m.h;
+    md.beta = m.beta;
+    for (int k = 0; k < 4; ++k) md.thr[k] = m.thr[k];
+    for (int k = 0; k < 5; ++k) md.col_off[k] = m.col_off[k];
+    md.max_col = 0;
+    for (int k = 0; k < 4; ++k) md.max_col = std::max(md.max_col, m.col_off[k + 1] - m.col_off[k]);
+    const size_t npb = (size_t)m.n * m.d;
+    if ((e = cudaMemcpyAsync(ws + s.model_dev, &md, sizeof md, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(ws + s.desc, m.desc.data(), npb * sizeof(Desc), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(ws + s.rec, m.rec.data(), npb * sizeof(Rec), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(ws + s.init, m.init.data(), npb * 4, cudaMemcpyHostToDevice, st)))
+      return PB_ECUDA;
+    if (c.alphas) {
+      std::vector<int32_t> idx(c.n_alphas);
+      std::iota(idx.begin(), idx.end(), 0);
+      std::stable_sort(idx.begin(), idx.end(),
+                       [&](int a, int b) { return c.alphas[a] < c.alphas[b]; });
+      for (int k = 0; k < c.n_alphas; ++k) {
+        sorted_alpha[i].push_back(c.alphas[idx[k]]);
+        slot_alpha[i].push_back(idx[k]);
+      }
+      // a repeated alpha would split its counts; reject it
+      for (int k = 1; k < c.n_alphas; ++k)
+        if (sorted_alpha[i][k] == sorted_alpha[i][k - 1]) return PB_EINVAL;
+      if ((e = cudaMemcpyAsync(ws + s.alpha_sorted, sorted_alpha[i].data(), c.n_alphas * 4,
+                               cudaMemcpyHostToDevice, st)) ||
+          (e = cudaMemcpyAsync(ws + s.alpha_slot, slot_alpha[i].data(), c.n_alphas * 4,
+                               cudaMemcpyHostToDevice, st)))
+        return PB_ECUDA;
+    }
+    RunModelDev& d = r->rm[i];
+    std::memset(&d, 0, sizeof d);
+    d.model = reinterpret_cast<const ModelDev*>(ws + s.model_dev);
+    d.desc = reinterpret_cast<const Desc*>(ws + s.desc);
+    d.rec = reinterpret_cast<const Rec*>(ws + s.rec);
+    d.state = reinterpret_cast<uint32_t*>(ws + s.state);
+    d.hist = reinterpret_cast<unsigned long long*>(ws + s.hist);
+    d.valid = reinterpret_cast<unsigned long long*>(ws + s.valid);
+    d.samples = reinterpret_cast<unsigned long long*>(ws + s.samples);
+    d.alpha_sorted = reinterpret_cast<const uint32_t*>(ws + s.alpha_sorted);
+    d.alpha_slot = reinterpret_cast<const int32_t*>(ws + s.alpha_slot);
+    d.amp = reinterpret_cast<double*>(ws + s.amp);
+    d.n_alphas = c.alphas ? c.n_alphas : 0;
+    d.bins = s.bins;
+    d.chains = c.chains;
+    d.groups = s.groups;
+    d.n_batches = s.n_batches;
+    d.burn_in = c.burn_in;
+    d.record_every = c.record_every;
+    d.seed_lo = (uint32_t)c.seed;
+    d.seed_hi = (uint32_t)(c.seed >> 32);
+    d.group_base = base;
+    init_ptrs[i] = reinterpret_cast<const uint32_t*>(ws + s.init);
+    for (uint32_t g = 0; g < s.groups; ++g) cost.push_back({(double)npb, base + g});
+    base += s.groups;
+    r->flips_per_sweep += (double)c.chains * (double)npb;
+  }
+  r->total_groups = base;
+  // Work list for the persistent launch: longest first (LPT order).
+  std::stable_sort(cost.begin(), cost.end(),
+                   [](const std::pair<double, uint32_t>& a, const std::pair<double, uint32_t>& b) {
+                     return a.first > b.first;
+                   });
+  for (auto& c : cost) work.push_back(c.second);
+  if ((e = cudaMemcpyAsync(ws + r->L.rm, r->rm.data(), sizeof(RunModelDev) * n_models,
+                           cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(ws + r->L.init_ptrs, init_ptrs.data(), sizeof(uint32_t*) * n_models,
+                           cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(ws + r->L.work, work.data(), work.size() * 4, cudaMemcpyHostToDevice, st)))
+    return PB_ECUDA;
+  if (sweep_prepare() != cudaSuccess) return PB_ECUDA;
+  choose_shape(r.get());
+  size_t init_smem = 0;
+  for (auto& m : r->models) init_smem = std::max(init_smem, (size_t)n_words(m->n, m->d) * 4);
+  e = launch_init(r->d_rm(), n_models, r->total_groups,
+                  reinterpret_cast<const uint32_t* const*>(ws + r->L.init_ptrs), init_smem,
+                  r->hdr(), st);
+  if (e != cudaSuccess) return PB_ECUDA;
+  // host copies must outlive the (possibly staged) async copies
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return PB_ECUDA;
+  if (cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess)
+    return PB_ECUDA;
+  *out = r.release();
+  return PB_OK;
+}
+
+PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
+  if (!r) return PB_EINVAL;
+  if (n_sweeps == 0) return PB_OK;
+  if (r->sweeps_done + n_sweeps > 0xFFFFFFFFull) return PB_ERANGE;
+  cudaGraphExec_t exec = nullptr;
+  auto it = r->graphs.find(n_sweeps);
+  if (it != r->graphs.end()) {
+    exec = it->second;
+  } else {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(r->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return PB_ECUDA;
+    if (r->persistent)
+      e = launch_sweeps_persistent(r->d_rm(), r->nm, reinterpret_cast<const uint32_t*>(r->ws + r->L.work),
+                                   r->total_groups, n_sweeps, r->threads, r->grid, r->smem, r->hdr(),
+                                   r->st);
+    else
+      e = launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->threads, r->smem, r->hdr(),
+                        r->st);
+    cudaError_t e2 = cudaStreamEndCapture(r->st, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return PB_ECUDA;
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return PB_ECUDA;
+    r->graphs[n_sweeps] = exec;
+  }
+  cudaEventRecord(r->ev0, r->st);
+  cudaError_t e = cudaGraphLaunch(exec, r->st);
+  cudaEventRecord(r->ev1, r->st);
+  if (e != cudaSuccess) return PB_ECUDA;
+  r->sweeps_done += n_sweeps;
+  r->timed = true;
+  r->last_flips = r->flips_per_sweep * n_sweeps;
+  return PB_OK;
+}
+
+PB_API int pb_run_wait(pb_run* r) {
+  if (!r) return PB_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(r->st);
+  if (e != cudaSuccess) return PB_ECUDA;
+  uint32_t status = 0;
+  e = cudaMemcpy(&status, &r->hdr()->status, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return PB_ECUDA;
+  return status == 0 ? PB_OK : (int)status;
+}
+
+PB_API int pb_run_histogram(const pb_run* r, int model, uint64_t* counts, uint64_t* valid_total,
+                            uint64_t* samples_total) {
+  if (!r || model < 0 || model >= r->nm) return PB_EINVAL;
+  const ModelSlots& s = r->L.ms[model];
+  if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
+  if (counts) {
+    std::vector<uint64_t> h((size_t)s.n_batches * s.bins * 8);
+    if (cudaMemcpy(h.data(), r->ws + s.hist, h.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return PB_ECUDA;
+    std::memset(counts, 0, (size_t)s.bins * 8 * 8);
+    for (uint32_t b = 0; b < s.n_batches; ++b)
+      for (size_t i = 0; i < (size_t)s.bins * 8; ++i) counts[i] += h[(size_t)b * s.bins * 8 + i];
+  }
+  std::vector<uint64_t> v(s.n_batches);
+  if (valid_total) {
+    if (cudaMemcpy(v.data(), r->ws + s.valid, s.n_batches * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return PB_ECUDA;
+    *valid_total = std::accumulate(v.begin(), v.end(), (uint64_t)0);
+  }
+  if (samples_total) {
+    if (cudaMemcpy(v.data(), r->ws + s.samples, s.n_batches * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return PB_ECUDA;
+    *samples_total = std::accumulate(v.begin(), v.end(), (uint64_t)0);
+  }
+  return PB_OK;
+}
+
+PB_API int pb_run_amplitudes(const pb_run* r, int model, int l2_normalize, double* re, double* im,
+                             double* se) {
+  if (!r || model < 0 || model >= r->nm || !re || !im) return PB_EINVAL;
+  const ModelSlots& s = r->L.ms[model];
+  cudaError_t e = launch_amplitudes(r->d_rm(), model, s.bins, l2_normalize, r->st);
+  if (e != cudaSuccess) return PB_ECUDA;
+  std::vector<double> a((size_t)s.bins * 3);
+  e = cudaMemcpyAsync(a.data(), r->ws + s.amp, a.size() * 8, cudaMemcpyDeviceToHost, r->st);
+  if (e != cudaSuccess) return PB_ECUDA;
+  if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
+  for (uint32_t i = 0; i < s.bins; ++i) {
+    re[i] = a[(size_t)i * 3];
+    im[i] = a[(size_t)i * 3 + 1];
+    if (se) se[i] = a[(size_t)i * 3 + 2];
+  }
+  return PB_OK;
+}
+
+PB_API int pb_run_get_state(const pb_run* r, int model, uint32_t* words, size_t bytes) {
+  if (!r || model < 0 || model >= r->nm || !words) return PB_EINVAL;
+  const ModelSlots& s = r->L.ms[model];
+  const size_t need = (size_t)s.groups * r->models[model]->n * r->models[model]->d * 4;
+  if (bytes < need) return PB_ERANGE;
+  if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
+  return cuda_status(cudaMemcpy(words, r->ws + s.state, need, cudaMemcpyDeviceToHost));
+}
+
+PB_API int pb_run_set_state(pb_run* r, int model, const uint32_t* words, size_t bytes) {
+  if (!r || model < 0 || model >= r->nm || !words) return PB_EINVAL;
+  const ModelSlots& s = r->L.ms[model];
+  const size_t need = (size_t)s.groups * r->models[model]->n * r->models[model]->d * 4;
+  if (bytes < need) return PB_ERANGE;
+  if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
+  return cuda_status(cudaMemcpy(r->ws + s.state, words, need, cudaMemcpyHostToDevice));
+}
+
+PB_API int pb_run_stats(pb_run* r, pb_run_stats_t* st) {
+  if (!r || !st) return PB_EINVAL;
+  st->sweeps_done = r->sweeps_done;
+  st->flips = r->flips_per_sweep * (double)r->sweeps_done;
+  st->last_ms = 0.0;
+  st->flips_per_s = 0.0;
+  if (r->timed) {
+    if (cudaEventSynchronize(r->ev1) != cudaSuccess) return PB_ECUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r->ev0, r->ev1) != cudaSuccess) return PB_ECUDA;
+    st->last_ms = ms;
+    st->flips_per_s = ms > 0 ? r->last_flips / (ms * 1e-3) : 0.0;
+  }
+  return PB_OK;
+}
+
+// Checkpoint blob: magic, sweep index, then per model: state, hist, valid, samples.
+PB_API int pb_run_checkpoint(const pb_run* r, void* host_buf, size_t bytes, size_t* bytes_needed) {
+  if (!r) return PB_EINVAL;
+  size_t need = 16;
+  for (int i = 0; i < r->nm; ++i) {
+    const ModelSlots& s = r->L.ms[i];
+    need += (size_t)s.groups * r->models[i]->n * r->models[i]->d * 4 +
+            (size_t)s.n_batches * s.bins * 64 + (size_t)s.n_batches * 16;
+  }
+  if (bytes_needed) *bytes_needed = need;
+  if (!host_buf) return PB_OK;
+  if (bytes < need) return PB_ERANGE;
+  if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
+  char* p = static_cast<char*>(host_buf);
+  uint64_t magic = 0x706269747343504bull;  // "pbitsCPK"
+  std::memcpy(p, &magic, 8);
+  uint64_t sw = r->sweeps_done;
+  std::memcpy(p + 8, &sw, 8);
+  p += 16;
+  for (int i = 0; i < r->nm; ++i) {
+    const ModelSlots& s = r->L.ms[i];
+    const size_t sb = (size_t)s.groups * r->models[i]->n * r->models[i]->d * 4;
+    const size_t hb = (size_t)s.n_batches * s.bins * 64;
+    if (cudaMemcpy(p, r->ws + s.state, sb, cudaMemcpyDeviceToHost) != cudaSuccess) return PB_ECUDA;
+    p += sb;
+    if (cudaMemcpy(p, r->ws + s.hist, hb, cudaMemcpyDeviceToHost) != cudaSuccess) return PB_ECUDA;
+    p += hb;
+    if (cudaMemcpy(p, r->ws + s.valid, s.n_batches * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PB_ECUDA;
+    p += s.n_batches * 8;
+    if (cudaMemcpy(p, r->ws + s.samples, s.n_batches * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PB_ECUDA;
+    p += s.n_batches * 8;
+  }
+  return PB_OK;
+}
+
+PB_API int pb_run_restore(pb_run* r, const void* host_buf, size_t bytes) {
+  if (!r || !host_buf) return PB_EINVAL;
+  size_t need = 0;
+  int rc = pb_run_checkpoint(r, nullptr, 0, &need);
+  if (rc != PB_OK) return rc;
+  if (bytes < need) return PB_ERANGE;
+  const char* p = static_cast<const char*>(host_buf);
+  uint64_t magic = 0, sw = 0;
+  std::memcpy(&magic, p, 8);
+  std::memcpy(&sw, p + 8, 8);
+  if (magic != 0x706269747343504bull || sw > 0xFFFFFFFFull) return PB_EINVAL;
+  p += 16;
+  if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
+  for (int i = 0; i < r->nm; ++i) {
+    const ModelSlots& s = r->L.ms[i];
+    const size_t sb = (size_t)s.groups * r->models[i]->n * r->models[i]->d * 4;
+    const size_t hb = (size_t)s.n_batches * s.bins * 64;
+    if (cudaMemcpy(r->ws + s.state, p, sb, cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;
+    p += sb;
+    if (cudaMemcpy(r->ws + s.hist, p, hb, cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;
+    p += hb;
+    if (cudaMemcpy(r->ws + s.valid, p, s.n_batches * 8, cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;
+    p += s.n_batches * 8;
+    if (cudaMemcpy(r->ws + s.samples, p, s.n_batches * 8, cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;
+    p += s.n_batches * 8;
+  }
+  uint32_t sw32 = (uint32_t)sw;
+  if (cudaMemcpy(&r->hdr()->sweep0, &sw32, 4, cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;
+  r->sweeps_done = sw;
+  return PB_OK;
+}
+
+PB_API void pb_run_free(pb_run* r) {
+  if (!r) return;
+  cudaStreamSynchronize(r->st);
+  for (auto& kv : r->graphs) cudaGraphExecDestroy(kv.second);
+  if (r->ev0) cudaEventDestroy(r->ev0);
+  if (r->ev1) cudaEventDestroy(r->ev1);
+  delete r;
+}
+
+PB_API int pb_philox_fill(const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t count,
+                          uint32_t* d_out, uintptr_t stream) {
+  if ((!d_ctr || !d_out) && count) return PB_EINVAL;
+  cudaError_t e = launch_philox_fill(d_ctr, k0, k1, count, d_out, reinterpret_cast<cudaStream_t>(stream));
+  return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,502 @@
+// Gibbs sweep, record and amplitude kernels (sm_103a).
+//
+// Layout: 32 chains are bit-sliced into one 32-bit word per p-bit (bit c =
+// chain 32 g + c of group g).  A CTA owns one group at a time and keeps the
+// group's image (all layers, (d+1) n words, plus a zero and an all-ones word)
+// in shared memory for the whole launch; global memory sees the image only at
+// the start and the end of a launch and the histogram atomics in between.
+//
+// One sweep = four colour classes in order (Fig. 2 Steps 1-2 for every p-bit);
+// p-bits of one class share no factor (the layer parity separates adjacent
+// layers, the second bit separates the control and target of a CNOT in the
+// next layer), so the threads of the CTA redraw a whole class in parallel.
+// After each recorded sweep the CTA evaluates every chain's validity and path
+// phase bit-sliced and adds one count to the bin (end state, phase class)
+// (Fig. 2 Step 3).
+#include <cuda_runtime.h>
+
+#include "pb_internal.h"
+#include "philox.cuh"
+
+namespace pb {
+
+// ---------------------------------------------------------------------------
+// Heat-bath draw for the 32 chains of one p-bit.
+//
+// Each chain compares its uniform u (bit 31-j = bit c of plane j) against a
+// threshold t chosen per chain between tA (lanes in `sel`) and tB.  The
+// comparison runs most significant plane first and stops as soon as every
+// lane is decided; lanes with t = 2^31 (`tail0`) are decided by plane 0.
+// Returns neg ^ [u < t].
+__device__ __forceinline__ uint32_t heat_bath_word(uint32_t neg, uint32_t sel, uint32_t tail0,
+                                                   uint32_t tA, uint32_t tB, uint32_t g,
+                                                   uint32_t sweep, uint32_t p, uint32_t k0,
+                                                   uint32_t k1) {
+  uint32_t lt = 0u, eq = ~0u;
+#pragma unroll 1
+  for (uint32_t grp = 0; grp < 8u; ++grp) {
+    const uint4 r = philox4x32_10(make_uint4(g, sweep, p, grp), k0, k1);
+    const uint32_t R[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (uint32_t w = 0; w < 4u; ++w) {
+      const uint32_t j = grp * 4u + w;
+      const uint32_t TA = (uint32_t)((int32_t)(tA << j) >> 31);
+      const uint32_t TB = (uint32_t)((int32_t)(tB << j) >> 31);
+      const uint32_t T = (sel & TA) | (~sel & TB);
+      lt |= eq & ~R[w] & T;
+      eq &= ~(R[w] ^ T);
+    }
+    eq &= ~tail0;
+    if (eq == 0u) break;
+  }
+  return neg ^ lt;
+}
+
+__device__ __forceinline__ void add3(uint32_t& f0, uint32_t& f1, uint32_t& f2, uint32_t x0,
+                                     uint32_t x1, uint32_t x2) {
+  const uint32_t c0 = f0 & x0;
+  f0 ^= x0;
+  const uint32_t t = f1 ^ x1;
+  const uint32_t c1 = (f1 & x1) | (c0 & t);
+  f1 = t ^ c0;
+  f2 ^= x2 ^ c1;
+}
+
+__device__ __forceinline__ int find_model(const RunModelDev* rm, int n_models, uint32_t flat) {
+  int lo = 0, hi = n_models - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rm[mid].group_base <= flat) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void set_status(WsHeader* hdr, int code) {
+  if (hdr) atomicCAS(&hdr->status, 0u, (uint32_t)code);
+}
+
+// Shared-memory image of one group: words, descriptors, record terms and the
+// reduction scratch.  Returns the byte count for (n, d, threads).
+__host__ __device__ inline size_t group_smem_bytes(int n, int d, int threads) {
+  const size_t words = ((size_t)n_words(n, d) + 3) & ~(size_t)3;
+  return words * 4 + (size_t)n * d * sizeof(Desc) + (size_t)n * d * sizeof(Rec) +
+         (size_t)(threads / 32) * 4 * sizeof(uint32_t);
+}
+
+// Runs `n_sweeps` sweeps (absolute indices sweep0...) of one chain group.
+__device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, uint32_t n_sweeps,
+                          uint32_t* smem, WsHeader* hdr) {
+  const ModelDev* mp = rm.model;
+  const int n = mp->n, d = mp->d, nw = mp->nw;
+  const int npb = n * d;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
+
+  uint32_t* W = smem;
+  Desc* sdesc = reinterpret_cast<Desc*>(smem + ((nw + 3) & ~3));
+  Rec* srec = reinterpret_cast<Rec*>(sdesc + npb);
+  uint32_t* red = reinterpret_cast<uint32_t*>(srec + npb);
+
+  // ---- load the group image and the tables
+  const uint32_t* gstate = rm.state + (size_t)g * npb;
+  for (int i = tid; i < nw; i += T) {
+    uint32_t v;
+    if (i < n) v = ((mp->beta >> i) & 1u) ? ~0u : 0u;        // clamped input layer
+    else if (i < (d + 1) * n) v = gstate[i - n];
+    else v = (i == zero_idx(n, d)) ? 0u : ~0u;
+    W[i] = v;
+  }
+  for (int i = tid; i < npb; i += T) {
+    Desc D = rm.desc[i];
+    bool ok = D.dst < nw;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) ok = ok && D.a[l] < nw && D.b[l] < nw;
+    if (!ok) {  // never write through a bad index: the entry is skipped
+      set_status(hdr, PB_EINVAL);
+      D.mflag = 0x80;
+    }
+    sdesc[i] = D;
+    Rec R = rm.rec[i];
+    if (R.vd >= nw || R.va >= nw || R.vb >= nw || R.pa >= nw || R.pb >= nw) {
+      set_status(hdr, PB_EINVAL);
+      R.vd = R.va = R.vb = R.pa = R.pb = (uint16_t)zero_idx(n, d);
+      R.w = 0;
+    }
+    srec[i] = R;
+  }
+  __syncthreads();
+
+  const uint32_t thr0 = mp->thr[0], thr1 = mp->thr[1], thr2 = mp->thr[2], thr3 = mp->thr[3];
+  const uint32_t k0 = rm.seed_lo, k1 = rm.seed_hi;
+  const uint32_t batch = g % rm.n_batches;
+
+  for (uint32_t s = 0; s < n_sweeps; ++s) {
+    const uint32_t sweep = sweep0 + s;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int c_hi = mp->col_off[c + 1];
+      for (int i = mp->col_off[c] + tid; i < c_hi; i += T) {
+        const Desc D = sdesc[i];
+        if (D.mflag & 0x80) continue;
+        const int m = D.mflag & 3;
+        const uint32_t r0 = W[D.a[0]] ^ W[D.b[0]];
+        const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
+        const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
+        uint32_t neg, sel, tail0, tA, tB;
+        if (m == 0) {
+          neg = 0u; sel = 0u; tail0 = ~0u; tA = thr0; tB = thr0;
+        } else if (m == 1) {
+          neg = r0; sel = 0u; tail0 = 0u; tA = thr1; tB = thr1;
+        } else if (m == 2) {
+          neg = r0 & r1; sel = ~(r0 ^ r1); tail0 = ~sel; tA = thr2; tB = thr0;
+        } else {
+          neg = (r0 & r1) | (r0 & r2) | (r1 & r2);
+          sel = ~(r0 ^ r1) & ~(r1 ^ r2);
+          tail0 = 0u; tA = thr3; tB = thr1;
+        }
+        const uint32_t p = (uint32_t)(D.dst - n) | (kTagSweep << 16);
+        W[D.dst] = heat_bath_word(neg, sel, tail0, tA, tB, g, sweep, p, k0, k1);
+      }
+      __syncthreads();
+    }
+
+    if (sweep < rm.burn_in || (sweep - rm.burn_in) % rm.record_every != 0) continue;
+
+    // ---- record (Fig. 2 Step 3): validity and phase, bit-sliced over chains
+    uint32_t viol = 0u, f0 = 0u, f1 = 0u, f2 = 0u;
+    for (int i = tid; i < npb; i += T) {
+      const Rec R = srec[i];
+      viol |= W[R.vd] ^ W[R.va] ^ W[R.vb];
+      const uint32_t x = W[R.pa] & W[R.pb];
+      add3(f0, f1, f2, (R.w & 1) ? x : 0u, (R.w & 2) ? x : 0u, (R.w & 4) ? x : 0u);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const uint32_t ov = __shfl_xor_sync(0xffffffffu, viol, off);
+      const uint32_t o0 = __shfl_xor_sync(0xffffffffu, f0, off);
+      const uint32_t o1 = __shfl_xor_sync(0xffffffffu, f1, off);
+      const uint32_t o2 = __shfl_xor_sync(0xffffffffu, f2, off);
+      viol |= ov;
+      add3(f0, f1, f2, o0, o1, o2);
+    }
+    if (lane == 0) {
+      red[warp * 4 + 0] = viol;
+      red[warp * 4 + 1] = f0;
+      red[warp * 4 + 2] = f1;
+      red[warp * 4 + 3] = f2;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      viol = 0u; f0 = f1 = f2 = 0u;
+      if (lane < nwarps) {
+        viol = red[lane * 4 + 0];
+        f0 = red[lane * 4 + 1];
+        f1 = red[lane * 4 + 2];
+        f2 = red[lane * 4 + 3];
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const uint32_t ov = __shfl_xor_sync(0xffffffffu, viol, off);
+        const uint32_t o0 = __shfl_xor_sync(0xffffffffu, f0, off);
+        const uint32_t o1 = __shfl_xor_sync(0xffffffffu, f1, off);
+        const uint32_t o2 = __shfl_xor_sync(0xffffffffu, f2, off);
+        viol |= ov;
+        add3(f0, f1, f2, o0, o1, o2);
+      }
+      // every lane now holds the group's words; lane = chain within the group
+      const uint32_t chain = g * 32u + (uint32_t)lane;
+      const bool active = chain < rm.chains;
+      const bool valid = active && !((viol >> lane) & 1u);
+      uint32_t alpha = 0u;
+      const uint32_t* last = W + d * n;
+      for (int q = 0; q < n; ++q) alpha |= ((last[q] >> lane) & 1u) << q;
+      const uint32_t phase = ((f0 >> lane) & 1u) | (((f1 >> lane) & 1u) << 1) |
+                             (((f2 >> lane) & 1u) << 2);
+      int bin = -1;
+      if (valid) {
+        if (rm.n_alphas == 0) {
+          bin = (int)alpha;
+        } else {
+          int lo = 0, hi = rm.n_alphas - 1;
+          while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            const uint32_t v = rm.alpha_sorted[mid];
+            if (v == alpha) { bin = rm.alpha_slot[mid]; break; }
+            if (v < alpha) lo = mid + 1; else hi = mid - 1;
+          }
+        }
+      }
+      if (bin >= 0)
+        atomicAdd(&rm.hist[((size_t)batch * rm.bins + (uint32_t)bin) * 8u + phase], 1ull);
+      const uint32_t nvalid = __popc(__ballot_sync(0xffffffffu, valid));
+      const uint32_t nactive = __popc(__ballot_sync(0xffffffffu, active));
+      if (lane == 0) {
+        atomicAdd(&rm.valid[batch], (unsigned long long)nvalid);
+        atomicAdd(&rm.samples[batch], (unsigned long long)nactive);
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- write the group image back
+  uint32_t* out = rm.state + (size_t)g * npb;
+  for (int i = tid; i < npb; i += T) out[i] = W[n + i];
+  __syncthreads();
+}
+
+// One CTA per chain group of every model of the run (flat group index).
+__global__ void __launch_bounds__(1024) sweep_kernel(const RunModelDev* __restrict__ rm,
+                                                     int n_models, uint32_t total_groups,
+                                                     uint32_t n_sweeps, WsHeader* hdr) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t sweep0 = hdr->sweep0;
+  const uint32_t flat = blockIdx.x;
+  if (flat >= total_groups) return;
+  const int mi = find_model(rm, n_models, flat);
+  const RunModelDev& r = rm[mi];
+  const uint32_t g = flat - r.group_base;
+  if (g >= r.groups) return;
+  run_group(r, g, sweep0, n_sweeps, smem, hdr);
+}
+
+// Persistent form: a fixed grid pops (model, group) items from a
+// cost-ordered work list with one atomic counter.  No CTA waits on another.
+__global__ void __launch_bounds__(1024) sweep_persistent_kernel(
+    const RunModelDev* __restrict__ rm, int n_models, const uint32_t* __restrict__ work,
+    uint32_t n_work, uint32_t n_sweeps, WsHeader* hdr) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t sweep0 = hdr->sweep0;
+  __shared__ uint32_t item;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(&hdr->work_next, 1u);
+    __syncthreads();
+    const uint32_t it = item;
+    __syncthreads();
+    if (it >= n_work) break;
+    const uint32_t flat = work[it];
+    const int mi = find_model(rm, n_models, flat);
+    const RunModelDev& r = rm[mi];
+    const uint32_t g = flat - r.group_base;
+    if (g < r.groups) run_group(r, g, sweep0, n_sweeps, smem, hdr);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initial chains: a valid path with random H outputs (tag-1 stream), every
+// other bit its deterministic value, layer by layer.
+__global__ void init_kernel(const RunModelDev* __restrict__ rm, int n_models,
+                            uint32_t total_groups, const uint32_t* const* __restrict__ init_tabs,
+                            WsHeader* hdr) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t flat = blockIdx.x;
+  if (flat >= total_groups) return;
+  const int mi = find_model(rm, n_models, flat);
+  const RunModelDev& r = rm[mi];
+  const uint32_t g = flat - r.group_base;
+  if (g >= r.groups) return;
+  const ModelDev* mp = r.model;
+  const int n = mp->n, d = mp->d, nw = mp->nw;
+  const uint32_t* itab = init_tabs[mi];  // per p-bit: 0xFFFFFFFF = H, else a | b << 16
+  uint32_t* W = smem;
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) {
+    uint32_t v = 0u;
+    if (i < n) v = ((mp->beta >> i) & 1u) ? ~0u : 0u;
+    else if (i == ones_idx(n, d)) v = ~0u;
+    W[i] = v;
+  }
+  __syncthreads();
+  for (int k = 1; k <= d; ++k) {
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      const int p = (k - 1) * n + q;
+      const uint32_t e = itab[p];
+      uint32_t v;
+      if (e == 0xFFFFFFFFu) {
+        v = philox4x32_10(make_uint4(g, 0u, (uint32_t)p | (kTagInit << 16), 0u), r.seed_lo,
+                          r.seed_hi).x;
+      } else {
+        const uint32_t a = e & 0xFFFFu, b = e >> 16;
+        if ((int)a >= nw || (int)b >= nw) { set_status(hdr, PB_EINVAL); v = 0u; }
+        else v = W[a] ^ W[b];
+      }
+      W[k * n + q] = v;
+    }
+    __syncthreads();
+  }
+  uint32_t* out = r.state + (size_t)g * n * d;
+  for (int i = threadIdx.x; i < n * d; i += blockDim.x) out[i] = W[n + i];
+}
+
+// ---------------------------------------------------------------------------
+// Amplitudes (Eq. U23 with uniform valid paths, exact integer phase classes):
+//   Z = sum_b cnt_b w^b = (c0 - c4) + (c1 - c3 - c5 + c7)/sqrt2
+//                      + i[(c2 - c6) + (c1 + c3 - c5 - c7)/sqrt2]
+//   psi = 2^{h/2} Z / valid.
+// The standard error comes from batch means over chain groups (Eq. U26),
+// with compensated (Kahan) FP64 accumulation of the batch sums.
+struct Kahan {
+  double s = 0.0, c = 0.0;
+  __device__ void add(double x) {
+    const double y = x - c;
+    const double t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+__device__ inline void phase_sum(const unsigned long long* c, double& re, double& im) {
+  const long long c0 = (long long)c[0], c1 = (long long)c[1], c2 = (long long)c[2],
+                  c3 = (long long)c[3], c4 = (long long)c[4], c5 = (long long)c[5],
+                  c6 = (long long)c[6], c7 = (long long)c[7];
+  const double inv_sqrt2 = 0.70710678118654752440;
+  re = (double)(c0 - c4) + (double)(c1 - c3 - c5 + c7) * inv_sqrt2;
+  im = (double)(c2 - c6) + (double)(c1 + c3 - c5 - c7) * inv_sqrt2;
+}
+
+__global__ void amplitude_kernel(const RunModelDev* __restrict__ rm_all, int model) {
+  const RunModelDev& rm = rm_all[model];
+  const uint32_t bin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin >= rm.bins) return;
+  const int h = rm.model->h;
+  const double scale_h = exp2(0.5 * (double)h);
+  unsigned long long tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long vtot = 0;
+  for (uint32_t b = 0; b < rm.n_batches; ++b) {
+    const unsigned long long* c = rm.hist + ((size_t)b * rm.bins + bin) * 8u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tot[k] += c[k];
+    vtot += rm.valid[b];
+  }
+  double re = 0.0, im = 0.0, se = 0.0;
+  if (vtot > 0) {
+    phase_sum(tot, re, im);
+    re *= scale_h / (double)vtot;
+    im *= scale_h / (double)vtot;
+    uint32_t nb = 0;
+    Kahan acc;
+    for (uint32_t b = 0; b < rm.n_batches; ++b) {
+      const unsigned long long vb = rm.valid[b];
+      if (vb == 0) continue;
+      ++nb;
+      double br, bi;
+      phase_sum(rm.hist + ((size_t)b * rm.bins + bin) * 8u, br, bi);
+      br = br * scale_h / (double)vb - re;
+      bi = bi * scale_h / (double)vb - im;
+      const double w = (double)vb / (double)vtot;
+      acc.add(w * w * (br * br + bi * bi));
+    }
+    se = nb > 1 ? sqrt(acc.s * (double)nb / (double)(nb - 1)) : 0.0;
+  }
+  double* out = rm.amp + (size_t)bin * 3u;
+  out[0] = re;
+  out[1] = im;
+  out[2] = se;
+}
+
+// L2 normalisation over the recorded bins (Fig. 2 Step 4), one CTA.
+__global__ void normalize_kernel(const RunModelDev* __restrict__ rm_all, int model) {
+  const RunModelDev& rm = rm_all[model];
+  __shared__ double part[1024];
+  Kahan acc;
+  for (uint32_t i = threadIdx.x; i < rm.bins; i += blockDim.x) {
+    const double* a = rm.amp + (size_t)i * 3u;
+    acc.add(a[0] * a[0] + a[1] * a[1]);
+  }
+  part[threadIdx.x] = acc.s;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double norm = sqrt(part[0]);
+  if (norm <= 0.0) return;
+  const double inv = 1.0 / norm;
+  for (uint32_t i = threadIdx.x; i < rm.bins; i += blockDim.x) {
+    double* a = rm.amp + (size_t)i * 3u;
+    a[0] *= inv;
+    a[1] *= inv;
+    a[2] *= inv;
+  }
+}
+
+__global__ void philox_fill_kernel(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                                   uint32_t count, uint32_t* __restrict__ out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  const uint4 r = philox4x32_10(c, k0, k1);
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (called by the runtime).
+cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
+                        const uint32_t* const* d_init_tabs, size_t smem_bytes, WsHeader* hdr,
+                        cudaStream_t st) {
+  init_kernel<<<total_groups, 32, smem_bytes, st>>>(d_rm, n_models, total_groups, d_init_tabs, hdr);
+  return cudaGetLastError();
+}
+
+// Sweep index advance after a launch (the sweep kernels read hdr->sweep0, so
+// one captured graph replays correctly any number of times).
+__global__ void advance_kernel(WsHeader* hdr, uint32_t n_sweeps) { hdr->sweep0 += n_sweeps; }
+
+cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
+                          uint32_t n_sweeps, int threads, size_t smem_bytes,
+                          WsHeader* hdr, cudaStream_t st) {
+  sweep_kernel<<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups,
+                                                          n_sweeps, hdr);
+  advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
+                                     uint32_t n_work, uint32_t n_sweeps,
+                                     int threads, int grid, size_t smem_bytes, WsHeader* hdr,
+                                     cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(&hdr->work_next, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  sweep_persistent_kernel<<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work,
+                                                              n_sweeps, hdr);
+  advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
+                              cudaStream_t st) {
+  const int tpb = 256;
+  amplitude_kernel<<<(bins + tpb - 1) / tpb, tpb, 0, st>>>(d_rm, model);
+  if (l2) normalize_kernel<<<1, 1024, 0, st>>>(d_rm, model);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t count,
+                               uint32_t* out, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  philox_fill_kernel<<<(count + 255) / 256, 256, 0, st>>>(ctr, k0, k1, count, out);
+  return cudaGetLastError();
+}
+
+size_t sweep_smem_bytes(int n, int d, int threads) { return group_smem_bytes(n, d, threads); }
+
+// Opt the sweep kernels into large dynamic shared memory (called once per
+// run, outside any stream capture).
+cudaError_t sweep_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(sweep_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              200 * 1024);
+}
+
+int sweep_max_blocks_per_sm(int threads, size_t smem) {
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_persistent_kernel, threads,
+                                                    smem) != cudaSuccess)
+    return 1;
+  return blocks;
+}
+
+}  // namespace pb

@@ -1,0 +1,340 @@
+"""Python binding of the C ABI in ``include/pbits.h`` (ctypes; marshalling only).
+
+Every step of the sampler runs in ``libpbits.so``; PyTorch supplies device
+memory (the run workspace) and the CUDA stream.  Loading fails loudly when
+the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpbits.so")
+
+PB_OK, PB_EINVAL, PB_ERANGE, PB_ENOMEM, PB_ECUDA, PB_ETIMEOUT, PB_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PB_GIBBS, PB_LEARNED = 0, 1
+
+_lib = None
+
+
+class PbError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code) if _lib else code} ({code})")
+
+
+class pb_gate(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("layer", ctypes.c_int32), ("q0", ctypes.c_int32),
+                ("q1", ctypes.c_int32)]
+
+
+class pb_model_info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("d", ctypes.c_int32), ("n_pbits", ctypes.c_int32),
+                ("h", ctypes.c_int32), ("M", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("J", ctypes.c_double), ("input_bits", ctypes.c_uint32),
+                ("thr", ctypes.c_uint32 * 4), ("colour_size", ctypes.c_int32 * 4)]
+
+
+class pb_run_cfg(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("chains", ctypes.c_uint32), ("burn_in", ctypes.c_uint32),
+                ("record_every", ctypes.c_uint32), ("n_batches", ctypes.c_uint32),
+                ("alphas", ctypes.POINTER(ctypes.c_uint32)), ("n_alphas", ctypes.c_int32),
+                ("sampler", ctypes.c_int32), ("proposal", ctypes.c_void_p),
+                ("mh_every", ctypes.c_uint32)]
+
+
+class pb_run_stats_t(ctypes.Structure):
+    _fields_ = [("sweeps_done", ctypes.c_uint64), ("flips", ctypes.c_double),
+                ("last_ms", ctypes.c_double), ("flips_per_s", ctypes.c_double)]
+
+
+# Exported entry points: name -> (restype, argtypes).  Tests check that the
+# library exports every one of them.
+_VP = ctypes.c_void_p
+_SIGS = {
+    "pb_version": (ctypes.c_int, []),
+    "pb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pb_compile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(pb_gate), ctypes.c_int,
+                                  ctypes.c_uint32, ctypes.c_double, ctypes.POINTER(_VP)]),
+    "pb_model_info": (ctypes.c_int, [_VP, ctypes.POINTER(pb_model_info_t)]),
+    "pb_model_colours": (ctypes.c_int, [_VP, _VP]),
+    "pb_model_free": (None, [_VP]),
+    "pb_workspace_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(pb_run_cfg), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_size_t)]),
+    "pb_run_create": (ctypes.c_int, [_VP, ctypes.POINTER(pb_run_cfg), ctypes.c_int, _VP,
+                                     ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(_VP)]),
+    "pb_run_sweeps": (ctypes.c_int, [_VP, ctypes.c_uint32]),
+    "pb_run_wait": (ctypes.c_int, [_VP]),
+    "pb_run_histogram": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "pb_run_amplitudes": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "pb_run_get_state": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_size_t]),
+    "pb_run_set_state": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_size_t]),
+    "pb_run_stats": (ctypes.c_int, [_VP, ctypes.POINTER(pb_run_stats_t)]),
+    "pb_run_checkpoint": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "pb_run_restore": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    "pb_run_free": (None, [_VP]),
+    "pb_philox_fill": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _VP,
+                                      ctypes.c_void_p]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libpbits.so (raises if it is missing: build it with
+    ``python -m paper_2007_07379_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: the CUDA library has not been built "
+                      "(python -m paper_2007_07379_gb300.build)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue  # reported by exported_symbols()
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols(path: str = LIB_PATH) -> dict[str, bool]:
+    lib = ctypes.CDLL(path)
+    return {name: hasattr(lib, name) for name in _SIGS}
+
+
+def strerror(code: int) -> str:
+    return load().pb_strerror(code).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != PB_OK:
+        raise PbError(rc, what)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def gate_array(gates) -> ctypes.Array:
+    g = np.asarray(gates, dtype=np.int32).reshape(-1, 4)
+    arr = (pb_gate * max(len(g), 1))()
+    for i, (op, layer, q0, q1) in enumerate(g):
+        arr[i] = pb_gate(int(op), int(layer), int(q0), int(q1))
+    return arr, len(g)
+
+
+class Model:
+    """A compiled circuit (pb_compile)."""
+
+    def __init__(self, n: int, d: int, gates, J: float, input_bits: int = 0):
+        lib = load()
+        arr, ng = gate_array(gates)
+        h = ctypes.c_void_p()
+        _check(lib.pb_compile(n, d, arr, ng, ctypes.c_uint32(input_bits), ctypes.c_double(J),
+                              ctypes.byref(h)), "pb_compile")
+        self._h = h
+        self.n, self.d = n, d
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = pb_model_info_t()
+        _check(load().pb_model_info(self._h, ctypes.byref(inf)), "pb_model_info")
+        return {"n": inf.n, "d": inf.d, "n_pbits": inf.n_pbits, "h": inf.h, "M": inf.M,
+                "rank": inf.rank, "J": inf.J, "input_bits": inf.input_bits,
+                "thr": list(inf.thr), "colour_size": list(inf.colour_size)}
+
+    def colours(self) -> np.ndarray:
+        out = np.zeros((self.d, self.n), dtype=np.int32)
+        _check(load().pb_model_colours(self._h, _ptr(out)), "pb_model_colours")
+        return out
+
+    def close(self):
+        if self._h:
+            load().pb_model_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class RunCfg:
+    seed: int
+    chains: int
+    burn_in: int = 0
+    record_every: int = 1
+    n_batches: int = 0
+    alphas: np.ndarray | None = None
+    sampler: int = PB_GIBBS
+    proposal: object = None
+    mh_every: int = 1
+
+
+def _cfg_array(cfgs: list[RunCfg]):
+    arr = (pb_run_cfg * len(cfgs))()
+    keep = []
+    for i, c in enumerate(cfgs):
+        al = None
+        if c.alphas is not None:
+            al = np.ascontiguousarray(c.alphas, dtype=np.uint32)
+            keep.append(al)
+        arr[i] = pb_run_cfg(c.seed & ((1 << 64) - 1), c.chains, c.burn_in, c.record_every, c.n_batches,
+                            al.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)) if al is not None else None,
+                            0 if al is None else len(al), c.sampler,
+                            c.proposal.handle if c.proposal is not None else None, c.mh_every)
+    return arr, keep
+
+
+def workspace_bytes(models: list[Model], cfgs: list[RunCfg]) -> int:
+    lib = load()
+    mh = (ctypes.c_void_p * len(models))(*[m.handle.value for m in models])
+    ca, keep = _cfg_array(cfgs)
+    out = ctypes.c_size_t(0)
+    _check(lib.pb_workspace_bytes(mh, ca, len(models), ctypes.byref(out)), "pb_workspace_bytes")
+    return out.value
+
+
+class Run:
+    """A set of chains on the GPU (pb_run_create ... pb_run_free).
+
+    The workspace is a torch uint8 CUDA tensor owned by this object; the
+    stream is torch's current stream unless one is given.
+    """
+
+    def __init__(self, models: list[Model], cfgs: list[RunCfg], stream=None, workspace=None):
+        import torch
+        lib = load()
+        self.models = list(models)
+        self.cfgs = list(cfgs)
+        nbytes = workspace_bytes(self.models, self.cfgs)
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        if workspace.numel() < nbytes or workspace.data_ptr() % 256:
+            raise ValueError("workspace too small or not 256-byte aligned")
+        self.workspace = workspace
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        mh = (ctypes.c_void_p * len(models))(*[m.handle.value for m in models])
+        ca, keep = _cfg_array(self.cfgs)
+        h = ctypes.c_void_p()
+        _check(lib.pb_run_create(mh, ca, len(models), ctypes.c_void_p(workspace.data_ptr()),
+                                 workspace.numel(), ctypes.c_void_p(self.stream.cuda_stream),
+                                 ctypes.byref(h)), "pb_run_create")
+        self._h = h
+
+    def bins(self, model: int = 0) -> int:
+        c = self.cfgs[model]
+        return len(c.alphas) if c.alphas is not None else (1 << self.models[model].n)
+
+    def groups(self, model: int = 0) -> int:
+        return (self.cfgs[model].chains + 31) // 32
+
+    def sweeps(self, n: int):
+        _check(load().pb_run_sweeps(self._h, n), "pb_run_sweeps")
+
+    def wait(self):
+        _check(load().pb_run_wait(self._h), "pb_run_wait")
+
+    def histogram(self, model: int = 0):
+        cnt = np.zeros((self.bins(model), 8), dtype=np.uint64)
+        v = ctypes.c_uint64(0)
+        s = ctypes.c_uint64(0)
+        _check(load().pb_run_histogram(self._h, model, _ptr(cnt), ctypes.byref(v), ctypes.byref(s)),
+               "pb_run_histogram")
+        return cnt, v.value, s.value
+
+    def amplitudes(self, model: int = 0, l2_normalize: bool = False):
+        b = self.bins(model)
+        re, im, se = np.zeros(b), np.zeros(b), np.zeros(b)
+        _check(load().pb_run_amplitudes(self._h, model, int(l2_normalize), _ptr(re), _ptr(im), _ptr(se)),
+               "pb_run_amplitudes")
+        return re + 1j * im, se
+
+    def get_state(self, model: int = 0) -> np.ndarray:
+        m = self.models[model]
+        out = np.zeros((self.groups(model), m.d, m.n), dtype=np.uint32)
+        _check(load().pb_run_get_state(self._h, model, _ptr(out), out.nbytes), "pb_run_get_state")
+        return out
+
+    def set_state(self, words: np.ndarray, model: int = 0):
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        _check(load().pb_run_set_state(self._h, model, _ptr(w), w.nbytes), "pb_run_set_state")
+
+    def stats(self) -> dict:
+        st = pb_run_stats_t()
+        _check(load().pb_run_stats(self._h, ctypes.byref(st)), "pb_run_stats")
+        return {"sweeps_done": st.sweeps_done, "flips": st.flips, "last_ms": st.last_ms,
+                "flips_per_s": st.flips_per_s}
+
+    def checkpoint(self) -> bytes:
+        lib = load()
+        need = ctypes.c_size_t(0)
+        _check(lib.pb_run_checkpoint(self._h, None, 0, ctypes.byref(need)), "pb_run_checkpoint")
+        buf = np.zeros(need.value, dtype=np.uint8)
+        _check(lib.pb_run_checkpoint(self._h, _ptr(buf), buf.nbytes, ctypes.byref(need)),
+               "pb_run_checkpoint")
+        return buf.tobytes()
+
+    def restore(self, blob: bytes):
+        buf = np.frombuffer(blob, dtype=np.uint8).copy()
+        _check(load().pb_run_restore(self._h, _ptr(buf), buf.nbytes), "pb_run_restore")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pb_run_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unslice_state(words: np.ndarray, chains: int) -> np.ndarray:
+    """Chain-sliced words [groups, d, n] -> per-chain layer words [chains, d]
+    (bit q of row k-1 = p-bit (k, q)).  Pure data movement."""
+    G, d, n = words.shape
+    out = np.zeros((G * 32, d), dtype=np.uint32)
+    for q in range(n):
+        bits = ((words[:, :, q][:, None, :] >> np.arange(32, dtype=np.uint32)[None, :, None]) & 1)
+        out |= (bits.reshape(G * 32, d).astype(np.uint32) << np.uint32(q))
+    return out[:chains]
+
+
+def slice_state(per_chain: np.ndarray, n: int) -> np.ndarray:
+    """Inverse of unslice_state (chains padded with zero to a multiple of 32)."""
+    C, d = per_chain.shape
+    G = (C + 31) // 32
+    pad = np.zeros((G * 32, d), dtype=np.uint32)
+    pad[:C] = per_chain
+    pad = pad.reshape(G, 32, d)
+    out = np.zeros((G, d, n), dtype=np.uint32)
+    for q in range(n):
+        bits = (pad >> np.uint32(q)) & 1  # [G, 32, d]
+        out[:, :, q] = np.sum(bits.astype(np.uint64) << np.arange(32, dtype=np.uint64)[None, :, None],
+                              axis=1).astype(np.uint32)
+    return out
+
+
+def philox_fill(ctr: np.ndarray, key: tuple[int, int]) -> np.ndarray:
+    """Philox4x32-10 of each counter row on the device (test hook)."""
+    import torch
+    c = torch.as_tensor(np.ascontiguousarray(ctr, dtype=np.uint32).view(np.int32)).cuda()
+    out = torch.empty_like(c)
+    st = torch.cuda.current_stream()
+    _check(load().pb_philox_fill(ctypes.c_void_p(c.data_ptr()), key[0], key[1], c.shape[0],
+                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream)),
+           "pb_philox_fill")
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32)
