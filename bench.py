@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the plain Gibbs path (p-bit flips/s).
+
+Workload: the mid circuit (random Clifford+T, n = 12 qubits, d = 20 layers,
+252 p-bits), 4096 chains, 1e5 sweeps in total.  A step is one pass of the hot
+path over the batch of chains: `--sweeps-per-step` Gibbs sweeps of every chain
+with a record (validity, phase, histogram bin) after each sweep, then the
+amplitude reduction of the 4096-bin histogram and its read-back.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank owns its own 4096 chains (global chain groups offset
+by rank, weak scaling) and the ranks combine their integer histograms with one
+all-reduce after the timed steps.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2007_07379_gb300 import workloads as W  # noqa: E402
+
+METRIC = "p-bit flips/s; wall time to 1% amplitude error (learned vs plain Gibbs)"
+UNIT = "flips/s"
+
+# Algorithmic integer work of one 32-chain word update, in 32-lane integer
+# instruction slots: expected Philox4x32-10 calls of the most-significant-
+# first comparison (each plane decides a chain with probability 1/2, calls of
+# 4 planes continue while any of the 32 chains is undecided) x (40 slots per
+# call + 4 planes x 4 slots of comparison) + 12 slots of links and store; plus
+# the record (8 slots per p-bit word) every sweep.
+PHILOX_SLOTS = 40
+PLANE_SLOTS = 4
+LINK_SLOTS = 12
+RECORD_SLOTS = 8
+
+
+def expected_calls(lanes: int = 32) -> float:
+    return sum(1.0 - (1.0 - 2.0 ** (-4 * c)) ** lanes for c in range(0, 9))
+
+
+def alg_slots_per_word() -> float:
+    return expected_calls(32) * (PHILOX_SLOTS + 4 * PLANE_SLOTS) + LINK_SLOTS + RECORD_SLOTS
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def gpu_id(dev) -> str:
+    """nvidia-smi identifier (UUID) of a torch device."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev.index or 0)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_rate(wl, budget_s: float = 12.0, chains: int | None = None):
+    """The oracle's reference Gibbs sampler on a bounded sample of the same
+    workload (host cores, OpenMP over chains).  Returns (flips/s, cores, sample)."""
+    import oracle
+    n, d = wl.n, wl.d
+    c = chains or 64
+    t0 = time.perf_counter()
+    oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=2)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    sweeps = max(2, int(budget_s / dt * 2 * 0.8))
+    sweeps = min(sweeps, 2000)
+    t0 = time.perf_counter()
+    oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=sweeps)
+    dt = time.perf_counter() - t0
+    flips = c * sweeps * n * d
+    return flips / dt, oracle.num_threads(), f"{c} chains x {sweeps} sweeps of the {wl.name} circuit ({dt:.1f} s)"
+
+
+def run_reference(args, wl):
+    """Reference arm: the CPU oracle as it stands, on the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n, d = wl.n, wl.d
+    c = 64
+    per_step = max(2, args.ref_sweeps)
+    for _ in range(args.warmup):
+        oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=1)
+    times = []
+    state = None
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=per_step,
+                         sweep0=k * per_step, state=state)
+        state = r["state"]
+        times.append(time.perf_counter() - t0)
+    flips = c * per_step * n * d * args.steps
+    value = flips / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "config": _config(wl, args, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{c} chains x {per_step} sweeps per step of the {wl.name} circuit"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(wl, args, world):
+    return {"workload": f"{wl.name}: random Clifford+T n={wl.n} d={wl.d} ({wl.n_pbits} p-bits), "
+                        f"{wl.chains} chains per GPU, {args.sweeps_per_step} sweeps per step, J={wl.J:.4f}",
+            "n": wl.n, "d": wl.d, "chains_per_gpu": wl.chains, "sweeps_per_step": args.sweeps_per_step,
+            "circuit_seed": 1000, "philox_key": wl.seed, "parallelism": f"chains sharded over {world} GPU(s)",
+            "l2": "flushed (256 MiB write) between timed steps; working set is on-chip by design"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweeps-per-step", type=int, default=10_000)
+    ap.add_argument("--ref-sweeps", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+
+    wl = W.mid()
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+
+    import torch
+    from paper_2007_07379_gb300 import pbits
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    pbits.load()
+
+    stream = torch.cuda.Stream(device=dev)
+    groups = (wl.chains + 31) // 32
+    S = args.sweeps_per_step
+    with torch.cuda.stream(stream):
+        model = pbits.Model(wl.n, wl.d, wl.gates, wl.J)
+        info = model.info()
+        cfg = pbits.RunCfg(seed=wl.seed, chains=wl.chains, group0=rank * groups)
+        run = pbits.Run([model], [cfg], stream=stream)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        for _ in range(args.warmup):
+            run.sweeps(S)
+            run.amplitudes()
+        torch.cuda.synchronize(dev)
+
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        sweep_ms = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(gpu_id(dev)) as clk:
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)  # evict L2 between timed steps (outside the events)
+                ev[k][0].record(stream)
+                run.sweeps(S)
+                run.amplitudes()  # reduction kernel + read-back; synchronises the stream
+                ev[k][1].record(stream)
+                sweep_ms.append(run.stats()["last_ms"])
+            torch.cuda.synchronize(dev)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+        # the single exchange of the method: integer sum of the histograms
+        cnt, valid, samples = run.histogram()
+        h = torch.tensor(cnt.astype(np.int64), device=dev)
+        torch.distributed.all_reduce(h)
+    flips_per_step = wl.chains * info["n"] * info["d"] * S
+    value = world * flips_per_step * args.steps / total_s
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel (the sweep launch): algorithmic integer
+    # instruction slots per launch / its duration, against the issue peak
+    peaks, peak_kind = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_slots = sms * 4 * 32 * sm_max * 1e6  # 4 schedulers x 32 lanes per SM per clock
+    words_per_launch = groups * wl.n * wl.d * S
+    alg_slots = words_per_launch * alg_slots_per_word()
+    launch_s = statistics.mean(sweep_ms) / 1e3
+    achieved = alg_slots / launch_s
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_slots / 1e12,
+                "unit": "T int32 lane-slots/s", "frac": achieved / peak_slots, "traffic": None,
+                "peak_basis": f"{sms} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind} sm_max)",
+                "kernel": "sweep_kernel", "launch_ms": statistics.mean(sweep_ms),
+                "alg_slots_per_flip": alg_slots_per_word() / 32}
+    prof = os.path.join(ROOT, "profiles", "sweep_kernel_mid_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                tr = json.load(f)
+            if tr.get("kernel_rev") == kernel_rev():
+                roofline["traffic"] = tr["dram_bytes_per_launch_per_sweep"] * S
+        except Exception:
+            pass
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(wl, rank, groups, S, dev, stream, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_oracle_rate(wl)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": _config(wl, args, world), "clocks": clocks, "e2e": e2e,
+            "gpu_launches": 3 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
+            "samples_per_s": world * wl.chains * S * args.steps / total_s,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def kernel_rev() -> str:
+    """Hash of the sources that make up the sweep kernel (ties a stored ncu
+    traffic figure to the kernel it was measured on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "philox.cuh", "pb_internal.h"):
+        with open(os.path.join(ROOT, "paper_2007_07379_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measure_e2e(wl, rank, groups, S, dev, stream, world):
+    """Same metric through the C ABI from host buffers: each step compiles the
+    host gate list, creates the run (tables copied host -> device, chains
+    initialised), runs S sweeps and copies the amplitudes back to the host."""
+    import torch
+    from paper_2007_07379_gb300 import pbits
+    steps = 3
+    cfg = pbits.RunCfg(seed=wl.seed, chains=wl.chains, group0=rank * groups)
+    nbytes = None
+    times = []
+    h2d = d2h = 0
+    with torch.cuda.stream(stream):
+        for k in range(steps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            model = pbits.Model(wl.n, wl.d, wl.gates, wl.J)
+            if nbytes is None:
+                nbytes = pbits.workspace_bytes([model], [cfg])
+                ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            run = pbits.Run([model], [cfg], stream=stream, workspace=ws)
+            run.sweeps(S)
+            psi, se = run.amplitudes()
+            dt = time.perf_counter() - t0
+            run.close()
+            model.close()
+            if k > 0:  # first pass warms the graph cache and allocator
+                times.append(dt)
+            npb = wl.n * wl.d
+            h2d = npb * (16 + 16 + 4) + 256 + 256 + 8
+            d2h = psi.size * 3 * 8
+    t = sum(times)
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+    value = world * wl.chains * wl.n * wl.d * S * steps / t
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": steps, "what": "pb_compile + pb_run_create + sweeps + pb_run_amplitudes"}
+
+
+if __name__ == "__main__":
+    main()

@@ -122,6 +122,9 @@ typedef struct {
   int32_t sampler;        /* PB_GIBBS or PB_LEARNED                            */
   const pb_mlp* proposal; /* trained MLP for PB_LEARNED, else NULL             */
   uint32_t mh_every;      /* PB_LEARNED: one suffix MH move every mh_every sweeps */
+  uint32_t group0;        /* global index of the first chain group: the chains
+                             here are 32*group0 ... (multi-rank sharding; the
+                             draws depend on the global index only)             */
 } pb_run_cfg;
 
 /* Bytes of device workspace that pb_run_create() needs for these models. */

@@ -65,7 +65,7 @@ struct RunModelDev {
   uint32_t burn_in, record_every;
   uint32_t seed_lo, seed_hi;
   uint32_t group_base;     // first flat group index of this model in a launch
-  uint32_t pad;
+  uint32_t group0;         // global index of group 0 (Philox counter word 0)
 };
 
 // Workspace header at offset 0.

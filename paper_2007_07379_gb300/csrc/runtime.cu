@@ -295,6 +295,7 @@ struct Layout {
 int check_cfg(const pb_model* m, const pb_run_cfg& c) {
   if (!m) return PB_EINVAL;
   if (c.chains == 0 || c.record_every == 0) return PB_EINVAL;
+  if ((uint64_t)c.group0 + (c.chains + 31) / 32 > 0xFFFFFFFFull) return PB_ERANGE;
   if (c.sampler != PB_GIBBS) return PB_EINVAL;  // the learned sampler has its own entry points
   if (c.alphas == nullptr) {
     if (c.n_alphas != 0) return PB_EINVAL;
@@ -524,6 +525,7 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
     d.seed_lo = (uint32_t)c.seed;
     d.seed_hi = (uint32_t)(c.seed >> 32);
     d.group_base = base;
+    d.group0 = c.group0;
     init_ptrs[i] = reinterpret_cast<const uint32_t*>(ws + s.init);
     for (uint32_t g = 0; g < s.groups; ++g) cost.push_back({(double)npb, base + g});
     base += s.groups;

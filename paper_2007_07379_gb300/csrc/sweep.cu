@@ -129,6 +129,7 @@ __device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, ui
   const uint32_t thr0 = mp->thr[0], thr1 = mp->thr[1], thr2 = mp->thr[2], thr3 = mp->thr[3];
   const uint32_t k0 = rm.seed_lo, k1 = rm.seed_hi;
   const uint32_t batch = g % rm.n_batches;
+  const uint32_t gglob = g + rm.group0;
 
   for (uint32_t s = 0; s < n_sweeps; ++s) {
     const uint32_t sweep = sweep0 + s;
@@ -155,7 +156,7 @@ __device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, ui
           tail0 = 0u; tA = thr3; tB = thr1;
         }
         const uint32_t p = (uint32_t)(D.dst - n) | (kTagSweep << 16);
-        W[D.dst] = heat_bath_word(neg, sel, tail0, tA, tB, g, sweep, p, k0, k1);
+        W[D.dst] = heat_bath_word(neg, sel, tail0, tA, tB, gglob, sweep, p, k0, k1);
       }
       __syncthreads();
     }
@@ -311,8 +312,8 @@ __global__ void init_kernel(const RunModelDev* __restrict__ rm, int n_models,
       const uint32_t e = itab[p];
       uint32_t v;
       if (e == 0xFFFFFFFFu) {
-        v = philox4x32_10(make_uint4(g, 0u, (uint32_t)p | (kTagInit << 16), 0u), r.seed_lo,
-                          r.seed_hi).x;
+        v = philox4x32_10(make_uint4(g + r.group0, 0u, (uint32_t)p | (kTagInit << 16), 0u),
+                          r.seed_lo, r.seed_hi).x;
       } else {
         const uint32_t a = e & 0xFFFFu, b = e >> 16;
         if ((int)a >= nw || (int)b >= nw) { set_status(hdr, PB_EINVAL); v = 0u; }

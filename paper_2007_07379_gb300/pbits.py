@@ -44,7 +44,7 @@ class pb_run_cfg(ctypes.Structure):
                 ("record_every", ctypes.c_uint32), ("n_batches", ctypes.c_uint32),
                 ("alphas", ctypes.POINTER(ctypes.c_uint32)), ("n_alphas", ctypes.c_int32),
                 ("sampler", ctypes.c_int32), ("proposal", ctypes.c_void_p),
-                ("mh_every", ctypes.c_uint32)]
+                ("mh_every", ctypes.c_uint32), ("group0", ctypes.c_uint32)]
 
 
 class pb_run_stats_t(ctypes.Structure):
@@ -179,6 +179,7 @@ class RunCfg:
     sampler: int = PB_GIBBS
     proposal: object = None
     mh_every: int = 1
+    group0: int = 0
 
 
 def _cfg_array(cfgs: list[RunCfg]):
@@ -192,7 +193,8 @@ def _cfg_array(cfgs: list[RunCfg]):
         arr[i] = pb_run_cfg(c.seed & ((1 << 64) - 1), c.chains, c.burn_in, c.record_every, c.n_batches,
                             al.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)) if al is not None else None,
                             0 if al is None else len(al), c.sampler,
-                            c.proposal.handle if c.proposal is not None else None, c.mh_every)
+                            c.proposal.handle if c.proposal is not None else None, c.mh_every,
+                            c.group0)
     return arr, keep
 
 
