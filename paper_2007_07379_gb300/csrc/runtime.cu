@@ -375,6 +375,8 @@ struct pb_run {
   uint64_t sweeps_done = 0;
   double flips_per_sweep = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaStream_t cap_st = nullptr;  // private stream for graph capture (the caller's
+                                  // stream may be the legacy default stream)
   bool timed = false;
   double last_flips = 0.0;
   std::map<uint32_t, cudaGraphExec_t> graphs;
@@ -401,7 +403,7 @@ void choose_shape(pb_run* r) {
   t = std::max(32, std::min(256, t));
   if (const char* e = std::getenv("PB_THREADS")) {
     int v = std::atoi(e);
-    if (v >= 32 && v <= 1024 && v % 32 == 0) t = v;
+    if (v >= 32 && v <= 256 && v % 32 == 0) t = v;
   }
   r->threads = t;
   size_t smem = 0;
@@ -571,16 +573,18 @@ PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
     exec = it->second;
   } else {
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(r->st, cudaStreamCaptureModeThreadLocal);
+    if (!r->cap_st && cudaStreamCreateWithFlags(&r->cap_st, cudaStreamNonBlocking) != cudaSuccess)
+      return PB_ECUDA;
+    cudaError_t e = cudaStreamBeginCapture(r->cap_st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return PB_ECUDA;
     if (r->persistent)
       e = launch_sweeps_persistent(r->d_rm(), r->nm, reinterpret_cast<const uint32_t*>(r->ws + r->L.work),
                                    r->total_groups, n_sweeps, r->threads, r->grid, r->smem, r->hdr(),
-                                   r->st);
+                                   r->cap_st);
     else
       e = launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->threads, r->smem, r->hdr(),
-                        r->st);
-    cudaError_t e2 = cudaStreamEndCapture(r->st, &graph);
+                        r->cap_st);
+    cudaError_t e2 = cudaStreamEndCapture(r->cap_st, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       return PB_ECUDA;
@@ -760,6 +764,7 @@ PB_API void pb_run_free(pb_run* r) {
   if (!r) return;
   cudaStreamSynchronize(r->st);
   for (auto& kv : r->graphs) cudaGraphExecDestroy(kv.second);
+  if (r->cap_st) cudaStreamDestroy(r->cap_st);
   if (r->ev0) cudaEventDestroy(r->ev0);
   if (r->ev1) cudaEventDestroy(r->ev1);
   delete r;

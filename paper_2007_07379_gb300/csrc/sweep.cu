@@ -25,32 +25,69 @@ namespace pb {
 //
 // Each chain compares its uniform u (bit 31-j = bit c of plane j) against a
 // threshold t chosen per chain between tA (lanes in `sel`) and tB.  The
-// comparison runs most significant plane first and stops as soon as every
-// lane is decided; lanes with t = 2^31 (`tail0`) are decided by plane 0.
-// Returns neg ^ [u < t].
-__device__ __forceinline__ uint32_t heat_bath_word(uint32_t neg, uint32_t sel, uint32_t tail0,
-                                                   uint32_t tA, uint32_t tB, uint32_t g,
-                                                   uint32_t sweep, uint32_t p, uint32_t k0,
-                                                   uint32_t k1) {
-  uint32_t lt = 0u, eq = ~0u;
-#pragma unroll 1
-  for (uint32_t grp = 0; grp < 8u; ++grp) {
-    const uint4 r = philox4x32_10(make_uint4(g, sweep, p, grp), k0, k1);
-    const uint32_t R[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-    for (uint32_t w = 0; w < 4u; ++w) {
-      const uint32_t j = grp * 4u + w;
-      const uint32_t TA = (uint32_t)((int32_t)(tA << j) >> 31);
-      const uint32_t TB = (uint32_t)((int32_t)(tB << j) >> 31);
-      const uint32_t T = (sel & TA) | (~sel & TB);
-      lt |= eq & ~R[w] & T;
-      eq &= ~(R[w] ^ T);
-    }
-    eq &= ~tail0;
-    if (eq == 0u) break;
+// comparison runs most significant plane first; a lane is decided at the
+// first plane where its bit differs from the threshold's, and lanes with
+// t = 2^31 (`tail0`) are decided by plane 0.  The result is neg ^ [u < t].
+struct HbClass {
+  uint32_t neg, sel, tail0, tA, tB;
+};
+
+// Link demands -> (neg, sel, thresholds).  v = sum_i (1 - 2 r_i):
+//   m=0: v=0 -> t0.  m=1: neg=r0, t1.  m=2: agree -> neg=r0, t2; else t0.
+//   m=3: neg = majority, unanimous -> t3, else t1.
+__device__ __forceinline__ HbClass classify(int m, uint32_t r0, uint32_t r1, uint32_t r2,
+                                            uint32_t thr0, uint32_t thr1, uint32_t thr2,
+                                            uint32_t thr3) {
+  HbClass k;
+  if (m == 0) {
+    k.neg = 0u; k.sel = 0u; k.tail0 = ~0u; k.tA = thr0; k.tB = thr0;
+  } else if (m == 1) {
+    k.neg = r0; k.sel = 0u; k.tail0 = 0u; k.tA = thr1; k.tB = thr1;
+  } else if (m == 2) {
+    k.neg = r0 & r1; k.sel = ~(r0 ^ r1); k.tail0 = ~k.sel; k.tA = thr2; k.tB = thr0;
+  } else {
+    k.neg = (r0 & r1) | (r0 & r2) | (r1 & r2);
+    k.sel = ~(r0 ^ r1) & ~(r1 ^ r2);
+    k.tail0 = 0u; k.tA = thr3; k.tB = thr1;
   }
-  return neg ^ lt;
+  return k;
 }
+
+// Four planes (one Philox output) of the comparison, planes 4 grp .. 4 grp+3.
+__device__ __forceinline__ void compare4(uint32_t& lt, uint32_t& eq, const HbClass& k, uint4 r,
+                                         uint32_t grp) {
+  const uint32_t R[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (uint32_t w = 0; w < 4u; ++w) {
+    const uint32_t j = grp * 4u + w;
+    const uint32_t TA = (uint32_t)((int32_t)(k.tA << j) >> 31);
+    const uint32_t TB = (uint32_t)((int32_t)(k.tB << j) >> 31);
+    const uint32_t T = (k.sel & TA) | (~k.sel & TB);
+    lt |= eq & ~R[w] & T;
+    eq &= ~(R[w] ^ T);
+  }
+}
+
+// Planes beyond the precomputed ones (rare): Philox calls grp0 .. 7.
+__device__ __forceinline__ void compare_tail(uint32_t& lt, uint32_t& eq, const HbClass& k,
+                                             uint32_t grp0, uint32_t g, uint32_t sweep, uint32_t p,
+                                             uint32_t k0, uint32_t k1) {
+#pragma unroll 1
+  for (uint32_t grp = grp0; grp < 8u && eq != 0u; ++grp)
+    compare4(lt, eq, k, philox4x32_10(make_uint4(g, sweep, p, grp), k0, k1), grp);
+}
+
+__device__ __forceinline__ uint32_t heat_bath_word(const HbClass& k, uint32_t g, uint32_t sweep,
+                                                   uint32_t p, uint32_t k0, uint32_t k1) {
+  uint32_t lt = 0u, eq = ~0u;
+  compare4(lt, eq, k, philox4x32_10(make_uint4(g, sweep, p, 0u), k0, k1), 0u);
+  eq &= ~k.tail0;
+  compare_tail(lt, eq, k, 1u, g, sweep, p, k0, k1);
+  return k.neg ^ lt;
+}
+
+// Number of Philox calls computed ahead of a colour class (12 planes).
+constexpr int kPre = 3;
 
 __device__ __forceinline__ void add3(uint32_t& f0, uint32_t& f1, uint32_t& f2, uint32_t x0,
                                      uint32_t x1, uint32_t x2) {
@@ -80,7 +117,7 @@ __device__ __forceinline__ void set_status(WsHeader* hdr, int code) {
 __host__ __device__ inline size_t group_smem_bytes(int n, int d, int threads) {
   const size_t words = ((size_t)n_words(n, d) + 3) & ~(size_t)3;
   return words * 4 + (size_t)n * d * sizeof(Desc) + (size_t)n * d * sizeof(Rec) +
-         (size_t)(threads / 32) * 4 * sizeof(uint32_t);
+         (size_t)2 * (threads / 32) * 4 * sizeof(uint32_t);
 }
 
 // Runs `n_sweeps` sweeps (absolute indices sweep0...) of one chain group.
@@ -131,32 +168,61 @@ __device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, ui
   const uint32_t batch = g % rm.n_batches;
   const uint32_t gglob = g + rm.group0;
 
+  // This thread's first p-bit of each colour class, kept in registers.
+  Desc mine[4];
+  bool has[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int i = mp->col_off[c] + tid;
+    has[c] = i < mp->col_off[c + 1] && !(sdesc[i < npb ? i : 0].mflag & 0x80);
+    mine[c] = sdesc[has[c] ? i : 0];
+  }
+  // Last-layer words for the output index, held by lanes q < n of warp 0.
+  const uint32_t* last = W + d * n;
+
   for (uint32_t s = 0; s < n_sweeps; ++s) {
     const uint32_t sweep = sweep0 + s;
+    // Philox planes do not depend on the chain state: compute the first
+    // 3 calls (12 planes) of every class up front, independent of each other.
+    uint4 pre[4][kPre];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int c_hi = mp->col_off[c + 1];
-      for (int i = mp->col_off[c] + tid; i < c_hi; i += T) {
-        const Desc D = sdesc[i];
-        if (D.mflag & 0x80) continue;
-        const int m = D.mflag & 3;
+      const uint32_t p = (uint32_t)(mine[c].dst - n) | (kTagSweep << 16);
+#pragma unroll
+      for (int j = 0; j < kPre; ++j)
+        pre[c][j] = has[c] ? philox4x32_10(make_uint4(gglob, sweep, p, (uint32_t)j), k0, k1)
+                           : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (has[c]) {
+        const Desc& D = mine[c];
         const uint32_t r0 = W[D.a[0]] ^ W[D.b[0]];
         const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
         const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
-        uint32_t neg, sel, tail0, tA, tB;
-        if (m == 0) {
-          neg = 0u; sel = 0u; tail0 = ~0u; tA = thr0; tB = thr0;
-        } else if (m == 1) {
-          neg = r0; sel = 0u; tail0 = 0u; tA = thr1; tB = thr1;
-        } else if (m == 2) {
-          neg = r0 & r1; sel = ~(r0 ^ r1); tail0 = ~sel; tA = thr2; tB = thr0;
-        } else {
-          neg = (r0 & r1) | (r0 & r2) | (r1 & r2);
-          sel = ~(r0 ^ r1) & ~(r1 ^ r2);
-          tail0 = 0u; tA = thr3; tB = thr1;
+        const HbClass k = classify(D.mflag & 3, r0, r1, r2, thr0, thr1, thr2, thr3);
+        uint32_t lt = 0u, eq = ~0u;
+        compare4(lt, eq, k, pre[c][0], 0u);
+        eq &= ~k.tail0;
+#pragma unroll
+        for (int j = 1; j < kPre; ++j) compare4(lt, eq, k, pre[c][j], (uint32_t)j);
+        if (eq != 0u) {
+          const uint32_t p = (uint32_t)(D.dst - n) | (kTagSweep << 16);
+          compare_tail(lt, eq, k, (uint32_t)kPre, gglob, sweep, p, k0, k1);
         }
+        W[D.dst] = k.neg ^ lt;
+      }
+      // further p-bits of the class when it is larger than the CTA
+      const int c_hi = mp->col_off[c + 1];
+      for (int i = mp->col_off[c] + tid + T; i < c_hi; i += T) {
+        const Desc D = sdesc[i];
+        if (D.mflag & 0x80) continue;
+        const uint32_t r0 = W[D.a[0]] ^ W[D.b[0]];
+        const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
+        const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
+        const HbClass k = classify(D.mflag & 3, r0, r1, r2, thr0, thr1, thr2, thr3);
         const uint32_t p = (uint32_t)(D.dst - n) | (kTagSweep << 16);
-        W[D.dst] = heat_bath_word(neg, sel, tail0, tA, tB, gglob, sweep, p, k0, k1);
+        W[D.dst] = heat_bath_word(k, gglob, sweep, p, k0, k1);
       }
       __syncthreads();
     }
@@ -171,6 +237,7 @@ __device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, ui
       const uint32_t x = W[R.pa] & W[R.pb];
       add3(f0, f1, f2, (R.w & 1) ? x : 0u, (R.w & 2) ? x : 0u, (R.w & 4) ? x : 0u);
     }
+    const uint32_t lastw = (warp == 0 && lane < n) ? last[lane] : 0u;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       const uint32_t ov = __shfl_xor_sync(0xffffffffu, viol, off);
@@ -180,20 +247,23 @@ __device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, ui
       viol |= ov;
       add3(f0, f1, f2, o0, o1, o2);
     }
+    // two slots of partials alternate between sweeps, so warp 0 can finish
+    // this record while the other warps start the next sweep
+    uint32_t* slot = red + (s & 1u) * 4 * nwarps;
     if (lane == 0) {
-      red[warp * 4 + 0] = viol;
-      red[warp * 4 + 1] = f0;
-      red[warp * 4 + 2] = f1;
-      red[warp * 4 + 3] = f2;
+      slot[warp * 4 + 0] = viol;
+      slot[warp * 4 + 1] = f0;
+      slot[warp * 4 + 2] = f1;
+      slot[warp * 4 + 3] = f2;
     }
     __syncthreads();
     if (warp == 0) {
       viol = 0u; f0 = f1 = f2 = 0u;
       if (lane < nwarps) {
-        viol = red[lane * 4 + 0];
-        f0 = red[lane * 4 + 1];
-        f1 = red[lane * 4 + 2];
-        f2 = red[lane * 4 + 3];
+        viol = slot[lane * 4 + 0];
+        f0 = slot[lane * 4 + 1];
+        f1 = slot[lane * 4 + 2];
+        f2 = slot[lane * 4 + 3];
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
@@ -204,13 +274,13 @@ __device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, ui
         viol |= ov;
         add3(f0, f1, f2, o0, o1, o2);
       }
-      // every lane now holds the group's words; lane = chain within the group
+      // lane = chain within the group
       const uint32_t chain = g * 32u + (uint32_t)lane;
       const bool active = chain < rm.chains;
       const bool valid = active && !((viol >> lane) & 1u);
       uint32_t alpha = 0u;
-      const uint32_t* last = W + d * n;
-      for (int q = 0; q < n; ++q) alpha |= ((last[q] >> lane) & 1u) << q;
+      for (int q = 0; q < n; ++q)
+        alpha |= ((__shfl_sync(0xffffffffu, lastw, q) >> lane) & 1u) << q;
       const uint32_t phase = ((f0 >> lane) & 1u) | (((f1 >> lane) & 1u) << 1) |
                              (((f2 >> lane) & 1u) << 2);
       int bin = -1;
@@ -236,8 +306,8 @@ __device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, ui
         atomicAdd(&rm.samples[batch], (unsigned long long)nactive);
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
 
   // ---- write the group image back
   uint32_t* out = rm.state + (size_t)g * npb;
@@ -246,7 +316,7 @@ __device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, ui
 }
 
 // One CTA per chain group of every model of the run (flat group index).
-__global__ void __launch_bounds__(1024) sweep_kernel(const RunModelDev* __restrict__ rm,
+__global__ void __launch_bounds__(256) sweep_kernel(const RunModelDev* __restrict__ rm,
                                                      int n_models, uint32_t total_groups,
                                                      uint32_t n_sweeps, WsHeader* hdr) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -262,7 +332,7 @@ __global__ void __launch_bounds__(1024) sweep_kernel(const RunModelDev* __restri
 
 // Persistent form: a fixed grid pops (model, group) items from a
 // cost-ordered work list with one atomic counter.  No CTA waits on another.
-__global__ void __launch_bounds__(1024) sweep_persistent_kernel(
+__global__ void __launch_bounds__(256) sweep_persistent_kernel(
     const RunModelDev* __restrict__ rm, int n_models, const uint32_t* __restrict__ work,
     uint32_t n_work, uint32_t n_sweeps, WsHeader* hdr) {
   extern __shared__ __align__(16) uint32_t smem[];
