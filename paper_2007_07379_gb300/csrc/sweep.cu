@@ -180,49 +180,55 @@ __device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, ui
   // Last-layer words for the output index, held by lanes q < n of warp 0.
   const uint32_t* last = W + d * n;
 
+  // Philox planes do not depend on the chain state, so the first kPre calls
+  // (12 planes) of each class are computed one sweep ahead, interleaved with
+  // the previous sweep's dependent comparison chains.
+  uint32_t pidx[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) pidx[c] = (uint32_t)(mine[c].dst - n) | (kTagSweep << 16);
+  uint4 pre[4][kPre];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int j = 0; j < kPre; ++j)
+      pre[c][j] = philox4x32_10(make_uint4(gglob, sweep0, pidx[c], (uint32_t)j), k0, k1);
+
   for (uint32_t s = 0; s < n_sweeps; ++s) {
     const uint32_t sweep = sweep0 + s;
-    // Philox planes do not depend on the chain state: compute the first
-    // 3 calls (12 planes) of every class up front, independent of each other.
-    uint4 pre[4][kPre];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const uint32_t p = (uint32_t)(mine[c].dst - n) | (kTagSweep << 16);
-#pragma unroll
-      for (int j = 0; j < kPre; ++j)
-        pre[c][j] = has[c] ? philox4x32_10(make_uint4(gglob, sweep, p, (uint32_t)j), k0, k1)
-                           : make_uint4(0u, 0u, 0u, 0u);
-    }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
+      uint32_t lt = 0u, eq = ~0u;
+      HbClass k;
+      const Desc& D = mine[c];
       if (has[c]) {
-        const Desc& D = mine[c];
         const uint32_t r0 = W[D.a[0]] ^ W[D.b[0]];
         const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
         const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
-        const HbClass k = classify(D.mflag & 3, r0, r1, r2, thr0, thr1, thr2, thr3);
-        uint32_t lt = 0u, eq = ~0u;
+        k = classify(D.mflag & 3, r0, r1, r2, thr0, thr1, thr2, thr3);
         compare4(lt, eq, k, pre[c][0], 0u);
         eq &= ~k.tail0;
 #pragma unroll
         for (int j = 1; j < kPre; ++j) compare4(lt, eq, k, pre[c][j], (uint32_t)j);
-        if (eq != 0u) {
-          const uint32_t p = (uint32_t)(D.dst - n) | (kTagSweep << 16);
-          compare_tail(lt, eq, k, (uint32_t)kPre, gglob, sweep, p, k0, k1);
-        }
+      }
+      // next sweep's planes for this class (independent work for the scheduler)
+#pragma unroll
+      for (int j = 0; j < kPre; ++j)
+        pre[c][j] = philox4x32_10(make_uint4(gglob, sweep + 1u, pidx[c], (uint32_t)j), k0, k1);
+      if (has[c]) {
+        if (eq != 0u) compare_tail(lt, eq, k, (uint32_t)kPre, gglob, sweep, pidx[c], k0, k1);
         W[D.dst] = k.neg ^ lt;
       }
       // further p-bits of the class when it is larger than the CTA
       const int c_hi = mp->col_off[c + 1];
       for (int i = mp->col_off[c] + tid + T; i < c_hi; i += T) {
-        const Desc D = sdesc[i];
-        if (D.mflag & 0x80) continue;
-        const uint32_t r0 = W[D.a[0]] ^ W[D.b[0]];
-        const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
-        const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
-        const HbClass k = classify(D.mflag & 3, r0, r1, r2, thr0, thr1, thr2, thr3);
-        const uint32_t p = (uint32_t)(D.dst - n) | (kTagSweep << 16);
-        W[D.dst] = heat_bath_word(k, gglob, sweep, p, k0, k1);
+        const Desc E = sdesc[i];
+        if (E.mflag & 0x80) continue;
+        const uint32_t r0 = W[E.a[0]] ^ W[E.b[0]];
+        const uint32_t r1 = W[E.a[1]] ^ W[E.b[1]];
+        const uint32_t r2 = W[E.a[2]] ^ W[E.b[2]];
+        const HbClass kk = classify(E.mflag & 3, r0, r1, r2, thr0, thr1, thr2, thr3);
+        const uint32_t p = (uint32_t)(E.dst - n) | (kTagSweep << 16);
+        W[E.dst] = heat_bath_word(kk, gglob, sweep, p, k0, k1);
       }
       __syncthreads();
     }

@@ -138,9 +138,9 @@ class Workload:
 
 
 def tiny() -> Workload:
-    """n=3, d=4 (15 p-bits), 1024 chains x 1e4 sweeps, J = 4."""
+    """n=3, d=4 (15 p-bits), 1024 chains x 1e4 sweeps."""
     g = random_circuit(3, 4, seed=0)
-    return Workload("tiny", 3, 4, g, chains=1024, sweeps=10_000, seed=0x5EED, J=4.0)
+    return Workload("tiny", 3, 4, g, chains=1024, sweeps=10_000, seed=0x5EED, J=default_J(3, 4, g))
 
 
 def mid() -> Workload:
