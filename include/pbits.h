@@ -140,7 +140,9 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs,
                          uintptr_t stream, pb_run** out);
 
 /* Enqueues n_sweeps further sweeps of every chain of every model (one
- * launch; asynchronous).  Sweep indices continue from the previous call. */
+ * launch, replayed from a CUDA graph cached per n_sweeps; asynchronous).
+ * Sweep indices continue from the previous call.  n_sweeps <= 2^26 per call
+ * (PB_ERANGE otherwise); the total over a run stays below 2^32. */
 PB_API int pb_run_sweeps(pb_run* run, uint32_t n_sweeps);
 
 /* Waits for the run's stream; returns PB_OK, PB_ECUDA or the device status

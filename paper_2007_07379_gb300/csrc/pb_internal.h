@@ -66,6 +66,9 @@ struct RunModelDev {
   uint32_t seed_lo, seed_hi;
   uint32_t group_base;     // first flat group index of this model in a launch
   uint32_t group0;         // global index of group 0 (Philox counter word 0)
+  uint32_t hist_smem;      // 1: a CTA counts into shared memory and adds its
+                           //    counts to `hist` once at the end of a launch
+  uint32_t pad;
 };
 
 // Workspace header at offset 0.

@@ -19,16 +19,17 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
                         const uint32_t* const* d_init_tabs, size_t smem_bytes, WsHeader* hdr,
                         cudaStream_t st);
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
-                          uint32_t n_sweeps, int threads, size_t smem_bytes, WsHeader* hdr,
-                          cudaStream_t st);
+                          uint32_t n_sweeps, int cons, int prod, int max_col, size_t smem_bytes,
+                          WsHeader* hdr, cudaStream_t st);
 cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
-                                     uint32_t n_work, uint32_t n_sweeps, int threads, int grid,
-                                     size_t smem_bytes, WsHeader* hdr, cudaStream_t st);
+                                     uint32_t n_work, uint32_t n_sweeps, int cons, int prod,
+                                     int max_col, int grid, size_t smem_bytes, WsHeader* hdr,
+                                     cudaStream_t st);
 cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
                               cudaStream_t st);
 cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t count,
                                uint32_t* out, cudaStream_t st);
-size_t sweep_smem_bytes(int n, int d, int threads);
+size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins);
 cudaError_t sweep_prepare();
 int sweep_max_blocks_per_sm(int threads, size_t smem);
 }  // namespace pb
@@ -369,6 +370,7 @@ struct pb_run {
   std::vector<RunModelDev> rm;
   uint32_t total_groups = 0;
   int threads = 32;
+  int cons = 32, prod = 32, max_col = 1;
   size_t smem = 0;
   bool persistent = false;
   int grid = 0;
@@ -388,26 +390,44 @@ namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PB_OK : PB_ECUDA; }
 
-// Launch shape: threads per CTA = the largest colour class rounded up to a
-// warp (one p-bit per thread per class), capped at 256; environment override
-// PB_THREADS; persistent scheduling for batched runs.
+// Launch shape: consumers = the largest colour class rounded up to a warp
+// (one p-bit per consumer per class), capped at 224; producers = kPre
+// Philox calls per p-bit of that class, capped at 352; plus one recorder
+// warp.  Environment overrides PB_CONS, PB_PROD (multiples of 32).
+// Persistent scheduling for batched runs.
 void choose_shape(pb_run* r) {
   int maxcol = 1;
-  int maxn = 1, maxd = 1;
-  for (auto& m : r->models) {
+  for (auto& m : r->models)
     for (int c = 0; c < 4; ++c) maxcol = std::max(maxcol, m->col_off[c + 1] - m->col_off[c]);
-    maxn = std::max(maxn, m->n);
-    maxd = std::max(maxd, m->d);
-  }
-  int t = ((maxcol + 31) / 32) * 32;
-  t = std::max(32, std::min(256, t));
-  if (const char* e = std::getenv("PB_THREADS")) {
+  auto up32 = [](int x) { return ((x + 31) / 32) * 32; };
+  int cons = std::max(32, std::min(224, up32(maxcol)));
+  int prod = std::max(32, std::min(352, up32(3 * maxcol)));
+  if (const char* e = std::getenv("PB_CONS")) {
     int v = std::atoi(e);
-    if (v >= 32 && v <= 256 && v % 32 == 0) t = v;
+    if (v >= 32 && v <= 224 && v % 32 == 0) cons = v;
   }
-  r->threads = t;
+  if (const char* e = std::getenv("PB_PROD")) {
+    int v = std::atoi(e);
+    if (v >= 32 && v <= 352 && v % 32 == 0) prod = v;
+  }
+  r->cons = cons;
+  r->prod = prod;
+  r->max_col = maxcol;
+  r->threads = cons + prod + 32;
+  // Shared-memory histograms: counted per CTA, added to the global counters
+  // once per launch.  Used when the bins fit (128 KiB for one circuit, 32 KiB
+  // per circuit in a batch so that several CTAs share an SM); otherwise the
+  // record adds to global memory directly.
+  const size_t cap = r->nm == 1 ? (128u << 10) : (32u << 10);
   size_t smem = 0;
-  for (auto& m : r->models) smem = std::max(smem, sweep_smem_bytes(m->n, m->d, t));
+  for (int i = 0; i < r->nm; ++i) {
+    const pb_model& m = *r->models[i];
+    const uint32_t bins = r->L.ms[i].bins;
+    const size_t base = sweep_smem_bytes(m.n, m.d, cons, maxcol, 0);
+    const bool use = (size_t)bins * 32 <= cap && base + (size_t)bins * 32 <= (200u << 10);
+    r->rm[i].hist_smem = use ? 1u : 0u;
+    smem = std::max(smem, sweep_smem_bytes(m.n, m.d, cons, maxcol, use ? bins : 0));
+  }
   r->smem = smem;
   r->persistent = r->nm > 1;
   if (const char* e = std::getenv("PB_PERSISTENT")) r->persistent = std::atoi(e) != 0;
@@ -415,7 +435,7 @@ void choose_shape(pb_run* r) {
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = sweep_max_blocks_per_sm(t, smem);
+    int per_sm = sweep_max_blocks_per_sm(r->threads, smem);
     r->grid = std::max(1, sms * std::max(1, per_sm));
     r->grid = (int)std::min<uint32_t>((uint32_t)r->grid, r->total_groups);
   }
@@ -540,14 +560,14 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
                      return a.first > b.first;
                    });
   for (auto& c : cost) work.push_back(c.second);
+  if (sweep_prepare() != cudaSuccess) return PB_ECUDA;
+  choose_shape(r.get());
   if ((e = cudaMemcpyAsync(ws + r->L.rm, r->rm.data(), sizeof(RunModelDev) * n_models,
                            cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(ws + r->L.init_ptrs, init_ptrs.data(), sizeof(uint32_t*) * n_models,
                            cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(ws + r->L.work, work.data(), work.size() * 4, cudaMemcpyHostToDevice, st)))
     return PB_ECUDA;
-  if (sweep_prepare() != cudaSuccess) return PB_ECUDA;
-  choose_shape(r.get());
   size_t init_smem = 0;
   for (auto& m : r->models) init_smem = std::max(init_smem, (size_t)n_words(m->n, m->d) * 4);
   e = launch_init(r->d_rm(), n_models, r->total_groups,
@@ -567,6 +587,7 @@ PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
   if (!r) return PB_EINVAL;
   if (n_sweeps == 0) return PB_OK;
   if (r->sweeps_done + n_sweeps > 0xFFFFFFFFull) return PB_ERANGE;
+  if (n_sweeps > (1u << 26)) return PB_ERANGE;  // per-launch u32 shared counters
   cudaGraphExec_t exec = nullptr;
   auto it = r->graphs.find(n_sweeps);
   if (it != r->graphs.end()) {
@@ -579,11 +600,11 @@ PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
     if (e != cudaSuccess) return PB_ECUDA;
     if (r->persistent)
       e = launch_sweeps_persistent(r->d_rm(), r->nm, reinterpret_cast<const uint32_t*>(r->ws + r->L.work),
-                                   r->total_groups, n_sweeps, r->threads, r->grid, r->smem, r->hdr(),
-                                   r->cap_st);
+                                   r->total_groups, n_sweeps, r->cons, r->prod, r->max_col, r->grid,
+                                   r->smem, r->hdr(), r->cap_st);
     else
-      e = launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->threads, r->smem, r->hdr(),
-                        r->cap_st);
+      e = launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->cons, r->prod, r->max_col,
+                        r->smem, r->hdr(), r->cap_st);
     cudaError_t e2 = cudaStreamEndCapture(r->cap_st, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);

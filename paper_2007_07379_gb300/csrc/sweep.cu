@@ -68,19 +68,24 @@ __device__ __forceinline__ void compare4(uint32_t& lt, uint32_t& eq, const HbCla
   }
 }
 
+// Out-of-line Philox for the rarely taken paths (keeps the hot loop small).
+__device__ __noinline__ uint4 philox_cold(uint4 c, uint32_t k0, uint32_t k1) {
+  return philox4x32_10(c, k0, k1);
+}
+
 // Planes beyond the precomputed ones (rare): Philox calls grp0 .. 7.
 __device__ __forceinline__ void compare_tail(uint32_t& lt, uint32_t& eq, const HbClass& k,
                                              uint32_t grp0, uint32_t g, uint32_t sweep, uint32_t p,
                                              uint32_t k0, uint32_t k1) {
 #pragma unroll 1
   for (uint32_t grp = grp0; grp < 8u && eq != 0u; ++grp)
-    compare4(lt, eq, k, philox4x32_10(make_uint4(g, sweep, p, grp), k0, k1), grp);
+    compare4(lt, eq, k, philox_cold(make_uint4(g, sweep, p, grp), k0, k1), grp);
 }
 
 __device__ __forceinline__ uint32_t heat_bath_word(const HbClass& k, uint32_t g, uint32_t sweep,
                                                    uint32_t p, uint32_t k0, uint32_t k1) {
   uint32_t lt = 0u, eq = ~0u;
-  compare4(lt, eq, k, philox4x32_10(make_uint4(g, sweep, p, 0u), k0, k1), 0u);
+  compare4(lt, eq, k, philox_cold(make_uint4(g, sweep, p, 0u), k0, k1), 0u);
   eq &= ~k.tail0;
   compare_tail(lt, eq, k, 1u, g, sweep, p, k0, k1);
   return k.neg ^ lt;
@@ -112,37 +117,158 @@ __device__ __forceinline__ void set_status(WsHeader* hdr, int code) {
   if (hdr) atomicCAS(&hdr->status, 0u, (uint32_t)code);
 }
 
-// Shared-memory image of one group: words, descriptors, record terms and the
-// reduction scratch.  Returns the byte count for (n, d, threads).
-__host__ __device__ inline size_t group_smem_bytes(int n, int d, int threads) {
-  const size_t words = ((size_t)n_words(n, d) + 3) & ~(size_t)3;
-  return words * 4 + (size_t)n * d * sizeof(Desc) + (size_t)n * d * sizeof(Rec) +
-         (size_t)2 * (threads / 32) * 4 * sizeof(uint32_t);
+// CTA roles: `cons` consumer threads redraw the p-bits of the current colour
+// class; `prod` producer threads compute the Philox planes of the next class
+// into shared memory; one recorder warp (the last) records the previous sweep.
+struct Shape {
+  int cons, prod;
+};
+
+// Consumer view of one p-bit of a class: the descriptor in branch-free form
+// and its threshold pair.  flags: bit 0 m == 2, bit 1 m == 0.
+struct ClassEnt {
+  Desc D;
+  uint32_t tA, tB, flags, pidx;
+};
+static_assert(sizeof(ClassEnt) == 32, "ClassEnt must be 32 bytes");
+
+// Shared-memory image of one group: words (image_words) and two snapshots,
+// descriptors, record terms, an optional histogram of hist_bins x 8 u32
+// counters, the consumers' class table and two plane buffers of
+// kPre x max_col Philox outputs.  The image holds the (d+1) n layer words,
+// ZERO, ONES and one scratch word (the store target of consumers without a
+// p-bit in a colour class), rounded up to 16 bytes.
+__host__ __device__ inline int image_words(int n, int d) { return (n_words(n, d) + 1 + 3) & ~3; }
+
+__host__ __device__ inline size_t group_smem_bytes(int n, int d, int cons, int max_col,
+                                                   uint32_t hist_bins) {
+  return (size_t)3 * image_words(n, d) * 4 + (size_t)n * d * sizeof(Desc) +
+         (size_t)n * d * sizeof(Rec) + (size_t)hist_bins * 8 * 4 +
+         (size_t)4 * cons * sizeof(ClassEnt) + (size_t)2 * kPre * max_col * sizeof(uint4);
 }
 
+// 32 x 32 bit transpose across a warp: on entry lane r holds row r; on
+// return lane c holds column c (bit r = bit c of row r).  Five butterfly
+// steps, each swapping the off-diagonal blocks of the current block size.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int j = 16 >> k;
+    const uint32_t M = masks[k];
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~M) | ((y & ~M) >> j)) : ((x & M) | ((y & M) << j));
+  }
+  return x;
+}
+
+// Record of one sweep (Fig. 2 Step 3), computed by the recorder warp from a
+// snapshot of the sweep's final state while the stage warps run the next
+// sweep, pipelined over the colour stages: read() gathers, for a range of
+// p-bits, the violation word and the phase (three bit planes, mod 8);
+// reduce() combines the lanes and takes the last layer; bin() adds one count
+// per valid chain to (end state alpha, phase class).
+struct Recorder {
+  uint32_t viol = 0u, f0 = 0u, f1 = 0u, f2 = 0u, lastw = 0u;
+
+  __device__ void clear() { viol = f0 = f1 = f2 = 0u; }
+
+  __device__ void read(const uint32_t* S, const Rec* srec, int lo, int hi, int lane) {
+#pragma unroll 2
+    for (int i = lo + lane; i < hi; i += 32) {
+      const Rec R = srec[i];
+      viol |= S[R.vd] ^ S[R.va] ^ S[R.vb];
+      const uint32_t x = S[R.pa] & S[R.pb];
+      add3(f0, f1, f2, (R.w & 1) ? x : 0u, (R.w & 2) ? x : 0u, (R.w & 4) ? x : 0u);
+    }
+  }
+
+  __device__ void reduce(const uint32_t* S, int n, int d, int lane) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const uint32_t ov = __shfl_xor_sync(0xffffffffu, viol, off);
+      const uint32_t o0 = __shfl_xor_sync(0xffffffffu, f0, off);
+      const uint32_t o1 = __shfl_xor_sync(0xffffffffu, f1, off);
+      const uint32_t o2 = __shfl_xor_sync(0xffffffffu, f2, off);
+      viol |= ov;
+      add3(f0, f1, f2, o0, o1, o2);
+    }
+    lastw = lane < n ? S[d * n + lane] : 0u;
+  }
+
+  __device__ void bin(const RunModelDev& rm, uint32_t g, uint32_t batch, int lane, uint32_t* shist,
+                      unsigned long long& n_valid, unsigned long long& n_samples) {
+    // lane = chain within the group; alpha bit q = bit `lane` of layer-d word q
+    const uint32_t chain = g * 32u + (uint32_t)lane;
+    const bool active = chain < rm.chains;
+    const bool valid = active && !((viol >> lane) & 1u);
+    const uint32_t alpha = warp_transpose32(lastw, lane);
+    const uint32_t phase = ((f0 >> lane) & 1u) | (((f1 >> lane) & 1u) << 1) |
+                           (((f2 >> lane) & 1u) << 2);
+    int bin = -1;
+    if (valid) {
+      const int na = rm.n_alphas;
+      if (na == 0) {
+        bin = (int)alpha;
+      } else {
+        int lo = 0, hi = na - 1;
+        while (lo <= hi) {
+          const int mid = (lo + hi) >> 1;
+          const uint32_t v = rm.alpha_sorted[mid];
+          if (v == alpha) { bin = rm.alpha_slot[mid]; break; }
+          if (v < alpha) lo = mid + 1; else hi = mid - 1;
+        }
+      }
+    }
+    if (bin >= 0) {
+      if (shist) atomicAdd(&shist[(uint32_t)bin * 8u + phase], 1u);
+      else atomicAdd(&rm.hist[((size_t)batch * rm.bins + (uint32_t)bin) * 8u + phase], 1ull);
+    }
+    n_valid += __popc(__ballot_sync(0xffffffffu, valid));
+    n_samples += __popc(__ballot_sync(0xffffffffu, active));
+  }
+};
+
 // Runs `n_sweeps` sweeps (absolute indices sweep0...) of one chain group.
-__device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, uint32_t n_sweeps,
-                          uint32_t* smem, WsHeader* hdr) {
-  const ModelDev* mp = rm.model;
-  const int n = mp->n, d = mp->d, nw = mp->nw;
+__device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, uint32_t n_sweeps,
+                          Shape sh, int max_col_all, uint32_t* smem, WsHeader* hdr) {
+  // run and model constants held in registers for the whole launch
+  const RunModelDev rm = rm_g;
+  const ModelDev md = *rm.model;
+  const int n = md.n, d = md.d, nw = md.nw;
   const int npb = n * d;
   const int tid = threadIdx.x, T = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
+  const bool recorder = warp == nwarps - 1;
+  const bool consumer = tid < sh.cons;
+  const bool producer = !consumer && !recorder;
+  const int ptid = tid - sh.cons;
 
+  const int iw = image_words(n, d);
   uint32_t* W = smem;
-  Desc* sdesc = reinterpret_cast<Desc*>(smem + ((nw + 3) & ~3));
+  // snapshots of the final state of even / odd sweeps at smem + iw (1 + parity)
+  Desc* sdesc = reinterpret_cast<Desc*>(smem + 3 * iw);
   Rec* srec = reinterpret_cast<Rec*>(sdesc + npb);
-  uint32_t* red = reinterpret_cast<uint32_t*>(srec + npb);
+  uint32_t* after_rec = reinterpret_cast<uint32_t*>(srec + npb);
+  uint32_t* shist = rm.hist_smem ? after_rec : nullptr;
+  const uint32_t hist_words = rm.bins * 8u;
+  ClassEnt* sclass = reinterpret_cast<ClassEnt*>(after_rec + (rm.hist_smem ? hist_words : 0u));
+  uint4* planes = reinterpret_cast<uint4*>(sclass + 4 * sh.cons);  // [2][max_col][kPre]
+  const int pbuf = max_col_all * kPre;
 
   // ---- load the group image and the tables
   const uint32_t* gstate = rm.state + (size_t)g * npb;
+#pragma unroll 1
   for (int i = tid; i < nw; i += T) {
     uint32_t v;
-    if (i < n) v = ((mp->beta >> i) & 1u) ? ~0u : 0u;        // clamped input layer
+    if (i < n) v = ((md.beta >> i) & 1u) ? ~0u : 0u;        // clamped input layer
     else if (i < (d + 1) * n) v = gstate[i - n];
     else v = (i == zero_idx(n, d)) ? 0u : ~0u;
     W[i] = v;
+    smem[iw + i] = v;
+    smem[2 * iw + i] = v;
   }
+#pragma unroll 1
   for (int i = tid; i < npb; i += T) {
     Desc D = rm.desc[i];
     bool ok = D.dst < nw;
@@ -161,170 +287,200 @@ __device__ void run_group(const RunModelDev& rm, uint32_t g, uint32_t sweep0, ui
     }
     srec[i] = R;
   }
+  if (shist) {
+#pragma unroll 1
+    for (uint32_t i = tid; i < hist_words; i += T) shist[i] = 0u;
+  }
   __syncthreads();
 
-  const uint32_t thr0 = mp->thr[0], thr1 = mp->thr[1], thr2 = mp->thr[2], thr3 = mp->thr[3];
+  const uint32_t thr0 = md.thr[0], thr1 = md.thr[1], thr2 = md.thr[2], thr3 = md.thr[3];
   const uint32_t k0 = rm.seed_lo, k1 = rm.seed_hi;
   const uint32_t batch = g % rm.n_batches;
   const uint32_t gglob = g + rm.group0;
+  // planes 1 .. lz-1 carry a zero bit in every threshold below 2^31: there
+  // only `eq &= ~R` remains of the comparison (t0 lanes are decided by plane 0)
+  const int lz = __clz(thr1 | 1u);
+  int col_lo[4], col_hi[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) { col_lo[c] = md.col_off[c]; col_hi[c] = md.col_off[c + 1]; }
+  auto lo_of = [&](int c) { return c == 0 ? col_lo[0] : c == 1 ? col_lo[1] : c == 2 ? col_lo[2] : col_lo[3]; };
+  auto hi_of = [&](int c) { return c == 0 ? col_hi[0] : c == 1 ? col_hi[1] : c == 2 ? col_hi[2] : col_hi[3]; };
 
-  // This thread's first p-bit of each colour class, kept in registers.
-  Desc mine[4];
-  bool has[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int i = mp->col_off[c] + tid;
-    has[c] = i < mp->col_off[c + 1] && !(sdesc[i < npb ? i : 0].mflag & 0x80);
-    mine[c] = sdesc[has[c] ? i : 0];
-  }
-  // Last-layer words for the output index, held by lanes q < n of warp 0.
-  const uint32_t* last = W + d * n;
-
-  // Philox planes do not depend on the chain state, so the first kPre calls
-  // (12 planes) of each class are computed one sweep ahead, interleaved with
-  // the previous sweep's dependent comparison chains.
-  uint32_t pidx[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) pidx[c] = (uint32_t)(mine[c].dst - n) | (kTagSweep << 16);
-  uint4 pre[4][kPre];
-#pragma unroll
-  for (int c = 0; c < 4; ++c)
-#pragma unroll
-    for (int j = 0; j < kPre; ++j)
-      pre[c][j] = philox4x32_10(make_uint4(gglob, sweep0, pidx[c], (uint32_t)j), k0, k1);
-
-  for (uint32_t s = 0; s < n_sweeps; ++s) {
-    const uint32_t sweep = sweep0 + s;
+  // Consumer class table (branch-free form): consumers without a p-bit get a
+  // dummy with links to ZERO that stores into the scratch word; a single link
+  // is duplicated so that the majority of (r0, r1, r2) is the demanded value
+  // for every link count m:  m=0: 0,0,0  m=1: r0,r0,0  m=2: r0,r1,0  m=3: r0,r1,r2.
+  if (consumer) {
+    const uint16_t scratch = (uint16_t)nw;
+    const uint16_t zw = (uint16_t)zero_idx(n, d);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      uint32_t lt = 0u, eq = ~0u;
-      HbClass k;
-      const Desc& D = mine[c];
-      if (has[c]) {
+      const int i = col_lo[c] + tid;
+      bool has = i < col_hi[c];
+      Desc D = sdesc[has ? i : 0];
+      has = has && !(D.mflag & 0x80);
+      if (!has) {
+        D.dst = scratch;
+        D.mflag = 0;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) { D.a[l] = zw; D.b[l] = zw; }
+      }
+      const int m = D.mflag & 3;
+      if (m == 1) { D.a[1] = D.a[0]; D.b[1] = D.b[0]; }
+      ClassEnt E;
+      E.D = D;
+      E.tA = m == 0 ? thr0 : (m == 1 ? thr1 : (m == 2 ? thr2 : thr3));
+      E.tB = (m == 0 || m == 2) ? thr0 : thr1;
+      E.flags = (m == 2 ? 1u : 0u) | (m == 0 ? 2u : 0u);
+      E.pidx = (uint32_t)(D.dst - n) | (kTagSweep << 16);
+      sclass[c * sh.cons + tid] = E;
+    }
+  }
+  // Producers: the planes of step 0 (class 0 of sweep0).
+  auto produce = [&](uint32_t step, uint4* buf) {
+    const int c = (int)(step & 3u);
+    const uint32_t sw = sweep0 + (step >> 2);
+    const int lo = lo_of(c), K = hi_of(c) - lo;
+#pragma unroll 1
+    for (int u = ptid; u < K * kPre; u += sh.prod) {
+      const int i = u / kPre, j = u - i * kPre;
+      const uint32_t p = (uint32_t)(sdesc[lo + i].dst - n) | (kTagSweep << 16);
+      buf[u] = philox4x32_10(make_uint4(gglob, sw, p, (uint32_t)j), k0, k1);
+    }
+  };
+  if (producer) produce(0u, planes);
+  __syncthreads();
+
+  Recorder rec;
+  bool bin_pending = false;
+  unsigned long long n_valid = 0ull, n_samples = 0ull;  // recorder warp only
+  auto recorded = [&](uint32_t t) {
+    return t >= rm.burn_in && (rm.record_every == 1u || (t - rm.burn_in) % rm.record_every == 0);
+  };
+  const uint32_t n_steps = 4u * n_sweeps;
+#pragma unroll 1
+  for (uint32_t t = 0; t < n_steps; ++t) {
+    const int c = (int)(t & 3u);
+    const uint32_t s = t >> 2;
+    const uint32_t sweep = sweep0 + s;
+    uint32_t* S = smem + iw * (1 + (s & 1u));
+    const uint4* cur = planes + (t & 1u) * pbuf;
+    if (consumer) {
+      const int lo = lo_of(c), hi = hi_of(c);
+#pragma unroll 1
+      for (int i = lo + tid, e = 0; i < hi || e == 0; i += sh.cons, ++e) {
+        // the first round uses the class table; further p-bits (a class larger
+        // than the consumers) are rare and read their descriptor directly
+        ClassEnt E;
+        if (e == 0) {
+          E = sclass[c * sh.cons + tid];
+        } else {
+          E.D = sdesc[i];
+          if (E.D.mflag & 0x80) continue;
+          const int m = E.D.mflag & 3;
+          if (m == 1) { E.D.a[1] = E.D.a[0]; E.D.b[1] = E.D.b[0]; }
+          E.tA = m == 0 ? thr0 : (m == 1 ? thr1 : (m == 2 ? thr2 : thr3));
+          E.tB = (m == 0 || m == 2) ? thr0 : thr1;
+          E.flags = (m == 2 ? 1u : 0u) | (m == 0 ? 2u : 0u);
+          E.pidx = (uint32_t)(E.D.dst - n) | (kTagSweep << 16);
+        }
+        const Desc& D = E.D;
         const uint32_t r0 = W[D.a[0]] ^ W[D.b[0]];
         const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
         const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
-        k = classify(D.mflag & 3, r0, r1, r2, thr0, thr1, thr2, thr3);
-        compare4(lt, eq, k, pre[c][0], 0u);
+        HbClass k;
+        k.neg = (r0 & r1) | (r2 & (r0 | r1));
+        k.sel = ~(r0 ^ r1) & (~(r1 ^ r2) | ((E.flags & 1u) ? ~0u : 0u));
+        k.tail0 = (E.flags & 2u) ? ~0u : ((E.flags & 1u) ? ~k.sel : 0u);
+        k.tA = E.tA;
+        k.tB = E.tB;
+        const int slot = i - lo;  // position in the class
+        uint4 R[kPre];
+        if (slot < hi - lo) {
+#pragma unroll
+          for (int j = 0; j < kPre; ++j) R[j] = cur[slot * kPre + j];
+        } else {
+#pragma unroll
+          for (int j = 0; j < kPre; ++j) R[j] = make_uint4(~0u, ~0u, ~0u, ~0u);
+        }
+        uint32_t lt = 0u, eq = ~0u;
+        compare4(lt, eq, k, R[0], 0u);
         eq &= ~k.tail0;
 #pragma unroll
-        for (int j = 1; j < kPre; ++j) compare4(lt, eq, k, pre[c][j], (uint32_t)j);
-      }
-      // next sweep's planes for this class (independent work for the scheduler)
-#pragma unroll
-      for (int j = 0; j < kPre; ++j)
-        pre[c][j] = philox4x32_10(make_uint4(gglob, sweep + 1u, pidx[c], (uint32_t)j), k0, k1);
-      if (has[c]) {
-        if (eq != 0u) compare_tail(lt, eq, k, (uint32_t)kPre, gglob, sweep, pidx[c], k0, k1);
-        W[D.dst] = k.neg ^ lt;
-      }
-      // further p-bits of the class when it is larger than the CTA
-      const int c_hi = mp->col_off[c + 1];
-      for (int i = mp->col_off[c] + tid + T; i < c_hi; i += T) {
-        const Desc E = sdesc[i];
-        if (E.mflag & 0x80) continue;
-        const uint32_t r0 = W[E.a[0]] ^ W[E.b[0]];
-        const uint32_t r1 = W[E.a[1]] ^ W[E.b[1]];
-        const uint32_t r2 = W[E.a[2]] ^ W[E.b[2]];
-        const HbClass kk = classify(E.mflag & 3, r0, r1, r2, thr0, thr1, thr2, thr3);
-        const uint32_t p = (uint32_t)(E.dst - n) | (kTagSweep << 16);
-        W[E.dst] = heat_bath_word(kk, gglob, sweep, p, k0, k1);
-      }
-      __syncthreads();
-    }
-
-    if (sweep < rm.burn_in || (sweep - rm.burn_in) % rm.record_every != 0) continue;
-
-    // ---- record (Fig. 2 Step 3): validity and phase, bit-sliced over chains
-    uint32_t viol = 0u, f0 = 0u, f1 = 0u, f2 = 0u;
-    for (int i = tid; i < npb; i += T) {
-      const Rec R = srec[i];
-      viol |= W[R.vd] ^ W[R.va] ^ W[R.vb];
-      const uint32_t x = W[R.pa] & W[R.pb];
-      add3(f0, f1, f2, (R.w & 1) ? x : 0u, (R.w & 2) ? x : 0u, (R.w & 4) ? x : 0u);
-    }
-    const uint32_t lastw = (warp == 0 && lane < n) ? last[lane] : 0u;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const uint32_t ov = __shfl_xor_sync(0xffffffffu, viol, off);
-      const uint32_t o0 = __shfl_xor_sync(0xffffffffu, f0, off);
-      const uint32_t o1 = __shfl_xor_sync(0xffffffffu, f1, off);
-      const uint32_t o2 = __shfl_xor_sync(0xffffffffu, f2, off);
-      viol |= ov;
-      add3(f0, f1, f2, o0, o1, o2);
-    }
-    // two slots of partials alternate between sweeps, so warp 0 can finish
-    // this record while the other warps start the next sweep
-    uint32_t* slot = red + (s & 1u) * 4 * nwarps;
-    if (lane == 0) {
-      slot[warp * 4 + 0] = viol;
-      slot[warp * 4 + 1] = f0;
-      slot[warp * 4 + 2] = f1;
-      slot[warp * 4 + 3] = f2;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      viol = 0u; f0 = f1 = f2 = 0u;
-      if (lane < nwarps) {
-        viol = slot[lane * 4 + 0];
-        f0 = slot[lane * 4 + 1];
-        f1 = slot[lane * 4 + 2];
-        f2 = slot[lane * 4 + 3];
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const uint32_t ov = __shfl_xor_sync(0xffffffffu, viol, off);
-        const uint32_t o0 = __shfl_xor_sync(0xffffffffu, f0, off);
-        const uint32_t o1 = __shfl_xor_sync(0xffffffffu, f1, off);
-        const uint32_t o2 = __shfl_xor_sync(0xffffffffu, f2, off);
-        viol |= ov;
-        add3(f0, f1, f2, o0, o1, o2);
-      }
-      // lane = chain within the group
-      const uint32_t chain = g * 32u + (uint32_t)lane;
-      const bool active = chain < rm.chains;
-      const bool valid = active && !((viol >> lane) & 1u);
-      uint32_t alpha = 0u;
-      for (int q = 0; q < n; ++q)
-        alpha |= ((__shfl_sync(0xffffffffu, lastw, q) >> lane) & 1u) << q;
-      const uint32_t phase = ((f0 >> lane) & 1u) | (((f1 >> lane) & 1u) << 1) |
-                             (((f2 >> lane) & 1u) << 2);
-      int bin = -1;
-      if (valid) {
-        if (rm.n_alphas == 0) {
-          bin = (int)alpha;
-        } else {
-          int lo = 0, hi = rm.n_alphas - 1;
-          while (lo <= hi) {
-            const int mid = (lo + hi) >> 1;
-            const uint32_t v = rm.alpha_sorted[mid];
-            if (v == alpha) { bin = rm.alpha_slot[mid]; break; }
-            if (v < alpha) lo = mid + 1; else hi = mid - 1;
+        for (int j = 1; j < kPre; ++j) {
+          if (4 * j + 3 < lz) {
+            eq &= ~(R[j].x | R[j].y | R[j].z | R[j].w);
+          } else {
+            compare4(lt, eq, k, R[j], (uint32_t)j);
           }
         }
+        if (eq != 0u) compare_tail(lt, eq, k, (uint32_t)kPre, gglob, sweep, E.pidx, k0, k1);
+        const uint32_t v = k.neg ^ lt;
+        W[D.dst] = v;
+        S[D.dst] = v;
       }
-      if (bin >= 0)
-        atomicAdd(&rm.hist[((size_t)batch * rm.bins + (uint32_t)bin) * 8u + phase], 1ull);
-      const uint32_t nvalid = __popc(__ballot_sync(0xffffffffu, valid));
-      const uint32_t nactive = __popc(__ballot_sync(0xffffffffu, active));
-      if (lane == 0) {
-        atomicAdd(&rm.valid[batch], (unsigned long long)nvalid);
-        atomicAdd(&rm.samples[batch], (unsigned long long)nactive);
+    } else if (producer) {
+      if (t + 1 < n_steps) produce(t + 1, planes + ((t + 1) & 1u) * pbuf);
+    } else {
+      // records run one sweep behind: the record of sweep s-1 reads its
+      // snapshot in classes 1-2 of sweep s, reduces in class 3 and is binned
+      // in class 0 of sweep s+1
+      if (c == 0 && bin_pending) {
+        rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
+        bin_pending = false;
       }
+      if (s > 0 && recorded(sweep - 1)) {
+        const uint32_t* Sp = smem + iw * (1 + ((s + 1u) & 1u));
+        if (c == 1) {
+          rec.clear();
+          rec.read(Sp, srec, 0, npb / 2, lane);
+        } else if (c == 2) {
+          rec.read(Sp, srec, npb / 2, npb, lane);
+        } else if (c == 3) {
+          rec.reduce(Sp, n, d, lane);
+          bin_pending = true;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // the records still in flight: the previous sweep's binning and the last sweep
+  if (recorder) {
+    if (bin_pending) rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
+    if (n_sweeps > 0 && recorded(sweep0 + n_sweeps - 1)) {
+      const uint32_t* Sl = smem + iw * (1 + ((n_sweeps - 1u) & 1u));
+      rec.clear();
+      rec.read(Sl, srec, 0, npb, lane);
+      rec.reduce(Sl, n, d, lane);
+      rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
     }
   }
   __syncthreads();
 
-  // ---- write the group image back
+  // ---- write the group image back, add the counts of this launch
   uint32_t* out = rm.state + (size_t)g * npb;
+#pragma unroll 1
   for (int i = tid; i < npb; i += T) out[i] = W[n + i];
+  if (shist) {
+    unsigned long long* gh = rm.hist + (size_t)batch * rm.bins * 8u;
+#pragma unroll 1
+    for (uint32_t i = tid; i < hist_words; i += T)
+      if (shist[i]) atomicAdd(&gh[i], (unsigned long long)shist[i]);
+  }
+  if (recorder && lane == 0) {
+    if (n_valid) atomicAdd(&rm_g.valid[batch], n_valid);
+    if (n_samples) atomicAdd(&rm_g.samples[batch], n_samples);
+  }
   __syncthreads();
 }
 
 // One CTA per chain group of every model of the run (flat group index).
-__global__ void __launch_bounds__(256) sweep_kernel(const RunModelDev* __restrict__ rm,
+constexpr int kMaxThreads = 608;  // 224 consumers + 352 producers + 1 recorder warp
+
+__global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const RunModelDev* __restrict__ rm,
                                                      int n_models, uint32_t total_groups,
-                                                     uint32_t n_sweeps, WsHeader* hdr) {
+                                                     uint32_t n_sweeps, Shape sh, int max_col,
+                                                     WsHeader* hdr) {
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t sweep0 = hdr->sweep0;
   const uint32_t flat = blockIdx.x;
@@ -333,14 +489,14 @@ __global__ void __launch_bounds__(256) sweep_kernel(const RunModelDev* __restric
   const RunModelDev& r = rm[mi];
   const uint32_t g = flat - r.group_base;
   if (g >= r.groups) return;
-  run_group(r, g, sweep0, n_sweeps, smem, hdr);
+  run_group(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
 }
 
 // Persistent form: a fixed grid pops (model, group) items from a
 // cost-ordered work list with one atomic counter.  No CTA waits on another.
-__global__ void __launch_bounds__(256) sweep_persistent_kernel(
+__global__ void __launch_bounds__(kMaxThreads) sweep_persistent_kernel(
     const RunModelDev* __restrict__ rm, int n_models, const uint32_t* __restrict__ work,
-    uint32_t n_work, uint32_t n_sweeps, WsHeader* hdr) {
+    uint32_t n_work, uint32_t n_sweeps, Shape sh, int max_col, WsHeader* hdr) {
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t sweep0 = hdr->sweep0;
   __shared__ uint32_t item;
@@ -354,7 +510,7 @@ __global__ void __launch_bounds__(256) sweep_persistent_kernel(
     const int mi = find_model(rm, n_models, flat);
     const RunModelDev& r = rm[mi];
     const uint32_t g = flat - r.group_base;
-    if (g < r.groups) run_group(r, g, sweep0, n_sweeps, smem, hdr);
+    if (g < r.groups) run_group(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
   }
 }
 
@@ -521,22 +677,25 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
 __global__ void advance_kernel(WsHeader* hdr, uint32_t n_sweeps) { hdr->sweep0 += n_sweeps; }
 
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
-                          uint32_t n_sweeps, int threads, size_t smem_bytes,
+                          uint32_t n_sweeps, int cons, int prod, int max_col, size_t smem_bytes,
                           WsHeader* hdr, cudaStream_t st) {
+  const int threads = cons + prod + 32;
   sweep_kernel<<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups,
-                                                          n_sweeps, hdr);
+                                                          n_sweeps, Shape{cons, prod}, max_col, hdr);
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
-                                     uint32_t n_work, uint32_t n_sweeps,
-                                     int threads, int grid, size_t smem_bytes, WsHeader* hdr,
+                                     uint32_t n_work, uint32_t n_sweeps, int cons, int prod,
+                                     int max_col, int grid, size_t smem_bytes, WsHeader* hdr,
                                      cudaStream_t st) {
+  const int threads = cons + prod + 32;
   cudaError_t e = cudaMemsetAsync(&hdr->work_next, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   sweep_persistent_kernel<<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work,
-                                                              n_sweeps, hdr);
+                                                              n_sweeps, Shape{cons, prod}, max_col,
+                                                              hdr);
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
 }
@@ -556,7 +715,9 @@ cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, ui
   return cudaGetLastError();
 }
 
-size_t sweep_smem_bytes(int n, int d, int threads) { return group_smem_bytes(n, d, threads); }
+size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins) {
+  return group_smem_bytes(n, d, cons, max_col, hist_bins);
+}
 
 // Opt the sweep kernels into large dynamic shared memory (called once per
 // run, outside any stream capture).
