@@ -134,15 +134,16 @@ def dist_env():
 
 def cpu_oracle_rate(wl, budget_s: float = 12.0, chains: int | None = None):
     """The oracle's reference Gibbs sampler on a bounded sample of the same
-    workload (host cores, OpenMP over chains).  Returns (flips/s, cores, sample)."""
+    workload (host cores, OpenMP over chains, about `budget_s` seconds).
+    Returns (flips/s, cores, sample)."""
     import oracle
     n, d = wl.n, wl.d
-    c = chains or 64
+    c = chains or 128
     t0 = time.perf_counter()
-    oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=2)
+    oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=20)
     dt = max(time.perf_counter() - t0, 1e-3)
-    sweeps = max(2, int(budget_s / dt * 2 * 0.8))
-    sweeps = min(sweeps, 2000)
+    sweeps = max(2, int(budget_s / dt * 20))
+    sweeps = min(sweeps, 200_000)
     t0 = time.perf_counter()
     oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=sweeps)
     dt = time.perf_counter() - t0
@@ -287,8 +288,9 @@ def main():
         try:
             with open(prof) as f:
                 tr = json.load(f)
-            if tr.get("kernel_rev") == kernel_rev():
-                roofline["traffic"] = tr["dram_bytes_per_launch_per_sweep"] * S
+            # the stored capture covers one launch of its own sweep count
+            if tr.get("kernel_rev") == kernel_rev() and tr.get("sweeps_per_launch") == S:
+                roofline["traffic"] = tr["dram_bytes_read_per_launch"] + tr["dram_bytes_write_per_launch"]
         except Exception:
             pass
 
