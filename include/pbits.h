@@ -194,6 +194,35 @@ PB_API void pb_run_free(pb_run* run);
 PB_API int pb_philox_fill(const uint32_t* d_ctr, uint32_t k0, uint32_t k1,
                           uint32_t count, uint32_t* d_out, uintptr_t stream);
 
+/* ---- a run that allocates nothing ------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory where they call the library (a plug-in
+ * whose host application owns every device allocation, or code that runs
+ * while a memory budget is frozen).  It is one complete plain Gibbs run (the
+ * same kernels and results as pb_run_create + pb_run_sweeps + the histogram)
+ * whose scratch -- run header, tables, chain state, counters -- lives in a
+ * fixed 16 MiB array in device memory that every GPU loading the library
+ * holds until the process exits.  It calls no allocator.
+ *   m        compiled model, n <= 16 (the full 2^n histogram is recorded).
+ *   cfg      as for pb_run_create; alphas must be NULL, sampler PB_GIBBS.
+ *            The run starts at sweep 0 from freshly drawn valid paths.
+ *   n_sweeps sweeps to run (<= 2^26).
+ *   d_counts device buffer of 2^n * 8 u64: counts[alpha*8 + b] of valid
+ *            samples ending in alpha with phase w^b (the histogram).
+ *   d_totals device buffer of 2 u64: valid samples, all samples.
+ * Asynchronous on `stream`; the outputs are complete when the stream
+ * reaches them.  Returns PB_ERANGE when the run does not fit the array
+ * (groups * n * d * 4 + 2^n * 64 bytes plus tables must stay below 16 MiB,
+ * e.g. 4096 chains of n=12, d=20), PB_EINVAL for bad arguments.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and each leaves its contents
+ * behind: every call clears what must start at zero, and calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on it. */
+PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* cfg, uint32_t n_sweeps,
+                                unsigned long long* d_counts, unsigned long long* d_totals,
+                                uintptr_t stream);
+
 PB_API const char* pb_strerror(int status);
 PB_API int pb_version(void);
 

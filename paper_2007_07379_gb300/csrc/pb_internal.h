@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "pbits.h"
 
@@ -84,3 +85,18 @@ constexpr uint32_t kTagInit = 1;
 constexpr uint32_t kTagMH = 2;
 
 }  // namespace pb
+
+// Compiled model (host side of pb_model).
+struct pb_model {
+  int n = 0, d = 0;
+  uint32_t beta = 0;
+  double J = 0.0;
+  uint32_t thr[4] = {0, 0, 0, 0};
+  int h = 0, M = 0, rank = 0;
+  int col_off[5] = {0, 0, 0, 0, 0};
+  std::vector<int32_t> colour;        // [d][n]
+  std::vector<pb::Desc> desc;         // colour-ordered
+  std::vector<pb::Rec> rec;           // by p = (k-1) n + q
+  std::vector<uint32_t> init;         // by p: 0xFFFFFFFF = H output, else a | b << 16
+  std::vector<pb_gate> gates;
+};

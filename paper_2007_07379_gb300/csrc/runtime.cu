@@ -36,22 +36,6 @@ int sweep_max_blocks_per_sm(int threads, size_t smem);
 
 using namespace pb;
 
-// ---------------------------------------------------------------------------
-// Compiled model (host).
-struct pb_model {
-  int n = 0, d = 0;
-  uint32_t beta = 0;
-  double J = 0.0;
-  uint32_t thr[4] = {0, 0, 0, 0};
-  int h = 0, M = 0, rank = 0;
-  int col_off[5] = {0, 0, 0, 0, 0};
-  std::vector<int32_t> colour;  // [d][n]
-  std::vector<Desc> desc;       // colour-ordered
-  std::vector<Rec> rec;         // by p = (k-1) n + q
-  std::vector<uint32_t> init;   // by p: 0xFFFFFFFF = H output, else a | b << 16
-  std::vector<pb_gate> gates;
-};
-
 namespace {
 
 // Gate occupying (layer, qubit): kind and partner / role.

@@ -79,6 +79,8 @@ _SIGS = {
     "pb_run_free": (None, [_VP]),
     "pb_philox_fill": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _VP,
                                       ctypes.c_void_p]),
+    "pb_gibbs_run_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(pb_run_cfg), ctypes.c_uint32, _VP, _VP,
+                                            ctypes.c_void_p]),
 }
 
 
@@ -340,3 +342,16 @@ def philox_fill(ctr: np.ndarray, key: tuple[int, int]) -> np.ndarray:
            "pb_philox_fill")
     torch.cuda.synchronize()
     return out.cpu().numpy().view(np.uint32)
+
+
+def gibbs_run_noalloc(model: Model, cfg: RunCfg, n_sweeps: int, counts, totals, stream=None):
+    """One plain Gibbs run whose scratch is the library's fixed device array
+    (pb_gibbs_run_noalloc).  `counts` (2^n * 8) and `totals` (2) are the
+    caller's int64 CUDA tensors; they hold the histogram and (valid, samples)
+    once the stream reaches the end of the call."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ca, keep = _cfg_array([cfg])
+    _check(load().pb_gibbs_run_noalloc(model.handle, ca, n_sweeps, ctypes.c_void_p(counts.data_ptr()),
+                                       ctypes.c_void_p(totals.data_ptr()),
+                                       ctypes.c_void_p(st.cuda_stream)), "pb_gibbs_run_noalloc")

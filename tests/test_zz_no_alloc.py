@@ -1,0 +1,56 @@
+"""The no-allocation run (pb_gibbs_run_noalloc), called through the C ABI.
+
+It serves callers that cannot allocate device memory at the call site, so
+its scratch is the library's fixed device array.  Two calls in a row must
+each reproduce the histogram and totals of the regular run (pb_run_create +
+pb_run_sweeps) bit for bit: the counts are integers, so the tolerance the
+other parity tests use for integers, exact equality, applies.  The file is
+named to run last, after every other test, and also passes alone.
+"""
+import numpy as np
+import pytest
+
+from paper_2007_07379_gb300 import build, pbits
+from paper_2007_07379_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    pbits.load()
+
+
+def test_noalloc_matches_regular_run_twice():
+    import torch
+    n, d, chains, sweeps = 7, 11, 200, 30
+    g = W.random_circuit(n, d, seed=77)
+    m = pbits.Model(n, d, g, 3.0)
+    cfg = pbits.RunCfg(seed=0x5EED + 9, chains=chains)
+    r = pbits.Run([m], [cfg])
+    r.sweeps(sweeps)
+    want_cnt, want_valid, want_samples = r.histogram()
+    for call in range(2):
+        counts = torch.full(((1 << n) * 8,), -1, dtype=torch.int64, device="cuda")
+        totals = torch.full((2,), -1, dtype=torch.int64, device="cuda")
+        pbits.gibbs_run_noalloc(m, cfg, sweeps, counts, totals)
+        torch.cuda.synchronize()
+        got = counts.cpu().numpy().view(np.uint64).reshape(-1, 8)
+        tot = totals.cpu().numpy()
+        assert np.array_equal(got, want_cnt), f"call {call}: histogram differs"
+        assert int(tot[0]) == want_valid and int(tot[1]) == want_samples, f"call {call}"
+
+
+def test_noalloc_rejects_oversize():
+    import torch
+    g = W.random_circuit(12, 20, seed=1)
+    m = pbits.Model(12, 20, g, 3.0)
+    counts = torch.zeros(4096 * 8, dtype=torch.int64, device="cuda")
+    totals = torch.zeros(2, dtype=torch.int64, device="cuda")
+    with pytest.raises(pbits.PbError) as e:
+        pbits.gibbs_run_noalloc(m, pbits.RunCfg(seed=1, chains=1 << 20), 1, counts, totals)
+    assert e.value.code == pbits.PB_ERANGE
