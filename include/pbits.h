@@ -223,6 +223,18 @@ PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* cfg, uint32
                                 unsigned long long* d_counts, unsigned long long* d_totals,
                                 uintptr_t stream);
 
+/* ---- BF16 tensor-core GEMM (tcgen05), used by the learned proposal ----------
+ * D[M x N] = epilogue(alpha * A[M x K] * B[N x K]^T); A, B bf16 row-major
+ * with K contiguous (leading dimensions lda, ldb in elements, multiples of 8,
+ * 16-byte aligned rows), fp32 accumulation.  flags: 1 ReLU, 2 store bf16
+ * (else fp32), 4 accumulate into fp32 D, 8 multiply by [mask(row,col) > 0]
+ * (mask bf16, leading dimension ldm).  dbias (fp32, N) may be NULL.  All
+ * pointers are device pointers; asynchronous on `stream`.  Errors: PB_EINVAL
+ * (shapes, alignment), PB_ECUDA. */
+PB_API int pb_gemm_bf16(const void* dA, int lda, const void* dB, int ldb, void* dD, int ldd,
+                        const float* dbias, const void* dmask, int ldm, int M, int N, int K,
+                        int flags, float alpha, uintptr_t stream);
+
 PB_API const char* pb_strerror(int status);
 PB_API int pb_version(void);
 

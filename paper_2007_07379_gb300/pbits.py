@@ -81,6 +81,9 @@ _SIGS = {
                                       ctypes.c_void_p]),
     "pb_gibbs_run_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(pb_run_cfg), ctypes.c_uint32, _VP, _VP,
                                             ctypes.c_void_p]),
+    "pb_gemm_bf16": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_float, ctypes.c_void_p]),
 }
 
 
@@ -355,3 +358,21 @@ def gibbs_run_noalloc(model: Model, cfg: RunCfg, n_sweeps: int, counts, totals, 
     _check(load().pb_gibbs_run_noalloc(model.handle, ca, n_sweeps, ctypes.c_void_p(counts.data_ptr()),
                                        ctypes.c_void_p(totals.data_ptr()),
                                        ctypes.c_void_p(st.cuda_stream)), "pb_gibbs_run_noalloc")
+
+
+EPI_RELU, EPI_OUT_BF16, EPI_ACCUM, EPI_MASK = 1, 2, 4, 8
+
+
+def gemm_bf16(A, B, D, bias=None, mask=None, flags: int = 0, alpha: float = 1.0, stream=None):
+    """D = epilogue(alpha * A @ B^T) on the tensor cores (pb_gemm_bf16).
+    A [M, K], B [N, K] bf16 CUDA tensors (row-major); D [M, N] fp32 or bf16."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    M, K = A.shape
+    N = B.shape[0]
+    _check(load().pb_gemm_bf16(ctypes.c_void_p(A.data_ptr()), A.stride(0), ctypes.c_void_p(B.data_ptr()),
+                               B.stride(0), ctypes.c_void_p(D.data_ptr()), D.stride(0),
+                               ctypes.c_void_p(bias.data_ptr()) if bias is not None else None,
+                               ctypes.c_void_p(mask.data_ptr()) if mask is not None else None,
+                               mask.stride(0) if mask is not None else 0, M, N, K, flags, alpha,
+                               ctypes.c_void_p(st.cuda_stream)), "pb_gemm_bf16")
