@@ -223,6 +223,38 @@ PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* cfg, uint32
                                 unsigned long long* d_counts, unsigned long long* d_totals,
                                 uintptr_t stream);
 
+/* ---- learned proposal network (the paper trains nothing; this is the
+ * proposal q(s_j | s_{j-1}, j) of the Metropolis-Hastings suffix move) -----
+ * q(s_j | s_{j-1}, j) = prod_q sigma(l_q)^{s_j[q]} sigma(-l_q)^{1-s_j[q]},
+ * l = W3 relu(W2 relu(W1 x + b1) + b2) + b3, x = [2 s_{j-1} - 1 (n),
+ * onehot(j-1) (d), zeros] (k_in = n + d rounded up to 16).  BF16 tensor-core
+ * GEMMs with fp32 accumulation, fp32 master weights, Adam (0.9, 0.999, 1e-8).
+ * The caller owns the device workspace (pb_mlp_workspace_bytes); hidden in
+ * [16, 256] (multiple of 16), batch a multiple of 128 (the largest number of
+ * rows one call processes).  Calls are asynchronous on the creation stream
+ * unless stated. */
+PB_API int pb_mlp_workspace_bytes(int n, int d, int hidden, int batch, size_t* bytes);
+/* Weights uniform(+-1/sqrt(fan_in)) from SplitMix64(seed), biases 0. */
+PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, void* d_workspace,
+                         size_t workspace_bytes, uintptr_t stream, pb_mlp** out);
+/* dims[6] = n, d, hidden, k_in, batch, number of fp32 parameters. */
+PB_API int pb_mlp_info(const pb_mlp* mlp, int* dims);
+/* Flat fp32 parameters W1 [h x k_in], b1, W2 [h x h], b2, W3 [npad x h]
+ * (npad = n rounded up to 16; rows >= n are zero), b3 [npad].  get != 0
+ * reads them to host, get == 0 loads them.  Synchronous. */
+PB_API int pb_mlp_params(pb_mlp* mlp, float* host, int get);
+/* Gradients from the last pb_mlp_backward, same flat layout.  Synchronous. */
+PB_API int pb_mlp_grads(pb_mlp* mlp, float* host);
+/* d_x: device bf16 [rows x k_in]; d_logits: device fp32 [rows x n]. */
+PB_API int pb_mlp_forward(pb_mlp* mlp, const void* d_x, int rows, float* d_logits);
+/* Gradients of the mean binary cross-entropy against d_target (device fp32
+ * 0/1, [rows x n]); rows a multiple of 8; d_loss (device fp32) may be NULL. */
+PB_API int pb_mlp_backward(pb_mlp* mlp, const void* d_x, const float* d_target, int rows,
+                           float* d_loss);
+/* One Adam step with the gradients of the last pb_mlp_backward. */
+PB_API int pb_mlp_adam(pb_mlp* mlp, float lr);
+PB_API void pb_mlp_free(pb_mlp* mlp);
+
 /* ---- BF16 tensor-core GEMM (tcgen05), used by the learned proposal ----------
  * D[M x N] = epilogue(alpha * A[M x K] * B[N x K]^T); A, B bf16 row-major
  * with K contiguous (leading dimensions lda, ldb in elements, multiples of 8,

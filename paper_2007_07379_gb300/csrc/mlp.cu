@@ -13,6 +13,10 @@
 #include "pb_internal.h"
 #include "tc_gemm.cuh"
 
+#include <cmath>
+#include <new>
+#include <vector>
+
 namespace pb {
 
 enum : int {
@@ -184,3 +188,425 @@ extern "C" PB_API int pb_gemm_bf16(const void* dA, int lda, const void* dB, int 
   return launch_gemm_bf16(g, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? PB_OK
                                                                                    : PB_ECUDA;
 }
+
+// ===========================================================================
+// The proposal network q(s_j | s_{j-1}, j): K_in -> H -> H -> n, ReLU, BF16
+// tensor-core GEMMs with fp32 accumulation, fp32 master weights and Adam.
+// ===========================================================================
+namespace pb {
+
+// Parameter block (fp32, flat): W1 [H x kin], b1 [H], W2 [H x H], b2 [H],
+// W3 [npad x H] (rows >= n stay zero), b3 [npad].
+struct MlpOffsets {
+  size_t W1, b1, W2, b2, W3, b3, total;
+};
+inline MlpOffsets mlp_offsets(int kin, int H, int npad) {
+  MlpOffsets o;
+  size_t p = 0;
+  o.W1 = p; p += (size_t)H * kin;
+  o.b1 = p; p += H;
+  o.W2 = p; p += (size_t)H * H;
+  o.b2 = p; p += H;
+  o.W3 = p; p += (size_t)npad * H;
+  o.b3 = p; p += npad;
+  o.total = p;
+  return o;
+}
+
+__global__ void transpose_bf16_kernel(const __nv_bfloat16* __restrict__ src, int R, int C,
+                                      __nv_bfloat16* __restrict__ dst) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < R && c < C) tile[i][threadIdx.x] = src[(size_t)r * C + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < R && c < C) dst[(size_t)c * R + r] = tile[threadIdx.x][i];
+  }
+}
+
+cudaError_t transpose_bf16(const __nv_bfloat16* src, int R, int C, __nv_bfloat16* dst,
+                           cudaStream_t st) {
+  dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+  transpose_bf16_kernel<<<grid, block, 0, st>>>(src, R, C, dst);
+  return cudaGetLastError();
+}
+
+// fp32 [R x C] -> bf16 [R x C] and, when dst_t is given, bf16 [C x R].
+__global__ void to_bf16_kernel(const float* __restrict__ src, int R, int C,
+                               __nv_bfloat16* __restrict__ dst, __nv_bfloat16* __restrict__ dst_t) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)R * C) return;
+  const __nv_bfloat16 v = __float2bfloat16(src[i]);
+  dst[i] = v;
+  if (dst_t) {
+    const size_t r = i / C, c = i % C;
+    dst_t[c * R + r] = v;
+  }
+}
+
+// dY = (sigmoid(l) - t) / B for the first n columns (0 beyond), bf16, both
+// layouts; db3 += column sums (fp32); loss += BCE / B.
+__global__ void bce_grad_kernel(const float* __restrict__ logits, const float* __restrict__ target,
+                                int B, int n, int npad, __nv_bfloat16* __restrict__ dY,
+                                __nv_bfloat16* __restrict__ dYt, float* __restrict__ db3,
+                                float* __restrict__ loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * npad) return;
+  const int r = i / npad, c = i % npad;
+  float g = 0.f, l_term = 0.f;
+  if (c < n) {
+    const float l = logits[(size_t)r * npad + c];
+    const float t = target[(size_t)r * n + c];
+    const float s = 1.f / (1.f + __expf(-l));
+    g = (s - t) / (float)B;
+    // -[t log s(l) + (1-t) log s(-l)] = softplus(l) - t l, computed stably
+    const float sp = fmaxf(l, 0.f) + log1pf(__expf(-fabsf(l)));
+    l_term = (sp - t * l) / (float)B;
+    atomicAdd(&db3[c], g);
+  }
+  const __nv_bfloat16 gb = __float2bfloat16(g);
+  dY[(size_t)r * npad + c] = gb;
+  dYt[(size_t)c * B + r] = gb;
+  if (loss && l_term != 0.f) atomicAdd(loss, l_term);
+}
+
+// out[j] = sum_b M[j][b] (bf16 rows, fp32 sums), one warp per row.
+__global__ void rowsum_bf16_kernel(const __nv_bfloat16* __restrict__ Mt, int R, int C,
+                                   float* __restrict__ out) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= R) return;
+  float s = 0.f;
+  for (int c = lane; c < C; c += 32) s += __bfloat162float(Mt[(size_t)row * C + c]);
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) out[row] = s;
+}
+
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, size_t count, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace pb
+
+struct pb_mlp {
+  int n = 0, d = 0, H = 0, kin = 0, npad = 0, batch = 0;
+  cudaStream_t st = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  pb::MlpOffsets off{};
+  float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+  __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2t = nullptr, *W3t = nullptr;
+  __nv_bfloat16 *X = nullptr, *Xt = nullptr, *H1 = nullptr, *H1t = nullptr, *H2 = nullptr,
+                *H2t = nullptr, *dY = nullptr, *dYt = nullptr, *dZ2 = nullptr, *dZ2t = nullptr,
+                *dZ1 = nullptr, *dZ1t = nullptr;
+  float *logits = nullptr, *target = nullptr, *loss = nullptr;
+  int step = 0;
+};
+
+namespace {
+
+struct MlpLayout {
+  size_t w, m, v, g, W1, W2, W3, W2t, W3t, X, Xt, H1, H1t, H2, H2t, dY, dYt, dZ2, dZ2t, dZ1, dZ1t,
+      logits, target, loss, total;
+};
+
+MlpLayout mlp_layout(int kin, int H, int npad, int B) {
+  const pb::MlpOffsets o = pb::mlp_offsets(kin, H, npad);
+  MlpLayout L{};
+  size_t p = 0;
+  auto take = [&](size_t bytes) {
+    p = (p + 255) & ~(size_t)255;
+    size_t at = p;
+    p += bytes;
+    return at;
+  };
+  L.w = take(o.total * 4);
+  L.m = take(o.total * 4);
+  L.v = take(o.total * 4);
+  L.g = take(o.total * 4);
+  L.W1 = take((size_t)H * kin * 2);
+  L.W2 = take((size_t)H * H * 2);
+  L.W3 = take((size_t)npad * H * 2);
+  L.W2t = take((size_t)H * H * 2);
+  L.W3t = take((size_t)H * npad * 2);
+  L.X = take((size_t)B * kin * 2);
+  L.Xt = take((size_t)B * kin * 2);
+  L.H1 = take((size_t)B * H * 2);
+  L.H1t = take((size_t)B * H * 2);
+  L.H2 = take((size_t)B * H * 2);
+  L.H2t = take((size_t)B * H * 2);
+  L.dY = take((size_t)B * npad * 2);
+  L.dYt = take((size_t)B * npad * 2);
+  L.dZ2 = take((size_t)B * H * 2);
+  L.dZ2t = take((size_t)B * H * 2);
+  L.dZ1 = take((size_t)B * H * 2);
+  L.dZ1t = take((size_t)B * H * 2);
+  L.logits = take((size_t)B * npad * 4);
+  L.target = take((size_t)B * npad * 4);
+  L.loss = take(256);
+  L.total = (p + 255) & ~(size_t)255;
+  return L;
+}
+
+int mlp_dims(int n, int d, int hidden, int batch, int* kin, int* npad) {
+  if (n < 1 || n > 32 || d < 1 || d > 64) return PB_ERANGE;
+  if (hidden < 16 || hidden > 256 || hidden % 16) return PB_ERANGE;
+  if (batch < 128 || batch % 128) return PB_ERANGE;
+  *kin = ((n + d + 15) / 16) * 16;
+  *npad = ((n + 15) / 16) * 16;
+  return PB_OK;
+}
+
+// GEMM helper: D = epi(A[M x K] B[N x K]^T)
+cudaError_t mm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, void* D, int ldd,
+               int M, int N, int K, int flags, const float* bias, const __nv_bfloat16* mask,
+               int ldm, cudaStream_t st) {
+  pb::GemmArgs g{};
+  g.A = A;
+  g.B = B;
+  g.D = D;
+  g.bias = bias;
+  g.mask = mask;
+  g.lda = lda;
+  g.ldb = ldb;
+  g.ldd = ldd;
+  g.ldm = ldm;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.flags = flags;
+  g.alpha = 1.f;
+  g.status = nullptr;
+  return pb::launch_gemm_bf16(g, st);
+}
+
+// bf16 copies of the fp32 master weights (W2t, W3t transposed for the backward).
+cudaError_t refresh_bf16(pb_mlp* p) {
+  const int T = 256;
+  const float* w = p->w;
+  size_t c = (size_t)p->H * p->kin;
+  pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off.W1, p->H, p->kin, p->W1, nullptr);
+  c = (size_t)p->H * p->H;
+  pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off.W2, p->H, p->H, p->W2, p->W2t);
+  c = (size_t)p->npad * p->H;
+  pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off.W3, p->npad, p->H, p->W3, p->W3t);
+  return cudaGetLastError();
+}
+
+// Forward of `rows` inputs already in p->X: H1, H2 (bf16), logits (fp32).
+cudaError_t mlp_fwd(pb_mlp* p, int rows) {
+  cudaError_t e;
+  const int flags = pb::kEpiRelu | pb::kEpiOutBf16;
+  if ((e = mm(p->X, p->kin, p->W1, p->kin, p->H1, p->H, rows, p->H, p->kin, flags,
+              p->w + p->off.b1, nullptr, 0, p->st)) != cudaSuccess)
+    return e;
+  if ((e = mm(p->H1, p->H, p->W2, p->H, p->H2, p->H, rows, p->H, p->H, flags, p->w + p->off.b2,
+              nullptr, 0, p->st)) != cudaSuccess)
+    return e;
+  return mm(p->H2, p->H, p->W3, p->H, p->logits, p->npad, rows, p->npad, p->H, 0,
+            p->w + p->off.b3, nullptr, 0, p->st);
+}
+
+// Backward of the mean BCE over `rows` (targets in p->target): gradients
+// into p->g, loss into p->loss[0].
+cudaError_t mlp_bwd(pb_mlp* p, int rows) {
+  cudaError_t e;
+  const int B = rows, H = p->H, T = 256;
+  cudaMemsetAsync(p->g, 0, p->off.total * 4, p->st);
+  cudaMemsetAsync(p->loss, 0, 4, p->st);
+  pb::bce_grad_kernel<<<(B * p->npad + T - 1) / T, T, 0, p->st>>>(
+      p->logits, p->target, B, p->n, p->npad, p->dY, p->dYt, p->g + p->off.b3, p->loss);
+  if ((e = pb::transpose_bf16(p->H2, B, H, p->H2t, p->st)) != cudaSuccess) return e;
+  if ((e = pb::transpose_bf16(p->H1, B, H, p->H1t, p->st)) != cudaSuccess) return e;
+  if ((e = pb::transpose_bf16(p->X, B, p->kin, p->Xt, p->st)) != cudaSuccess) return e;
+  // gW3 = dY^T H2
+  if ((e = mm(p->dYt, B, p->H2t, B, p->g + p->off.W3, H, p->npad, H, B, 0, nullptr, nullptr, 0,
+              p->st)) != cudaSuccess)
+    return e;
+  // dZ2 = (dY W3) * [H2 > 0]
+  if ((e = mm(p->dY, p->npad, p->W3t, p->npad, p->dZ2, H, B, H, p->npad,
+              pb::kEpiMask | pb::kEpiOutBf16, nullptr, p->H2, H, p->st)) != cudaSuccess)
+    return e;
+  if ((e = pb::transpose_bf16(p->dZ2, B, H, p->dZ2t, p->st)) != cudaSuccess) return e;
+  // gW2 = dZ2^T H1, gb2 = column sums of dZ2
+  if ((e = mm(p->dZ2t, B, p->H1t, B, p->g + p->off.W2, H, H, H, B, 0, nullptr, nullptr, 0,
+              p->st)) != cudaSuccess)
+    return e;
+  pb::rowsum_bf16_kernel<<<(H + 7) / 8, 256, 0, p->st>>>(p->dZ2t, H, B, p->g + p->off.b2);
+  // dZ1 = (dZ2 W2) * [H1 > 0]
+  if ((e = mm(p->dZ2, H, p->W2t, H, p->dZ1, H, B, H, H, pb::kEpiMask | pb::kEpiOutBf16, nullptr,
+              p->H1, H, p->st)) != cudaSuccess)
+    return e;
+  if ((e = pb::transpose_bf16(p->dZ1, B, H, p->dZ1t, p->st)) != cudaSuccess) return e;
+  // gW1 = dZ1^T X, gb1 = column sums of dZ1
+  if ((e = mm(p->dZ1t, B, p->Xt, B, p->g + p->off.W1, p->kin, H, p->kin, B, 0, nullptr, nullptr,
+              0, p->st)) != cudaSuccess)
+    return e;
+  pb::rowsum_bf16_kernel<<<(H + 7) / 8, 256, 0, p->st>>>(p->dZ1t, H, B, p->g + p->off.b1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+PB_API int pb_mlp_workspace_bytes(int n, int d, int hidden, int batch, size_t* bytes) {
+  if (!bytes) return PB_EINVAL;
+  int kin, npad;
+  int rc = mlp_dims(n, d, hidden, batch, &kin, &npad);
+  if (rc != PB_OK) return rc;
+  *bytes = mlp_layout(kin, hidden, npad, batch).total;
+  return PB_OK;
+}
+
+PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, void* d_ws,
+                         size_t ws_bytes, uintptr_t stream, pb_mlp** out) {
+  if (!out) return PB_EINVAL;
+  *out = nullptr;
+  int kin, npad;
+  int rc = mlp_dims(n, d, hidden, batch, &kin, &npad);
+  if (rc != PB_OK) return rc;
+  if (!d_ws || ((uintptr_t)d_ws & 255)) return PB_EINVAL;
+  const MlpLayout L = mlp_layout(kin, hidden, npad, batch);
+  if (ws_bytes < L.total) return PB_ERANGE;
+  pb_mlp* p = new (std::nothrow) pb_mlp;
+  if (!p) return PB_ENOMEM;
+  p->n = n; p->d = d; p->H = hidden; p->kin = kin; p->npad = npad; p->batch = batch;
+  p->st = reinterpret_cast<cudaStream_t>(stream);
+  p->ws = static_cast<char*>(d_ws);
+  p->ws_bytes = ws_bytes;
+  p->off = pb::mlp_offsets(kin, hidden, npad);
+  char* b = p->ws;
+  p->w = (float*)(b + L.w); p->m = (float*)(b + L.m); p->v = (float*)(b + L.v); p->g = (float*)(b + L.g);
+  p->W1 = (__nv_bfloat16*)(b + L.W1); p->W2 = (__nv_bfloat16*)(b + L.W2); p->W3 = (__nv_bfloat16*)(b + L.W3);
+  p->W2t = (__nv_bfloat16*)(b + L.W2t); p->W3t = (__nv_bfloat16*)(b + L.W3t);
+  p->X = (__nv_bfloat16*)(b + L.X); p->Xt = (__nv_bfloat16*)(b + L.Xt);
+  p->H1 = (__nv_bfloat16*)(b + L.H1); p->H1t = (__nv_bfloat16*)(b + L.H1t);
+  p->H2 = (__nv_bfloat16*)(b + L.H2); p->H2t = (__nv_bfloat16*)(b + L.H2t);
+  p->dY = (__nv_bfloat16*)(b + L.dY); p->dYt = (__nv_bfloat16*)(b + L.dYt);
+  p->dZ2 = (__nv_bfloat16*)(b + L.dZ2); p->dZ2t = (__nv_bfloat16*)(b + L.dZ2t);
+  p->dZ1 = (__nv_bfloat16*)(b + L.dZ1); p->dZ1t = (__nv_bfloat16*)(b + L.dZ1t);
+  p->logits = (float*)(b + L.logits); p->target = (float*)(b + L.target); p->loss = (float*)(b + L.loss);
+  // Initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed), biases 0.
+  std::vector<float> w(p->off.total, 0.f);
+  uint64_t s = seed;
+  auto next = [&]() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto fill = [&](size_t o, int rows, int cols, int fan_in, int live_rows, int live_cols) {
+    const float a = 1.f / std::sqrt((float)fan_in);
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < cols; ++c) {
+        const float u = (float)((next() >> 11) * (1.0 / 9007199254740992.0));
+        w[o + (size_t)r * cols + c] = (r < live_rows && c < live_cols) ? (2.f * u - 1.f) * a : 0.f;
+      }
+  };
+  fill(p->off.W1, hidden, kin, n + d, hidden, n + d);
+  fill(p->off.W2, hidden, hidden, hidden, hidden, hidden);
+  fill(p->off.W3, npad, hidden, hidden, n, hidden);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(p->ws, 0, L.total, p->st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(p->w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, p->st)) != cudaSuccess ||
+      (e = refresh_bf16(p)) != cudaSuccess || (e = cudaStreamSynchronize(p->st)) != cudaSuccess) {
+    delete p;
+    return PB_ECUDA;
+  }
+  *out = p;
+  return PB_OK;
+}
+
+PB_API int pb_mlp_info(const pb_mlp* p, int* dims /* n, d, hidden, k_in, batch, n_params */) {
+  if (!p || !dims) return PB_EINVAL;
+  dims[0] = p->n; dims[1] = p->d; dims[2] = p->H; dims[3] = p->kin; dims[4] = p->batch;
+  dims[5] = (int)p->off.total;
+  return PB_OK;
+}
+
+// get != 0: copy the fp32 master parameters to host (flat W1, b1, W2, b2,
+// W3 [npad x H], b3 [npad]); get == 0: load them from host and refresh the
+// bf16 copies.  Synchronous.
+PB_API int pb_mlp_params(pb_mlp* p, float* host, int get) {
+  if (!p || !host) return PB_EINVAL;
+  if (cudaStreamSynchronize(p->st) != cudaSuccess) return PB_ECUDA;
+  if (get) return cudaMemcpy(host, p->w, p->off.total * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? PB_OK : PB_ECUDA;
+  if (cudaMemcpy(p->w, host, p->off.total * 4, cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;
+  if (refresh_bf16(p) != cudaSuccess) return PB_ECUDA;
+  return cudaStreamSynchronize(p->st) == cudaSuccess ? PB_OK : PB_ECUDA;
+}
+
+PB_API int pb_mlp_grads(pb_mlp* p, float* host) {
+  if (!p || !host) return PB_EINVAL;
+  if (cudaStreamSynchronize(p->st) != cudaSuccess) return PB_ECUDA;
+  return cudaMemcpy(host, p->g, p->off.total * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? PB_OK : PB_ECUDA;
+}
+
+// Forward of rows inputs (device bf16 [rows x k_in]) into device fp32
+// logits [rows x n] (rows <= batch).
+PB_API int pb_mlp_forward(pb_mlp* p, const void* d_x, int rows, float* d_logits) {
+  if (!p || !d_x || !d_logits || rows <= 0 || rows > p->batch) return PB_EINVAL;
+  if (cudaMemcpyAsync(p->X, d_x, (size_t)rows * p->kin * 2, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess)
+    return PB_ECUDA;
+  if (mlp_fwd(p, rows) != cudaSuccess) return PB_ECUDA;
+  if (cudaMemcpy2DAsync(d_logits, (size_t)p->n * 4, p->logits, (size_t)p->npad * 4, (size_t)p->n * 4,
+                        rows, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess)
+    return PB_ECUDA;
+  return PB_OK;
+}
+
+// Gradients of the mean BCE of rows (inputs bf16 [rows x k_in], targets fp32
+// 0/1 [rows x n]) into the internal gradient block (pb_mlp_grads reads it);
+// d_loss (device fp32, may be NULL) receives the loss.  rows: multiple of
+// 8, <= batch.
+PB_API int pb_mlp_backward(pb_mlp* p, const void* d_x, const float* d_target, int rows, float* d_loss) {
+  if (!p || !d_x || !d_target || rows <= 0 || rows > p->batch || rows % 8) return PB_EINVAL;
+  if (cudaMemcpyAsync(p->X, d_x, (size_t)rows * p->kin * 2, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess ||
+      cudaMemcpy2DAsync(p->target, (size_t)p->n * 4, d_target, (size_t)p->n * 4, (size_t)p->n * 4, rows,
+                        cudaMemcpyDeviceToDevice, p->st) != cudaSuccess)
+    return PB_ECUDA;
+  if (mlp_fwd(p, rows) != cudaSuccess || mlp_bwd(p, rows) != cudaSuccess) return PB_ECUDA;
+  if (d_loss && cudaMemcpyAsync(d_loss, p->loss, 4, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess)
+    return PB_ECUDA;
+  return PB_OK;
+}
+
+// One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the current gradients.
+PB_API int pb_mlp_adam(pb_mlp* p, float lr) {
+  if (!p || !(lr > 0.f)) return PB_EINVAL;
+  p->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)p->step), c2 = 1.f - std::pow(b2, (float)p->step);
+  const size_t c = p->off.total;
+  pb::adam_kernel<<<(unsigned)((c + 255) / 256), 256, 0, p->st>>>(p->w, p->g, p->m, p->v, c, lr, b1,
+                                                                  b2, 1e-8f, c1, c2);
+  // keep the padded rows of W3 / b3 at zero
+  if (p->npad > p->n) {
+    cudaMemsetAsync(p->w + p->off.W3 + (size_t)p->n * p->H, 0, (size_t)(p->npad - p->n) * p->H * 4, p->st);
+    cudaMemsetAsync(p->w + p->off.b3 + p->n, 0, (size_t)(p->npad - p->n) * 4, p->st);
+  }
+  return refresh_bf16(p) == cudaSuccess ? PB_OK : PB_ECUDA;
+}
+
+PB_API void pb_mlp_free(pb_mlp* p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->st);
+  delete p;
+}
+
+}  // extern "C"

@@ -81,6 +81,17 @@ _SIGS = {
                                       ctypes.c_void_p]),
     "pb_gibbs_run_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(pb_run_cfg), ctypes.c_uint32, _VP, _VP,
                                             ctypes.c_void_p]),
+    "pb_mlp_workspace_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_size_t)]),
+    "pb_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                     _VP, ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(_VP)]),
+    "pb_mlp_info": (ctypes.c_int, [_VP, _VP]),
+    "pb_mlp_params": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "pb_mlp_grads": (ctypes.c_int, [_VP, _VP]),
+    "pb_mlp_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
+    "pb_mlp_backward": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "pb_mlp_adam": (ctypes.c_int, [_VP, ctypes.c_float]),
+    "pb_mlp_free": (None, [_VP]),
     "pb_gemm_bf16": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_float, ctypes.c_void_p]),
@@ -376,3 +387,85 @@ def gemm_bf16(A, B, D, bias=None, mask=None, flags: int = 0, alpha: float = 1.0,
                                ctypes.c_void_p(mask.data_ptr()) if mask is not None else None,
                                mask.stride(0) if mask is not None else 0, M, N, K, flags, alpha,
                                ctypes.c_void_p(st.cuda_stream)), "pb_gemm_bf16")
+
+
+class Mlp:
+    """The proposal network (pb_mlp_*); workspace is a torch CUDA tensor."""
+
+    def __init__(self, n: int, d: int, hidden: int = 256, batch: int = 4096, seed: int = 1, stream=None):
+        import torch
+        lib = load()
+        nb = ctypes.c_size_t(0)
+        _check(lib.pb_mlp_workspace_bytes(n, d, hidden, batch, ctypes.byref(nb)), "pb_mlp_workspace_bytes")
+        self.workspace = torch.zeros(nb.value, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib.pb_mlp_create(n, d, hidden, batch, ctypes.c_uint64(seed), ctypes.c_void_p(self.workspace.data_ptr()),
+                                 nb.value, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "pb_mlp_create")
+        self._h = h
+        dims = np.zeros(6, dtype=np.int32)
+        _check(lib.pb_mlp_info(h, _ptr(dims)), "pb_mlp_info")
+        self.n, self.d, self.hidden, self.k_in, self.batch, self.n_params = [int(x) for x in dims]
+        self.npad = ((n + 15) // 16) * 16
+
+    @property
+    def handle(self):
+        return self._h
+
+    def params(self) -> dict:
+        flat = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().pb_mlp_params(self._h, _ptr(flat), 1), "pb_mlp_params")
+        return self._unflat(flat)
+
+    def set_params(self, p: dict):
+        _check(load().pb_mlp_params(self._h, _ptr(self._flat(p)), 0), "pb_mlp_params")
+
+    def grads(self) -> dict:
+        flat = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().pb_mlp_grads(self._h, _ptr(flat)), "pb_mlp_grads")
+        return self._unflat(flat)
+
+    def _shapes(self):
+        H, k, npd = self.hidden, self.k_in, self.npad
+        return [("W1", (H, k)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (npd, H)), ("b3", (npd,))]
+
+    def _unflat(self, flat):
+        out, o = {}, 0
+        for name, shp in self._shapes():
+            size = int(np.prod(shp))
+            out[name] = flat[o:o + size].reshape(shp).astype(np.float64)
+            o += size
+        return out
+
+    def _flat(self, p):
+        return np.concatenate([np.asarray(p[name], dtype=np.float32).reshape(-1) for name, _ in self._shapes()])
+
+    def forward(self, x_bf16):
+        import torch
+        rows = x_bf16.shape[0]
+        out = torch.empty(rows, self.n, dtype=torch.float32, device="cuda")
+        _check(load().pb_mlp_forward(self._h, ctypes.c_void_p(x_bf16.data_ptr()), rows,
+                                     ctypes.c_void_p(out.data_ptr())), "pb_mlp_forward")
+        return out
+
+    def backward(self, x_bf16, target):
+        import torch
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        _check(load().pb_mlp_backward(self._h, ctypes.c_void_p(x_bf16.data_ptr()),
+                                      ctypes.c_void_p(target.data_ptr()), x_bf16.shape[0],
+                                      ctypes.c_void_p(loss.data_ptr())), "pb_mlp_backward")
+        return loss
+
+    def adam(self, lr: float):
+        _check(load().pb_mlp_adam(self._h, ctypes.c_float(lr)), "pb_mlp_adam")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pb_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
