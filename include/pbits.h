@@ -255,6 +255,34 @@ PB_API int pb_mlp_backward(pb_mlp* mlp, const void* d_x, const float* d_target, 
 PB_API int pb_mlp_adam(pb_mlp* mlp, float lr);
 PB_API void pb_mlp_free(pb_mlp* mlp);
 
+/* ---- learned proposal: Metropolis-Hastings suffix move (Fig. 2 Steps 1-2,
+ * "Metropolis-Hastings" acceptance on |e^{-E}|) -------------------------------
+ * One move per call per move index: k* in 1..d is drawn from the seed and
+ * the move index; every chain of model `model` proposes s'_{k*}..s'_d layer
+ * by layer from the network and accepts with
+ *   min(1, e^{-J (v(s') - v(s))} q(s_{k*..d} | s_{k*-1}) / q(s'_{k*..d} | s_{k*-1})),
+ * v = violated links of layers k*..d (Re E = J v).  The move keeps the
+ * sampled distribution (the J-penalty Boltzmann law of the Gibbs sweeps), so
+ * it is interleaved with pb_run_sweeps, whose records count the samples.
+ * Scratch: a caller device workspace of pb_mh_workspace_bytes (256-byte
+ * aligned).  Runs on the run's stream; returns when the moves are done,
+ * with the number of accepted proposals in *accepted (may be NULL). */
+PB_API int pb_mh_workspace_bytes(const pb_run* run, int model, size_t* bytes);
+PB_API int pb_mh_moves(pb_run* run, int model, pb_mlp* mlp, uint32_t move0, uint32_t n_moves,
+                       void* d_workspace, size_t workspace_bytes, uint64_t* accepted);
+/* Appends the valid paths among the chains of `model` (per-chain layer
+ * words s_1..s_d, d u32 each) to d_paths at the device counter *d_count
+ * (u64, caller-initialised), up to `capacity` paths.  Workspace as for
+ * pb_mh_moves.  Synchronous. */
+PB_API int pb_run_collect_paths(pb_run* run, int model, void* d_workspace, size_t workspace_bytes,
+                                uint32_t* d_paths, uint64_t capacity, uint64_t* d_count);
+/* `steps` Adam steps of the network on batches of `rows` (input s_{j-1}, j;
+ * target s_j) drawn uniformly from the n_paths collected paths (Philox,
+ * key = seed); the loss of each step goes to d_losses[step] (device fp32,
+ * may be NULL).  Asynchronous on the network's stream. */
+PB_API int pb_mlp_train_paths(pb_mlp* mlp, const uint32_t* d_paths, uint64_t n_paths, uint32_t beta,
+                              int steps, int rows, float lr, uint64_t seed, float* d_losses);
+
 /* ---- BF16 tensor-core GEMM (tcgen05), used by the learned proposal ----------
  * D[M x N] = epilogue(alpha * A[M x K] * B[N x K]^T); A, B bf16 row-major
  * with K contiguous (leading dimensions lda, ldb in elements, multiples of 8,

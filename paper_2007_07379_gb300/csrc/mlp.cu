@@ -301,21 +301,6 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
 
 }  // namespace pb
 
-struct pb_mlp {
-  int n = 0, d = 0, H = 0, kin = 0, npad = 0, batch = 0;
-  cudaStream_t st = nullptr;
-  char* ws = nullptr;
-  size_t ws_bytes = 0;
-  pb::MlpOffsets off{};
-  float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
-  __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2t = nullptr, *W3t = nullptr;
-  __nv_bfloat16 *X = nullptr, *Xt = nullptr, *H1 = nullptr, *H1t = nullptr, *H2 = nullptr,
-                *H2t = nullptr, *dY = nullptr, *dYt = nullptr, *dZ2 = nullptr, *dZ2t = nullptr,
-                *dZ1 = nullptr, *dZ1t = nullptr;
-  float *logits = nullptr, *target = nullptr, *loss = nullptr;
-  int step = 0;
-};
-
 namespace {
 
 struct MlpLayout {
@@ -398,11 +383,11 @@ cudaError_t refresh_bf16(pb_mlp* p) {
   const int T = 256;
   const float* w = p->w;
   size_t c = (size_t)p->H * p->kin;
-  pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off.W1, p->H, p->kin, p->W1, nullptr);
+  pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off_W1, p->H, p->kin, p->W1, nullptr);
   c = (size_t)p->H * p->H;
-  pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off.W2, p->H, p->H, p->W2, p->W2t);
+  pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off_W2, p->H, p->H, p->W2, p->W2t);
   c = (size_t)p->npad * p->H;
-  pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off.W3, p->npad, p->H, p->W3, p->W3t);
+  pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off_W3, p->npad, p->H, p->W3, p->W3t);
   return cudaGetLastError();
 }
 
@@ -411,13 +396,13 @@ cudaError_t mlp_fwd(pb_mlp* p, int rows) {
   cudaError_t e;
   const int flags = pb::kEpiRelu | pb::kEpiOutBf16;
   if ((e = mm(p->X, p->kin, p->W1, p->kin, p->H1, p->H, rows, p->H, p->kin, flags,
-              p->w + p->off.b1, nullptr, 0, p->st)) != cudaSuccess)
+              p->w + p->off_b1, nullptr, 0, p->st)) != cudaSuccess)
     return e;
-  if ((e = mm(p->H1, p->H, p->W2, p->H, p->H2, p->H, rows, p->H, p->H, flags, p->w + p->off.b2,
+  if ((e = mm(p->H1, p->H, p->W2, p->H, p->H2, p->H, rows, p->H, p->H, flags, p->w + p->off_b2,
               nullptr, 0, p->st)) != cudaSuccess)
     return e;
   return mm(p->H2, p->H, p->W3, p->H, p->logits, p->npad, rows, p->npad, p->H, 0,
-            p->w + p->off.b3, nullptr, 0, p->st);
+            p->w + p->off_b3, nullptr, 0, p->st);
 }
 
 // Backward of the mean BCE over `rows` (targets in p->target): gradients
@@ -425,15 +410,15 @@ cudaError_t mlp_fwd(pb_mlp* p, int rows) {
 cudaError_t mlp_bwd(pb_mlp* p, int rows) {
   cudaError_t e;
   const int B = rows, H = p->H, T = 256;
-  cudaMemsetAsync(p->g, 0, p->off.total * 4, p->st);
+  cudaMemsetAsync(p->g, 0, p->n_params * 4, p->st);
   cudaMemsetAsync(p->loss, 0, 4, p->st);
   pb::bce_grad_kernel<<<(B * p->npad + T - 1) / T, T, 0, p->st>>>(
-      p->logits, p->target, B, p->n, p->npad, p->dY, p->dYt, p->g + p->off.b3, p->loss);
+      p->logits, p->target, B, p->n, p->npad, p->dY, p->dYt, p->g + p->off_b3, p->loss);
   if ((e = pb::transpose_bf16(p->H2, B, H, p->H2t, p->st)) != cudaSuccess) return e;
   if ((e = pb::transpose_bf16(p->H1, B, H, p->H1t, p->st)) != cudaSuccess) return e;
   if ((e = pb::transpose_bf16(p->X, B, p->kin, p->Xt, p->st)) != cudaSuccess) return e;
   // gW3 = dY^T H2
-  if ((e = mm(p->dYt, B, p->H2t, B, p->g + p->off.W3, H, p->npad, H, B, 0, nullptr, nullptr, 0,
+  if ((e = mm(p->dYt, B, p->H2t, B, p->g + p->off_W3, H, p->npad, H, B, 0, nullptr, nullptr, 0,
               p->st)) != cudaSuccess)
     return e;
   // dZ2 = (dY W3) * [H2 > 0]
@@ -442,24 +427,43 @@ cudaError_t mlp_bwd(pb_mlp* p, int rows) {
     return e;
   if ((e = pb::transpose_bf16(p->dZ2, B, H, p->dZ2t, p->st)) != cudaSuccess) return e;
   // gW2 = dZ2^T H1, gb2 = column sums of dZ2
-  if ((e = mm(p->dZ2t, B, p->H1t, B, p->g + p->off.W2, H, H, H, B, 0, nullptr, nullptr, 0,
+  if ((e = mm(p->dZ2t, B, p->H1t, B, p->g + p->off_W2, H, H, H, B, 0, nullptr, nullptr, 0,
               p->st)) != cudaSuccess)
     return e;
-  pb::rowsum_bf16_kernel<<<(H + 7) / 8, 256, 0, p->st>>>(p->dZ2t, H, B, p->g + p->off.b2);
+  pb::rowsum_bf16_kernel<<<(H + 7) / 8, 256, 0, p->st>>>(p->dZ2t, H, B, p->g + p->off_b2);
   // dZ1 = (dZ2 W2) * [H1 > 0]
   if ((e = mm(p->dZ2, H, p->W2t, H, p->dZ1, H, B, H, H, pb::kEpiMask | pb::kEpiOutBf16, nullptr,
               p->H1, H, p->st)) != cudaSuccess)
     return e;
   if ((e = pb::transpose_bf16(p->dZ1, B, H, p->dZ1t, p->st)) != cudaSuccess) return e;
   // gW1 = dZ1^T X, gb1 = column sums of dZ1
-  if ((e = mm(p->dZ1t, B, p->Xt, B, p->g + p->off.W1, p->kin, H, p->kin, B, 0, nullptr, nullptr,
+  if ((e = mm(p->dZ1t, B, p->Xt, B, p->g + p->off_W1, p->kin, H, p->kin, B, 0, nullptr, nullptr,
               0, p->st)) != cudaSuccess)
     return e;
-  pb::rowsum_bf16_kernel<<<(H + 7) / 8, 256, 0, p->st>>>(p->dZ1t, H, B, p->g + p->off.b1);
+  pb::rowsum_bf16_kernel<<<(H + 7) / 8, 256, 0, p->st>>>(p->dZ1t, H, B, p->g + p->off_b1);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+namespace pb {
+cudaError_t mlp_forward_rows(pb_mlp* p, int rows) { return mlp_fwd(p, rows); }
+cudaError_t mlp_backward_rows(pb_mlp* p, int rows) { return mlp_bwd(p, rows); }
+cudaError_t mlp_adam_step(pb_mlp* p, float lr) {
+  p->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)p->step), c2 = 1.f - std::pow(b2, (float)p->step);
+  const size_t c = p->n_params;
+  adam_kernel<<<(unsigned)((c + 255) / 256), 256, 0, p->st>>>(p->w, p->g, p->m, p->v, c, lr, b1, b2,
+                                                             1e-8f, c1, c2);
+  // keep the padded rows of W3 / b3 at zero
+  if (p->npad > p->n) {
+    cudaMemsetAsync(p->w + p->off_W3 + (size_t)p->n * p->H, 0, (size_t)(p->npad - p->n) * p->H * 4, p->st);
+    cudaMemsetAsync(p->w + p->off_b3 + p->n, 0, (size_t)(p->npad - p->n) * 4, p->st);
+  }
+  return refresh_bf16(p);
+}
+}  // namespace pb
 
 extern "C" {
 
@@ -488,7 +492,11 @@ PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, voi
   p->st = reinterpret_cast<cudaStream_t>(stream);
   p->ws = static_cast<char*>(d_ws);
   p->ws_bytes = ws_bytes;
-  p->off = pb::mlp_offsets(kin, hidden, npad);
+  {
+    const pb::MlpOffsets o = pb::mlp_offsets(kin, hidden, npad);
+    p->off_W1 = o.W1; p->off_b1 = o.b1; p->off_W2 = o.W2; p->off_b2 = o.b2;
+    p->off_W3 = o.W3; p->off_b3 = o.b3; p->n_params = o.total;
+  }
   char* b = p->ws;
   p->w = (float*)(b + L.w); p->m = (float*)(b + L.m); p->v = (float*)(b + L.v); p->g = (float*)(b + L.g);
   p->W1 = (__nv_bfloat16*)(b + L.W1); p->W2 = (__nv_bfloat16*)(b + L.W2); p->W3 = (__nv_bfloat16*)(b + L.W3);
@@ -501,7 +509,7 @@ PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, voi
   p->dZ1 = (__nv_bfloat16*)(b + L.dZ1); p->dZ1t = (__nv_bfloat16*)(b + L.dZ1t);
   p->logits = (float*)(b + L.logits); p->target = (float*)(b + L.target); p->loss = (float*)(b + L.loss);
   // Initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed), biases 0.
-  std::vector<float> w(p->off.total, 0.f);
+  std::vector<float> w(p->n_params, 0.f);
   uint64_t s = seed;
   auto next = [&]() {
     s += 0x9E3779B97F4A7C15ull;
@@ -518,9 +526,9 @@ PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, voi
         w[o + (size_t)r * cols + c] = (r < live_rows && c < live_cols) ? (2.f * u - 1.f) * a : 0.f;
       }
   };
-  fill(p->off.W1, hidden, kin, n + d, hidden, n + d);
-  fill(p->off.W2, hidden, hidden, hidden, hidden, hidden);
-  fill(p->off.W3, npad, hidden, hidden, n, hidden);
+  fill(p->off_W1, hidden, kin, n + d, hidden, n + d);
+  fill(p->off_W2, hidden, hidden, hidden, hidden, hidden);
+  fill(p->off_W3, npad, hidden, hidden, n, hidden);
   cudaError_t e;
   if ((e = cudaMemsetAsync(p->ws, 0, L.total, p->st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(p->w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, p->st)) != cudaSuccess ||
@@ -535,7 +543,7 @@ PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, voi
 PB_API int pb_mlp_info(const pb_mlp* p, int* dims /* n, d, hidden, k_in, batch, n_params */) {
   if (!p || !dims) return PB_EINVAL;
   dims[0] = p->n; dims[1] = p->d; dims[2] = p->H; dims[3] = p->kin; dims[4] = p->batch;
-  dims[5] = (int)p->off.total;
+  dims[5] = (int)p->n_params;
   return PB_OK;
 }
 
@@ -545,8 +553,8 @@ PB_API int pb_mlp_info(const pb_mlp* p, int* dims /* n, d, hidden, k_in, batch, 
 PB_API int pb_mlp_params(pb_mlp* p, float* host, int get) {
   if (!p || !host) return PB_EINVAL;
   if (cudaStreamSynchronize(p->st) != cudaSuccess) return PB_ECUDA;
-  if (get) return cudaMemcpy(host, p->w, p->off.total * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? PB_OK : PB_ECUDA;
-  if (cudaMemcpy(p->w, host, p->off.total * 4, cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;
+  if (get) return cudaMemcpy(host, p->w, p->n_params * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? PB_OK : PB_ECUDA;
+  if (cudaMemcpy(p->w, host, p->n_params * 4, cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;
   if (refresh_bf16(p) != cudaSuccess) return PB_ECUDA;
   return cudaStreamSynchronize(p->st) == cudaSuccess ? PB_OK : PB_ECUDA;
 }
@@ -554,7 +562,7 @@ PB_API int pb_mlp_params(pb_mlp* p, float* host, int get) {
 PB_API int pb_mlp_grads(pb_mlp* p, float* host) {
   if (!p || !host) return PB_EINVAL;
   if (cudaStreamSynchronize(p->st) != cudaSuccess) return PB_ECUDA;
-  return cudaMemcpy(host, p->g, p->off.total * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? PB_OK : PB_ECUDA;
+  return cudaMemcpy(host, p->g, p->n_params * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? PB_OK : PB_ECUDA;
 }
 
 // Forward of rows inputs (device bf16 [rows x k_in]) into device fp32
@@ -589,18 +597,7 @@ PB_API int pb_mlp_backward(pb_mlp* p, const void* d_x, const float* d_target, in
 // One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the current gradients.
 PB_API int pb_mlp_adam(pb_mlp* p, float lr) {
   if (!p || !(lr > 0.f)) return PB_EINVAL;
-  p->step += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - std::pow(b1, (float)p->step), c2 = 1.f - std::pow(b2, (float)p->step);
-  const size_t c = p->off.total;
-  pb::adam_kernel<<<(unsigned)((c + 255) / 256), 256, 0, p->st>>>(p->w, p->g, p->m, p->v, c, lr, b1,
-                                                                  b2, 1e-8f, c1, c2);
-  // keep the padded rows of W3 / b3 at zero
-  if (p->npad > p->n) {
-    cudaMemsetAsync(p->w + p->off.W3 + (size_t)p->n * p->H, 0, (size_t)(p->npad - p->n) * p->H * 4, p->st);
-    cudaMemsetAsync(p->w + p->off.b3 + p->n, 0, (size_t)(p->npad - p->n) * 4, p->st);
-  }
-  return refresh_bf16(p) == cudaSuccess ? PB_OK : PB_ECUDA;
+  return pb::mlp_adam_step(p, lr) == cudaSuccess ? PB_OK : PB_ECUDA;
 }
 
 PB_API void pb_mlp_free(pb_mlp* p) {

@@ -4,6 +4,9 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
 #include "pbits.h"
 
 namespace pb {
@@ -100,3 +103,38 @@ struct pb_model {
   std::vector<uint32_t> init;         // by p: 0xFFFFFFFF = H output, else a | b << 16
   std::vector<pb_gate> gates;
 };
+
+// Proposal network (host side of pb_mlp): fp32 master weights, Adam state,
+// bf16 copies for the tensor cores and the batch buffers of one call.
+struct pb_mlp {
+  int n = 0, d = 0, H = 0, kin = 0, npad = 0, batch = 0;
+  cudaStream_t st = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  size_t off_W1 = 0, off_b1 = 0, off_W2 = 0, off_b2 = 0, off_W3 = 0, off_b3 = 0, n_params = 0;
+  float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+  __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2t = nullptr, *W3t = nullptr;
+  __nv_bfloat16 *X = nullptr, *Xt = nullptr, *H1 = nullptr, *H1t = nullptr, *H2 = nullptr,
+                *H2t = nullptr, *dY = nullptr, *dYt = nullptr, *dZ2 = nullptr, *dZ2t = nullptr,
+                *dZ1 = nullptr, *dZ1t = nullptr;
+  float *logits = nullptr, *target = nullptr, *loss = nullptr;
+  int step = 0;
+};
+
+namespace pb {
+// Forward / backward of `rows` rows already staged in mlp->X (and
+// mlp->target): logits in mlp->logits [rows x npad], gradients in mlp->g.
+cudaError_t mlp_forward_rows(pb_mlp* p, int rows);
+cudaError_t mlp_backward_rows(pb_mlp* p, int rows);
+cudaError_t mlp_adam_step(pb_mlp* p, float lr);
+
+// What the learned-proposal code needs to know about one model of a run.
+struct RunView {
+  cudaStream_t st;
+  uint32_t* state;  // [group][k-1][q] chain words
+  const pb_model* model;
+  uint32_t chains, groups, group0;
+  uint64_t seed;
+};
+int run_view(const pb_run* r, int model, RunView* out);
+}  // namespace pb

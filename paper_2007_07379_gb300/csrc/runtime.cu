@@ -775,6 +775,24 @@ PB_API void pb_run_free(pb_run* r) {
   delete r;
 }
 
+}  // extern "C"
+
+namespace pb {
+int run_view(const pb_run* r, int model, RunView* out) {
+  if (!r || !out || model < 0 || model >= r->nm) return PB_EINVAL;
+  out->st = r->st;
+  out->state = r->rm[model].state;
+  out->model = r->models[model].get();
+  out->chains = r->cfgs[model].chains;
+  out->groups = r->rm[model].groups;
+  out->group0 = r->cfgs[model].group0;
+  out->seed = r->cfgs[model].seed;
+  return PB_OK;
+}
+}  // namespace pb
+
+extern "C" {
+
 PB_API int pb_philox_fill(const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t count,
                           uint32_t* d_out, uintptr_t stream) {
   if ((!d_ctr || !d_out) && count) return PB_EINVAL;

@@ -92,6 +92,13 @@ _SIGS = {
     "pb_mlp_backward": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "pb_mlp_adam": (ctypes.c_int, [_VP, ctypes.c_float]),
     "pb_mlp_free": (None, [_VP]),
+    "pb_mh_workspace_bytes": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "pb_mh_moves": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_uint32, ctypes.c_uint32, _VP,
+                                   ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]),
+    "pb_run_collect_paths": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_size_t, _VP, ctypes.c_uint64,
+                                            _VP]),
+    "pb_mlp_train_paths": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_float, ctypes.c_uint64, _VP]),
     "pb_gemm_bf16": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_float, ctypes.c_void_p]),
@@ -469,3 +476,46 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+class Learned:
+    """Learned-proposal sampler on one model of a run: path collection,
+    training of the network and Metropolis-Hastings suffix moves."""
+
+    def __init__(self, run: Run, mlp: Mlp, model: int = 0):
+        import torch
+        self.run, self.mlp, self.model = run, mlp, model
+        nb = ctypes.c_size_t(0)
+        _check(load().pb_mh_workspace_bytes(run._h, model, ctypes.byref(nb)), "pb_mh_workspace_bytes")
+        self.workspace = torch.zeros(nb.value, dtype=torch.uint8, device="cuda")
+        self.moves = 0
+        self.accepted = 0
+        self.proposed = 0
+
+    def step(self, n_moves: int = 1) -> int:
+        acc = ctypes.c_uint64(0)
+        _check(load().pb_mh_moves(self.run._h, self.model, self.mlp.handle, self.moves, n_moves,
+                                  ctypes.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
+                                  ctypes.byref(acc)), "pb_mh_moves")
+        self.moves += n_moves
+        self.accepted += acc.value
+        self.proposed += n_moves * self.run.cfgs[self.model].chains
+        return acc.value
+
+    def collect(self, paths, count):
+        """Append the valid chain paths to `paths` (int32 [cap, d] CUDA tensor);
+        `count` is an int64 [1] CUDA tensor holding the fill level."""
+        _check(load().pb_run_collect_paths(self.run._h, self.model, ctypes.c_void_p(self.workspace.data_ptr()),
+                                           self.workspace.numel(), ctypes.c_void_p(paths.data_ptr()),
+                                           paths.shape[0], ctypes.c_void_p(count.data_ptr())),
+               "pb_run_collect_paths")
+
+
+def train_on_paths(mlp: Mlp, paths, n_paths: int, beta: int, steps: int, rows: int, lr: float, seed: int):
+    """Adam steps on uniform (path, layer) batches; returns the per-step losses."""
+    import torch
+    losses = torch.zeros(steps, dtype=torch.float32, device="cuda")
+    _check(load().pb_mlp_train_paths(mlp.handle, ctypes.c_void_p(paths.data_ptr()), n_paths, beta, steps,
+                                     rows, ctypes.c_float(lr), ctypes.c_uint64(seed),
+                                     ctypes.c_void_p(losses.data_ptr())), "pb_mlp_train_paths")
+    return losses
