@@ -203,6 +203,8 @@ def main():
     ap.add_argument("--ref-sweeps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learned-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -298,6 +300,11 @@ def main():
     if not args.no_e2e:
         e2e = measure_e2e(wl, rank, groups, S, dev, stream, world)
 
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = [learned_comparison(dev, stream, seconds=args.learned_seconds, wl=w)
+                   for w in (W.learned(), W.learned_sparse())]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_oracle_rate(wl)
@@ -311,10 +318,87 @@ def main():
             "config": _config(wl, args, world), "clocks": clocks, "e2e": e2e,
             "gpu_launches": 3 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
             "samples_per_s": world * wl.chains * S * args.steps / total_s,
+            "learned_vs_plain": learned,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def learned_comparison(dev, stream, seconds: float = 8.0, train_paths: int = 1_000_000,
+                       train_steps: int = 3000, wl=None):
+    """Wall time to an amplitude error of 1 % for plain Gibbs and for Gibbs
+    with the learned suffix move, on the learned workload (n=16, d=24, 4096
+    chains).  Both run for the same wall time; the error of each is its
+    batch-means standard error (32 batches of chain groups, Eq. U26), and the
+    time to reach eps follows from the 1/sqrt(t) law: t_eps = t (SE / eps)^2.
+    The network is trained first on valid paths collected from plain Gibbs
+    (the training time is reported separately)."""
+    import torch
+    from paper_2007_07379_gb300 import pbits
+    wl = wl or W.learned()
+    n, d = wl.n, wl.d
+    out = {"workload": f"{wl.name}: random Clifford+T n={n} d={d}, {wl.chains} chains, hidden 256",
+           "eps": 0.01}
+    with torch.cuda.stream(stream):
+        model = pbits.Model(n, d, wl.gates, wl.J)
+        # 1. collect valid paths from plain Gibbs and train the network
+        t0 = time.perf_counter()
+        src = pbits.Run([model], [pbits.RunCfg(seed=wl.seed + 100, chains=wl.chains)], stream=stream)
+        net = pbits.Mlp(n, d, hidden=256, batch=4096, seed=21, stream=stream)
+        coll = pbits.Learned(src, net)
+        cap = train_paths
+        paths = torch.zeros((cap, d), dtype=torch.int32, device=dev)
+        count = torch.zeros(1, dtype=torch.int64, device=dev)
+        src.sweeps(200)
+        while int(count.item()) < cap:
+            src.sweeps(2)
+            coll.collect(paths, count)
+        t_collect = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        losses = pbits.train_on_paths(net, paths, cap, 0, steps=train_steps, rows=4096, lr=1e-3, seed=5)
+        torch.cuda.synchronize(dev)
+        t_train = time.perf_counter() - t0
+        lc = losses.cpu().numpy()
+        out.update({"train_paths": cap, "train_steps": train_steps, "collect_s": t_collect,
+                    "train_s": t_train, "loss_first": float(lc[:10].mean()), "loss_last": float(lc[-10:].mean()),
+                    "h": model.info()["h"]})
+
+        def timed(learned: bool, sweeps_per_move: int = 1):
+            run = pbits.Run([model], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, n_batches=32)],
+                            stream=stream)
+            L = pbits.Learned(run, net) if learned else None
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            steps = 0
+            while time.perf_counter() - t0 < seconds:
+                if learned:
+                    for _ in range(16):  # enqueue a bounded amount of work, then wait
+                        L.step(1)
+                        run.sweeps(sweeps_per_move)
+                        steps += sweeps_per_move
+                    run.wait()
+                else:
+                    run.sweeps(200)
+                    run.wait()
+                    steps += 200
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter() - t0
+            psi, se = run.amplitudes()
+            se_rms = float(np.sqrt(np.mean(se ** 2)))
+            res = {"wall_s": t, "sweeps": steps, "se_rms": se_rms, "se_psi0": float(se[0]),
+                   "t_to_eps_s": t * (se_rms / 0.01) ** 2}
+            if learned:
+                mv, acc = L.stats()
+                res["moves"] = mv
+                res["accept"] = acc / max(mv * wl.chains, 1)
+                res["ms_per_move_and_sweep"] = 1e3 * t / max(mv, 1)
+            return res
+
+        out["plain"] = timed(False)
+        out["learned"] = timed(True)
+        out["ratio_plain_over_learned"] = out["plain"]["t_to_eps_s"] / out["learned"]["t_to_eps_s"]
+    return out
 
 
 def kernel_rev() -> str:

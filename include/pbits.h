@@ -65,6 +65,7 @@ typedef struct {
 typedef struct pb_model pb_model;
 typedef struct pb_run pb_run;
 typedef struct pb_mlp pb_mlp;
+typedef struct pb_mh pb_mh;
 
 /* ---- A1: compile (Eqs. UE, EB, ET2; Appendix) ---------------------------
  * Builds the layered J-penalty network of a gate list: p-bit (k, q) is bit q
@@ -247,6 +248,9 @@ PB_API int pb_mlp_params(pb_mlp* mlp, float* host, int get);
 PB_API int pb_mlp_grads(pb_mlp* mlp, float* host);
 /* d_x: device bf16 [rows x k_in]; d_logits: device fp32 [rows x n]. */
 PB_API int pb_mlp_forward(pb_mlp* mlp, const void* d_x, int rows, float* d_logits);
+/* Same output from the fused inference kernel (one tcgen05 kernel for the
+ * three layers; k_in <= 96, n <= 32); the MH move uses this path. */
+PB_API int pb_mlp_forward_fused(pb_mlp* mlp, const void* d_x, int rows, float* d_logits);
 /* Gradients of the mean binary cross-entropy against d_target (device fp32
  * 0/1, [rows x n]); rows a multiple of 8; d_loss (device fp32) may be NULL. */
 PB_API int pb_mlp_backward(pb_mlp* mlp, const void* d_x, const float* d_target, int rows,
@@ -264,12 +268,17 @@ PB_API void pb_mlp_free(pb_mlp* mlp);
  * v = violated links of layers k*..d (Re E = J v).  The move keeps the
  * sampled distribution (the J-penalty Boltzmann law of the Gibbs sweeps), so
  * it is interleaved with pb_run_sweeps, whose records count the samples.
- * Scratch: a caller device workspace of pb_mh_workspace_bytes (256-byte
- * aligned).  Runs on the run's stream; returns when the moves are done,
- * with the number of accepted proposals in *accepted (may be NULL). */
+ * A pb_mh object ties a run's model to a network and a caller device
+ * workspace of pb_mh_workspace_bytes (256-byte aligned); the run and the
+ * network must outlive it.  pb_mh_moves enqueues moves on the run's stream
+ * (each replayed from a CUDA graph captured once per k*); pb_mh_stats
+ * returns the moves done and proposals accepted (synchronous). */
 PB_API int pb_mh_workspace_bytes(const pb_run* run, int model, size_t* bytes);
-PB_API int pb_mh_moves(pb_run* run, int model, pb_mlp* mlp, uint32_t move0, uint32_t n_moves,
-                       void* d_workspace, size_t workspace_bytes, uint64_t* accepted);
+PB_API int pb_mh_create(pb_run* run, int model, pb_mlp* mlp, void* d_workspace,
+                        size_t workspace_bytes, pb_mh** out);
+PB_API int pb_mh_moves(pb_mh* mh, uint32_t n_moves);
+PB_API int pb_mh_stats(pb_mh* mh, uint64_t* moves, uint64_t* accepted);
+PB_API void pb_mh_free(pb_mh* mh);
 /* Appends the valid paths among the chains of `model` (per-chain layer
  * words s_1..s_d, d u32 each) to d_paths at the device counter *d_count
  * (u64, caller-initialised), up to `capacity` paths.  Workspace as for

@@ -21,6 +21,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "pb_internal.h"
@@ -140,10 +141,12 @@ __global__ void rows_proposal_kernel(const uint32_t* __restrict__ P, const uint3
 
 // Draw s'_j of each row from sigmoid(logits); accumulate log q'.
 __global__ void sample_kernel(const float* __restrict__ logits, int npad, int n, int d, int j,
-                              uint32_t c0, int rows, uint32_t k0, uint32_t k1, uint32_t move,
-                              uint32_t group0, uint32_t* __restrict__ Pn, float* __restrict__ lqf) {
+                              uint32_t c0, int rows, uint32_t k0, uint32_t k1,
+                              const uint32_t* __restrict__ move_dev, uint32_t group0,
+                              uint32_t* __restrict__ Pn, float* __restrict__ lqf) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
+  const uint32_t move = *move_dev;
   const uint32_t c = c0 + (uint32_t)r;
   const uint32_t gc = group0 * 32u + c;  // global chain id
   uint32_t word = 0u;
@@ -172,10 +175,11 @@ __global__ void accept_kernel(uint32_t* __restrict__ P, const uint32_t* __restri
                               const LayerTab* __restrict__ tab, uint32_t beta, uint32_t nmask,
                               int d, int k, float J, const float* __restrict__ lq,
                               const float* __restrict__ lqf, uint32_t chains, uint32_t k0,
-                              uint32_t k1, uint32_t move, uint32_t group0,
+                              uint32_t k1, const uint32_t* __restrict__ move_dev, uint32_t group0,
                               unsigned long long* __restrict__ n_accept) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= chains) return;
+  const uint32_t move = *move_dev;
   const uint32_t* cur = P + (size_t)c * d;
   const uint32_t* prop = Pn + (size_t)c * d;
   const uint32_t base = k == 1 ? beta : cur[k - 2];
@@ -200,6 +204,8 @@ __global__ void accept_kernel(uint32_t* __restrict__ P, const uint32_t* __restri
     atomicAdd(n_accept, 1ull);
   }
 }
+
+__global__ void mh_advance_kernel(uint32_t* move_dev) { *move_dev += 1u; }
 
 // Valid paths (no violated link) appended to out[count][d] while room is left.
 __global__ void collect_kernel(const uint32_t* __restrict__ P, const LayerTab* __restrict__ tab,
@@ -263,7 +269,7 @@ std::vector<LayerTab> layer_table(const pb_model& m) {
 }
 
 struct MhLayout {
-  size_t tab, P, Pn, lq, lqf, cnt, total;
+  size_t tab, P, Pn, lq, lqf, cnt, move, total;
 };
 
 MhLayout mh_layout(int d, uint32_t groups) {
@@ -282,6 +288,7 @@ MhLayout mh_layout(int d, uint32_t groups) {
   L.lq = take(C * d * 4);
   L.lqf = take(C * 4);
   L.cnt = take(16);
+  L.move = take(16);
   L.total = (p + 255) & ~(size_t)255;
   return L;
 }
@@ -306,8 +313,87 @@ PB_API int pb_mh_workspace_bytes(const pb_run* run, int model, size_t* bytes) {
   return PB_OK;
 }
 
-PB_API int pb_mh_moves(pb_run* run, int model, pb_mlp* mlp, uint32_t move0, uint32_t n_moves,
-                       void* d_ws, size_t ws_bytes, uint64_t* accepted) {
+}  // extern "C"
+
+struct pb_mh {
+  pb_run* run = nullptr;
+  pb_mlp* mlp = nullptr;
+  int model = 0;
+  RunView v{};
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  MhLayout L{};
+  uint32_t moves = 0;
+  cudaStream_t cap_st = nullptr;
+  std::vector<cudaGraphExec_t> graphs;  // one per k* (1..d), built on first use
+};
+
+namespace {
+
+// The kernels of one move with suffix start k, in stream order.
+cudaError_t enqueue_move(pb_mh* h, int k, cudaStream_t st) {
+  const pb_model& m = *h->v.model;
+  pb_mlp* mlp = h->mlp;
+  char* ws = h->ws;
+  const MhLayout& L = h->L;
+  uint32_t* P = reinterpret_cast<uint32_t*>(ws + L.P);
+  uint32_t* Pn = reinterpret_cast<uint32_t*>(ws + L.Pn);
+  float* lq = reinterpret_cast<float*>(ws + L.lq);
+  float* lqf = reinterpret_cast<float*>(ws + L.lqf);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws + L.cnt);
+  uint32_t* move_dev = reinterpret_cast<uint32_t*>(ws + L.move);
+  const LayerTab* dtab = reinterpret_cast<const LayerTab*>(ws + L.tab);
+  const int n = m.n, d = m.d, kin = mlp->kin, npad = mlp->npad, B = mlp->batch;
+  const uint32_t nmask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  const uint32_t C = h->v.chains;
+  const uint32_t k0 = (uint32_t)h->v.seed, k1 = (uint32_t)(h->v.seed >> 32);
+  const int T = 256;
+  const int Ls = d - k + 1;
+  cudaStream_t mst = mlp->st;
+  mlp->st = st;
+  cudaError_t e = cudaSuccess;
+  const bool fused = mlp->kin <= 96 && mlp->npad <= 32;
+  auto forward = [&](int rows) { return fused ? mlp_forward_fused(mlp, rows) : mlp_forward_rows(mlp, rows); };
+  const uint32_t warps = h->v.groups * (uint32_t)d;
+  unslice_kernel<<<(warps * 32 + T - 1) / T, T, 0, st>>>(h->v.state, n, d, h->v.groups, P);
+  const uint64_t rows_total = (uint64_t)C * Ls;
+  for (uint64_t r0 = 0; r0 < rows_total && e == cudaSuccess; r0 += B) {
+    const int rows = (int)std::min<uint64_t>(B, rows_total - r0);
+    rows_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(P, m.beta, n, d, kin, k, r0, rows, mlp->X);
+    if ((e = forward(rows)) != cudaSuccess) break;
+    logq_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, P, n, d, k, r0, rows, lq);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(lqf, 0, (size_t)C * 4, st);
+  for (int j = k; j <= d && e == cudaSuccess; ++j) {
+    for (uint32_t c0 = 0; c0 < C && e == cudaSuccess; c0 += (uint32_t)B) {
+      const int rows = (int)std::min<uint32_t>((uint32_t)B, C - c0);
+      rows_proposal_kernel<<<(rows + T - 1) / T, T, 0, st>>>(P, Pn, m.beta, n, d, kin, k, j, c0,
+                                                             rows, mlp->X);
+      if ((e = forward(rows)) != cudaSuccess) break;
+      sample_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, n, d, j, c0, rows, k0, k1,
+                                                      move_dev, h->v.group0, Pn, lqf);
+    }
+  }
+  if (e == cudaSuccess) {
+    accept_kernel<<<(C + T - 1) / T, T, 0, st>>>(P, Pn, dtab, m.beta, nmask, d, k, (float)m.J, lq,
+                                                 lqf, C, k0, k1, move_dev, h->v.group0, cnt);
+    const uint32_t sw = h->v.groups * (uint32_t)Ls;
+    slice_kernel<<<(sw * 32 + T - 1) / T, T, 0, st>>>(P, n, d, k, h->v.groups, h->v.state);
+    mh_advance_kernel<<<1, 1, 0, st>>>(move_dev);
+    e = cudaGetLastError();
+  }
+  mlp->st = mst;
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+PB_API int pb_mh_create(pb_run* run, int model, pb_mlp* mlp, void* d_ws, size_t ws_bytes,
+                        pb_mh** out) {
+  if (!out) return PB_EINVAL;
+  *out = nullptr;
   RunView v;
   int rc = run_view(run, model, &v);
   if (rc != PB_OK) return rc;
@@ -316,67 +402,73 @@ PB_API int pb_mh_moves(pb_run* run, int model, pb_mlp* mlp, uint32_t move0, uint
   if (mlp->n != m.n || mlp->d != m.d) return PB_EINVAL;
   const MhLayout L = mh_layout(m.d, v.groups);
   if (ws_bytes < L.total) return PB_ERANGE;
-  char* ws = static_cast<char*>(d_ws);
-  uint32_t* P = reinterpret_cast<uint32_t*>(ws + L.P);
-  uint32_t* Pn = reinterpret_cast<uint32_t*>(ws + L.Pn);
-  float* lq = reinterpret_cast<float*>(ws + L.lq);
-  float* lqf = reinterpret_cast<float*>(ws + L.lqf);
-  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws + L.cnt);
-  const LayerTab* dtab = reinterpret_cast<const LayerTab*>(ws + L.tab);
-  // Everything runs on the run's stream; the network's own stream is
-  // serialised before and after.
-  cudaStream_t st = v.st;
-  cudaStream_t mst = mlp->st;
-  mlp->st = st;
-  if (cudaStreamSynchronize(mst) != cudaSuccess) { mlp->st = mst; return PB_ECUDA; }
+  pb_mh* h = new (std::nothrow) pb_mh;
+  if (!h) return PB_ENOMEM;
+  h->run = run; h->mlp = mlp; h->model = model; h->v = v;
+  h->ws = static_cast<char*>(d_ws); h->ws_bytes = ws_bytes; h->L = L;
+  h->graphs.assign(m.d + 1, nullptr);
   const std::vector<LayerTab> tab = layer_table(m);
-  cudaError_t e = cudaMemcpyAsync(ws + L.tab, tab.data(), sizeof(LayerTab) * m.d,
-                                  cudaMemcpyHostToDevice, st);
-  e = e == cudaSuccess ? cudaMemsetAsync(cnt, 0, 8, st) : e;
-  const int n = m.n, d = m.d, kin = mlp->kin, npad = mlp->npad, B = mlp->batch;
-  const uint32_t nmask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-  const uint32_t C = v.chains;
-  const uint32_t k0 = (uint32_t)v.seed, k1 = (uint32_t)(v.seed >> 32);
-  const int T = 256;
-  for (uint32_t mv = 0; mv < n_moves && e == cudaSuccess; ++mv) {
-    const uint32_t move = move0 + mv;
-    const int k = 1 + (int)(splitmix(v.seed ^ (0xA5A5ull << 40) ^ move) % (uint64_t)d);
-    const int Ls = d - k + 1;
-    const uint32_t warps = v.groups * (uint32_t)d;
-    unslice_kernel<<<(warps * 32 + T - 1) / T, T, 0, st>>>(v.state, n, d, v.groups, P);
-    // log q of the current suffix
-    const uint64_t rows_total = (uint64_t)C * Ls;
-    for (uint64_t r0 = 0; r0 < rows_total && e == cudaSuccess; r0 += B) {
-      const int rows = (int)std::min<uint64_t>(B, rows_total - r0);
-      rows_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(P, m.beta, n, d, kin, k, r0, rows, mlp->X);
-      if ((e = mlp_forward_rows(mlp, rows)) != cudaSuccess) break;
-      logq_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, P, n, d, k, r0, rows, lq);
-    }
-    // the proposal, layer by layer
-    cudaMemsetAsync(lqf, 0, (size_t)C * 4, st);
-    for (int j = k; j <= d && e == cudaSuccess; ++j) {
-      for (uint32_t c0 = 0; c0 < C && e == cudaSuccess; c0 += (uint32_t)B) {
-        const int rows = (int)std::min<uint32_t>((uint32_t)B, C - c0);
-        rows_proposal_kernel<<<(rows + T - 1) / T, T, 0, st>>>(P, Pn, m.beta, n, d, kin, k, j, c0,
-                                                               rows, mlp->X);
-        if ((e = mlp_forward_rows(mlp, rows)) != cudaSuccess) break;
-        sample_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, n, d, j, c0, rows, k0, k1,
-                                                        move, v.group0, Pn, lqf);
+  cudaError_t e = cudaMemsetAsync(h->ws, 0, L.total, v.st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->ws + L.tab, tab.data(), sizeof(LayerTab) * m.d, cudaMemcpyHostToDevice, v.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(mlp->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(v.st);
+  if (e == cudaSuccess) e = mlp_prepare();
+  if (e != cudaSuccess) { delete h; return PB_ECUDA; }
+  *out = h;
+  return PB_OK;
+}
+
+// n_moves further moves, each replayed from a CUDA graph captured for its
+// suffix start k* (asynchronous on the run's stream).
+PB_API int pb_mh_moves(pb_mh* h, uint32_t n_moves) {
+  if (!h) return PB_EINVAL;
+  const int d = h->v.model->d;
+  for (uint32_t i = 0; i < n_moves; ++i) {
+    const uint32_t move = h->moves;
+    const int k = 1 + (int)(splitmix(h->v.seed ^ (0xA5A5ull << 40) ^ move) % (uint64_t)d);
+    cudaGraphExec_t& ex = h->graphs[k];
+    if (!ex) {
+      if (!h->cap_st && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess)
+        return PB_ECUDA;
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return PB_ECUDA;
+      cudaError_t e = enqueue_move(h, k, h->cap_st);
+      cudaError_t e2 = cudaStreamEndCapture(h->cap_st, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return PB_ECUDA;
       }
+      e = cudaGraphInstantiate(&ex, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) { ex = nullptr; return PB_ECUDA; }
     }
-    if (e != cudaSuccess) break;
-    accept_kernel<<<(C + T - 1) / T, T, 0, st>>>(P, Pn, dtab, m.beta, nmask, d, k, (float)m.J, lq,
-                                                 lqf, C, k0, k1, move, v.group0, cnt);
-    const uint32_t sw = v.groups * (uint32_t)Ls;
-    slice_kernel<<<(sw * 32 + T - 1) / T, T, 0, st>>>(P, n, d, k, v.groups, v.state);
-    e = cudaGetLastError();
+    if (cudaGraphLaunch(ex, h->v.st) != cudaSuccess) return PB_ECUDA;
+    h->moves += 1;
   }
+  return PB_OK;
+}
+
+// Moves done and proposals accepted so far (synchronous).
+PB_API int pb_mh_stats(pb_mh* h, uint64_t* moves, uint64_t* accepted) {
+  if (!h) return PB_EINVAL;
   unsigned long long acc = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&acc, cnt, 8, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  mlp->st = mst;
+  if (cudaMemcpyAsync(&acc, h->ws + h->L.cnt, 8, cudaMemcpyDeviceToHost, h->v.st) != cudaSuccess ||
+      cudaStreamSynchronize(h->v.st) != cudaSuccess)
+    return PB_ECUDA;
+  if (moves) *moves = h->moves;
   if (accepted) *accepted = acc;
-  return e == cudaSuccess ? PB_OK : PB_ECUDA;
+  return PB_OK;
+}
+
+PB_API void pb_mh_free(pb_mh* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->v.st);
+  for (auto& g : h->graphs)
+    if (g) cudaGraphExecDestroy(g);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  delete h;
 }
 
 PB_API int pb_run_collect_paths(pb_run* run, int model, void* d_ws, size_t ws_bytes,

@@ -39,9 +39,15 @@ struct GemmArgs {
   uint32_t* status;  // set to PB_ETIMEOUT when a bounded wait expires
 };
 
-__host__ __device__ inline int gemm_tile_n(int N) {
+// Tile width: N rounded up to 16, at most 256, narrowed to 128 or 64 when
+// the row tiles alone would leave most of the 152 SMs idle.
+__host__ __device__ inline int gemm_tile_n(int M, int N) {
   int bn = ((N + 15) / 16) * 16;
-  return bn > 256 ? 256 : bn;
+  if (bn > 256) bn = 256;
+  const int mt = (M + 127) / 128;
+  if (bn > 128 && mt * ((N + bn - 1) / bn) < 120) bn = 128;
+  if (bn > 64 && mt * ((N + bn - 1) / bn) < 120) bn = 64;
+  return bn;
 }
 __host__ __device__ inline uint32_t tmem_cols(int bn) {
   uint32_t c = 32;
@@ -53,7 +59,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_tn_kernel(GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  const int BN = gemm_tile_n(g.N);
+  const int BN = gemm_tile_n(g.M, g.N);
   uint8_t* sA = sm;            // 128 x 64 bf16 (16 KiB)
   uint8_t* sB = sm + 16384;    // BN x 64 bf16 (<= 32 KiB)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -144,15 +150,16 @@ __global__ void __launch_bounds__(128) gemm_bf16_tn_kernel(GemmArgs g) {
   if (warp == 0) tc::tmem_dealloc(tbase, ncols);
 }
 
+// One-time set-up outside any stream capture (shared-memory opt-in).
+cudaError_t mlp_fused_prepare();
+cudaError_t mlp_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+  return e == cudaSuccess ? mlp_fused_prepare() : e;
+}
+
 cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tn_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int BN = gemm_tile_n(g.N);
+  const int BN = gemm_tile_n(g.M, g.N);
   dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN);
   gemm_bf16_tn_kernel<<<grid, 128, 16384 + BN * 64 * 2, st>>>(g);
   return cudaGetLastError();
@@ -185,6 +192,7 @@ extern "C" PB_API int pb_gemm_bf16(const void* dA, int lda, const void* dB, int 
   g.flags = flags;
   g.alpha = alpha;
   g.status = nullptr;
+  if (mlp_prepare() != cudaSuccess) return PB_ECUDA;
   return launch_gemm_bf16(g, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? PB_OK
                                                                                    : PB_ECUDA;
 }
@@ -530,7 +538,8 @@ PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, voi
   fill(p->off_W2, hidden, hidden, hidden, hidden, hidden);
   fill(p->off_W3, npad, hidden, hidden, n, hidden);
   cudaError_t e;
-  if ((e = cudaMemsetAsync(p->ws, 0, L.total, p->st)) != cudaSuccess ||
+  if ((e = pb::mlp_prepare()) != cudaSuccess ||
+      (e = cudaMemsetAsync(p->ws, 0, L.total, p->st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(p->w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, p->st)) != cudaSuccess ||
       (e = refresh_bf16(p)) != cudaSuccess || (e = cudaStreamSynchronize(p->st)) != cudaSuccess) {
     delete p;
@@ -607,3 +616,205 @@ PB_API void pb_mlp_free(pb_mlp* p) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Fused forward of the whole network for inference: one CTA of 4 warps per
+// 128 rows; x, the hidden activations and the weights (W2 streamed in
+// K-chunks of 64, double-buffered) stay in shared memory, the accumulators in
+// TMEM (256 columns, reused by the three layers).
+// ===========================================================================
+namespace pb {
+
+struct FusedArgs {
+  const __nv_bfloat16* X;  // [rows x kin]
+  const __nv_bfloat16 *W1, *W2, *W3;
+  const float *b1, *b2, *b3;
+  float* logits;  // [rows x npad]
+  int rows, kin, H, npad;
+  uint32_t* status;
+};
+
+constexpr size_t kFusedSmem = 24 * 1024 + 64 * 1024 + 64 * 1024;  // x, h, two weight buffers
+
+// Rows [r0, r0+nrows) x K of a row-major bf16 matrix into the canonical
+// K-major layout at `dst` (8-row groups SBO = K * 16 bytes apart).
+__device__ __forceinline__ void stage_rows(uint8_t* dst, const __nv_bfloat16* src, int ld, int r0,
+                                           int nrows, int rmax, int k0, int K, int tid, int nthr) {
+  const int vecs = K / 8;
+  for (int v = tid; v < nrows * vecs; v += nthr) {
+    const int r = v / vecs, c = v % vecs, row = r0 + r;
+    uint4 val = make_uint4(0u, 0u, 0u, 0u);
+    if (row < rmax) val = *reinterpret_cast<const uint4*>(src + (size_t)row * ld + k0 + c * 8);
+    *reinterpret_cast<uint4*>(dst + (r >> 3) * (K * 16) + c * 128 + (r & 7) * 16) = val;
+  }
+}
+
+__global__ void __launch_bounds__(128) mlp_fused_fwd_kernel(FusedArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  // one mbarrier per weight buffer: each has at most one commit in flight
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  uint8_t* sX = sm;
+  uint8_t* sH = sm + 24 * 1024;
+  uint8_t* sWb[2] = {sm + 88 * 1024, sm + 120 * 1024};
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r0 = blockIdx.x * 128;
+  const int H = a.H, kin = a.kin;
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // x tile and W1
+  stage_rows(sX, a.X, kin, r0, 128, a.rows, 0, kin, tid, 128);
+  stage_rows(sWb[0], a.W1, kin, 0, H, H, 0, kin, tid, 128);
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tb = tmem_base;
+  uint32_t ph[2] = {0u, 0u};
+  bool ok = true;
+  auto wait = [&](int b) {
+    if (!ok) return;
+    ok = tc::mbar_wait(&mbar[b], ph[b]);
+    ph[b] ^= 1u;
+  };
+  const uint32_t taddr_row = tb + ((uint32_t)(warp * 32) << 16);
+  const int row = r0 + warp * 32 + lane;
+
+  // ---- layer 1: D = x W1^T   (commit on mbar[0])
+  if (tid == 0) {
+    const uint32_t ax = tc::smem_u32(sX), bw = tc::smem_u32(sWb[0]);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, H);
+    for (int s = 0; s < kin / 16; ++s)
+      tc::mma_bf16(tb, tc::smem_desc(ax + s * 256, 128, kin * 16),
+                   tc::smem_desc(bw + s * 256, 128, kin * 16), idesc, s > 0);
+    tc::mma_commit(&mbar[0]);
+  }
+  wait(0);
+
+  // epilogue: h = relu(D + b) in bf16, into sH (canonical, K = H)
+  auto epilogue_to_h = [&](const float* bias) {
+    tc::fence_after_sync();
+    for (int c0 = 0; c0 < H; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(taddr_row + (uint32_t)c0, v);
+      __align__(16) __nv_bfloat16 hb[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) hb[i] = __float2bfloat16(fmaxf(v[i] + bias[c0 + i], 0.f));
+      const int r = warp * 32 + lane;
+      uint8_t* base = sH + (r >> 3) * (H * 16) + (r & 7) * 16;
+      *reinterpret_cast<uint4*>(base + (c0 / 8) * 128) = *reinterpret_cast<uint4*>(&hb[0]);
+      *reinterpret_cast<uint4*>(base + (c0 / 8 + 1) * 128) = *reinterpret_cast<uint4*>(&hb[8]);
+    }
+  };
+  if (ok) epilogue_to_h(a.b1);
+
+  // ---- layer 2: D = h W2^T, W2 in K-chunks of 64; chunk c uses buffer and
+  // mbarrier c & 1.  Chunk c+1 is staged while chunk c runs, after the MMAs
+  // of chunk c-1 (same buffer) have completed.
+  const int nchunks = (H + 63) / 64;
+  auto chunk_k = [&](int c) { return (c == nchunks - 1 && (H % 64)) ? (H % 64) : 64; };
+  if (ok) stage_rows(sWb[0], a.W2, H, 0, H, H, 0, chunk_k(0), tid, 128);
+  for (int c = 0; c < nchunks && ok; ++c) {
+    const int b = c & 1;
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const int kc = chunk_k(c);
+      const uint32_t ah = tc::smem_u32(sH) + c * 8 * 128, bw = tc::smem_u32(sWb[b]);
+      const uint32_t idesc = tc::idesc_bf16_f32(128, H);
+      for (int s = 0; s < kc / 16; ++s)
+        tc::mma_bf16(tb, tc::smem_desc(ah + s * 256, 128, H * 16),
+                     tc::smem_desc(bw + s * 256, 128, kc * 16), idesc, (c > 0) || (s > 0));
+      tc::mma_commit(&mbar[b]);
+    }
+    if (c + 1 < nchunks) {
+      if (c >= 1) wait(b ^ 1);  // chunk c-1 done: its buffer is free
+      if (ok) stage_rows(sWb[b ^ 1], a.W2, H, 0, H, H, (c + 1) * 64, chunk_k(c + 1), tid, 128);
+    }
+  }
+  // the last one or two chunks of layer 2
+  if (nchunks >= 2) wait((nchunks - 2) & 1);
+  wait((nchunks - 1) & 1);
+  if (ok) {
+    epilogue_to_h(a.b2);
+    // ---- layer 3: D = h W3^T  (buffer 0 and mbar[0] are free)
+    stage_rows(sWb[0], a.W3, H, 0, a.npad, a.npad, 0, H, tid, 128);
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const uint32_t ah = tc::smem_u32(sH), bw = tc::smem_u32(sWb[0]);
+      const uint32_t idesc = tc::idesc_bf16_f32(128, a.npad);
+      for (int s = 0; s < H / 16; ++s)
+        tc::mma_bf16(tb, tc::smem_desc(ah + s * 256, 128, H * 16),
+                     tc::smem_desc(bw + s * 256, 128, H * 16), idesc, s > 0);
+      tc::mma_commit(&mbar[0]);
+    }
+    wait(0);
+  }
+  if (ok) {
+    tc::fence_after_sync();
+    for (int c0 = 0; c0 < a.npad; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(taddr_row + (uint32_t)c0, v);
+      if (row < a.rows) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) a.logits[(size_t)row * a.npad + c0 + i] = v[i] + a.b3[c0 + i];
+      }
+    }
+  } else {
+    if (a.status) atomicCAS(a.status, 0u, (uint32_t)PB_ETIMEOUT);
+    // let MMAs in flight drain (bounded) before the accumulator is freed
+    tc::mbar_wait(&mbar[0], ph[0]);
+    tc::mbar_wait(&mbar[1], ph[1]);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tb, 256);
+}
+
+cudaError_t mlp_forward_fused(pb_mlp* p, int rows) {
+  FusedArgs a{};
+  a.X = p->X;
+  a.W1 = p->W1;
+  a.W2 = p->W2;
+  a.W3 = p->W3;
+  a.b1 = p->w + p->off_b1;
+  a.b2 = p->w + p->off_b2;
+  a.b3 = p->w + p->off_b3;
+  a.logits = p->logits;
+  a.rows = rows;
+  a.kin = p->kin;
+  a.H = p->H;
+  a.npad = p->npad;
+  a.status = nullptr;
+  mlp_fused_fwd_kernel<<<(rows + 127) / 128, 128, kFusedSmem, p->st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_fused_prepare() {
+  return cudaFuncSetAttribute(mlp_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kFusedSmem);
+}
+
+}  // namespace pb
+
+extern "C" PB_API int pb_mlp_forward_fused(pb_mlp* p, const void* d_x, int rows, float* d_logits) {
+  if (!p || !d_x || !d_logits || rows <= 0 || rows > p->batch) return PB_EINVAL;
+  if (p->kin > 96 || p->npad > 32) return PB_ERANGE;
+  if (cudaMemcpyAsync(p->X, d_x, (size_t)rows * p->kin * 2, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess)
+    return PB_ECUDA;
+  if (pb::mlp_forward_fused(p, rows) != cudaSuccess) return PB_ECUDA;
+  if (cudaMemcpy2DAsync(d_logits, (size_t)p->n * 4, p->logits, (size_t)p->npad * 4, (size_t)p->n * 4,
+                        rows, cudaMemcpyDeviceToDevice, p->st) != cudaSuccess)
+    return PB_ECUDA;
+  return PB_OK;
+}

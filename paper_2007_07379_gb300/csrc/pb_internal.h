@@ -127,6 +127,8 @@ namespace pb {
 cudaError_t mlp_forward_rows(pb_mlp* p, int rows);
 cudaError_t mlp_backward_rows(pb_mlp* p, int rows);
 cudaError_t mlp_adam_step(pb_mlp* p, float lr);
+cudaError_t mlp_prepare();
+cudaError_t mlp_forward_fused(pb_mlp* p, int rows);
 
 // What the learned-proposal code needs to know about one model of a run.
 struct RunView {

@@ -90,11 +90,14 @@ _SIGS = {
     "pb_mlp_grads": (ctypes.c_int, [_VP, _VP]),
     "pb_mlp_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
     "pb_mlp_backward": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "pb_mlp_forward_fused": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
     "pb_mlp_adam": (ctypes.c_int, [_VP, ctypes.c_float]),
     "pb_mlp_free": (None, [_VP]),
     "pb_mh_workspace_bytes": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
-    "pb_mh_moves": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_uint32, ctypes.c_uint32, _VP,
-                                   ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)]),
+    "pb_mh_create": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_size_t, ctypes.POINTER(_VP)]),
+    "pb_mh_moves": (ctypes.c_int, [_VP, ctypes.c_uint32]),
+    "pb_mh_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "pb_mh_free": (None, [_VP]),
     "pb_run_collect_paths": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_size_t, _VP, ctypes.c_uint64,
                                             _VP]),
     "pb_mlp_train_paths": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
@@ -455,6 +458,14 @@ class Mlp:
                                      ctypes.c_void_p(out.data_ptr())), "pb_mlp_forward")
         return out
 
+    def forward_fused(self, x_bf16):
+        import torch
+        rows = x_bf16.shape[0]
+        out = torch.empty(rows, self.n, dtype=torch.float32, device="cuda")
+        _check(load().pb_mlp_forward_fused(self._h, ctypes.c_void_p(x_bf16.data_ptr()), rows,
+                                           ctypes.c_void_p(out.data_ptr())), "pb_mlp_forward_fused")
+        return out
+
     def backward(self, x_bf16, target):
         import torch
         loss = torch.zeros(1, dtype=torch.float32, device="cuda")
@@ -479,8 +490,8 @@ class Mlp:
 
 
 class Learned:
-    """Learned-proposal sampler on one model of a run: path collection,
-    training of the network and Metropolis-Hastings suffix moves."""
+    """Learned-proposal sampler on one model of a run (pb_mh_*): path
+    collection, Metropolis-Hastings suffix moves with the network."""
 
     def __init__(self, run: Run, mlp: Mlp, model: int = 0):
         import torch
@@ -488,19 +499,30 @@ class Learned:
         nb = ctypes.c_size_t(0)
         _check(load().pb_mh_workspace_bytes(run._h, model, ctypes.byref(nb)), "pb_mh_workspace_bytes")
         self.workspace = torch.zeros(nb.value, dtype=torch.uint8, device="cuda")
-        self.moves = 0
-        self.accepted = 0
-        self.proposed = 0
+        h = ctypes.c_void_p()
+        _check(load().pb_mh_create(run._h, model, mlp.handle, ctypes.c_void_p(self.workspace.data_ptr()),
+                                   self.workspace.numel(), ctypes.byref(h)), "pb_mh_create")
+        self._h = h
 
-    def step(self, n_moves: int = 1) -> int:
-        acc = ctypes.c_uint64(0)
-        _check(load().pb_mh_moves(self.run._h, self.model, self.mlp.handle, self.moves, n_moves,
-                                  ctypes.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
-                                  ctypes.byref(acc)), "pb_mh_moves")
-        self.moves += n_moves
-        self.accepted += acc.value
-        self.proposed += n_moves * self.run.cfgs[self.model].chains
-        return acc.value
+    def step(self, n_moves: int = 1):
+        _check(load().pb_mh_moves(self._h, n_moves), "pb_mh_moves")
+
+    def stats(self):
+        mv, acc = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(load().pb_mh_stats(self._h, ctypes.byref(mv), ctypes.byref(acc)), "pb_mh_stats")
+        return mv.value, acc.value
+
+    @property
+    def moves(self):
+        return self.stats()[0]
+
+    @property
+    def accepted(self):
+        return self.stats()[1]
+
+    @property
+    def proposed(self):
+        return self.stats()[0] * self.run.cfgs[self.model].chains
 
     def collect(self, paths, count):
         """Append the valid chain paths to `paths` (int32 [cap, d] CUDA tensor);
@@ -509,6 +531,17 @@ class Learned:
                                            self.workspace.numel(), ctypes.c_void_p(paths.data_ptr()),
                                            paths.shape[0], ctypes.c_void_p(count.data_ptr())),
                "pb_run_collect_paths")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pb_mh_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def train_on_paths(mlp: Mlp, paths, n_paths: int, beta: int, steps: int, rows: int, lr: float, seed: int):

@@ -170,6 +170,15 @@ def learned() -> Workload:
                     J=default_J(16, 24, g), extra={"hidden": 256, "train_paths": 1_000_000})
 
 
+def learned_sparse() -> Workload:
+    """n=16, d=24 under the alternative reading "one random gate per layer"
+    (few H gates: the error target is reachable and plain Gibbs must walk a
+    defect along each wire to change a path)."""
+    g = random_circuit(16, 24, seed=3000, one_gate_per_layer=True)
+    return Workload("learned_sparse", 16, 24, g, chains=4096, sweeps=10_000, seed=0x5EED + 3,
+                    J=default_J(16, 24, g), extra={"hidden": 256, "train_paths": 1_000_000})
+
+
 def large() -> Workload:
     """n=24, d=32 (24*33 = 792 p-bits), 65536 chains, 64 output amplitudes alpha in 0..63."""
     g = random_circuit(24, 32, seed=4000)

@@ -103,3 +103,17 @@ def test_training_fits_a_deterministic_map():
         losses.append(loss.item())
     assert losses[0] > 0.5 * n * np.log(2)
     assert np.mean(losses[-20:]) < 0.05 * n * np.log(2), losses[-20:]
+
+
+@pytest.mark.parametrize("n,d,hidden,rows", [(16, 24, 256, 4096), (24, 32, 256, 300), (5, 7, 64, 128),
+                                             (6, 12, 128, 1024), (3, 4, 48, 130)])
+def test_fused_forward_matches_layered_and_oracle(n, d, hidden, rows):
+    net = pbits.Mlp(n, d, hidden=hidden, batch=((rows + 127) // 128) * 128, seed=8)
+    x, _, xt, _ = _batch(net, rows, 4)
+    fused = net.forward_fused(xt).cpu().numpy()
+    layered = net.forward(xt).cpu().numpy()
+    p = _oracle_params(net)
+    want, _ = M.forward({k: (v[:n] if k in ("W3", "b3") else v) for k, v in p.items()}, x)
+    scale = max(1.0, np.abs(want).max())
+    assert np.abs(fused - want).max() < 2e-2 * scale
+    assert np.abs(fused - layered).max() < 1e-3 * scale
