@@ -81,14 +81,21 @@ __global__ void slice_kernel(const uint32_t* __restrict__ P, int n, int d, int k
   if (lane < n) state[((size_t)g * d + j) * n + lane] = y;
 }
 
+// Row x = [2 s_{j-1} - 1 (n), onehot(j-1) (d), 0...] in bf16, written in
+// 16-byte pieces (k_in is a multiple of 16).
 __device__ __forceinline__ void write_row(__nv_bfloat16* X, int kin, int n, int d, int row,
                                           uint32_t prev, int j) {
-  __nv_bfloat16* x = X + (size_t)row * kin;
-  for (int i = 0; i < kin; ++i) {
-    float v = 0.f;
-    if (i < n) v = ((prev >> i) & 1u) ? 1.f : -1.f;
-    else if (i == n + j - 1) v = 1.f;
-    x[i] = __float2bfloat16(v);
+  uint4* x = reinterpret_cast<uint4*>(X + (size_t)row * kin);
+  const __nv_bfloat16 one = __float2bfloat16(1.f), mone = __float2bfloat16(-1.f),
+                      zero = __float2bfloat16(0.f);
+  for (int i0 = 0; i0 < kin; i0 += 8) {
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = i0 + t;
+      v[t] = i < n ? (((prev >> i) & 1u) ? one : mone) : (i == n + j - 1 ? one : zero);
+    }
+    x[i0 / 8] = *reinterpret_cast<const uint4*>(v);
   }
 }
 
@@ -353,25 +360,32 @@ cudaError_t enqueue_move(pb_mh* h, int k, cudaStream_t st) {
   mlp->st = st;
   cudaError_t e = cudaSuccess;
   const bool fused = mlp->kin <= 96 && mlp->npad <= 32;
-  auto forward = [&](int rows) { return fused ? mlp_forward_fused(mlp, rows) : mlp_forward_rows(mlp, rows); };
   const uint32_t warps = h->v.groups * (uint32_t)d;
   unslice_kernel<<<(warps * 32 + T - 1) / T, T, 0, st>>>(h->v.state, n, d, h->v.groups, P);
-  const uint64_t rows_total = (uint64_t)C * Ls;
-  for (uint64_t r0 = 0; r0 < rows_total && e == cudaSuccess; r0 += B) {
-    const int rows = (int)std::min<uint64_t>(B, rows_total - r0);
-    rows_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(P, m.beta, n, d, kin, k, r0, rows, mlp->X);
-    if ((e = forward(rows)) != cudaSuccess) break;
-    logq_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, P, n, d, k, r0, rows, lq);
-  }
-  if (e == cudaSuccess) e = cudaMemsetAsync(lqf, 0, (size_t)C * 4, st);
-  for (int j = k; j <= d && e == cudaSuccess; ++j) {
-    for (uint32_t c0 = 0; c0 < C && e == cudaSuccess; c0 += (uint32_t)B) {
-      const int rows = (int)std::min<uint32_t>((uint32_t)B, C - c0);
-      rows_proposal_kernel<<<(rows + T - 1) / T, T, 0, st>>>(P, Pn, m.beta, n, d, kin, k, j, c0,
-                                                             rows, mlp->X);
-      if ((e = forward(rows)) != cudaSuccess) break;
-      sample_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, n, d, j, c0, rows, k0, k1,
-                                                      move_dev, h->v.group0, Pn, lqf);
+  if (fused) {
+    // one launch for log q of the current suffix, one per proposal layer
+    e = mlp_fused_logq(mlp, P, m.beta, (int)C, k, lq, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lqf, 0, (size_t)C * 4, st);
+    if (e == cudaSuccess)
+      e = mlp_fused_sample(mlp, P, Pn, m.beta, (int)C, k, k, d, lqf, k0, k1, move_dev, h->v.group0, st);
+  } else {
+    const uint64_t rows_total = (uint64_t)C * Ls;
+    for (uint64_t r0 = 0; r0 < rows_total && e == cudaSuccess; r0 += B) {
+      const int rows = (int)std::min<uint64_t>(B, rows_total - r0);
+      rows_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(P, m.beta, n, d, kin, k, r0, rows, mlp->X);
+      if ((e = mlp_forward_rows(mlp, rows)) != cudaSuccess) break;
+      logq_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, P, n, d, k, r0, rows, lq);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(lqf, 0, (size_t)C * 4, st);
+    for (int j = k; j <= d && e == cudaSuccess; ++j) {
+      for (uint32_t c0 = 0; c0 < C && e == cudaSuccess; c0 += (uint32_t)B) {
+        const int rows = (int)std::min<uint32_t>((uint32_t)B, C - c0);
+        rows_proposal_kernel<<<(rows + T - 1) / T, T, 0, st>>>(P, Pn, m.beta, n, d, kin, k, j, c0,
+                                                               rows, mlp->X);
+        if ((e = mlp_forward_rows(mlp, rows)) != cudaSuccess) break;
+        sample_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, n, d, j, c0, rows, k0, k1,
+                                                        move_dev, h->v.group0, Pn, lqf);
+      }
     }
   }
   if (e == cudaSuccess) {

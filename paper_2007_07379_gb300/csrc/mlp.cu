@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "pb_internal.h"
+#include "philox.cuh"
 #include "tc_gemm.cuh"
 
 #include <cmath>
@@ -83,18 +84,17 @@ __global__ void __launch_bounds__(128) gemm_bf16_tn_kernel(GemmArgs g) {
     // stage A (128 x 64) and B (BN x 64): one 16-byte vector = 8 K-elements
     for (int v = tid; v < 128 * 8; v += 128) {
       const int r = v >> 3, c = v & 7, k = k0 + c * 8, row = m0 + r;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (row < g.M && k < g.K)
-        val = *reinterpret_cast<const uint4*>(g.A + (size_t)row * g.lda + k);
-      *reinterpret_cast<uint4*>(sA + tc::chunk_offset(r, c * 8)) = val;
+      const bool in = row < g.M && k < g.K;
+      tc::cp_async16(sA + tc::chunk_offset(r, c * 8),
+                     in ? (const void*)(g.A + (size_t)row * g.lda + k) : (const void*)g.A, in ? 16u : 0u);
     }
     for (int v = tid; v < BN * 8; v += 128) {
       const int r = v >> 3, c = v & 7, k = k0 + c * 8, row = n0 + r;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      if (row < g.N && k < g.K)
-        val = *reinterpret_cast<const uint4*>(g.B + (size_t)row * g.ldb + k);
-      *reinterpret_cast<uint4*>(sB + tc::chunk_offset(r, c * 8)) = val;
+      const bool in = row < g.N && k < g.K;
+      tc::cp_async16(sB + tc::chunk_offset(r, c * 8),
+                     in ? (const void*)(g.B + (size_t)row * g.ldb + k) : (const void*)g.B, in ? 16u : 0u);
     }
+    tc::cp_async_wait_all();
     tc::fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -625,31 +625,68 @@ PB_API void pb_mlp_free(pb_mlp* p) {
 // ===========================================================================
 namespace pb {
 
+// Modes of the fused kernel:
+//   kFusedLogits  rows of x from global memory -> logits to global memory;
+//   kFusedLogQ    rows (chain c, layer j = k + blockIdx.y) built from the
+//                 per-chain words P -> lq[c d + j-1] = log q(P[c][j-1] | x);
+//   kFusedSample  rows (chain c, layer j) built from P (j == k) or Pn (j > k)
+//                 -> s'_j drawn from q into Pn[c][j-1], lqf[c] += log q(s'_j | x).
+enum : int { kFusedLogits = 0, kFusedLogQ = 1, kFusedSample = 2 };
+
 struct FusedArgs {
-  const __nv_bfloat16* X;  // [rows x kin]
+  const __nv_bfloat16* X;  // [rows x kin] (kFusedLogits)
   const __nv_bfloat16 *W1, *W2, *W3;
   const float *b1, *b2, *b3;
-  float* logits;  // [rows x npad]
+  float* logits;  // [rows x npad] (kFusedLogits)
   int rows, kin, H, npad;
   uint32_t* status;
+  // per-chain modes
+  const uint32_t* P;
+  uint32_t* Pn;
+  float* lq;
+  float* lqf;
+  const uint32_t* move_dev;
+  uint32_t beta, k0, k1, group0;
+  int n, d, k, j, jlast;  // kFusedSample: layers j .. jlast, one after the other
 };
 
 constexpr size_t kFusedSmem = 24 * 1024 + 64 * 1024 + 64 * 1024;  // x, h, two weight buffers
 
 // Rows [r0, r0+nrows) x K of a row-major bf16 matrix into the canonical
 // K-major layout at `dst` (8-row groups SBO = K * 16 bytes apart).
+// The copies are asynchronous (cp.async, zero-filled past rmax); the caller
+// waits with tc::cp_async_wait_all() before the data is used.
 __device__ __forceinline__ void stage_rows(uint8_t* dst, const __nv_bfloat16* src, int ld, int r0,
                                            int nrows, int rmax, int k0, int K, int tid, int nthr) {
   const int vecs = K / 8;
   for (int v = tid; v < nrows * vecs; v += nthr) {
     const int r = v / vecs, c = v % vecs, row = r0 + r;
-    uint4 val = make_uint4(0u, 0u, 0u, 0u);
-    if (row < rmax) val = *reinterpret_cast<const uint4*>(src + (size_t)row * ld + k0 + c * 8);
-    *reinterpret_cast<uint4*>(dst + (r >> 3) * (K * 16) + c * 128 + (r & 7) * 16) = val;
+    const bool in = row < rmax;
+    tc::cp_async16(dst + (r >> 3) * (K * 16) + c * 128 + (r & 7) * 16,
+                   in ? (const void*)(src + (size_t)row * ld + k0 + c * 8) : (const void*)src,
+                   in ? 16u : 0u);
   }
 }
 
-__global__ void __launch_bounds__(128) mlp_fused_fwd_kernel(FusedArgs a) {
+// Row x = [2 prev - 1 (n), onehot(j-1) (d), 0...] of this thread into the
+// canonical layout of the x tile (row r of 128, SBO = kin * 16).
+__device__ __forceinline__ void build_x_row(uint8_t* sX, int kin, int n, int r, uint32_t prev, int j) {
+  const __nv_bfloat16 one = __float2bfloat16(1.f), mone = __float2bfloat16(-1.f),
+                      zero = __float2bfloat16(0.f);
+  uint8_t* base = sX + (r >> 3) * (kin * 16) + (r & 7) * 16;
+  for (int c = 0; c < kin / 8; ++c) {
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = c * 8 + t;
+      v[t] = i < n ? (((prev >> i) & 1u) ? one : mone) : (i == n + j - 1 ? one : zero);
+    }
+    *reinterpret_cast<uint4*>(base + c * 128) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   // one mbarrier per weight buffer: each has at most one commit in flight
   __shared__ uint64_t mbar[2];
@@ -667,13 +704,7 @@ __global__ void __launch_bounds__(128) mlp_fused_fwd_kernel(FusedArgs a) {
     tc::mbar_init(&mbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // x tile and W1
-  stage_rows(sX, a.X, kin, r0, 128, a.rows, 0, kin, tid, 128);
-  stage_rows(sWb[0], a.W1, kin, 0, H, H, 0, kin, tid, 128);
-  tc::fence_proxy_async_smem();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
+  __syncthreads();  // TMEM address and barrier initialisation visible
   const uint32_t tb = tmem_base;
   uint32_t ph[2] = {0u, 0u};
   bool ok = true;
@@ -684,6 +715,28 @@ __global__ void __launch_bounds__(128) mlp_fused_fwd_kernel(FusedArgs a) {
   };
   const uint32_t taddr_row = tb + ((uint32_t)(warp * 32) << 16);
   const int row = r0 + warp * 32 + lane;
+  const int jfirst = MODE == kFusedLogQ ? a.k + (int)blockIdx.y : a.j;
+  const int jend = MODE == kFusedSample ? a.jlast : jfirst;
+  for (int jl = jfirst; jl <= jend && ok; ++jl) {
+  // x tile and W1
+  // (per-chain modes: row = chain r0 + r, layer j)
+  if (MODE == kFusedLogits) {
+    stage_rows(sX, a.X, kin, r0, 128, a.rows, 0, kin, tid, 128);
+  } else {
+    const int c = r0 + tid;
+    uint32_t prev = a.beta;
+    if (c < a.rows && jl > 1) {
+      const uint32_t* src = (MODE == kFusedSample && jl > a.k) ? a.Pn : a.P;
+      prev = src[(size_t)c * a.d + (jl - 2)];
+    }
+    build_x_row(sX, kin, a.n, tid, prev, jl);
+  }
+  stage_rows(sWb[0], a.W1, kin, 0, H, H, 0, kin, tid, 128);
+  tc::cp_async_wait_all();
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
 
   // ---- layer 1: D = x W1^T   (commit on mbar[0])
   if (tid == 0) {
@@ -721,6 +774,7 @@ __global__ void __launch_bounds__(128) mlp_fused_fwd_kernel(FusedArgs a) {
   if (ok) stage_rows(sWb[0], a.W2, H, 0, H, H, 0, chunk_k(0), tid, 128);
   for (int c = 0; c < nchunks && ok; ++c) {
     const int b = c & 1;
+    tc::cp_async_wait_all();
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -746,6 +800,7 @@ __global__ void __launch_bounds__(128) mlp_fused_fwd_kernel(FusedArgs a) {
     epilogue_to_h(a.b2);
     // ---- layer 3: D = h W3^T  (buffer 0 and mbar[0] are free)
     stage_rows(sWb[0], a.W3, H, 0, a.npad, a.npad, 0, H, tid, 128);
+    tc::cp_async_wait_all();
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -762,14 +817,54 @@ __global__ void __launch_bounds__(128) mlp_fused_fwd_kernel(FusedArgs a) {
   }
   if (ok) {
     tc::fence_after_sync();
+    // logits of this thread's row (npad <= 32)
+    float l[32];
     for (int c0 = 0; c0 < a.npad; c0 += 16) {
       float v[16];
       tc::tmem_ld16(taddr_row + (uint32_t)c0, v);
-      if (row < a.rows) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) a.logits[(size_t)row * a.npad + c0 + i] = v[i] + a.b3[c0 + i];
+      for (int i = 0; i < 16; ++i) l[c0 + i] = v[i] + a.b3[c0 + i];
+    }
+    if (row < a.rows) {
+      if (MODE == kFusedLogits) {
+        for (int i = 0; i < a.npad; ++i) a.logits[(size_t)row * a.npad + i] = l[i];
+      } else if (MODE == kFusedLogQ) {
+        // log q of the current layer word: sum_q log sigma(+-l_q)
+        const uint32_t bits = a.P[(size_t)row * a.d + (jl - 1)];
+        float sq = 0.f;
+        for (int q = 0; q < a.n; ++q) {
+          const float z = ((bits >> q) & 1u) ? -l[q] : l[q];
+          sq -= fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z)));
+        }
+        a.lq[(size_t)row * a.d + (jl - 1)] = sq;
+      } else {
+        // draw s'_j bit by bit: u < sigmoid(l_q), u from Philox (chain,
+        // move, (j-1) | tag 2 << 16, q/4)
+        const uint32_t move = *a.move_dev;
+        const uint32_t gc = a.group0 * 32u + (uint32_t)row;
+        uint32_t word = 0u;
+        float sq = 0.f;
+        uint4 u4 = make_uint4(0u, 0u, 0u, 0u);
+        for (int q = 0; q < a.n; ++q) {
+          if ((q & 3) == 0)
+            u4 = philox4x32_10(make_uint4(gc, move, (uint32_t)(jl - 1) | (kTagMH << 16),
+                                          (uint32_t)(q >> 2)), a.k0, a.k1);
+          const uint32_t u = (q & 3) == 0 ? u4.x : (q & 3) == 1 ? u4.y : (q & 3) == 2 ? u4.z : u4.w;
+          const float p1 = 1.f / (1.f + __expf(-l[q]));
+          const float uf = ((float)(u >> 8) + 0.5f) * (1.f / 16777216.f);
+          const uint32_t b = uf < p1 ? 1u : 0u;
+          word |= b << q;
+          const float z = b ? -l[q] : l[q];
+          sq -= fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z)));
+        }
+        a.Pn[(size_t)row * a.d + (jl - 1)] = word;
+        a.lqf[row] += sq;
       }
     }
+  }
+  }  // layers
+  if (ok) {
+    // nothing left
   } else {
     if (a.status) atomicCAS(a.status, 0u, (uint32_t)PB_ETIMEOUT);
     // let MMAs in flight drain (bounded) before the accumulator is freed
@@ -779,6 +874,62 @@ __global__ void __launch_bounds__(128) mlp_fused_fwd_kernel(FusedArgs a) {
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tb, 256);
+}
+
+template __global__ void mlp_fused_kernel<kFusedLogits>(FusedArgs);
+template __global__ void mlp_fused_kernel<kFusedLogQ>(FusedArgs);
+template __global__ void mlp_fused_kernel<kFusedSample>(FusedArgs);
+
+static FusedArgs fused_args(pb_mlp* p, int rows) {
+  FusedArgs a{};
+  a.jlast = 0;
+  a.W1 = p->W1;
+  a.W2 = p->W2;
+  a.W3 = p->W3;
+  a.b1 = p->w + p->off_b1;
+  a.b2 = p->w + p->off_b2;
+  a.b3 = p->w + p->off_b3;
+  a.rows = rows;
+  a.kin = p->kin;
+  a.H = p->H;
+  a.npad = p->npad;
+  a.n = p->n;
+  a.d = p->d;
+  return a;
+}
+
+// log q of the current suffix layers k..d of all chains (one launch).
+cudaError_t mlp_fused_logq(pb_mlp* p, const uint32_t* P, uint32_t beta, int chains, int k, float* lq,
+                           cudaStream_t st) {
+  FusedArgs a = fused_args(p, chains);
+  a.P = P;
+  a.beta = beta;
+  a.k = k;
+  a.lq = lq;
+  dim3 grid((chains + 127) / 128, p->d - k + 1);
+  mlp_fused_kernel<kFusedLogQ><<<grid, 128, kFusedSmem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Layers j .. jlast of the proposal for all chains (one launch; each CTA
+// carries its 128 chains through the layers in turn).
+cudaError_t mlp_fused_sample(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uint32_t beta, int chains,
+                             int k, int j, int jlast, float* lqf, uint32_t k0, uint32_t k1,
+                             const uint32_t* move_dev, uint32_t group0, cudaStream_t st) {
+  FusedArgs a = fused_args(p, chains);
+  a.P = P;
+  a.Pn = Pn;
+  a.beta = beta;
+  a.k = k;
+  a.j = j;
+  a.jlast = jlast;
+  a.lqf = lqf;
+  a.k0 = k0;
+  a.k1 = k1;
+  a.move_dev = move_dev;
+  a.group0 = group0;
+  mlp_fused_kernel<kFusedSample><<<(chains + 127) / 128, 128, kFusedSmem, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t mlp_forward_fused(pb_mlp* p, int rows) {
@@ -796,13 +947,20 @@ cudaError_t mlp_forward_fused(pb_mlp* p, int rows) {
   a.H = p->H;
   a.npad = p->npad;
   a.status = nullptr;
-  mlp_fused_fwd_kernel<<<(rows + 127) / 128, 128, kFusedSmem, p->st>>>(a);
+  mlp_fused_kernel<kFusedLogits><<<(rows + 127) / 128, 128, kFusedSmem, p->st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t mlp_fused_prepare() {
-  return cudaFuncSetAttribute(mlp_fused_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kFusedSmem);
+  cudaError_t e = cudaFuncSetAttribute(mlp_fused_kernel<kFusedLogits>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_fused_kernel<kFusedLogQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFusedSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_fused_kernel<kFusedSample>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+  return e;
 }
 
 }  // namespace pb

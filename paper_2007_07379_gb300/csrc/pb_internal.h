@@ -129,6 +129,11 @@ cudaError_t mlp_backward_rows(pb_mlp* p, int rows);
 cudaError_t mlp_adam_step(pb_mlp* p, float lr);
 cudaError_t mlp_prepare();
 cudaError_t mlp_forward_fused(pb_mlp* p, int rows);
+cudaError_t mlp_fused_logq(pb_mlp* p, const uint32_t* P, uint32_t beta, int chains, int k, float* lq,
+                           cudaStream_t st);
+cudaError_t mlp_fused_sample(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uint32_t beta, int chains,
+                             int k, int j, int jlast, float* lqf, uint32_t k0, uint32_t k1,
+                             const uint32_t* move_dev, uint32_t group0, cudaStream_t st);
 
 // What the learned-proposal code needs to know about one model of a run.
 struct RunView {
