@@ -222,3 +222,28 @@ def test_mid_workload_sampled_parity():
     # stationary valid fraction (1 + e^{-J})^{-M} is reached from a valid start
     p = (1 + np.exp(-wl.J)) ** (-m.info()["M"])
     assert 0.3 * p < valid / samples <= 1.0
+
+
+def test_sharded_runs_sum_to_the_single_run():
+    """Rank-style sharding on one GPU: the chain ranges of two ranks (global
+    group offsets) run separately; their integer histograms add up to the
+    single run of all chains bit for bit."""
+    from paper_2007_07379_gb300 import dist as D
+    n, d, chains = 6, 9, 200
+    g = W.random_circuit(n, d, 8)
+    _, full = _gpu_run(n, d, g, 3.0, 33, chains, sweeps=(20,))
+    want = full.histogram()
+    tot_cnt, tot_valid, tot_samples = 0, 0, 0
+    states = []
+    for rank in range(2):
+        c, g0 = D.shard(chains, rank, 2)
+        m = pbits.Model(n, d, g, 3.0)
+        r = pbits.Run([m], [pbits.RunCfg(seed=33, chains=c, group0=g0)])
+        r.sweeps(20)
+        cnt, valid, samples = r.histogram()
+        tot_cnt = tot_cnt + cnt
+        tot_valid += valid
+        tot_samples += samples
+        states.append(pbits.unslice_state(r.get_state(), c))
+    assert np.array_equal(tot_cnt, want[0]) and tot_valid == want[1] and tot_samples == want[2]
+    assert np.array_equal(np.concatenate(states), pbits.unslice_state(full.get_state(), chains))
