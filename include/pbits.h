@@ -180,6 +180,22 @@ typedef struct {
 } pb_run_stats_t;
 PB_API int pb_run_stats(pb_run* run, pb_run_stats_t* stats);
 
+/* CTA shape of the sweep launches: consumer threads (redraw one colour
+ * class, 32..224), producer threads (Philox planes of the next class,
+ * 32..352), both multiples of 32, plus one recorder warp; blocks_per_sm
+ * caps the persistent grid of batched runs (0 = as many as fit).  The
+ * results do not depend on the shape. */
+PB_API int pb_run_set_shape(pb_run* run, int consumers, int producers, int blocks_per_sm);
+PB_API int pb_run_get_shape(const pb_run* run, int* consumers, int* producers, int* blocks_per_sm,
+                            int* grid);
+/* Autotuner: times trial_sweeps sweeps of each candidate shape on the run
+ * itself (the run's state, counters and sweep index are restored after
+ * every trial, so the run is unchanged) and keeps the fastest.  cache_path
+ * (may be NULL): a text file of earlier results keyed by the run's (n, d,
+ * chains) list; a hit applies the cached shape without trials.  *best_ms
+ * (may be NULL) receives the time of trial_sweeps sweeps with that shape. */
+PB_API int pb_run_tune(pb_run* run, uint32_t trial_sweeps, const char* cache_path, double* best_ms);
+
 /* Checkpoint: chain words, counters and the sweep index of every model.
  * bytes_needed is written when host_buf is NULL.  Restore puts them back;
  * since the draws are counter-based the resumed run is bit-identical to an

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -354,7 +355,7 @@ struct pb_run {
   std::vector<RunModelDev> rm;
   uint32_t total_groups = 0;
   int threads = 32;
-  int cons = 32, prod = 32, max_col = 1;
+  int cons = 32, prod = 32, max_col = 1, blocks_per_sm = 0;
   size_t smem = 0;
   bool persistent = false;
   int grid = 0;
@@ -379,21 +380,12 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? PB_OK : PB_ECUDA; }
 // Philox calls per p-bit of that class, capped at 352; plus one recorder
 // warp.  Environment overrides PB_CONS, PB_PROD (multiples of 32).
 // Persistent scheduling for batched runs.
-void choose_shape(pb_run* r) {
+// Applies a CTA shape (consumer and producer threads, multiples of 32) to
+// the run: shared-memory size, histogram placement and the persistent grid.
+void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
   int maxcol = 1;
   for (auto& m : r->models)
     for (int c = 0; c < 4; ++c) maxcol = std::max(maxcol, m->col_off[c + 1] - m->col_off[c]);
-  auto up32 = [](int x) { return ((x + 31) / 32) * 32; };
-  int cons = std::max(32, std::min(224, up32(maxcol)));
-  int prod = std::max(32, std::min(352, up32(3 * maxcol)));
-  if (const char* e = std::getenv("PB_CONS")) {
-    int v = std::atoi(e);
-    if (v >= 32 && v <= 224 && v % 32 == 0) cons = v;
-  }
-  if (const char* e = std::getenv("PB_PROD")) {
-    int v = std::atoi(e);
-    if (v >= 32 && v <= 352 && v % 32 == 0) prod = v;
-  }
   r->cons = cons;
   r->prod = prod;
   r->max_col = maxcol;
@@ -415,14 +407,39 @@ void choose_shape(pb_run* r) {
   r->smem = smem;
   r->persistent = r->nm > 1;
   if (const char* e = std::getenv("PB_PERSISTENT")) r->persistent = std::atoi(e) != 0;
+  r->grid = 0;
   if (r->persistent) {
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = sweep_max_blocks_per_sm(r->threads, smem);
+    if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
     r->grid = std::max(1, sms * std::max(1, per_sm));
     r->grid = (int)std::min<uint32_t>((uint32_t)r->grid, r->total_groups);
   }
+  r->blocks_per_sm = blocks_per_sm;
+}
+
+// Default launch shape: consumers = the largest colour class rounded up to
+// a warp (one p-bit per consumer per class), capped at 224; producers = 3
+// Philox calls per p-bit of that class, capped at 352; plus one recorder
+// warp.  Environment overrides PB_CONS, PB_PROD (multiples of 32).
+void choose_shape(pb_run* r) {
+  int maxcol = 1;
+  for (auto& m : r->models)
+    for (int c = 0; c < 4; ++c) maxcol = std::max(maxcol, m->col_off[c + 1] - m->col_off[c]);
+  auto up32 = [](int x) { return ((x + 31) / 32) * 32; };
+  int cons = std::max(32, std::min(224, up32(maxcol)));
+  int prod = std::max(32, std::min(352, up32(3 * maxcol)));
+  if (const char* e = std::getenv("PB_CONS")) {
+    int v = std::atoi(e);
+    if (v >= 32 && v <= 224 && v % 32 == 0) cons = v;
+  }
+  if (const char* e = std::getenv("PB_PROD")) {
+    int v = std::atoi(e);
+    if (v >= 32 && v <= 352 && v % 32 == 0) prod = v;
+  }
+  apply_shape(r, cons, prod, 0);
 }
 
 }  // namespace
@@ -680,6 +697,104 @@ PB_API int pb_run_set_state(pb_run* r, int model, const uint32_t* words, size_t 
   if (bytes < need) return PB_ERANGE;
   if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
   return cuda_status(cudaMemcpy(r->ws + s.state, words, need, cudaMemcpyHostToDevice));
+}
+
+// Sets the CTA shape of a run (cached graphs are rebuilt on the next call).
+PB_API int pb_run_set_shape(pb_run* r, int consumers, int producers, int blocks_per_sm) {
+  if (!r) return PB_EINVAL;
+  if (consumers < 32 || consumers > 224 || consumers % 32) return PB_EINVAL;
+  if (producers < 32 || producers > 352 || producers % 32) return PB_EINVAL;
+  if (blocks_per_sm < 0) return PB_EINVAL;
+  if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
+  apply_shape(r, consumers, producers, blocks_per_sm);
+  for (auto& kv : r->graphs) cudaGraphExecDestroy(kv.second);
+  r->graphs.clear();
+  if (cudaMemcpy(r->ws + r->L.rm, r->rm.data(), sizeof(RunModelDev) * r->nm, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return PB_ECUDA;
+  return PB_OK;
+}
+
+PB_API int pb_run_get_shape(const pb_run* r, int* consumers, int* producers, int* blocks_per_sm,
+                            int* grid) {
+  if (!r) return PB_EINVAL;
+  if (consumers) *consumers = r->cons;
+  if (producers) *producers = r->prod;
+  if (blocks_per_sm) *blocks_per_sm = r->blocks_per_sm;
+  if (grid) *grid = r->grid;
+  return PB_OK;
+}
+
+// Autotuner: times `trial_sweeps` sweeps for each candidate CTA shape on the
+// run itself, restoring the run's state after every trial, and keeps the
+// fastest.  With cache_path, a previous result for the same set of (n, d,
+// chains) is reused without trials and new results are appended.
+PB_API int pb_run_tune(pb_run* r, uint32_t trial_sweeps, const char* cache_path, double* best_ms) {
+  if (!r || trial_sweeps == 0) return PB_EINVAL;
+  // key: the run's shapes
+  uint64_t key = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
+  for (int i = 0; i < r->nm; ++i) {
+    mix((uint64_t)r->models[i]->n);
+    mix((uint64_t)r->models[i]->d);
+    mix((uint64_t)r->cfgs[i].chains);
+  }
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      unsigned long long k;
+      int c, p, b;
+      double ms;
+      int found = 0, bc = 0, bp = 0, bb = 0;
+      double bms = 0;
+      while (std::fscanf(f, "%llx %d %d %d %lf", &k, &c, &p, &b, &ms) == 5)
+        if (k == key) { found = 1; bc = c; bp = p; bb = b; bms = ms; }
+      std::fclose(f);
+      if (found) {
+        if (best_ms) *best_ms = bms;
+        return pb_run_set_shape(r, bc, bp, bb);
+      }
+    }
+  }
+  size_t need = 0;
+  int rc = pb_run_checkpoint(r, nullptr, 0, &need);
+  if (rc != PB_OK) return rc;
+  std::vector<char> blob(need);
+  if ((rc = pb_run_checkpoint(r, blob.data(), need, &need)) != PB_OK) return rc;
+  const uint64_t sweeps_before = r->sweeps_done;
+  int maxcol = 1;
+  for (auto& m : r->models)
+    for (int c = 0; c < 4; ++c) maxcol = std::max(maxcol, m->col_off[c + 1] - m->col_off[c]);
+  const int up = ((maxcol + 31) / 32) * 32;
+  std::vector<int> cons_c, prod_c, bpsm_c = {0};
+  for (int c : {64, 128, 224})
+    if (c <= std::max(64, up)) cons_c.push_back(c);
+  for (int p : {96, 192, 352})
+    if (p <= std::max(96, ((3 * maxcol + 31) / 32) * 32)) prod_c.push_back(p);
+  if (r->nm > 1) bpsm_c = {1, 2, 0};
+  double best = 1e30;
+  int bc = r->cons, bp = r->prod, bb = r->blocks_per_sm;
+  for (int c : cons_c)
+    for (int p : prod_c)
+      for (int b : bpsm_c) {
+        if ((rc = pb_run_set_shape(r, c, p, b)) != PB_OK) return rc;
+        // first launch builds the graph; time the second
+        if ((rc = pb_run_sweeps(r, trial_sweeps)) != PB_OK) return rc;
+        if ((rc = pb_run_sweeps(r, trial_sweeps)) != PB_OK) return rc;
+        pb_run_stats_t st;
+        if ((rc = pb_run_stats(r, &st)) != PB_OK) return rc;
+        if (st.last_ms < best) { best = st.last_ms; bc = c; bp = p; bb = b; }
+        if ((rc = pb_run_restore(r, blob.data(), blob.size())) != PB_OK) return rc;
+        r->sweeps_done = sweeps_before;
+      }
+  if ((rc = pb_run_set_shape(r, bc, bp, bb)) != PB_OK) return rc;
+  if (best_ms) *best_ms = best;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "%llx %d %d %d %.6f\n", (unsigned long long)key, bc, bp, bb, best);
+      std::fclose(f);
+    }
+  }
+  return PB_OK;
 }
 
 PB_API int pb_run_stats(pb_run* r, pb_run_stats_t* st) {

@@ -77,6 +77,10 @@ _SIGS = {
     "pb_run_checkpoint": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "pb_run_restore": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "pb_run_free": (None, [_VP]),
+    "pb_run_set_shape": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "pb_run_get_shape": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "pb_run_tune": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]),
     "pb_philox_fill": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _VP,
                                       ctypes.c_void_p]),
     "pb_gibbs_run_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(pb_run_cfg), ctypes.c_uint32, _VP, _VP,
@@ -303,6 +307,21 @@ class Run:
         _check(load().pb_run_stats(self._h, ctypes.byref(st)), "pb_run_stats")
         return {"sweeps_done": st.sweeps_done, "flips": st.flips, "last_ms": st.last_ms,
                 "flips_per_s": st.flips_per_s}
+
+    def set_shape(self, consumers: int, producers: int, blocks_per_sm: int = 0):
+        _check(load().pb_run_set_shape(self._h, consumers, producers, blocks_per_sm), "pb_run_set_shape")
+
+    def shape(self) -> dict:
+        v = [ctypes.c_int(0) for _ in range(4)]
+        _check(load().pb_run_get_shape(self._h, *[ctypes.byref(x) for x in v]), "pb_run_get_shape")
+        return {"consumers": v[0].value, "producers": v[1].value, "blocks_per_sm": v[2].value,
+                "grid": v[3].value}
+
+    def tune(self, trial_sweeps: int = 200, cache_path: str | None = None) -> float:
+        ms = ctypes.c_double(0)
+        _check(load().pb_run_tune(self._h, trial_sweeps, cache_path.encode() if cache_path else None,
+                                  ctypes.byref(ms)), "pb_run_tune")
+        return ms.value
 
     def checkpoint(self) -> bytes:
         lib = load()
