@@ -204,6 +204,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--learned-seconds", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -300,6 +301,11 @@ def main():
     if not args.no_e2e:
         e2e = measure_e2e(wl, rank, groups, S, dev, stream, world)
 
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra["batched"] = batched_measurement(dev, stream)
+        extra["large"] = large_measurement(dev, stream)
+
     learned = None
     if rank == 0 and not args.no_learned:
         learned = [learned_comparison(dev, stream, seconds=args.learned_seconds, wl=w)
@@ -319,6 +325,7 @@ def main():
             "gpu_launches": 3 * args.steps, "roofline": roofline, "cpu_baseline": cpu,
             "samples_per_s": world * wl.chains * S * args.steps / total_s,
             "learned_vs_plain": learned,
+            "other_workloads": extra,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -399,6 +406,60 @@ def learned_comparison(dev, stream, seconds: float = 8.0, train_paths: int = 1_0
         out["learned"] = timed(True)
         out["ratio_plain_over_learned"] = out["plain"]["t_to_eps_s"] / out["learned"]["t_to_eps_s"]
     return out
+
+
+def batched_measurement(dev, stream, sweeps: int = 10_000):
+    """The batched workload: 256 random circuits (n in [6,20], d in [8,40],
+    chains max(256, 2^ceil(n/2))), 1e4 sweeps each, in one persistent,
+    graph-captured launch with an autotuned CTA shape."""
+    import torch
+    from paper_2007_07379_gb300 import pbits
+    wls = W.batched()
+    with torch.cuda.stream(stream):
+        models = [pbits.Model(w.n, w.d, w.gates, w.J) for w in wls]
+        cfgs = [pbits.RunCfg(seed=w.seed, chains=w.chains) for w in wls]
+        run = pbits.Run(models, cfgs, stream=stream)
+        t0 = time.perf_counter()
+        run.tune(trial_sweeps=50)
+        t_tune = time.perf_counter() - t0
+        run.sweeps(sweeps)
+        run.wait()
+        ms = run.stats()["last_ms"]
+    flips = sum(w.chains * w.n * w.d for w in wls) * sweeps
+    return {"workload": "batched: 256 random Clifford+T circuits, n~U[6,20], d~U[8,40], "
+                        "chains max(256, 2^ceil(n/2)), 1e4 sweeps, one persistent launch",
+            "circuits": len(wls), "chains": sum(w.chains for w in wls), "sweeps": sweeps,
+            "launch_ms": ms, "flips_per_s": flips / (ms * 1e-3), "tune_s": t_tune,
+            "shape": run.shape()}
+
+
+def large_measurement(dev, stream, sweeps: int = 2000, moves: int = 20):
+    """The large workload: n=24, d=32 (792 p-bits), 65536 chains, 64 output
+    amplitudes; plain sweeps and learned suffix moves (untrained network:
+    the cost of a move does not depend on the weights)."""
+    import torch
+    from paper_2007_07379_gb300 import pbits
+    wl = W.large()
+    with torch.cuda.stream(stream):
+        m = pbits.Model(wl.n, wl.d, wl.gates, wl.J)
+        run = pbits.Run([m], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, alphas=wl.alphas)],
+                        stream=stream)
+        run.sweeps(200)
+        run.sweeps(sweeps)
+        run.wait()
+        ms = run.stats()["last_ms"]
+        net = pbits.Mlp(wl.n, wl.d, hidden=256, batch=4096, seed=3, stream=stream)
+        L = pbits.Learned(run, net)
+        L.step(2)
+        run.wait()
+        t0 = time.perf_counter()
+        L.step(moves)
+        run.wait()
+        t_move = (time.perf_counter() - t0) / moves
+    flips = wl.chains * wl.n * wl.d * sweeps
+    return {"workload": "large: random Clifford+T n=24 d=32 (792 p-bits), 65536 chains, 64 amplitudes",
+            "sweeps": sweeps, "launch_ms": ms, "flips_per_s": flips / (ms * 1e-3),
+            "ms_per_mh_move": t_move * 1e3}
 
 
 def kernel_rev() -> str:
