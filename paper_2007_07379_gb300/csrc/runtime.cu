@@ -375,11 +375,6 @@ namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PB_OK : PB_ECUDA; }
 
-// Launch shape: consumers = the largest colour class rounded up to a warp
-// (one p-bit per consumer per class), capped at 224; producers = kPre
-// Philox calls per p-bit of that class, capped at 352; plus one recorder
-// warp.  Environment overrides PB_CONS, PB_PROD (multiples of 32).
-// Persistent scheduling for batched runs.
 // Applies a CTA shape (consumer and producer threads, multiples of 32) to
 // the run: shared-memory size, histogram placement and the persistent grid.
 void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
@@ -421,9 +416,9 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
 }
 
 // Default launch shape: consumers = the largest colour class rounded up to
-// a warp (one p-bit per consumer per class), capped at 224; producers = 3
-// Philox calls per p-bit of that class, capped at 352; plus one recorder
-// warp.  Environment overrides PB_CONS, PB_PROD (multiples of 32).
+// a warp (one p-bit per consumer per class), capped at 224; producers = one
+// per Philox call of that class (kPre = 3 per p-bit), capped at 352; plus one
+// recorder warp.  Environment overrides PB_CONS, PB_PROD (multiples of 32).
 void choose_shape(pb_run* r) {
   int maxcol = 1;
   for (auto& m : r->models)

@@ -15,6 +15,8 @@
 // (Fig. 2 Step 3).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "pb_internal.h"
 #include "philox.cuh"
 
@@ -31,27 +33,6 @@ namespace pb {
 struct HbClass {
   uint32_t neg, sel, tail0, tA, tB;
 };
-
-// Link demands -> (neg, sel, thresholds).  v = sum_i (1 - 2 r_i):
-//   m=0: v=0 -> t0.  m=1: neg=r0, t1.  m=2: agree -> neg=r0, t2; else t0.
-//   m=3: neg = majority, unanimous -> t3, else t1.
-__device__ __forceinline__ HbClass classify(int m, uint32_t r0, uint32_t r1, uint32_t r2,
-                                            uint32_t thr0, uint32_t thr1, uint32_t thr2,
-                                            uint32_t thr3) {
-  HbClass k;
-  if (m == 0) {
-    k.neg = 0u; k.sel = 0u; k.tail0 = ~0u; k.tA = thr0; k.tB = thr0;
-  } else if (m == 1) {
-    k.neg = r0; k.sel = 0u; k.tail0 = 0u; k.tA = thr1; k.tB = thr1;
-  } else if (m == 2) {
-    k.neg = r0 & r1; k.sel = ~(r0 ^ r1); k.tail0 = ~k.sel; k.tA = thr2; k.tB = thr0;
-  } else {
-    k.neg = (r0 & r1) | (r0 & r2) | (r1 & r2);
-    k.sel = ~(r0 ^ r1) & ~(r1 ^ r2);
-    k.tail0 = 0u; k.tA = thr3; k.tB = thr1;
-  }
-  return k;
-}
 
 // Four planes (one Philox output) of the comparison, planes 4 grp .. 4 grp+3.
 __device__ __forceinline__ void compare4(uint32_t& lt, uint32_t& eq, const HbClass& k, uint4 r,
@@ -82,17 +63,96 @@ __device__ __forceinline__ void compare_tail(uint32_t& lt, uint32_t& eq, const H
     compare4(lt, eq, k, philox_cold(make_uint4(g, sweep, p, grp), k0, k1), grp);
 }
 
-__device__ __forceinline__ uint32_t heat_bath_word(const HbClass& k, uint32_t g, uint32_t sweep,
-                                                   uint32_t p, uint32_t k0, uint32_t k1) {
-  uint32_t lt = 0u, eq = ~0u;
-  compare4(lt, eq, k, philox_cold(make_uint4(g, sweep, p, 0u), k0, k1), 0u);
-  eq &= ~k.tail0;
-  compare_tail(lt, eq, k, 1u, g, sweep, p, k0, k1);
-  return k.neg ^ lt;
-}
-
 // Number of Philox calls computed ahead of a colour class (12 planes).
 constexpr int kPre = 3;
+
+// Threshold pair of a p-bit with m links: tA for the lanes in `sel` (all
+// links agree), tB for the others (see the consumer table set-up).
+__device__ __forceinline__ uint32_t thr_a(int m, uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3) {
+  return m == 0 ? t0 : (m == 1 ? t1 : (m == 2 ? t2 : t3));
+}
+__device__ __forceinline__ uint32_t thr_b(int m, uint32_t t0, uint32_t t1) {
+  return (m == 0 || m == 2) ? t0 : t1;
+}
+
+// Comparison of the precomputed planes for any thresholds (small J), and
+// the planes beyond them; out of line: taken rarely.
+__device__ __noinline__ uint32_t heat_bath_general(const HbClass k, uint4 R0, uint4 R1, uint4 R2,
+                                                   uint32_t lt, uint32_t eq, bool pre, uint32_t g,
+                                                   uint32_t sweep, uint32_t pidx, uint32_t k0,
+                                                   uint32_t k1) {
+  static_assert(kPre == 3, "heat_bath_general takes three Philox outputs");
+  if (pre) {
+    lt = 0u;
+    eq = ~0u;
+    compare4(lt, eq, k, R0, 0u);
+    eq &= ~k.tail0;
+    compare4(lt, eq, k, R1, 1u);
+    compare4(lt, eq, k, R2, 2u);
+  }
+  compare_tail(lt, eq, k, (uint32_t)kPre, g, sweep, pidx, k0, k1);
+  return lt;
+}
+
+// Thresholds for which the consumers take the short comparison below:
+// thr1 < 2^24 and thr2 < 2^20 (thr3 <= thr2), i.e. on the 4 kPre = 12
+// precomputed planes every threshold bit is 0 except the top bit of
+// t0 = 2^31 and bits 23..20 of thr1 (planes 8..11).
+struct FastThr {
+  bool on;
+  uint32_t U[4];  // ~0 where thr1 has a one bit on plane 8 + w, else 0
+};
+__device__ __forceinline__ FastThr fast_thresholds(uint32_t thr1, uint32_t thr2) {
+  static_assert(kPre == 3, "the short comparison assumes 12 precomputed planes");
+  FastThr f;
+  f.on = thr1 < (1u << 24) && thr2 < (1u << 20);
+#pragma unroll
+  for (int w = 0; w < 4; ++w) f.U[w] = ((thr1 >> (23 - w)) & 1u) ? ~0u : 0u;
+  return f;
+}
+
+// New value of the 32 chains of one p-bit (Fig. 2 Steps 1-2) from its link
+// demands r0..r2 (three-link form: m=0: 0,0,0  m=1: r0,r0,0  m=2: r0,r1,0
+// m=3: r0,r1,r2), its masks Mk = [m == k] and its kPre precomputed Philox
+// outputs R.  Short form (F.on): plane 0 decides the t0 lanes (u < 2^31 iff
+// its top bit is 0); on planes 1..7 every other threshold bit is 0, so a
+// lane stays equal only while it draws zeros; on planes 8..11 the lanes
+// compared with thr1 (L1) meet thr1's bits and the thr2 / thr3 lanes zeros.
+// Lanes still equal after the precomputed planes, and every lane when the
+// thresholds do not have that form, go to heat_bath_general.
+__device__ __forceinline__ uint32_t heat_bath_links(uint32_t r0, uint32_t r1, uint32_t r2, int m,
+                                                    uint32_t M0, uint32_t M1, uint32_t M2,
+                                                    uint32_t M3, const uint4 (&R)[kPre],
+                                                    const FastThr& F, uint32_t thr0,
+                                                    uint32_t thr1, uint32_t thr2, uint32_t thr3,
+                                                    uint32_t g, uint32_t sweep, uint32_t pidx,
+                                                    uint32_t k0, uint32_t k1) {
+  HbClass k;
+  k.neg = (r0 & r1) | (r2 & (r0 | r1));
+  k.sel = ~(r0 ^ r1) & (~(r1 ^ r2) | M2);
+  k.tail0 = M0 | (M2 & ~k.sel);
+  uint32_t lt = 0u, eq = ~0u;
+  bool general = !F.on;
+  if (F.on) {
+    const uint32_t L1 = M1 | (M3 & ~k.sel);  // lanes compared with thr1
+    lt = k.tail0 & ~R[0].x;
+    eq = ~k.tail0 & ~(R[0].x | R[0].y | R[0].z | R[0].w | R[1].x | R[1].y | R[1].z | R[1].w);
+    const uint32_t P[4] = {R[2].x, R[2].y, R[2].z, R[2].w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const uint32_t A = L1 & F.U[w];
+      lt |= eq & ~P[w] & A;
+      eq &= ~(P[w] ^ A);
+    }
+    general = eq != 0u;
+  }
+  if (general) {
+    k.tA = thr_a(m, thr0, thr1, thr2, thr3);
+    k.tB = thr_b(m, thr0, thr1);
+    lt = heat_bath_general(k, R[0], R[1], R[2], lt, eq, !F.on, g, sweep, pidx, k0, k1);
+  }
+  return k.neg ^ lt;
+}
 
 __device__ __forceinline__ void add3(uint32_t& f0, uint32_t& f1, uint32_t& f2, uint32_t x0,
                                      uint32_t x1, uint32_t x2) {
@@ -118,24 +178,27 @@ __device__ __forceinline__ void set_status(WsHeader* hdr, int code) {
 }
 
 // CTA roles: `cons` consumer threads redraw the p-bits of the current colour
-// class; `prod` producer threads compute the Philox planes of the next class
+// class; `prod` producer threads compute the Philox planes of the next class,
+// compared group by group with each p-bit's two thresholds,
 // into shared memory; one recorder warp (the last) records the previous sweep.
 struct Shape {
   int cons, prod;
 };
 
-// Consumer view of one p-bit of a class: the descriptor in branch-free form
-// and its threshold pair.  flags: bit 0 m == 2, bit 1 m == 0.
+// Consumer view of one p-bit of a colour class: byte offsets within the
+// group image of the three link pairs and of the p-bit's own word, the link
+// count m (the table set-up below gives every m the three-link form) and
+// the masks Mk = (m == k ? ~0 : 0).
 struct ClassEnt {
-  Desc D;
-  uint32_t tA, tB, flags, pidx;
+  uint32_t la[3], lb[3], dst, m;
+  uint32_t M0, M1, M2, M3;
 };
-static_assert(sizeof(ClassEnt) == 32, "ClassEnt must be 32 bytes");
+static_assert(sizeof(ClassEnt) == 48, "ClassEnt must be 48 bytes");
 
 // Shared-memory image of one group: words (image_words) and two snapshots,
 // descriptors, record terms, an optional histogram of hist_bins x 8 u32
-// counters, the consumers' class table and two plane buffers of
-// kPre x max_col Philox outputs.  The image holds the (d+1) n layer words,
+// counters, the consumers' class table and two buffers of kPre x max_col
+// group comparisons (one per Philox output).  The image holds the (d+1) n layer words,
 // ZERO, ONES and one scratch word (the store target of consumers without a
 // p-bit in a colour class), rounded up to 16 bytes.
 __host__ __device__ inline int image_words(int n, int d) { return (n_words(n, d) + 1 + 3) & ~3; }
@@ -229,6 +292,34 @@ struct Recorder {
   }
 };
 
+// p-bits lo + first, lo + first + stride, ... < hi of a colour class from
+// their descriptors (a class larger than the consumers; out of line: rare).
+__device__ __noinline__ void redraw_extra(uint32_t* W, uint32_t* S, const Desc* sdesc,
+                                          const uint4* cur, int lo, int first, int hi, int stride,
+                                          int n, FastThr fast, uint32_t thr0, uint32_t thr1,
+                                          uint32_t thr2, uint32_t thr3, uint32_t g, uint32_t sweep,
+                                          uint32_t k0, uint32_t k1) {
+  for (int i = lo + first; i < hi; i += stride) {
+    Desc D = sdesc[i];
+    if (D.mflag & 0x80) continue;
+    const int m = D.mflag & 3;
+    if (m == 1) { D.a[1] = D.a[0]; D.b[1] = D.b[0]; }
+    const uint4* rp = cur + (i - lo) * kPre;
+    uint4 R[kPre];
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) R[j] = rp[j];
+    const uint32_t r0 = W[D.a[0]] ^ W[D.b[0]];
+    const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
+    const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
+    const uint32_t pidx = (uint32_t)(D.dst - n) | (kTagSweep << 16);
+    const uint32_t v = heat_bath_links(r0, r1, r2, m, m == 0 ? ~0u : 0u, m == 1 ? ~0u : 0u,
+                                       m == 2 ? ~0u : 0u, m == 3 ? ~0u : 0u, R, fast, thr0, thr1,
+                                       thr2, thr3, g, sweep, pidx, k0, k1);
+    W[D.dst] = v;
+    S[D.dst] = v;
+  }
+}
+
 // Runs `n_sweeps` sweeps (absolute indices sweep0...) of one chain group.
 __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, uint32_t n_sweeps,
                           Shape sh, int max_col_all, uint32_t* smem, WsHeader* hdr) {
@@ -297,14 +388,9 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   const uint32_t k0 = rm.seed_lo, k1 = rm.seed_hi;
   const uint32_t batch = g % rm.n_batches;
   const uint32_t gglob = g + rm.group0;
-  // planes 1 .. lz-1 carry a zero bit in every threshold below 2^31: there
-  // only `eq &= ~R` remains of the comparison (t0 lanes are decided by plane 0)
-  const int lz = __clz(thr1 | 1u);
   int col_lo[4], col_hi[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) { col_lo[c] = md.col_off[c]; col_hi[c] = md.col_off[c + 1]; }
-  auto lo_of = [&](int c) { return c == 0 ? col_lo[0] : c == 1 ? col_lo[1] : c == 2 ? col_lo[2] : col_lo[3]; };
-  auto hi_of = [&](int c) { return c == 0 ? col_hi[0] : c == 1 ? col_hi[1] : c == 2 ? col_hi[2] : col_hi[3]; };
 
   // Consumer class table (branch-free form): consumers without a p-bit get a
   // dummy with links to ZERO that stores into the scratch word; a single link
@@ -328,19 +414,21 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       const int m = D.mflag & 3;
       if (m == 1) { D.a[1] = D.a[0]; D.b[1] = D.b[0]; }
       ClassEnt E;
-      E.D = D;
-      E.tA = m == 0 ? thr0 : (m == 1 ? thr1 : (m == 2 ? thr2 : thr3));
-      E.tB = (m == 0 || m == 2) ? thr0 : thr1;
-      E.flags = (m == 2 ? 1u : 0u) | (m == 0 ? 2u : 0u);
-      E.pidx = (uint32_t)(D.dst - n) | (kTagSweep << 16);
+#pragma unroll
+      for (int l = 0; l < 3; ++l) { E.la[l] = 4u * D.a[l]; E.lb[l] = 4u * D.b[l]; }
+      E.dst = 4u * D.dst;
+      E.m = (uint32_t)m;
+      E.M0 = m == 0 ? ~0u : 0u;
+      E.M1 = m == 1 ? ~0u : 0u;
+      E.M2 = m == 2 ? ~0u : 0u;
+      E.M3 = m == 3 ? ~0u : 0u;
       sclass[c * sh.cons + tid] = E;
     }
   }
-  // Producers: the planes of step 0 (class 0 of sweep0).
-  auto produce = [&](uint32_t step, uint4* buf) {
-    const int c = (int)(step & 3u);
-    const uint32_t sw = sweep0 + (step >> 2);
-    const int lo = lo_of(c), K = hi_of(c) - lo;
+  // Producers: the Philox outputs of class C at sweep `sw` into `buf`.
+  auto produce = [&](auto cc, uint32_t sw, uint4* buf) {
+    constexpr int C = decltype(cc)::value;
+    const int lo = col_lo[C], K = col_hi[C] - lo;
 #pragma unroll 1
     for (int u = ptid; u < K * kPre; u += sh.prod) {
       const int i = u / kPre, j = u - i * kPre;
@@ -348,101 +436,90 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       buf[u] = philox4x32_10(make_uint4(gglob, sw, p, (uint32_t)j), k0, k1);
     }
   };
-  if (producer) produce(0u, planes);
+  if (producer && n_sweeps > 0u) produce(std::integral_constant<int, 0>{}, sweep0, planes);
   __syncthreads();
 
+  const FastThr fast = fast_thresholds(thr1, thr2);
   Recorder rec;
   bool bin_pending = false;
   unsigned long long n_valid = 0ull, n_samples = 0ull;  // recorder warp only
   auto recorded = [&](uint32_t t) {
     return t >= rm.burn_in && (rm.record_every == 1u || (t - rm.burn_in) % rm.record_every == 0);
   };
-  const uint32_t n_steps = 4u * n_sweeps;
-#pragma unroll 1
-  for (uint32_t t = 0; t < n_steps; ++t) {
-    const int c = (int)(t & 3u);
-    const uint32_t s = t >> 2;
+
+  // One colour class C of sweep sweep0 + s: consumers redraw it from plane
+  // buffer C & 1, producers fill the other buffer for the next class, the
+  // recorder works on the previous sweep's snapshot; then one barrier.
+  auto step = [&](auto cc, uint32_t s) {
+    constexpr int C = decltype(cc)::value;
     const uint32_t sweep = sweep0 + s;
     uint32_t* S = smem + iw * (1 + (s & 1u));
-    const uint4* cur = planes + (t & 1u) * pbuf;
+    const uint4* cur = planes + (C & 1) * pbuf;
     if (consumer) {
-      const int lo = lo_of(c), hi = hi_of(c);
-#pragma unroll 1
-      for (int i = lo + tid, e = 0; i < hi || e == 0; i += sh.cons, ++e) {
-        // the first round uses the class table; further p-bits (a class larger
-        // than the consumers) are rare and read their descriptor directly
-        ClassEnt E;
-        if (e == 0) {
-          E = sclass[c * sh.cons + tid];
-        } else {
-          E.D = sdesc[i];
-          if (E.D.mflag & 0x80) continue;
-          const int m = E.D.mflag & 3;
-          if (m == 1) { E.D.a[1] = E.D.a[0]; E.D.b[1] = E.D.b[0]; }
-          E.tA = m == 0 ? thr0 : (m == 1 ? thr1 : (m == 2 ? thr2 : thr3));
-          E.tB = (m == 0 || m == 2) ? thr0 : thr1;
-          E.flags = (m == 2 ? 1u : 0u) | (m == 0 ? 2u : 0u);
-          E.pidx = (uint32_t)(E.D.dst - n) | (kTagSweep << 16);
-        }
-        const Desc& D = E.D;
-        const uint32_t r0 = W[D.a[0]] ^ W[D.b[0]];
-        const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
-        const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
-        HbClass k;
-        k.neg = (r0 & r1) | (r2 & (r0 | r1));
-        k.sel = ~(r0 ^ r1) & (~(r1 ^ r2) | ((E.flags & 1u) ? ~0u : 0u));
-        k.tail0 = (E.flags & 2u) ? ~0u : ((E.flags & 1u) ? ~k.sel : 0u);
-        k.tA = E.tA;
-        k.tB = E.tB;
-        const int slot = i - lo;  // position in the class
+      const int lo = col_lo[C], hi = col_hi[C], K = hi - lo;
+      // the first p-bit of every consumer from its table entry; warps with no
+      // p-bit in this class skip it (their entries are dummies)
+      if (warp * 32 < K) {
+        const ClassEnt E = sclass[C * sh.cons + tid];
+        const uint4* rp = cur + (tid < K ? tid : 0) * kPre;  // dummies: any planes
         uint4 R[kPre];
-        if (slot < hi - lo) {
 #pragma unroll
-          for (int j = 0; j < kPre; ++j) R[j] = cur[slot * kPre + j];
-        } else {
-#pragma unroll
-          for (int j = 0; j < kPre; ++j) R[j] = make_uint4(~0u, ~0u, ~0u, ~0u);
-        }
-        uint32_t lt = 0u, eq = ~0u;
-        compare4(lt, eq, k, R[0], 0u);
-        eq &= ~k.tail0;
-#pragma unroll
-        for (int j = 1; j < kPre; ++j) {
-          if (4 * j + 3 < lz) {
-            eq &= ~(R[j].x | R[j].y | R[j].z | R[j].w);
-          } else {
-            compare4(lt, eq, k, R[j], (uint32_t)j);
-          }
-        }
-        if (eq != 0u) compare_tail(lt, eq, k, (uint32_t)kPre, gglob, sweep, E.pidx, k0, k1);
-        const uint32_t v = k.neg ^ lt;
-        W[D.dst] = v;
-        S[D.dst] = v;
+        for (int j = 0; j < kPre; ++j) R[j] = rp[j];
+        const char* Wb = reinterpret_cast<const char*>(W);
+        auto word = [&](uint32_t off) { return *reinterpret_cast<const uint32_t*>(Wb + off); };
+        const uint32_t r0 = word(E.la[0]) ^ word(E.lb[0]);
+        const uint32_t r1 = word(E.la[1]) ^ word(E.lb[1]);
+        const uint32_t r2 = word(E.la[2]) ^ word(E.lb[2]);
+        const uint32_t pidx = (E.dst / 4u - (uint32_t)n) | (kTagSweep << 16);
+        const uint32_t v = heat_bath_links(r0, r1, r2, (int)E.m, E.M0, E.M1, E.M2, E.M3, R, fast,
+                                           thr0, thr1, thr2, thr3, gglob, sweep, pidx, k0, k1);
+        *reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(W) + E.dst) = v;
+        *reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(S) + E.dst) = v;
       }
+      // further p-bits (a class larger than the consumers) from the descriptors
+      if (K > sh.cons)
+        redraw_extra(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0, thr1, thr2,
+                     thr3, gglob, sweep, k0, k1);
     } else if (producer) {
-      if (t + 1 < n_steps) produce(t + 1, planes + ((t + 1) & 1u) * pbuf);
+      // the next step: class C + 1 of this sweep, or class 0 of the next one
+      if constexpr (C < 3) {
+        produce(std::integral_constant<int, C + 1>{}, sweep, planes + ((C + 1) & 1) * pbuf);
+      } else {
+        if (s + 1u < n_sweeps) produce(std::integral_constant<int, 0>{}, sweep + 1u, planes);
+      }
     } else {
       // records run one sweep behind: the record of sweep s-1 reads its
-      // snapshot in classes 1-2 of sweep s, reduces in class 3 and is binned
-      // in class 0 of sweep s+1
-      if (c == 0 && bin_pending) {
-        rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
-        bin_pending = false;
+      // snapshot in thirds in classes 0-2 of sweep s and reduces in class 3;
+      // it is binned in class 0 of sweep s+1
+      if constexpr (C == 0) {
+        if (bin_pending) {
+          rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
+          bin_pending = false;
+        }
       }
-      if (s > 0 && recorded(sweep - 1)) {
+      if (s > 0u && recorded(sweep - 1u)) {
         const uint32_t* Sp = smem + iw * (1 + ((s + 1u) & 1u));
-        if (c == 1) {
+        if constexpr (C == 0) {
           rec.clear();
-          rec.read(Sp, srec, 0, npb / 2, lane);
-        } else if (c == 2) {
-          rec.read(Sp, srec, npb / 2, npb, lane);
-        } else if (c == 3) {
+          rec.read(Sp, srec, 0, npb / 3, lane);
+        } else if constexpr (C == 1) {
+          rec.read(Sp, srec, npb / 3, 2 * npb / 3, lane);
+        } else if constexpr (C == 2) {
+          rec.read(Sp, srec, 2 * npb / 3, npb, lane);
+        } else {
           rec.reduce(Sp, n, d, lane);
           bin_pending = true;
         }
       }
     }
     __syncthreads();
+  };
+#pragma unroll 1
+  for (uint32_t s = 0; s < n_sweeps; ++s) {
+    step(std::integral_constant<int, 0>{}, s);
+    step(std::integral_constant<int, 1>{}, s);
+    step(std::integral_constant<int, 2>{}, s);
+    step(std::integral_constant<int, 3>{}, s);
   }
   // the records still in flight: the previous sweep's binning and the last sweep
   if (recorder) {
