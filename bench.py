@@ -37,13 +37,19 @@ UNIT = "flips/s"
 # Algorithmic integer work of one 32-chain word update, in 32-lane integer
 # instruction slots: expected Philox4x32-10 calls of the most-significant-
 # first comparison (each plane decides a chain with probability 1/2, calls of
-# 4 planes continue while any of the 32 chains is undecided) x (40 slots per
-# call + 4 planes x 4 slots of comparison) + 12 slots of links and store; plus
-# the record (8 slots per p-bit word) every sweep.
-PHILOX_SLOTS = 40
+# 4 planes continue while any of the 32 chains is undecided) x (20 widening
+# multiplies + 20 three-input XORs per call + 4 planes x 4 slots of
+# comparison) + 12 slots of links and store; plus the record (8 slots per
+# p-bit word) every sweep.  The multiplies run on the integer multiply pipe,
+# everything else on the integer logic pipe; each pipe issues 64 lanes per
+# clock per SM (2 warp-instructions), so the logic pipe, which carries most
+# of the work, is the bound.
+PHILOX_MUL_SLOTS = 20
+PHILOX_XOR_SLOTS = 20
 PLANE_SLOTS = 4
 LINK_SLOTS = 12
 RECORD_SLOTS = 8
+LOGIC_LANES_PER_SM = 64
 
 
 def expected_calls(lanes: int = 32) -> float:
@@ -51,7 +57,14 @@ def expected_calls(lanes: int = 32) -> float:
 
 
 def alg_slots_per_word() -> float:
-    return expected_calls(32) * (PHILOX_SLOTS + 4 * PLANE_SLOTS) + LINK_SLOTS + RECORD_SLOTS
+    """All algorithmic integer slots (both pipes) per 32-chain word."""
+    return (expected_calls(32) * (PHILOX_MUL_SLOTS + PHILOX_XOR_SLOTS + 4 * PLANE_SLOTS)
+            + LINK_SLOTS + RECORD_SLOTS)
+
+
+def alg_logic_slots_per_word() -> float:
+    """Algorithmic slots on the integer logic pipe per 32-chain word."""
+    return expected_calls(32) * (PHILOX_XOR_SLOTS + 4 * PLANE_SLOTS) + LINK_SLOTS + RECORD_SLOTS
 
 
 def _peaks():
@@ -270,22 +283,26 @@ def main():
     value = world * flips_per_step * args.steps / total_s
     clocks = clk.summary()
 
-    # roofline of the dominant kernel (the sweep launch): algorithmic integer
-    # instruction slots per launch / its duration, against the issue peak
+    # roofline of the dominant kernel (the sweep launch): algorithmic logic-
+    # pipe lane operations per launch / its duration, against the logic pipe
     peaks, peak_kind = _peaks()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_slots = sms * 4 * 32 * sm_max * 1e6  # 4 schedulers x 32 lanes per SM per clock
+    peak_ops = sms * LOGIC_LANES_PER_SM * sm_max * 1e6
     words_per_launch = groups * wl.n * wl.d * S
-    alg_slots = words_per_launch * alg_slots_per_word()
+    alg_ops = words_per_launch * alg_logic_slots_per_word()
     launch_s = statistics.mean(sweep_ms) / 1e3
-    achieved = alg_slots / launch_s
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_slots / 1e12,
-                "unit": "T int32 lane-slots/s", "frac": achieved / peak_slots, "traffic": None,
-                "peak_basis": f"{sms} SMs x 128 lanes x {sm_max:.0f} MHz ({peak_kind} sm_max)",
+    achieved = alg_ops / launch_s
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "T int32 logic ops/s", "frac": achieved / peak_ops, "traffic": None,
+                "peak_basis": f"{sms} SMs x {LOGIC_LANES_PER_SM} int32 logic lanes per clock "
+                              f"x {sm_max:.0f} MHz ({peak_kind} sm_max)",
                 "kernel": "sweep_kernel", "launch_ms": statistics.mean(sweep_ms),
-                "alg_slots_per_flip": alg_slots_per_word() / 32}
+                "alg_logic_ops_per_flip": alg_logic_slots_per_word() / 32,
+                "alg_mul_ops_per_flip": expected_calls(32) * PHILOX_MUL_SLOTS / 32,
+                "frac_of_issue": words_per_launch * alg_slots_per_word() / launch_s
+                / (sms * 128 * sm_max * 1e6)}
     prof = os.path.join(ROOT, "profiles", "sweep_kernel_mid_traffic.json")
     if os.path.exists(prof):
         try:
