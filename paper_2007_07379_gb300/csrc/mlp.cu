@@ -14,6 +14,7 @@
 #include "philox.cuh"
 #include "tc_gemm.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -256,6 +257,21 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, int R, int C,
   }
 }
 
+// Columns [k0, k0 + K) of a row-major bf16 [R x ld] matrix into the canonical
+// K-major image the tensor cores read from shared memory: core matrices of
+// 8 rows x 8 elements (128 bytes), K-adjacent ones 128 bytes apart, 8-row
+// groups K * 16 bytes apart.
+__global__ void pack_canonical_kernel(const __nv_bfloat16* __restrict__ src, int R, int ld, int k0,
+                                      int K, __nv_bfloat16* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // one 8-element vector
+  const int vecs = K / 8;
+  if (i >= R * vecs) return;
+  const int r = i / vecs, c = i % vecs;
+  const uint4 v = *reinterpret_cast<const uint4*>(src + (size_t)r * ld + k0 + c * 8);
+  *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(dst) + (size_t)(r >> 3) * (K * 16) + c * 128 +
+                            (r & 7) * 16) = v;
+}
+
 // dY = (sigmoid(l) - t) / B for the first n columns (0 beyond), bf16, both
 // layouts; db3 += column sums (fp32); loss += BCE / B.
 __global__ void bce_grad_kernel(const float* __restrict__ logits, const float* __restrict__ target,
@@ -312,8 +328,8 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
 namespace {
 
 struct MlpLayout {
-  size_t w, m, v, g, W1, W2, W3, W2t, W3t, X, Xt, H1, H1t, H2, H2t, dY, dYt, dZ2, dZ2t, dZ1, dZ1t,
-      logits, target, loss, total;
+  size_t w, m, v, g, W1, W2, W3, W2t, W3t, W1p, W2p, W3p, X, Xt, H1, H1t, H2, H2t, dY, dYt, dZ2,
+      dZ2t, dZ1, dZ1t, logits, target, loss, total;
 };
 
 MlpLayout mlp_layout(int kin, int H, int npad, int B) {
@@ -335,6 +351,9 @@ MlpLayout mlp_layout(int kin, int H, int npad, int B) {
   L.W3 = take((size_t)npad * H * 2);
   L.W2t = take((size_t)H * H * 2);
   L.W3t = take((size_t)H * npad * 2);
+  L.W1p = take((size_t)H * kin * 2);
+  L.W2p = take((size_t)H * H * 2);
+  L.W3p = take((size_t)npad * H * 2);
   L.X = take((size_t)B * kin * 2);
   L.Xt = take((size_t)B * kin * 2);
   L.H1 = take((size_t)B * H * 2);
@@ -396,6 +415,15 @@ cudaError_t refresh_bf16(pb_mlp* p) {
   pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off_W2, p->H, p->H, p->W2, p->W2t);
   c = (size_t)p->npad * p->H;
   pb::to_bf16_kernel<<<(unsigned)((c + T - 1) / T), T, 0, p->st>>>(w + p->off_W3, p->npad, p->H, p->W3, p->W3t);
+  // canonical images for the fused kernel (W2 in K-chunks of 64)
+  auto pack = [&](const __nv_bfloat16* src, int R, int ld, int k0, int K, __nv_bfloat16* dst) {
+    const int v = R * (K / 8);
+    pb::pack_canonical_kernel<<<(v + T - 1) / T, T, 0, p->st>>>(src, R, ld, k0, K, dst);
+  };
+  pack(p->W1, p->H, p->kin, 0, p->kin, p->W1p);
+  for (int k0 = 0; k0 < p->H; k0 += 64)
+    pack(p->W2, p->H, p->H, k0, std::min(64, p->H - k0), p->W2p + (size_t)p->H * k0);
+  pack(p->W3, p->npad, p->H, 0, p->H, p->W3p);
   return cudaGetLastError();
 }
 
@@ -509,6 +537,8 @@ PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, voi
   p->w = (float*)(b + L.w); p->m = (float*)(b + L.m); p->v = (float*)(b + L.v); p->g = (float*)(b + L.g);
   p->W1 = (__nv_bfloat16*)(b + L.W1); p->W2 = (__nv_bfloat16*)(b + L.W2); p->W3 = (__nv_bfloat16*)(b + L.W3);
   p->W2t = (__nv_bfloat16*)(b + L.W2t); p->W3t = (__nv_bfloat16*)(b + L.W3t);
+  p->W1p = (__nv_bfloat16*)(b + L.W1p); p->W2p = (__nv_bfloat16*)(b + L.W2p);
+  p->W3p = (__nv_bfloat16*)(b + L.W3p);
   p->X = (__nv_bfloat16*)(b + L.X); p->Xt = (__nv_bfloat16*)(b + L.Xt);
   p->H1 = (__nv_bfloat16*)(b + L.H1); p->H1t = (__nv_bfloat16*)(b + L.H1t);
   p->H2 = (__nv_bfloat16*)(b + L.H2); p->H2t = (__nv_bfloat16*)(b + L.H2t);
@@ -635,7 +665,7 @@ enum : int { kFusedLogits = 0, kFusedLogQ = 1, kFusedSample = 2 };
 
 struct FusedArgs {
   const __nv_bfloat16* X;  // [rows x kin] (kFusedLogits)
-  const __nv_bfloat16 *W1, *W2, *W3;
+  const __nv_bfloat16 *W1p, *W2p, *W3p;  // canonical images (W2 in K-chunks of 64)
   const float *b1, *b2, *b3;
   float* logits;  // [rows x npad] (kFusedLogits)
   int rows, kin, H, npad;
@@ -648,9 +678,38 @@ struct FusedArgs {
   const uint32_t* move_dev;
   uint32_t beta, k0, k1, group0;
   int n, d, k, j, jlast;  // kFusedSample: layers j .. jlast, one after the other
+  // shared-memory layout (byte offsets; fused_layout) and W2 chunk buffers
+  uint32_t offH, offW1, offW3, offB, offWb, chunk_bytes;
+  int nb;
 };
 
-constexpr size_t kFusedSmem = 24 * 1024 + 64 * 1024 + 64 * 1024;  // x, h, two weight buffers
+// Dynamic shared memory of the fused kernel, sized per network: the x tile
+// (128 x kin), the h tile (128 x H), W1, W3 and the biases resident for the
+// whole launch, and nb buffers for the K-chunks of W2 (64 columns each)
+// streamed in by bulk copies; nb is as large as the space allows.
+constexpr size_t kFusedSmemMax = 226 * 1024;  // with the kernel's 1 KB of static shared memory
+
+inline size_t round_kb(size_t b) { return (b + 1023) & ~(size_t)1023; }
+
+// Fills the layout fields of `a`; returns the dynamic shared-memory size (0
+// when not even two chunk buffers fit).
+inline size_t fused_layout(FusedArgs& a) {
+  const size_t X = round_kb((size_t)128 * a.kin * 2), Hs = round_kb((size_t)128 * a.H * 2);
+  const size_t W1 = round_kb((size_t)a.H * a.kin * 2), W3 = round_kb((size_t)a.npad * a.H * 2);
+  const size_t B = round_kb((size_t)(2 * a.H + a.npad) * 4);
+  const int nchunks = (a.H + 63) / 64;
+  const size_t chunk = round_kb((size_t)a.H * std::min(64, a.H) * 2);
+  a.offH = (uint32_t)X;
+  a.offW1 = (uint32_t)(X + Hs);
+  a.offW3 = (uint32_t)(X + Hs + W1);
+  a.offB = (uint32_t)(X + Hs + W1 + W3);
+  a.offWb = (uint32_t)(X + Hs + W1 + W3 + B);
+  a.chunk_bytes = (uint32_t)chunk;
+  const size_t fixed = a.offWb;
+  if (fixed + std::min(2, nchunks) * chunk > kFusedSmemMax) return 0;
+  a.nb = (int)std::min<size_t>((size_t)nchunks, (kFusedSmemMax - fixed) / chunk);
+  return fixed + (size_t)a.nb * chunk;
+}
 
 // Rows [r0, r0+nrows) x K of a row-major bf16 matrix into the canonical
 // K-major layout at `dst` (8-row groups SBO = K * 16 bytes apart).
@@ -688,188 +747,266 @@ __device__ __forceinline__ void build_x_row(uint8_t* sX, int kin, int n, int r, 
 template <int MODE>
 __global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  // one mbarrier per weight buffer: each has at most one commit in flight
-  __shared__ uint64_t mbar[2];
+  // mbarriers: wbar = W1 and W3 delivered; lbar[b] = the W2 chunk in buffer
+  // b delivered; cbar[b] = the MMAs reading buffer b done (committed only
+  // when the buffer is refilled within the same GEMM); done = all MMAs of
+  // the current GEMM done (every thread waits once per GEMM); drain = all
+  // MMAs done (after a failed wait only)
+  constexpr int kMaxNb = 4;
+  __shared__ uint64_t bars[2 + 2 * kMaxNb + 1];
   __shared__ uint32_t tmem_base;
+  uint64_t* wbar = &bars[0];
+  uint64_t* done = &bars[1];
+  uint64_t* drain = &bars[2];
+  uint64_t* lbar = &bars[3];
+  uint64_t* cbar = &bars[3 + kMaxNb];
   uint8_t* sX = sm;
-  uint8_t* sH = sm + 24 * 1024;
-  uint8_t* sWb[2] = {sm + 88 * 1024, sm + 120 * 1024};
+  uint8_t* sH = sm + a.offH;
+  uint8_t* sW1 = sm + a.offW1;
+  uint8_t* sW3 = sm + a.offW3;
+  float* sB = reinterpret_cast<float*>(sm + a.offB);  // b1 [H], b2 [H], b3 [npad]
+  uint8_t* sWb = sm + a.offWb;                           // nb chunk buffers
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r0 = blockIdx.x * 128;
-  const int H = a.H, kin = a.kin;
+  const int H = a.H, kin = a.kin, npad = a.npad, nb = min(a.nb, kMaxNb);
+  const int nchunks = (H + 63) / 64;
+  auto chunk_k = [&](int c) { return (c == nchunks - 1 && (H % 64)) ? (H % 64) : 64; };
+  const int jfirst = MODE == kFusedLogQ ? a.k + (int)blockIdx.y : a.j;
+  const int jend = MODE == kFusedSample ? a.jlast : jfirst;
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
   if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
+    for (int i = 0; i < 2 + 2 * kMaxNb + 1; ++i) tc::mbar_init(&bars[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();  // TMEM address and barrier initialisation visible
+  for (int i = tid; i < H; i += 128) {
+    sB[i] = a.b1[i];
+    sB[H + i] = a.b2[i];
+  }
+  for (int i = tid; i < npad; i += 128) sB[2 * H + i] = a.b3[i];
+  __syncthreads();  // TMEM address, barriers and biases visible
   const uint32_t tb = tmem_base;
-  uint32_t ph[2] = {0u, 0u};
   bool ok = true;
-  auto wait = [&](int b) {
+  uint32_t dph = 0u;  // parity of `done` (every thread)
+  // thread 0: parities and the copies still to be waited for
+  uint32_t wph = 0u, lph[kMaxNb] = {0u, 0u, 0u, 0u}, cph[kMaxNb] = {0u, 0u, 0u, 0u};
+  bool lpend[kMaxNb] = {false, false, false, false};
+  // After a failed wait the thread skips further waits and work but keeps
+  // the same sequence of CTA barriers as the others.
+  auto wait_on = [&](uint64_t* bar, uint32_t& ph) {
     if (!ok) return;
-    ok = tc::mbar_wait(&mbar[b], ph[b]);
-    ph[b] ^= 1u;
+    ok = tc::mbar_wait(bar, ph);
+    if (ok) ph ^= 1u;
   };
+  // K-chunk c of W2 into buffer b (thread 0; the buffer is free)
+  auto load_chunk = [&](int c, int b) {
+    const uint32_t bytes = (uint32_t)(H * chunk_k(c) * 2);
+    tc::mbar_expect_tx(&lbar[b], bytes);
+    tc::bulk_load(sWb + (size_t)b * a.chunk_bytes, a.W2p + (size_t)H * c * 64, bytes, &lbar[b]);
+    lpend[b] = true;
+  };
+  // the first min(nb, nchunks) chunks of the next GEMM over W2
+  auto prefetch_w2 = [&]() {
+    for (int c = 0; c < nb && c < nchunks; ++c) load_chunk(c, c);
+  };
+  if (tid == 0) {
+    const uint32_t w1 = (uint32_t)(H * kin * 2), w3 = (uint32_t)(npad * H * 2);
+    tc::mbar_expect_tx(wbar, w1 + w3);
+    tc::bulk_load(sW1, a.W1p, w1, wbar);
+    tc::bulk_load(sW3, a.W3p, w3, wbar);
+    prefetch_w2();
+  }
   const uint32_t taddr_row = tb + ((uint32_t)(warp * 32) << 16);
   const int row = r0 + warp * 32 + lane;
-  const int jfirst = MODE == kFusedLogQ ? a.k + (int)blockIdx.y : a.j;
-  const int jend = MODE == kFusedSample ? a.jlast : jfirst;
-  for (int jl = jfirst; jl <= jend && ok; ++jl) {
-  // x tile and W1
-  // (per-chain modes: row = chain r0 + r, layer j)
-  if (MODE == kFusedLogits) {
-    stage_rows(sX, a.X, kin, r0, 128, a.rows, 0, kin, tid, 128);
-  } else {
-    const int c = r0 + tid;
-    uint32_t prev = a.beta;
-    if (c < a.rows && jl > 1) {
-      const uint32_t* src = (MODE == kFusedSample && jl > a.k) ? a.Pn : a.P;
-      prev = src[(size_t)c * a.d + (jl - 2)];
-    }
-    build_x_row(sX, kin, a.n, tid, prev, jl);
-  }
-  stage_rows(sWb[0], a.W1, kin, 0, H, H, 0, kin, tid, 128);
-  tc::cp_async_wait_all();
-  tc::fence_proxy_async_smem();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-
-  // ---- layer 1: D = x W1^T   (commit on mbar[0])
-  if (tid == 0) {
-    const uint32_t ax = tc::smem_u32(sX), bw = tc::smem_u32(sWb[0]);
-    const uint32_t idesc = tc::idesc_bf16_f32(128, H);
-    for (int s = 0; s < kin / 16; ++s)
-      tc::mma_bf16(tb, tc::smem_desc(ax + s * 256, 128, kin * 16),
-                   tc::smem_desc(bw + s * 256, 128, kin * 16), idesc, s > 0);
-    tc::mma_commit(&mbar[0]);
-  }
-  wait(0);
-
-  // epilogue: h = relu(D + b) in bf16, into sH (canonical, K = H)
-  auto epilogue_to_h = [&](const float* bias) {
+  // generic-proxy shared writes of all threads visible to the tensor core
+  auto publish = [&]() {
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
     tc::fence_after_sync();
-    for (int c0 = 0; c0 < H; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(taddr_row + (uint32_t)c0, v);
-      __align__(16) __nv_bfloat16 hb[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) hb[i] = __float2bfloat16(fmaxf(v[i] + bias[c0 + i], 0.f));
-      const int r = warp * 32 + lane;
-      uint8_t* base = sH + (r >> 3) * (H * 16) + (r & 7) * 16;
-      *reinterpret_cast<uint4*>(base + (c0 / 8) * 128) = *reinterpret_cast<uint4*>(&hb[0]);
-      *reinterpret_cast<uint4*>(base + (c0 / 8 + 1) * 128) = *reinterpret_cast<uint4*>(&hb[8]);
-    }
   };
-  if (ok) epilogue_to_h(a.b1);
-
-  // ---- layer 2: D = h W2^T, W2 in K-chunks of 64; chunk c uses buffer and
-  // mbarrier c & 1.  Chunk c+1 is staged while chunk c runs, after the MMAs
-  // of chunk c-1 (same buffer) have completed.
-  const int nchunks = (H + 63) / 64;
-  auto chunk_k = [&](int c) { return (c == nchunks - 1 && (H % 64)) ? (H % 64) : 64; };
-  if (ok) stage_rows(sWb[0], a.W2, H, 0, H, H, 0, chunk_k(0), tid, 128);
-  for (int c = 0; c < nchunks && ok; ++c) {
-    const int b = c & 1;
-    tc::cp_async_wait_all();
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
+  auto wait_done = [&]() {
+    wait_on(done, dph);
     tc::fence_after_sync();
-    if (tid == 0) {
-      const int kc = chunk_k(c);
-      const uint32_t ah = tc::smem_u32(sH) + c * 8 * 128, bw = tc::smem_u32(sWb[b]);
-      const uint32_t idesc = tc::idesc_bf16_f32(128, H);
-      for (int s = 0; s < kc / 16; ++s)
-        tc::mma_bf16(tb, tc::smem_desc(ah + s * 256, 128, H * 16),
-                     tc::smem_desc(bw + s * 256, 128, kc * 16), idesc, (c > 0) || (s > 0));
-      tc::mma_commit(&mbar[b]);
-    }
-    if (c + 1 < nchunks) {
-      if (c >= 1) wait(b ^ 1);  // chunk c-1 done: its buffer is free
-      if (ok) stage_rows(sWb[b ^ 1], a.W2, H, 0, H, H, (c + 1) * 64, chunk_k(c + 1), tid, 128);
-    }
-  }
-  // the last one or two chunks of layer 2
-  if (nchunks >= 2) wait((nchunks - 2) & 1);
-  wait((nchunks - 1) & 1);
-  if (ok) {
-    epilogue_to_h(a.b2);
-    // ---- layer 3: D = h W3^T  (buffer 0 and mbar[0] are free)
-    stage_rows(sWb[0], a.W3, H, 0, a.npad, a.npad, 0, H, tid, 128);
-    tc::cp_async_wait_all();
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (tid == 0) {
-      const uint32_t ah = tc::smem_u32(sH), bw = tc::smem_u32(sWb[0]);
-      const uint32_t idesc = tc::idesc_bf16_f32(128, a.npad);
-      for (int s = 0; s < H / 16; ++s)
-        tc::mma_bf16(tb, tc::smem_desc(ah + s * 256, 128, H * 16),
-                     tc::smem_desc(bw + s * 256, 128, H * 16), idesc, s > 0);
-      tc::mma_commit(&mbar[0]);
-    }
-    wait(0);
-  }
-  if (ok) {
-    tc::fence_after_sync();
-    // logits of this thread's row (npad <= 32)
-    float l[32];
-    for (int c0 = 0; c0 < a.npad; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(taddr_row + (uint32_t)c0, v);
+  };
+  // h = relu(D + b) in bf16, into sH (canonical, K = H), 64 columns per TMEM read
+  auto epilogue_to_h = [&](const float* bias) {
+    const int r = warp * 32 + lane;
+    uint8_t* base = sH + (r >> 3) * (H * 16) + (r & 7) * 16;
+    for (int c0 = 0; c0 < H; c0 += 64) {
+      float v[64];
+      tc::tmem_ld64(taddr_row + (uint32_t)c0, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) l[c0 + i] = v[i] + a.b3[c0 + i];
-    }
-    if (row < a.rows) {
-      if (MODE == kFusedLogits) {
-        for (int i = 0; i < a.npad; ++i) a.logits[(size_t)row * a.npad + i] = l[i];
-      } else if (MODE == kFusedLogQ) {
-        // log q of the current layer word: sum_q log sigma(+-l_q)
-        const uint32_t bits = a.P[(size_t)row * a.d + (jl - 1)];
-        float sq = 0.f;
-        for (int q = 0; q < a.n; ++q) {
-          const float z = ((bits >> q) & 1u) ? -l[q] : l[q];
-          sq -= fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z)));
+      for (int g = 0; g < 8; ++g) {
+        if (c0 + 8 * g < H) {
+          __align__(16) __nv_bfloat162 hb[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int c = c0 + 8 * g + 2 * i;
+            hb[i] = __floats2bfloat162_rn(fmaxf(v[8 * g + 2 * i] + bias[c], 0.f),
+                                          fmaxf(v[8 * g + 2 * i + 1] + bias[c + 1], 0.f));
+          }
+          *reinterpret_cast<uint4*>(base + ((c0 >> 3) + g) * 128) = *reinterpret_cast<uint4*>(hb);
         }
-        a.lq[(size_t)row * a.d + (jl - 1)] = sq;
-      } else {
-        // draw s'_j bit by bit: u < sigmoid(l_q), u from Philox (chain,
-        // move, (j-1) | tag 2 << 16, q/4)
-        const uint32_t move = *a.move_dev;
-        const uint32_t gc = a.group0 * 32u + (uint32_t)row;
-        uint32_t word = 0u;
-        float sq = 0.f;
-        uint4 u4 = make_uint4(0u, 0u, 0u, 0u);
-        for (int q = 0; q < a.n; ++q) {
-          if ((q & 3) == 0)
-            u4 = philox4x32_10(make_uint4(gc, move, (uint32_t)(jl - 1) | (kTagMH << 16),
-                                          (uint32_t)(q >> 2)), a.k0, a.k1);
-          const uint32_t u = (q & 3) == 0 ? u4.x : (q & 3) == 1 ? u4.y : (q & 3) == 2 ? u4.z : u4.w;
-          const float p1 = 1.f / (1.f + __expf(-l[q]));
-          const float uf = ((float)(u >> 8) + 0.5f) * (1.f / 16777216.f);
-          const uint32_t b = uf < p1 ? 1u : 0u;
-          word |= b << q;
-          const float z = b ? -l[q] : l[q];
-          sq -= fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z)));
-        }
-        a.Pn[(size_t)row * a.d + (jl - 1)] = word;
-        a.lqf[row] += sq;
       }
     }
-  }
+  };
+
+  // per-chain modes: this thread's chain, its previous layer word and the
+  // running log q of the proposal
+  const int chain = r0 + tid;
+  uint32_t prev = a.beta;
+  if (MODE != kFusedLogits && chain < a.rows && jfirst > 1)
+    prev = a.P[(size_t)chain * a.d + (jfirst - 2)];
+  float lq_acc = 0.f;
+
+  for (int jl = jfirst; jl <= jend; ++jl) {
+    // ---- x tile (row = chain r0 + r at layer jl, or a staged input row)
+    if (MODE == kFusedLogits) {
+      stage_rows(sX, a.X, kin, r0, 128, a.rows, 0, kin, tid, 128);
+      tc::cp_async_wait_all();
+    } else {
+      build_x_row(sX, kin, a.n, tid, prev, jl);
+    }
+    publish();
+
+    // ---- layer 1: D = x W1^T
+    if (tid == 0) {
+      if (jl == jfirst) wait_on(wbar, wph);
+      if (ok) {
+        const uint32_t ax = tc::smem_u32(sX), bw = tc::smem_u32(sW1);
+        const uint32_t idesc = tc::idesc_bf16_f32(128, H);
+        for (int s = 0; s < kin / 16; ++s)
+          tc::mma_bf16(tb, tc::smem_desc(ax + s * 256, 128, kin * 16),
+                       tc::smem_desc(bw + s * 256, 128, kin * 16), idesc, s > 0);
+      }
+      tc::mma_commit(done);
+    }
+    wait_done();
+    if (ok) epilogue_to_h(sB);
+    publish();
+
+    // ---- layer 2: D = h W2^T over the K-chunks of W2 (chunk c in buffer
+    // c % nb); chunk c + nb - 1 is fetched once the MMAs of chunk c - 1 are done
+    if (tid == 0) {
+      for (int c = 0; c < nchunks; ++c) {
+        const int b = c % nb;
+        wait_on(&lbar[b], lph[b]);
+        if (!ok) continue;
+        lpend[b] = false;
+        const int kc = chunk_k(c);
+        const uint32_t ah = tc::smem_u32(sH) + c * 8 * 128;
+        const uint32_t bw = tc::smem_u32(sWb + (size_t)b * a.chunk_bytes);
+        const uint32_t idesc = tc::idesc_bf16_f32(128, H);
+        for (int s = 0; s < kc / 16; ++s)
+          tc::mma_bf16(tb, tc::smem_desc(ah + s * 256, 128, H * 16),
+                       tc::smem_desc(bw + s * 256, 128, kc * 16), idesc, (c > 0) || (s > 0));
+        if (c + nb < nchunks) tc::mma_commit(&cbar[b]);  // buffer b is refilled below
+        if (c >= 1 && c - 1 + nb < nchunks) {
+          const int bp = (c - 1) % nb;
+          wait_on(&cbar[bp], cph[bp]);
+          if (ok) load_chunk(c - 1 + nb, bp);
+        }
+      }
+      tc::mma_commit(done);
+    }
+    wait_done();
+    // every W2 buffer is free: thread 0 fetches the next layer's first chunks
+    if (tid == 0 && ok && jl < jend) prefetch_w2();
+    if (ok) epilogue_to_h(sB + H);
+    publish();
+
+    // ---- layer 3: D = h W3^T
+    if (tid == 0) {
+      if (ok) {
+        const uint32_t ah = tc::smem_u32(sH), bw = tc::smem_u32(sW3);
+        const uint32_t idesc = tc::idesc_bf16_f32(128, npad);
+        for (int s = 0; s < H / 16; ++s)
+          tc::mma_bf16(tb, tc::smem_desc(ah + s * 256, 128, H * 16),
+                       tc::smem_desc(bw + s * 256, 128, H * 16), idesc, s > 0);
+      }
+      tc::mma_commit(done);
+    }
+    wait_done();
+    if (ok) {
+      // logits of this thread's row (npad is 16 or 32)
+      float l[32];
+      if (npad > 16) {
+        tc::tmem_ld32(taddr_row, l);
+      } else {
+        float v[16];
+        tc::tmem_ld16(taddr_row, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) l[i] = v[i];
+#pragma unroll
+        for (int i = 16; i < 32; ++i) l[i] = 0.f;
+      }
+      const float* b3 = sB + 2 * H;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) l[i] += i < npad ? b3[i] : 0.f;
+      if (row < a.rows) {
+        if (MODE == kFusedLogits) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (i < npad) a.logits[(size_t)row * npad + i] = l[i];
+        } else if (MODE == kFusedLogQ) {
+          // log q of the current layer word: sum_q log sigma(+-l_q)
+          const uint32_t bits = a.P[(size_t)row * a.d + (jl - 1)];
+          float sq = 0.f;
+#pragma unroll
+          for (int qb = 0; qb < 32; ++qb) {
+            if (qb < a.n) {
+              const float z = ((bits >> qb) & 1u) ? -l[qb] : l[qb];
+              sq -= fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z)));
+            }
+          }
+          a.lq[(size_t)row * a.d + (jl - 1)] = sq;
+        } else {
+          // draw s'_j bit by bit: u < sigmoid(l_q), u from Philox (chain,
+          // move, (j-1) | tag 2 << 16, q/4)
+          const uint32_t move = *a.move_dev;
+          const uint32_t gc = a.group0 * 32u + (uint32_t)row;
+          uint32_t word = 0u;
+          float sq = 0.f;
+          uint4 u4 = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+          for (int qb = 0; qb < 32; ++qb) {
+            if (qb < a.n) {
+              if ((qb & 3) == 0)
+                u4 = philox4x32_10(make_uint4(gc, move, (uint32_t)(jl - 1) | (kTagMH << 16),
+                                              (uint32_t)(qb >> 2)), a.k0, a.k1);
+              const uint32_t u = (qb & 3) == 0 ? u4.x : (qb & 3) == 1 ? u4.y : (qb & 3) == 2 ? u4.z : u4.w;
+              const float p1 = 1.f / (1.f + __expf(-l[qb]));
+              const float uf = ((float)(u >> 8) + 0.5f) * (1.f / 16777216.f);
+              const uint32_t bit = uf < p1 ? 1u : 0u;
+              word |= bit << qb;
+              const float z = bit ? -l[qb] : l[qb];
+              sq -= fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z)));
+            }
+          }
+          a.Pn[(size_t)row * a.d + (jl - 1)] = word;
+          lq_acc += sq;
+          prev = word;
+        }
+      }
+    }
+    // the TMEM reads of this layer are complete before the next layer's MMAs
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
   }  // layers
-  if (ok) {
-    // nothing left
-  } else {
-    if (a.status) atomicCAS(a.status, 0u, (uint32_t)PB_ETIMEOUT);
-    // let MMAs in flight drain (bounded) before the accumulator is freed
-    tc::mbar_wait(&mbar[0], ph[0]);
-    tc::mbar_wait(&mbar[1], ph[1]);
+  if (MODE == kFusedSample && ok && row < a.rows) a.lqf[row] += lq_acc;
+  if (!__syncthreads_and(ok)) {
+    if (tid == 0) {
+      if (a.status) atomicCAS(a.status, 0u, (uint32_t)PB_ETIMEOUT);
+      // let MMAs and copies still in flight drain (bounded waits) before the
+      // accumulator and the shared memory are given up
+      tc::mma_commit(drain);
+      tc::mbar_wait(drain, 0u);
+      for (int b = 0; b < kMaxNb; ++b)
+        if (lpend[b]) tc::mbar_wait(&lbar[b], lph[b]);
+      if (wph == 0u) tc::mbar_wait(wbar, wph);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -883,9 +1020,9 @@ template __global__ void mlp_fused_kernel<kFusedSample>(FusedArgs);
 static FusedArgs fused_args(pb_mlp* p, int rows) {
   FusedArgs a{};
   a.jlast = 0;
-  a.W1 = p->W1;
-  a.W2 = p->W2;
-  a.W3 = p->W3;
+  a.W1p = p->W1p;
+  a.W2p = p->W2p;
+  a.W3p = p->W3p;
   a.b1 = p->w + p->off_b1;
   a.b2 = p->w + p->off_b2;
   a.b3 = p->w + p->off_b3;
@@ -907,7 +1044,9 @@ cudaError_t mlp_fused_logq(pb_mlp* p, const uint32_t* P, uint32_t beta, int chai
   a.k = k;
   a.lq = lq;
   dim3 grid((chains + 127) / 128, p->d - k + 1);
-  mlp_fused_kernel<kFusedLogQ><<<grid, 128, kFusedSmem, st>>>(a);
+  const size_t smem = fused_layout(a);
+  if (smem == 0) return cudaErrorInvalidValue;
+  mlp_fused_kernel<kFusedLogQ><<<grid, 128, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -928,16 +1067,18 @@ cudaError_t mlp_fused_sample(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uint32_
   a.k1 = k1;
   a.move_dev = move_dev;
   a.group0 = group0;
-  mlp_fused_kernel<kFusedSample><<<(chains + 127) / 128, 128, kFusedSmem, st>>>(a);
+  const size_t smem = fused_layout(a);
+  if (smem == 0) return cudaErrorInvalidValue;
+  mlp_fused_kernel<kFusedSample><<<(chains + 127) / 128, 128, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t mlp_forward_fused(pb_mlp* p, int rows) {
   FusedArgs a{};
   a.X = p->X;
-  a.W1 = p->W1;
-  a.W2 = p->W2;
-  a.W3 = p->W3;
+  a.W1p = p->W1p;
+  a.W2p = p->W2p;
+  a.W3p = p->W3p;
   a.b1 = p->w + p->off_b1;
   a.b2 = p->w + p->off_b2;
   a.b3 = p->w + p->off_b3;
@@ -947,19 +1088,22 @@ cudaError_t mlp_forward_fused(pb_mlp* p, int rows) {
   a.H = p->H;
   a.npad = p->npad;
   a.status = nullptr;
-  mlp_fused_kernel<kFusedLogits><<<(rows + 127) / 128, 128, kFusedSmem, p->st>>>(a);
+  a.n = p->n;
+  const size_t smem = fused_layout(a);
+  if (smem == 0) return cudaErrorInvalidValue;
+  mlp_fused_kernel<kFusedLogits><<<(rows + 127) / 128, 128, smem, p->st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t mlp_fused_prepare() {
   cudaError_t e = cudaFuncSetAttribute(mlp_fused_kernel<kFusedLogits>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_fused_kernel<kFusedLogQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kFusedSmem);
+                             (int)kFusedSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_fused_kernel<kFusedSample>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemMax);
   return e;
 }
 

@@ -114,6 +114,9 @@ struct pb_mlp {
   size_t off_W1 = 0, off_b1 = 0, off_W2 = 0, off_b2 = 0, off_W3 = 0, off_b3 = 0, n_params = 0;
   float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
   __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2t = nullptr, *W3t = nullptr;
+  // W1, W2 (in K-chunks of 64) and W3 in the tensor cores' canonical K-major
+  // shared-memory layout, loaded by the fused kernel with one bulk copy each
+  __nv_bfloat16 *W1p = nullptr, *W2p = nullptr, *W3p = nullptr;
   __nv_bfloat16 *X = nullptr, *Xt = nullptr, *H1 = nullptr, *H1t = nullptr, *H2 = nullptr,
                 *H2t = nullptr, *dY = nullptr, *dYt = nullptr, *dZ2 = nullptr, *dZ2t = nullptr,
                 *dZ1 = nullptr, *dZ1t = nullptr;
