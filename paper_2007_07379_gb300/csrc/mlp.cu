@@ -687,7 +687,7 @@ struct FusedArgs {
 // (128 x kin), the h tile (128 x H), W1, W3 and the biases resident for the
 // whole launch, and nb buffers for the K-chunks of W2 (64 columns each)
 // streamed in by bulk copies; nb is as large as the space allows.
-constexpr size_t kFusedSmemMax = 226 * 1024;  // with the kernel's 1 KB of static shared memory
+constexpr size_t kFusedSmemMax = 224 * 1024;  // with the kernel's static shared memory (< 3 KB)
 
 inline size_t round_kb(size_t b) { return (b + 1023) & ~(size_t)1023; }
 
@@ -727,25 +727,34 @@ __device__ __forceinline__ void stage_rows(uint8_t* dst, const __nv_bfloat16* sr
   }
 }
 
-// Row x = [2 prev - 1 (n), onehot(j-1) (d), 0...] of this thread into the
-// canonical layout of the x tile (row r of 128, SBO = kin * 16).
-__device__ __forceinline__ void build_x_row(uint8_t* sX, int kin, int n, int r, uint32_t prev, int j) {
-  const __nv_bfloat16 one = __float2bfloat16(1.f), mone = __float2bfloat16(-1.f),
-                      zero = __float2bfloat16(0.f);
+// Elements [8 c_lo, 8 c_hi) of row r of the x tile (canonical layout, SBO =
+// kin * 16): x = [2 prev - 1 (n), onehot(j-1) (d), 0...], written as bf16
+// bit patterns (1.0 = 0x3F80, -1.0 = 0xBF80).
+__device__ __forceinline__ void build_x_part(uint8_t* sX, int kin, int n, int r, uint32_t prev,
+                                             int j, int c_lo, int c_hi) {
   uint8_t* base = sX + (r >> 3) * (kin * 16) + (r & 7) * 16;
-  for (int c = 0; c < kin / 8; ++c) {
-    __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int i = c * 8 + t;
-      v[t] = i < n ? (((prev >> i) & 1u) ? one : mone) : (i == n + j - 1 ? one : zero);
-    }
-    *reinterpret_cast<uint4*>(base + c * 128) = *reinterpret_cast<const uint4*>(v);
+  auto elem = [&](int i) -> uint32_t {
+    if (i < n) return ((prev >> i) & 1u) ? 0x3F80u : 0xBF80u;
+    return i == n + j - 1 ? 0x3F80u : 0u;
+  };
+  for (int c = c_lo; c < c_hi; ++c) {
+    uint4 w;
+    w.x = elem(8 * c) | (elem(8 * c + 1) << 16);
+    w.y = elem(8 * c + 2) | (elem(8 * c + 3) << 16);
+    w.z = elem(8 * c + 4) | (elem(8 * c + 5) << 16);
+    w.w = elem(8 * c + 6) | (elem(8 * c + 7) << 16);
+    *reinterpret_cast<uint4*>(base + c * 128) = w;
   }
 }
 
+// log(1 + e^{-|l|}), the shared part of log sigma(l) and log sigma(-l):
+// log sigma(+-l) = -(max(-+l, 0) + softplus_tail(l)).  Both fused modes that
+// evaluate log q use this one expression, so a proposal's log q computed
+// while it is drawn equals the one computed later for the same path.
+__device__ __forceinline__ float softplus_tail(float l) { return __logf(1.f + __expf(-fabsf(l))); }
+
 template <int MODE>
-__global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   // mbarriers: wbar = W1 and W3 delivered; lbar[b] = the W2 chunk in buffer
   // b delivered; cbar[b] = the MMAs reading buffer b done (committed only
@@ -755,6 +764,9 @@ __global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
   constexpr int kMaxNb = 4;
   __shared__ uint64_t bars[2 + 2 * kMaxNb + 1];
   __shared__ uint32_t tmem_base;
+  // the two halves of a row exchange their bits and log q terms here
+  __shared__ uint32_t xw[2][128];
+  __shared__ float xq[2][128];
   uint64_t* wbar = &bars[0];
   uint64_t* done = &bars[1];
   uint64_t* drain = &bars[2];
@@ -766,7 +778,11 @@ __global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
   uint8_t* sW3 = sm + a.offW3;
   float* sB = reinterpret_cast<float*>(sm + a.offB);  // b1 [H], b2 [H], b3 [npad]
   uint8_t* sWb = sm + a.offWb;                           // nb chunk buffers
+  // 256 threads: warp w reads TMEM lanes 32 (w & 3) .. +31 (its rows) and
+  // handles half (w >> 2) of the columns, x elements and bits of those rows
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
+  const int rl = quad * 32 + lane;  // row within the tile
   const int r0 = blockIdx.x * 128;
   const int H = a.H, kin = a.kin, npad = a.npad, nb = min(a.nb, kMaxNb);
   const int nchunks = (H + 63) / 64;
@@ -779,11 +795,11 @@ __global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
     for (int i = 0; i < 2 + 2 * kMaxNb + 1; ++i) tc::mbar_init(&bars[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < H; i += 128) {
+  for (int i = tid; i < H; i += 256) {
     sB[i] = a.b1[i];
     sB[H + i] = a.b2[i];
   }
-  for (int i = tid; i < npad; i += 128) sB[2 * H + i] = a.b3[i];
+  for (int i = tid; i < npad; i += 256) sB[2 * H + i] = a.b3[i];
   __syncthreads();  // TMEM address, barriers and biases visible
   const uint32_t tb = tmem_base;
   bool ok = true;
@@ -816,8 +832,8 @@ __global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
     tc::bulk_load(sW3, a.W3p, w3, wbar);
     prefetch_w2();
   }
-  const uint32_t taddr_row = tb + ((uint32_t)(warp * 32) << 16);
-  const int row = r0 + warp * 32 + lane;
+  const uint32_t taddr_row = tb + ((uint32_t)(quad * 32) << 16);
+  const int row = r0 + rl;
   // generic-proxy shared writes of all threads visible to the tensor core
   auto publish = [&]() {
     tc::fence_proxy_async_smem();
@@ -829,23 +845,25 @@ __global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
     wait_on(done, dph);
     tc::fence_after_sync();
   };
-  // h = relu(D + b) in bf16, into sH (canonical, K = H), 64 columns per TMEM read
+  // h = relu(D + b) in bf16, into sH (canonical, K = H): this thread's row,
+  // columns [half H/2, (half + 1) H/2), 64 columns per TMEM read
+  const int hc_lo = half * (H / 2), hc_hi = hc_lo + H / 2;
   auto epilogue_to_h = [&](const float* bias) {
-    const int r = warp * 32 + lane;
-    uint8_t* base = sH + (r >> 3) * (H * 16) + (r & 7) * 16;
-    for (int c0 = 0; c0 < H; c0 += 64) {
+    uint8_t* base = sH + (rl >> 3) * (H * 16) + (rl & 7) * 16;
+    for (int c0 = hc_lo; c0 < hc_hi; c0 += 64) {
       float v[64];
       tc::tmem_ld64(taddr_row + (uint32_t)c0, v);
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
-        if (c0 + 8 * g < H) {
+        if (c0 + 8 * g < hc_hi) {
+          const float4 bl = *reinterpret_cast<const float4*>(bias + c0 + 8 * g);
+          const float4 bh = *reinterpret_cast<const float4*>(bias + c0 + 8 * g + 4);
+          const float bv[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
           __align__(16) __nv_bfloat162 hb[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int c = c0 + 8 * g + 2 * i;
-            hb[i] = __floats2bfloat162_rn(fmaxf(v[8 * g + 2 * i] + bias[c], 0.f),
-                                          fmaxf(v[8 * g + 2 * i + 1] + bias[c + 1], 0.f));
-          }
+          for (int i = 0; i < 4; ++i)
+            hb[i] = __floats2bfloat162_rn(fmaxf(v[8 * g + 2 * i] + bv[2 * i], 0.f),
+                                          fmaxf(v[8 * g + 2 * i + 1] + bv[2 * i + 1], 0.f));
           *reinterpret_cast<uint4*>(base + ((c0 >> 3) + g) * 128) = *reinterpret_cast<uint4*>(hb);
         }
       }
@@ -854,7 +872,7 @@ __global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
 
   // per-chain modes: this thread's chain, its previous layer word and the
   // running log q of the proposal
-  const int chain = r0 + tid;
+  const int chain = row;
   uint32_t prev = a.beta;
   if (MODE != kFusedLogits && chain < a.rows && jfirst > 1)
     prev = a.P[(size_t)chain * a.d + (jfirst - 2)];
@@ -863,10 +881,10 @@ __global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
   for (int jl = jfirst; jl <= jend; ++jl) {
     // ---- x tile (row = chain r0 + r at layer jl, or a staged input row)
     if (MODE == kFusedLogits) {
-      stage_rows(sX, a.X, kin, r0, 128, a.rows, 0, kin, tid, 128);
+      stage_rows(sX, a.X, kin, r0, 128, a.rows, 0, kin, tid, 256);
       tc::cp_async_wait_all();
     } else {
-      build_x_row(sX, kin, a.n, tid, prev, jl);
+      build_x_part(sX, kin, a.n, rl, prev, jl, half * (kin / 16), (half + 1) * (kin / 16));
     }
     publish();
 
@@ -928,8 +946,12 @@ __global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
       tc::mma_commit(done);
     }
     wait_done();
+    // logits of this thread's row (npad is 16 or 32); the row's bits are
+    // split between the two halves by Philox output (4 bits each):
+    // half h takes bits 4 g .. 4 g + 3 for the g with g % 2 == h
+    uint32_t word = 0u;
+    float sq = 0.f;
     if (ok) {
-      // logits of this thread's row (npad is 16 or 32)
       float l[32];
       if (npad > 16) {
         tc::tmem_ld32(taddr_row, l);
@@ -946,56 +968,68 @@ __global__ void __launch_bounds__(128) mlp_fused_kernel(FusedArgs a) {
       for (int i = 0; i < 32; ++i) l[i] += i < npad ? b3[i] : 0.f;
       if (row < a.rows) {
         if (MODE == kFusedLogits) {
+          if (half == 0) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (i < npad) a.logits[(size_t)row * npad + i] = l[i];
+            for (int i = 0; i < 32; ++i)
+              if (i < npad) a.logits[(size_t)row * npad + i] = l[i];
+          }
         } else if (MODE == kFusedLogQ) {
           // log q of the current layer word: sum_q log sigma(+-l_q)
           const uint32_t bits = a.P[(size_t)row * a.d + (jl - 1)];
-          float sq = 0.f;
 #pragma unroll
           for (int qb = 0; qb < 32; ++qb) {
-            if (qb < a.n) {
+            if (qb < a.n && ((qb >> 2) & 1) == half) {
               const float z = ((bits >> qb) & 1u) ? -l[qb] : l[qb];
-              sq -= fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z)));
+              sq -= fmaxf(z, 0.f) + softplus_tail(l[qb]);
             }
           }
-          a.lq[(size_t)row * a.d + (jl - 1)] = sq;
         } else {
           // draw s'_j bit by bit: u < sigmoid(l_q), u from Philox (chain,
           // move, (j-1) | tag 2 << 16, q/4)
           const uint32_t move = *a.move_dev;
           const uint32_t gc = a.group0 * 32u + (uint32_t)row;
-          uint32_t word = 0u;
-          float sq = 0.f;
           uint4 u4 = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
           for (int qb = 0; qb < 32; ++qb) {
-            if (qb < a.n) {
+            if (qb < a.n && ((qb >> 2) & 1) == half) {
               if ((qb & 3) == 0)
                 u4 = philox4x32_10(make_uint4(gc, move, (uint32_t)(jl - 1) | (kTagMH << 16),
                                               (uint32_t)(qb >> 2)), a.k0, a.k1);
               const uint32_t u = (qb & 3) == 0 ? u4.x : (qb & 3) == 1 ? u4.y : (qb & 3) == 2 ? u4.z : u4.w;
-              const float p1 = 1.f / (1.f + __expf(-l[qb]));
+              const float e = __expf(-fabsf(l[qb]));
+              const float r = __fdividef(1.f, 1.f + e);
+              const float p1 = l[qb] >= 0.f ? r : e * r;  // sigma(l)
               const float uf = ((float)(u >> 8) + 0.5f) * (1.f / 16777216.f);
               const uint32_t bit = uf < p1 ? 1u : 0u;
               word |= bit << qb;
               const float z = bit ? -l[qb] : l[qb];
-              sq -= fmaxf(z, 0.f) + log1pf(__expf(-fabsf(z)));
+              sq -= fmaxf(z, 0.f) + softplus_tail(l[qb]);
             }
           }
-          a.Pn[(size_t)row * a.d + (jl - 1)] = word;
-          lq_acc += sq;
-          prev = word;
         }
       }
     }
-    // the TMEM reads of this layer are complete before the next layer's MMAs
+    if (MODE != kFusedLogits) {
+      xw[half][rl] = word;
+      xq[half][rl] = sq;
+    }
+    // the TMEM reads of this layer are complete before the next layer's
+    // MMAs, and the halves' bits are exchanged
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    if (MODE != kFusedLogits && ok && row < a.rows) {
+      const float sql = xq[0][rl] + xq[1][rl];
+      if (MODE == kFusedLogQ) {
+        if (half == 0) a.lq[(size_t)row * a.d + (jl - 1)] = sql;
+      } else {
+        prev = xw[0][rl] | xw[1][rl];
+        if (half == 0) a.Pn[(size_t)row * a.d + (jl - 1)] = prev;
+        lq_acc += sql;
+      }
+    }
   }  // layers
-  if (MODE == kFusedSample && ok && row < a.rows) a.lqf[row] += lq_acc;
+  if (MODE == kFusedSample && ok && row < a.rows && half == 0) a.lqf[row] += lq_acc;
   if (!__syncthreads_and(ok)) {
     if (tid == 0) {
       if (a.status) atomicCAS(a.status, 0u, (uint32_t)PB_ETIMEOUT);
@@ -1046,7 +1080,7 @@ cudaError_t mlp_fused_logq(pb_mlp* p, const uint32_t* P, uint32_t beta, int chai
   dim3 grid((chains + 127) / 128, p->d - k + 1);
   const size_t smem = fused_layout(a);
   if (smem == 0) return cudaErrorInvalidValue;
-  mlp_fused_kernel<kFusedLogQ><<<grid, 128, smem, st>>>(a);
+  mlp_fused_kernel<kFusedLogQ><<<grid, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1069,7 +1103,7 @@ cudaError_t mlp_fused_sample(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uint32_
   a.group0 = group0;
   const size_t smem = fused_layout(a);
   if (smem == 0) return cudaErrorInvalidValue;
-  mlp_fused_kernel<kFusedSample><<<(chains + 127) / 128, 128, smem, st>>>(a);
+  mlp_fused_kernel<kFusedSample><<<(chains + 127) / 128, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1091,7 +1125,7 @@ cudaError_t mlp_forward_fused(pb_mlp* p, int rows) {
   a.n = p->n;
   const size_t smem = fused_layout(a);
   if (smem == 0) return cudaErrorInvalidValue;
-  mlp_fused_kernel<kFusedLogits><<<(rows + 127) / 128, 128, smem, p->st>>>(a);
+  mlp_fused_kernel<kFusedLogits><<<(rows + 127) / 128, 256, smem, p->st>>>(a);
   return cudaGetLastError();
 }
 
