@@ -46,7 +46,7 @@ def _load():
             lib.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
             lib.orc_philox4x32_10.restype = None
             for name in ("orc_statevector", "orc_pathsum_exact", "orc_gf2_rank",
-                         "orc_colour", "orc_gibbs", "orc_violations", "orc_path_phase",
+                         "orc_colour", "orc_gibbs", "orc_elim", "orc_violations", "orc_path_phase",
                          "orc_thresholds"):
                 getattr(lib, name).restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
@@ -164,6 +164,33 @@ def gibbs(n: int, d: int, gates, *, J: float, seed: int, chains: int, sweeps: in
                        _p(cnt), ctypes.byref(valid), ctypes.byref(samples))
     if rc != 0:
         raise ValueError(f"orc_gibbs failed ({rc})")
+    return {"state": st, "cnt": cnt, "valid": valid.value, "samples": samples.value}
+
+
+def elim(n: int, d: int, gates, *, seed: int, chains: int, sweeps: int, beta: int = 0,
+         chain0: int = 0, sweep0: int = 0, burn_in: int = 0, record_every: int = 1, alphas=None):
+    """Exact i.i.d. path sampler on the eliminated network (R2).  Returns
+    dict(state[chains, d] u32 = each chain's last drawn path, cnt[bins, 8]
+    u64, valid, samples)."""
+    lib = _load()
+    g = _gates(gates)
+    st = np.zeros((chains, d), dtype=np.uint32)
+    if alphas is None:
+        bins = 1 << n
+        al = None
+    else:
+        al = np.ascontiguousarray(alphas, dtype=np.uint32)
+        bins = len(al)
+    cnt = np.zeros((bins, 8), dtype=np.uint64)
+    valid = ctypes.c_uint64(0)
+    samples = ctypes.c_uint64(0)
+    rc = lib.orc_elim(n, d, _p(g), len(g), ctypes.c_uint32(beta), ctypes.c_uint64(seed),
+                      ctypes.c_uint32(chain0), ctypes.c_uint32(chains), ctypes.c_uint32(sweep0),
+                      ctypes.c_uint32(sweeps), ctypes.c_uint32(burn_in), ctypes.c_uint32(record_every),
+                      _p(st), None if al is None else _p(al), 0 if al is None else len(al),
+                      _p(cnt), ctypes.byref(valid), ctypes.byref(samples))
+    if rc != 0:
+        raise ValueError(f"orc_elim failed ({rc})")
     return {"state": st, "cnt": cnt, "valid": valid.value, "samples": samples.value}
 
 

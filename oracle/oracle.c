@@ -29,6 +29,9 @@
  *                       e^{-J}"), following the Fig. 2 flowchart: propose by
  *                       heat-bath (Glauber) on Re E, accept, add the phase
  *                       exp(-i Im E) to the bin of the end state.
+ *   orc_elim            exact i.i.d. path sampler on the eliminated network
+ *                       (Appendix: non-H bits as functions of the previous
+ *                       layer, H outputs fair coins), recorded like orc_gibbs.
  *
  * Parity status: every function is pinned by tests under tests/ (hand-worked
  * values of Sec. 4, Eq. stdT, norm invariants, exact agreement of the path sum
@@ -597,6 +600,107 @@ int orc_gibbs(int n, int d, const orc_gate* g, int ng, uint32_t beta, double J,
         }
       }
       for (int k = 1; k <= d; ++k) st[k - 1] = s[k];
+    }
+#pragma omp critical
+    {
+      if (my_cnt)
+        for (uint64_t i = 0; i < bins * 8; ++i) cnt[i] += my_cnt[i];
+      *valid_total += my_valid;
+      *samples_total += my_samples;
+    }
+    free(my_cnt);
+    free(s);
+  }
+  free(net.gate_of);
+  return err ? -4 : 0;
+}
+
+/* Exact path sampler on the eliminated network (R2; Appendix: with the
+ * J-penalty links removed, the non-H bits are functions of the previous
+ * layer and each H output is a free fair coin).  A sample is one pass from
+ * the clamped input: layer by layer, an H output (k, q) of chain c at
+ * sample t is bit (c mod 32) of word 0 of Philox(c >> 5, t, p | 4 << 16, 0),
+ * p = (k-1) n + q; every other bit is its gate's deterministic value.  The
+ * path is valid by construction, so every recorded sample adds one count to
+ * (end state, phase) (Fig. 2 Step 3) and the samples are i.i.d. and uniform
+ * over the 2^h valid paths.
+ *
+ *   sweep0, sweeps, burn_in, record_every: sample indices t = sweep0 ..
+ *       sweep0 + sweeps - 1; only recorded ones (t >= burn_in and
+ *       (t - burn_in) % record_every == 0) are drawn.
+ *   state (optional, chains x d): the last drawn path of each chain.
+ *   alphas, cnt, valid_total, samples_total: as for orc_gibbs. */
+int orc_elim(int n, int d, const orc_gate* g, int ng, uint32_t beta, uint64_t seed,
+             uint32_t chain0, uint32_t chains, uint32_t sweep0, uint32_t sweeps,
+             uint32_t burn_in, uint32_t record_every, uint32_t* state,
+             const uint32_t* alphas, int n_alphas, uint64_t* cnt, uint64_t* valid_total,
+             uint64_t* samples_total) {
+  if (check_circuit(n, d, g, ng) != 0) return -1;
+  if (record_every == 0) return -1;
+  if (!alphas && n > 24) return -2;
+  orc_net net = {n, d, ng, g, (int32_t*)malloc((size_t)n * d * sizeof(int32_t))};
+  if (!net.gate_of) return -3;
+  memset(net.gate_of, -1, (size_t)n * d * sizeof(int32_t));
+  for (int i = 0; i < ng; ++i) {
+    net.gate_of[g[i].layer * n + g[i].q0] = i;
+    if (gate_arity(g[i].op) == 2) net.gate_of[g[i].layer * n + g[i].q1] = i;
+  }
+  const uint32_t nmask = (n == 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  const uint64_t bins = alphas ? (uint64_t)n_alphas : (1ull << n);
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  int err = 0;
+
+#pragma omp parallel reduction(| : err)
+  {
+    uint64_t* my_cnt = (uint64_t*)calloc(bins * 8, sizeof(uint64_t));
+    uint64_t my_valid = 0, my_samples = 0;
+    uint32_t* s = (uint32_t*)calloc((size_t)d + 1, sizeof(uint32_t));
+    if (!my_cnt || !s) err = 1;
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t ci = 0; ci < (int64_t)chains; ++ci) {
+      if (err) continue;
+      const uint32_t chain = chain0 + (uint32_t)ci;
+      int drawn = 0;
+      for (uint32_t i = 0; i < sweeps; ++i) {
+        const uint32_t t = sweep0 + i;
+        if (!(t >= burn_in && (t - burn_in) % record_every == 0)) continue;
+        s[0] = beta & nmask;
+        for (int k = 1; k <= d; ++k) {
+          uint32_t w = 0;
+          for (int q = 0; q < n; ++q) {
+            const int gi = net.gate_of[(k - 1) * n + q];
+            int b;
+            if (gi >= 0 && g[gi].op == ORC_H) {
+              const uint32_t p = (uint32_t)((k - 1) * n + q);
+              uint32_t ctr[4] = {chain >> 5, t, p | (4u << 16), 0}, out[4];
+              orc_philox4x32_10(ctr, key, out);
+              b = (int)((out[0] >> (chain & 31)) & 1u);
+            } else if (gi < 0) {
+              b = bit(s[k - 1], q);
+            } else {
+              const orc_gate* G = &g[gi];
+              const int ystar = det_output(G->op, gate_index(G, s[k - 1]));
+              b = (q == G->q0) ? (ystar & 1) : ((ystar >> 1) & 1);
+            }
+            w |= (uint32_t)b << q;
+          }
+          s[k] = w;
+        }
+        drawn = 1;
+        ++my_samples;
+        if (total_violations(&net, s) != 0) { err = 1; break; }  /* cannot happen */
+        ++my_valid;
+        const int ph = path_phase(&net, s);
+        if (ph < 0) { err = 1; break; }
+        if (alphas) {
+          for (int a = 0; a < n_alphas; ++a)
+            if (alphas[a] == s[d]) { my_cnt[(uint64_t)a * 8 + ph] += 1; break; }
+        } else {
+          my_cnt[(uint64_t)s[d] * 8 + ph] += 1;
+        }
+      }
+      if (state && drawn)
+        for (int k = 1; k <= d; ++k) state[(size_t)ci * d + k - 1] = s[k];
     }
 #pragma omp critical
     {
