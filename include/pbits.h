@@ -109,7 +109,18 @@ PB_API void pb_model_free(pb_model* m);
  * tag 1 = initial H outputs).  A p-bit whose violation count changes by v
  * when it goes 0 -> 1 is redrawn as [v < 0] XOR [u < thr[|v|]]  (heat-bath,
  * Fig. 2 Steps 1-2).  One sweep visits the four colour classes in order. */
-enum { PB_GIBBS = 0, PB_LEARNED = 1 };
+enum { PB_GIBBS = 0, PB_LEARNED = 1, PB_ELIM = 2 };
+/* PB_ELIM: the exact sampler on the eliminated network (Appendix: without
+ * the link constraints every non-H bit is a function of the previous layer
+ * and each H output a fair coin).  A "sweep" of such a run draws, for every
+ * chain, a fresh path from the clamped input: H output p = (k-1) n + q of
+ * chain c at sample t is bit c % 32 of word 0 of Philox4x32-10 at counter
+ * (c / 32, t, p | 4 << 16, 0), every other bit its deterministic value; each
+ * recorded sample is valid and is binned like a Gibbs sample.  The samples
+ * are i.i.d. and uniform over the 2^h valid paths (the comparator for the
+ * Gibbs and learned samplers).  All models of a run use one sampler;
+ * pb_run_set_shape / pb_run_tune have no effect on a PB_ELIM run and the
+ * learned-proposal calls reject it. */
 
 typedef struct {
   uint64_t seed;          /* Philox key                                        */
@@ -120,7 +131,7 @@ typedef struct {
   uint32_t n_batches;     /* SE batches over chain groups (0 = automatic)      */
   const uint32_t* alphas; /* bins to record; NULL = full 2^n histogram (n<=22)  */
   int32_t n_alphas;
-  int32_t sampler;        /* PB_GIBBS or PB_LEARNED                            */
+  int32_t sampler;        /* PB_GIBBS or PB_ELIM (PB_LEARNED: see pb_mh_create) */
   const pb_mlp* proposal; /* trained MLP for PB_LEARNED, else NULL             */
   uint32_t mh_every;      /* PB_LEARNED: one suffix MH move every mh_every sweeps */
   uint32_t group0;        /* global index of the first chain group: the chains

@@ -86,6 +86,7 @@ struct WsHeader {
 constexpr uint32_t kTagSweep = 0;
 constexpr uint32_t kTagInit = 1;
 constexpr uint32_t kTagMH = 2;
+constexpr uint32_t kTagElim = 4;  // exact sampler's H outputs (tag 3: training rows)
 
 }  // namespace pb
 

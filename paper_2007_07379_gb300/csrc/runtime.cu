@@ -26,6 +26,10 @@ cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, cons
                                      uint32_t n_work, uint32_t n_sweeps, int cons, int prod,
                                      int max_col, int grid, size_t smem_bytes, WsHeader* hdr,
                                      cudaStream_t st);
+cudaError_t launch_elim(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
+                        const uint32_t* const* d_init_tabs, uint32_t n_sweeps, size_t smem_bytes,
+                        WsHeader* hdr, cudaStream_t st);
+size_t elim_smem_bytes(int n, int d);
 cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
                               cudaStream_t st);
 cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t count,
@@ -282,7 +286,8 @@ int check_cfg(const pb_model* m, const pb_run_cfg& c) {
   if (!m) return PB_EINVAL;
   if (c.chains == 0 || c.record_every == 0) return PB_EINVAL;
   if ((uint64_t)c.group0 + (c.chains + 31) / 32 > 0xFFFFFFFFull) return PB_ERANGE;
-  if (c.sampler != PB_GIBBS) return PB_EINVAL;  // the learned sampler has its own entry points
+  // the learned sampler has its own entry points (pb_mh_*) on a PB_GIBBS run
+  if (c.sampler != PB_GIBBS && c.sampler != PB_ELIM) return PB_EINVAL;
   if (c.alphas == nullptr) {
     if (c.n_alphas != 0) return PB_EINVAL;
     if (m->n > 22) return PB_ERANGE;
@@ -358,6 +363,8 @@ struct pb_run {
   int cons = 32, prod = 32, max_col = 1, blocks_per_sm = 0;
   size_t smem = 0;
   bool persistent = false;
+  bool elim = false;       // PB_ELIM run: exact i.i.d. paths instead of sweeps
+  size_t elim_smem = 0;
   int grid = 0;
   uint64_t sweeps_done = 0;
   double flips_per_sweep = 0.0;
@@ -469,6 +476,11 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
   r->nm = n_models;
   r->cfgs.assign(cfgs, cfgs + n_models);
   for (int i = 0; i < n_models; ++i) r->models.emplace_back(new pb_model(*models[i]));
+  // one sampler per run
+  for (int i = 1; i < n_models; ++i)
+    if (cfgs[i].sampler != cfgs[0].sampler) return PB_EINVAL;
+  r->elim = cfgs[0].sampler == PB_ELIM;
+  for (auto& m : r->models) r->elim_smem = std::max(r->elim_smem, elim_smem_bytes(m->n, m->d));
 
   cudaStream_t st = r->st;
   char* ws = r->ws;
@@ -594,7 +606,11 @@ PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
       return PB_ECUDA;
     cudaError_t e = cudaStreamBeginCapture(r->cap_st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return PB_ECUDA;
-    if (r->persistent)
+    if (r->elim)
+      e = launch_elim(r->d_rm(), r->nm, r->total_groups,
+                      reinterpret_cast<const uint32_t* const*>(r->ws + r->L.init_ptrs), n_sweeps,
+                      r->elim_smem, r->hdr(), r->cap_st);
+    else if (r->persistent)
       e = launch_sweeps_persistent(r->d_rm(), r->nm, reinterpret_cast<const uint32_t*>(r->ws + r->L.work),
                                    r->total_groups, n_sweeps, r->cons, r->prod, r->max_col, r->grid,
                                    r->smem, r->hdr(), r->cap_st);
@@ -726,6 +742,10 @@ PB_API int pb_run_get_shape(const pb_run* r, int* consumers, int* producers, int
 // chains) is reused without trials and new results are appended.
 PB_API int pb_run_tune(pb_run* r, uint32_t trial_sweeps, const char* cache_path, double* best_ms) {
   if (!r || trial_sweeps == 0) return PB_EINVAL;
+  if (r->elim) {  // one fixed shape
+    if (best_ms) *best_ms = 0.0;
+    return PB_OK;
+  }
   // key: the run's shapes
   uint64_t key = 1469598103934665603ull;
   auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
@@ -890,6 +910,7 @@ PB_API void pb_run_free(pb_run* r) {
 namespace pb {
 int run_view(const pb_run* r, int model, RunView* out) {
   if (!r || !out || model < 0 || model >= r->nm) return PB_EINVAL;
+  if (r->elim) return PB_EINVAL;  // moves act on Gibbs chains
   out->st = r->st;
   out->state = r->rm[model].state;
   out->model = r->models[model].get();

@@ -637,6 +637,99 @@ __global__ void init_kernel(const RunModelDev* __restrict__ rm, int n_models,
 }
 
 // ---------------------------------------------------------------------------
+// Exact path sampler on the eliminated network (R2; Appendix: without the
+// link constraints the non-H bits are functions of the previous layer and
+// each H output is a fair coin).  Each recorded sample draws a fresh path
+// from the clamped input, layer by layer -- an H output (k, q) of chain c at
+// sample t is bit (c mod 32) of word 0 of Philox(c / 32, t, p | 4 << 16, 0),
+// every other bit the XOR of two words given by the init table -- and
+// records it (Fig. 2 Step 3; every path is valid).  One CTA per chain group;
+// warp w takes the launch's samples w, w + kElimWarps, ... in its own
+// shared-memory image; lane q writes word q of a layer.
+constexpr int kElimWarps = 8;
+
+__global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
+    const RunModelDev* __restrict__ rm, int n_models, uint32_t total_groups,
+    const uint32_t* const* __restrict__ init_tabs, uint32_t n_sweeps, WsHeader* hdr) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t sweep0 = hdr->sweep0;
+  const uint32_t flat = blockIdx.x;
+  if (flat >= total_groups) return;
+  const int mi = find_model(rm, n_models, flat);
+  const RunModelDev& r = rm[mi];
+  const uint32_t g = flat - r.group_base;
+  if (g >= r.groups) return;
+  const ModelDev md = *r.model;
+  const int n = md.n, d = md.d, nw = md.nw, npb = n * d;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* W = smem + warp * image_words(n, d);
+  const uint32_t* itab = init_tabs[mi];  // per p-bit: 0xFFFFFFFF = H, else a | b << 16
+  // record terms index the image: a bad table is reported, never followed
+  int bad = 0;
+  for (int i = threadIdx.x; i < npb; i += blockDim.x) {
+    const Rec R = r.rec[i];
+    bad |= (R.vd >= nw || R.va >= nw || R.vb >= nw || R.pa >= nw || R.pb >= nw) ? 1 : 0;
+  }
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0) set_status(hdr, PB_EINVAL);
+    return;
+  }
+  for (int i = lane; i < nw; i += 32) {
+    uint32_t v = 0u;
+    if (i < n) v = ((md.beta >> i) & 1u) ? ~0u : 0u;  // clamped input layer
+    else if (i == ones_idx(n, d)) v = ~0u;
+    W[i] = v;
+  }
+  __syncwarp();
+  auto recorded = [&](uint32_t t) {
+    return t >= r.burn_in && (r.record_every == 1u || (t - r.burn_in) % r.record_every == 0);
+  };
+  const uint32_t gglob = g + r.group0, batch = g % r.n_batches;
+  Recorder rec;
+  unsigned long long n_valid = 0ull, n_samples = 0ull;
+#pragma unroll 1
+  for (uint32_t i = (uint32_t)warp; i < n_sweeps; i += kElimWarps) {
+    const uint32_t t = sweep0 + i;
+    if (!recorded(t)) continue;
+#pragma unroll 1
+    for (int k = 1; k <= d; ++k) {
+      if (lane < n) {
+        const int p = (k - 1) * n + lane;
+        const uint32_t e = itab[p];
+        uint32_t v;
+        if (e == 0xFFFFFFFFu) {
+          v = philox4x32_10(make_uint4(gglob, t, (uint32_t)p | (kTagElim << 16), 0u), r.seed_lo,
+                            r.seed_hi).x;
+        } else {
+          const uint32_t a = e & 0xFFFFu, b = e >> 16;
+          if ((int)a >= nw || (int)b >= nw) { set_status(hdr, PB_EINVAL); v = 0u; }
+          else v = W[a] ^ W[b];
+        }
+        W[k * n + lane] = v;
+      }
+      __syncwarp();
+    }
+    rec.clear();
+    rec.read(W, r.rec, 0, npb, lane);
+    rec.reduce(W, n, d, lane);
+    rec.bin(r, g, batch, lane, nullptr, n_valid, n_samples);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (n_valid) atomicAdd(&r.valid[batch], n_valid);
+    if (n_samples) atomicAdd(&r.samples[batch], n_samples);
+  }
+  // the group's state: the path of the launch's last recorded sample
+  int last = -1;
+  for (int i = (int)n_sweeps - 1; i >= 0; --i)
+    if (recorded(sweep0 + (uint32_t)i)) { last = i; break; }
+  if (last >= 0 && warp == last % kElimWarps) {
+    uint32_t* out = r.state + (size_t)g * npb;
+    for (int i = lane; i < npb; i += 32) out[i] = W[n + i];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Amplitudes (Eq. U23 with uniform valid paths, exact integer phase classes):
 //   Z = sum_b cnt_b w^b = (c0 - c4) + (c1 - c3 - c5 + c7)/sqrt2
 //                      + i[(c2 - c6) + (c1 + c3 - c5 - c7)/sqrt2]
@@ -777,6 +870,17 @@ cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, cons
   return cudaGetLastError();
 }
 
+cudaError_t launch_elim(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
+                        const uint32_t* const* d_init_tabs, uint32_t n_sweeps, size_t smem_bytes,
+                        WsHeader* hdr, cudaStream_t st) {
+  elim_kernel<<<total_groups, kElimWarps * 32, smem_bytes, st>>>(d_rm, n_models, total_groups,
+                                                                 d_init_tabs, n_sweeps, hdr);
+  advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
+  return cudaGetLastError();
+}
+
+size_t elim_smem_bytes(int n, int d) { return (size_t)kElimWarps * image_words(n, d) * 4; }
+
 cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
                               cudaStream_t st) {
   const int tpb = 256;
@@ -801,6 +905,8 @@ size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins)
 cudaError_t sweep_prepare() {
   cudaError_t e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(elim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(sweep_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               200 * 1024);
