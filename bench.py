@@ -321,6 +321,7 @@ def main():
     extra = {}
     if rank == 0 and not args.no_extra:
         extra["batched"] = batched_measurement(dev, stream)
+        extra["elim"] = elim_measurement(dev, stream)
         extra["large"] = large_measurement(dev, stream)
 
     learned = None
@@ -419,10 +420,53 @@ def learned_comparison(dev, stream, seconds: float = 8.0, train_paths: int = 1_0
                 res["ms_per_move_and_sweep"] = 1e3 * t / max(mv, 1)
             return res
 
+        def timed_elim():
+            # the i.i.d. ceiling: exact paths on the eliminated network
+            run = pbits.Run([model], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, n_batches=32,
+                                                   sampler=pbits.PB_ELIM)], stream=stream)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            steps = 0
+            while time.perf_counter() - t0 < seconds:
+                run.sweeps(200)
+                run.wait()
+                steps += 200
+            t = time.perf_counter() - t0
+            psi, se = run.amplitudes()
+            se_rms = float(np.sqrt(np.mean(se ** 2)))
+            return {"wall_s": t, "samples_per_chain": steps, "se_rms": se_rms, "se_psi0": float(se[0]),
+                    "t_to_eps_s": t * (se_rms / 0.01) ** 2}
+
         out["plain"] = timed(False)
         out["learned"] = timed(True)
+        out["elim"] = timed_elim()
         out["ratio_plain_over_learned"] = out["plain"]["t_to_eps_s"] / out["learned"]["t_to_eps_s"]
+        out["ratio_elim_over_learned"] = out["elim"]["t_to_eps_s"] / out["learned"]["t_to_eps_s"]
     return out
+
+
+def elim_measurement(dev, stream, samples: int = 10_000):
+    """Exact i.i.d. path sampler (PB_ELIM) on the mid workload: path samples
+    per second and the equivalent p-bit assignments per second."""
+    import torch
+    from paper_2007_07379_gb300 import pbits
+    wl = W.mid()
+    with torch.cuda.stream(stream):
+        m = pbits.Model(wl.n, wl.d, wl.gates, wl.J)
+        run = pbits.Run([m], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, sampler=pbits.PB_ELIM)],
+                        stream=stream)
+        run.sweeps(samples)
+        run.wait()
+        best = None
+        for _ in range(3):
+            run.sweeps(samples)
+            run.wait()
+            ms = run.stats()["last_ms"]
+            best = ms if best is None else min(best, ms)
+    return {"workload": f"mid (n={wl.n}, d={wl.d}), {wl.chains} chains, exact i.i.d. paths",
+            "samples": samples, "launch_ms": best,
+            "paths_per_s": wl.chains * samples / (best / 1e3),
+            "pbit_assignments_per_s": wl.chains * wl.n * wl.d * samples / (best / 1e3)}
 
 
 def batched_measurement(dev, stream, sweeps: int = 10_000):
