@@ -46,7 +46,7 @@ def _load():
             lib.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
             lib.orc_philox4x32_10.restype = None
             for name in ("orc_statevector", "orc_pathsum_exact", "orc_gf2_rank",
-                         "orc_colour", "orc_gibbs", "orc_elim", "orc_violations", "orc_path_phase",
+                         "orc_colour", "orc_gibbs", "orc_elim", "orc_elim_clamped", "orc_violations", "orc_path_phase",
                          "orc_thresholds"):
                 getattr(lib, name).restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
@@ -192,6 +192,36 @@ def elim(n: int, d: int, gates, *, seed: int, chains: int, sweeps: int, beta: in
     if rc != 0:
         raise ValueError(f"orc_elim failed ({rc})")
     return {"state": st, "cnt": cnt, "valid": valid.value, "samples": samples.value}
+
+
+def elim_clamped(n: int, d: int, gates, *, alpha: int, seed: int, chains: int, sweeps: int,
+                 beta: int = 0, chain0: int = 0, sweep0: int = 0, burn_in: int = 0,
+                 record_every: int = 1):
+    """Exact sampler with the end state clamped to alpha.  Returns
+    dict(state, cnt[8] u64, samples, consistent, nfree, rank)."""
+    lib = _load()
+    g = _gates(gates)
+    st = np.zeros((chains, d), dtype=np.uint32)
+    cnt = np.zeros(8, dtype=np.uint64)
+    samples = ctypes.c_uint64(0)
+    cons, nfree, rank = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    rc = lib.orc_elim_clamped(n, d, _p(g), len(g), ctypes.c_uint32(beta), ctypes.c_uint32(alpha),
+                              ctypes.c_uint64(seed), ctypes.c_uint32(chain0), ctypes.c_uint32(chains),
+                              ctypes.c_uint32(sweep0), ctypes.c_uint32(sweeps), ctypes.c_uint32(burn_in),
+                              ctypes.c_uint32(record_every), _p(st), _p(cnt), ctypes.byref(samples),
+                              ctypes.byref(cons), ctypes.byref(nfree), ctypes.byref(rank))
+    if rc != 0:
+        raise ValueError(f"orc_elim_clamped failed ({rc})")
+    return {"state": st, "cnt": cnt, "samples": samples.value, "consistent": bool(cons.value),
+            "nfree": nfree.value, "rank": rank.value}
+
+
+def clamped_amplitude(cnt8: np.ndarray, samples: int, h: int, rank: int) -> complex:
+    """2^{h/2 - r} sum_phi cnt[phi] w^phi / T (0 when nothing was drawn)."""
+    if samples == 0:
+        return 0j
+    w = np.exp(1j * np.pi / 4 * np.arange(8))
+    return complex(2.0 ** (h / 2 - rank) * np.sum(np.asarray(cnt8, dtype=np.float64) * w) / samples)
 
 
 def violations(n: int, d: int, gates, state: np.ndarray, beta: int = 0) -> np.ndarray:

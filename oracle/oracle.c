@@ -32,6 +32,9 @@
  *   orc_elim            exact i.i.d. path sampler on the eliminated network
  *                       (Appendix: non-H bits as functions of the previous
  *                       layer, H outputs fair coins), recorded like orc_gibbs.
+ *   orc_elim_clamped    the same with the end state fixed to one output
+ *                       alpha (uniform over the paths to alpha, by GF(2)
+ *                       elimination).
  *
  * Parity status: every function is pinned by tests under tests/ (hand-worked
  * values of Sec. 4, Eq. stdT, norm invariants, exact agreement of the path sum
@@ -712,6 +715,150 @@ int orc_elim(int n, int d, const orc_gate* g, int ng, uint32_t beta, uint64_t se
     free(my_cnt);
     free(s);
   }
+  free(net.gate_of);
+  return err ? -4 : 0;
+}
+
+/* End state s_d of the path whose H outputs (in p order) are x[0..h-1]. */
+static uint32_t propagate_with(const orc_net* net, uint32_t beta, const uint8_t* x, uint32_t* s) {
+  const int n = net->n, d = net->d;
+  const uint32_t nmask = (n == 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  int j = 0;
+  s[0] = beta & nmask;
+  for (int k = 1; k <= d; ++k) {
+    uint32_t w = 0;
+    for (int q = 0; q < n; ++q) {
+      const int gi = net->gate_of[(k - 1) * n + q];
+      int b;
+      if (gi >= 0 && net->g[gi].op == ORC_H) {
+        b = x[j++];
+      } else if (gi < 0) {
+        b = bit(s[k - 1], q);
+      } else {
+        const orc_gate* G = &net->g[gi];
+        const int ystar = det_output(G->op, gate_index(G, s[k - 1]));
+        b = (q == G->q0) ? (ystar & 1) : ((ystar >> 1) & 1);
+      }
+      w |= (uint32_t)b << q;
+    }
+    s[k] = w;
+  }
+  return s[d];
+}
+
+/* Output-clamped exact sampler ("for a given input beta and output alpha",
+ * Sec. 3, with the eliminated network of the Appendix).  Every wire bit is
+ * an affine function over GF(2) of the H outputs x (in p order), so
+ * s_d = A x + c, and the valid paths ending at alpha are the solutions of
+ * A x = alpha + c: an affine subspace of dimension h - r, or none.  A and c
+ * come from h + 1 probe paths (x = 0 and the unit vectors).  With the
+ * reduced row echelon form of [A | alpha + c] (unique), the free variables
+ * (non-pivot columns, increasing) take the draws z_0, z_1, ..., and each
+ * pivot variable is its row's right-hand side XOR the free variables in
+ * that row.  Draw z_b of chain c at sample t: bit (c mod 32) of word b mod 4
+ * of Philox(c >> 5, t, (b >> 2) | 5 << 16, 0).  Each recorded sample adds one
+ * count to cnt[phase]; the estimator of U_{alpha,beta} =
+ * 2^{-h/2} sum_{paths to alpha} w^phase is 2^{h/2 - r} sum_phi cnt[phi] w^phi / T.
+ *
+ *   consistent_out : 1 if alpha is reachable (else no sample is drawn).
+ *   nfree_out, rank_out : h - r and r.
+ *   state (optional, chains x d): the last drawn path of each chain. */
+int orc_elim_clamped(int n, int d, const orc_gate* g, int ng, uint32_t beta, uint32_t alpha,
+                     uint64_t seed, uint32_t chain0, uint32_t chains, uint32_t sweep0,
+                     uint32_t sweeps, uint32_t burn_in, uint32_t record_every, uint32_t* state,
+                     uint64_t* cnt8, uint64_t* samples_total, int* consistent_out,
+                     int* nfree_out, int* rank_out) {
+  if (check_circuit(n, d, g, ng) != 0) return -1;
+  if (record_every == 0) return -1;
+  orc_net net = {n, d, ng, g, (int32_t*)malloc((size_t)n * d * sizeof(int32_t))};
+  if (!net.gate_of) return -3;
+  memset(net.gate_of, -1, (size_t)n * d * sizeof(int32_t));
+  for (int i = 0; i < ng; ++i) {
+    net.gate_of[g[i].layer * n + g[i].q0] = i;
+    if (gate_arity(g[i].op) == 2) net.gate_of[g[i].layer * n + g[i].q1] = i;
+  }
+  int h = 0;
+  for (int i = 0; i < ng; ++i) h += g[i].op == ORC_H;
+  /* augmented matrix M[row q][col j], col h = right-hand side */
+  uint8_t* M = (uint8_t*)calloc((size_t)n * (h + 1), 1);
+  uint8_t* x = (uint8_t*)calloc((size_t)h + 1, 1);
+  uint32_t* s = (uint32_t*)calloc((size_t)d + 1, sizeof(uint32_t));
+  int* pivot_col = (int*)malloc(sizeof(int) * (size_t)(n + 1));
+  int* free_col = (int*)malloc(sizeof(int) * (size_t)(h + 1));
+  if (!M || !x || !s || !pivot_col || !free_col) return -3;
+  const uint32_t c0 = propagate_with(&net, beta, x, s);
+  for (int j = 0; j < h; ++j) {
+    x[j] = 1;
+    const uint32_t cj = propagate_with(&net, beta, x, s);
+    x[j] = 0;
+    for (int q = 0; q < n; ++q) M[(size_t)q * (h + 1) + j] = (uint8_t)bit(cj ^ c0, q);
+  }
+  for (int q = 0; q < n; ++q) M[(size_t)q * (h + 1) + h] = (uint8_t)bit(alpha ^ c0, q);
+  /* Gauss-Jordan elimination over GF(2) */
+  int r = 0;
+  for (int j = 0; j < h && r < n; ++j) {
+    int piv = -1;
+    for (int q = r; q < n; ++q)
+      if (M[(size_t)q * (h + 1) + j]) { piv = q; break; }
+    if (piv < 0) continue;
+    if (piv != r)
+      for (int c = 0; c <= h; ++c) {
+        uint8_t t = M[(size_t)piv * (h + 1) + c];
+        M[(size_t)piv * (h + 1) + c] = M[(size_t)r * (h + 1) + c];
+        M[(size_t)r * (h + 1) + c] = t;
+      }
+    for (int q = 0; q < n; ++q)
+      if (q != r && M[(size_t)q * (h + 1) + j])
+        for (int c = 0; c <= h; ++c) M[(size_t)q * (h + 1) + c] ^= M[(size_t)r * (h + 1) + c];
+    pivot_col[r++] = j;
+  }
+  int consistent = 1;
+  for (int q = r; q < n; ++q)
+    if (M[(size_t)q * (h + 1) + h]) consistent = 0;
+  int nfree = 0;
+  for (int j = 0, i = 0; j < h; ++j) {
+    if (i < r && pivot_col[i] == j) { ++i; continue; }
+    free_col[nfree++] = j;
+  }
+  *consistent_out = consistent;
+  *nfree_out = nfree;
+  *rank_out = r;
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  int err = 0;
+  uint64_t my_samples = 0;
+  if (consistent) {
+    for (uint32_t ci = 0; ci < chains && !err; ++ci) {
+      const uint32_t chain = chain0 + ci;
+      int drawn = 0;
+      for (uint32_t i = 0; i < sweeps; ++i) {
+        const uint32_t t = sweep0 + i;
+        if (!(t >= burn_in && (t - burn_in) % record_every == 0)) continue;
+        /* free variables from the draws, pivots from their rows */
+        for (int b = 0; b < nfree; ++b) {
+          uint32_t ctr[4] = {chain >> 5, t, ((uint32_t)b >> 2) | (5u << 16), 0}, out[4];
+          orc_philox4x32_10(ctr, key, out);
+          x[free_col[b]] = (uint8_t)((out[b & 3] >> (chain & 31)) & 1u);
+        }
+        for (int row = 0; row < r; ++row) {
+          uint8_t v = M[(size_t)row * (h + 1) + h];
+          for (int b = 0; b < nfree; ++b)
+            if (M[(size_t)row * (h + 1) + free_col[b]]) v ^= x[free_col[b]];
+          x[pivot_col[row]] = v;
+        }
+        if (propagate_with(&net, beta, x, s) != alpha) { err = 1; break; }
+        if (total_violations(&net, s) != 0) { err = 1; break; }
+        const int ph = path_phase(&net, s);
+        if (ph < 0) { err = 1; break; }
+        cnt8[ph] += 1;
+        ++my_samples;
+        drawn = 1;
+      }
+      if (state && drawn)
+        for (int k = 1; k <= d; ++k) state[(size_t)ci * d + k - 1] = s[k];
+    }
+  }
+  *samples_total += my_samples;
+  free(M); free(x); free(s); free(pivot_col); free(free_col);
   free(net.gate_of);
   return err ? -4 : 0;
 }

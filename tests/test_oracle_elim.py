@@ -107,3 +107,63 @@ def test_differs_from_the_gibbs_init_stream():
     e = oracle.elim(n, d, g, seed=9, chains=64, sweeps=1)
     gi = oracle.gibbs(n, d, g, J=3.0, seed=9, chains=64, sweeps=0)
     assert not np.array_equal(e["state"], gi["state"])
+
+
+# ---- the output-clamped sampler (end state fixed to alpha, GF(2) elimination)
+
+def _hkeys(g, d, state):
+    return state & _hmask(g, d)
+
+
+def test_clamped_paths_end_at_alpha_and_are_uniform():
+    """The paths to alpha form an affine space of dimension h - r: every draw
+    is a valid path ending at alpha, the draws are uniform over the 2^{h-r}
+    paths (chi-square), and nfree + rank = h with the rank of orc_gf2_rank."""
+    n, d = 4, 8
+    g = W.random_circuit(n, d, seed=17)
+    h, rank = oracle.gf2_rank(n, d, g)
+    assert 3 <= h - rank <= 8
+    exact = oracle.statevector(n, d, g)
+    a = int(np.argmax(np.abs(exact)))
+    r = oracle.elim_clamped(n, d, g, alpha=a, seed=2, chains=8192, sweeps=1)
+    assert r["consistent"] and r["nfree"] == h - rank and r["rank"] == rank
+    assert r["samples"] == 8192
+    st = r["state"]
+    assert np.all(st[:, d - 1] == a)
+    assert np.all(oracle.violations(n, d, g, st) == 0)
+    uniq, counts = np.unique(_hkeys(g, d, st), axis=0, return_counts=True)
+    assert len(uniq) == 2 ** (h - rank)
+    from scipy.stats import chisquare
+    assert chisquare(counts).pvalue > 1e-4
+
+
+def test_clamped_amplitudes_within_5_se():
+    """Per sample X = 2^{h/2-r} w^phase with E X = psi_alpha, so
+    SE = sqrt((2^{h-2r} - |psi_alpha|^2) / T); an unreachable alpha draws
+    nothing and has psi_alpha = 0 exactly."""
+    for n, d, seed in ((4, 8, 17), (5, 6, 3), (3, 9, 12)):
+        g = W.random_circuit(n, d, seed)
+        exact = oracle.statevector(n, d, g)
+        h, rank = oracle.gf2_rank(n, d, g)
+        for a in range(1 << n):
+            r = oracle.elim_clamped(n, d, g, alpha=a, seed=a + 5, chains=256, sweeps=40)
+            if not r["consistent"]:
+                assert r["samples"] == 0 and abs(exact[a]) < 1e-12
+                continue
+            est = oracle.clamped_amplitude(r["cnt"], r["samples"], h, rank)
+            se = np.sqrt(max(2.0 ** (h - 2 * rank) - abs(exact[a]) ** 2, 0.0) / r["samples"])
+            assert abs(est - exact[a]) <= 5 * se + 1e-12, (n, d, seed, a, est, exact[a], se)
+
+
+def test_clamped_ranges_compose():
+    n, d = 4, 8
+    g = W.random_circuit(n, d, seed=17)
+    a = oracle.elim_clamped(n, d, g, alpha=3, seed=8, chains=80, sweeps=12)
+    p1 = oracle.elim_clamped(n, d, g, alpha=3, seed=8, chains=30, sweeps=12)
+    p2 = oracle.elim_clamped(n, d, g, alpha=3, seed=8, chains=50, chain0=30, sweeps=12)
+    q1 = oracle.elim_clamped(n, d, g, alpha=3, seed=8, chains=80, sweeps=5)
+    q2 = oracle.elim_clamped(n, d, g, alpha=3, seed=8, chains=80, sweeps=7, sweep0=5)
+    assert np.array_equal(a["cnt"], p1["cnt"] + p2["cnt"])
+    assert np.array_equal(a["state"], np.concatenate([p1["state"], p2["state"]]))
+    assert np.array_equal(a["cnt"], q1["cnt"] + q2["cnt"])
+    assert np.array_equal(a["state"], q2["state"])
