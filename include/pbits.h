@@ -109,7 +109,7 @@ PB_API void pb_model_free(pb_model* m);
  * tag 1 = initial H outputs).  A p-bit whose violation count changes by v
  * when it goes 0 -> 1 is redrawn as [v < 0] XOR [u < thr[|v|]]  (heat-bath,
  * Fig. 2 Steps 1-2).  One sweep visits the four colour classes in order. */
-enum { PB_GIBBS = 0, PB_LEARNED = 1, PB_ELIM = 2 };
+enum { PB_GIBBS = 0, PB_LEARNED = 1, PB_ELIM = 2, PB_ELIM_CLAMP = 3 };
 /* PB_ELIM: the exact sampler on the eliminated network (Appendix: without
  * the link constraints every non-H bit is a function of the previous layer
  * and each H output a fair coin).  A "sweep" of such a run draws, for every
@@ -120,7 +120,18 @@ enum { PB_GIBBS = 0, PB_LEARNED = 1, PB_ELIM = 2 };
  * are i.i.d. and uniform over the 2^h valid paths (the comparator for the
  * Gibbs and learned samplers).  All models of a run use one sampler;
  * pb_run_set_shape / pb_run_tune have no effect on a PB_ELIM run and the
- * learned-proposal calls reject it. */
+ * learned-proposal calls reject it.
+ * PB_ELIM_CLAMP: the exact sampler with the end state fixed to one output
+ * (cfg.alphas = {alpha}, n_alphas = 1; "for a given input beta and output
+ * alpha", Sec. 3).  Every wire bit is affine over GF(2) in the H outputs x
+ * (in p order), s_d = A x + c; the paths to alpha solve A x = alpha + c.  With
+ * the reduced row echelon form of [A | alpha + c] the free variables
+ * (non-pivot columns, increasing) take the draws z_b -- bit c % 32 of word
+ * b % 4 of Philox4x32-10 at (c / 32, t, (b / 4) | 5 << 16, 0) -- and each
+ * pivot variable its row's right-hand side XOR the free variables in that
+ * row.  The amplitude is 2^{h/2 - r} sum_phi cnt[phi] w^phi / T (SE smaller
+ * than the unclamped estimator's by 2^{r/2}); an unreachable alpha draws
+ * nothing and reads 0.  PB_ELIM and PB_ELIM_CLAMP models may share a run. */
 
 typedef struct {
   uint64_t seed;          /* Philox key                                        */
@@ -131,7 +142,7 @@ typedef struct {
   uint32_t n_batches;     /* SE batches over chain groups (0 = automatic)      */
   const uint32_t* alphas; /* bins to record; NULL = full 2^n histogram (n<=22)  */
   int32_t n_alphas;
-  int32_t sampler;        /* PB_GIBBS or PB_ELIM (PB_LEARNED: see pb_mh_create) */
+  int32_t sampler;        /* PB_GIBBS, PB_ELIM or PB_ELIM_CLAMP (PB_LEARNED: pb_mh_create) */
   const pb_mlp* proposal; /* trained MLP for PB_LEARNED, else NULL             */
   uint32_t mh_every;      /* PB_LEARNED: one suffix MH move every mh_every sweeps */
   uint32_t group0;        /* global index of the first chain group: the chains

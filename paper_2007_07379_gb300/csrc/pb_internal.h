@@ -72,7 +72,13 @@ struct RunModelDev {
   uint32_t group0;         // global index of group 0 (Philox counter word 0)
   uint32_t hist_smem;      // 1: a CTA counts into shared memory and adds its
                            //    counts to `hist` once at the end of a launch
-  uint32_t pad;
+  int32_t amp_shift;       // amplitude scale 2^{h/2 + amp_shift} (-rank when clamped)
+  // output-clamped exact sampler (PB_ELIM_CLAMP; else clamp_tab = nullptr):
+  // per p-bit (1 + clamp_mw) words -- an H output's constant bit and its
+  // mask over the clamp_nfree free draws
+  const uint32_t* clamp_tab;
+  int32_t clamp_mw, clamp_nfree, clamp_ok;  // clamp_ok = 0: alpha unreachable
+  int32_t pad2;
 };
 
 // Workspace header at offset 0.
@@ -87,6 +93,7 @@ constexpr uint32_t kTagSweep = 0;
 constexpr uint32_t kTagInit = 1;
 constexpr uint32_t kTagMH = 2;
 constexpr uint32_t kTagElim = 4;  // exact sampler's H outputs (tag 3: training rows)
+constexpr uint32_t kTagClamp = 5;  // free draws of the output-clamped exact sampler
 
 }  // namespace pb
 

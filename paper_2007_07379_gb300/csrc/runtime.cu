@@ -29,7 +29,7 @@ cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, cons
 cudaError_t launch_elim(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                         const uint32_t* const* d_init_tabs, uint32_t n_sweeps, size_t smem_bytes,
                         WsHeader* hdr, cudaStream_t st);
-size_t elim_smem_bytes(int n, int d);
+size_t elim_smem_bytes(int n, int d, int zwords);
 cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
                               cudaStream_t st);
 cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t count,
@@ -273,9 +273,97 @@ namespace {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 
 struct ModelSlots {
-  size_t model_dev, desc, rec, init, state, hist, valid, samples, alpha_sorted, alpha_slot, amp;
+  size_t model_dev, desc, rec, init, state, hist, valid, samples, alpha_sorted, alpha_slot, amp,
+      clamp;
   uint32_t bins, groups, n_batches;
+  int clamp_mw;  // mask words per p-bit of the clamp table (0: not clamped)
 };
+
+// Output clamping for the exact sampler (PB_ELIM_CLAMP).  The wire bits are
+// affine over GF(2) in the H outputs x (in p order): s_d = A x + c.  A and c
+// come from h + 1 evaluations of the init table (one chain, bit values), and
+// the paths to alpha solve A x = alpha + c.  Gauss-Jordan on the augmented
+// rows (bitsets) gives the unique reduced row echelon form; the free
+// variables (non-pivot columns, increasing) take the draws z_b, each pivot
+// variable its row's right-hand side XOR the free variables in its row.
+struct ClampTable {
+  bool ok = false;
+  int rank = 0, nfree = 0;
+  std::vector<uint32_t> tab;  // per p-bit: constant, then mw mask words
+};
+
+ClampTable build_clamp(const pb_model& m, uint32_t alpha, int mw) {
+  const int n = m.n, d = m.d, npb = n * d, nw = n_words(n, d);
+  std::vector<int> hp;  // p of the j-th H output
+  for (int p = 0; p < npb; ++p)
+    if (m.init[p] == 0xFFFFFFFFu) hp.push_back(p);
+  const int h = (int)hp.size();
+  auto end_state = [&](const std::vector<uint8_t>& x) {
+    std::vector<uint8_t> W(nw, 0);
+    for (int q = 0; q < n; ++q) W[q] = (uint8_t)((m.beta >> q) & 1u);
+    W[ones_idx(n, d)] = 1;
+    int j = 0;
+    for (int p = 0; p < npb; ++p) {
+      const uint32_t e = m.init[p];
+      W[n + p] = e == 0xFFFFFFFFu ? x[j++] : (uint8_t)(W[e & 0xFFFFu] ^ W[e >> 16]);
+    }
+    uint32_t s = 0;
+    for (int q = 0; q < n; ++q) s |= (uint32_t)W[d * n + q] << q;
+    return s;
+  };
+  const int words = (h + 1 + 63) / 64;  // augmented row: h columns + right-hand side
+  std::vector<std::vector<uint64_t>> row(n, std::vector<uint64_t>(words, 0));
+  auto get = [&](int q, int c) { return (int)((row[q][c >> 6] >> (c & 63)) & 1u); };
+  auto set = [&](int q, int c) { row[q][c >> 6] |= 1ull << (c & 63); };
+  std::vector<uint8_t> x(h, 0);
+  const uint32_t c0 = end_state(x);
+  for (int j = 0; j < h; ++j) {
+    x[j] = 1;
+    const uint32_t cj = end_state(x) ^ c0;
+    x[j] = 0;
+    for (int q = 0; q < n; ++q)
+      if ((cj >> q) & 1u) set(q, j);
+  }
+  for (int q = 0; q < n; ++q)
+    if (((alpha ^ c0) >> q) & 1u) set(q, h);
+  std::vector<int> pivot;
+  int r = 0;
+  for (int j = 0; j < h && r < n; ++j) {
+    int piv = -1;
+    for (int q = r; q < n; ++q)
+      if (get(q, j)) { piv = q; break; }
+    if (piv < 0) continue;
+    std::swap(row[piv], row[r]);
+    for (int q = 0; q < n; ++q)
+      if (q != r && get(q, j))
+        for (int w = 0; w < words; ++w) row[q][w] ^= row[r][w];
+    pivot.push_back(j);
+    ++r;
+  }
+  ClampTable t;
+  t.rank = r;
+  t.ok = true;
+  for (int q = r; q < n; ++q)
+    if (get(q, h)) t.ok = false;
+  std::vector<int> free_of(h, -1), row_of(h, -1);
+  for (int i = 0; i < r; ++i) row_of[pivot[i]] = i;
+  for (int j = 0; j < h; ++j)
+    if (row_of[j] < 0) free_of[j] = t.nfree++;
+  t.tab.assign((size_t)npb * (1 + mw), 0u);
+  for (int j = 0; j < h; ++j) {
+    uint32_t* e = &t.tab[(size_t)hp[j] * (1 + mw)];
+    if (free_of[j] >= 0) {
+      const int b = free_of[j];
+      e[1 + b / 32] |= 1u << (b % 32);
+    } else {
+      const int i = row_of[j];
+      e[0] = (uint32_t)get(i, h);
+      for (int c = 0; c < h; ++c)
+        if (free_of[c] >= 0 && get(i, c)) e[1 + free_of[c] / 32] |= 1u << (free_of[c] % 32);
+    }
+  }
+  return t;
+}
 
 struct Layout {
   size_t hdr = 0, rm = 0, init_ptrs = 0, work = 0, total = 0;
@@ -287,7 +375,8 @@ int check_cfg(const pb_model* m, const pb_run_cfg& c) {
   if (c.chains == 0 || c.record_every == 0) return PB_EINVAL;
   if ((uint64_t)c.group0 + (c.chains + 31) / 32 > 0xFFFFFFFFull) return PB_ERANGE;
   // the learned sampler has its own entry points (pb_mh_*) on a PB_GIBBS run
-  if (c.sampler != PB_GIBBS && c.sampler != PB_ELIM) return PB_EINVAL;
+  if (c.sampler != PB_GIBBS && c.sampler != PB_ELIM && c.sampler != PB_ELIM_CLAMP) return PB_EINVAL;
+  if (c.sampler == PB_ELIM_CLAMP && (c.alphas == nullptr || c.n_alphas != 1)) return PB_EINVAL;
   if (c.alphas == nullptr) {
     if (c.n_alphas != 0) return PB_EINVAL;
     if (m->n > 22) return PB_ERANGE;
@@ -341,6 +430,8 @@ int plan(pb_model* const* models, const pb_run_cfg* cfgs, int nm, Layout& L) {
     s.alpha_sorted = take((size_t)(c.alphas ? c.n_alphas : 0) * 4);
     s.alpha_slot = take((size_t)(c.alphas ? c.n_alphas : 0) * 4);
     s.amp = take((size_t)s.bins * 3 * 8);
+    s.clamp_mw = c.sampler == PB_ELIM_CLAMP ? std::max(1, (m->h + 31) / 32) : 0;
+    s.clamp = take(npb * (size_t)(1 + s.clamp_mw) * 4 * (s.clamp_mw > 0 ? 1 : 0));
   }
   L.work = take((size_t)total_groups * 4);
   L.total = align_up(off, 256);
@@ -363,8 +454,9 @@ struct pb_run {
   int cons = 32, prod = 32, max_col = 1, blocks_per_sm = 0;
   size_t smem = 0;
   bool persistent = false;
-  bool elim = false;       // PB_ELIM run: exact i.i.d. paths instead of sweeps
+  bool elim = false;       // exact-sampler run: i.i.d. paths instead of sweeps
   size_t elim_smem = 0;
+  std::vector<std::vector<uint32_t>> clamp_keep;
   int grid = 0;
   uint64_t sweeps_done = 0;
   double flips_per_sweep = 0.0;
@@ -476,11 +568,13 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
   r->nm = n_models;
   r->cfgs.assign(cfgs, cfgs + n_models);
   for (int i = 0; i < n_models; ++i) r->models.emplace_back(new pb_model(*models[i]));
-  // one sampler per run
+  // one sampler family per run: Gibbs, or the exact samplers
+  auto exact = [](int smp) { return smp == PB_ELIM || smp == PB_ELIM_CLAMP; };
   for (int i = 1; i < n_models; ++i)
-    if (cfgs[i].sampler != cfgs[0].sampler) return PB_EINVAL;
-  r->elim = cfgs[0].sampler == PB_ELIM;
-  for (auto& m : r->models) r->elim_smem = std::max(r->elim_smem, elim_smem_bytes(m->n, m->d));
+    if (exact(cfgs[i].sampler) != exact(cfgs[0].sampler)) return PB_EINVAL;
+  r->elim = exact(cfgs[0].sampler);
+  for (auto& m : r->models)
+    r->elim_smem = std::max(r->elim_smem, elim_smem_bytes(m->n, m->d, (m->h + 3) & ~3));
 
   cudaStream_t st = r->st;
   char* ws = r->ws;
@@ -556,6 +650,18 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
     d.seed_hi = (uint32_t)(c.seed >> 32);
     d.group_base = base;
     d.group0 = c.group0;
+    if (c.sampler == PB_ELIM_CLAMP) {
+      ClampTable t = build_clamp(m, c.alphas[0], s.clamp_mw);
+      if ((e = cudaMemcpyAsync(ws + s.clamp, t.tab.data(), t.tab.size() * 4, cudaMemcpyHostToDevice,
+                               st)) != cudaSuccess)
+        return PB_ECUDA;
+      r->clamp_keep.push_back(std::move(t.tab));  // host copy outlives the async copy
+      d.clamp_tab = reinterpret_cast<const uint32_t*>(ws + s.clamp);
+      d.clamp_mw = s.clamp_mw;
+      d.clamp_nfree = t.nfree;
+      d.clamp_ok = t.ok ? 1 : 0;
+      d.amp_shift = -t.rank;
+    }
     init_ptrs[i] = reinterpret_cast<const uint32_t*>(ws + s.init);
     for (uint32_t g = 0; g < s.groups; ++g) cost.push_back({(double)npb, base + g});
     base += s.groups;

@@ -646,11 +646,15 @@ __global__ void init_kernel(const RunModelDev* __restrict__ rm, int n_models,
 // records it (Fig. 2 Step 3; every path is valid).  One CTA per chain group;
 // warp w takes the launch's samples w, w + kElimWarps, ... in its own
 // shared-memory image; lane q writes word q of a layer.
+// Output-clamped models (clamp_tab set): the sample's free draws z_b are
+// bit c % 32 of word b % 4 of Philox(c / 32, t, (b / 4) | 5 << 16, 0), and an
+// H output is its table constant XOR the z_b of its mask (GF(2) elimination
+// on the host), so every path ends at the clamped output.
 constexpr int kElimWarps = 8;
 
 __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
     const RunModelDev* __restrict__ rm, int n_models, uint32_t total_groups,
-    const uint32_t* const* __restrict__ init_tabs, uint32_t n_sweeps, WsHeader* hdr) {
+    const uint32_t* const* __restrict__ init_tabs, uint32_t n_sweeps, int wstride, WsHeader* hdr) {
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t sweep0 = hdr->sweep0;
   const uint32_t flat = blockIdx.x;
@@ -662,7 +666,15 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
   const ModelDev md = *r.model;
   const int n = md.n, d = md.d, nw = md.nw, npb = n * d;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t* W = smem + warp * image_words(n, d);
+  uint32_t* W = smem + warp * wstride;       // path image
+  uint32_t* Z = W + image_words(n, d);       // free draws of a clamped sample
+  const uint32_t* ctab = r.clamp_tab;
+  const int cmw = r.clamp_mw, nfree = r.clamp_nfree;
+  if (ctab && (!r.clamp_ok || image_words(n, d) + nfree > wstride)) {
+    if (!r.clamp_ok) return;  // unreachable output: nothing to draw
+    if (threadIdx.x == 0) set_status(hdr, PB_EINVAL);
+    return;
+  }
   const uint32_t* itab = init_tabs[mi];  // per p-bit: 0xFFFFFFFF = H, else a | b << 16
   // record terms index the image: a bad table is reported, never followed
   int bad = 0;
@@ -691,13 +703,36 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
   for (uint32_t i = (uint32_t)warp; i < n_sweeps; i += kElimWarps) {
     const uint32_t t = sweep0 + i;
     if (!recorded(t)) continue;
+    if (ctab) {
+#pragma unroll 1
+      for (int b0 = 4 * lane; b0 < nfree; b0 += 128) {
+        const uint4 z = philox4x32_10(make_uint4(gglob, t, (uint32_t)(b0 >> 2) | (kTagClamp << 16), 0u),
+                                      r.seed_lo, r.seed_hi);
+        Z[b0] = z.x;
+        if (b0 + 1 < nfree) Z[b0 + 1] = z.y;
+        if (b0 + 2 < nfree) Z[b0 + 2] = z.z;
+        if (b0 + 3 < nfree) Z[b0 + 3] = z.w;
+      }
+      __syncwarp();
+    }
 #pragma unroll 1
     for (int k = 1; k <= d; ++k) {
       if (lane < n) {
         const int p = (k - 1) * n + lane;
         const uint32_t e = itab[p];
         uint32_t v;
-        if (e == 0xFFFFFFFFu) {
+        if (e == 0xFFFFFFFFu && ctab) {
+          const uint32_t* ce = ctab + (size_t)p * (1 + cmw);
+          v = ce[0] ? ~0u : 0u;
+          for (int w = 0; w < cmw; ++w) {
+            uint32_t msk = ce[1 + w];
+            while (msk) {
+              const int b = 32 * w + __ffs((int)msk) - 1;
+              if (b < nfree) v ^= Z[b];
+              msk &= msk - 1u;
+            }
+          }
+        } else if (e == 0xFFFFFFFFu) {
           v = philox4x32_10(make_uint4(gglob, t, (uint32_t)p | (kTagElim << 16), 0u), r.seed_lo,
                             r.seed_hi).x;
         } else {
@@ -760,7 +795,7 @@ __global__ void amplitude_kernel(const RunModelDev* __restrict__ rm_all, int mod
   const uint32_t bin = blockIdx.x * blockDim.x + threadIdx.x;
   if (bin >= rm.bins) return;
   const int h = rm.model->h;
-  const double scale_h = exp2(0.5 * (double)h);
+  const double scale_h = exp2(0.5 * (double)h + (double)rm.amp_shift);
   unsigned long long tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   unsigned long long vtot = 0;
   for (uint32_t b = 0; b < rm.n_batches; ++b) {
@@ -870,16 +905,21 @@ cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, cons
   return cudaGetLastError();
 }
 
+// smem_bytes from elim_smem_bytes: kElimWarps equal per-warp regions
 cudaError_t launch_elim(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                         const uint32_t* const* d_init_tabs, uint32_t n_sweeps, size_t smem_bytes,
                         WsHeader* hdr, cudaStream_t st) {
+  const int wstride = (int)(smem_bytes / (4 * kElimWarps));
   elim_kernel<<<total_groups, kElimWarps * 32, smem_bytes, st>>>(d_rm, n_models, total_groups,
-                                                                 d_init_tabs, n_sweeps, hdr);
+                                                                 d_init_tabs, n_sweeps, wstride, hdr);
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
 }
 
-size_t elim_smem_bytes(int n, int d) { return (size_t)kElimWarps * image_words(n, d) * 4; }
+// Per warp: the path image and up to `zwords` free draws (16-byte multiples).
+size_t elim_smem_bytes(int n, int d, int zwords) {
+  return (size_t)kElimWarps * (size_t)(image_words(n, d) + ((zwords + 3) & ~3)) * 4;
+}
 
 cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
                               cudaStream_t st) {

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpbits.so")
 
 PB_OK, PB_EINVAL, PB_ERANGE, PB_ENOMEM, PB_ECUDA, PB_ETIMEOUT, PB_ESTATE = 0, -1, -2, -3, -4, -5, -6
-PB_GIBBS, PB_LEARNED, PB_ELIM = 0, 1, 2
+PB_GIBBS, PB_LEARNED, PB_ELIM, PB_ELIM_CLAMP = 0, 1, 2, 3
 
 _lib = None
 

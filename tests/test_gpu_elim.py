@@ -100,3 +100,76 @@ def test_learned_moves_reject_an_elim_run():
     net = pbits.Mlp(n, d, hidden=64, batch=128, seed=1)
     with pytest.raises(Exception):
         pbits.Learned(r, net)
+
+
+# ---- output-clamped exact sampler (PB_ELIM_CLAMP)
+
+def _clamp_cfg(seed, chains, alpha, n_batches=8, sampler=None):
+    return pbits.RunCfg(seed=seed, chains=chains, alphas=np.array([alpha], dtype=np.uint32),
+                        n_batches=n_batches, sampler=pbits.PB_ELIM_CLAMP if sampler is None else sampler)
+
+
+@pytest.mark.parametrize("n,d,cseed,chains,sweeps", [(4, 8, 17, 300, 20), (5, 6, 3, 64, 9),
+                                                     (12, 20, 1000, 4096, 4)])
+def test_clamped_bit_exact_vs_oracle(n, d, cseed, chains, sweeps):
+    g = W.random_circuit(n, d, cseed)
+    exact = oracle.statevector(n, d, g)
+    h, rank = oracle.gf2_rank(n, d, g)
+    reach = [a for a in range(1 << n) if abs(exact[a]) > 1e-9][:2]
+    unreach = [a for a in range(1 << n)
+               if not oracle.elim_clamped(n, d, g, alpha=a, seed=1, chains=1, sweeps=0)["consistent"]][:1]
+    for a in reach + unreach:
+        m = pbits.Model(n, d, g, W.default_J(n, d, g))
+        r = pbits.Run([m], [_clamp_cfg(41 + a, chains, a)])
+        r.sweeps(sweeps)
+        r.wait()
+        cnt, valid, samples = r.histogram()
+        ref = oracle.elim_clamped(n, d, g, alpha=a, seed=41 + a, chains=chains, sweeps=sweeps)
+        assert samples == ref["samples"] == valid
+        assert np.array_equal(cnt[0], ref["cnt"])
+        psi, se = r.amplitudes()
+        want = oracle.clamped_amplitude(ref["cnt"], ref["samples"], h, rank)
+        assert abs(psi[0] - want) <= 1e-12 * max(1.0, abs(want))
+        if ref["consistent"]:
+            assert np.array_equal(pbits.unslice_state(r.get_state(), chains), ref["state"])
+        else:
+            assert samples == 0 and psi[0] == 0
+
+
+def test_clamped_se_is_2_to_the_r_over_2_smaller_on_mid():
+    """Mid (h = 33, r = 12): the clamped estimator of psi_0 has SE
+    sqrt((2^{h-2r} - |psi|^2) / T), 2^{r/2} = 64 times the unclamped one's
+    sqrt((2^{h-r} - |psi|^2) / T); the batch-means SE agrees with it."""
+    wl = W.mid()
+    h, rank = oracle.gf2_rank(wl.n, wl.d, wl.gates)
+    m = pbits.Model(wl.n, wl.d, wl.gates, wl.J)
+    r = pbits.Run([m], [_clamp_cfg(wl.seed, wl.chains, 0, n_batches=32)])
+    r.sweeps(2000)
+    psi, se = r.amplitudes()
+    _, _, samples = r.histogram()
+    psi0 = oracle.statevector(wl.n, wl.d, wl.gates)[0]
+    se_closed = np.sqrt(max(2.0 ** (h - 2 * rank) - abs(psi0) ** 2, 0.0) / samples)
+    assert abs(se[0] / se_closed - 1.0) < 0.5
+    assert abs(psi[0] - psi0) <= 5 * se_closed
+    # the unclamped exact sampler over the same samples: 64x the SE on psi_0
+    ru = pbits.Run([m], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, n_batches=32,
+                                      sampler=pbits.PB_ELIM)])
+    ru.sweeps(2000)
+    _, se_u = ru.amplitudes()
+    ratio = se_u[0] / se[0]
+    assert 2 ** (rank / 2) * 0.6 < ratio < 2 ** (rank / 2) * 1.6, ratio
+
+
+def test_clamped_and_unclamped_models_share_a_run():
+    n, d = 4, 8
+    g = W.random_circuit(n, d, 17)
+    m1 = pbits.Model(n, d, g, W.default_J(n, d, g))
+    m2 = pbits.Model(n, d, g, W.default_J(n, d, g))
+    r = pbits.Run([m1, m2], [_clamp_cfg(5, 100, 3), pbits.RunCfg(seed=6, chains=70, sampler=pbits.PB_ELIM)])
+    r.sweeps(11)
+    c1, v1, s1 = r.histogram(0)
+    c2, v2, s2 = r.histogram(1)
+    ref1 = oracle.elim_clamped(n, d, g, alpha=3, seed=5, chains=100, sweeps=11)
+    ref2 = oracle.elim(n, d, g, seed=6, chains=70, sweeps=11)
+    assert np.array_equal(c1[0], ref1["cnt"]) and s1 == ref1["samples"]
+    assert np.array_equal(c2, ref2["cnt"]) and s2 == ref2["samples"]
