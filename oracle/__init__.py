@@ -126,12 +126,13 @@ def thresholds(J: float) -> np.ndarray:
 
 
 def colour(n: int, d: int, gates) -> np.ndarray:
-    """Colour class (0..3) of every p-bit, shape [d, n] (row k-1 = layer k)."""
+    """Colour class (0..3) of every p-bit, shape [d, n] (row k-1 = layer k):
+    the sweep visits the classes in increasing order."""
     lib = _load()
     g = _gates(gates)
     col = np.zeros((d, n), dtype=np.int32)
     rc = lib.orc_colour(n, d, _p(g), len(g), _p(col))
-    if rc != 0:
+    if rc <= 0:
         raise ValueError("orc_colour failed")
     return col
 

@@ -424,21 +424,89 @@ static int path_phase(const orc_net* net, const uint32_t* s) {
   return ph & 7;
 }
 
-/* Colour of p-bit (k, q): the four classes of one sweep, in order,
- *   0: odd k, q not a CNOT target in layer k+1
- *   1: odd k, q a CNOT target in layer k+1
- *   2: even k, not a target in layer k+1
- *   3: even k, target in layer k+1.
- * Factors join only layers k-1, k (one bit of layer k each) except the CNOT
- * link of layer k+1, which joins s_k[control] and s_k[target]; so bits of one
- * class never share a factor and may be drawn in any order. */
-static int pbit_colour(const orc_net* net, int k, int q) {
-  int tgt = 0;
-  if (k < net->d) {
-    int gi = net->gate_of[k * net->n + q]; /* layer index k maps s_k->s_{k+1} */
-    if (gi >= 0 && net->g[gi].op == ORC_CNOT && net->g[gi].q1 == q) tgt = 1;
+/* Colour classes of one sweep.  Two p-bits interact when they belong to one
+ * link (factor): a non-H output bit (k, q) together with the layer-(k-1)
+ * bits its deterministic value depends on -- (k-1, q) for an identity wire,
+ * S, T and CZ, (k-1, c) for a CNOT control output, (k-1, t) and (k-1, c) for a
+ * CNOT target output.  Layer 0 is clamped and interacts with nothing.  A
+ * class holds no two interacting p-bits, so its bits may be redrawn in any
+ * order (in parallel).
+ *
+ * Rule (DSATUR, Brelaz 1979, with fixed tie-breaks): repeatedly take the
+ * uncoloured p-bit with the most distinct colours among its coloured
+ * neighbours, then the most neighbours, then the lowest p = (k-1) n + q, and
+ * give it the smallest colour none of its neighbours has.  If that needs
+ * more than four colours, use instead the fixed four classes
+ *   2 [k even] + [q is a CNOT target in layer k+1]
+ * (layer parity separates adjacent layers; the second bit separates the
+ * control and target inputs of a CNOT).  Returns the number of classes. */
+static int pbit_colours(const orc_net* net, int32_t* colour) {
+  const int n = net->n, d = net->d, N = n * d;
+  enum { MAXN = 8 };  /* neighbours per p-bit: at most 6 in this network */
+  int* nb = (int*)malloc(sizeof(int) * (size_t)N * MAXN);
+  int* deg = (int*)calloc((size_t)N, sizeof(int));
+  uint32_t* seen = (uint32_t*)calloc((size_t)N, sizeof(uint32_t)); /* colours of neighbours */
+  if (!nb || !deg || !seen) { free(nb); free(deg); free(seen); return -1; }
+  int over = 0;
+  /* join the variables of every link pairwise */
+  for (int k = 1; k <= d; ++k) {
+    for (int q = 0; q < n; ++q) {
+      int vars[3], nv = 0;
+      vars[nv++] = (k - 1) * n + q;
+      const int gi = net->gate_of[(k - 1) * n + q];
+      int in0 = q, in1 = -1;
+      if (gi >= 0) {
+        const orc_gate* G = &net->g[gi];
+        if (G->op == ORC_H) continue; /* no link */
+        if (G->op == ORC_CNOT) {
+          if (q == G->q1) { in0 = G->q1; in1 = G->q0; } else { in0 = G->q0; }
+        }
+      }
+      if (k >= 2) {
+        vars[nv++] = (k - 2) * n + in0;
+        if (in1 >= 0) vars[nv++] = (k - 2) * n + in1;
+      }
+      for (int a = 0; a < nv; ++a)
+        for (int b = 0; b < nv; ++b) {
+          if (a == b) continue;
+          const int u = vars[a], v = vars[b];
+          int dup = 0;
+          for (int e = 0; e < deg[u]; ++e) dup |= nb[u * MAXN + e] == v;
+          if (dup) continue;
+          if (deg[u] == MAXN) { over = 1; continue; }
+          nb[u * MAXN + deg[u]++] = v;
+        }
+    }
   }
-  return 2 * ((k % 2) == 0) + tgt;
+  int ncol = 0;
+  for (int i = 0; i < N; ++i) colour[i] = -1;
+  for (int step = 0; step < N && !over; ++step) {
+    int best = -1, bsat = -1, bdeg = -1;
+    for (int v = 0; v < N; ++v) {
+      if (colour[v] >= 0) continue;
+      const int sat = __builtin_popcount(seen[v]);
+      if (sat > bsat || (sat == bsat && deg[v] > bdeg)) { best = v; bsat = sat; bdeg = deg[v]; }
+    }
+    int c = 0;
+    while (c < 32 && ((seen[best] >> c) & 1u)) ++c;
+    colour[best] = c;
+    if (c + 1 > ncol) ncol = c + 1;
+    for (int e = 0; e < deg[best]; ++e) seen[nb[best * MAXN + e]] |= 1u << c;
+  }
+  if (over || ncol > 4) {
+    ncol = 4;
+    for (int k = 1; k <= d; ++k)
+      for (int q = 0; q < n; ++q) {
+        int tgt = 0;
+        if (k < d) {
+          const int gi = net->gate_of[k * n + q]; /* layer index k maps s_k -> s_{k+1} */
+          if (gi >= 0 && net->g[gi].op == ORC_CNOT && net->g[gi].q1 == q) tgt = 1;
+        }
+        colour[(k - 1) * n + q] = 2 * ((k % 2) == 0) + tgt;
+      }
+  }
+  free(nb); free(deg); free(seen);
+  return ncol;
 }
 
 int orc_colour(int n, int d, const orc_gate* g, int ng, int32_t* colour) {
@@ -450,10 +518,9 @@ int orc_colour(int n, int d, const orc_gate* g, int ng, int32_t* colour) {
     net.gate_of[g[i].layer * n + g[i].q0] = i;
     if (gate_arity(g[i].op) == 2) net.gate_of[g[i].layer * n + g[i].q1] = i;
   }
-  for (int k = 1; k <= d; ++k)
-    for (int q = 0; q < n; ++q) colour[(k - 1) * n + q] = pbit_colour(&net, k, q);
+  const int ncol = pbit_colours(&net, colour);
   free(net.gate_of);
-  return 0;
+  return ncol < 0 ? -3 : ncol;
 }
 
 /* Counter-based draws.  Key = seed; counter = (chain >> 5, sweep,
@@ -504,7 +571,7 @@ static int init_bit(uint64_t seed, uint32_t chain, uint32_t p) {
  *                       added to the bin of the end state).
  *   valid_total, samples_total : counters of valid / all recorded samples.
  *
- * One sweep visits the four colour classes in order; within a class every
+ * One sweep visits the colour classes (pbit_colours) in order; within a class every
  * p-bit gets  v = viol(bit=1) - viol(bit=0)  (the change of Re E / J) and is
  * redrawn as  [v < 0] XOR [u < thr[|v|]]:  P(1) = 1/(1 + e^{J v}).
  * Invalid samples (any violated bit) carry U_C = 0 and add nothing. */
@@ -527,6 +594,10 @@ int orc_gibbs(int n, int d, const orc_gate* g, int ng, uint32_t beta, double J,
   }
   const uint32_t nmask = (n == 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
   const uint64_t bins = alphas ? (uint64_t)n_alphas : (1ull << n);
+  int32_t* col = (int32_t*)malloc((size_t)n * d * sizeof(int32_t));
+  if (!col) { free(net.gate_of); return -3; }
+  const int ncol = pbit_colours(&net, col);
+  if (ncol < 0) { free(col); free(net.gate_of); return -3; }
   int err = 0;
 
 #pragma omp parallel reduction(| : err)
@@ -565,10 +636,10 @@ int orc_gibbs(int n, int d, const orc_gate* g, int ng, uint32_t beta, double J,
       }
       for (uint32_t t = 0; t < sweeps; ++t) {
         const uint32_t sweep = sweep0 + t;
-        for (int colour = 0; colour < 4; ++colour) {
+        for (int colour = 0; colour < ncol; ++colour) {
           for (int k = 1; k <= d; ++k) {
             for (int q = 0; q < n; ++q) {
-              if (pbit_colour(&net, k, q) != colour) continue;
+              if (col[(k - 1) * n + q] != colour) continue;
               /* change of the violation count when bit (k,q) goes 0 -> 1;
                * only layers k-1 -> k and k -> k+1 involve s_k. */
               uint32_t keep = s[k];
@@ -614,6 +685,7 @@ int orc_gibbs(int n, int d, const orc_gate* g, int ng, uint32_t beta, double J,
     free(my_cnt);
     free(s);
   }
+  free(col);
   free(net.gate_of);
   return err ? -4 : 0;
 }

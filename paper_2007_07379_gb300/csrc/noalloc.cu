@@ -19,8 +19,8 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
                         const uint32_t* const* d_init_tabs, size_t smem_bytes, WsHeader* hdr,
                         cudaStream_t st);
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
-                          uint32_t n_sweeps, int cons, int prod, int max_col, size_t smem_bytes,
-                          WsHeader* hdr, cudaStream_t st);
+                          uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
+                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st);
 size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins);
 cudaError_t sweep_prepare();
 }  // namespace pb
@@ -93,8 +93,11 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
   // Shape as for a single-model run.
-  int maxcol = 1;
-  for (int c = 0; c < 4; ++c) maxcol = std::max(maxcol, m->col_off[c + 1] - m->col_off[c]);
+  int maxcol = 1, nc = 2;  // largest class; colour steps per sweep
+  for (int c = 0; c < 4; ++c) {
+    maxcol = std::max(maxcol, m->col_off[c + 1] - m->col_off[c]);
+    if (m->col_off[c + 1] > m->col_off[c]) nc = std::max(nc, c + 1);
+  }
   auto up32 = [](int x) { return ((x + 31) / 32) * 32; };
   const int cons = std::max(32, std::min(224, up32(maxcol)));
   const int prod = std::max(32, std::min(352, up32(3 * maxcol)));
@@ -156,7 +159,7 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
                        (size_t)n_words(n, d) * 4, hdr, st)) != cudaSuccess)
     return PB_ECUDA;
   if (n_sweeps > 0 &&
-      (e = launch_sweeps(d_rm, 1, groups, n_sweeps, cons, prod, maxcol, smem, hdr, st)) != cudaSuccess)
+      (e = launch_sweeps(d_rm, 1, groups, n_sweeps, cons, prod, maxcol, nc, smem, hdr, st)) != cudaSuccess)
     return PB_ECUDA;
   if ((e = cudaMemcpyAsync(d_counts, base + o_hist, (size_t)bins * 8 * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_totals, base + o_cnt, 2 * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)

@@ -20,12 +20,12 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
                         const uint32_t* const* d_init_tabs, size_t smem_bytes, WsHeader* hdr,
                         cudaStream_t st);
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
-                          uint32_t n_sweeps, int cons, int prod, int max_col, size_t smem_bytes,
-                          WsHeader* hdr, cudaStream_t st);
+                          uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
+                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st);
 cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
                                      uint32_t n_work, uint32_t n_sweeps, int cons, int prod,
-                                     int max_col, int grid, size_t smem_bytes, WsHeader* hdr,
-                                     cudaStream_t st);
+                                     int max_col, int nc, int grid, size_t smem_bytes,
+                                     WsHeader* hdr, cudaStream_t st);
 cudaError_t launch_elim(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                         const uint32_t* const* d_init_tabs, uint32_t n_sweeps, size_t smem_bytes,
                         WsHeader* hdr, cudaStream_t st);
@@ -203,6 +203,47 @@ PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t 
       m->rec[p] = R;
     }
   }
+  // Colour classes: p-bits that share a link interact; a p-bit's neighbours
+  // are the p-bit words among its link demands W[a_l] ^ W[b_l].  DSATUR
+  // (Brelaz) with fixed tie-breaks: the uncoloured p-bit with the most
+  // distinct neighbour colours, then the most neighbours, then the lowest p,
+  // takes the smallest colour its neighbours lack.  More than four colours
+  // (not met in practice: at most six neighbours) falls back to the fixed
+  // classes 2 [k even] + [CNOT target in layer k+1] set above.
+  {
+    std::vector<std::vector<int>> nb(npb);
+    for (int p = 0; p < npb; ++p) {
+      const pb::Desc& D = by_p[p];
+      for (int l = 0; l < (D.mflag & 3); ++l)
+        for (int w : {(int)D.a[l], (int)D.b[l]})
+          if (w >= n && w < (d + 1) * n && w - n != p &&
+              std::find(nb[p].begin(), nb[p].end(), w - n) == nb[p].end())
+            nb[p].push_back(w - n);
+    }
+    std::vector<int> col(npb, -1);
+    std::vector<uint32_t> seen(npb, 0u);
+    int ncol = 0;
+    for (int step = 0; step < npb; ++step) {
+      int best = -1, bsat = -1, bdeg = -1;
+      for (int v = 0; v < npb; ++v) {
+        if (col[v] >= 0) continue;
+        const int sat = __builtin_popcount(seen[v]);
+        if (sat > bsat || (sat == bsat && (int)nb[v].size() > bdeg)) {
+          best = v;
+          bsat = sat;
+          bdeg = (int)nb[v].size();
+        }
+      }
+      int c = 0;
+      while (c < 32 && ((seen[best] >> c) & 1u)) ++c;
+      col[best] = c;
+      ncol = std::max(ncol, c + 1);
+      for (int u : nb[best]) seen[u] |= 1u << c;
+    }
+    if (ncol <= 4)
+      for (int p = 0; p < npb; ++p) m->colour[p] = col[p];
+  }
+
   // colour-ordered descriptors
   for (int c = 0; c < 4; ++c) {
     m->col_off[c] = (int)m->desc.size();
@@ -454,6 +495,7 @@ struct pb_run {
   int cons = 32, prod = 32, max_col = 1, blocks_per_sm = 0;
   size_t smem = 0;
   bool persistent = false;
+  int nc = 2;              // colour steps per sweep (largest over the models)
   bool elim = false;       // exact-sampler run: i.i.d. paths instead of sweeps
   size_t elim_smem = 0;
   std::vector<std::vector<uint32_t>> clamp_keep;
@@ -573,6 +615,9 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
   for (int i = 1; i < n_models; ++i)
     if (exact(cfgs[i].sampler) != exact(cfgs[0].sampler)) return PB_EINVAL;
   r->elim = exact(cfgs[0].sampler);
+  for (auto& m : r->models)
+    for (int c = 0; c < 4; ++c)
+      if (m->col_off[c + 1] > m->col_off[c]) r->nc = std::max(r->nc, c + 1);
   for (auto& m : r->models)
     r->elim_smem = std::max(r->elim_smem, elim_smem_bytes(m->n, m->d, (m->h + 3) & ~3));
 
@@ -718,11 +763,11 @@ PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
                       r->elim_smem, r->hdr(), r->cap_st);
     else if (r->persistent)
       e = launch_sweeps_persistent(r->d_rm(), r->nm, reinterpret_cast<const uint32_t*>(r->ws + r->L.work),
-                                   r->total_groups, n_sweeps, r->cons, r->prod, r->max_col, r->grid,
-                                   r->smem, r->hdr(), r->cap_st);
+                                   r->total_groups, n_sweeps, r->cons, r->prod, r->max_col, r->nc,
+                                   r->grid, r->smem, r->hdr(), r->cap_st);
     else
       e = launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->cons, r->prod, r->max_col,
-                        r->smem, r->hdr(), r->cap_st);
+                        r->nc, r->smem, r->hdr(), r->cap_st);
     cudaError_t e2 = cudaStreamEndCapture(r->cap_st, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);

@@ -321,6 +321,8 @@ __device__ __noinline__ void redraw_extra(uint32_t* W, uint32_t* S, const Desc* 
 }
 
 // Runs `n_sweeps` sweeps (absolute indices sweep0...) of one chain group.
+// NC = colour steps per sweep (2..4; the model's classes NC.. are empty).
+template <int NC>
 __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, uint32_t n_sweeps,
                           Shape sh, int max_col_all, uint32_t* smem, WsHeader* hdr) {
   // run and model constants held in registers for the whole launch
@@ -454,7 +456,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     constexpr int C = decltype(cc)::value;
     const uint32_t sweep = sweep0 + s;
     uint32_t* S = smem + iw * (1 + (s & 1u));
-    const uint4* cur = planes + (C & 1) * pbuf;
+    // plane buffer of global step s NC + C
+    const uint4* cur = planes + ((s * (uint32_t)NC + (uint32_t)C) & 1u) * pbuf;
     if (consumer) {
       const int lo = col_lo[C], hi = col_hi[C], K = hi - lo;
       // the first p-bit of every consumer from its table entry; warps with no
@@ -482,15 +485,17 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
                      thr3, gglob, sweep, k0, k1);
     } else if (producer) {
       // the next step: class C + 1 of this sweep, or class 0 of the next one
-      if constexpr (C < 3) {
-        produce(std::integral_constant<int, C + 1>{}, sweep, planes + ((C + 1) & 1) * pbuf);
+      const uint32_t nxt = s * (uint32_t)NC + (uint32_t)C + 1u;
+      if constexpr (C + 1 < NC) {
+        produce(std::integral_constant<int, C + 1>{}, sweep, planes + (nxt & 1u) * pbuf);
       } else {
-        if (s + 1u < n_sweeps) produce(std::integral_constant<int, 0>{}, sweep + 1u, planes);
+        if (s + 1u < n_sweeps)
+          produce(std::integral_constant<int, 0>{}, sweep + 1u, planes + (nxt & 1u) * pbuf);
       }
     } else {
       // records run one sweep behind: the record of sweep s-1 reads its
-      // snapshot in thirds in classes 0-2 of sweep s and reduces in class 3;
-      // it is binned in class 0 of sweep s+1
+      // snapshot in NC-1 parts in steps 0..NC-2 of sweep s and reduces in
+      // step NC-1; it is binned in step 0 of sweep s+1
       if constexpr (C == 0) {
         if (bin_pending) {
           rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
@@ -499,13 +504,9 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       }
       if (s > 0u && recorded(sweep - 1u)) {
         const uint32_t* Sp = smem + iw * (1 + ((s + 1u) & 1u));
-        if constexpr (C == 0) {
-          rec.clear();
-          rec.read(Sp, srec, 0, npb / 3, lane);
-        } else if constexpr (C == 1) {
-          rec.read(Sp, srec, npb / 3, 2 * npb / 3, lane);
-        } else if constexpr (C == 2) {
-          rec.read(Sp, srec, 2 * npb / 3, npb, lane);
+        if constexpr (C == 0) rec.clear();
+        if constexpr (C + 1 < NC) {
+          rec.read(Sp, srec, C * npb / (NC - 1), (C + 1) * npb / (NC - 1), lane);
         } else {
           rec.reduce(Sp, n, d, lane);
           bin_pending = true;
@@ -518,8 +519,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   for (uint32_t s = 0; s < n_sweeps; ++s) {
     step(std::integral_constant<int, 0>{}, s);
     step(std::integral_constant<int, 1>{}, s);
-    step(std::integral_constant<int, 2>{}, s);
-    step(std::integral_constant<int, 3>{}, s);
+    if constexpr (NC > 2) step(std::integral_constant<int, 2>{}, s);
+    if constexpr (NC > 3) step(std::integral_constant<int, 3>{}, s);
   }
   // the records still in flight: the previous sweep's binning and the last sweep
   if (recorder) {
@@ -554,6 +555,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
 // One CTA per chain group of every model of the run (flat group index).
 constexpr int kMaxThreads = 608;  // 224 consumers + 352 producers + 1 recorder warp
 
+template <int NC>
 __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const RunModelDev* __restrict__ rm,
                                                      int n_models, uint32_t total_groups,
                                                      uint32_t n_sweeps, Shape sh, int max_col,
@@ -566,11 +568,12 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const RunModelDev* _
   const RunModelDev& r = rm[mi];
   const uint32_t g = flat - r.group_base;
   if (g >= r.groups) return;
-  run_group(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
+  run_group<NC>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
 }
 
 // Persistent form: a fixed grid pops (model, group) items from a
 // cost-ordered work list with one atomic counter.  No CTA waits on another.
+template <int NC>
 __global__ void __launch_bounds__(kMaxThreads) sweep_persistent_kernel(
     const RunModelDev* __restrict__ rm, int n_models, const uint32_t* __restrict__ work,
     uint32_t n_work, uint32_t n_sweeps, Shape sh, int max_col, WsHeader* hdr) {
@@ -587,7 +590,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_persistent_kernel(
     const int mi = find_model(rm, n_models, flat);
     const RunModelDev& r = rm[mi];
     const uint32_t g = flat - r.group_base;
-    if (g < r.groups) run_group(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
+    if (g < r.groups) run_group<NC>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
   }
 }
 
@@ -881,26 +884,42 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
 // one captured graph replays correctly any number of times).
 __global__ void advance_kernel(WsHeader* hdr, uint32_t n_sweeps) { hdr->sweep0 += n_sweeps; }
 
+// nc: colour steps per sweep (the largest over the launch's models; 2..4).
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
-                          uint32_t n_sweeps, int cons, int prod, int max_col, size_t smem_bytes,
-                          WsHeader* hdr, cudaStream_t st) {
+                          uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
+                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st) {
   const int threads = cons + prod + 32;
-  sweep_kernel<<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups,
-                                                          n_sweeps, Shape{cons, prod}, max_col, hdr);
+  const Shape sh{cons, prod};
+  if (nc <= 2)
+    sweep_kernel<2><<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups,
+                                                               n_sweeps, sh, max_col, hdr);
+  else if (nc == 3)
+    sweep_kernel<3><<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups,
+                                                               n_sweeps, sh, max_col, hdr);
+  else
+    sweep_kernel<4><<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups,
+                                                               n_sweeps, sh, max_col, hdr);
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
                                      uint32_t n_work, uint32_t n_sweeps, int cons, int prod,
-                                     int max_col, int grid, size_t smem_bytes, WsHeader* hdr,
-                                     cudaStream_t st) {
+                                     int max_col, int nc, int grid, size_t smem_bytes,
+                                     WsHeader* hdr, cudaStream_t st) {
   const int threads = cons + prod + 32;
   cudaError_t e = cudaMemsetAsync(&hdr->work_next, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  sweep_persistent_kernel<<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work,
-                                                              n_sweeps, Shape{cons, prod}, max_col,
-                                                              hdr);
+  const Shape sh{cons, prod};
+  if (nc <= 2)
+    sweep_persistent_kernel<2><<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work,
+                                                                  n_sweeps, sh, max_col, hdr);
+  else if (nc == 3)
+    sweep_persistent_kernel<3><<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work,
+                                                                  n_sweeps, sh, max_col, hdr);
+  else
+    sweep_persistent_kernel<4><<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work,
+                                                                  n_sweeps, sh, max_col, hdr);
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
 }
@@ -943,18 +962,22 @@ size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins)
 // Opt the sweep kernels into large dynamic shared memory (called once per
 // run, outside any stream capture).
 cudaError_t sweep_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(elim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(sweep_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              200 * 1024);
+  const int big = 200 * 1024;
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(sweep_kernel<2>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_persistent_kernel<2>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_persistent_kernel<3>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_persistent_kernel<4>, a, big)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(elim_kernel, a, big);
 }
 
 int sweep_max_blocks_per_sm(int threads, size_t smem) {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_persistent_kernel, threads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_persistent_kernel<4>, threads,
                                                     smem) != cudaSuccess)
     return 1;
   return blocks;
