@@ -463,10 +463,28 @@ def elim_measurement(dev, stream, samples: int = 10_000):
             run.wait()
             ms = run.stats()["last_ms"]
             best = ms if best is None else min(best, ms)
+        # one amplitude with the end state clamped (psi_0): its SE at this
+        # budget and the time to an absolute error (1 SE) of 1e-2 and 1e-3
+        runc = pbits.Run([m], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, n_batches=32,
+                                            alphas=np.array([0], dtype=np.uint32),
+                                            sampler=pbits.PB_ELIM_CLAMP)], stream=stream)
+        runc.sweeps(samples)
+        runc.wait()
+        runc.sweeps(samples)
+        runc.wait()
+        ms_c = runc.stats()["last_ms"]
+        _, se_c = runc.amplitudes()
+        _, se_u = run.amplitudes()
+    t_c = 2 * ms_c / 1e3  # both launches recorded
     return {"workload": f"mid (n={wl.n}, d={wl.d}), {wl.chains} chains, exact i.i.d. paths",
             "samples": samples, "launch_ms": best,
             "paths_per_s": wl.chains * samples / (best / 1e3),
-            "pbit_assignments_per_s": wl.chains * wl.n * wl.d * samples / (best / 1e3)}
+            "pbit_assignments_per_s": wl.chains * wl.n * wl.d * samples / (best / 1e3),
+            "clamped_psi0": {"launch_ms": ms_c, "se": float(se_c[0]),
+                             # the unclamped run recorded 4 launches, this one 2
+                             "se_unclamped_same_samples": float(se_u[0]) * np.sqrt(2.0),
+                             "t_to_1e-2_s": t_c * (float(se_c[0]) / 1e-2) ** 2,
+                             "t_to_1e-3_s": t_c * (float(se_c[0]) / 1e-3) ** 2}}
 
 
 def batched_measurement(dev, stream, sweeps: int = 10_000):
