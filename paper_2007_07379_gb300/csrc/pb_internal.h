@@ -89,6 +89,10 @@ struct WsHeader {
   uint32_t pad[61];
 };
 
+// Dynamic shared memory the sweep and exact-sampler kernels may use per CTA
+// (227 KB per block on sm_103a, less their static shared memory).
+constexpr size_t kSweepSmemMax = 226 * 1024;
+
 constexpr uint32_t kTagSweep = 0;
 constexpr uint32_t kTagInit = 1;
 constexpr uint32_t kTagMH = 2;

@@ -536,7 +536,7 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
     const pb_model& m = *r->models[i];
     const uint32_t bins = r->L.ms[i].bins;
     const size_t base = sweep_smem_bytes(m.n, m.d, cons, maxcol, 0);
-    const bool use = (size_t)bins * 32 <= cap && base + (size_t)bins * 32 <= (200u << 10);
+    const bool use = (size_t)bins * 32 <= cap && base + (size_t)bins * 32 <= kSweepSmemMax;
     r->rm[i].hist_smem = use ? 1u : 0u;
     smem = std::max(smem, sweep_smem_bytes(m.n, m.d, cons, maxcol, use ? bins : 0));
   }
@@ -721,6 +721,7 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
   for (auto& c : cost) work.push_back(c.second);
   if (sweep_prepare() != cudaSuccess) return PB_ECUDA;
   choose_shape(r.get());
+  if (r->smem > kSweepSmemMax || r->elim_smem > kSweepSmemMax) return PB_ERANGE;
   if ((e = cudaMemcpyAsync(ws + r->L.rm, r->rm.data(), sizeof(RunModelDev) * n_models,
                            cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemcpyAsync(ws + r->L.init_ptrs, init_ptrs.data(), sizeof(uint32_t*) * n_models,
@@ -868,7 +869,12 @@ PB_API int pb_run_set_shape(pb_run* r, int consumers, int producers, int blocks_
   if (producers < 32 || producers > 352 || producers % 32) return PB_EINVAL;
   if (blocks_per_sm < 0) return PB_EINVAL;
   if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
+  const int c0 = r->cons, p0 = r->prod, b0 = r->blocks_per_sm;
   apply_shape(r, consumers, producers, blocks_per_sm);
+  if (r->smem > kSweepSmemMax) {  // the shape does not fit: keep the old one
+    apply_shape(r, c0, p0, b0);
+    return PB_ERANGE;
+  }
   for (auto& kv : r->graphs) cudaGraphExecDestroy(kv.second);
   r->graphs.clear();
   if (cudaMemcpy(r->ws + r->L.rm, r->rm.data(), sizeof(RunModelDev) * r->nm, cudaMemcpyHostToDevice) !=
@@ -942,7 +948,9 @@ PB_API int pb_run_tune(pb_run* r, uint32_t trial_sweeps, const char* cache_path,
   for (int c : cons_c)
     for (int p : prod_c)
       for (int b : bpsm_c) {
-        if ((rc = pb_run_set_shape(r, c, p, b)) != PB_OK) return rc;
+        rc = pb_run_set_shape(r, c, p, b);
+        if (rc == PB_ERANGE) continue;  // a shape that does not fit in shared memory
+        if (rc != PB_OK) return rc;
         // first launch builds the graph; time the second
         if ((rc = pb_run_sweeps(r, trial_sweeps)) != PB_OK) return rc;
         if ((rc = pb_run_sweeps(r, trial_sweeps)) != PB_OK) return rc;

@@ -962,7 +962,7 @@ size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins)
 // Opt the sweep kernels into large dynamic shared memory (called once per
 // run, outside any stream capture).
 cudaError_t sweep_prepare() {
-  const int big = 200 * 1024;
+  const int big = (int)kSweepSmemMax;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(sweep_kernel<2>, a, big)) != cudaSuccess ||

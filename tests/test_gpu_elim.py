@@ -29,15 +29,17 @@ def _elim_run(n, d, g, seed, chains, alphas=None, burn_in=0, record_every=1, n_b
 
 
 @pytest.mark.parametrize("n,d,cseed,chains,sweeps", [(3, 4, 0, 1024, 50), (5, 8, 21, 100, 33),
-                                                     (12, 20, 1000, 4096, 6), (1, 6, -1, 64, 40)])
+                                                     (12, 20, 1000, 4096, 6), (1, 6, -1, 64, 40),
+                                                     (32, 64, 3, 40, 3), (6, 1, 4, 33, 7)])
 def test_bit_exact_vs_oracle(n, d, cseed, chains, sweeps):
     g = W.hadamard_chain(d) if cseed < 0 else W.random_circuit(n, d, cseed)
-    m, r = _elim_run(n, d, g, seed=77, chains=chains)
+    alphas = np.arange(16, dtype=np.uint32) if n > 20 else None
+    m, r = _elim_run(n, d, g, seed=77, chains=chains, alphas=alphas)
     r.sweeps(sweeps)
     r.wait()
     cnt, valid, samples = r.histogram()
     state = pbits.unslice_state(r.get_state(), chains)
-    ref = oracle.elim(n, d, g, seed=77, chains=chains, sweeps=sweeps)
+    ref = oracle.elim(n, d, g, seed=77, chains=chains, sweeps=sweeps, alphas=alphas)
     assert samples == ref["samples"] == chains * sweeps
     assert valid == ref["valid"] == samples
     assert np.array_equal(cnt, ref["cnt"])

@@ -58,6 +58,9 @@ CASES = [
     ("input_bits", 4, 9, 23, 64, 3.0, 0b1011),
     ("wide", 32, 3, 9, 64, 4.0, 0),
     ("deep", 2, 64, 31, 32, 3.0, 0),
+    ("max", 32, 64, 3, 40, None, 0),     # the largest model: 2048 p-bits
+    ("one_layer", 6, 1, 4, 64, 3.0, 0),  # no two p-bits interact: one class
+    ("no_h", 5, 8, 12, 64, 3.0, 0b101),  # h = 0: a single valid path
 ]
 
 
@@ -66,7 +69,11 @@ def _circuit(name, n, d, seed):
         return W.hadamard_chain(d)
     if name == "ghz":
         return W.ghz(n)
-    return W.random_circuit(n, d, seed)
+    g = W.random_circuit(n, d, seed)
+    if name == "no_h":
+        g = np.array(g)
+        g[g[:, 0] == W.H, 0] = W.T
+    return g
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
@@ -247,3 +254,24 @@ def test_sharded_runs_sum_to_the_single_run():
         states.append(pbits.unslice_state(r.get_state(), c))
     assert np.array_equal(tot_cnt, want[0]) and tot_valid == want[1] and tot_samples == want[2]
     assert np.array_equal(np.concatenate(states), pbits.unslice_state(full.get_state(), chains))
+
+
+def test_zero_sweeps_and_the_single_path_of_an_h_free_circuit():
+    """h = 0: the only valid path is the deterministic one, so every valid
+    sample lands in one (alpha, phase) bin and |psi_alpha| = 1 exactly."""
+    n, d = 5, 8
+    g = np.array(W.random_circuit(n, d, 12))
+    g[g[:, 0] == W.H, 0] = W.T
+    m, r = _gpu_run(n, d, g, 3.0, 99, 256, beta=0b101)
+    r.sweeps(0)
+    cnt0, v0, s0 = r.histogram()
+    assert v0 == 0 and s0 == 0 and cnt0.sum() == 0
+    r.sweeps(50)
+    cnt, valid, samples = r.histogram()
+    assert samples == 256 * 50 and valid > 0
+    nz = np.argwhere(cnt > 0)
+    assert len(nz) == 1 and cnt[tuple(nz[0])] == valid
+    psi, se = r.amplitudes()
+    # every batch estimates the same exact value: SE is rounding residue only
+    assert abs(abs(psi[nz[0][0]]) - 1.0) < 1e-12 and np.all(se < 1e-15)
+    assert np.allclose(psi, oracle.statevector(n, d, g, beta=0b101), atol=1e-12)
