@@ -443,7 +443,6 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
 
   const FastThr fast = fast_thresholds(thr1, thr2);
   Recorder rec;
-  bool bin_pending = false;
   unsigned long long n_valid = 0ull, n_samples = 0ull;  // recorder warp only
   auto recorded = [&](uint32_t t) {
     return t >= rm.burn_in && (rm.record_every == 1u || (t - rm.burn_in) % rm.record_every == 0);
@@ -494,14 +493,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       }
     } else {
       // records run one sweep behind: the record of sweep s-1 reads its
-      // snapshot in NC-1 parts in steps 0..NC-2 of sweep s and reduces in
-      // step NC-1; it is binned in step 0 of sweep s+1
-      if constexpr (C == 0) {
-        if (bin_pending) {
-          rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
-          bin_pending = false;
-        }
-      }
+      // snapshot in NC-1 parts in steps 0..NC-2 of sweep s, then reduces
+      // and bins in step NC-1
       if (s > 0u && recorded(sweep - 1u)) {
         const uint32_t* Sp = smem + iw * (1 + ((s + 1u) & 1u));
         if constexpr (C == 0) rec.clear();
@@ -509,7 +502,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
           rec.read(Sp, srec, C * npb / (NC - 1), (C + 1) * npb / (NC - 1), lane);
         } else {
           rec.reduce(Sp, n, d, lane);
-          bin_pending = true;
+          rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
         }
       }
     }
@@ -522,9 +515,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     if constexpr (NC > 2) step(std::integral_constant<int, 2>{}, s);
     if constexpr (NC > 3) step(std::integral_constant<int, 3>{}, s);
   }
-  // the records still in flight: the previous sweep's binning and the last sweep
+  // the record still in flight: the last sweep's
   if (recorder) {
-    if (bin_pending) rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
     if (n_sweeps > 0 && recorded(sweep0 + n_sweeps - 1)) {
       const uint32_t* Sl = smem + iw * (1 + ((n_sweeps - 1u) & 1u));
       rec.clear();
