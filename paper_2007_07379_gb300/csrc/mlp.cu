@@ -687,7 +687,7 @@ struct FusedArgs {
 // (128 x kin), the h tile (128 x H), W1, W3 and the biases resident for the
 // whole launch, and nb buffers for the K-chunks of W2 (64 columns each)
 // streamed in by bulk copies; nb is as large as the space allows.
-constexpr size_t kFusedSmemMax = 224 * 1024;  // with the kernel's static shared memory (< 3 KB)
+constexpr size_t kFusedSmemMax = 222 * 1024;  // with the kernel's static shared memory (< 5 KB)
 
 inline size_t round_kb(size_t b) { return (b + 1023) & ~(size_t)1023; }
 
@@ -753,8 +753,13 @@ __device__ __forceinline__ void build_x_part(uint8_t* sX, int kin, int n, int r,
 // while it is drawn equals the one computed later for the same path.
 __device__ __forceinline__ float softplus_tail(float l) { return __logf(1.f + __expf(-fabsf(l))); }
 
+// Threads per row of the fused kernel: warps w, w + 4, ... share TMEM lane
+// quadrant w % 4 (rows 32 (w % 4) ..) and split each row's work.
+constexpr int kFusedParts = 4;
+constexpr int kFusedThreads = 128 * kFusedParts;
+
 template <int MODE>
-__global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(kFusedThreads) mlp_fused_kernel(FusedArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   // mbarriers: wbar = W1 and W3 delivered; lbar[b] = the W2 chunk in buffer
   // b delivered; cbar[b] = the MMAs reading buffer b done (committed only
@@ -764,9 +769,9 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
   constexpr int kMaxNb = 4;
   __shared__ uint64_t bars[2 + 2 * kMaxNb + 1];
   __shared__ uint32_t tmem_base;
-  // the two halves of a row exchange their bits and log q terms here
-  __shared__ uint32_t xw[2][128];
-  __shared__ float xq[2][128];
+  // the parts of a row exchange their bits and log q terms here
+  __shared__ uint32_t xw[kFusedParts][128];
+  __shared__ float xq[kFusedParts][128];
   uint64_t* wbar = &bars[0];
   uint64_t* done = &bars[1];
   uint64_t* drain = &bars[2];
@@ -778,10 +783,10 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
   uint8_t* sW3 = sm + a.offW3;
   float* sB = reinterpret_cast<float*>(sm + a.offB);  // b1 [H], b2 [H], b3 [npad]
   uint8_t* sWb = sm + a.offWb;                           // nb chunk buffers
-  // 256 threads: warp w reads TMEM lanes 32 (w & 3) .. +31 (its rows) and
-  // handles half (w >> 2) of the columns, x elements and bits of those rows
+  // warp w reads TMEM lanes 32 (w & 3) .. +31 (its rows) and handles part
+  // w >> 2 (of kFusedParts) of the columns, x elements and bits of those rows
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, half = warp >> 2;
+  const int quad = warp & 3, part = warp >> 2;
   const int rl = quad * 32 + lane;  // row within the tile
   const int r0 = blockIdx.x * 128;
   const int H = a.H, kin = a.kin, npad = a.npad, nb = min(a.nb, kMaxNb);
@@ -795,11 +800,11 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
     for (int i = 0; i < 2 + 2 * kMaxNb + 1; ++i) tc::mbar_init(&bars[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < H; i += 256) {
+  for (int i = tid; i < H; i += kFusedThreads) {
     sB[i] = a.b1[i];
     sB[H + i] = a.b2[i];
   }
-  for (int i = tid; i < npad; i += 256) sB[2 * H + i] = a.b3[i];
+  for (int i = tid; i < npad; i += kFusedThreads) sB[2 * H + i] = a.b3[i];
   __syncthreads();  // TMEM address, barriers and biases visible
   const uint32_t tb = tmem_base;
   bool ok = true;
@@ -846,8 +851,10 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
     tc::fence_after_sync();
   };
   // h = relu(D + b) in bf16, into sH (canonical, K = H): this thread's row,
-  // columns [half H/2, (half + 1) H/2), 64 columns per TMEM read
-  const int hc_lo = half * (H / 2), hc_hi = hc_lo + H / 2;
+  // the part's share of the 8-column groups; one 64-column TMEM read covers
+  // it (a share is at most 64 columns and starts at most at column 192)
+  const int ngrp = H / 8;
+  const int hc_lo = 8 * (part * ngrp / kFusedParts), hc_hi = 8 * ((part + 1) * ngrp / kFusedParts);
   auto epilogue_to_h = [&](const float* bias) {
     uint8_t* base = sH + (rl >> 3) * (H * 16) + (rl & 7) * 16;
     for (int c0 = hc_lo; c0 < hc_hi; c0 += 64) {
@@ -881,10 +888,11 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
   for (int jl = jfirst; jl <= jend; ++jl) {
     // ---- x tile (row = chain r0 + r at layer jl, or a staged input row)
     if (MODE == kFusedLogits) {
-      stage_rows(sX, a.X, kin, r0, 128, a.rows, 0, kin, tid, 256);
+      stage_rows(sX, a.X, kin, r0, 128, a.rows, 0, kin, tid, kFusedThreads);
       tc::cp_async_wait_all();
     } else {
-      build_x_part(sX, kin, a.n, rl, prev, jl, half * (kin / 16), (half + 1) * (kin / 16));
+      build_x_part(sX, kin, a.n, rl, prev, jl, part * (kin / 8) / kFusedParts,
+                   (part + 1) * (kin / 8) / kFusedParts);
     }
     publish();
 
@@ -948,7 +956,7 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
     wait_done();
     // logits of this thread's row (npad is 16 or 32); the row's bits are
     // split between the two halves by Philox output (4 bits each):
-    // half h takes bits 4 g .. 4 g + 3 for the g with g % 2 == h
+    // part p takes bits 4 g .. 4 g + 3 for the g with g % kFusedParts == p
     uint32_t word = 0u;
     float sq = 0.f;
     if (ok) {
@@ -968,7 +976,7 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
       for (int i = 0; i < 32; ++i) l[i] += i < npad ? b3[i] : 0.f;
       if (row < a.rows) {
         if (MODE == kFusedLogits) {
-          if (half == 0) {
+          if (part == 0) {
 #pragma unroll
             for (int i = 0; i < 32; ++i)
               if (i < npad) a.logits[(size_t)row * npad + i] = l[i];
@@ -978,7 +986,7 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
           const uint32_t bits = a.P[(size_t)row * a.d + (jl - 1)];
 #pragma unroll
           for (int qb = 0; qb < 32; ++qb) {
-            if (qb < a.n && ((qb >> 2) & 1) == half) {
+            if (qb < a.n && (qb >> 2) % kFusedParts == part) {
               const float z = ((bits >> qb) & 1u) ? -l[qb] : l[qb];
               sq -= fmaxf(z, 0.f) + softplus_tail(l[qb]);
             }
@@ -991,7 +999,7 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
           uint4 u4 = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
           for (int qb = 0; qb < 32; ++qb) {
-            if (qb < a.n && ((qb >> 2) & 1) == half) {
+            if (qb < a.n && (qb >> 2) % kFusedParts == part) {
               if ((qb & 3) == 0)
                 u4 = philox4x32_10(make_uint4(gc, move, (uint32_t)(jl - 1) | (kTagMH << 16),
                                               (uint32_t)(qb >> 2)), a.k0, a.k1);
@@ -1010,8 +1018,8 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
       }
     }
     if (MODE != kFusedLogits) {
-      xw[half][rl] = word;
-      xq[half][rl] = sq;
+      xw[part][rl] = word;
+      xq[part][rl] = sq;
     }
     // the TMEM reads of this layer are complete before the next layer's
     // MMAs, and the halves' bits are exchanged
@@ -1019,17 +1027,23 @@ __global__ void __launch_bounds__(256) mlp_fused_kernel(FusedArgs a) {
     __syncthreads();
     tc::fence_after_sync();
     if (MODE != kFusedLogits && ok && row < a.rows) {
-      const float sql = xq[0][rl] + xq[1][rl];
+      float sql = 0.f;
+      uint32_t wrd = 0u;
+#pragma unroll
+      for (int q = 0; q < kFusedParts; ++q) {
+        sql += xq[q][rl];
+        wrd |= xw[q][rl];
+      }
       if (MODE == kFusedLogQ) {
-        if (half == 0) a.lq[(size_t)row * a.d + (jl - 1)] = sql;
+        if (part == 0) a.lq[(size_t)row * a.d + (jl - 1)] = sql;
       } else {
-        prev = xw[0][rl] | xw[1][rl];
-        if (half == 0) a.Pn[(size_t)row * a.d + (jl - 1)] = prev;
+        prev = wrd;
+        if (part == 0) a.Pn[(size_t)row * a.d + (jl - 1)] = prev;
         lq_acc += sql;
       }
     }
   }  // layers
-  if (MODE == kFusedSample && ok && row < a.rows && half == 0) a.lqf[row] += lq_acc;
+  if (MODE == kFusedSample && ok && row < a.rows && part == 0) a.lqf[row] += lq_acc;
   if (!__syncthreads_and(ok)) {
     if (tid == 0) {
       if (a.status) atomicCAS(a.status, 0u, (uint32_t)PB_ETIMEOUT);
@@ -1080,7 +1094,7 @@ cudaError_t mlp_fused_logq(pb_mlp* p, const uint32_t* P, uint32_t beta, int chai
   dim3 grid((chains + 127) / 128, p->d - k + 1);
   const size_t smem = fused_layout(a);
   if (smem == 0) return cudaErrorInvalidValue;
-  mlp_fused_kernel<kFusedLogQ><<<grid, 256, smem, st>>>(a);
+  mlp_fused_kernel<kFusedLogQ><<<grid, kFusedThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1103,7 +1117,7 @@ cudaError_t mlp_fused_sample(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uint32_
   a.group0 = group0;
   const size_t smem = fused_layout(a);
   if (smem == 0) return cudaErrorInvalidValue;
-  mlp_fused_kernel<kFusedSample><<<(chains + 127) / 128, 256, smem, st>>>(a);
+  mlp_fused_kernel<kFusedSample><<<(chains + 127) / 128, kFusedThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1125,7 +1139,7 @@ cudaError_t mlp_forward_fused(pb_mlp* p, int rows) {
   a.n = p->n;
   const size_t smem = fused_layout(a);
   if (smem == 0) return cudaErrorInvalidValue;
-  mlp_fused_kernel<kFusedLogits><<<(rows + 127) / 128, 256, smem, p->st>>>(a);
+  mlp_fused_kernel<kFusedLogits><<<(rows + 127) / 128, kFusedThreads, smem, p->st>>>(a);
   return cudaGetLastError();
 }
 
