@@ -206,10 +206,14 @@ __global__ void accept_kernel(uint32_t* __restrict__ P, const uint32_t* __restri
   const uint32_t gc = group0 * 32u + c;
   const uint32_t u = philox4x32_10(make_uint4(gc, move, 0xFFFFu | (kTagMH << 16), 0u), k0, k1).x;
   const float uf = ((float)(u >> 8) + 0.5f) * (1.f / 16777216.f);
-  if (logf(uf) < logA) {
+  const bool acc = logf(uf) < logA;
+  // one counter update per warp (the accepted lanes' count)
+  const unsigned act = __activemask();
+  const unsigned accm = __ballot_sync(act, acc);
+  if (accm != 0u && (int)(threadIdx.x & 31u) == __ffs((int)act) - 1)
+    atomicAdd(n_accept, (unsigned long long)__popc(accm));
+  if (acc)
     for (int j = k; j <= d; ++j) P[(size_t)c * d + (j - 1)] = prop[j - 1];
-    atomicAdd(n_accept, 1ull);
-  }
 }
 
 __global__ void mh_advance_kernel(uint32_t* move_dev) { *move_dev += 1u; }
