@@ -18,20 +18,22 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "general.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-H, S, T, CNOT, CZ = 0, 1, 2, 3, 4
+H, S, T, CNOT, CZ, U = 0, 1, 2, 3, 4, 5
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc, OpenMP, -O2)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile oracle.c and general.c into liboracle.so (gcc, OpenMP, -O2)."""
+    if force or not os.path.exists(_LIB) or \
+            os.path.getmtime(_LIB) < max(os.path.getmtime(s) for s in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC", "-shared",
-             _SRC, "-o", tmp, "-lm"])
+            ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fopenmp",
+             "-fPIC", "-shared"] + _SRCS + ["-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -47,7 +49,8 @@ def _load():
             lib.orc_philox4x32_10.restype = None
             for name in ("orc_statevector", "orc_pathsum_exact", "orc_gf2_rank",
                          "orc_colour", "orc_gibbs", "orc_elim", "orc_elim_clamped", "orc_violations", "orc_path_phase",
-                         "orc_thresholds"):
+                         "orc_thresholds", "orc_u_statevector", "orc_u_pathstats", "orc_u_gibbs",
+                         "orc_u_elim", "orc_u_log2z"):
                 getattr(lib, name).restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -252,3 +255,121 @@ def estimate_amplitudes(cnt: np.ndarray, valid: int, h: int) -> np.ndarray:
     """Eq. U23 with uniform valid paths: psi_hat = 2^{h/2} sum_b cnt[.,b] w^b / valid."""
     w = np.exp(1j * np.pi * np.arange(8) / 4.0)
     return (cnt.astype(np.float64) @ w) * (2.0 ** (h / 2.0)) / max(valid, 1)
+
+
+# ---- general one-qubit gates (general.c)
+
+def _mats(gates, mats) -> np.ndarray:
+    """Gate matrices as float64 [n_gates, 8]: Re/Im of U00, U01, U10, U11
+    (rows = output bit); rows of non-U gates are ignored."""
+    g = _gates(gates)
+    m = np.zeros((len(g), 8), dtype=np.float64)
+    if mats is not None:
+        c = np.asarray(mats, dtype=np.complex128).reshape(len(g), 4)
+        m[:, 0::2] = c.real
+        m[:, 1::2] = c.imag
+    return np.ascontiguousarray(m)
+
+
+def u_statevector(n: int, d: int, gates, mats, beta: int = 0) -> np.ndarray:
+    """FP64 state vector of a circuit with general one-qubit gates (op U)."""
+    lib = _load()
+    g = _gates(gates)
+    m = _mats(g, mats)
+    re = np.zeros(1 << n)
+    im = np.zeros(1 << n)
+    rc = lib.orc_u_statevector(n, d, _p(g), len(g), _p(m), ctypes.c_uint32(beta), _p(re), _p(im))
+    if rc != 0:
+        raise ValueError(f"orc_u_statevector failed ({rc})")
+    return re + 1j * im
+
+
+def u_pathstats(n: int, d: int, gates, mats, beta: int = 0) -> dict:
+    """Brute-force path sum per output: U (complex), zabs = sum |U_C|,
+    s2 = sum |U_C|^2, npath = nonzero paths; std_weighted = sqrt(zabs^2 - |U|^2)
+    and std_uniform = sqrt(npath s2 - |U|^2) (Eq. U30, paths to each output)."""
+    lib = _load()
+    g = _gates(gates)
+    m = _mats(g, mats)
+    N = 1 << n
+    ure, uim, zabs, s2 = (np.zeros(N) for _ in range(4))
+    npath = np.zeros(N, dtype=np.uint64)
+    rc = lib.orc_u_pathstats(n, d, _p(g), len(g), _p(m), ctypes.c_uint32(beta), _p(ure), _p(uim),
+                             _p(zabs), _p(s2), _p(npath))
+    if rc != 0:
+        raise ValueError(f"orc_u_pathstats failed ({rc})")
+    U = ure + 1j * uim
+    a2 = np.abs(U) ** 2
+    return {"U": U, "zabs": zabs, "s2": s2, "npath": npath,
+            "std_weighted": np.sqrt(np.maximum(zabs ** 2 - a2, 0.0)),
+            "std_uniform": np.sqrt(np.maximum(npath.astype(np.float64) * s2 - a2, 0.0))}
+
+
+def u_log2z(n: int, d: int, gates, mats) -> float:
+    lib = _load()
+    g = _gates(gates)
+    m = _mats(g, mats)
+    out = ctypes.c_double(0.0)
+    rc = lib.orc_u_log2z(n, d, _p(g), len(g), _p(m), ctypes.byref(out))
+    if rc != 0:
+        raise ValueError(f"orc_u_log2z failed ({rc})")
+    return out.value
+
+
+def _u_run(fn, n, d, gates, mats, chains, alphas, extra_args, state_arg):
+    lib = _load()
+    g = _gates(gates)
+    m = _mats(g, mats)
+    if alphas is None:
+        bins, al = 1 << n, None
+    else:
+        al = np.ascontiguousarray(alphas, dtype=np.uint32)
+        bins = len(al)
+    sre, sim = np.zeros(bins), np.zeros(bins)
+    cnt = np.zeros(bins, dtype=np.uint64)
+    valid, samples, l2z = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_double(0.0)
+    rc = getattr(lib, fn)(n, d, _p(g), len(g), _p(m), *extra_args, state_arg,
+                          None if al is None else _p(al), 0 if al is None else len(al),
+                          _p(sre), _p(sim), _p(cnt), ctypes.byref(valid), ctypes.byref(samples),
+                          ctypes.byref(l2z))
+    if rc != 0:
+        raise ValueError(f"{fn} failed ({rc})")
+    return {"sum": sre + 1j * sim, "cnt": cnt, "valid": valid.value, "samples": samples.value,
+            "log2z": l2z.value}
+
+
+def u_gibbs(n: int, d: int, gates, mats, *, J: float, seed: int, chains: int, sweeps: int,
+            beta: int = 0, chain0: int = 0, sweep0: int = 0, burn_in: int = 0,
+            record_every: int = 1, state: np.ndarray | None = None, alphas=None) -> dict:
+    """Reference Gibbs run with general one-qubit gates (proposal by heat-bath
+    on the J energy, Metropolis acceptance on the coupling energy).  Returns
+    dict(state, sum = sum of e^{i arg U_C} per bin, cnt, valid, samples, log2z);
+    psi = 2^log2z sum / valid."""
+    init = 1 if state is None else 0
+    st = np.zeros((chains, d), dtype=np.uint32) if state is None else \
+        np.ascontiguousarray(state, dtype=np.uint32).copy()
+    args = (ctypes.c_uint32(beta), ctypes.c_double(J), ctypes.c_uint64(seed), ctypes.c_uint32(chain0),
+            ctypes.c_uint32(chains), ctypes.c_uint32(sweep0), ctypes.c_uint32(sweeps),
+            ctypes.c_uint32(burn_in), ctypes.c_uint32(record_every), init)
+    out = _u_run("orc_u_gibbs", n, d, gates, mats, chains, alphas, args, _p(st))
+    out["state"] = st
+    return out
+
+
+def u_elim(n: int, d: int, gates, mats, *, seed: int, chains: int, sweeps: int, beta: int = 0,
+           chain0: int = 0, sweep0: int = 0, burn_in: int = 0, record_every: int = 1,
+           alphas=None) -> dict:
+    """Exact i.i.d. sampler with general one-qubit gates; outputs as u_gibbs
+    (state = each chain's last drawn path)."""
+    st = np.zeros((chains, d), dtype=np.uint32)
+    args = (ctypes.c_uint32(beta), ctypes.c_uint64(seed), ctypes.c_uint32(chain0),
+            ctypes.c_uint32(chains), ctypes.c_uint32(sweep0), ctypes.c_uint32(sweeps),
+            ctypes.c_uint32(burn_in), ctypes.c_uint32(record_every))
+    out = _u_run("orc_u_elim", n, d, gates, mats, chains, alphas, args, _p(st))
+    out["state"] = st
+    return out
+
+
+def u_estimate(run: dict) -> np.ndarray:
+    """psi_hat = 2^log2z * (sum of phases) / valid (Eq. U23 with p_C ~ |U_C|)."""
+    return run["sum"] * (2.0 ** run["log2z"]) / max(run["valid"], 1)

@@ -22,8 +22,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-H, S, T, CNOT, CZ = 0, 1, 2, 3, 4
-GATE_NAMES = {H: "H", S: "S", T: "T", CNOT: "CNOT", CZ: "CZ"}
+H, S, T, CNOT, CZ, U = 0, 1, 2, 3, 4, 5
+GATE_NAMES = {H: "H", S: "S", T: "T", CNOT: "CNOT", CZ: "CZ", U: "U"}
 _MASK64 = (1 << 64) - 1
 
 
@@ -93,6 +93,47 @@ def random_circuit(n: int, d: int, seed: int, one_gate_per_layer: bool = False) 
                 rows.append((op, layer, q, -1))
                 free[q] = False
     return np.asarray(rows, dtype=np.int32).reshape(-1, 4)
+
+
+def rotated_h(theta: float) -> np.ndarray:
+    """The rotated Hadamard of Eq. HadT, [[cos t, sin t], [sin t, -cos t]]
+    (rows = output bit): t = pi/4 is H, t = pi/2 the classical NOT."""
+    c, s = np.cos(theta), np.sin(theta)
+    return np.array([[c, s], [s, -c]], dtype=np.complex128)
+
+
+def u3(theta: float, phi: float, lam: float) -> np.ndarray:
+    """The usual three-angle one-qubit unitary
+    [[cos(t/2), -e^{i lam} sin(t/2)], [e^{i phi} sin(t/2), e^{i(phi+lam)} cos(t/2)]]."""
+    c, s = np.cos(theta / 2), np.sin(theta / 2)
+    return np.array([[c, -np.exp(1j * lam) * s],
+                     [np.exp(1j * phi) * s, np.exp(1j * (phi + lam)) * c]], dtype=np.complex128)
+
+
+def rotated_h_chain(d: int, theta: float):
+    """n = 1, d rotated Hadamards in series (Sec. 4.2, Fig. 5): (gates, mats)
+    with mats complex128[d, 2, 2]."""
+    g = np.asarray([(U, k, 0, -1) for k in range(d)], dtype=np.int32).reshape(-1, 4)
+    return g, np.stack([rotated_h(theta)] * d)
+
+
+def random_general_circuit(n: int, d: int, seed: int, frac_u: float = 0.3):
+    """random_circuit(n, d, seed) with each one-qubit gate replaced, with
+    probability frac_u, by a U gate of three angles drawn uniformly in
+    [0, 2 pi) (SplitMix64(seed ^ 0x9E37)).  Returns (gates, mats), mats
+    complex128[n_gates, 2, 2] (zero rows for the other gates)."""
+    g = random_circuit(n, d, seed).copy()
+    rng = SplitMix64(seed ^ 0x9E37)
+    mats = np.zeros((len(g), 2, 2), dtype=np.complex128)
+
+    def unif() -> float:
+        return (rng.next() >> 11) * (2.0 ** -53)
+
+    for i in range(len(g)):
+        if g[i, 0] in (H, S, T) and unif() < frac_u:
+            g[i, 0] = U
+            mats[i] = u3(2 * np.pi * unif(), 2 * np.pi * unif(), 2 * np.pi * unif())
+    return g, mats
 
 
 def hadamard_chain(d: int) -> np.ndarray:
