@@ -54,7 +54,20 @@ typedef enum {
  *        with the global phase fixed so that <0|G|0> = 1)
  *   CNOT: control q0, target q1, x_t -> x_t XOR x_c  (Appendix, "CNOT Gate")
  *   CZ  = diag(1,1,1,-1) on (q0, q1)  (diagonal two-qubit gate, Appendix)   */
-typedef enum { PB_H = 0, PB_S = 1, PB_T = 2, PB_CNOT = 3, PB_CZ = 4 } pb_op;
+typedef enum { PB_H = 0, PB_S = 1, PB_T = 2, PB_CNOT = 3, PB_CZ = 4, PB_U = 5 } pb_op;
+/* PB_U: a general one-qubit gate with a caller-given 2x2 complex matrix U
+ * (pb_compile_u; Sec. 2 Eq. EB, e.g. the rotated Hadamard of Eq. HadT).  U
+ * must be unitary within 1e-9 (max |(U^dagger U - I)_ij|).  Kinds:
+ *   diagonal      (U01 = U10 = 0 exactly): the output copies the input, a
+ *                 different output bit costs J (a J-linked copy);
+ *   anti-diagonal (U00 = U11 = 0 exactly): the output is NOT the input
+ *                 (a J-linked NOT);
+ *   coupled       (all four entries nonzero): a free output bit with the real
+ *                 energy K [s_out != s_in], K = ln(a / b), a = (|U00| + |U11|)/2,
+ *                 b = (|U01| + |U10|)/2, |z| = hypot(Re z, Im z) (Eq. EB for a
+ *                 unitary: the one-body terms cancel into this two-body term);
+ *   one zero entry only: rejected (PB_EINVAL).
+ * Every PB_U gate adds the phase arg U(s_out, s_in) to the path. */
 
 /* One gate: layer in [0, d) maps s_layer to s_{layer+1}; 1-qubit gates set
  * q1 = -1.  Each qubit appears at most once per layer. */
@@ -82,6 +95,33 @@ PB_API int pb_compile(int n_qubits, int n_layers, const pb_gate* gates,
                       int n_gates, uint32_t input_bits, double J,
                       pb_model** out);
 
+/* pb_compile with general one-qubit gates (op PB_U).  mats: 8 doubles per
+ * gate row (host, caller-owned; rows of other ops are ignored, NULL allowed
+ * when no row is PB_U): Re U00, Im U00, Re U01, Im U01, Re U10, Im U10,
+ * Re U11, Im U11 with U_yx = <y|U|x> (row = output bit).  A model with a
+ * PB_U gate records complex phase sums instead of the 8 phase classes
+ * (pb_run_phase_sums; pb_run_histogram returns PB_ESTATE for it), and a
+ * model with a coupled gate samples p_C ~ |U_C| (Eq. weightedS):
+ *   Gibbs (PB_GIBBS): the heat-bath draw on the J-penalty energy proposes
+ *     x' for p-bit x = (k, q); if x' != x, the flip is accepted when
+ *     dK = K_in (1 - 2 e_in) + K_out (1 - 2 e_out) <= 0, else when
+ *     u' < min(floor(2^32 e^{-dK}), 2^32 - 1), with K_in, e_in = x XOR
+ *     s_{k-1,q} for a coupled gate in layer k-1 on q (else 0, 0), K_out,
+ *     e_out = x XOR s_{k+1,q} for a coupled gate in layer k on q (else 0, 0),
+ *     and u' the uniform of the tag-6 stream (Metropolis-Hastings with the
+ *     heat-bath as proposal, Fig. 2 Steps 1-2).
+ *   Exact sampler (PB_ELIM): a coupled output is s_in XOR [u < floor(2^32
+ *     b / (a + b))], u the tag-4 uniform of that p-bit (planes j = 0..31 as
+ *     for the sweep's draws).
+ * The amplitude estimate is 2^{log2z} (sum of phases) / valid, log2z =
+ * h/2 + sum over coupled gates of log2(a + b).  Such models may not use
+ * PB_ELIM_CLAMP when a gate is coupled, the learned proposal or
+ * pb_gibbs_run_noalloc (PB_EINVAL).  Errors as pb_compile, plus PB_EINVAL
+ * for a matrix that is not unitary or has a single zero entry. */
+PB_API int pb_compile_u(int n_qubits, int n_layers, const pb_gate* gates,
+                        int n_gates, const double* mats, uint32_t input_bits,
+                        double J, pb_model** out);
+
 typedef struct {
   int32_t n, d;        /* qubits, gate layers                          */
   int32_t n_pbits;     /* n (d + 1), input layer included              */
@@ -92,6 +132,9 @@ typedef struct {
   uint32_t input_bits;
   uint32_t thr[4];     /* heat-bath thresholds for |v| = 0..3         */
   int32_t colour_size[4];
+  int32_t n_u;         /* PB_U gates                                   */
+  int32_t n_coupled;   /* coupled PB_U gates (free outputs)            */
+  double log2z;        /* log2 of the estimator scale (h/2 + ...)      */
 } pb_model_info_t;
 
 PB_API int pb_model_info(const pb_model* m, pb_model_info_t* info);
@@ -106,7 +149,8 @@ PB_API void pb_model_free(pb_model* m);
  * sweep t for p-bit p = (k-1) n + q are Philox4x32-10 outputs under key =
  * seed at counter (c / 32, t, p | tag << 16, j / 4), word j % 4, j = 0..31:
  * bit c % 32 of word j is bit 31-j of the chain's uniform u (tag 0 = sweep,
- * tag 1 = initial H outputs).  A p-bit whose violation count changes by v
+ * tag 1 = initial H and coupled-PB_U outputs, tag 6 = the Metropolis
+ * acceptance of coupled p-bits).  A p-bit whose violation count changes by v
  * when it goes 0 -> 1 is redrawn as [v < 0] XOR [u < thr[|v|]]  (heat-bath,
  * Fig. 2 Steps 1-2).  One sweep visits the four colour classes in order. */
 enum { PB_GIBBS = 0, PB_LEARNED = 1, PB_ELIM = 2, PB_ELIM_CLAMP = 3 };
@@ -178,8 +222,18 @@ PB_API int pb_run_wait(pb_run* run);
 PB_API int pb_run_histogram(const pb_run* run, int model, uint64_t* counts,
                             uint64_t* valid_total, uint64_t* samples_total);
 
+/* Phase sums of model `model` (synchronous), any model: per bin, summed over
+ * batches, re + i im = sum over the valid recorded samples ending there of
+ * e^{i arg U_C} (FP64 sums of the device's per-sample phases: fixed-point
+ * angles of 2^-32 turn per PB_U gate, sincospi in FP64), counts = their
+ * number.  For a model without PB_U gates the sums are formed from the
+ * exact phase classes.  Any pointer may be NULL. */
+PB_API int pb_run_phase_sums(const pb_run* run, int model, double* re, double* im,
+                             uint64_t* counts, uint64_t* valid_total, uint64_t* samples_total);
+
 /* Amplitude estimates (Eq. U23, uniform valid paths; computed on the device):
- * psi[bin] = 2^{h/2} sum_b counts[bin][b] w^b / valid_total, and its standard
+ * psi[bin] = 2^{h/2} sum_b counts[bin][b] w^b / valid_total (with PB_U gates
+ * 2^{log2z} times the phase sum / valid_total), and its standard
  * error from batch means over chain groups (Eq. U26).  l2_normalize != 0
  * divides by the L2 norm over the recorded bins (Fig. 2 Step 4).
  * re, im, se: host arrays of `bins` doubles (se may be NULL). */

@@ -20,7 +20,7 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
                         cudaStream_t st);
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
-                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st);
+                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt = false);
 size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins);
 cudaError_t sweep_prepare();
 }  // namespace pb
@@ -63,6 +63,7 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
   if (!m || !cfg || !d_counts || !d_totals) return PB_EINVAL;
   if (cfg->sampler != PB_GIBBS || cfg->alphas != nullptr || cfg->n_alphas != 0) return PB_EINVAL;
   if (cfg->chains == 0 || cfg->record_every == 0) return PB_EINVAL;
+  if (m->wgt) return PB_EINVAL;  // general one-qubit gates: use pb_run_create
   if (m->n > 16) return PB_ERANGE;
   if (n_sweeps > (1u << 26)) return PB_ERANGE;
   if ((uint64_t)cfg->group0 + (cfg->chains + 31) / 32 > 0xFFFFFFFFull) return PB_ERANGE;

@@ -23,7 +23,8 @@ __host__ __device__ inline int n_words(int n, int d) { return (d + 1) * n + 2; }
 // v = sum_i (1 - 2 r_i) when it goes 0 -> 1.
 struct Desc {
   uint16_t dst;   // word index of the p-bit (k*n + q)
-  uint8_t mflag;  // bits 0-1: m (links), bit 2: link 0 is the p-bit's own link
+  uint8_t mflag;  // bits 0-1: m (links), bit 2: link 0 is the p-bit's own link,
+                  // bit 3: coupled (Metropolis acceptance, see Cpl)
   uint8_t pair;   // threshold pair: 0 (t0,t0) 1 (t1,t1) 2 (t2,t0) 3 (t3,t1)
   uint16_t a[3];
   uint16_t b[3];
@@ -41,6 +42,31 @@ struct Rec {
 };
 static_assert(sizeof(Rec) == 16, "Rec must be 16 bytes");
 
+// Coupling of one p-bit to the neighbours of its coupled general gates
+// (32 bytes, by p; models with PB_U gates only).  Category c = e_in + 2 e_out
+// with e_in = x ^ W[win], e_out = x ^ W[wout] (win / wout = the p-bit's own
+// word where it has no such neighbour): a proposed flip is accepted always
+// (amask bit c) or when the tag-6 uniform is below A[c].  B: the exact
+// sampler's threshold of a coupled output.  flags bit 0: the p-bit has a
+// coupling; bit 1: it is the output of a coupled gate.
+struct Cpl {
+  uint16_t win, wout;
+  uint32_t amask;
+  uint32_t A[4];
+  uint32_t B;
+  uint32_t flags;
+};
+static_assert(sizeof(Cpl) == 32, "Cpl must be 32 bytes");
+
+// Phase of one general gate (32 bytes): ph[2 y + x] = arg U_yx in units of
+// 2^-32 turn, y = bit W[wout], x = bit W[win] of the chain.
+struct UPh {
+  uint32_t ph[4];
+  uint16_t wout, win;
+  uint32_t pad[3];
+};
+static_assert(sizeof(UPh) == 32, "UPh must be 32 bytes");
+
 // Per-model device header (in the workspace).
 struct ModelDev {
   int32_t n, d, nw;        // qubits, layers, words per group image
@@ -49,6 +75,10 @@ struct ModelDev {
   uint32_t thr[4];
   int32_t col_off[5];      // descriptor ranges per colour class
   int32_t max_col;         // largest colour class
+  int32_t wgt;             // 1: PB_U gates (complex phase sums, couplings)
+  int32_t n_ug;            // PB_U gates (UPh entries)
+  int32_t pad0;
+  double log2z;            // log2 of the estimator scale
 };
 
 // Per-model run entry (device), one per model of a run.
@@ -79,6 +109,11 @@ struct RunModelDev {
   const uint32_t* clamp_tab;
   int32_t clamp_mw, clamp_nfree, clamp_ok;  // clamp_ok = 0: alpha unreachable
   int32_t pad2;
+  // models with PB_U gates (else nullptr): couplings by p, gate phases.
+  // Their histogram slots per (batch, bin) are {re (double), im (double),
+  // count (u64), unused...} instead of 8 phase-class counters.
+  const Cpl* cpl;
+  const UPh* uph;
 };
 
 // Workspace header at offset 0.
@@ -98,6 +133,7 @@ constexpr uint32_t kTagInit = 1;
 constexpr uint32_t kTagMH = 2;
 constexpr uint32_t kTagElim = 4;  // exact sampler's H outputs (tag 3: training rows)
 constexpr uint32_t kTagClamp = 5;  // free draws of the output-clamped exact sampler
+constexpr uint32_t kTagCouple = 6;  // Metropolis acceptance of coupled p-bits
 
 }  // namespace pb
 
@@ -112,8 +148,14 @@ struct pb_model {
   std::vector<int32_t> colour;        // [d][n]
   std::vector<pb::Desc> desc;         // colour-ordered
   std::vector<pb::Rec> rec;           // by p = (k-1) n + q
-  std::vector<uint32_t> init;         // by p: 0xFFFFFFFF = H output, else a | b << 16
+  std::vector<uint32_t> init;         // by p: 0xFFFFFFFF = free output, else a | b << 16
   std::vector<pb_gate> gates;
+  // general one-qubit gates
+  bool wgt = false;                   // any PB_U gate
+  int n_u = 0, n_coupled = 0;
+  double log2z = 0.0;
+  std::vector<pb::Cpl> cpl;           // by p (wgt only)
+  std::vector<pb::UPh> uph;           // one per PB_U gate
 };
 
 // Proposal network (host side of pb_mlp): fp32 master weights, Adam state,

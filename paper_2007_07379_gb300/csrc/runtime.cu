@@ -21,7 +21,7 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
                         cudaStream_t st);
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
-                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st);
+                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt = false);
 cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
                                      uint32_t n_work, uint32_t n_sweeps, int cons, int prod,
                                      int max_col, int nc, int grid, size_t smem_bytes,
@@ -48,7 +48,51 @@ struct Slot {
   int op = -1;       // -1 identity wire
   int partner = -1;  // other qubit of a 2-qubit gate
   bool target = false;  // CNOT target
+  int ukind = 0;     // PB_U: kUDiag, kUAnti or kUCoupled
+  double a = 0.0, b = 0.0, K = 0.0;  // PB_U magnitudes and coupling
 };
+
+enum { kUDiag = 1, kUAnti = 2, kUCoupled = 3 };
+
+// Kind of a PB_U matrix (8 doubles: Re/Im of U00, U01, U10, U11, row =
+// output) with its magnitudes a = (|U00|+|U11|)/2, b = (|U01|+|U10|)/2 and
+// coupling K = ln(a/b) (Eq. EB for a unitary); -1 when it is not unitary
+// within 1e-9 or has a single zero entry.
+int classify_u(const double* m, double& a, double& b, double& K) {
+  auto re = [&](int y, int x) { return m[2 * (2 * y + x)]; };
+  auto im = [&](int y, int x) { return m[2 * (2 * y + x) + 1]; };
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      double sr = 0.0, si = 0.0;  // (U^dagger U)_ij
+      for (int y = 0; y < 2; ++y) {
+        sr += re(y, i) * re(y, j) + im(y, i) * im(y, j);
+        si += re(y, i) * im(y, j) - im(y, i) * re(y, j);
+      }
+      if (!(std::fabs(sr - (i == j ? 1.0 : 0.0)) <= 1e-9) || !(std::fabs(si) <= 1e-9)) return -1;
+    }
+  auto zero = [&](int y, int x) { return re(y, x) == 0.0 && im(y, x) == 0.0; };
+  a = 0.5 * (std::hypot(re(0, 0), im(0, 0)) + std::hypot(re(1, 1), im(1, 1)));
+  b = 0.5 * (std::hypot(re(0, 1), im(0, 1)) + std::hypot(re(1, 0), im(1, 0)));
+  K = 0.0;
+  const bool z00 = zero(0, 0), z01 = zero(0, 1), z10 = zero(1, 0), z11 = zero(1, 1);
+  if (z01 && z10 && !z00 && !z11) return kUDiag;
+  if (z00 && z11 && !z01 && !z10) return kUAnti;
+  if (z00 || z01 || z10 || z11) return -1;
+  K = std::log(a / b);
+  return kUCoupled;
+}
+
+// floor(2^32 x) for x >= 0, capped at 2^32 - 1 (a uniform u accepts when u < it).
+uint32_t u32_threshold(double x) {
+  const double t = std::floor(x * 4294967296.0);
+  return t >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)t;
+}
+
+// arg z in units of 2^-32 turn (mod 2^32).
+uint32_t fixed_turns(double re, double im) {
+  const double t = std::atan2(im, re) / (2.0 * M_PI);  // [-1/2, 1/2]
+  return (uint32_t)(uint64_t)(int64_t)std::llround(t * 4294967296.0);
+}
 
 // GF(2) rank of the rows (bitsets over the H variables), by inserting each
 // row into an XOR basis keyed by its highest set bit.
@@ -94,6 +138,11 @@ PB_API const char* pb_strerror(int s) {
 
 PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t input_bits,
                       double J, pb_model** out) {
+  return pb_compile_u(n, d, gates, n_gates, nullptr, input_bits, J, out);
+}
+
+PB_API int pb_compile_u(int n, int d, const pb_gate* gates, int n_gates, const double* mats,
+                        uint32_t input_bits, double J, pb_model** out) {
   if (!out) return PB_EINVAL;
   *out = nullptr;
   if (n < 1 || n > 32 || d < 1 || d > 64) return PB_ERANGE;
@@ -104,13 +153,18 @@ PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t 
   std::vector<Slot> slot((size_t)d * n);
   for (int i = 0; i < n_gates; ++i) {
     const pb_gate& g = gates[i];
-    if (g.op < PB_H || g.op > PB_CZ || g.layer < 0 || g.layer >= d) return PB_EINVAL;
+    if (g.op < PB_H || g.op > PB_U || g.layer < 0 || g.layer >= d) return PB_EINVAL;
     if (g.q0 < 0 || g.q0 >= n) return PB_EINVAL;
     const bool two = g.op == PB_CNOT || g.op == PB_CZ;
     if (two && (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0)) return PB_EINVAL;
     Slot& s0 = slot[(size_t)g.layer * n + g.q0];
     if (s0.op != -1) return PB_EINVAL;
     s0.op = g.op;
+    if (g.op == PB_U) {
+      if (!mats) return PB_EINVAL;
+      s0.ukind = classify_u(mats + 8 * (size_t)i, s0.a, s0.b, s0.K);
+      if (s0.ukind < 0) return PB_EINVAL;
+    }
     if (two) {
       Slot& s1 = slot[(size_t)g.layer * n + g.q1];
       if (s1.op != -1) return PB_EINVAL;
@@ -138,6 +192,16 @@ PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t 
   const uint16_t Z = (uint16_t)zero_idx(n, d), O = (uint16_t)ones_idx(n, d);
   auto at = [&](int layer, int q) -> const Slot& { return slot[(size_t)layer * n + q]; };
   auto word = [&](int k, int q) -> uint16_t { return (uint16_t)(k * n + q); };
+  // free outputs: H and coupled PB_U; the second word of a single-input
+  // link: the CNOT control (target), ONES (anti-diagonal PB_U: NOT), ZERO
+  auto is_free = [](const Slot& s) { return s.op == PB_H || (s.op == PB_U && s.ukind == kUCoupled); };
+  auto coupled = [](const Slot& s) { return s.op == PB_U && s.ukind == kUCoupled; };
+  for (int i = 0; i < n_gates; ++i)
+    if (gates[i].op == PB_U) {
+      m->wgt = true;
+      ++m->n_u;
+      m->n_coupled += coupled(at(gates[i].layer, gates[i].q0)) ? 1 : 0;
+    }
 
   const int npb = n * d;
   std::vector<Desc> by_p(npb);
@@ -154,18 +218,23 @@ PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t 
       bool own = false;
       // own link: gate layer k-1 produces s_k
       const Slot& prod = at(k - 1, q);
-      if (prod.op != PB_H) {
+      auto second = [&](const Slot& s, int layer) -> uint16_t {
+        if (s.op == PB_CNOT && s.target) return word(layer, s.partner);
+        if (s.op == PB_U && s.ukind == kUAnti) return O;
+        return Z;
+      };
+      if (!is_free(prod)) {
         own = true;
         D.a[m_links] = word(k - 1, q);
-        D.b[m_links] = (prod.op == PB_CNOT && prod.target) ? word(k - 1, prod.partner) : Z;
+        D.b[m_links] = second(prod, k - 1);
         ++m_links;
       }
       bool tgt_next = false;
       if (k < d) {
         const Slot& cons = at(k, q);  // gate layer k consumes s_k
-        if (cons.op != PB_H) {        // the wire's next bit demands s_k[q]
+        if (!is_free(cons)) {         // the wire's next bit demands s_k[q]
           D.a[m_links] = word(k + 1, q);
-          D.b[m_links] = (cons.op == PB_CNOT && cons.target) ? word(k, cons.partner) : Z;
+          D.b[m_links] = second(cons, k);
           ++m_links;
         }
         if (cons.op == PB_CNOT && !cons.target) {  // control: the target's next bit
@@ -176,6 +245,30 @@ PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t 
         tgt_next = cons.op == PB_CNOT && cons.target;
       }
       D.mflag = (uint8_t)(m_links | (own ? 4 : 0));
+      if (m->wgt) {  // couplings of the p-bit (Metropolis acceptance table)
+        Cpl C{};
+        C.win = C.wout = D.dst;
+        double kin = 0.0, kout = 0.0;
+        if (coupled(prod)) {
+          C.win = word(k - 1, q);
+          kin = prod.K;
+          C.flags |= 3u;
+          C.B = u32_threshold(prod.b / (prod.a + prod.b));
+        }
+        if (k < d && coupled(at(k, q))) {
+          C.wout = word(k + 1, q);
+          kout = at(k, q).K;
+          C.flags |= 1u;
+        }
+        for (int c = 0; c < 4; ++c) {
+          const int ein = c & 1, eout = c >> 1;
+          const double dk = kin * (double)(1 - 2 * ein) + kout * (double)(1 - 2 * eout);
+          if (dk <= 0.0) C.amask |= 1u << c;
+          else C.A[c] = u32_threshold(std::exp(-dk));
+        }
+        if (C.flags & 1u) D.mflag |= 8;
+        m->cpl.push_back(C);
+      }
       static const uint8_t pair_of_m[4] = {0, 1, 2, 3};
       D.pair = pair_of_m[m_links];
       by_p[p] = D;
@@ -212,14 +305,22 @@ PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t 
   // classes 2 [k even] + [CNOT target in layer k+1] set above.
   {
     std::vector<std::vector<int>> nb(npb);
+    auto join = [&](int p, int u) {
+      if (std::find(nb[p].begin(), nb[p].end(), u) == nb[p].end()) nb[p].push_back(u);
+    };
     for (int p = 0; p < npb; ++p) {
       const pb::Desc& D = by_p[p];
       for (int l = 0; l < (D.mflag & 3); ++l)
         for (int w : {(int)D.a[l], (int)D.b[l]})
-          if (w >= n && w < (d + 1) * n && w - n != p &&
-              std::find(nb[p].begin(), nb[p].end(), w - n) == nb[p].end())
-            nb[p].push_back(w - n);
+          if (w >= n && w < (d + 1) * n && w - n != p) join(p, w - n);
     }
+    // a coupled PB_U in layer L >= 1 joins p-bits (L, q) and (L + 1, q)
+    for (int L = 1; L < d; ++L)
+      for (int q = 0; q < n; ++q)
+        if (coupled(at(L, q))) {
+          join((L - 1) * n + q, L * n + q);
+          join(L * n + q, (L - 1) * n + q);
+        }
     std::vector<int> col(npb, -1);
     std::vector<uint32_t> seen(npb, 0u);
     int ncol = 0;
@@ -252,19 +353,39 @@ PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t 
   }
   m->col_off[4] = (int)m->desc.size();
 
-  // h, M and the GF(2) rank of H outputs -> s_d
+  // general gates: phases (units of 2^-32 turn) and the estimator scale
+  // log2z = h/2 + sum over coupled gates of log2(a + b), in gate order
+  double l2z = 0.0;
+  for (int i = 0; i < n_gates; ++i) {
+    const pb_gate& g = gates[i];
+    if (g.op == PB_H) l2z += 0.5;
+    if (g.op != PB_U) continue;
+    const Slot& s = at(g.layer, g.q0);
+    if (s.ukind == kUCoupled) l2z += std::log2(s.a + s.b);
+    UPh P{};
+    const double* mu = mats + 8 * (size_t)i;
+    for (int y = 0; y < 2; ++y)
+      for (int x = 0; x < 2; ++x) P.ph[2 * y + x] = fixed_turns(mu[2 * (2 * y + x)], mu[2 * (2 * y + x) + 1]);
+    P.wout = word(g.layer + 1, g.q0);
+    P.win = word(g.layer, g.q0);
+    m->uph.push_back(P);
+  }
+  m->log2z = l2z;
+
+  // h, M and the GF(2) rank of the free outputs (H, coupled PB_U) -> s_d
   int h = 0;
   for (int i = 0; i < n_gates; ++i) h += gates[i].op == PB_H;
   m->h = h;
-  m->M = npb - h;
+  m->M = npb - h - m->n_coupled;
   {
-    std::vector<std::vector<uint64_t>> wire(n, std::vector<uint64_t>((h + 63) / 64 + 1, 0));
+    const int nvar = h + m->n_coupled;
+    std::vector<std::vector<uint64_t>> wire(n, std::vector<uint64_t>((nvar + 63) / 64 + 1, 0));
     int var = 0;
     for (int L = 0; L < d; ++L) {
       std::vector<std::vector<uint64_t>> nxt = wire;
       for (int q = 0; q < n; ++q) {
         const Slot& s = at(L, q);
-        if (s.op == PB_H) {
+        if (is_free(s)) {
           std::fill(nxt[q].begin(), nxt[q].end(), 0);
           nxt[q][var >> 6] |= 1ull << (var & 63);
           ++var;
@@ -274,7 +395,7 @@ PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t 
       }
       wire.swap(nxt);
     }
-    m->rank = h > 0 ? gf2_rank_rows(wire, h) : 0;
+    m->rank = nvar > 0 ? gf2_rank_rows(wire, nvar) : 0;
   }
   *out = m.release();
   return PB_OK;
@@ -294,6 +415,9 @@ PB_API int pb_model_info(const pb_model* m, pb_model_info_t* info) {
     info->thr[i] = m->thr[i];
     info->colour_size[i] = m->col_off[i + 1] - m->col_off[i];
   }
+  info->n_u = m->n_u;
+  info->n_coupled = m->n_coupled;
+  info->log2z = m->wgt ? m->log2z : 0.5 * m->h;
   return PB_OK;
 }
 
@@ -315,7 +439,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 
 struct ModelSlots {
   size_t model_dev, desc, rec, init, state, hist, valid, samples, alpha_sorted, alpha_slot, amp,
-      clamp;
+      clamp, cpl, uph;
   uint32_t bins, groups, n_batches;
   int clamp_mw;  // mask words per p-bit of the clamp table (0: not clamped)
 };
@@ -418,6 +542,8 @@ int check_cfg(const pb_model* m, const pb_run_cfg& c) {
   // the learned sampler has its own entry points (pb_mh_*) on a PB_GIBBS run
   if (c.sampler != PB_GIBBS && c.sampler != PB_ELIM && c.sampler != PB_ELIM_CLAMP) return PB_EINVAL;
   if (c.sampler == PB_ELIM_CLAMP && (c.alphas == nullptr || c.n_alphas != 1)) return PB_EINVAL;
+  // clamping assumes uniform free outputs: no coupled general gate
+  if (c.sampler == PB_ELIM_CLAMP && m->n_coupled > 0) return PB_EINVAL;
   if (c.alphas == nullptr) {
     if (c.n_alphas != 0) return PB_EINVAL;
     if (m->n > 22) return PB_ERANGE;
@@ -473,6 +599,8 @@ int plan(pb_model* const* models, const pb_run_cfg* cfgs, int nm, Layout& L) {
     s.amp = take((size_t)s.bins * 3 * 8);
     s.clamp_mw = c.sampler == PB_ELIM_CLAMP ? std::max(1, (m->h + 31) / 32) : 0;
     s.clamp = take(npb * (size_t)(1 + s.clamp_mw) * 4 * (s.clamp_mw > 0 ? 1 : 0));
+    s.cpl = take(m->wgt ? npb * sizeof(Cpl) : 0);
+    s.uph = take(m->uph.size() * sizeof(UPh));
   }
   L.work = take((size_t)total_groups * 4);
   L.total = align_up(off, 256);
@@ -495,6 +623,7 @@ struct pb_run {
   int cons = 32, prod = 32, max_col = 1, blocks_per_sm = 0;
   size_t smem = 0;
   bool persistent = false;
+  bool wgt = false;        // some model has PB_U gates (the general-gate kernels)
   int nc = 2;              // colour steps per sweep (largest over the models)
   bool elim = false;       // exact-sampler run: i.i.d. paths instead of sweeps
   size_t elim_smem = 0;
@@ -543,6 +672,7 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
   r->smem = smem;
   r->persistent = r->nm > 1;
   if (const char* e = std::getenv("PB_PERSISTENT")) r->persistent = std::atoi(e) != 0;
+  if (r->wgt) r->persistent = false;  // general-gate sweeps: one CTA per group
   r->grid = 0;
   if (r->persistent) {
     int dev = 0, sms = 1;
@@ -615,6 +745,7 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
   for (int i = 1; i < n_models; ++i)
     if (exact(cfgs[i].sampler) != exact(cfgs[0].sampler)) return PB_EINVAL;
   r->elim = exact(cfgs[0].sampler);
+  for (auto& m : r->models) r->wgt = r->wgt || m->wgt;
   for (auto& m : r->models)
     for (int c = 0; c < 4; ++c)
       if (m->col_off[c + 1] > m->col_off[c]) r->nc = std::max(r->nc, c + 1);
@@ -648,11 +779,19 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
     for (int k = 0; k < 5; ++k) md.col_off[k] = m.col_off[k];
     md.max_col = 0;
     for (int k = 0; k < 4; ++k) md.max_col = std::max(md.max_col, m.col_off[k + 1] - m.col_off[k]);
+    md.wgt = m.wgt ? 1 : 0;
+    md.n_ug = (int32_t)m.uph.size();
+    md.log2z = m.log2z;
     const size_t npb = (size_t)m.n * m.d;
     if ((e = cudaMemcpyAsync(ws + s.model_dev, &md, sizeof md, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(ws + s.desc, m.desc.data(), npb * sizeof(Desc), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(ws + s.rec, m.rec.data(), npb * sizeof(Rec), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(ws + s.init, m.init.data(), npb * 4, cudaMemcpyHostToDevice, st)))
+      return PB_ECUDA;
+    if (m.wgt &&
+        ((e = cudaMemcpyAsync(ws + s.cpl, m.cpl.data(), npb * sizeof(Cpl), cudaMemcpyHostToDevice, st)) ||
+         (!m.uph.empty() && (e = cudaMemcpyAsync(ws + s.uph, m.uph.data(), m.uph.size() * sizeof(UPh),
+                                                 cudaMemcpyHostToDevice, st)))))
       return PB_ECUDA;
     if (c.alphas) {
       std::vector<int32_t> idx(c.n_alphas);
@@ -695,6 +834,10 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
     d.seed_hi = (uint32_t)(c.seed >> 32);
     d.group_base = base;
     d.group0 = c.group0;
+    if (m.wgt) {
+      d.cpl = reinterpret_cast<const Cpl*>(ws + s.cpl);
+      d.uph = reinterpret_cast<const UPh*>(ws + s.uph);
+    }
     if (c.sampler == PB_ELIM_CLAMP) {
       ClampTable t = build_clamp(m, c.alphas[0], s.clamp_mw);
       if ((e = cudaMemcpyAsync(ws + s.clamp, t.tab.data(), t.tab.size() * 4, cudaMemcpyHostToDevice,
@@ -768,7 +911,7 @@ PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
                                    r->grid, r->smem, r->hdr(), r->cap_st);
     else
       e = launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->cons, r->prod, r->max_col,
-                        r->nc, r->smem, r->hdr(), r->cap_st);
+                        r->nc, r->smem, r->hdr(), r->cap_st, r->wgt);
     cudaError_t e2 = cudaStreamEndCapture(r->cap_st, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -799,10 +942,58 @@ PB_API int pb_run_wait(pb_run* r) {
   return status == 0 ? PB_OK : (int)status;
 }
 
+PB_API int pb_run_phase_sums(const pb_run* r, int model, double* re, double* im, uint64_t* counts,
+                             uint64_t* valid_total, uint64_t* samples_total) {
+  if (!r || model < 0 || model >= r->nm) return PB_EINVAL;
+  const ModelSlots& s = r->L.ms[model];
+  if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
+  std::vector<uint64_t> h((size_t)s.n_batches * s.bins * 8);
+  if (cudaMemcpy(h.data(), r->ws + s.hist, h.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PB_ECUDA;
+  const bool wgt = r->models[model]->wgt;
+  for (uint32_t i = 0; i < s.bins; ++i) {
+    double sr = 0.0, si = 0.0;
+    uint64_t cn = 0;
+    for (uint32_t b = 0; b < s.n_batches; ++b) {
+      const uint64_t* c = &h[((size_t)b * s.bins + i) * 8];
+      if (wgt) {
+        double x, y;
+        std::memcpy(&x, &c[0], 8);
+        std::memcpy(&y, &c[1], 8);
+        sr += x;
+        si += y;
+        cn += c[2];
+      } else {
+        for (int k = 0; k < 8; ++k) {
+          sr += (double)c[k] * std::cos(M_PI / 4.0 * k);
+          si += (double)c[k] * std::sin(M_PI / 4.0 * k);
+          cn += c[k];
+        }
+      }
+    }
+    if (re) re[i] = sr;
+    if (im) im[i] = si;
+    if (counts) counts[i] = cn;
+  }
+  std::vector<uint64_t> v(s.n_batches);
+  if (valid_total) {
+    if (cudaMemcpy(v.data(), r->ws + s.valid, s.n_batches * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return PB_ECUDA;
+    *valid_total = std::accumulate(v.begin(), v.end(), (uint64_t)0);
+  }
+  if (samples_total) {
+    if (cudaMemcpy(v.data(), r->ws + s.samples, s.n_batches * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return PB_ECUDA;
+    *samples_total = std::accumulate(v.begin(), v.end(), (uint64_t)0);
+  }
+  return PB_OK;
+}
+
 PB_API int pb_run_histogram(const pb_run* r, int model, uint64_t* counts, uint64_t* valid_total,
                             uint64_t* samples_total) {
   if (!r || model < 0 || model >= r->nm) return PB_EINVAL;
   const ModelSlots& s = r->L.ms[model];
+  if (r->models[model]->wgt && counts) return PB_ESTATE;  // phase sums, not classes
   if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
   if (counts) {
     std::vector<uint64_t> h((size_t)s.n_batches * s.bins * 8);
@@ -1070,6 +1261,8 @@ namespace pb {
 int run_view(const pb_run* r, int model, RunView* out) {
   if (!r || !out || model < 0 || model >= r->nm) return PB_EINVAL;
   if (r->elim) return PB_EINVAL;  // moves act on Gibbs chains
+  // the learned move's acceptance knows the J energy only
+  if (r->models[model]->wgt) return PB_EINVAL;
   out->st = r->st;
   out->state = r->rm[model].state;
   out->model = r->models[model].get();

@@ -154,6 +154,43 @@ __device__ __forceinline__ uint32_t heat_bath_links(uint32_t r0, uint32_t r1, ui
   return k.neg ^ lt;
 }
 
+// Metropolis acceptance of the proposed values `prop` of a coupled p-bit
+// whose current values are `old` (general one-qubit gates, Eq. EB): a lane
+// that would flip, of category c = e_in + 2 e_out (e_in = old ^ W[win],
+// e_out = old ^ W[wout]), keeps the flip when amask bit c is set or its
+// tag-6 uniform is below A[c] -- the bit-sliced comparison of
+// compare4, planes most significant first, stopped once every lane is
+// decided.  Out of line: only coupled p-bits of general-gate models.
+__device__ __noinline__ uint32_t couple_accept(const uint32_t* W, const Cpl* cpl, uint32_t old,
+                                               uint32_t prop, uint32_t g, uint32_t sweep,
+                                               uint32_t p, uint32_t k0, uint32_t k1) {
+  const uint32_t flip = old ^ prop;
+  if (flip == 0u) return old;
+  const Cpl C = *cpl;
+  const uint32_t e1 = old ^ W[C.win], e2 = old ^ W[C.wout];
+  const uint32_t cat[4] = {~e1 & ~e2, e1 & ~e2, ~e1 & e2, e1 & e2};
+  uint32_t always = 0u;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if ((C.amask >> i) & 1u) always |= cat[i];
+  uint32_t eq = flip & ~always, lt = 0u;
+#pragma unroll 1
+  for (uint32_t grp = 0; grp < 8u && eq != 0u; ++grp) {
+    const uint4 r = philox4x32_10(make_uint4(g, sweep, p | (kTagCouple << 16), grp), k0, k1);
+    const uint32_t R[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (uint32_t w = 0; w < 4u; ++w) {
+      const uint32_t j = grp * 4u + w;
+      uint32_t T = 0u;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) T |= cat[i] & (uint32_t)((int32_t)(C.A[i] << j) >> 31);
+      lt |= eq & ~R[w] & T;
+      eq &= ~(R[w] ^ T);
+    }
+  }
+  return old ^ (flip & (always | lt));
+}
+
 __device__ __forceinline__ void add3(uint32_t& f0, uint32_t& f1, uint32_t& f2, uint32_t x0,
                                      uint32_t x1, uint32_t x2) {
   const uint32_t c0 = f0 & x0;
@@ -233,8 +270,20 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
 // per valid chain to (end state alpha, phase class).
 struct Recorder {
   uint32_t viol = 0u, f0 = 0u, f1 = 0u, f2 = 0u, lastw = 0u;
+  uint32_t phi = 0u;  // general gates: this lane's chain's phase, 2^-32 turn
 
-  __device__ void clear() { viol = f0 = f1 = f2 = 0u; }
+  __device__ void clear() { viol = f0 = f1 = f2 = phi = 0u; }
+
+  // Phases of general gates lo..hi-1 for the lane's own chain.
+  __device__ void read_u(const uint32_t* S, const UPh* uph, int lo, int hi, int lane) {
+#pragma unroll 1
+    for (int i = lo; i < hi; ++i) {
+      const UPh U = uph[i];
+      const uint32_t y = (S[U.wout] >> lane) & 1u, x = (S[U.win] >> lane) & 1u;
+      const uint32_t a0 = y ? U.ph[2] : U.ph[0], a1 = y ? U.ph[3] : U.ph[1];
+      phi += x ? a1 : a0;
+    }
+  }
 
   __device__ void read(const uint32_t* S, const Rec* srec, int lo, int hi, int lane) {
 #pragma unroll 2
@@ -259,6 +308,9 @@ struct Recorder {
     lastw = lane < n ? S[d * n + lane] : 0u;
   }
 
+  // WGT: models with general gates (rm.cpl set) add e^{i 2 pi phase} in FP64
+  // (re, im, count per bin) instead of one count per phase class.
+  template <bool WGT>
   __device__ void bin(const RunModelDev& rm, uint32_t g, uint32_t batch, int lane, uint32_t* shist,
                       unsigned long long& n_valid, unsigned long long& n_samples) {
     // lane = chain within the group; alpha bit q = bit `lane` of layer-d word q
@@ -284,8 +336,31 @@ struct Recorder {
       }
     }
     if (bin >= 0) {
-      if (shist) atomicAdd(&shist[(uint32_t)bin * 8u + phase], 1u);
-      else atomicAdd(&rm.hist[((size_t)batch * rm.bins + (uint32_t)bin) * 8u + phase], 1ull);
+      bool done = false;
+      if constexpr (WGT) {
+        if (rm.cpl != nullptr) {
+          // angle = the general gates' phases + the phase class (2^29 per pi/4)
+          const uint32_t ang = phi + (phase << 29);
+          double sn, cs;
+          sincospi((double)(int32_t)ang * 0x1p-31, &sn, &cs);
+          if (shist) {
+            double* sd = reinterpret_cast<double*>(shist);
+            atomicAdd(&sd[2u * (uint32_t)bin], cs);
+            atomicAdd(&sd[2u * (uint32_t)bin + 1u], sn);
+            atomicAdd(&shist[4u * rm.bins + (uint32_t)bin], 1u);
+          } else {
+            unsigned long long* c = rm.hist + ((size_t)batch * rm.bins + (uint32_t)bin) * 8u;
+            atomicAdd(reinterpret_cast<double*>(c), cs);
+            atomicAdd(reinterpret_cast<double*>(c + 1), sn);
+            atomicAdd(c + 2, 1ull);
+          }
+          done = true;
+        }
+      }
+      if (!done) {
+        if (shist) atomicAdd(&shist[(uint32_t)bin * 8u + phase], 1u);
+        else atomicAdd(&rm.hist[((size_t)batch * rm.bins + (uint32_t)bin) * 8u + phase], 1ull);
+      }
     }
     n_valid += __popc(__ballot_sync(0xffffffffu, valid));
     n_samples += __popc(__ballot_sync(0xffffffffu, active));
@@ -293,12 +368,14 @@ struct Recorder {
 };
 
 // p-bits lo + first, lo + first + stride, ... < hi of a colour class from
-// their descriptors (a class larger than the consumers; out of line: rare).
-__device__ __noinline__ void redraw_extra(uint32_t* W, uint32_t* S, const Desc* sdesc,
-                                          const uint4* cur, int lo, int first, int hi, int stride,
-                                          int n, FastThr fast, uint32_t thr0, uint32_t thr1,
-                                          uint32_t thr2, uint32_t thr3, uint32_t g, uint32_t sweep,
-                                          uint32_t k0, uint32_t k1) {
+// their descriptors (a class larger than the consumers; rare).  cpl: the
+// coupling table of a general-gate model, else nullptr.
+__device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc* sdesc,
+                                            const uint4* cur, int lo, int first, int hi,
+                                            int stride, int n, FastThr fast, uint32_t thr0,
+                                            uint32_t thr1, uint32_t thr2, uint32_t thr3,
+                                            uint32_t g, uint32_t sweep, uint32_t k0, uint32_t k1,
+                                            const Cpl* cpl) {
   for (int i = lo + first; i < hi; i += stride) {
     Desc D = sdesc[i];
     if (D.mflag & 0x80) continue;
@@ -312,17 +389,44 @@ __device__ __noinline__ void redraw_extra(uint32_t* W, uint32_t* S, const Desc* 
     const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
     const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
     const uint32_t pidx = (uint32_t)(D.dst - n) | (kTagSweep << 16);
-    const uint32_t v = heat_bath_links(r0, r1, r2, m, m == 0 ? ~0u : 0u, m == 1 ? ~0u : 0u,
-                                       m == 2 ? ~0u : 0u, m == 3 ? ~0u : 0u, R, fast, thr0, thr1,
-                                       thr2, thr3, g, sweep, pidx, k0, k1);
+    uint32_t v = heat_bath_links(r0, r1, r2, m, m == 0 ? ~0u : 0u, m == 1 ? ~0u : 0u,
+                                 m == 2 ? ~0u : 0u, m == 3 ? ~0u : 0u, R, fast, thr0, thr1,
+                                 thr2, thr3, g, sweep, pidx, k0, k1);
+    if (cpl && (D.mflag & 8)) {
+      const uint32_t p = (uint32_t)(D.dst - n);
+      v = couple_accept(W, cpl + p, W[D.dst], v, g, sweep, p, k0, k1);
+    }
     W[D.dst] = v;
     S[D.dst] = v;
   }
 }
 
+// Out-of-line entries (the plain one keeps the hot kernel's call site small:
+// one argument more there costs register spills).
+__device__ __noinline__ void redraw_extra(uint32_t* W, uint32_t* S, const Desc* sdesc,
+                                          const uint4* cur, int lo, int first, int hi, int stride,
+                                          int n, FastThr fast, uint32_t thr0, uint32_t thr1,
+                                          uint32_t thr2, uint32_t thr3, uint32_t g, uint32_t sweep,
+                                          uint32_t k0, uint32_t k1) {
+  redraw_body(W, S, sdesc, cur, lo, first, hi, stride, n, fast, thr0, thr1, thr2, thr3, g, sweep,
+              k0, k1, nullptr);
+}
+__device__ __noinline__ void redraw_extra_coupled(uint32_t* W, uint32_t* S, const Desc* sdesc,
+                                                  const uint4* cur, int lo, int first, int hi,
+                                                  int stride, int n, FastThr fast, uint32_t thr0,
+                                                  uint32_t thr1, uint32_t thr2, uint32_t thr3,
+                                                  uint32_t g, uint32_t sweep, uint32_t k0,
+                                                  uint32_t k1, const Cpl* cpl) {
+  redraw_body(W, S, sdesc, cur, lo, first, hi, stride, n, fast, thr0, thr1, thr2, thr3, g, sweep,
+              k0, k1, cpl);
+}
+
 // Runs `n_sweeps` sweeps (absolute indices sweep0...) of one chain group.
 // NC = colour steps per sweep (2..4; the model's classes NC.. are empty).
-template <int NC>
+// WGT: the instantiation for runs with general-gate models (coupled p-bits
+// get the Metropolis acceptance, records add FP64 phases); plain models run
+// through it unchanged.
+template <int NC, bool WGT>
 __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, uint32_t n_sweeps,
                           Shape sh, int max_col_all, uint32_t* smem, WsHeader* hdr) {
   // run and model constants held in registers for the whole launch
@@ -337,6 +441,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   const bool producer = !consumer && !recorder;
   const int ptid = tid - sh.cons;
 
+  const bool wgt_m = WGT && rm.cpl != nullptr;
+  const int nug = md.n_ug;
   const int iw = image_words(n, d);
   uint32_t* W = smem;
   // snapshots of the final state of even / odd sweeps at smem + iw (1 + parity)
@@ -384,6 +490,19 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
 #pragma unroll 1
     for (uint32_t i = tid; i < hist_words; i += T) shist[i] = 0u;
   }
+  if (wgt_m) {
+    // coupling and phase tables index the image: a bad table is reported,
+    // never followed (the whole group returns before any work)
+    int bad = 0;
+#pragma unroll 1
+    for (int i = tid; i < npb; i += T) bad |= (rm.cpl[i].win >= nw || rm.cpl[i].wout >= nw) ? 1 : 0;
+#pragma unroll 1
+    for (int i = tid; i < nug; i += T) bad |= (rm.uph[i].win >= nw || rm.uph[i].wout >= nw) ? 1 : 0;
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) set_status(hdr, PB_EINVAL);
+      return;
+    }
+  }
   __syncthreads();
 
   const uint32_t thr0 = md.thr[0], thr1 = md.thr[1], thr2 = md.thr[2], thr3 = md.thr[3];
@@ -420,6 +539,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       for (int l = 0; l < 3; ++l) { E.la[l] = 4u * D.a[l]; E.lb[l] = 4u * D.b[l]; }
       E.dst = 4u * D.dst;
       E.m = (uint32_t)m;
+      if (WGT && (D.mflag & 8)) E.m |= 0x100u;  // coupled: Metropolis acceptance
       E.M0 = m == 0 ? ~0u : 0u;
       E.M1 = m == 1 ? ~0u : 0u;
       E.M2 = m == 2 ? ~0u : 0u;
@@ -473,15 +593,27 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         const uint32_t r1 = word(E.la[1]) ^ word(E.lb[1]);
         const uint32_t r2 = word(E.la[2]) ^ word(E.lb[2]);
         const uint32_t pidx = (E.dst / 4u - (uint32_t)n) | (kTagSweep << 16);
-        const uint32_t v = heat_bath_links(r0, r1, r2, (int)E.m, E.M0, E.M1, E.M2, E.M3, R, fast,
-                                           thr0, thr1, thr2, thr3, gglob, sweep, pidx, k0, k1);
+        uint32_t v = heat_bath_links(r0, r1, r2, (int)(WGT ? (E.m & 3u) : E.m), E.M0, E.M1, E.M2,
+                                     E.M3, R, fast, thr0, thr1, thr2, thr3, gglob, sweep, pidx,
+                                     k0, k1);
+        if constexpr (WGT) {
+          if (E.m & 0x100u) {
+            const uint32_t p = E.dst / 4u - (uint32_t)n;
+            v = couple_accept(W, rm.cpl + p, word(E.dst), v, gglob, sweep, p, k0, k1);
+          }
+        }
         *reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(W) + E.dst) = v;
         *reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(S) + E.dst) = v;
       }
       // further p-bits (a class larger than the consumers) from the descriptors
-      if (K > sh.cons)
-        redraw_extra(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0, thr1, thr2,
-                     thr3, gglob, sweep, k0, k1);
+      if (K > sh.cons) {
+        if constexpr (WGT)
+          redraw_extra_coupled(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0,
+                               thr1, thr2, thr3, gglob, sweep, k0, k1, rm.cpl);
+        else
+          redraw_extra(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0, thr1, thr2,
+                       thr3, gglob, sweep, k0, k1);
+      }
     } else if (producer) {
       // the next step: class C + 1 of this sweep, or class 0 of the next one
       const uint32_t nxt = s * (uint32_t)NC + (uint32_t)C + 1u;
@@ -500,9 +632,10 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         if constexpr (C == 0) rec.clear();
         if constexpr (C + 1 < NC) {
           rec.read(Sp, srec, C * npb / (NC - 1), (C + 1) * npb / (NC - 1), lane);
+          if (wgt_m) rec.read_u(Sp, rm.uph, C * nug / (NC - 1), (C + 1) * nug / (NC - 1), lane);
         } else {
           rec.reduce(Sp, n, d, lane);
-          rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
+          rec.bin<WGT>(rm_g, g, batch, lane, shist, n_valid, n_samples);
         }
       }
     }
@@ -521,8 +654,9 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       const uint32_t* Sl = smem + iw * (1 + ((n_sweeps - 1u) & 1u));
       rec.clear();
       rec.read(Sl, srec, 0, npb, lane);
+      if (wgt_m) rec.read_u(Sl, rm.uph, 0, nug, lane);
       rec.reduce(Sl, n, d, lane);
-      rec.bin(rm_g, g, batch, lane, shist, n_valid, n_samples);
+      rec.bin<WGT>(rm_g, g, batch, lane, shist, n_valid, n_samples);
     }
   }
   __syncthreads();
@@ -531,7 +665,18 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   uint32_t* out = rm.state + (size_t)g * npb;
 #pragma unroll 1
   for (int i = tid; i < npb; i += T) out[i] = W[n + i];
-  if (shist) {
+  if (shist && wgt_m) {  // (re, im) doubles per bin, then u32 counts
+    const double* sd = reinterpret_cast<const double*>(shist);
+#pragma unroll 1
+    for (uint32_t i = tid; i < rm.bins; i += T) {
+      const uint32_t cn = shist[4u * rm.bins + i];
+      if (!cn) continue;
+      unsigned long long* c = rm.hist + ((size_t)batch * rm.bins + i) * 8u;
+      atomicAdd(reinterpret_cast<double*>(c), sd[2u * i]);
+      atomicAdd(reinterpret_cast<double*>(c + 1), sd[2u * i + 1u]);
+      atomicAdd(c + 2, (unsigned long long)cn);
+    }
+  } else if (shist) {
     unsigned long long* gh = rm.hist + (size_t)batch * rm.bins * 8u;
 #pragma unroll 1
     for (uint32_t i = tid; i < hist_words; i += T)
@@ -547,7 +692,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
 // One CTA per chain group of every model of the run (flat group index).
 constexpr int kMaxThreads = 608;  // 224 consumers + 352 producers + 1 recorder warp
 
-template <int NC>
+template <int NC, bool WGT>
 __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const RunModelDev* __restrict__ rm,
                                                      int n_models, uint32_t total_groups,
                                                      uint32_t n_sweeps, Shape sh, int max_col,
@@ -560,7 +705,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const RunModelDev* _
   const RunModelDev& r = rm[mi];
   const uint32_t g = flat - r.group_base;
   if (g >= r.groups) return;
-  run_group<NC>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
+  run_group<NC, WGT>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
 }
 
 // Persistent form: a fixed grid pops (model, group) items from a
@@ -582,7 +727,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_persistent_kernel(
     const int mi = find_model(rm, n_models, flat);
     const RunModelDev& r = rm[mi];
     const uint32_t g = flat - r.group_base;
-    if (g < r.groups) run_group<NC>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
+    if (g < r.groups) run_group<NC, false>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
   }
 }
 
@@ -677,6 +822,9 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
     const Rec R = r.rec[i];
     bad |= (R.vd >= nw || R.va >= nw || R.vb >= nw || R.pa >= nw || R.pb >= nw) ? 1 : 0;
   }
+  if (r.cpl)
+    for (int i = threadIdx.x; i < md.n_ug; i += blockDim.x)
+      bad |= (r.uph[i].win >= nw || r.uph[i].wout >= nw) ? 1 : 0;
   if (__syncthreads_or(bad)) {
     if (threadIdx.x == 0) set_status(hdr, PB_EINVAL);
     return;
@@ -727,6 +875,24 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
               msk &= msk - 1u;
             }
           }
+        } else if (e == 0xFFFFFFFFu && r.cpl && (r.cpl[p].flags & 2u)) {
+          // coupled general gate: s_in ^ [u < B], u from the tag-4 planes of
+          // this p-bit, most significant first, compared bit-sliced
+          const uint32_t B = r.cpl[p].B;
+          uint32_t lt = 0u, eq = ~0u;
+#pragma unroll 1
+          for (uint32_t grp = 0; grp < 8u && eq != 0u; ++grp) {
+            const uint4 rr = philox4x32_10(make_uint4(gglob, t, (uint32_t)p | (kTagElim << 16), grp),
+                                           r.seed_lo, r.seed_hi);
+            const uint32_t R[4] = {rr.x, rr.y, rr.z, rr.w};
+#pragma unroll
+            for (uint32_t w = 0; w < 4u; ++w) {
+              const uint32_t Tb = (uint32_t)((int32_t)(B << (grp * 4u + w)) >> 31);
+              lt |= eq & ~R[w] & Tb;
+              eq &= ~(R[w] ^ Tb);
+            }
+          }
+          v = W[p] ^ lt;  // W[(k-1) n + q]: the gate's input bit
         } else if (e == 0xFFFFFFFFu) {
           v = philox4x32_10(make_uint4(gglob, t, (uint32_t)p | (kTagElim << 16), 0u), r.seed_lo,
                             r.seed_hi).x;
@@ -741,8 +907,10 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
     }
     rec.clear();
     rec.read(W, r.rec, 0, npb, lane);
+    if (r.cpl) rec.read_u(W, r.uph, 0, md.n_ug, lane);
     rec.reduce(W, n, d, lane);
-    rec.bin(r, g, batch, lane, nullptr, n_valid, n_samples);
+    if (r.cpl) rec.bin<true>(r, g, batch, lane, nullptr, n_valid, n_samples);
+    else rec.bin<false>(r, g, batch, lane, nullptr, n_valid, n_samples);
     __syncwarp();
   }
   if (lane == 0) {
@@ -785,23 +953,53 @@ __device__ inline void phase_sum(const unsigned long long* c, double& re, double
   im = (double)(c2 - c6) + (double)(c1 + c3 - c5 - c7) * inv_sqrt2;
 }
 
+// Phase sum of one batch's bin: the 8 exact classes, or (general gates) the
+// FP64 (re, im) slots.
+__device__ inline void batch_sum(const RunModelDev& rm, bool wgt, uint32_t b, uint32_t bin,
+                                 double& re, double& im) {
+  const unsigned long long* c = rm.hist + ((size_t)b * rm.bins + bin) * 8u;
+  if (wgt) {
+    re = __longlong_as_double((long long)c[0]);
+    im = __longlong_as_double((long long)c[1]);
+  } else {
+    phase_sum(c, re, im);
+  }
+}
+
 __global__ void amplitude_kernel(const RunModelDev* __restrict__ rm_all, int model) {
   const RunModelDev& rm = rm_all[model];
   const uint32_t bin = blockIdx.x * blockDim.x + threadIdx.x;
   if (bin >= rm.bins) return;
   const int h = rm.model->h;
-  const double scale_h = exp2(0.5 * (double)h + (double)rm.amp_shift);
+  const bool wgt = rm.model->wgt != 0;
+  // 2^{h/2} (Clifford+T: every valid path has |U_C| = 2^{-h/2}); general
+  // gates: 2^{log2z}, the sum of |U_C| over all paths
+  const double scale_h = wgt ? exp2(rm.model->log2z + (double)rm.amp_shift)
+                             : exp2(0.5 * (double)h + (double)rm.amp_shift);
   unsigned long long tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double wre = 0.0, wim = 0.0;
   unsigned long long vtot = 0;
   for (uint32_t b = 0; b < rm.n_batches; ++b) {
     const unsigned long long* c = rm.hist + ((size_t)b * rm.bins + bin) * 8u;
+    if (wgt) {
+      double x, y;
+      batch_sum(rm, true, b, bin, x, y);
+      wre += x;
+      wim += y;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) tot[k] += c[k];
+      for (int k = 0; k < 8; ++k) tot[k] += c[k];
+    }
     vtot += rm.valid[b];
   }
   double re = 0.0, im = 0.0, se = 0.0;
   if (vtot > 0) {
-    phase_sum(tot, re, im);
+    if (wgt) {
+      re = wre;
+      im = wim;
+    } else {
+      phase_sum(tot, re, im);
+    }
     re *= scale_h / (double)vtot;
     im *= scale_h / (double)vtot;
     uint32_t nb = 0;
@@ -811,7 +1009,7 @@ __global__ void amplitude_kernel(const RunModelDev* __restrict__ rm_all, int mod
       if (vb == 0) continue;
       ++nb;
       double br, bi;
-      phase_sum(rm.hist + ((size_t)b * rm.bins + bin) * 8u, br, bi);
+      batch_sum(rm, wgt, b, bin, br, bi);
       br = br * scale_h / (double)vb - re;
       bi = bi * scale_h / (double)vb - im;
       const double w = (double)vb / (double)vtot;
@@ -877,20 +1075,25 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
 __global__ void advance_kernel(WsHeader* hdr, uint32_t n_sweeps) { hdr->sweep0 += n_sweeps; }
 
 // nc: colour steps per sweep (the largest over the launch's models; 2..4).
+// wgt: some model has general one-qubit gates (the WGT instantiation).
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
-                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st) {
+                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt) {
   const int threads = cons + prod + 32;
   const Shape sh{cons, prod};
-  if (nc <= 2)
-    sweep_kernel<2><<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups,
-                                                               n_sweeps, sh, max_col, hdr);
-  else if (nc == 3)
-    sweep_kernel<3><<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups,
-                                                               n_sweeps, sh, max_col, hdr);
-  else
-    sweep_kernel<4><<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups,
-                                                               n_sweeps, sh, max_col, hdr);
+  auto go = [&](auto kern) {
+    kern<<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups, n_sweeps, sh,
+                                                    max_col, hdr);
+  };
+  if (wgt) {
+    if (nc <= 2) go(sweep_kernel<2, true>);
+    else if (nc == 3) go(sweep_kernel<3, true>);
+    else go(sweep_kernel<4, true>);
+  } else {
+    if (nc <= 2) go(sweep_kernel<2, false>);
+    else if (nc == 3) go(sweep_kernel<3, false>);
+    else go(sweep_kernel<4, false>);
+  }
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
 }
@@ -957,9 +1160,12 @@ cudaError_t sweep_prepare() {
   const int big = (int)kSweepSmemMax;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(sweep_kernel<2>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<3>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<4>, a, big)) != cudaSuccess ||
+  if ((e = cudaFuncSetAttribute(sweep_kernel<2, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<2, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4, true>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_persistent_kernel<2>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_persistent_kernel<3>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_persistent_kernel<4>, a, big)) != cudaSuccess)

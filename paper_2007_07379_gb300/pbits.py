@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libpbits.so")
 
 PB_OK, PB_EINVAL, PB_ERANGE, PB_ENOMEM, PB_ECUDA, PB_ETIMEOUT, PB_ESTATE = 0, -1, -2, -3, -4, -5, -6
 PB_GIBBS, PB_LEARNED, PB_ELIM, PB_ELIM_CLAMP = 0, 1, 2, 3
+PB_U = 5
 
 _lib = None
 
@@ -36,7 +37,8 @@ class pb_model_info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("d", ctypes.c_int32), ("n_pbits", ctypes.c_int32),
                 ("h", ctypes.c_int32), ("M", ctypes.c_int32), ("rank", ctypes.c_int32),
                 ("J", ctypes.c_double), ("input_bits", ctypes.c_uint32),
-                ("thr", ctypes.c_uint32 * 4), ("colour_size", ctypes.c_int32 * 4)]
+                ("thr", ctypes.c_uint32 * 4), ("colour_size", ctypes.c_int32 * 4),
+                ("n_u", ctypes.c_int32), ("n_coupled", ctypes.c_int32), ("log2z", ctypes.c_double)]
 
 
 class pb_run_cfg(ctypes.Structure):
@@ -60,6 +62,8 @@ _SIGS = {
     "pb_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "pb_compile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(pb_gate), ctypes.c_int,
                                   ctypes.c_uint32, ctypes.c_double, ctypes.POINTER(_VP)]),
+    "pb_compile_u": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(pb_gate), ctypes.c_int,
+                                    _VP, ctypes.c_uint32, ctypes.c_double, ctypes.POINTER(_VP)]),
     "pb_model_info": (ctypes.c_int, [_VP, ctypes.POINTER(pb_model_info_t)]),
     "pb_model_colours": (ctypes.c_int, [_VP, _VP]),
     "pb_model_free": (None, [_VP]),
@@ -70,6 +74,7 @@ _SIGS = {
     "pb_run_sweeps": (ctypes.c_int, [_VP, ctypes.c_uint32]),
     "pb_run_wait": (ctypes.c_int, [_VP]),
     "pb_run_histogram": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "pb_run_phase_sums": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pb_run_amplitudes": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
     "pb_run_get_state": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_size_t]),
     "pb_run_set_state": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_size_t]),
@@ -158,15 +163,32 @@ def gate_array(gates) -> ctypes.Array:
     return arr, len(g)
 
 
-class Model:
-    """A compiled circuit (pb_compile)."""
+def mat_array(n_gates: int, mats) -> np.ndarray:
+    """Gate matrices (complex [n_gates, 2, 2], rows = output bit) as the
+    float64 [n_gates, 8] rows of pb_compile_u."""
+    m = np.zeros((max(n_gates, 1), 8), dtype=np.float64)
+    if mats is not None and n_gates:
+        c = np.asarray(mats, dtype=np.complex128).reshape(n_gates, 4)
+        m[:n_gates, 0::2] = c.real
+        m[:n_gates, 1::2] = c.imag
+    return np.ascontiguousarray(m)
 
-    def __init__(self, n: int, d: int, gates, J: float, input_bits: int = 0):
+
+class Model:
+    """A compiled circuit (pb_compile; pb_compile_u when `mats` gives the
+    matrices of PB_U gates, complex [n_gates, 2, 2])."""
+
+    def __init__(self, n: int, d: int, gates, J: float, input_bits: int = 0, mats=None):
         lib = load()
         arr, ng = gate_array(gates)
         h = ctypes.c_void_p()
-        _check(lib.pb_compile(n, d, arr, ng, ctypes.c_uint32(input_bits), ctypes.c_double(J),
-                              ctypes.byref(h)), "pb_compile")
+        if mats is None:
+            _check(lib.pb_compile(n, d, arr, ng, ctypes.c_uint32(input_bits), ctypes.c_double(J),
+                                  ctypes.byref(h)), "pb_compile")
+        else:
+            m = mat_array(ng, mats)
+            _check(lib.pb_compile_u(n, d, arr, ng, _ptr(m), ctypes.c_uint32(input_bits),
+                                    ctypes.c_double(J), ctypes.byref(h)), "pb_compile_u")
         self._h = h
         self.n, self.d = n, d
 
@@ -179,7 +201,8 @@ class Model:
         _check(load().pb_model_info(self._h, ctypes.byref(inf)), "pb_model_info")
         return {"n": inf.n, "d": inf.d, "n_pbits": inf.n_pbits, "h": inf.h, "M": inf.M,
                 "rank": inf.rank, "J": inf.J, "input_bits": inf.input_bits,
-                "thr": list(inf.thr), "colour_size": list(inf.colour_size)}
+                "thr": list(inf.thr), "colour_size": list(inf.colour_size),
+                "n_u": inf.n_u, "n_coupled": inf.n_coupled, "log2z": inf.log2z}
 
     def colours(self) -> np.ndarray:
         out = np.zeros((self.d, self.n), dtype=np.int32)
@@ -284,6 +307,18 @@ class Run:
         _check(load().pb_run_histogram(self._h, model, _ptr(cnt), ctypes.byref(v), ctypes.byref(s)),
                "pb_run_histogram")
         return cnt, v.value, s.value
+
+    def phase_sums(self, model: int = 0):
+        """(sums complex[bins] = sum of e^{i arg U_C} over valid samples per bin,
+        counts u64[bins], valid, samples) -- any model."""
+        b = self.bins(model)
+        re, im = np.zeros(b), np.zeros(b)
+        cnt = np.zeros(b, dtype=np.uint64)
+        v = ctypes.c_uint64(0)
+        s = ctypes.c_uint64(0)
+        _check(load().pb_run_phase_sums(self._h, model, _ptr(re), _ptr(im), _ptr(cnt), ctypes.byref(v),
+                                        ctypes.byref(s)), "pb_run_phase_sums")
+        return re + 1j * im, cnt, v.value, s.value
 
     def amplitudes(self, model: int = 0, l2_normalize: bool = False):
         b = self.bins(model)

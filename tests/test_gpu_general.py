@@ -1,0 +1,174 @@
+"""General one-qubit gates (PB_U; Eq. EB, Eq. HadT) on the GPU against the
+oracle's orc_u_gibbs / orc_u_elim: identical Philox draws give identical
+chain states and per-output sample counts (bit-exact), and the FP64 phase
+sums agree within the bound of the device's fixed-point angles."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_07379_gb300 import build, pbits
+from paper_2007_07379_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    pbits.load()
+
+
+def _sum_tol(counts, n_u):
+    """Per bin: each sample's angle is a sum of n_u phases rounded to 2^-32
+    turn (error <= n_u 2^-33 turn = n_u pi 2^-32 rad) plus the class angle
+    (exact), sincospi in FP64 (~1e-16) and FP64 sums in another order
+    (~1e-16 per term): |delta| <= count (n_u * 7.4e-10 + 1e-15) + 1e-12."""
+    return counts.astype(np.float64) * (n_u * 7.4e-10 + 1e-15) + 1e-12
+
+
+def _circuit(kind, n, d, seed):
+    if kind == "rot":
+        return W.rotated_h_chain(d, 0.3 + 0.01 * seed)
+    return W.random_general_circuit(n, d, seed, frac_u=0.35)
+
+
+CASES = [("gen", 3, 5, 7, 256, 40), ("gen", 5, 8, 21, 100, 33), ("rot", 1, 10, 0, 64, 50),
+         ("gen", 12, 20, 1000, 4096, 6), ("gen", 32, 64, 3, 40, 3), ("gen", 6, 1, 4, 33, 7)]
+
+
+@pytest.mark.parametrize("kind,n,d,seed,chains,sweeps", CASES)
+def test_gibbs_bit_exact_vs_oracle(kind, n, d, seed, chains, sweeps):
+    g, mats = _circuit(kind, n, d, seed)
+    J = 3.0
+    alphas = np.arange(16, dtype=np.uint32) if n > 20 else None
+    m = pbits.Model(n, d, g, J, mats=mats)
+    inf = m.info()
+    assert inf["n_u"] == int(np.sum(g[:, 0] == W.U))
+    r = pbits.Run([m], [pbits.RunCfg(seed=77, chains=chains, alphas=alphas)])
+    r.sweeps(sweeps)
+    r.wait()
+    sums, cnt, valid, samples = r.phase_sums()
+    ref = oracle.u_gibbs(n, d, g, mats, J=J, seed=77, chains=chains, sweeps=sweeps, alphas=alphas)
+    assert np.array_equal(pbits.unslice_state(r.get_state(), chains), ref["state"])
+    assert samples == ref["samples"] and valid == ref["valid"]
+    assert np.array_equal(cnt, ref["cnt"])
+    assert np.all(np.abs(sums - ref["sum"]) <= _sum_tol(cnt, inf["n_u"]))
+    assert np.isclose(inf["log2z"], ref["log2z"], rtol=0, atol=1e-12)
+    psi, _ = r.amplitudes()
+    want = oracle.u_estimate(ref)
+    scale = 2.0 ** ref["log2z"] / max(valid, 1)
+    assert np.all(np.abs(psi - want) <= scale * _sum_tol(cnt, inf["n_u"]) + 1e-12)
+
+
+def test_plain_and_general_models_share_a_run():
+    """The general-gate kernel runs plain models unchanged (8 exact phase
+    classes), and both match their oracles bit-exactly."""
+    n, d = 5, 8
+    gp = W.random_circuit(n, d, 21)
+    gu, mats = W.random_general_circuit(n, d, 22, frac_u=0.5)
+    mp = pbits.Model(n, d, gp, W.default_J(n, d, gp))
+    mu = pbits.Model(n, d, gu, 2.5, mats=mats)
+    r = pbits.Run([mp, mu], [pbits.RunCfg(seed=5, chains=96), pbits.RunCfg(seed=6, chains=70)])
+    r.sweeps(17)
+    cp, vp, sp = r.histogram(0)
+    refp = oracle.gibbs(n, d, gp, J=W.default_J(n, d, gp), seed=5, chains=96, sweeps=17)
+    assert np.array_equal(cp, refp["cnt"]) and vp == refp["valid"] and sp == refp["samples"]
+    assert np.array_equal(pbits.unslice_state(r.get_state(0), 96), refp["state"])
+    sums, cnt, vu, su = r.phase_sums(1)
+    refu = oracle.u_gibbs(n, d, gu, mats, J=2.5, seed=6, chains=70, sweeps=17)
+    assert np.array_equal(cnt, refu["cnt"]) and vu == refu["valid"] and su == refu["samples"]
+    assert np.array_equal(pbits.unslice_state(r.get_state(1), 70), refu["state"])
+    assert np.all(np.abs(sums - refu["sum"]) <= _sum_tol(cnt, int(np.sum(gu[:, 0] == W.U))))
+    with pytest.raises(pbits.PbError):
+        r.histogram(1)
+
+
+def test_shape_invariance_with_large_classes():
+    """32 consumers: most colour classes exceed them, so the coupled p-bits
+    beyond the first 32 take the out-of-line path; results are unchanged."""
+    n, d = 12, 20
+    g, mats = W.random_general_circuit(n, d, 1000, frac_u=0.35)
+    m = pbits.Model(n, d, g, 3.0, mats=mats)
+    r = pbits.Run([m], [pbits.RunCfg(seed=9, chains=256)])
+    r.set_shape(32, 96)
+    r.sweeps(9)
+    sums, cnt, valid, samples = r.phase_sums()
+    ref = oracle.u_gibbs(n, d, g, mats, J=3.0, seed=9, chains=256, sweeps=9)
+    assert np.array_equal(pbits.unslice_state(r.get_state(), 256), ref["state"])
+    assert np.array_equal(cnt, ref["cnt"]) and valid == ref["valid"]
+
+
+def test_global_histogram_path():
+    """n = 14: 2^14 bins do not fit the shared-memory histogram; the record
+    adds to global memory directly."""
+    n, d = 14, 6
+    g, mats = W.random_general_circuit(n, d, 5, frac_u=0.4)
+    m = pbits.Model(n, d, g, 3.0, mats=mats)
+    r = pbits.Run([m], [pbits.RunCfg(seed=3, chains=64, burn_in=2, record_every=2)])
+    r.sweeps(11)
+    sums, cnt, valid, samples = r.phase_sums()
+    ref = oracle.u_gibbs(n, d, g, mats, J=3.0, seed=3, chains=64, sweeps=11, burn_in=2, record_every=2)
+    assert np.array_equal(cnt, ref["cnt"]) and valid == ref["valid"] and samples == ref["samples"]
+    assert np.all(np.abs(sums - ref["sum"]) <= _sum_tol(cnt, int(np.sum(g[:, 0] == W.U))))
+
+
+@pytest.mark.parametrize("kind,n,d,seed,chains,sweeps", [("gen", 3, 5, 7, 300, 20), ("rot", 1, 10, 1, 64, 30),
+                                                         ("gen", 12, 20, 1000, 4096, 4)])
+def test_elim_bit_exact_vs_oracle(kind, n, d, seed, chains, sweeps):
+    g, mats = _circuit(kind, n, d, seed)
+    m = pbits.Model(n, d, g, 3.0, mats=mats)
+    r = pbits.Run([m], [pbits.RunCfg(seed=41, chains=chains, sampler=pbits.PB_ELIM)])
+    r.sweeps(sweeps)
+    sums, cnt, valid, samples = r.phase_sums()
+    ref = oracle.u_elim(n, d, g, mats, seed=41, chains=chains, sweeps=sweeps)
+    assert samples == valid == ref["samples"] == chains * sweeps
+    assert np.array_equal(cnt, ref["cnt"])
+    assert np.array_equal(pbits.unslice_state(r.get_state(), chains), ref["state"])
+    assert np.all(np.abs(sums - ref["sum"]) <= _sum_tol(cnt, int(np.sum(g[:, 0] == W.U))))
+
+
+def test_rotated_chain_converges():
+    """d = 10 rotated Hadamards (t = 0.3): the Gibbs estimate of both
+    amplitudes lies within 5 batch-means SE of (1, 0), and the exact
+    sampler's SE matches its closed form sqrt((Z Z_alpha - |U|^2) / T)."""
+    d, th = 10, 0.3
+    g, mats = W.rotated_h_chain(d, th)
+    m = pbits.Model(1, d, g, 3.0, mats=mats)
+    r = pbits.Run([m], [pbits.RunCfg(seed=1, chains=4096, burn_in=100, n_batches=32)])
+    r.sweeps(3000)
+    psi, se = r.amplitudes()
+    exact = oracle.u_statevector(1, d, g, mats)
+    assert np.all(np.abs(psi - exact) <= 5 * se + 1e-9), (psi, se)
+    assert np.all(se < 0.05)
+    e = pbits.Run([m], [pbits.RunCfg(seed=2, chains=4096, n_batches=32, sampler=pbits.PB_ELIM)])
+    e.sweeps(500)
+    psi_e, se_e = e.amplitudes()
+    ps = oracle.u_pathstats(1, d, g, mats)
+    Z = 2 ** m.info()["log2z"]
+    _, _, _, T = e.phase_sums()
+    se_closed = np.sqrt(np.maximum(Z * ps["zabs"] - np.abs(exact) ** 2, 0) / T)
+    assert np.all(np.abs(psi_e - exact) <= 5 * se_closed + 1e-12)
+    assert np.all(np.abs(se_e / se_closed - 1) < 0.5)
+
+
+def test_rejections():
+    n, d = 4, 6
+    g, mats = W.random_general_circuit(n, d, 2, frac_u=0.9)
+    assert np.sum(g[:, 0] == W.U) > 0
+    m = pbits.Model(n, d, g, 3.0, mats=mats)
+    assert m.info()["n_coupled"] > 0
+    with pytest.raises(pbits.PbError):  # clamping assumes uniform free outputs
+        pbits.Run([m], [pbits.RunCfg(seed=1, chains=32, alphas=np.array([0], np.uint32),
+                                     sampler=pbits.PB_ELIM_CLAMP)])
+    r = pbits.Run([m], [pbits.RunCfg(seed=1, chains=64)])
+    net = pbits.Mlp(n, d, hidden=64, batch=128, seed=1)
+    with pytest.raises(Exception):
+        pbits.Learned(r, net)
+    bad = mats.copy()
+    i = int(np.flatnonzero(g[:, 0] == W.U)[0])
+    bad[i] = np.array([[1, 0], [0, 2]])
+    with pytest.raises(pbits.PbError):
+        pbits.Model(n, d, g, 3.0, mats=bad)
