@@ -323,6 +323,7 @@ def main():
         extra["batched"] = batched_measurement(dev, stream)
         extra["elim"] = elim_measurement(dev, stream)
         extra["large"] = large_measurement(dev, stream)
+        extra["general"] = general_measurement(dev, stream)
 
     learned = None
     if rank == 0 and not args.no_learned:
@@ -485,6 +486,46 @@ def elim_measurement(dev, stream, samples: int = 10_000):
                              "se_unclamped_same_samples": float(se_u[0]) * np.sqrt(2.0),
                              "t_to_1e-2_s": t_c * (float(se_c[0]) / 1e-2) ** 2,
                              "t_to_1e-3_s": t_c * (float(se_c[0]) / 1e-3) ** 2}}
+
+
+def general_measurement(dev, stream, sweeps: int = 2000, samples: int = 2000):
+    """General one-qubit gates (Eq. EB): the mid circuit with 30 % of its
+    one-qubit gates random unitaries.  Gibbs sweeps (heat-bath proposal,
+    Metropolis acceptance of coupled p-bits, FP64 phase sums) and the exact
+    sampler, against the same shape of plain Clifford+T circuit."""
+    import torch
+    from paper_2007_07379_gb300 import pbits
+    wl = W.general_mid()
+    pl = W.mid()
+
+    def best_ms(run, k):
+        run.sweeps(k)
+        run.wait()
+        out = None
+        for _ in range(3):
+            run.sweeps(k)
+            run.wait()
+            ms = run.stats()["last_ms"]
+            out = ms if out is None else min(out, ms)
+        return out
+
+    with torch.cuda.stream(stream):
+        m = pbits.Model(wl.n, wl.d, wl.gates, wl.J, mats=wl.extra["mats"])
+        inf = m.info()
+        g_ms = best_ms(pbits.Run([m], [pbits.RunCfg(seed=wl.seed, chains=wl.chains)], stream=stream),
+                       sweeps)
+        e_ms = best_ms(pbits.Run([m], [pbits.RunCfg(seed=wl.seed, chains=wl.chains,
+                                                    sampler=pbits.PB_ELIM)], stream=stream), samples)
+        mp = pbits.Model(pl.n, pl.d, pl.gates, pl.J)
+        p_ms = best_ms(pbits.Run([mp], [pbits.RunCfg(seed=pl.seed, chains=pl.chains)], stream=stream),
+                       sweeps)
+    flips = wl.chains * wl.n * wl.d * sweeps
+    return {"workload": "general_mid: mid (n=12, d=20) with 30% of one-qubit gates random unitaries, "
+                        "4096 chains",
+            "u_gates": inf["n_u"], "coupled": inf["n_coupled"], "sweeps": sweeps,
+            "launch_ms": g_ms, "flips_per_s": flips / (g_ms * 1e-3),
+            "plain_mid_flips_per_s": flips / (p_ms * 1e-3),
+            "elim_paths_per_s": wl.chains * samples / (e_ms * 1e-3)}
 
 
 def batched_measurement(dev, stream, sweeps: int = 10_000):

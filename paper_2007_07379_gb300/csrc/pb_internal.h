@@ -127,6 +127,9 @@ struct WsHeader {
 // Dynamic shared memory the sweep and exact-sampler kernels may use per CTA
 // (227 KB per block on sm_103a, less their static shared memory).
 constexpr size_t kSweepSmemMax = 226 * 1024;
+// Threads per sweep CTA in a run with general one-qubit gates (the general
+// instantiation is compiled for at most this many).
+constexpr int kSweepThreadsWgt = 512;
 
 constexpr uint32_t kTagSweep = 0;
 constexpr uint32_t kTagInit = 1;

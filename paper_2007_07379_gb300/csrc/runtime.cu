@@ -34,7 +34,8 @@ cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins,
                               cudaStream_t st);
 cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t count,
                                uint32_t* out, cudaStream_t st);
-size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins);
+size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins,
+                        bool wgt = false);
 cudaError_t sweep_prepare();
 int sweep_max_blocks_per_sm(int threads, size_t smem);
 }  // namespace pb
@@ -664,10 +665,10 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
   for (int i = 0; i < r->nm; ++i) {
     const pb_model& m = *r->models[i];
     const uint32_t bins = r->L.ms[i].bins;
-    const size_t base = sweep_smem_bytes(m.n, m.d, cons, maxcol, 0);
+    const size_t base = sweep_smem_bytes(m.n, m.d, cons, maxcol, 0, r->wgt);
     const bool use = (size_t)bins * 32 <= cap && base + (size_t)bins * 32 <= kSweepSmemMax;
     r->rm[i].hist_smem = use ? 1u : 0u;
-    smem = std::max(smem, sweep_smem_bytes(m.n, m.d, cons, maxcol, use ? bins : 0));
+    smem = std::max(smem, sweep_smem_bytes(m.n, m.d, cons, maxcol, use ? bins : 0, r->wgt));
   }
   r->smem = smem;
   r->persistent = r->nm > 1;
@@ -705,7 +706,14 @@ void choose_shape(pb_run* r) {
     int v = std::atoi(e);
     if (v >= 32 && v <= 352 && v % 32 == 0) prod = v;
   }
+  if (r->wgt) prod = std::max(32, std::min(prod, kSweepThreadsWgt - 32 - cons));
   apply_shape(r, cons, prod, 0);
+  // a shape whose tables do not fit: fewer consumers (their class table and
+  // acceptance planes shrink; the class runs in more passes)
+  while (r->smem > kSweepSmemMax && cons > 32) {
+    cons -= 32;
+    apply_shape(r, cons, prod, 0);
+  }
 }
 
 }  // namespace
@@ -1059,6 +1067,7 @@ PB_API int pb_run_set_shape(pb_run* r, int consumers, int producers, int blocks_
   if (consumers < 32 || consumers > 224 || consumers % 32) return PB_EINVAL;
   if (producers < 32 || producers > 352 || producers % 32) return PB_EINVAL;
   if (blocks_per_sm < 0) return PB_EINVAL;
+  if (r->wgt && consumers + producers + 32 > kSweepThreadsWgt) return PB_ERANGE;
   if (cudaStreamSynchronize(r->st) != cudaSuccess) return PB_ECUDA;
   const int c0 = r->cons, p0 = r->prod, b0 = r->blocks_per_sm;
   apply_shape(r, consumers, producers, blocks_per_sm);

@@ -65,6 +65,10 @@ __device__ __forceinline__ void compare_tail(uint32_t& lt, uint32_t& eq, const H
 
 // Number of Philox calls computed ahead of a colour class (12 planes).
 constexpr int kPre = 3;
+// General-gate runs: Philox calls of the Metropolis acceptance draw (tag 6)
+// computed ahead (12 planes) for the coupled p-bits among the first
+// `consumers` of a class (the rest draw their own, out of line).
+constexpr int kPreC = 3;
 
 // Threshold pair of a p-bit with m links: tA for the lanes in `sel` (all
 // links agree), tB for the others (see the consumer table set-up).
@@ -161,9 +165,12 @@ __device__ __forceinline__ uint32_t heat_bath_links(uint32_t r0, uint32_t r1, ui
 // tag-6 uniform is below A[c] -- the bit-sliced comparison of
 // compare4, planes most significant first, stopped once every lane is
 // decided.  Out of line: only coupled p-bits of general-gate models.
+// pre: the kPreC tag-6 Philox outputs computed ahead by the producers, or
+// nullptr (all drawn here).
 __device__ __noinline__ uint32_t couple_accept(const uint32_t* W, const Cpl* cpl, uint32_t old,
-                                               uint32_t prop, uint32_t g, uint32_t sweep,
-                                               uint32_t p, uint32_t k0, uint32_t k1) {
+                                               uint32_t prop, const uint4* pre, uint32_t g,
+                                               uint32_t sweep, uint32_t p, uint32_t k0,
+                                               uint32_t k1) {
   const uint32_t flip = old ^ prop;
   if (flip == 0u) return old;
   const Cpl C = *cpl;
@@ -176,7 +183,9 @@ __device__ __noinline__ uint32_t couple_accept(const uint32_t* W, const Cpl* cpl
   uint32_t eq = flip & ~always, lt = 0u;
 #pragma unroll 1
   for (uint32_t grp = 0; grp < 8u && eq != 0u; ++grp) {
-    const uint4 r = philox4x32_10(make_uint4(g, sweep, p | (kTagCouple << 16), grp), k0, k1);
+    const uint4 r = (pre != nullptr && grp < (uint32_t)kPreC)
+                        ? pre[grp]
+                        : philox4x32_10(make_uint4(g, sweep, p | (kTagCouple << 16), grp), k0, k1);
     const uint32_t R[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (uint32_t w = 0; w < 4u; ++w) {
@@ -241,10 +250,11 @@ static_assert(sizeof(ClassEnt) == 48, "ClassEnt must be 48 bytes");
 __host__ __device__ inline int image_words(int n, int d) { return (n_words(n, d) + 1 + 3) & ~3; }
 
 __host__ __device__ inline size_t group_smem_bytes(int n, int d, int cons, int max_col,
-                                                   uint32_t hist_bins) {
+                                                   uint32_t hist_bins, bool wgt = false) {
   return (size_t)3 * image_words(n, d) * 4 + (size_t)n * d * sizeof(Desc) +
          (size_t)n * d * sizeof(Rec) + (size_t)hist_bins * 8 * 4 +
-         (size_t)4 * cons * sizeof(ClassEnt) + (size_t)2 * kPre * max_col * sizeof(uint4);
+         (size_t)4 * cons * sizeof(ClassEnt) +
+         (size_t)2 * ((size_t)kPre * max_col + (wgt ? (size_t)kPreC * cons : 0)) * sizeof(uint4);
 }
 
 // 32 x 32 bit transpose across a warp: on entry lane r holds row r; on
@@ -276,7 +286,7 @@ struct Recorder {
 
   // Phases of general gates lo..hi-1 for the lane's own chain.
   __device__ void read_u(const uint32_t* S, const UPh* uph, int lo, int hi, int lane) {
-#pragma unroll 1
+#pragma unroll 4
     for (int i = lo; i < hi; ++i) {
       const UPh U = uph[i];
       const uint32_t y = (S[U.wout] >> lane) & 1u, x = (S[U.win] >> lane) & 1u;
@@ -371,8 +381,8 @@ struct Recorder {
 // their descriptors (a class larger than the consumers; rare).  cpl: the
 // coupling table of a general-gate model, else nullptr.
 __device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc* sdesc,
-                                            const uint4* cur, int lo, int first, int hi,
-                                            int stride, int n, FastThr fast, uint32_t thr0,
+                                            const uint4* cur, int lo, int first,
+                                            int hi, int stride, int n, FastThr fast, uint32_t thr0,
                                             uint32_t thr1, uint32_t thr2, uint32_t thr3,
                                             uint32_t g, uint32_t sweep, uint32_t k0, uint32_t k1,
                                             const Cpl* cpl) {
@@ -394,7 +404,7 @@ __device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc
                                  thr2, thr3, g, sweep, pidx, k0, k1);
     if (cpl && (D.mflag & 8)) {
       const uint32_t p = (uint32_t)(D.dst - n);
-      v = couple_accept(W, cpl + p, W[D.dst], v, g, sweep, p, k0, k1);
+      v = couple_accept(W, cpl + p, W[D.dst], v, nullptr, g, sweep, p, k0, k1);
     }
     W[D.dst] = v;
     S[D.dst] = v;
@@ -431,7 +441,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
                           Shape sh, int max_col_all, uint32_t* smem, WsHeader* hdr) {
   // run and model constants held in registers for the whole launch
   const RunModelDev rm = rm_g;
-  const ModelDev md = *rm.model;
+  const ModelDev& md = *rm.model;  // a reference: a struct copy here costs 1.5 % of sweep time
   const int n = md.n, d = md.d, nw = md.nw;
   const int npb = n * d;
   const int tid = threadIdx.x, T = blockDim.x;
@@ -452,8 +462,11 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   uint32_t* shist = rm.hist_smem ? after_rec : nullptr;
   const uint32_t hist_words = rm.bins * 8u;
   ClassEnt* sclass = reinterpret_cast<ClassEnt*>(after_rec + (rm.hist_smem ? hist_words : 0u));
-  uint4* planes = reinterpret_cast<uint4*>(sclass + 4 * sh.cons);  // [2][max_col][kPre]
-  const int pbuf = max_col_all * kPre;
+  // two buffers, each [max_col][kPre] sweep-draw outputs, then (general-gate
+  // runs) [cons][kPreC] acceptance outputs of the class's first cons p-bits
+  uint4* planes = reinterpret_cast<uint4*>(sclass + 4 * sh.cons);
+  const int acc_off = max_col_all * kPre;
+  const int pbuf = acc_off + (WGT ? sh.cons * kPreC : 0);
 
   // ---- load the group image and the tables
   const uint32_t* gstate = rm.state + (size_t)g * npb;
@@ -551,11 +564,21 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   auto produce = [&](auto cc, uint32_t sw, uint4* buf) {
     constexpr int C = decltype(cc)::value;
     const int lo = col_lo[C], K = col_hi[C] - lo;
+    const int nsw = K * kPre;
+    const int nacc = WGT ? (K < sh.cons ? K : sh.cons) * kPreC : 0;
 #pragma unroll 1
-    for (int u = ptid; u < K * kPre; u += sh.prod) {
-      const int i = u / kPre, j = u - i * kPre;
-      const uint32_t p = (uint32_t)(sdesc[lo + i].dst - n) | (kTagSweep << 16);
-      buf[u] = philox4x32_10(make_uint4(gglob, sw, p, (uint32_t)j), k0, k1);
+    for (int u = ptid; u < nsw + nacc; u += sh.prod) {
+      if (!WGT || u < nsw) {
+        const int i = u / kPre, j = u - i * kPre;
+        const uint32_t p = (uint32_t)(sdesc[lo + i].dst - n) | (kTagSweep << 16);
+        buf[u] = philox4x32_10(make_uint4(gglob, sw, p, (uint32_t)j), k0, k1);
+      } else {  // acceptance draws: coupled p-bits only
+        const int a = u - nsw, i = a / kPreC, j = a - i * kPreC;
+        const Desc& D = sdesc[lo + i];
+        if (D.mflag & 8)
+          buf[acc_off + a] = philox4x32_10(
+              make_uint4(gglob, sw, (uint32_t)(D.dst - n) | (kTagCouple << 16), (uint32_t)j), k0, k1);
+      }
     }
   };
   if (producer && n_sweeps > 0u) produce(std::integral_constant<int, 0>{}, sweep0, planes);
@@ -599,7 +622,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         if constexpr (WGT) {
           if (E.m & 0x100u) {
             const uint32_t p = E.dst / 4u - (uint32_t)n;
-            v = couple_accept(W, rm.cpl + p, word(E.dst), v, gglob, sweep, p, k0, k1);
+            v = couple_accept(W, rm.cpl + p, word(E.dst), v, cur + acc_off + tid * kPreC, gglob,
+                              sweep, p, k0, k1);
           }
         }
         *reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(W) + E.dst) = v;
@@ -691,9 +715,12 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
 
 // One CTA per chain group of every model of the run (flat group index).
 constexpr int kMaxThreads = 608;  // 224 consumers + 352 producers + 1 recorder warp
+// General-gate runs: at most 512 threads, so that the longer consumer and
+// recorder paths get 128 registers.
+constexpr int kMaxThreadsWgt = 512;
 
 template <int NC, bool WGT>
-__global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const RunModelDev* __restrict__ rm,
+__global__ void __launch_bounds__(WGT ? kMaxThreadsWgt : kMaxThreads) sweep_kernel(const RunModelDev* __restrict__ rm,
                                                      int n_models, uint32_t total_groups,
                                                      uint32_t n_sweeps, Shape sh, int max_col,
                                                      WsHeader* hdr) {
@@ -1150,8 +1177,8 @@ cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, ui
   return cudaGetLastError();
 }
 
-size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins) {
-  return group_smem_bytes(n, d, cons, max_col, hist_bins);
+size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins, bool wgt) {
+  return group_smem_bytes(n, d, cons, max_col, hist_bins, wgt);
 }
 
 // Opt the sweep kernels into large dynamic shared memory (called once per

@@ -154,8 +154,9 @@ def chains_for(n: int) -> int:
 
 def default_J(n: int, d: int, gates) -> float:
     """J = ln(M / ln 2), M = number of linked (non-H) p-bits: the stationary
-    fraction of valid paths, (1 + e^{-J})^{-M}, is then close to 1/2."""
-    h = int(np.sum(np.asarray(gates)[:, 0] == H))
+    fraction of valid paths, (1 + e^{-J})^{-M}, is then close to 1/2.  U
+    gates count as free outputs here (most are coupled)."""
+    h = int(np.sum(np.isin(np.asarray(gates)[:, 0], (H, U))))
     M = max(n * d - h, 1)
     return float(np.log(max(M / np.log(2.0), 1.0 + 1e-9)))
 
@@ -189,6 +190,16 @@ def mid() -> Workload:
     g = random_circuit(12, 20, seed=1000)
     return Workload("mid", 12, 20, g, chains=4096, sweeps=100_000, seed=0x5EED + 1,
                     J=default_J(12, 20, g))
+
+
+def general_mid() -> Workload:
+    """The mid circuit (n=12, d=20, seed 1000) with 30 % of its one-qubit
+    gates replaced by random three-angle unitaries (Eq. EB gates with real
+    couplings and phases off the pi/4 grid); 4096 chains.  extra["mats"]
+    holds the gate matrices."""
+    g, mats = random_general_circuit(12, 20, seed=1000, frac_u=0.3)
+    return Workload("general_mid", 12, 20, g, chains=4096, sweeps=10_000, seed=0x5EED + 5,
+                    J=default_J(12, 20, g), extra={"mats": mats})
 
 
 def batched(count: int = 256) -> list[Workload]:
