@@ -224,8 +224,9 @@ PB_API int pb_run_histogram(const pb_run* run, int model, uint64_t* counts,
 
 /* Phase sums of model `model` (synchronous), any model: per bin, summed over
  * batches, re + i im = sum over the valid recorded samples ending there of
- * e^{i arg U_C} (FP64 sums of the device's per-sample phases: fixed-point
- * angles of 2^-32 turn per PB_U gate, sincospi in FP64), counts = their
+ * e^{i arg U_C} (FP64 sums of the device's per-sample phasors: fixed-point
+ * angles of 2^-32 turn per PB_U gate, the phasor by sincospif in FP32, each
+ * term within 3e-7 of the exact one), counts = their
  * number.  For a model without PB_U gates the sums are formed from the
  * exact phase classes.  Any pointer may be NULL. */
 PB_API int pb_run_phase_sums(const pb_run* run, int model, double* re, double* im,

@@ -166,15 +166,19 @@ __device__ __forceinline__ uint32_t heat_bath_links(uint32_t r0, uint32_t r1, ui
 // compare4, planes most significant first, stopped once every lane is
 // decided.  Out of line: only coupled p-bits of general-gate models.
 // pre: the kPreC tag-6 Philox outputs computed ahead by the producers, or
-// nullptr (all drawn here).
-__device__ __noinline__ uint32_t couple_accept(const uint32_t* W, const Cpl* cpl, uint32_t old,
-                                               uint32_t prop, const uint4* pre, uint32_t g,
-                                               uint32_t sweep, uint32_t p, uint32_t k0,
-                                               uint32_t k1) {
+// nullptr (all drawn here).  Inlined into the consumer's main pass (a call
+// there costs more than the body: live registers around it), out of line
+// for the rare extra p-bits.
+// C: the p-bit's coupling entry; win_w / wout_w: W[C.win], W[C.wout] (the
+// caller loads them ahead of the heat-bath draw).
+__device__ __forceinline__ uint32_t couple_accept_body(const Cpl& C, uint32_t win_w,
+                                                       uint32_t wout_w, uint32_t old, uint32_t prop,
+                                                       const uint4* pre, uint32_t g,
+                                                       uint32_t sweep, uint32_t p, uint32_t k0,
+                                                       uint32_t k1) {
   const uint32_t flip = old ^ prop;
   if (flip == 0u) return old;
-  const Cpl C = *cpl;
-  const uint32_t e1 = old ^ W[C.win], e2 = old ^ W[C.wout];
+  const uint32_t e1 = old ^ win_w, e2 = old ^ wout_w;
   const uint32_t cat[4] = {~e1 & ~e2, e1 & ~e2, ~e1 & e2, e1 & e2};
   uint32_t always = 0u;
 #pragma unroll
@@ -185,7 +189,7 @@ __device__ __noinline__ uint32_t couple_accept(const uint32_t* W, const Cpl* cpl
   for (uint32_t grp = 0; grp < 8u && eq != 0u; ++grp) {
     const uint4 r = (pre != nullptr && grp < (uint32_t)kPreC)
                         ? pre[grp]
-                        : philox4x32_10(make_uint4(g, sweep, p | (kTagCouple << 16), grp), k0, k1);
+                        : philox_cold(make_uint4(g, sweep, p | (kTagCouple << 16), grp), k0, k1);
     const uint32_t R[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (uint32_t w = 0; w < 4u; ++w) {
@@ -198,6 +202,13 @@ __device__ __noinline__ uint32_t couple_accept(const uint32_t* W, const Cpl* cpl
     }
   }
   return old ^ (flip & (always | lt));
+}
+__device__ __noinline__ uint32_t couple_accept(const uint32_t* W, const Cpl* cpl, uint32_t old,
+                                               uint32_t prop, const uint4* pre, uint32_t g,
+                                               uint32_t sweep, uint32_t p, uint32_t k0,
+                                               uint32_t k1) {
+  const Cpl C = *cpl;
+  return couple_accept_body(C, W[C.win], W[C.wout], old, prop, pre, g, sweep, p, k0, k1);
 }
 
 __device__ __forceinline__ void add3(uint32_t& f0, uint32_t& f1, uint32_t& f2, uint32_t x0,
@@ -284,10 +295,33 @@ struct Recorder {
 
   __device__ void clear() { viol = f0 = f1 = f2 = phi = 0u; }
 
-  // Phases of general gates lo..hi-1 for the lane's own chain.
+  // Phases of general gates lo..hi-1 for the lane's own chain, eight gates
+  // per batch with every load of a batch issued before the first use.
   __device__ void read_u(const uint32_t* S, const UPh* uph, int lo, int hi, int lane) {
-#pragma unroll 4
-    for (int i = lo; i < hi; ++i) {
+    int i = lo;
+#pragma unroll 1
+    for (; i + 8 <= hi; i += 8) {
+      uint4 ph[8];
+      uint32_t ww[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        ph[j] = *reinterpret_cast<const uint4*>(uph[i + j].ph);
+        ww[j] = *reinterpret_cast<const uint32_t*>(&uph[i + j].wout);  // wout | win << 16
+      }
+      uint32_t y[8], x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        y[j] = (S[ww[j] & 0xFFFFu] >> lane) & 1u;
+        x[j] = (S[ww[j] >> 16] >> lane) & 1u;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t a0 = y[j] ? ph[j].z : ph[j].x, a1 = y[j] ? ph[j].w : ph[j].y;
+        phi += x[j] ? a1 : a0;
+      }
+    }
+#pragma unroll 1
+    for (; i < hi; ++i) {
       const UPh U = uph[i];
       const uint32_t y = (S[U.wout] >> lane) & 1u, x = (S[U.win] >> lane) & 1u;
       const uint32_t a0 = y ? U.ph[2] : U.ph[0], a1 = y ? U.ph[3] : U.ph[1];
@@ -318,6 +352,57 @@ struct Recorder {
     lastw = lane < n ? S[d * n + lane] : 0u;
   }
 
+  // The phasor of this lane's record: the general gates' phases plus the
+  // phase class (2^29 per pi/4), in FP32 (FP64 issues far slower on this
+  // part): the angle rounds to 24 bits (<= pi 2^-24 rad) and sincospif adds
+  // about one ulp, so each term is within 3e-7 of e^{i angle}.
+  __device__ void phasor(uint32_t phase, double& cs, double& sn) const {
+    const uint32_t ang = phi + (phase << 29);
+    float snf, csf;
+    sincospif((float)(int32_t)ang * 0x1p-31f, &snf, &csf);
+    cs = (double)csf;
+    sn = (double)snf;
+  }
+
+  // Few bins (<= 8): all lanes would hit a handful of FP64 counters, so the
+  // warp sums each distinct bin's terms with shuffles and one lane adds them
+  // (whole warp, convergent).
+  __device__ void bin_few(const RunModelDev& rm, uint32_t batch, int lane, uint32_t* shist,
+                          int bin) {
+    const uint32_t phase = ((f0 >> lane) & 1u) | (((f1 >> lane) & 1u) << 1) |
+                           (((f2 >> lane) & 1u) << 2);
+    double cs, sn;
+    phasor(phase, cs, sn);
+    const bool has = bin >= 0;
+    unsigned pending = __ballot_sync(0xffffffffu, has);
+    while (pending) {
+      const int leader = __ffs((int)pending) - 1;
+      const int b = __shfl_sync(0xffffffffu, bin, leader);
+      const bool mine = has && bin == b;
+      const unsigned m = __ballot_sync(0xffffffffu, mine);
+      double r = mine ? cs : 0.0, q = mine ? sn : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        r += __shfl_xor_sync(0xffffffffu, r, off);
+        q += __shfl_xor_sync(0xffffffffu, q, off);
+      }
+      if (lane == leader) {
+        if (shist) {
+          double* sd = reinterpret_cast<double*>(shist);
+          atomicAdd(&sd[2u * (uint32_t)b], r);
+          atomicAdd(&sd[2u * (uint32_t)b + 1u], q);
+          atomicAdd(&shist[4u * rm.bins + (uint32_t)b], (uint32_t)__popc(m));
+        } else {
+          unsigned long long* c = rm.hist + ((size_t)batch * rm.bins + (uint32_t)b) * 8u;
+          atomicAdd(reinterpret_cast<double*>(c), r);
+          atomicAdd(reinterpret_cast<double*>(c + 1), q);
+          atomicAdd(c + 2, (unsigned long long)__popc(m));
+        }
+      }
+      pending &= ~m;
+    }
+  }
+
   // WGT: models with general gates (rm.cpl set) add e^{i 2 pi phase} in FP64
   // (re, im, count per bin) instead of one count per phase class.
   template <bool WGT>
@@ -345,14 +430,18 @@ struct Recorder {
         }
       }
     }
+    if constexpr (WGT) {
+      if (rm.cpl != nullptr && rm.bins <= 8u) {  // whole warp here: see bin_few
+        bin_few(rm, batch, lane, shist, bin);
+        bin = -1;
+      }
+    }
     if (bin >= 0) {
       bool done = false;
       if constexpr (WGT) {
         if (rm.cpl != nullptr) {
-          // angle = the general gates' phases + the phase class (2^29 per pi/4)
-          const uint32_t ang = phi + (phase << 29);
-          double sn, cs;
-          sincospi((double)(int32_t)ang * 0x1p-31, &sn, &cs);
+          double cs, sn;
+          phasor(phase, cs, sn);
           if (shist) {
             double* sd = reinterpret_cast<double*>(shist);
             atomicAdd(&sd[2u * (uint32_t)bin], cs);
@@ -616,14 +705,26 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         const uint32_t r1 = word(E.la[1]) ^ word(E.lb[1]);
         const uint32_t r2 = word(E.la[2]) ^ word(E.lb[2]);
         const uint32_t pidx = (E.dst / 4u - (uint32_t)n) | (kTagSweep << 16);
+        // coupled p-bit: its coupling entry and neighbour words, loaded
+        // ahead so that their latency overlaps the heat-bath draw
+        Cpl Cp{};
+        uint32_t old_w = 0u, win_w = 0u, wout_w = 0u;
+        if constexpr (WGT) {
+          if (E.m & 0x100u) {
+            Cp = rm.cpl[E.dst / 4u - (uint32_t)n];
+            old_w = word(E.dst);
+            win_w = W[Cp.win];
+            wout_w = W[Cp.wout];
+          }
+        }
         uint32_t v = heat_bath_links(r0, r1, r2, (int)(WGT ? (E.m & 3u) : E.m), E.M0, E.M1, E.M2,
                                      E.M3, R, fast, thr0, thr1, thr2, thr3, gglob, sweep, pidx,
                                      k0, k1);
         if constexpr (WGT) {
           if (E.m & 0x100u) {
             const uint32_t p = E.dst / 4u - (uint32_t)n;
-            v = couple_accept(W, rm.cpl + p, word(E.dst), v, cur + acc_off + tid * kPreC, gglob,
-                              sweep, p, k0, k1);
+            v = couple_accept_body(Cp, win_w, wout_w, old_w, v, cur + acc_off + tid * kPreC,
+                                   gglob, sweep, p, k0, k1);
           }
         }
         *reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(W) + E.dst) = v;

@@ -24,9 +24,10 @@ def _lib():
 def _sum_tol(counts, n_u):
     """Per bin: each sample's angle is a sum of n_u phases rounded to 2^-32
     turn (error <= n_u 2^-33 turn = n_u pi 2^-32 rad) plus the class angle
-    (exact), sincospi in FP64 (~1e-16) and FP64 sums in another order
-    (~1e-16 per term): |delta| <= count (n_u * 7.4e-10 + 1e-15) + 1e-12."""
-    return counts.astype(np.float64) * (n_u * 7.4e-10 + 1e-15) + 1e-12
+    (exact); the device rounds the angle to FP32 (<= pi 2^-24 = 1.9e-7 rad)
+    and takes sincospif (about one ulp, 6e-8), then sums in FP64 in another
+    order (~1e-16 per term): |delta| <= count (n_u * 7.4e-10 + 3e-7) + 1e-12."""
+    return counts.astype(np.float64) * (n_u * 7.4e-10 + 3e-7) + 1e-12
 
 
 def _circuit(kind, n, d, seed):
