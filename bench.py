@@ -145,6 +145,14 @@ def dist_env():
     return rank, world, local
 
 
+def _oracle_gibbs(oracle, wl, **kw):
+    """The oracle's reference Gibbs sampler for the workload (the general-gate
+    one when the circuit has gate matrices)."""
+    if "mats" in wl.extra:
+        return oracle.u_gibbs(wl.n, wl.d, wl.gates, wl.extra["mats"], J=wl.J, seed=wl.seed, **kw)
+    return oracle.gibbs(wl.n, wl.d, wl.gates, J=wl.J, seed=wl.seed, **kw)
+
+
 def cpu_oracle_rate(wl, budget_s: float = 12.0, chains: int | None = None):
     """The oracle's reference Gibbs sampler on a bounded sample of the same
     workload (host cores, OpenMP over chains, about `budget_s` seconds).
@@ -153,12 +161,12 @@ def cpu_oracle_rate(wl, budget_s: float = 12.0, chains: int | None = None):
     n, d = wl.n, wl.d
     c = chains or 128
     t0 = time.perf_counter()
-    oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=20)
+    _oracle_gibbs(oracle, wl, chains=c, sweeps=20)
     dt = max(time.perf_counter() - t0, 1e-3)
     sweeps = max(2, int(budget_s / dt * 20))
     sweeps = min(sweeps, 200_000)
     t0 = time.perf_counter()
-    oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=sweeps)
+    _oracle_gibbs(oracle, wl, chains=c, sweeps=sweeps)
     dt = time.perf_counter() - t0
     flips = c * sweeps * n * d
     return flips / dt, oracle.num_threads(), f"{c} chains x {sweeps} sweeps of the {wl.name} circuit ({dt:.1f} s)"
@@ -175,13 +183,12 @@ def run_reference(args, wl):
     c = 64
     per_step = max(2, args.ref_sweeps)
     for _ in range(args.warmup):
-        oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=1)
+        _oracle_gibbs(oracle, wl, chains=c, sweeps=1)
     times = []
     state = None
     for k in range(args.steps):
         t0 = time.perf_counter()
-        r = oracle.gibbs(n, d, wl.gates, J=wl.J, seed=wl.seed, chains=c, sweeps=per_step,
-                         sweep0=k * per_step, state=state)
+        r = _oracle_gibbs(oracle, wl, chains=c, sweeps=per_step, sweep0=k * per_step, state=state)
         state = r["state"]
         times.append(time.perf_counter() - t0)
     flips = c * per_step * n * d * args.steps
@@ -198,8 +205,16 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def _model(pbits, wl):
+    """The workload's compiled circuit (general one-qubit gates when it has
+    gate matrices)."""
+    return pbits.Model(wl.n, wl.d, wl.gates, wl.J, mats=wl.extra.get("mats"))
+
+
 def _config(wl, args, world):
-    return {"workload": f"{wl.name}: random Clifford+T n={wl.n} d={wl.d} ({wl.n_pbits} p-bits), "
+    kind = ("random Clifford+T + 30% random one-qubit unitaries" if "mats" in wl.extra
+            else "random Clifford+T")
+    return {"workload": f"{wl.name}: {kind} n={wl.n} d={wl.d} ({wl.n_pbits} p-bits), "
                         f"{wl.chains} chains per GPU, {args.sweeps_per_step} sweeps per step, J={wl.J:.4f}",
             "n": wl.n, "d": wl.d, "chains_per_gpu": wl.chains, "sweeps_per_step": args.sweeps_per_step,
             "circuit_seed": 1000, "philox_key": wl.seed, "parallelism": f"chains sharded over {world} GPU(s)",
@@ -219,11 +234,14 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--learned-seconds", type=float, default=8.0)
+    ap.add_argument("--workload", default="mid", choices=["mid", "general_mid"],
+                    help="headline circuit: mid (Clifford+T) or general_mid (30%% of the "
+                         "one-qubit gates random unitaries)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
 
-    wl = W.mid()
+    wl = W.mid() if args.workload == "mid" else W.general_mid()
     if args.impl == "reference":
         run_reference(args, wl)
         return
@@ -244,7 +262,7 @@ def main():
     groups = (wl.chains + 31) // 32
     S = args.sweeps_per_step
     with torch.cuda.stream(stream):
-        model = pbits.Model(wl.n, wl.d, wl.gates, wl.J)
+        model = _model(pbits, wl)
         info = model.info()
         cfg = pbits.RunCfg(seed=wl.seed, chains=wl.chains, group0=rank * groups)
         run = pbits.Run([model], [cfg], stream=stream)
@@ -608,7 +626,7 @@ def measure_e2e(wl, rank, groups, S, dev, stream, world):
         for k in range(steps + 1):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            model = pbits.Model(wl.n, wl.d, wl.gates, wl.J)
+            model = _model(pbits, wl)
             if nbytes is None:
                 nbytes = pbits.workspace_bytes([model], [cfg])
                 ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
