@@ -18,7 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "general.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "general.c"), os.path.join(_HERE, "shor.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -27,7 +27,7 @@ H, S, T, CNOT, CZ, U = 0, 1, 2, 3, 4, 5
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c and general.c into liboracle.so (gcc, OpenMP, -O2)."""
+    """Compile oracle.c, general.c and shor.c into liboracle.so (gcc, OpenMP, -O2)."""
     if force or not os.path.exists(_LIB) or \
             os.path.getmtime(_LIB) < max(os.path.getmtime(s) for s in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
@@ -50,8 +50,10 @@ def _load():
             for name in ("orc_statevector", "orc_pathsum_exact", "orc_gf2_rank",
                          "orc_colour", "orc_gibbs", "orc_elim", "orc_elim_clamped", "orc_violations", "orc_path_phase",
                          "orc_thresholds", "orc_u_statevector", "orc_u_pathstats", "orc_u_gibbs",
-                         "orc_u_elim", "orc_u_log2z"):
+                         "orc_u_elim", "orc_u_log2z", "orc_shor_columns", "orc_shor_prob_at"):
                 getattr(lib, name).restype = ctypes.c_int
+            lib.orc_modexp.restype = ctypes.c_uint64
+            lib.orc_modexp.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
             lib.orc_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -373,3 +375,36 @@ def u_elim(n: int, d: int, gates, mats, *, seed: int, chains: int, sweeps: int, 
 def u_estimate(run: dict) -> np.ndarray:
     """psi_hat = 2^log2z * (sum of phases) / valid (Eq. U23 with p_C ~ |U_C|)."""
     return run["sum"] * (2.0 ** run["log2z"]) / max(run["valid"], 1)
+
+
+# ---- column sampling of the period-finding circuit (shor.c)
+
+def modexp(a: int, x: int, N: int) -> int:
+    return int(_load().orc_modexp(a, x, N))
+
+
+def shor_columns(N: int, a: int, n: int, x) -> tuple[np.ndarray, np.ndarray]:
+    """prob[k] = sum_y |sum_{i: y_i = y} 2^{-n/2} e^{2 pi i k x_i / 2^n}|^2 / T for
+    k < 2^n (n <= 24), and y_i = a^{x_i} mod N."""
+    lib = _load()
+    xs = np.ascontiguousarray(x, dtype=np.uint32)
+    prob = np.zeros(1 << n)
+    y = np.zeros(len(xs), dtype=np.uint64)
+    rc = lib.orc_shor_columns(ctypes.c_uint64(N), ctypes.c_uint64(a), n, _p(xs),
+                              ctypes.c_uint32(len(xs)), _p(prob), _p(y))
+    if rc != 0:
+        raise ValueError(f"orc_shor_columns failed ({rc})")
+    return prob, y
+
+
+def shor_prob_at(N: int, a: int, n: int, x, ks) -> np.ndarray:
+    """prob at the given k values (any n <= 32)."""
+    lib = _load()
+    xs = np.ascontiguousarray(x, dtype=np.uint32)
+    kk = np.ascontiguousarray(ks, dtype=np.uint64)
+    out = np.zeros(len(kk))
+    rc = lib.orc_shor_prob_at(ctypes.c_uint64(N), ctypes.c_uint64(a), n, _p(xs),
+                              ctypes.c_uint32(len(xs)), _p(kk), ctypes.c_uint32(len(kk)), _p(out))
+    if rc != 0:
+        raise ValueError(f"orc_shor_prob_at failed ({rc})")
+    return out

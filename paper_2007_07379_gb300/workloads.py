@@ -236,3 +236,38 @@ def large() -> Workload:
     g = random_circuit(24, 32, seed=4000)
     return Workload("large", 24, 32, g, chains=65536, sweeps=10_000, seed=0x5EED + 4,
                     J=default_J(24, 32, g), alphas=np.arange(64, dtype=np.uint32))
+
+
+# ---- column sampling of the period-finding circuit (Sec. 5.2)
+
+@dataclass
+class ShorWorkload:
+    name: str
+    N: int
+    a: int
+    n: int           # bits of the first register (t = n = ceil(log2 N), Sec. 5.2)
+    T: int           # column samples
+    seed: int
+    r: int           # the known order of a mod N (for checking only)
+
+    def columns(self) -> np.ndarray:
+        return shor_columns(self.n, self.T, self.seed)
+
+
+def shor_columns(n: int, T: int, seed: int) -> np.ndarray:
+    """T column indices uniform in [0, 2^n): the top n bits of SplitMix64(seed)
+    draws, uint32."""
+    rng = SplitMix64(seed)
+    return np.asarray([rng.next() >> (64 - n) for _ in range(T)], dtype=np.uint32)
+
+
+def shor_paper() -> ShorWorkload:
+    """f(x) = 10424^x mod 98743069 (27 bits, order 78) with 250 column samples
+    (Sec. 5.3: 250 columns of 2^27, about 5923 s on one laptop core)."""
+    return ShorWorkload("shor_78", 98743069, 10424, 27, 250, 0x5EED + 6, 78)
+
+
+def shor_table1(gamma: int = 3) -> ShorWorkload:
+    """The Table 1 case: N = 961307 (20 bits), a = 5, order 479568, with
+    gamma * r column samples (Sec. 5.2: T = gamma r, 2 <= gamma <= 4)."""
+    return ShorWorkload("shor_table1", 961307, 5, 20, gamma * 479568, 0x5EED + 7, 479568)
