@@ -342,6 +342,7 @@ def main():
         extra["elim"] = elim_measurement(dev, stream)
         extra["large"] = large_measurement(dev, stream)
         extra["general"] = general_measurement(dev, stream)
+        extra["shor"] = shor_measurement(dev, stream)
 
     learned = None
     if rank == 0 and not args.no_learned:
@@ -544,6 +545,47 @@ def general_measurement(dev, stream, sweeps: int = 2000, samples: int = 2000):
             "launch_ms": g_ms, "flips_per_s": flips / (g_ms * 1e-3),
             "plain_mid_flips_per_s": flips / (p_ms * 1e-3),
             "elim_paths_per_s": wl.chains * samples / (e_ms * 1e-3)}
+
+
+def shor_measurement(dev, stream):
+    """Column sampling of the period-finding circuit (Sec. 5.2): the paper's
+    27-bit example (order 78, 250 columns; 5923 s on one laptop core) and
+    the Table 1 case (N = 961307, order 479568, T = 3 r; 32 hours there).
+    Time of one pb_shor_columns call from host column indices to the device
+    distribution (modular powers, sort, column walk), the order read off as
+    the number of peaks above 2.2 / 2^n, and the column walk's FP32 rate."""
+    import torch
+    from paper_2007_07379_gb300 import pbits
+    out = {}
+    peak_fp32 = None
+    props = torch.cuda.get_device_properties(dev)
+    peaks, _ = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_fp32 = props.multi_processor_count * 128 * sm_max * 1e6  # FP32 lanes per clock
+    for wl in (W.shor_paper(), W.shor_table1(3)):
+        x = wl.columns()
+        with torch.cuda.stream(stream):
+            sc = pbits.ShorColumns(wl.n, wl.T, stream=stream)
+            sc.run(wl.N, wl.a, x)
+            stream.synchronize()
+            best = None
+            for _ in range(3):
+                t0 = time.perf_counter()
+                sc.run(wl.N, wl.a, x)
+                stream.synchronize()
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+            M = 2 ** wl.n
+            count, _, mx = sc.peaks(2.2 / M, 0)
+        steps = float(M) * wl.T  # (k, sample) pairs
+        # per pair: 2 FADD (sums) + 4 (complex rotation) FP32 lane operations
+        out[wl.name] = {"N": wl.N, "a": wl.a, "n": wl.n, "T": wl.T, "order": wl.r,
+                        "peaks_found": count, "call_s": best, "pairs_per_s": steps / best,
+                        "fp32_frac_lower_bound": steps * 6 / best / peak_fp32,
+                        "paper_s": 5923.0 if wl.name == "shor_78" else 32 * 3600.0}
+        del sc
+        torch.cuda.empty_cache()
+    return out
 
 
 def batched_measurement(dev, stream, sweeps: int = 10_000):

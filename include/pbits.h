@@ -398,6 +398,42 @@ PB_API int pb_gemm_bf16(const void* dA, int lda, const void* dB, int ldb, void* 
                         const float* dbias, const void* dmask, int ldm, int M, int N, int K,
                         int flags, float alpha, uintptr_t stream);
 
+/* ---- column sampling of the period-finding circuit (Sec. 5.2 and its
+ * column-sampling figure) ------------------------------------------------
+ * Sample i is a column x_i (0 <= x_i < 2^n) of the inverse QFT on the first
+ * register (t = n bits, Sec. 5.2); its entries 2^{-n/2} e^{2 pi i k x_i / 2^n}
+ * are added to column y_i = a^{x_i} mod N of psi, and
+ *   prob[k] = sum_y |psi[k, y]|^2 / T,  k = 0 .. 2^n - 1
+ * (sums to 1 when the drawn columns are distinct; every column once gives
+ * the exact distribution of the first register).  The order r of a mod N
+ * shows as r peaks near multiples of 2^n / r (Sec. 5.2: T = gamma r
+ * samples, 2 <= gamma <= 4).
+ * Device computation: modular exponentiation, a sort of the samples by
+ * (y, x), then per k a walk over the sorted samples (FP32 phasors: an exact
+ * integer phase k x mod 2^n per sample, re-anchored every 32 k; each term
+ * within about 1e-5 of the exact one; FP64 output).
+ *   N in [2, 2^32), n in [1, 32], 1 <= T <= 2^26, x: host array of T column
+ *   indices < 2^n (caller-owned; the draws are the caller's, so that they
+ *   can be shared and reproduced).  d_workspace: device, 256-byte aligned,
+ *   >= pb_shor_workspace_bytes(n, T).  d_prob: device, 2^n doubles (written).
+ *   y_out: optional host array of T u64 receiving y_i (synchronous when
+ *   given).  Asynchronous on `stream` otherwise.
+ *   Errors: PB_EINVAL (NULL, misaligned, x_i >= 2^n), PB_ERANGE (sizes),
+ *   PB_ECUDA. */
+PB_API int pb_shor_workspace_bytes(int n, uint32_t T, size_t* bytes);
+PB_API int pb_shor_columns(uint64_t N, uint64_t a, int n, const uint32_t* x, uint32_t T,
+                           void* d_workspace, size_t workspace_bytes, double* d_prob,
+                           uint64_t* y_out, uintptr_t stream);
+/* Peaks of prob (2^n doubles on the device): the local maxima in k (cyclic;
+ * >= the left neighbour and > the right one) with prob >= threshold.
+ * *count = their number; positions (optional host array) receives the first
+ * max_positions of them in increasing k; *max_prob (optional) the largest
+ * prob.  d_workspace: device, 256-byte aligned, >= 256 + 8 max_positions
+ * bytes (a column-sampling workspace may be reused).  Synchronous. */
+PB_API int pb_shor_peaks(const double* d_prob, int n, double threshold, void* d_workspace,
+                         size_t workspace_bytes, uint64_t* positions, uint32_t max_positions,
+                         uint32_t* count, double* max_prob, uintptr_t stream);
+
 PB_API const char* pb_strerror(int status);
 PB_API int pb_version(void);
 

@@ -111,6 +111,12 @@ _SIGS = {
                                             _VP]),
     "pb_mlp_train_paths": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_float, ctypes.c_uint64, _VP]),
+    "pb_shor_workspace_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_size_t)]),
+    "pb_shor_columns": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _VP, ctypes.c_uint32,
+                                       _VP, ctypes.c_size_t, _VP, _VP, ctypes.c_void_p]),
+    "pb_shor_peaks": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, _VP, ctypes.c_size_t, _VP,
+                                     ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "pb_gemm_bf16": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP, _VP,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_float, ctypes.c_void_p]),
@@ -606,3 +612,41 @@ def train_on_paths(mlp: Mlp, paths, n_paths: int, beta: int, steps: int, rows: i
                                      rows, ctypes.c_float(lr), ctypes.c_uint64(seed),
                                      ctypes.c_void_p(losses.data_ptr())), "pb_mlp_train_paths")
     return losses
+
+
+class ShorColumns:
+    """Column sampling of the period-finding circuit (pb_shor_columns): the
+    device buffers (torch) and the calls."""
+
+    def __init__(self, n: int, T: int, stream=None):
+        import torch
+        lib = load()
+        self.n, self.T = n, T
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        nb = ctypes.c_size_t(0)
+        _check(lib.pb_shor_workspace_bytes(n, T, ctypes.byref(nb)), "pb_shor_workspace_bytes")
+        self.ws = torch.empty(max(nb.value, 256 + 8 * 4096), dtype=torch.uint8, device="cuda")
+        self.prob = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+
+    def run(self, N: int, a: int, x, want_y: bool = False):
+        """Fills self.prob (device); returns y_i (host u64) when want_y."""
+        xs = np.ascontiguousarray(x, dtype=np.uint32)
+        assert len(xs) == self.T
+        y = np.zeros(self.T, dtype=np.uint64) if want_y else None
+        _check(load().pb_shor_columns(ctypes.c_uint64(N), ctypes.c_uint64(a), self.n, _ptr(xs),
+                                      ctypes.c_uint32(self.T), ctypes.c_void_p(self.ws.data_ptr()),
+                                      self.ws.numel(), ctypes.c_void_p(self.prob.data_ptr()),
+                                      None if y is None else _ptr(y),
+                                      ctypes.c_void_p(self.stream.cuda_stream)), "pb_shor_columns")
+        return y
+
+    def peaks(self, threshold: float, max_positions: int = 4096):
+        """(count, positions u64 (first max_positions, increasing), max prob)."""
+        pos = np.zeros(max(max_positions, 1), dtype=np.uint64)
+        c = ctypes.c_uint32(0)
+        mx = ctypes.c_double(0.0)
+        _check(load().pb_shor_peaks(ctypes.c_void_p(self.prob.data_ptr()), self.n, ctypes.c_double(threshold),
+                                    ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(), _ptr(pos),
+                                    ctypes.c_uint32(max_positions), ctypes.byref(c), ctypes.byref(mx),
+                                    ctypes.c_void_p(self.stream.cuda_stream)), "pb_shor_peaks")
+        return c.value, pos[:min(c.value, max_positions)], mx.value
