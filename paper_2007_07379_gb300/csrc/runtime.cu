@@ -28,7 +28,7 @@ cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, cons
                                      WsHeader* hdr, cudaStream_t st);
 cudaError_t launch_elim(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                         const uint32_t* const* d_init_tabs, uint32_t n_sweeps, size_t smem_bytes,
-                        WsHeader* hdr, cudaStream_t st);
+                        WsHeader* hdr, cudaStream_t st, bool wgt);
 size_t elim_smem_bytes(int n, int d, int zwords);
 cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
                               cudaStream_t st);
@@ -912,7 +912,7 @@ PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
     if (r->elim)
       e = launch_elim(r->d_rm(), r->nm, r->total_groups,
                       reinterpret_cast<const uint32_t* const*>(r->ws + r->L.init_ptrs), n_sweeps,
-                      r->elim_smem, r->hdr(), r->cap_st);
+                      r->elim_smem, r->hdr(), r->cap_st, r->wgt);
     else if (r->persistent)
       e = launch_sweeps_persistent(r->d_rm(), r->nm, reinterpret_cast<const uint32_t*>(r->ws + r->L.work),
                                    r->total_groups, n_sweeps, r->cons, r->prod, r->max_col, r->nc,

@@ -920,6 +920,9 @@ __global__ void init_kernel(const RunModelDev* __restrict__ rm, int n_models,
 // on the host), so every path ends at the clamped output.
 constexpr int kElimWarps = 8;
 
+// WGT: the instantiation for runs with general-gate models (coupled coins,
+// phasor records); plain runs take the plain one.
+template <bool WGT>
 __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
     const RunModelDev* __restrict__ rm, int n_models, uint32_t total_groups,
     const uint32_t* const* __restrict__ init_tabs, uint32_t n_sweeps, int wstride, WsHeader* hdr) {
@@ -950,7 +953,7 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
     const Rec R = r.rec[i];
     bad |= (R.vd >= nw || R.va >= nw || R.vb >= nw || R.pa >= nw || R.pb >= nw) ? 1 : 0;
   }
-  if (r.cpl)
+  if (WGT && r.cpl)
     for (int i = threadIdx.x; i < md.n_ug; i += blockDim.x)
       bad |= (r.uph[i].win >= nw || r.uph[i].wout >= nw) ? 1 : 0;
   if (__syncthreads_or(bad)) {
@@ -1003,7 +1006,7 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
               msk &= msk - 1u;
             }
           }
-        } else if (e == 0xFFFFFFFFu && r.cpl && (r.cpl[p].flags & 2u)) {
+        } else if (WGT && e == 0xFFFFFFFFu && r.cpl && (r.cpl[p].flags & 2u)) {
           // coupled general gate: s_in ^ [u < B], u from the tag-4 planes of
           // this p-bit, most significant first, compared bit-sliced
           const uint32_t B = r.cpl[p].B;
@@ -1035,10 +1038,9 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
     }
     rec.clear();
     rec.read(W, r.rec, 0, npb, lane);
-    if (r.cpl) rec.read_u(W, r.uph, 0, md.n_ug, lane);
+    if (WGT && r.cpl) rec.read_u(W, r.uph, 0, md.n_ug, lane);
     rec.reduce(W, n, d, lane);
-    if (r.cpl) rec.bin<true>(r, g, batch, lane, nullptr, n_valid, n_samples);
-    else rec.bin<false>(r, g, batch, lane, nullptr, n_valid, n_samples);
+    rec.bin<WGT>(r, g, batch, lane, nullptr, n_valid, n_samples);
     __syncwarp();
   }
   if (lane == 0) {
@@ -1250,10 +1252,14 @@ cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, cons
 // smem_bytes from elim_smem_bytes: kElimWarps equal per-warp regions
 cudaError_t launch_elim(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                         const uint32_t* const* d_init_tabs, uint32_t n_sweeps, size_t smem_bytes,
-                        WsHeader* hdr, cudaStream_t st) {
+                        WsHeader* hdr, cudaStream_t st, bool wgt) {
   const int wstride = (int)(smem_bytes / (4 * kElimWarps));
-  elim_kernel<<<total_groups, kElimWarps * 32, smem_bytes, st>>>(d_rm, n_models, total_groups,
-                                                                 d_init_tabs, n_sweeps, wstride, hdr);
+  if (wgt)
+    elim_kernel<true><<<total_groups, kElimWarps * 32, smem_bytes, st>>>(
+        d_rm, n_models, total_groups, d_init_tabs, n_sweeps, wstride, hdr);
+  else
+    elim_kernel<false><<<total_groups, kElimWarps * 32, smem_bytes, st>>>(
+        d_rm, n_models, total_groups, d_init_tabs, n_sweeps, wstride, hdr);
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
 }
@@ -1298,7 +1304,8 @@ cudaError_t sweep_prepare() {
       (e = cudaFuncSetAttribute(sweep_persistent_kernel<3>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_persistent_kernel<4>, a, big)) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(elim_kernel, a, big);
+  if ((e = cudaFuncSetAttribute(elim_kernel<false>, a, big)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(elim_kernel<true>, a, big);
 }
 
 int sweep_max_blocks_per_sm(int threads, size_t smem) {
