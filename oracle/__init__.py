@@ -23,7 +23,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-H, S, T, CNOT, CZ, U = 0, 1, 2, 3, 4, 5
+H, S, T, CNOT, CZ, U, X, U2 = 0, 1, 2, 3, 4, 5, 6, 7
 
 
 def build(force: bool = False) -> str:
@@ -50,7 +50,8 @@ def _load():
             for name in ("orc_statevector", "orc_pathsum_exact", "orc_gf2_rank",
                          "orc_colour", "orc_gibbs", "orc_elim", "orc_elim_clamped", "orc_violations", "orc_path_phase",
                          "orc_thresholds", "orc_u_statevector", "orc_u_pathstats", "orc_u_gibbs",
-                         "orc_u_elim", "orc_u_log2z", "orc_shor_columns", "orc_shor_prob_at"):
+                         "orc_u_elim", "orc_u_log2z", "orc_shor_columns", "orc_shor_prob_at",
+                         "orc_u_colour"):
                 getattr(lib, name).restype = ctypes.c_int
             lib.orc_modexp.restype = ctypes.c_uint64
             lib.orc_modexp.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
@@ -261,23 +262,30 @@ def estimate_amplitudes(cnt: np.ndarray, valid: int, h: int) -> np.ndarray:
 
 # ---- general one-qubit gates (general.c)
 
-def _mats(gates, mats) -> np.ndarray:
-    """Gate matrices as float64 [n_gates, 8]: Re/Im of U00, U01, U10, U11
-    (rows = output bit); rows of non-U gates are ignored."""
+def _mats(gates, mats, mats2=None) -> np.ndarray:
+    """Gate matrices as float64 [n_gates, 32]: a U row's first 8 entries are
+    Re/Im of U00, U01, U10, U11 (rows = output bit, from `mats` [ng, 2, 2]);
+    a U2 row holds Re/Im of its 4x4 matrix row-major (from `mats2`
+    [ng, 4, 4], basis index x_{q0} + 2 x_{q1}); other rows are ignored."""
     g = _gates(gates)
-    m = np.zeros((len(g), 8), dtype=np.float64)
+    m = np.zeros((len(g), 32), dtype=np.float64)
     if mats is not None:
         c = np.asarray(mats, dtype=np.complex128).reshape(len(g), 4)
-        m[:, 0::2] = c.real
-        m[:, 1::2] = c.imag
+        m[:, 0:8:2] = c.real
+        m[:, 1:8:2] = c.imag
+    if mats2 is not None:
+        c2 = np.asarray(mats2, dtype=np.complex128).reshape(len(g), 16)
+        rows = g[:, 0] == U2
+        m[rows, 0::2] = c2[rows].real
+        m[rows, 1::2] = c2[rows].imag
     return np.ascontiguousarray(m)
 
 
-def u_statevector(n: int, d: int, gates, mats, beta: int = 0) -> np.ndarray:
-    """FP64 state vector of a circuit with general one-qubit gates (op U)."""
+def u_statevector(n: int, d: int, gates, mats, beta: int = 0, mats2=None) -> np.ndarray:
+    """FP64 state vector of a circuit with general gates (ops U, X, U2)."""
     lib = _load()
     g = _gates(gates)
-    m = _mats(g, mats)
+    m = _mats(g, mats, mats2)
     re = np.zeros(1 << n)
     im = np.zeros(1 << n)
     rc = lib.orc_u_statevector(n, d, _p(g), len(g), _p(m), ctypes.c_uint32(beta), _p(re), _p(im))
@@ -286,13 +294,13 @@ def u_statevector(n: int, d: int, gates, mats, beta: int = 0) -> np.ndarray:
     return re + 1j * im
 
 
-def u_pathstats(n: int, d: int, gates, mats, beta: int = 0) -> dict:
+def u_pathstats(n: int, d: int, gates, mats, beta: int = 0, mats2=None) -> dict:
     """Brute-force path sum per output: U (complex), zabs = sum |U_C|,
     s2 = sum |U_C|^2, npath = nonzero paths; std_weighted = sqrt(zabs^2 - |U|^2)
     and std_uniform = sqrt(npath s2 - |U|^2) (Eq. U30, paths to each output)."""
     lib = _load()
     g = _gates(gates)
-    m = _mats(g, mats)
+    m = _mats(g, mats, mats2)
     N = 1 << n
     ure, uim, zabs, s2 = (np.zeros(N) for _ in range(4))
     npath = np.zeros(N, dtype=np.uint64)
@@ -307,10 +315,10 @@ def u_pathstats(n: int, d: int, gates, mats, beta: int = 0) -> dict:
             "std_uniform": np.sqrt(np.maximum(npath.astype(np.float64) * s2 - a2, 0.0))}
 
 
-def u_log2z(n: int, d: int, gates, mats) -> float:
+def u_log2z(n: int, d: int, gates, mats, mats2=None) -> float:
     lib = _load()
     g = _gates(gates)
-    m = _mats(g, mats)
+    m = _mats(g, mats, mats2)
     out = ctypes.c_double(0.0)
     rc = lib.orc_u_log2z(n, d, _p(g), len(g), _p(m), ctypes.byref(out))
     if rc != 0:
@@ -318,10 +326,10 @@ def u_log2z(n: int, d: int, gates, mats) -> float:
     return out.value
 
 
-def _u_run(fn, n, d, gates, mats, chains, alphas, extra_args, state_arg):
+def _u_run(fn, n, d, gates, mats, chains, alphas, extra_args, state_arg, mats2=None):
     lib = _load()
     g = _gates(gates)
-    m = _mats(g, mats)
+    m = _mats(g, mats, mats2)
     if alphas is None:
         bins, al = 1 << n, None
     else:
@@ -342,7 +350,8 @@ def _u_run(fn, n, d, gates, mats, chains, alphas, extra_args, state_arg):
 
 def u_gibbs(n: int, d: int, gates, mats, *, J: float, seed: int, chains: int, sweeps: int,
             beta: int = 0, chain0: int = 0, sweep0: int = 0, burn_in: int = 0,
-            record_every: int = 1, state: np.ndarray | None = None, alphas=None) -> dict:
+            record_every: int = 1, state: np.ndarray | None = None, alphas=None,
+            mats2=None) -> dict:
     """Reference Gibbs run with general one-qubit gates (proposal by heat-bath
     on the J energy, Metropolis acceptance on the coupling energy).  Returns
     dict(state, sum = sum of e^{i arg U_C} per bin, cnt, valid, samples, log2z);
@@ -353,21 +362,21 @@ def u_gibbs(n: int, d: int, gates, mats, *, J: float, seed: int, chains: int, sw
     args = (ctypes.c_uint32(beta), ctypes.c_double(J), ctypes.c_uint64(seed), ctypes.c_uint32(chain0),
             ctypes.c_uint32(chains), ctypes.c_uint32(sweep0), ctypes.c_uint32(sweeps),
             ctypes.c_uint32(burn_in), ctypes.c_uint32(record_every), init)
-    out = _u_run("orc_u_gibbs", n, d, gates, mats, chains, alphas, args, _p(st))
+    out = _u_run("orc_u_gibbs", n, d, gates, mats, chains, alphas, args, _p(st), mats2)
     out["state"] = st
     return out
 
 
 def u_elim(n: int, d: int, gates, mats, *, seed: int, chains: int, sweeps: int, beta: int = 0,
            chain0: int = 0, sweep0: int = 0, burn_in: int = 0, record_every: int = 1,
-           alphas=None) -> dict:
+           alphas=None, mats2=None) -> dict:
     """Exact i.i.d. sampler with general one-qubit gates; outputs as u_gibbs
     (state = each chain's last drawn path)."""
     st = np.zeros((chains, d), dtype=np.uint32)
     args = (ctypes.c_uint32(beta), ctypes.c_uint64(seed), ctypes.c_uint32(chain0),
             ctypes.c_uint32(chains), ctypes.c_uint32(sweep0), ctypes.c_uint32(sweeps),
             ctypes.c_uint32(burn_in), ctypes.c_uint32(record_every))
-    out = _u_run("orc_u_elim", n, d, gates, mats, chains, alphas, args, _p(st))
+    out = _u_run("orc_u_elim", n, d, gates, mats, chains, alphas, args, _p(st), mats2)
     out["state"] = st
     return out
 
@@ -408,3 +417,15 @@ def shor_prob_at(N: int, a: int, n: int, x, ks) -> np.ndarray:
     if rc != 0:
         raise ValueError(f"orc_shor_prob_at failed ({rc})")
     return out
+
+
+def u_colour(n: int, d: int, gates, mats=None, mats2=None) -> np.ndarray:
+    """Colour classes [d, n] of a general circuit (the sweep order)."""
+    lib = _load()
+    g = _gates(gates)
+    m = _mats(g, mats, mats2)
+    col = np.zeros((d, n), dtype=np.int32)
+    rc = lib.orc_u_colour(n, d, _p(g), len(g), _p(m), _p(col))
+    if rc <= 0:
+        raise ValueError("orc_u_colour failed")
+    return col

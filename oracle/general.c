@@ -8,9 +8,20 @@
  *
  * A gate row with op = ORC_U (5) carries a 2x2 complex matrix U, rows =
  * output bit, columns = input bit (U_yx = <y|U|x>, the kbordermatrix of
- * Sec. 2), stored as mats[8 i + 0..7] = Re U00, Im U00, Re U01, Im U01,
- * Re U10, Im U10, Re U11, Im U11 for gate row i.  Rows with other ops are the
- * Clifford+T gates of oracle.c; their mats entries are ignored.
+ * Sec. 2), stored as mats[32 i + 0..7] = Re U00, Im U00, Re U01, Im U01,
+ * Re U10, Im U10, Re U11, Im U11 for gate row i.  op = ORC_X (6) is the
+ * Pauli X of the Appendix (a deterministic NOT, no phase).  op = ORC_U2 (7)
+ * is a two-qubit gate on (q0, q1) with a 4x4 complex matrix,
+ * mats[32 i + 2 (4 y + x)] = Re, + 1 = Im of <y|U|x>, basis index
+ * x = x_{q0} + 2 x_{q1} (the order 00, 10, 01, 11 of Eq. ET2); it must be
+ * unitary within 1e-9 with exactly one nonzero entry per column (a
+ * permutation with phases: SWAP, the Appendix's exchange operator J12,
+ * controlled phases, ...).  Every permutation of two bits is affine over
+ * GF(2), so each output bit is a copy or an XOR of the input bits, possibly
+ * complemented; an output bit that is the complement of an XOR of both
+ * inputs is rejected (the J-penalty links carry at most two words).  Rows
+ * with other ops are the Clifford+T gates of oracle.c; their mats entries
+ * are ignored.
  *
  * Paths and weights (Eq. U, Eq. path): the weight of a path is the product
  * of its layer elements, complex FP64 here.  Sampling (Eq. weightedS): a path
@@ -58,15 +69,15 @@ typedef struct {
   int32_t op, layer, q0, q1;
 } orc_gate;
 
-enum { G_H = 0, G_S = 1, G_T = 2, G_CNOT = 3, G_CZ = 4, G_U = 5 };
+enum { G_H = 0, G_S = 1, G_T = 2, G_CNOT = 3, G_CZ = 4, G_U = 5, G_X = 6, G_U2 = 7 };
 enum { K_STD = 0, K_DIAG = 1, K_ANTI = 2, K_COUPLED = 3 };
+enum { MAT = 32 }; /* doubles per gate row of mats */
 
 /* from oracle.c */
 void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]);
-int orc_colour(int n, int d, const orc_gate* g, int ng, int32_t* colour);
 int orc_thresholds(double J, uint32_t thr[4]);
 
-static int arity(int op) { return (op == G_CNOT || op == G_CZ) ? 2 : 1; }
+static int arity(int op) { return (op == G_CNOT || op == G_CZ || op == G_U2) ? 2 : 1; }
 static int bitof(uint32_t w, int q) { return (int)((w >> q) & 1u); }
 
 /* ------------------------------------------------------------------------ */
@@ -97,7 +108,52 @@ static void std_entry(int op, int y, int x, double* re, double* im) {
     case G_CZ: /* diag(1, 1, 1, -1) */
       if (y == x) *re = (x == 3) ? -1.0 : 1.0;
       break;
+    case G_X: /* [[0, 1], [1, 0]] */
+      if (y != x) *re = 1.0;
+      break;
   }
+}
+
+static void u2_entry(const double* m32, int y, int x, double* re, double* im) {
+  const int k = 2 * (4 * y + x);
+  *re = m32[k];
+  *im = m32[k + 1];
+}
+
+/* A two-qubit gate: unitary within 1e-9, one nonzero per column; perm[x] =
+ * the row of column x's nonzero; dmask[o] (bit u: output bit o depends on
+ * input bit u) and cbit[o] of the affine map.  -1 if rejected. */
+static int u2_classify(const double* m, int perm[4], int dmask[2], int cbit[2]) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double sr = 0.0, si = 0.0;
+      for (int y = 0; y < 4; ++y) {
+        double ar, ai, br, bi;
+        u2_entry(m, y, i, &ar, &ai);
+        u2_entry(m, y, j, &br, &bi);
+        sr += ar * br + ai * bi;
+        si += ar * bi - ai * br;
+      }
+      if (fabs(sr - (i == j ? 1.0 : 0.0)) > 1e-9 || fabs(si) > 1e-9) return -1;
+    }
+  for (int x = 0; x < 4; ++x) {
+    int nz = 0;
+    for (int y = 0; y < 4; ++y) {
+      double r, i;
+      u2_entry(m, y, x, &r, &i);
+      if (r != 0.0 || i != 0.0) { perm[x] = y; ++nz; }
+    }
+    if (nz != 1) return -1;
+  }
+  for (int o = 0; o < 2; ++o) {
+    const int c = (perm[0] >> o) & 1, al = ((perm[1] >> o) & 1) ^ c, be = ((perm[2] >> o) & 1) ^ c;
+    if ((((perm[3] >> o) & 1) ^ c) != (al ^ be)) return -1; /* not affine (cannot happen) */
+    dmask[o] = al | (be << 1);
+    cbit[o] = c;
+    if (dmask[o] == 0) return -1;
+    if (dmask[o] == 3 && c) return -1; /* complement of x1 XOR x2: not representable */
+  }
+  return 0;
 }
 
 static void u_entry(const double* m8, int y, int x, double* re, double* im) {
@@ -141,7 +197,8 @@ static int u_kind(const double* m8, double* a, double* b, double* K) {
 /* Complex element <y|G|x> of gate row i (its own index convention). */
 static void gate_elem(const orc_gate* G, const double* mats, int i, int y, int x, double* re,
                       double* im) {
-  if (G->op == G_U) u_entry(mats + 8 * i, y, x, re, im);
+  if (G->op == G_U) u_entry(mats + (size_t)MAT * i, y, x, re, im);
+  else if (G->op == G_U2) u2_entry(mats + (size_t)MAT * i, y, x, re, im);
   else std_entry(G->op, y, x, re, im);
 }
 
@@ -156,10 +213,13 @@ typedef struct {
   int32_t* gate_of; /* [d][n] gate row acting on (layer, qubit), or -1 */
   int* kind;        /* per gate row: K_STD or the ORC_U kind */
   double *a, *b, *K;
+  int (*perm)[4];   /* per gate row (ORC_U2): the permutation */
+  int (*dmask)[2], (*cbit)[2];
 } unet;
 
 static void unet_free(unet* u) {
   free(u->gate_of); free(u->kind); free(u->a); free(u->b); free(u->K);
+  free(u->perm); free(u->dmask); free(u->cbit);
 }
 
 /* Checks the circuit and classifies its gates; 0 on success. */
@@ -172,11 +232,17 @@ static int unet_init(unet* u, int n, int d, const orc_gate* g, int ng, const dou
   u->a = (double*)calloc((size_t)ng + 1, sizeof(double));
   u->b = (double*)calloc((size_t)ng + 1, sizeof(double));
   u->K = (double*)calloc((size_t)ng + 1, sizeof(double));
-  if (!u->gate_of || !u->kind || !u->a || !u->b || !u->K) { unet_free(u); return -3; }
+  u->perm = calloc((size_t)ng + 1, sizeof *u->perm);
+  u->dmask = calloc((size_t)ng + 1, sizeof *u->dmask);
+  u->cbit = calloc((size_t)ng + 1, sizeof *u->cbit);
+  if (!u->gate_of || !u->kind || !u->a || !u->b || !u->K || !u->perm || !u->dmask || !u->cbit) {
+    unet_free(u);
+    return -3;
+  }
   for (int i = 0; i < n * d; ++i) u->gate_of[i] = -1;
   for (int i = 0; i < ng; ++i) {
     const orc_gate* G = &g[i];
-    if (G->op < 0 || G->op > G_U || G->layer < 0 || G->layer >= d || G->q0 < 0 || G->q0 >= n) {
+    if (G->op < 0 || G->op > G_U2 || G->layer < 0 || G->layer >= d || G->q0 < 0 || G->q0 >= n) {
       unet_free(u); return -1;
     }
     if (arity(G->op) == 2 && (G->q1 < 0 || G->q1 >= n || G->q1 == G->q0)) { unet_free(u); return -1; }
@@ -191,9 +257,15 @@ static int unet_init(unet* u, int n, int d, const orc_gate* g, int ng, const dou
     u->kind[i] = K_STD;
     if (G->op == G_U) {
       if (!mats) { unet_free(u); return -1; }
-      const int k = u_kind(mats + 8 * i, &u->a[i], &u->b[i], &u->K[i]);
+      const int k = u_kind(mats + (size_t)MAT * i, &u->a[i], &u->b[i], &u->K[i]);
       if (k < 0) { unet_free(u); return -1; }
       u->kind[i] = k;
+    }
+    if (G->op == G_U2) {
+      if (!mats || u2_classify(mats + (size_t)MAT * i, u->perm[i], u->dmask[i], u->cbit[i]) != 0) {
+        unet_free(u);
+        return -1;
+      }
     }
   }
   return 0;
@@ -346,6 +418,12 @@ static int layer_viol(const unet* u, int L, uint32_t x, uint32_t y) {
         if (u->kind[gi] == K_DIAG) v += bitof(x, q) != bitof(y, q);
         else if (u->kind[gi] == K_ANTI) v += bitof(x, q) == bitof(y, q);
         break;
+      case G_X: v += bitof(x, q) == bitof(y, q); break;
+      case G_U2: {
+        const int o = (q == G->q0) ? 0 : 1;
+        v += ((u->perm[gi][gidx(G, x)] >> o) & 1) != bitof(y, q);
+        break;
+      }
     }
   }
   return v;
@@ -382,6 +460,8 @@ static int det_bit(const unet* u, int L, int q, uint32_t x) {
   const orc_gate* G = &u->g[gi];
   if (G->op == G_CNOT && q == G->q1) return bitof(x, q) ^ bitof(x, G->q0);
   if (G->op == G_U && u->kind[gi] == K_ANTI) return bitof(x, q) ^ 1;
+  if (G->op == G_X) return bitof(x, q) ^ 1;
+  if (G->op == G_U2) return (u->perm[gi][gidx(G, x)] >> ((q == G->q0) ? 0 : 1)) & 1;
   return bitof(x, q);
 }
 
@@ -390,6 +470,95 @@ static int is_free(const unet* u, int L, int q) {
   const int gi = u->gate_of[L * u->n + q];
   if (gi < 0) return 0;
   return u->g[gi].op == G_H || (u->g[gi].op == G_U && u->kind[gi] == K_COUPLED);
+}
+
+/* Colour classes of one sweep: the rule of oracle.c's pbit_colours (DSATUR,
+ * Brelaz 1979: the uncoloured p-bit with the most distinct neighbour colours,
+ * then the most neighbours, then the lowest p, takes the smallest colour its
+ * neighbours lack; more than four colours fall back to the fixed classes
+ * 2 [k even] + [the p-bit is the second input of a two-input output bit in
+ * layer k]) on the factor graph of these gates: the output bit (L+1, q) of
+ * every non-H gate or identity wire is one factor with the input bits it
+ * depends on -- (L, q) for an identity wire, S, T, CZ, X and any U (a
+ * coupled U's energy joins the same two bits), (L, q) and (L, c) for a CNOT
+ * target, the inputs in the affine map of a U2 output.  Layer 0 is clamped.
+ * Returns the number of classes. */
+static int u_colours(const unet* u, int32_t* colour) {
+  const int n = u->n, d = u->d, N = n * d;
+  enum { MAXN = 16 };
+  int* nb = (int*)malloc(sizeof(int) * (size_t)N * MAXN);
+  int* deg = (int*)calloc((size_t)N, sizeof(int));
+  uint32_t* seen = (uint32_t*)calloc((size_t)N, sizeof(uint32_t));
+  if (!nb || !deg || !seen) { free(nb); free(deg); free(seen); return -1; }
+  int over = 0;
+  for (int L = 0; L < d; ++L)
+    for (int q = 0; q < n; ++q) {
+      int vars[3], nv = 0, ins[2], ni = 0;
+      vars[nv++] = L * n + q; /* p-bit (L+1, q) */
+      const int gi = u->gate_of[L * n + q];
+      if (gi < 0) {
+        ins[ni++] = q;
+      } else {
+        const orc_gate* G = &u->g[gi];
+        if (G->op == G_H) continue;
+        if (G->op == G_CNOT) {
+          ins[ni++] = q;
+          if (q == G->q1) ins[ni++] = G->q0;
+        } else if (G->op == G_U2) {
+          const int dm = u->dmask[gi][(q == G->q0) ? 0 : 1];
+          if (dm & 1) ins[ni++] = G->q0;
+          if (dm & 2) ins[ni++] = G->q1;
+        } else {
+          ins[ni++] = q;
+        }
+      }
+      if (L >= 1)
+        for (int t = 0; t < ni; ++t) vars[nv++] = (L - 1) * n + ins[t];
+      for (int a = 0; a < nv; ++a)
+        for (int b = 0; b < nv; ++b) {
+          if (a == b) continue;
+          const int x = vars[a], y = vars[b];
+          int dup = 0;
+          for (int e = 0; e < deg[x]; ++e) dup |= nb[x * MAXN + e] == y;
+          if (dup) continue;
+          if (deg[x] == MAXN) { over = 1; continue; }
+          nb[x * MAXN + deg[x]++] = y;
+        }
+    }
+  int ncol = 0;
+  for (int i = 0; i < N; ++i) colour[i] = -1;
+  for (int step = 0; step < N && !over; ++step) {
+    int best = -1, bsat = -1, bdeg = -1;
+    for (int v = 0; v < N; ++v) {
+      if (colour[v] >= 0) continue;
+      const int sat = __builtin_popcount(seen[v]);
+      if (sat > bsat || (sat == bsat && deg[v] > bdeg)) { best = v; bsat = sat; bdeg = deg[v]; }
+    }
+    int c = 0;
+    while (c < 32 && ((seen[best] >> c) & 1u)) ++c;
+    colour[best] = c;
+    if (c + 1 > ncol) ncol = c + 1;
+    for (int e = 0; e < deg[best]; ++e) seen[nb[best * MAXN + e]] |= 1u << c;
+  }
+  if (over || ncol > 4) {
+    ncol = 4;
+    for (int k = 1; k <= d; ++k)
+      for (int q = 0; q < n; ++q) {
+        int second = 0;
+        if (k < d) {
+          const int gi = u->gate_of[k * n + q];
+          if (gi >= 0) {
+            const orc_gate* G = &u->g[gi];
+            if (G->op == G_CNOT && G->q1 == q) second = 1;
+            if (G->op == G_U2 && G->q1 == q && (u->dmask[gi][0] == 3 || u->dmask[gi][1] == 3))
+              second = 1;
+          }
+        }
+        colour[(k - 1) * n + q] = 2 * ((k % 2) == 0) + second;
+      }
+  }
+  free(nb); free(deg); free(seen);
+  return ncol;
 }
 
 /* The 32-bit uniform of chain c: bit (c mod 32) of successive Philox output
@@ -446,9 +615,8 @@ static void add_sample(const unet* u, const uint32_t* s, const uint32_t* alphas,
  * valid recorded samples ending there of e^{i arg U_C}, cnt = their number.
  * The estimator is psi_alpha = 2^{log2z} (sre + i sim) / valid_total.
  *
- * Sweep: the colour classes of orc_colour, computed with every ORC_U gate
- * given the factor structure of a one-qubit non-H gate (a two-body factor
- * between (k-1, q) and (k, q)).  Update of p-bit x = (k, q), p = (k-1) n + q:
+ * Sweep: the colour classes of u_colours.  Update of p-bit x = (k, q),
+ * p = (k-1) n + q:
  *   Step 1 (proposal, heat-bath on the J-penalty energy): v = change of the
  *     violation count when x goes 0 -> 1, u = uniform32(tag 0),
  *     x' = [v < 0] XOR [u < thr[|v|]].
@@ -475,13 +643,9 @@ int orc_u_gibbs(int n, int d, const orc_gate* g, int ng, const double* mats, uin
   uint32_t thr[4];
   if (orc_thresholds(J, thr) != 0) { unet_free(&u); return -1; }
   if (log2z) *log2z = log2_scale(&u);
-  /* colouring: ORC_U as a one-qubit non-H gate (S) */
-  orc_gate* gc = (orc_gate*)malloc(sizeof(orc_gate) * (size_t)(ng > 0 ? ng : 1));
   int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)n * d);
-  if (!gc || !col) { free(gc); free(col); unet_free(&u); return -3; }
-  for (int i = 0; i < ng; ++i) { gc[i] = g[i]; if (gc[i].op == G_U) gc[i].op = G_S; }
-  const int ncol = orc_colour(n, d, gc, ng, col);
-  free(gc);
+  if (!col) { unet_free(&u); return -3; }
+  const int ncol = u_colours(&u, col);
   if (ncol <= 0) { free(col); unet_free(&u); return -3; }
   const uint32_t nmask = (n == 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
   const uint64_t bins = alphas ? (uint64_t)n_alphas : (1ull << n);
@@ -653,4 +817,14 @@ int orc_u_elim(int n, int d, const orc_gate* g, int ng, const double* mats, uint
   }
   unet_free(&u);
   return err ? -4 : 0;
+}
+
+/* Colour classes (u_colours) of a general circuit, [d][n]; the number of
+ * classes, or <= 0 on error. */
+int orc_u_colour(int n, int d, const orc_gate* g, int ng, const double* mats, int32_t* colour) {
+  unet u;
+  if (unet_init(&u, n, d, g, ng, mats) != 0) return -1;
+  const int ncol = u_colours(&u, colour);
+  unet_free(&u);
+  return ncol;
 }

@@ -22,8 +22,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-H, S, T, CNOT, CZ, U = 0, 1, 2, 3, 4, 5
-GATE_NAMES = {H: "H", S: "S", T: "T", CNOT: "CNOT", CZ: "CZ", U: "U"}
+H, S, T, CNOT, CZ, U, X, U2 = 0, 1, 2, 3, 4, 5, 6, 7
+GATE_NAMES = {H: "H", S: "S", T: "T", CNOT: "CNOT", CZ: "CZ", U: "U", X: "X", U2: "U2"}
 _MASK64 = (1 << 64) - 1
 
 
@@ -108,6 +108,68 @@ def u3(theta: float, phi: float, lam: float) -> np.ndarray:
     c, s = np.cos(theta / 2), np.sin(theta / 2)
     return np.array([[c, -np.exp(1j * lam) * s],
                      [np.exp(1j * phi) * s, np.exp(1j * (phi + lam)) * c]], dtype=np.complex128)
+
+
+# Two-qubit gates as 4x4 matrices, rows = output, basis index x_{q0} + 2 x_{q1}
+# (the order 00, 10, 01, 11 of Eq. ET2).
+
+def swap_matrix() -> np.ndarray:
+    m = np.zeros((4, 4), dtype=np.complex128)
+    for x in range(4):
+        y = ((x & 1) << 1) | (x >> 1)
+        m[y, x] = 1.0
+    return m
+
+
+def exchange_matrix(gamma: float) -> np.ndarray:
+    """The Appendix's two-qubit exchange operator J12:
+    diag(e^{i g/2}, e^{-i g/2}, e^{-i g/2}, e^{i g/2})."""
+    return np.diag(np.exp(0.5j * gamma * np.array([1, -1, -1, 1]))).astype(np.complex128)
+
+
+def iswap_matrix() -> np.ndarray:
+    m = swap_matrix()
+    m[2, 1] = m[1, 2] = 1j
+    return m
+
+
+def cphase_matrix(theta: float) -> np.ndarray:
+    return np.diag([1, 1, 1, np.exp(1j * theta)]).astype(np.complex128)
+
+
+def cnot_matrix(control_is_q0: bool = True) -> np.ndarray:
+    m = np.zeros((4, 4), dtype=np.complex128)
+    for x in range(4):
+        c, t = (x & 1, x >> 1) if control_is_q0 else (x >> 1, x & 1)
+        t ^= c
+        y = (c | (t << 1)) if control_is_q0 else (t | (c << 1))
+        m[y, x] = 1.0
+    return m
+
+
+def random_two_qubit_circuit(n: int, d: int, seed: int, frac: float = 0.5):
+    """random_circuit(n, d, seed) with each CNOT / CZ replaced, with
+    probability frac, by a U2 gate drawn from {SWAP, exchange J12(g), iSWAP,
+    controlled phase(t), CNOT with the control on q1} (angles uniform in
+    [0, 2 pi)) and each one-qubit gate replaced, with probability frac / 4,
+    by X.  Returns (gates, mats2) with mats2 complex128[n_gates, 4, 4]."""
+    g = random_circuit(n, d, seed).copy()
+    rng = SplitMix64(seed ^ 0x51A7)
+    mats2 = np.zeros((len(g), 4, 4), dtype=np.complex128)
+
+    def unif() -> float:
+        return (rng.next() >> 11) * (2.0 ** -53)
+
+    for i in range(len(g)):
+        if g[i, 0] in (CNOT, CZ) and unif() < frac:
+            kind = rng.below(5)
+            ang = 2 * np.pi * unif()
+            mats2[i] = (swap_matrix(), exchange_matrix(ang), iswap_matrix(), cphase_matrix(ang),
+                        cnot_matrix(False))[kind]
+            g[i, 0] = U2
+        elif g[i, 0] in (H, S, T) and unif() < frac / 4:
+            g[i, 0] = X
+    return g, mats2
 
 
 def rotated_h_chain(d: int, theta: float):

@@ -10,12 +10,12 @@ import oracle
 from paper_2007_07379_gb300 import workloads as W
 
 
-def _kron_unitary(n, d, gates, mats):
+def _kron_unitary(n, d, gates, mats, mats2=None):
     """Full 2^n x 2^n circuit matrix from numpy products of per-gate
     embeddings (basis index bit q = qubit q), independent of the oracle."""
     N = 1 << n
     std = {W.H: np.array([[1, 1], [1, -1]]) / np.sqrt(2), W.S: np.diag([1, 1j]),
-           W.T: np.diag([1, np.exp(1j * np.pi / 4)])}
+           W.T: np.diag([1, np.exp(1j * np.pi / 4)]), W.X: np.array([[0, 1], [1, 0]])}
     Utot = np.eye(N, dtype=np.complex128)
     for layer in range(d):
         for i, (op, L, q0, q1) in enumerate(gates):
@@ -23,11 +23,16 @@ def _kron_unitary(n, d, gates, mats):
                 continue
             G = np.zeros((N, N), dtype=np.complex128)
             for x in range(N):
-                if op in (W.H, W.S, W.T, W.U):
+                if op in (W.H, W.S, W.T, W.U, W.X):
                     m = mats[i] if op == W.U else std[op]
                     for yb in (0, 1):
                         y = (x & ~(1 << q0)) | (yb << q0)
                         G[y, x] += m[yb, (x >> q0) & 1]
+                elif op == W.U2:
+                    xl = ((x >> q0) & 1) | (((x >> q1) & 1) << 1)
+                    for yl in range(4):
+                        y = (x & ~(1 << q0) & ~(1 << q1)) | ((yl & 1) << q0) | ((yl >> 1) << q1)
+                        G[y, x] += mats2[i][yl, xl]
                 elif op == W.CNOT:
                     y = x ^ ((((x >> q0) & 1)) << q1)
                     G[y, x] = 1
@@ -313,3 +318,98 @@ def test_rejects_bad_matrices():
                 np.array([[0, 1], [1, 1]]) / np.sqrt(2)):
         with pytest.raises(ValueError):
             oracle.u_statevector(1, 1, g, bad[None].astype(np.complex128))
+
+
+
+# ---- X and two-qubit permutations with phases (U2)
+
+def test_two_qubit_gates_against_matrix_products():
+    for n, d, seed in ((2, 4, 1), (3, 6, 3), (4, 6, 8), (5, 5, 11)):
+        g, m2 = W.random_two_qubit_circuit(n, d, seed, frac=0.9)
+        assert np.sum(g[:, 0] == W.U2) >= 1
+        want = _kron_unitary(n, d, g, None, m2)[:, 0]
+        assert np.allclose(oracle.u_statevector(n, d, g, None, mats2=m2), want, atol=1e-12)
+        ps = oracle.u_pathstats(n, d, g, None, mats2=m2) if n * d <= 24 else None
+        if ps is not None:
+            assert np.allclose(ps["U"], want, atol=1e-12)
+
+
+def test_exchange_operator_closed_form():
+    """H on both qubits, then J12(g): amplitudes (1/2) e^{i g/2 (1-2 s1)(1-2 s2)}
+    (the Appendix's energy of the exchange operator)."""
+    gam = 0.83
+    g = np.array([[W.H, 0, 0, -1], [W.H, 0, 1, -1], [W.U2, 1, 0, 1]], dtype=np.int32)
+    m2 = np.zeros((3, 4, 4), dtype=np.complex128)
+    m2[2] = W.exchange_matrix(gam)
+    s1 = np.array([0, 1, 0, 1]); s2 = np.array([0, 0, 1, 1])
+    want = 0.5 * np.exp(0.5j * gam * (1 - 2 * s1) * (1 - 2 * s2))
+    assert np.allclose(oracle.u_statevector(2, 2, g, None, mats2=m2), want, atol=1e-14)
+
+
+def test_u2_as_cnot_and_cz_reproduces_the_clifford_t_sampler():
+    """A U2 holding the CNOT (or CZ) matrix has the same links, colouring and
+    draws as the CNOT (CZ) gate: identical chain states; its phases equal the
+    exact phase classes."""
+    w = np.exp(1j * np.pi * np.arange(8) / 4)
+    for n, d, seed in ((4, 6, 5), (6, 8, 21)):
+        g = W.random_circuit(n, d, seed)
+        gu = g.copy()
+        m2 = np.zeros((len(g), 4, 4), dtype=np.complex128)
+        for i in range(len(g)):
+            if g[i, 0] == W.CNOT:
+                gu[i, 0] = W.U2
+                m2[i] = W.cnot_matrix(True)
+            elif g[i, 0] == W.CZ:
+                gu[i, 0] = W.U2
+                m2[i] = np.diag([1, 1, 1, -1])
+        assert np.sum(gu[:, 0] == W.U2) > 0
+        assert np.array_equal(oracle.u_colour(n, d, gu, None, m2), oracle.colour(n, d, g))
+        J = W.default_J(n, d, g)
+        a = oracle.gibbs(n, d, g, J=J, seed=3, chains=96, sweeps=30)
+        b = oracle.u_gibbs(n, d, gu, None, J=J, seed=3, chains=96, sweeps=30, mats2=m2)
+        assert np.array_equal(a["state"], b["state"])
+        assert np.array_equal(a["cnt"].sum(axis=1), b["cnt"])
+        assert np.allclose(a["cnt"].astype(np.float64) @ w, b["sum"], atol=1e-9)
+
+
+def test_u_colour_matches_the_clifford_t_colouring():
+    for n, d, seed in ((3, 5, 2), (8, 12, 7), (12, 20, 1000)):
+        g = W.random_circuit(n, d, seed)
+        assert np.array_equal(oracle.u_colour(n, d, g), oracle.colour(n, d, g))
+
+
+@pytest.mark.parametrize("n,d,seed", [(3, 5, 4), (4, 4, 9), (2, 6, 13)])
+def test_two_qubit_circuits_converge(n, d, seed):
+    g, m2 = W.random_two_qubit_circuit(n, d, seed, frac=0.9)
+    exact = oracle.u_statevector(n, d, g, None, mats2=m2)
+    ests = []
+    for b in range(16):
+        r = oracle.u_gibbs(n, d, g, None, J=3.0, seed=21, chains=64, chain0=64 * b, sweeps=500,
+                           burn_in=50, mats2=m2)
+        ests.append(oracle.u_estimate(r))
+    ests = np.array(ests)
+    est, se = ests.mean(axis=0), ests.std(axis=0, ddof=1) / 4
+    assert np.all(np.abs(est - exact) <= 5 * np.maximum(se, 1e-3)), (est, exact, se)
+    e = oracle.u_elim(n, d, g, None, seed=5, chains=2048, sweeps=40, mats2=m2)
+    ps = oracle.u_pathstats(n, d, g, None, mats2=m2)
+    Z = 2 ** e["log2z"]
+    se_e = np.sqrt(np.maximum(Z * ps["zabs"] - np.abs(exact) ** 2, 0) / e["samples"])
+    assert np.all(np.abs(oracle.u_estimate(e) - exact) <= 5 * se_e + 1e-12)
+
+
+def test_rejects_unrepresentable_two_qubit_gates():
+    g = np.array([[W.U2, 0, 0, 1]], dtype=np.int32)
+    bad = []
+    # a general (non-permutation) unitary: H on q0 as a 4x4
+    h = np.kron(np.eye(2), np.array([[1, 1], [1, -1]]) / np.sqrt(2))
+    bad.append(h)
+    # output q0 = NOT(x1 XOR x2): y = (1 ^ x1 ^ x2) | x2 << 1
+    m = np.zeros((4, 4), dtype=np.complex128)
+    for x in range(4):
+        x1, x2 = x & 1, x >> 1
+        m[(1 ^ x1 ^ x2) | (x2 << 1), x] = 1
+    bad.append(m)
+    bad.append(2 * W.swap_matrix())  # not unitary
+    for b in bad:
+        with pytest.raises(ValueError):
+            oracle.u_statevector(2, 1, g, None, mats2=b[None])
