@@ -54,7 +54,22 @@ typedef enum {
  *        with the global phase fixed so that <0|G|0> = 1)
  *   CNOT: control q0, target q1, x_t -> x_t XOR x_c  (Appendix, "CNOT Gate")
  *   CZ  = diag(1,1,1,-1) on (q0, q1)  (diagonal two-qubit gate, Appendix)   */
-typedef enum { PB_H = 0, PB_S = 1, PB_T = 2, PB_CNOT = 3, PB_CZ = 4, PB_U = 5 } pb_op;
+typedef enum { PB_H = 0, PB_S = 1, PB_T = 2, PB_CNOT = 3, PB_CZ = 4, PB_U = 5, PB_X = 6,
+               PB_U2 = 7 } pb_op;
+/* PB_X: Pauli X, a deterministic NOT (Appendix, "Pauli-X"): the output is
+ * J-linked to the complement of the input; no phase.  A plain gate (no
+ * matrix; the model stays a Clifford+T-type model).
+ * PB_U2: a two-qubit gate on (q0, q1) with a caller-given 4x4 complex matrix
+ * (pb_compile_g), basis index x = x_{q0} + 2 x_{q1} (the order 00, 10, 01, 11
+ * of Eq. ET2), rows = outputs.  It must be unitary within 1e-9 with exactly
+ * one nonzero entry per column: a permutation of the two bits with phases
+ * (SWAP, iSWAP, controlled phases, the Appendix's exchange operator J12,
+ * CNOT either way).  Every such permutation is affine over GF(2), so each
+ * output bit is J-linked to a copy, a complement, or the XOR of the two
+ * inputs; an output equal to the complement of the XOR is rejected
+ * (PB_EINVAL), as is any gate with a column of more than one nonzero
+ * (general two-qubit tables, Eq. ET2, are not supported).  The phase
+ * arg U(pi(x), x) of the column taken is added to the path. */
 /* PB_U: a general one-qubit gate with a caller-given 2x2 complex matrix U
  * (pb_compile_u; Sec. 2 Eq. EB, e.g. the rotated Hadamard of Eq. HadT).  U
  * must be unitary within 1e-9 (max |(U^dagger U - I)_ij|).  Kinds:
@@ -121,6 +136,14 @@ PB_API int pb_compile(int n_qubits, int n_layers, const pb_gate* gates,
 PB_API int pb_compile_u(int n_qubits, int n_layers, const pb_gate* gates,
                         int n_gates, const double* mats, uint32_t input_bits,
                         double J, pb_model** out);
+
+/* pb_compile_u with a row stride: mats holds mat_stride doubles per gate
+ * row (8: one-qubit matrices only; 32: room for PB_U2's 4x4 matrix,
+ * mats[32 i + 2 (4 y + x)] = Re <y|U|x>, + 1 = Im; a PB_U row uses its first
+ * 8 as in pb_compile_u).  PB_U2 rows need mat_stride >= 32 (PB_EINVAL). */
+PB_API int pb_compile_g(int n_qubits, int n_layers, const pb_gate* gates,
+                        int n_gates, const double* mats, int mat_stride,
+                        uint32_t input_bits, double J, pb_model** out);
 
 typedef struct {
   int32_t n, d;        /* qubits, gate layers                          */

@@ -29,16 +29,19 @@
 
 namespace pb {
 
-// Gate layer L (s_L -> s_{L+1}) in per-chain form: H outputs and CNOT pairs.
+// Gate layer L (s_L -> s_{L+1}) in per-chain form: H outputs, X (NOT)
+// bits and CNOT pairs.
 struct LayerTab {
   uint32_t hmask;
+  uint32_t xmask;
   uint32_t ncnot;
   uint8_t c[16], t[16];
 };
 
-// Deterministic map of a non-H layer: CNOT targets take control XOR target.
+// Deterministic map of a non-H layer: X bits flip, CNOT targets take
+// control XOR target.
 __device__ __forceinline__ uint32_t layer_map(const LayerTab& L, uint32_t x) {
-  uint32_t y = x;
+  uint32_t y = x ^ L.xmask;
   for (uint32_t i = 0; i < L.ncnot; ++i) y ^= ((x >> L.c[i]) & 1u) << L.t[i];
   return y;
 }
@@ -270,6 +273,7 @@ std::vector<LayerTab> layer_table(const pb_model& m) {
   for (const pb_gate& g : m.gates) {
     LayerTab& L = t[g.layer];
     if (g.op == PB_H) L.hmask |= 1u << g.q0;
+    if (g.op == PB_X) L.xmask |= 1u << g.q0;
     if (g.op == PB_CNOT && L.ncnot < 16) {
       L.c[L.ncnot] = (uint8_t)g.q0;
       L.t[L.ncnot] = (uint8_t)g.q1;

@@ -51,7 +51,51 @@ struct Slot {
   bool target = false;  // CNOT target
   int ukind = 0;     // PB_U: kUDiag, kUAnti or kUCoupled
   double a = 0.0, b = 0.0, K = 0.0;  // PB_U magnitudes and coupling
+  int gi = -1;       // gate row
+  int u2o = 0;       // PB_U2: 0 on q0, 1 on q1 (this qubit's output and input index)
 };
+
+// A PB_U2 gate's permutation and the affine map of its output bits:
+// output o = cbit[o] XOR (input 0 if dmask[o] & 1) XOR (input 1 if dmask[o] & 2).
+struct U2Map {
+  int perm[4] = {0, 0, 0, 0};
+  int dmask[2] = {0, 0}, cbit[2] = {0, 0};
+};
+
+// PB_U2 matrix (32 doubles: Re/Im of <y|U|x>, row-major 4x4): unitary within
+// 1e-9, exactly one nonzero per column, no output equal to the complement
+// of the XOR of both inputs.  false if rejected.
+bool classify_u2(const double* m, U2Map& u) {
+  auto re = [&](int y, int x) { return m[2 * (4 * y + x)]; };
+  auto im = [&](int y, int x) { return m[2 * (4 * y + x) + 1]; };
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double sr = 0.0, si = 0.0;  // (U^dagger U)_ij
+      for (int y = 0; y < 4; ++y) {
+        sr += re(y, i) * re(y, j) + im(y, i) * im(y, j);
+        si += re(y, i) * im(y, j) - im(y, i) * re(y, j);
+      }
+      if (!(std::fabs(sr - (i == j ? 1.0 : 0.0)) <= 1e-9) || !(std::fabs(si) <= 1e-9)) return false;
+    }
+  for (int x = 0; x < 4; ++x) {
+    int nz = 0;
+    for (int y = 0; y < 4; ++y)
+      if (re(y, x) != 0.0 || im(y, x) != 0.0) {
+        u.perm[x] = y;
+        ++nz;
+      }
+    if (nz != 1) return false;
+  }
+  for (int o = 0; o < 2; ++o) {
+    const int c = (u.perm[0] >> o) & 1;
+    const int al = ((u.perm[1] >> o) & 1) ^ c, be = ((u.perm[2] >> o) & 1) ^ c;
+    if ((((u.perm[3] >> o) & 1) ^ c) != (al ^ be)) return false;
+    u.dmask[o] = al | (be << 1);
+    u.cbit[o] = c;
+    if (u.dmask[o] == 0 || (u.dmask[o] == 3 && c)) return false;
+  }
+  return true;
+}
 
 enum { kUDiag = 1, kUAnti = 2, kUCoupled = 3 };
 
@@ -144,7 +188,13 @@ PB_API int pb_compile(int n, int d, const pb_gate* gates, int n_gates, uint32_t 
 
 PB_API int pb_compile_u(int n, int d, const pb_gate* gates, int n_gates, const double* mats,
                         uint32_t input_bits, double J, pb_model** out) {
+  return pb_compile_g(n, d, gates, n_gates, mats, 8, input_bits, J, out);
+}
+
+PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const double* mats,
+                        int stride, uint32_t input_bits, double J, pb_model** out) {
   if (!out) return PB_EINVAL;
+  if (stride < 8) return PB_EINVAL;
   *out = nullptr;
   if (n < 1 || n > 32 || d < 1 || d > 64) return PB_ERANGE;
   if (n_gates < 0 || (n_gates > 0 && !gates)) return PB_EINVAL;
@@ -152,19 +202,24 @@ PB_API int pb_compile_u(int n, int d, const pb_gate* gates, int n_gates, const d
   if (n < 32 && (input_bits >> n) != 0) return PB_EINVAL;
 
   std::vector<Slot> slot((size_t)d * n);
+  std::vector<U2Map> u2map((size_t)std::max(n_gates, 1));
   for (int i = 0; i < n_gates; ++i) {
     const pb_gate& g = gates[i];
-    if (g.op < PB_H || g.op > PB_U || g.layer < 0 || g.layer >= d) return PB_EINVAL;
+    if (g.op < PB_H || g.op > PB_U2 || g.layer < 0 || g.layer >= d) return PB_EINVAL;
     if (g.q0 < 0 || g.q0 >= n) return PB_EINVAL;
-    const bool two = g.op == PB_CNOT || g.op == PB_CZ;
+    const bool two = g.op == PB_CNOT || g.op == PB_CZ || g.op == PB_U2;
     if (two && (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0)) return PB_EINVAL;
     Slot& s0 = slot[(size_t)g.layer * n + g.q0];
     if (s0.op != -1) return PB_EINVAL;
     s0.op = g.op;
+    s0.gi = i;
     if (g.op == PB_U) {
       if (!mats) return PB_EINVAL;
-      s0.ukind = classify_u(mats + 8 * (size_t)i, s0.a, s0.b, s0.K);
+      s0.ukind = classify_u(mats + (size_t)stride * i, s0.a, s0.b, s0.K);
       if (s0.ukind < 0) return PB_EINVAL;
+    }
+    if (g.op == PB_U2) {
+      if (!mats || stride < 32 || !classify_u2(mats + (size_t)stride * i, u2map[i])) return PB_EINVAL;
     }
     if (two) {
       Slot& s1 = slot[(size_t)g.layer * n + g.q1];
@@ -173,6 +228,8 @@ PB_API int pb_compile_u(int n, int d, const pb_gate* gates, int n_gates, const d
       s1.op = g.op;
       s1.partner = g.q0;
       s1.target = (g.op == PB_CNOT);
+      s1.gi = i;
+      s1.u2o = 1;
     }
   }
 
@@ -198,7 +255,7 @@ PB_API int pb_compile_u(int n, int d, const pb_gate* gates, int n_gates, const d
   auto is_free = [](const Slot& s) { return s.op == PB_H || (s.op == PB_U && s.ukind == kUCoupled); };
   auto coupled = [](const Slot& s) { return s.op == PB_U && s.ukind == kUCoupled; };
   for (int i = 0; i < n_gates; ++i)
-    if (gates[i].op == PB_U) {
+    if (gates[i].op == PB_U || gates[i].op == PB_U2) {
       m->wgt = true;
       ++m->n_u;
       m->n_coupled += coupled(at(gates[i].layer, gates[i].q0)) ? 1 : 0;
@@ -222,16 +279,44 @@ PB_API int pb_compile_u(int n, int d, const pb_gate* gates, int n_gates, const d
       auto second = [&](const Slot& s, int layer) -> uint16_t {
         if (s.op == PB_CNOT && s.target) return word(layer, s.partner);
         if (s.op == PB_U && s.ukind == kUAnti) return O;
+        if (s.op == PB_X) return O;
         return Z;
       };
-      if (!is_free(prod)) {
+      // qubit of input u (0: q0, 1: q1) of the PB_U2 on this slot
+      auto u2q = [&](const Slot& s, int u) { return ((s.u2o == 0) == (u == 0)) ? q : s.partner; };
+      if (prod.op == PB_U2) {  // own link: this output's affine map
+        const U2Map& um = u2map[prod.gi];
+        const int o = prod.u2o, dm = um.dmask[o];
+        own = true;
+        if (dm == 3) {
+          D.a[m_links] = word(k - 1, u2q(prod, 0));
+          D.b[m_links] = word(k - 1, u2q(prod, 1));
+        } else {
+          D.a[m_links] = word(k - 1, u2q(prod, dm == 1 ? 0 : 1));
+          D.b[m_links] = um.cbit[o] ? O : Z;
+        }
+        ++m_links;
+      } else if (!is_free(prod)) {
         own = true;
         D.a[m_links] = word(k - 1, q);
         D.b[m_links] = second(prod, k - 1);
         ++m_links;
       }
       bool tgt_next = false;
-      if (k < d) {
+      if (k < d && at(k, q).op == PB_U2) {
+        // the outputs of the next layer's PB_U2 whose map reads this input
+        const Slot& cons = at(k, q);
+        const U2Map& um = u2map[cons.gi];
+        const int me = cons.u2o;
+        for (int o = 0; o < 2; ++o) {
+          if (!((um.dmask[o] >> me) & 1)) continue;
+          const int qo = (o == me) ? q : cons.partner;  // the qubit carrying output o
+          D.a[m_links] = word(k + 1, qo);
+          D.b[m_links] = um.dmask[o] == 3 ? word(k, cons.partner) : (um.cbit[o] ? O : Z);
+          ++m_links;
+        }
+        tgt_next = me == 1 && (um.dmask[0] == 3 || um.dmask[1] == 3);
+      } else if (k < d) {
         const Slot& cons = at(k, q);  // gate layer k consumes s_k
         if (!is_free(cons)) {         // the wire's next bit demands s_k[q]
           D.a[m_links] = word(k + 1, q);
@@ -360,11 +445,23 @@ PB_API int pb_compile_u(int n, int d, const pb_gate* gates, int n_gates, const d
   for (int i = 0; i < n_gates; ++i) {
     const pb_gate& g = gates[i];
     if (g.op == PB_H) l2z += 0.5;
+    if (g.op == PB_U2) {  // phase of the column taken: arg U(pi(x), x), x = x_{q0} + 2 x_{q1}
+      UPh P{};
+      const double* mu = mats + (size_t)stride * i;
+      for (int x = 0; x < 4; ++x) {
+        const int y = u2map[i].perm[x];
+        P.ph[x] = fixed_turns(mu[2 * (4 * y + x)], mu[2 * (4 * y + x) + 1]);
+      }
+      P.win = word(g.layer, g.q0);   // bit x_{q0}: the recorder's "x"
+      P.wout = word(g.layer, g.q1);  // bit x_{q1}: the recorder's "y" (ph[2 y + x])
+      m->uph.push_back(P);
+      continue;
+    }
     if (g.op != PB_U) continue;
     const Slot& s = at(g.layer, g.q0);
     if (s.ukind == kUCoupled) l2z += std::log2(s.a + s.b);
     UPh P{};
-    const double* mu = mats + 8 * (size_t)i;
+    const double* mu = mats + (size_t)stride * i;
     for (int y = 0; y < 2; ++y)
       for (int x = 0; x < 2; ++x) P.ph[2 * y + x] = fixed_turns(mu[2 * (2 * y + x)], mu[2 * (2 * y + x) + 1]);
     P.wout = word(g.layer + 1, g.q0);
@@ -392,6 +489,11 @@ PB_API int pb_compile_u(int n, int d, const pb_gate* gates, int n_gates, const d
           ++var;
         } else if (s.op == PB_CNOT && s.target) {
           for (size_t w = 0; w < nxt[q].size(); ++w) nxt[q][w] = wire[q][w] ^ wire[s.partner][w];
+        } else if (s.op == PB_U2) {  // the linear part of this output's affine map
+          const int dm = u2map[s.gi].dmask[s.u2o];
+          const int qa = s.u2o == 0 ? q : s.partner, qb = s.u2o == 0 ? s.partner : q;  // q0, q1
+          for (size_t w = 0; w < nxt[q].size(); ++w)
+            nxt[q][w] = ((dm & 1) ? wire[qa][w] : 0ull) ^ ((dm & 2) ? wire[qb][w] : 0ull);
         }
       }
       wire.swap(nxt);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libpbits.so")
 
 PB_OK, PB_EINVAL, PB_ERANGE, PB_ENOMEM, PB_ECUDA, PB_ETIMEOUT, PB_ESTATE = 0, -1, -2, -3, -4, -5, -6
 PB_GIBBS, PB_LEARNED, PB_ELIM, PB_ELIM_CLAMP = 0, 1, 2, 3
-PB_U = 5
+PB_U, PB_X, PB_U2 = 5, 6, 7
 
 _lib = None
 
@@ -64,6 +64,9 @@ _SIGS = {
                                   ctypes.c_uint32, ctypes.c_double, ctypes.POINTER(_VP)]),
     "pb_compile_u": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(pb_gate), ctypes.c_int,
                                     _VP, ctypes.c_uint32, ctypes.c_double, ctypes.POINTER(_VP)]),
+    "pb_compile_g": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(pb_gate), ctypes.c_int,
+                                    _VP, ctypes.c_int, ctypes.c_uint32, ctypes.c_double,
+                                    ctypes.POINTER(_VP)]),
     "pb_model_info": (ctypes.c_int, [_VP, ctypes.POINTER(pb_model_info_t)]),
     "pb_model_colours": (ctypes.c_int, [_VP, _VP]),
     "pb_model_free": (None, [_VP]),
@@ -169,14 +172,21 @@ def gate_array(gates) -> ctypes.Array:
     return arr, len(g)
 
 
-def mat_array(n_gates: int, mats) -> np.ndarray:
-    """Gate matrices (complex [n_gates, 2, 2], rows = output bit) as the
-    float64 [n_gates, 8] rows of pb_compile_u."""
-    m = np.zeros((max(n_gates, 1), 8), dtype=np.float64)
+def mat_array(n_gates: int, mats, mats2=None) -> np.ndarray:
+    """Gate matrices as the float64 rows of pb_compile_g: one-qubit matrices
+    (complex [n_gates, 2, 2], rows = output bit) in the first 8 entries of a
+    row; with mats2 (complex [n_gates, 4, 4], basis index x_{q0} + 2 x_{q1})
+    32 entries per row, the 4x4 row-major."""
+    w = 32 if mats2 is not None else 8
+    m = np.zeros((max(n_gates, 1), w), dtype=np.float64)
     if mats is not None and n_gates:
         c = np.asarray(mats, dtype=np.complex128).reshape(n_gates, 4)
-        m[:n_gates, 0::2] = c.real
-        m[:n_gates, 1::2] = c.imag
+        m[:n_gates, 0:8:2] = c.real
+        m[:n_gates, 1:8:2] = c.imag
+    if mats2 is not None and n_gates:
+        c2 = np.asarray(mats2, dtype=np.complex128).reshape(n_gates, 16)
+        m[:n_gates, 0::2] = np.where(np.abs(c2) > 0, c2.real, m[:n_gates, 0::2])
+        m[:n_gates, 1::2] = np.where(np.abs(c2) > 0, c2.imag, m[:n_gates, 1::2])
     return np.ascontiguousarray(m)
 
 
@@ -184,17 +194,18 @@ class Model:
     """A compiled circuit (pb_compile; pb_compile_u when `mats` gives the
     matrices of PB_U gates, complex [n_gates, 2, 2])."""
 
-    def __init__(self, n: int, d: int, gates, J: float, input_bits: int = 0, mats=None):
+    def __init__(self, n: int, d: int, gates, J: float, input_bits: int = 0, mats=None,
+                 mats2=None):
         lib = load()
         arr, ng = gate_array(gates)
         h = ctypes.c_void_p()
-        if mats is None:
+        if mats is None and mats2 is None:
             _check(lib.pb_compile(n, d, arr, ng, ctypes.c_uint32(input_bits), ctypes.c_double(J),
                                   ctypes.byref(h)), "pb_compile")
         else:
-            m = mat_array(ng, mats)
-            _check(lib.pb_compile_u(n, d, arr, ng, _ptr(m), ctypes.c_uint32(input_bits),
-                                    ctypes.c_double(J), ctypes.byref(h)), "pb_compile_u")
+            m = mat_array(ng, mats, mats2)
+            _check(lib.pb_compile_g(n, d, arr, ng, _ptr(m), m.shape[1], ctypes.c_uint32(input_bits),
+                                    ctypes.c_double(J), ctypes.byref(h)), "pb_compile_g")
         self._h = h
         self.n, self.d = n, d
 

@@ -173,3 +173,78 @@ def test_rejections():
     bad[i] = np.array([[1, 0], [0, 2]])
     with pytest.raises(pbits.PbError):
         pbits.Model(n, d, g, 3.0, mats=bad)
+
+
+# ---- X and two-qubit permutations with phases (PB_X, PB_U2)
+
+TWO_Q = [(3, 5, 4, 256, 40), (5, 8, 21, 100, 33), (12, 20, 1000, 4096, 6), (32, 64, 3, 40, 3),
+         (6, 1, 4, 33, 7)]
+
+
+@pytest.mark.parametrize("n,d,seed,chains,sweeps", TWO_Q)
+def test_two_qubit_gates_bit_exact_vs_oracle(n, d, seed, chains, sweeps):
+    g, m2 = W.random_two_qubit_circuit(n, d, seed, frac=0.8)
+    alphas = np.arange(16, dtype=np.uint32) if n > 20 else None
+    m = pbits.Model(n, d, g, 3.0, mats2=m2)
+    r = pbits.Run([m], [pbits.RunCfg(seed=13, chains=chains, alphas=alphas)])
+    r.sweeps(sweeps)
+    sums, cnt, valid, samples = r.phase_sums()
+    ref = oracle.u_gibbs(n, d, g, None, J=3.0, seed=13, chains=chains, sweeps=sweeps, alphas=alphas,
+                         mats2=m2)
+    assert np.array_equal(pbits.unslice_state(r.get_state(), chains), ref["state"])
+    assert np.array_equal(cnt, ref["cnt"]) and valid == ref["valid"] and samples == ref["samples"]
+    n_u = int(np.sum(g[:, 0] == W.U2))
+    assert np.all(np.abs(sums - ref["sum"]) <= _sum_tol(cnt, n_u))
+
+
+def test_x_gates_run_on_the_plain_kernel():
+    """X without matrices: a plain model (exact phase classes), identical to
+    the general oracle's sampler."""
+    n, d = 6, 10
+    g, _ = W.random_two_qubit_circuit(n, d, 8, frac=0.0)
+    g = g.copy()
+    for i in range(0, len(g), 3):
+        if g[i, 0] in (W.S, W.T):
+            g[i, 0] = W.X
+    assert np.sum(g[:, 0] == W.X) > 0
+    m = pbits.Model(n, d, g, 3.0)
+    assert m.info()["n_u"] == 0
+    r = pbits.Run([m], [pbits.RunCfg(seed=4, chains=200)])
+    r.sweeps(15)
+    cnt, valid, samples = r.histogram()
+    ref = oracle.u_gibbs(n, d, g, None, J=3.0, seed=4, chains=200, sweeps=15)
+    assert np.array_equal(pbits.unslice_state(r.get_state(), 200), ref["state"])
+    assert np.array_equal(cnt.sum(axis=1), ref["cnt"]) and valid == ref["valid"]
+    w = np.exp(1j * np.pi * np.arange(8) / 4)
+    assert np.allclose(cnt.astype(np.float64) @ w, ref["sum"], atol=1e-9)
+
+
+@pytest.mark.parametrize("n,d,seed,chains,sweeps", [(3, 5, 4, 300, 20), (12, 20, 1000, 4096, 4)])
+def test_two_qubit_gates_exact_sampler(n, d, seed, chains, sweeps):
+    g, m2 = W.random_two_qubit_circuit(n, d, seed, frac=0.8)
+    m = pbits.Model(n, d, g, 3.0, mats2=m2)
+    r = pbits.Run([m], [pbits.RunCfg(seed=41, chains=chains, sampler=pbits.PB_ELIM)])
+    r.sweeps(sweeps)
+    sums, cnt, valid, samples = r.phase_sums()
+    ref = oracle.u_elim(n, d, g, None, seed=41, chains=chains, sweeps=sweeps, mats2=m2)
+    assert samples == valid == ref["samples"]
+    assert np.array_equal(cnt, ref["cnt"])
+    assert np.array_equal(pbits.unslice_state(r.get_state(), chains), ref["state"])
+    assert np.all(np.abs(sums - ref["sum"]) <= _sum_tol(cnt, int(np.sum(g[:, 0] == W.U2))))
+
+
+def test_exchange_operator_circuit_converges():
+    """H on two qubits, the exchange operator J12(g), H again: the Gibbs
+    estimate lies within 5 SE of the state vector."""
+    gam = 1.3
+    g = np.array([[W.H, 0, 0, -1], [W.H, 0, 1, -1], [W.U2, 1, 0, 1], [W.H, 2, 0, -1],
+                  [W.H, 2, 1, -1]], dtype=np.int32)
+    m2 = np.zeros((5, 4, 4), dtype=np.complex128)
+    m2[2] = W.exchange_matrix(gam)
+    exact = oracle.u_statevector(2, 3, g, None, mats2=m2)
+    m = pbits.Model(2, 3, g, 3.0, mats2=m2)
+    r = pbits.Run([m], [pbits.RunCfg(seed=9, chains=4096, burn_in=50, n_batches=32)])
+    r.sweeps(2000)
+    psi, se = r.amplitudes()
+    assert np.all(np.abs(psi - exact) <= 5 * se + 1e-9), (psi, exact, se)
+    assert np.all(se < 0.02)

@@ -100,3 +100,31 @@ def test_slice_roundtrip():
     w = pbits.slice_state(per, 7)
     assert w.shape == (3, 5, 7)
     assert np.array_equal(pbits.unslice_state(w, 70), per)
+
+
+@pytest.mark.parametrize("n,d,seed", [(3, 5, 4), (6, 10, 8), (12, 20, 1000), (5, 8, 21)])
+def test_compile_general_gates_matches_oracle(n, d, seed):
+    """X and two-qubit permutation gates: the colour classes (the sweep
+    order the parity tests rely on) equal the oracle's; info counts them."""
+    g, m2 = W.random_two_qubit_circuit(n, d, seed, frac=0.8)
+    m = pbits.Model(n, d, g, 3.0, mats2=m2)
+    assert np.array_equal(m.colours(), oracle.u_colour(n, d, g, None, m2))
+    inf = m.info()
+    assert inf["n_u"] == int(np.sum(g[:, 0] == W.U2))
+    assert inf["log2z"] == 0.5 * int(np.sum(g[:, 0] == W.H))
+    gu, mu = W.random_general_circuit(n, d, seed, frac_u=0.4)
+    mm = pbits.Model(n, d, gu, 3.0, mats=mu)
+    assert np.array_equal(mm.colours(), oracle.u_colour(n, d, gu, mu))
+
+
+def test_compile_rejects_unrepresentable_two_qubit_gates():
+    g = np.array([[W.U2, 0, 0, 1]], dtype=np.int32)
+    m = np.zeros((4, 4), dtype=np.complex128)
+    for x in range(4):
+        x1, x2 = x & 1, x >> 1
+        m[(1 ^ x1 ^ x2) | (x2 << 1), x] = 1
+    h = np.kron(np.eye(2), np.array([[1, 1], [1, -1]]) / np.sqrt(2))
+    for bad in (m, h, 2 * W.swap_matrix()):
+        with pytest.raises(pbits.PbError):
+            pbits.Model(2, 1, g, 3.0, mats2=bad[None])
+    pbits.Model(2, 1, g, 3.0, mats2=W.swap_matrix()[None])
