@@ -85,9 +85,10 @@ typedef enum { PB_H = 0, PB_S = 1, PB_T = 2, PB_CNOT = 3, PB_CZ = 4, PB_U = 5, P
  * Every PB_U gate adds the phase arg U(s_out, s_in) to the path. */
 
 /* One gate: layer in [0, d) maps s_layer to s_{layer+1}; 1-qubit gates set
- * q1 = -1.  Each qubit appears at most once per layer. */
+ * q1 = -1, gates on fewer than three qubits q2 = -1.  Each qubit appears at
+ * most once per layer. */
 typedef struct {
-  int32_t op, layer, q0, q1;
+  int32_t op, layer, q0, q1, q2;
 } pb_gate;
 
 typedef struct pb_model pb_model;

@@ -61,8 +61,15 @@ def _load():
 
 
 def _gates(gates) -> np.ndarray:
-    g = np.ascontiguousarray(np.asarray(gates, dtype=np.int32).reshape(-1, 4))
-    return g
+    """Gate rows (op, layer, q0, q1[, q2]) as int32 [n, 5] (q2 = -1 when absent)."""
+    a = np.asarray(gates, dtype=np.int32)
+    if a.size == 0:
+        return np.zeros((0, 5), dtype=np.int32)
+    if a.ndim == 1:
+        a = a.reshape(-1, 4)
+    if a.shape[1] == 4:
+        a = np.concatenate([a, -np.ones((len(a), 1), dtype=np.int32)], axis=1)
+    return np.ascontiguousarray(a)
 
 
 def _p(a: np.ndarray):

@@ -66,7 +66,7 @@
 #endif
 
 typedef struct {
-  int32_t op, layer, q0, q1;
+  int32_t op, layer, q0, q1, q2; /* q2: third qubit of a three-qubit gate, else -1 */
 } orc_gate;
 
 enum { G_H = 0, G_S = 1, G_T = 2, G_CNOT = 3, G_CZ = 4, G_U = 5, G_X = 6, G_U2 = 7 };

@@ -50,7 +50,7 @@
 #endif
 
 typedef struct {
-  int32_t op, layer, q0, q1;
+  int32_t op, layer, q0, q1, q2; /* q2: third qubit of a three-qubit gate, else -1 */
 } orc_gate;
 
 enum { ORC_H = 0, ORC_S = 1, ORC_T = 2, ORC_CNOT = 3, ORC_CZ = 4 };

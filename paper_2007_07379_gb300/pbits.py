@@ -30,7 +30,7 @@ class PbError(RuntimeError):
 
 class pb_gate(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int32), ("layer", ctypes.c_int32), ("q0", ctypes.c_int32),
-                ("q1", ctypes.c_int32)]
+                ("q1", ctypes.c_int32), ("q2", ctypes.c_int32)]
 
 
 class pb_model_info_t(ctypes.Structure):
@@ -165,10 +165,17 @@ def _ptr(a: np.ndarray):
 
 
 def gate_array(gates) -> ctypes.Array:
-    g = np.asarray(gates, dtype=np.int32).reshape(-1, 4)
+    """Gate rows (op, layer, q0, q1[, q2]) as pb_gate structs (q2 = -1 when
+    the rows have four columns)."""
+    g = np.asarray(gates, dtype=np.int32)
+    if g.size == 0:
+        g = np.zeros((0, 5), dtype=np.int32)
+    elif g.ndim == 1:
+        g = g.reshape(-1, 4)
     arr = (pb_gate * max(len(g), 1))()
-    for i, (op, layer, q0, q1) in enumerate(g):
-        arr[i] = pb_gate(int(op), int(layer), int(q0), int(q1))
+    for i, row in enumerate(g):
+        q2 = int(row[4]) if len(row) > 4 else -1
+        arr[i] = pb_gate(int(row[0]), int(row[1]), int(row[2]), int(row[3]), q2)
     return arr, len(g)
 
 
