@@ -23,7 +23,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-H, S, T, CNOT, CZ, U, X, U2 = 0, 1, 2, 3, 4, 5, 6, 7
+H, S, T, CNOT, CZ, U, X, U2, CCX = 0, 1, 2, 3, 4, 5, 6, 7, 8
 
 
 def build(force: bool = False) -> str:

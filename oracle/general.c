@@ -21,7 +21,9 @@
  * complemented; an output bit that is the complement of an XOR of both
  * inputs is rejected (the J-penalty links carry at most two words).  Rows
  * with other ops are the Clifford+T gates of oracle.c; their mats entries
- * are ignored.
+ * are ignored.  op = ORC_CCX (8) is the Toffoli gate of the Appendix on
+ * (q0, q1, q2), controls q0 and q1, target q2: x_{q2} XOR= x_{q0} x_{q1},
+ * a deterministic gate whose target output is J-linked to that value.
  *
  * Paths and weights (Eq. U, Eq. path): the weight of a path is the product
  * of its layer elements, complex FP64 here.  Sampling (Eq. weightedS): a path
@@ -69,7 +71,7 @@ typedef struct {
   int32_t op, layer, q0, q1, q2; /* q2: third qubit of a three-qubit gate, else -1 */
 } orc_gate;
 
-enum { G_H = 0, G_S = 1, G_T = 2, G_CNOT = 3, G_CZ = 4, G_U = 5, G_X = 6, G_U2 = 7 };
+enum { G_H = 0, G_S = 1, G_T = 2, G_CNOT = 3, G_CZ = 4, G_U = 5, G_X = 6, G_U2 = 7, G_CCX = 8 };
 enum { K_STD = 0, K_DIAG = 1, K_ANTI = 2, K_COUPLED = 3 };
 enum { MAT = 32 }; /* doubles per gate row of mats */
 
@@ -77,7 +79,9 @@ enum { MAT = 32 }; /* doubles per gate row of mats */
 void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]);
 int orc_thresholds(double J, uint32_t thr[4]);
 
-static int arity(int op) { return (op == G_CNOT || op == G_CZ || op == G_U2) ? 2 : 1; }
+static int arity(int op) {
+  return op == G_CCX ? 3 : (op == G_CNOT || op == G_CZ || op == G_U2) ? 2 : 1;
+}
 static int bitof(uint32_t w, int q) { return (int)((w >> q) & 1u); }
 
 /* ------------------------------------------------------------------------ */
@@ -110,6 +114,9 @@ static void std_entry(int op, int y, int x, double* re, double* im) {
       break;
     case G_X: /* [[0, 1], [1, 0]] */
       if (y != x) *re = 1.0;
+      break;
+    case G_CCX: /* controls q0, q1, target q2 (x = x0 + 2 x1 + 4 x2): x2 ^= x0 x1 */
+      if (y == (x ^ (((x & 1) && (x & 2)) ? 4 : 0))) *re = 1.0;
       break;
   }
 }
@@ -203,7 +210,9 @@ static void gate_elem(const orc_gate* G, const double* mats, int i, int y, int x
 }
 
 static int gidx(const orc_gate* G, uint32_t w) {
-  return arity(G->op) == 2 ? bitof(w, G->q0) + 2 * bitof(w, G->q1) : bitof(w, G->q0);
+  const int a = arity(G->op);
+  if (a == 3) return bitof(w, G->q0) + 2 * bitof(w, G->q1) + 4 * bitof(w, G->q2);
+  return a == 2 ? bitof(w, G->q0) + 2 * bitof(w, G->q1) : bitof(w, G->q0);
 }
 
 typedef struct {
@@ -242,17 +251,25 @@ static int unet_init(unet* u, int n, int d, const orc_gate* g, int ng, const dou
   for (int i = 0; i < n * d; ++i) u->gate_of[i] = -1;
   for (int i = 0; i < ng; ++i) {
     const orc_gate* G = &g[i];
-    if (G->op < 0 || G->op > G_U2 || G->layer < 0 || G->layer >= d || G->q0 < 0 || G->q0 >= n) {
+    if (G->op < 0 || G->op > G_CCX || G->layer < 0 || G->layer >= d || G->q0 < 0 || G->q0 >= n) {
       unet_free(u); return -1;
     }
-    if (arity(G->op) == 2 && (G->q1 < 0 || G->q1 >= n || G->q1 == G->q0)) { unet_free(u); return -1; }
+    if (arity(G->op) >= 2 && (G->q1 < 0 || G->q1 >= n || G->q1 == G->q0)) { unet_free(u); return -1; }
+    if (arity(G->op) == 3 && (G->q2 < 0 || G->q2 >= n || G->q2 == G->q0 || G->q2 == G->q1)) {
+      unet_free(u); return -1;
+    }
     int* s0 = &u->gate_of[G->layer * n + G->q0];
     if (*s0 >= 0) { unet_free(u); return -1; }
     *s0 = i;
-    if (arity(G->op) == 2) {
+    if (arity(G->op) >= 2) {
       int* s1 = &u->gate_of[G->layer * n + G->q1];
       if (*s1 >= 0) { unet_free(u); return -1; }
       *s1 = i;
+    }
+    if (arity(G->op) == 3) {
+      int* s2 = &u->gate_of[G->layer * n + G->q2];
+      if (*s2 >= 0) { unet_free(u); return -1; }
+      *s2 = i;
     }
     u->kind[i] = K_STD;
     if (G->op == G_U) {
@@ -310,18 +327,19 @@ int orc_u_statevector(int n, int d, const orc_gate* g, int ng, const double* mat
     for (int i = 0; i < ng; ++i) {
       const orc_gate* G = &g[i];
       if (G->layer != L) continue;
-      const int two = arity(G->op) == 2, dim = two ? 4 : 2;
-      const uint64_t m0 = 1ull << G->q0, m1 = two ? (1ull << G->q1) : 0;
+      const int ar = arity(G->op), dim = 1 << ar;
+      const uint64_t m0 = 1ull << G->q0, m1 = ar >= 2 ? (1ull << G->q1) : 0,
+                     m2 = ar == 3 ? (1ull << G->q2) : 0;
       memset(nr, 0, N * sizeof(double));
       memset(ni, 0, N * sizeof(double));
       for (uint64_t idx = 0; idx < N; ++idx) {
-        const int x = (int)((idx & m0) ? 1 : 0) + (two && (idx & m1) ? 2 : 0);
-        const uint64_t rest = idx & ~(m0 | m1);
+        const int x = ((idx & m0) ? 1 : 0) + ((idx & m1) ? 2 : 0) + ((idx & m2) ? 4 : 0);
+        const uint64_t rest = idx & ~(m0 | m1 | m2);
         for (int y = 0; y < dim; ++y) {
           double er, ei;
           gate_elem(G, mats, i, y, x, &er, &ei);
           if (er == 0.0 && ei == 0.0) continue;
-          const uint64_t j = rest | ((y & 1) ? m0 : 0) | ((y & 2) ? m1 : 0);
+          const uint64_t j = rest | ((y & 1) ? m0 : 0) | ((y & 2) ? m1 : 0) | ((y & 4) ? m2 : 0);
           nr[j] += er * re[idx] - ei * im[idx];
           ni[j] += er * im[idx] + ei * re[idx];
         }
@@ -419,6 +437,10 @@ static int layer_viol(const unet* u, int L, uint32_t x, uint32_t y) {
         else if (u->kind[gi] == K_ANTI) v += bitof(x, q) == bitof(y, q);
         break;
       case G_X: v += bitof(x, q) == bitof(y, q); break;
+      case G_CCX:
+        if (q == G->q2) v += bitof(y, q) != (bitof(x, q) ^ (bitof(x, G->q0) & bitof(x, G->q1)));
+        else v += bitof(x, q) != bitof(y, q);
+        break;
       case G_U2: {
         const int o = (q == G->q0) ? 0 : 1;
         v += ((u->perm[gi][gidx(G, x)] >> o) & 1) != bitof(y, q);
@@ -461,6 +483,7 @@ static int det_bit(const unet* u, int L, int q, uint32_t x) {
   if (G->op == G_CNOT && q == G->q1) return bitof(x, q) ^ bitof(x, G->q0);
   if (G->op == G_U && u->kind[gi] == K_ANTI) return bitof(x, q) ^ 1;
   if (G->op == G_X) return bitof(x, q) ^ 1;
+  if (G->op == G_CCX && q == G->q2) return bitof(x, q) ^ (bitof(x, G->q0) & bitof(x, G->q1));
   if (G->op == G_U2) return (u->perm[gi][gidx(G, x)] >> ((q == G->q0) ? 0 : 1)) & 1;
   return bitof(x, q);
 }
@@ -493,7 +516,7 @@ static int u_colours(const unet* u, int32_t* colour) {
   int over = 0;
   for (int L = 0; L < d; ++L)
     for (int q = 0; q < n; ++q) {
-      int vars[3], nv = 0, ins[2], ni = 0;
+      int vars[4], nv = 0, ins[3], ni = 0;
       vars[nv++] = L * n + q; /* p-bit (L+1, q) */
       const int gi = u->gate_of[L * n + q];
       if (gi < 0) {
@@ -508,6 +531,10 @@ static int u_colours(const unet* u, int32_t* colour) {
           const int dm = u->dmask[gi][(q == G->q0) ? 0 : 1];
           if (dm & 1) ins[ni++] = G->q0;
           if (dm & 2) ins[ni++] = G->q1;
+        } else if (G->op == G_CCX && q == G->q2) { /* target: t' = t ^ c0 c1 */
+          ins[ni++] = q;
+          ins[ni++] = G->q0;
+          ins[ni++] = G->q1;
         } else {
           ins[ni++] = q;
         }
@@ -541,6 +568,10 @@ static int u_colours(const unet* u, int32_t* colour) {
     for (int e = 0; e < deg[best]; ++e) seen[nb[best * MAXN + e]] |= 1u << c;
   }
   if (over || ncol > 4) {
+    /* the fixed classes separate at most two inputs of one factor: a
+     * Toffoli's four-bit factor needs the computed colouring */
+    for (int i = 0; i < u->ng; ++i)
+      if (u->g[i].op == G_CCX) { free(nb); free(deg); free(seen); return -2; }
     ncol = 4;
     for (int k = 1; k <= d; ++k)
       for (int q = 0; q < n; ++q) {
@@ -552,6 +583,7 @@ static int u_colours(const unet* u, int32_t* colour) {
             if (G->op == G_CNOT && G->q1 == q) second = 1;
             if (G->op == G_U2 && G->q1 == q && (u->dmask[gi][0] == 3 || u->dmask[gi][1] == 3))
               second = 1;
+            if (G->op == G_CCX && G->q2 == q) second = 1;
           }
         }
         colour[(k - 1) * n + q] = 2 * ((k % 2) == 0) + second;

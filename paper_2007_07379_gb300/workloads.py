@@ -22,8 +22,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-H, S, T, CNOT, CZ, U, X, U2 = 0, 1, 2, 3, 4, 5, 6, 7
-GATE_NAMES = {H: "H", S: "S", T: "T", CNOT: "CNOT", CZ: "CZ", U: "U", X: "X", U2: "U2"}
+H, S, T, CNOT, CZ, U, X, U2, CCX = 0, 1, 2, 3, 4, 5, 6, 7, 8
+GATE_NAMES = {H: "H", S: "S", T: "T", CNOT: "CNOT", CZ: "CZ", U: "U", X: "X", U2: "U2", CCX: "CCX"}
 _MASK64 = (1 << 64) - 1
 
 
@@ -170,6 +170,28 @@ def random_two_qubit_circuit(n: int, d: int, seed: int, frac: float = 0.5):
         elif g[i, 0] in (H, S, T) and unif() < frac / 4:
             g[i, 0] = X
     return g, mats2
+
+
+def random_ccx_circuit(n: int, d: int, seed: int, frac: float = 0.5) -> np.ndarray:
+    """random_circuit(n, d, seed) where, in each layer with probability frac,
+    three qubits that carry one-qubit gates there are replaced by a Toffoli
+    (controls the first two, target the third, in the layer's random
+    order).  int32[n_gates, 5] rows (op, layer, q0, q1, q2)."""
+    g = random_circuit(n, d, seed)
+    rng = SplitMix64(seed ^ 0xCC0)
+    rows = []
+    for layer in range(d):
+        lg = [tuple(int(v) for v in r) + (-1,) for r in g if r[1] == layer]
+        ones = [r for r in lg if r[0] in (H, S, T)]
+        if len(ones) >= 3 and (rng.next() >> 11) * (2.0 ** -53) < frac:
+            pick = []
+            pool = list(ones)
+            for _ in range(3):
+                pick.append(pool.pop(rng.below(len(pool))))
+            lg = [r for r in lg if r not in pick]
+            lg.append((CCX, layer, pick[0][2], pick[1][2], pick[2][2]))
+        rows.extend(lg)
+    return np.asarray(rows, dtype=np.int32).reshape(-1, 5)
 
 
 def rotated_h_chain(d: int, theta: float):

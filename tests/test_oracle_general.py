@@ -413,3 +413,78 @@ def test_rejects_unrepresentable_two_qubit_gates():
     for b in bad:
         with pytest.raises(ValueError):
             oracle.u_statevector(2, 1, g, None, mats2=b[None])
+
+
+
+# ---- the Toffoli gate (CCX)
+
+def _ccx_unitary(n, d, gates):
+    """Circuit matrix with the CCX gates (rows (op, layer, q0, q1, q2))
+    embedded directly; other gates through _kron_unitary, layer by layer."""
+    N = 1 << n
+    Utot = np.eye(N, dtype=np.complex128)
+    for layer in range(d):
+        lg = [r for r in gates if r[1] == layer]
+        rest = np.array([r[:4] for r in lg if r[0] != W.CCX], dtype=np.int32).reshape(-1, 4).copy()
+        rest[:, 1] = 0
+        Utot = _kron_unitary(n, 1, rest, None) @ Utot
+        for r in lg:
+            if r[0] != W.CCX:
+                continue
+            G = np.zeros((N, N))
+            for x in range(N):
+                y = x ^ ((((x >> r[2]) & 1) & ((x >> r[3]) & 1)) << r[4])
+                G[y, x] = 1
+            Utot = G @ Utot
+    return Utot
+
+
+def test_ccx_truth_table():
+    g = np.array([[W.CCX, 0, 0, 1, 2]], dtype=np.int32)
+    for beta in range(8):
+        want = np.zeros(8)
+        want[beta ^ (4 if (beta & 1) and (beta & 2) else 0)] = 1
+        assert np.allclose(oracle.u_statevector(3, 1, g, None, beta=beta), want)
+
+
+@pytest.mark.parametrize("n,d,seed", [(3, 4, 1), (4, 5, 2), (5, 6, 7), (6, 4, 11)])
+def test_ccx_circuits_against_matrix_products(n, d, seed):
+    g = W.random_ccx_circuit(n, d, seed, frac=0.9)
+    assert np.sum(g[:, 0] == W.CCX) >= 1
+    want = _ccx_unitary(n, d, g)[:, 0]
+    assert np.allclose(oracle.u_statevector(n, d, g, None), want, atol=1e-12)
+    if n * d <= 24:
+        assert np.allclose(oracle.u_pathstats(n, d, g, None)["U"], want, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,d,seed", [(4, 5, 2), (5, 6, 7), (8, 10, 3), (12, 20, 1000)])
+def test_ccx_colouring_is_proper(n, d, seed):
+    """No two p-bits of one colour class share a factor (a Toffoli target's
+    factor holds four p-bits)."""
+    g = W.random_ccx_circuit(n, d, seed, frac=0.7)
+    col = oracle.u_colour(n, d, g)
+    for r in g:
+        if r[0] != W.CCX or r[1] == 0:
+            continue
+        k = r[1]  # p-bits (k, q) are row k - 1
+        fac = [col[k, r[4]], col[k - 1, r[4]], col[k - 1, r[2]], col[k - 1, r[3]]]
+        assert len(set(fac)) == 4
+
+
+@pytest.mark.parametrize("n,d,seed", [(3, 4, 1), (4, 5, 2), (5, 4, 9)])
+def test_ccx_circuits_converge(n, d, seed):
+    g = W.random_ccx_circuit(n, d, seed, frac=0.9)
+    exact = oracle.u_statevector(n, d, g, None)
+    ests = []
+    for b in range(16):
+        r = oracle.u_gibbs(n, d, g, None, J=3.0, seed=31, chains=64, chain0=64 * b, sweeps=500,
+                           burn_in=50)
+        ests.append(oracle.u_estimate(r))
+    ests = np.array(ests)
+    est, se = ests.mean(axis=0), ests.std(axis=0, ddof=1) / 4
+    assert np.all(np.abs(est - exact) <= 5 * np.maximum(se, 1e-3)), (est, exact, se)
+    e = oracle.u_elim(n, d, g, None, seed=5, chains=2048, sweeps=40)
+    ps = oracle.u_pathstats(n, d, g, None)
+    Z = 2 ** e["log2z"]
+    se_e = np.sqrt(np.maximum(Z * ps["zabs"] - np.abs(exact) ** 2, 0) / e["samples"])
+    assert np.all(np.abs(oracle.u_estimate(e) - exact) <= 5 * se_e + 1e-12)
