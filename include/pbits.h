@@ -55,7 +55,16 @@ typedef enum {
  *   CNOT: control q0, target q1, x_t -> x_t XOR x_c  (Appendix, "CNOT Gate")
  *   CZ  = diag(1,1,1,-1) on (q0, q1)  (diagonal two-qubit gate, Appendix)   */
 typedef enum { PB_H = 0, PB_S = 1, PB_T = 2, PB_CNOT = 3, PB_CZ = 4, PB_U = 5, PB_X = 6,
-               PB_U2 = 7 } pb_op;
+               PB_U2 = 7, PB_CCX = 8 } pb_op;
+/* PB_CCX: the Toffoli gate (Appendix, "CCNOT"): controls q0, q1, target q2,
+ * s_{q2} -> s_{q2} XOR (s_{q0} AND s_{q1}); every output bit is J-linked to
+ * its deterministic value.  The target's link holds an AND, and through it
+ * a control's demanded value depends on the other control, so the p-bits
+ * around a Toffoli take the general-gate kernels (per-lane link counts);
+ * the four bits of the target's factor need four distinct colour classes
+ * (PB_ERANGE when the colouring needs more than four).  Not with
+ * PB_ELIM_CLAMP (the wires are not affine), the learned proposal or the
+ * no-allocation run (PB_EINVAL); pb_model_info's rank reads -1. */
 /* PB_X: Pauli X, a deterministic NOT (Appendix, "Pauli-X"): the output is
  * J-linked to the complement of the input; no phase.  A plain gate (no
  * matrix; the model stays a Clifford+T-type model).

@@ -24,7 +24,8 @@ __host__ __device__ inline int n_words(int n, int d) { return (d + 1) * n + 2; }
 struct Desc {
   uint16_t dst;   // word index of the p-bit (k*n + q)
   uint8_t mflag;  // bits 0-1: m (links), bit 2: link 0 is the p-bit's own link,
-                  // bit 3: coupled (Metropolis acceptance, see Cpl)
+                  // bit 3: coupled (Metropolis acceptance, see Cpl),
+                  // bit 4: general links (a Toffoli's, see GLink)
   uint8_t pair;   // threshold pair: 0 (t0,t0) 1 (t1,t1) 2 (t2,t0) 3 (t3,t1)
   uint16_t a[3];
   uint16_t b[3];
@@ -32,13 +33,14 @@ struct Desc {
 static_assert(sizeof(Desc) == 16, "Desc must be 16 bytes");
 
 // Record term of one p-bit (16 bytes): violation word W[vd]^W[va]^W[vb]
-// (all ZERO when the p-bit has no own link) and phase term
-// w * (W[pa] & W[pb]) with w in {0, 1, 2, 4} units of pi/4.
+// (all ZERO when the p-bit has no own link; general-gate runs read
+// W[vd]^W[va]^(W[vb]&W[vc]), vc = ONES except on a Toffoli target) and phase
+// term w * (W[pa] & W[pb]) with w in {0, 1, 2, 4} units of pi/4.
 struct Rec {
   uint16_t vd, va, vb;
   uint16_t pa, pb;
   uint16_t w;
-  uint16_t pad[2];
+  uint16_t vc, pad;
 };
 static_assert(sizeof(Rec) == 16, "Rec must be 16 bytes");
 
@@ -57,6 +59,18 @@ struct Cpl {
   uint32_t flags;
 };
 static_assert(sizeof(Cpl) == 32, "Cpl must be 32 bytes");
+
+// General links of a p-bit next to a Toffoli gate (32 bytes, by p): link i
+// demands r_i = W[a] ^ (W[b] & W[c]) and counts where W[e] is set (e = ZERO:
+// no link; a plain link has c = e = ONES; a control's link through the
+// target is active where the other control is 1).  Link 0 is the own link
+// when the p-bit has one (its value for the initial path and the exact
+// sampler).
+struct GLink {
+  uint16_t a[3], b[3], c[3], e[3];
+  uint32_t pad[2];
+};
+static_assert(sizeof(GLink) == 32, "GLink must be 32 bytes");
 
 // Phase of one general gate (32 bytes): ph[2 y + x] = arg U_yx in units of
 // 2^-32 turn, y = bit W[wout], x = bit W[win] of the chain.
@@ -114,6 +128,7 @@ struct RunModelDev {
   // count (u64), unused...} instead of 8 phase-class counters.
   const Cpl* cpl;
   const UPh* uph;
+  const GLink* glk;        // models with Toffoli gates, else nullptr
 };
 
 // Workspace header at offset 0.
@@ -159,6 +174,8 @@ struct pb_model {
   double log2z = 0.0;
   std::vector<pb::Cpl> cpl;           // by p (wgt only)
   std::vector<pb::UPh> uph;           // one per PB_U gate
+  int n_ccx = 0;                      // Toffoli gates
+  std::vector<pb::GLink> glk;         // by p (Toffoli models only)
 };
 
 // Proposal network (host side of pb_mlp): fp32 master weights, Adam state,

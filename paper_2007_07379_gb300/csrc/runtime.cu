@@ -52,7 +52,8 @@ struct Slot {
   int ukind = 0;     // PB_U: kUDiag, kUAnti or kUCoupled
   double a = 0.0, b = 0.0, K = 0.0;  // PB_U magnitudes and coupling
   int gi = -1;       // gate row
-  int u2o = 0;       // PB_U2: 0 on q0, 1 on q1 (this qubit's output and input index)
+  int u2o = 0;       // PB_U2: 0 on q0, 1 on q1 (this qubit's output and input index);
+                     // PB_CCX: 0, 1 on the controls q0, q1, 2 on the target q2
 };
 
 // A PB_U2 gate's permutation and the affine map of its output bits:
@@ -205,10 +206,18 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
   std::vector<U2Map> u2map((size_t)std::max(n_gates, 1));
   for (int i = 0; i < n_gates; ++i) {
     const pb_gate& g = gates[i];
-    if (g.op < PB_H || g.op > PB_U2 || g.layer < 0 || g.layer >= d) return PB_EINVAL;
+    if (g.op < PB_H || g.op > PB_CCX || g.layer < 0 || g.layer >= d) return PB_EINVAL;
     if (g.q0 < 0 || g.q0 >= n) return PB_EINVAL;
-    const bool two = g.op == PB_CNOT || g.op == PB_CZ || g.op == PB_U2;
+    const bool two = g.op == PB_CNOT || g.op == PB_CZ || g.op == PB_U2 || g.op == PB_CCX;
     if (two && (g.q1 < 0 || g.q1 >= n || g.q1 == g.q0)) return PB_EINVAL;
+    if (g.op == PB_CCX) {
+      if (g.q2 < 0 || g.q2 >= n || g.q2 == g.q0 || g.q2 == g.q1) return PB_EINVAL;
+      Slot& s2 = slot[(size_t)g.layer * n + g.q2];
+      if (s2.op != -1) return PB_EINVAL;
+      s2.op = g.op;
+      s2.gi = i;
+      s2.u2o = 2;
+    }
     Slot& s0 = slot[(size_t)g.layer * n + g.q0];
     if (s0.op != -1) return PB_EINVAL;
     s0.op = g.op;
@@ -254,12 +263,18 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
   // link: the CNOT control (target), ONES (anti-diagonal PB_U: NOT), ZERO
   auto is_free = [](const Slot& s) { return s.op == PB_H || (s.op == PB_U && s.ukind == kUCoupled); };
   auto coupled = [](const Slot& s) { return s.op == PB_U && s.ukind == kUCoupled; };
-  for (int i = 0; i < n_gates; ++i)
+  for (int i = 0; i < n_gates; ++i) {
     if (gates[i].op == PB_U || gates[i].op == PB_U2) {
       m->wgt = true;
       ++m->n_u;
       m->n_coupled += coupled(at(gates[i].layer, gates[i].q0)) ? 1 : 0;
     }
+    if (gates[i].op == PB_CCX) {  // general links: the general-gate kernels
+      m->wgt = true;
+      ++m->n_ccx;
+    }
+  }
+  if (m->n_ccx) m->glk.assign((size_t)n * d, GLink{});
 
   const int npb = n * d;
   std::vector<Desc> by_p(npb);
@@ -331,6 +346,43 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
         tgt_next = cons.op == PB_CNOT && cons.target;
       }
       D.mflag = (uint8_t)(m_links | (own ? 4 : 0));
+      // Toffoli: every link of its target output and of its inputs in the
+      // general form r = W[a] ^ (W[b] & W[c]), counted where W[e]
+      const bool ccx_out = prod.op == PB_CCX && prod.u2o == 2;
+      const bool ccx_in = k < d && at(k, q).op == PB_CCX;
+      bool ccx_target_out = false;
+      if (ccx_out || ccx_in) {
+        GLink G{};
+        for (int l = 0; l < 3; ++l) G.a[l] = G.b[l] = G.c[l] = G.e[l] = Z;
+        int nl = 0;
+        auto add = [&](uint16_t a, uint16_t b, uint16_t c, uint16_t e) {
+          G.a[nl] = a; G.b[nl] = b; G.c[nl] = c; G.e[nl] = e;
+          ++nl;
+        };
+        if (ccx_out) {  // own: t' = t ^ (c0 & c1)
+          const pb_gate& tg = gates[prod.gi];
+          add(word(k - 1, tg.q2), word(k - 1, tg.q0), word(k - 1, tg.q1), O);
+          ccx_target_out = true;
+        } else if (own) {
+          add(D.a[0], D.b[0], O, O);
+        }
+        if (ccx_in) {
+          const Slot& cons = at(k, q);
+          const pb_gate& tg = gates[cons.gi];
+          if (cons.u2o == 2) {  // target input: t = t' ^ (c0 & c1)
+            add(word(k + 1, tg.q2), word(k, tg.q0), word(k, tg.q1), O);
+          } else {              // a control: its copy, and t' ^ t where the other control is 1
+            add(word(k + 1, q), Z, O, O);
+            add(word(k + 1, tg.q2), word(k, tg.q2), O, word(k, cons.u2o == 0 ? tg.q1 : tg.q0));
+          }
+        } else {
+          for (int l = own ? 1 : 0; l < m_links; ++l) add(D.a[l], D.b[l], O, O);
+        }
+        m->glk[(size_t)(k - 1) * n + q] = G;
+        D.mflag |= 0x10;
+        own = own || ccx_out;
+        tgt_next = ccx_in && at(k, q).u2o == 2;
+      }
       if (m->wgt) {  // couplings of the p-bit (Metropolis acceptance table)
         Cpl C{};
         C.win = C.wout = D.dst;
@@ -362,9 +414,17 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
 
       Rec R{};
       R.vd = R.va = R.vb = Z;
+      R.vc = O;
       R.pa = R.pb = Z;
       R.w = 0;
-      if (own) {
+      if (ccx_target_out) {  // violation t' ^ t ^ (c0 & c1); the initial value from link 0
+        const GLink& G = m->glk[(size_t)(k - 1) * n + q];
+        R.vd = D.dst;
+        R.va = G.a[0];
+        R.vb = G.b[0];
+        R.vc = G.c[0];
+        m->init[p] = 0xFFFFFFFEu;
+      } else if (own) {
         R.vd = D.dst;
         R.va = D.a[0];
         R.vb = D.b[0];
@@ -396,6 +456,13 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
     };
     for (int p = 0; p < npb; ++p) {
       const pb::Desc& D = by_p[p];
+      if (D.mflag & 0x10) {  // general links: every word of every link
+        const GLink& G = m->glk[p];
+        for (int l = 0; l < 3; ++l)
+          for (int w : {(int)G.a[l], (int)G.b[l], (int)G.c[l], (int)G.e[l]})
+            if (w >= n && w < (d + 1) * n && w - n != p) join(p, w - n);
+        continue;
+      }
       for (int l = 0; l < (D.mflag & 3); ++l)
         for (int w : {(int)D.a[l], (int)D.b[l]})
           if (w >= n && w < (d + 1) * n && w - n != p) join(p, w - n);
@@ -429,6 +496,8 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
     }
     if (ncol <= 4)
       for (int p = 0; p < npb; ++p) m->colour[p] = col[p];
+    else if (m->n_ccx)  // the fixed classes cannot separate a Toffoli's four-bit factor
+      return PB_ERANGE;
   }
 
   // colour-ordered descriptors
@@ -475,7 +544,9 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
   for (int i = 0; i < n_gates; ++i) h += gates[i].op == PB_H;
   m->h = h;
   m->M = npb - h - m->n_coupled;
-  {
+  if (m->n_ccx) {
+    m->rank = -1;  // a Toffoli makes the wires non-affine in the free outputs
+  } else {
     const int nvar = h + m->n_coupled;
     std::vector<std::vector<uint64_t>> wire(n, std::vector<uint64_t>((nvar + 63) / 64 + 1, 0));
     int var = 0;
@@ -542,7 +613,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 
 struct ModelSlots {
   size_t model_dev, desc, rec, init, state, hist, valid, samples, alpha_sorted, alpha_slot, amp,
-      clamp, cpl, uph;
+      clamp, cpl, uph, glk;
   uint32_t bins, groups, n_batches;
   int clamp_mw;  // mask words per p-bit of the clamp table (0: not clamped)
 };
@@ -646,7 +717,7 @@ int check_cfg(const pb_model* m, const pb_run_cfg& c) {
   if (c.sampler != PB_GIBBS && c.sampler != PB_ELIM && c.sampler != PB_ELIM_CLAMP) return PB_EINVAL;
   if (c.sampler == PB_ELIM_CLAMP && (c.alphas == nullptr || c.n_alphas != 1)) return PB_EINVAL;
   // clamping assumes uniform free outputs: no coupled general gate
-  if (c.sampler == PB_ELIM_CLAMP && m->n_coupled > 0) return PB_EINVAL;
+  if (c.sampler == PB_ELIM_CLAMP && (m->n_coupled > 0 || m->n_ccx > 0)) return PB_EINVAL;
   if (c.alphas == nullptr) {
     if (c.n_alphas != 0) return PB_EINVAL;
     if (m->n > 22) return PB_ERANGE;
@@ -704,6 +775,7 @@ int plan(pb_model* const* models, const pb_run_cfg* cfgs, int nm, Layout& L) {
     s.clamp = take(npb * (size_t)(1 + s.clamp_mw) * 4 * (s.clamp_mw > 0 ? 1 : 0));
     s.cpl = take(m->wgt ? npb * sizeof(Cpl) : 0);
     s.uph = take(m->uph.size() * sizeof(UPh));
+    s.glk = take(m->glk.size() * sizeof(GLink));
   }
   L.work = take((size_t)total_groups * 4);
   L.total = align_up(off, 256);
@@ -901,6 +973,8 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
     if (m.wgt &&
         ((e = cudaMemcpyAsync(ws + s.cpl, m.cpl.data(), npb * sizeof(Cpl), cudaMemcpyHostToDevice, st)) ||
          (!m.uph.empty() && (e = cudaMemcpyAsync(ws + s.uph, m.uph.data(), m.uph.size() * sizeof(UPh),
+                                                 cudaMemcpyHostToDevice, st))) ||
+         (!m.glk.empty() && (e = cudaMemcpyAsync(ws + s.glk, m.glk.data(), m.glk.size() * sizeof(GLink),
                                                  cudaMemcpyHostToDevice, st)))))
       return PB_ECUDA;
     if (c.alphas) {
@@ -947,6 +1021,7 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
     if (m.wgt) {
       d.cpl = reinterpret_cast<const Cpl*>(ws + s.cpl);
       d.uph = reinterpret_cast<const UPh*>(ws + s.uph);
+      if (!m.glk.empty()) d.glk = reinterpret_cast<const GLink*>(ws + s.glk);
     }
     if (c.sampler == PB_ELIM_CLAMP) {
       ClampTable t = build_clamp(m, c.alphas[0], s.clamp_mw);

@@ -211,6 +211,54 @@ __device__ __noinline__ uint32_t couple_accept(const uint32_t* W, const Cpl* cpl
   return couple_accept_body(C, W[C.win], W[C.wout], old, prop, pre, g, sweep, p, k0, k1);
 }
 
+// Heat-bath draw of a p-bit with general links (next to a Toffoli gate): per
+// lane the active links that demand 0 (z) and 1 (o) are counted in two-bit
+// bit-sliced counters, v = z - o, and the new value is [v < 0] XOR
+// [u < thr[|v|]] -- the plain rule with the link count varying by lane --
+// from the same planes (the kPre precomputed Philox outputs, then further
+// ones of the same counter).  Out of line: only Toffoli-adjacent p-bits.
+__device__ __noinline__ uint32_t glink_heat_bath(const uint32_t* W, const GLink* gp,
+                                                 const uint4* rp, uint32_t thr0, uint32_t thr1,
+                                                 uint32_t thr2, uint32_t thr3, uint32_t g,
+                                                 uint32_t sweep, uint32_t pidx, uint32_t k0,
+                                                 uint32_t k1) {
+  const GLink G = *gp;
+  uint32_t z0 = 0u, z1 = 0u, o0 = 0u, o1 = 0u;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const uint32_t act = W[G.e[l]];
+    const uint32_t r = W[G.a[l]] ^ (W[G.b[l]] & W[G.c[l]]);
+    const uint32_t one = act & r, zero = act & ~r;
+    o1 |= o0 & one;  // counts stay <= 3: no carry out of bit 1
+    o0 ^= one;
+    z1 |= z0 & zero;
+    z0 ^= zero;
+  }
+  const uint32_t neg = (o1 & ~z1) | (~(o1 ^ z1) & o0 & ~z0);  // o > z
+  const uint32_t v0 = ~(o1 ^ z1) & ~(o0 ^ z0);                 // |v| = 0
+  const uint32_t ozero = ~o1 & ~o0, zzero = ~z1 & ~z0;
+  const uint32_t ge2 = (ozero & z1) | (zzero & o1);            // |v| >= 2
+  const uint32_t v3 = (ozero & z1 & z0) | (zzero & o1 & o0);
+  const uint32_t v2 = ge2 & ~v3, v1 = ~v0 & ~ge2;
+  uint32_t lt = 0u, eq = ~0u;
+#pragma unroll 1
+  for (uint32_t grp = 0; grp < 8u && eq != 0u; ++grp) {
+    const uint4 r = grp < (uint32_t)kPre ? rp[grp] : philox_cold(make_uint4(g, sweep, pidx, grp), k0, k1);
+    const uint32_t R[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (uint32_t w = 0; w < 4u; ++w) {
+      const uint32_t j = grp * 4u + w;
+      const uint32_t T = (v0 & (uint32_t)((int32_t)(thr0 << j) >> 31)) |
+                         (v1 & (uint32_t)((int32_t)(thr1 << j) >> 31)) |
+                         (v2 & (uint32_t)((int32_t)(thr2 << j) >> 31)) |
+                         (v3 & (uint32_t)((int32_t)(thr3 << j) >> 31));
+      lt |= eq & ~R[w] & T;
+      eq &= ~(R[w] ^ T);
+    }
+  }
+  return neg ^ lt;
+}
+
 __device__ __forceinline__ void add3(uint32_t& f0, uint32_t& f1, uint32_t& f2, uint32_t x0,
                                      uint32_t x1, uint32_t x2) {
   const uint32_t c0 = f0 & x0;
@@ -329,11 +377,15 @@ struct Recorder {
     }
   }
 
+  // ANDV: general-gate runs, where a Toffoli target's term is
+  // W[vd] ^ W[va] ^ (W[vb] & W[vc]) (vc = ONES elsewhere).
+  template <bool ANDV = false>
   __device__ void read(const uint32_t* S, const Rec* srec, int lo, int hi, int lane) {
 #pragma unroll 2
     for (int i = lo + lane; i < hi; i += 32) {
       const Rec R = srec[i];
-      viol |= S[R.vd] ^ S[R.va] ^ S[R.vb];
+      if constexpr (ANDV) viol |= S[R.vd] ^ S[R.va] ^ (S[R.vb] & S[R.vc]);
+      else viol |= S[R.vd] ^ S[R.va] ^ S[R.vb];
       const uint32_t x = S[R.pa] & S[R.pb];
       add3(f0, f1, f2, (R.w & 1) ? x : 0u, (R.w & 2) ? x : 0u, (R.w & 4) ? x : 0u);
     }
@@ -474,7 +526,7 @@ __device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc
                                             int hi, int stride, int n, FastThr fast, uint32_t thr0,
                                             uint32_t thr1, uint32_t thr2, uint32_t thr3,
                                             uint32_t g, uint32_t sweep, uint32_t k0, uint32_t k1,
-                                            const Cpl* cpl) {
+                                            const Cpl* cpl, const GLink* glk) {
   for (int i = lo + first; i < hi; i += stride) {
     Desc D = sdesc[i];
     if (D.mflag & 0x80) continue;
@@ -488,9 +540,12 @@ __device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc
     const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
     const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
     const uint32_t pidx = (uint32_t)(D.dst - n) | (kTagSweep << 16);
-    uint32_t v = heat_bath_links(r0, r1, r2, m, m == 0 ? ~0u : 0u, m == 1 ? ~0u : 0u,
-                                 m == 2 ? ~0u : 0u, m == 3 ? ~0u : 0u, R, fast, thr0, thr1,
-                                 thr2, thr3, g, sweep, pidx, k0, k1);
+    uint32_t v = (glk && (D.mflag & 0x10))
+                     ? glink_heat_bath(W, glk + (D.dst - n), rp, thr0, thr1, thr2, thr3, g, sweep,
+                                       pidx, k0, k1)
+                     : heat_bath_links(r0, r1, r2, m, m == 0 ? ~0u : 0u, m == 1 ? ~0u : 0u,
+                                       m == 2 ? ~0u : 0u, m == 3 ? ~0u : 0u, R, fast, thr0, thr1,
+                                       thr2, thr3, g, sweep, pidx, k0, k1);
     if (cpl && (D.mflag & 8)) {
       const uint32_t p = (uint32_t)(D.dst - n);
       v = couple_accept(W, cpl + p, W[D.dst], v, nullptr, g, sweep, p, k0, k1);
@@ -508,16 +563,16 @@ __device__ __noinline__ void redraw_extra(uint32_t* W, uint32_t* S, const Desc* 
                                           uint32_t thr2, uint32_t thr3, uint32_t g, uint32_t sweep,
                                           uint32_t k0, uint32_t k1) {
   redraw_body(W, S, sdesc, cur, lo, first, hi, stride, n, fast, thr0, thr1, thr2, thr3, g, sweep,
-              k0, k1, nullptr);
+              k0, k1, nullptr, nullptr);
 }
 __device__ __noinline__ void redraw_extra_coupled(uint32_t* W, uint32_t* S, const Desc* sdesc,
                                                   const uint4* cur, int lo, int first, int hi,
                                                   int stride, int n, FastThr fast, uint32_t thr0,
                                                   uint32_t thr1, uint32_t thr2, uint32_t thr3,
                                                   uint32_t g, uint32_t sweep, uint32_t k0,
-                                                  uint32_t k1, const Cpl* cpl) {
+                                                  uint32_t k1, const Cpl* cpl, const GLink* glk) {
   redraw_body(W, S, sdesc, cur, lo, first, hi, stride, n, fast, thr0, thr1, thr2, thr3, g, sweep,
-              k0, k1, cpl);
+              k0, k1, cpl, glk);
 }
 
 // Runs `n_sweeps` sweeps (absolute indices sweep0...) of one chain group.
@@ -581,9 +636,10 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     }
     sdesc[i] = D;
     Rec R = rm.rec[i];
-    if (R.vd >= nw || R.va >= nw || R.vb >= nw || R.pa >= nw || R.pb >= nw) {
+    if (R.vd >= nw || R.va >= nw || R.vb >= nw || R.pa >= nw || R.pb >= nw || (WGT && R.vc >= nw)) {
       set_status(hdr, PB_EINVAL);
       R.vd = R.va = R.vb = R.pa = R.pb = (uint16_t)zero_idx(n, d);
+      R.vc = (uint16_t)ones_idx(n, d);
       R.w = 0;
     }
     srec[i] = R;
@@ -600,6 +656,12 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     for (int i = tid; i < npb; i += T) bad |= (rm.cpl[i].win >= nw || rm.cpl[i].wout >= nw) ? 1 : 0;
 #pragma unroll 1
     for (int i = tid; i < nug; i += T) bad |= (rm.uph[i].win >= nw || rm.uph[i].wout >= nw) ? 1 : 0;
+    if (rm.glk)
+#pragma unroll 1
+      for (int i = tid; i < npb; i += T)
+        for (int l = 0; l < 3; ++l)
+          bad |= (rm.glk[i].a[l] >= nw || rm.glk[i].b[l] >= nw || rm.glk[i].c[l] >= nw ||
+                  rm.glk[i].e[l] >= nw) ? 1 : 0;
     if (__syncthreads_or(bad)) {
       if (tid == 0) set_status(hdr, PB_EINVAL);
       return;
@@ -641,7 +703,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       for (int l = 0; l < 3; ++l) { E.la[l] = 4u * D.a[l]; E.lb[l] = 4u * D.b[l]; }
       E.dst = 4u * D.dst;
       E.m = (uint32_t)m;
-      if (WGT && (D.mflag & 8)) E.m |= 0x100u;  // coupled: Metropolis acceptance
+      if (WGT && (D.mflag & 8)) E.m |= 0x100u;     // coupled: Metropolis acceptance
+      if (WGT && (D.mflag & 0x10)) E.m |= 0x200u;  // general links (Toffoli)
       E.M0 = m == 0 ? ~0u : 0u;
       E.M1 = m == 1 ? ~0u : 0u;
       E.M2 = m == 2 ? ~0u : 0u;
@@ -707,8 +770,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         const uint32_t pidx = (E.dst / 4u - (uint32_t)n) | (kTagSweep << 16);
         // coupled p-bit: its coupling entry and neighbour words, loaded
         // ahead so that their latency overlaps the heat-bath draw
-        Cpl Cp{};
-        uint32_t old_w = 0u, win_w = 0u, wout_w = 0u;
+        [[maybe_unused]] Cpl Cp{};
+        [[maybe_unused]] uint32_t old_w = 0u, win_w = 0u, wout_w = 0u;
         if constexpr (WGT) {
           if (E.m & 0x100u) {
             Cp = rm.cpl[E.dst / 4u - (uint32_t)n];
@@ -717,9 +780,13 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
             wout_w = W[Cp.wout];
           }
         }
-        uint32_t v = heat_bath_links(r0, r1, r2, (int)(WGT ? (E.m & 3u) : E.m), E.M0, E.M1, E.M2,
-                                     E.M3, R, fast, thr0, thr1, thr2, thr3, gglob, sweep, pidx,
-                                     k0, k1);
+        uint32_t v;
+        if (WGT && (E.m & 0x200u))
+          v = glink_heat_bath(W, rm.glk + (E.dst / 4u - (uint32_t)n), rp, thr0, thr1, thr2, thr3,
+                              gglob, sweep, pidx, k0, k1);
+        else
+          v = heat_bath_links(r0, r1, r2, (int)(WGT ? (E.m & 3u) : E.m), E.M0, E.M1, E.M2, E.M3, R,
+                              fast, thr0, thr1, thr2, thr3, gglob, sweep, pidx, k0, k1);
         if constexpr (WGT) {
           if (E.m & 0x100u) {
             const uint32_t p = E.dst / 4u - (uint32_t)n;
@@ -734,7 +801,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       if (K > sh.cons) {
         if constexpr (WGT)
           redraw_extra_coupled(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0,
-                               thr1, thr2, thr3, gglob, sweep, k0, k1, rm.cpl);
+                               thr1, thr2, thr3, gglob, sweep, k0, k1, rm.cpl, rm.glk);
         else
           redraw_extra(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0, thr1, thr2,
                        thr3, gglob, sweep, k0, k1);
@@ -756,7 +823,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         const uint32_t* Sp = smem + iw * (1 + ((s + 1u) & 1u));
         if constexpr (C == 0) rec.clear();
         if constexpr (C + 1 < NC) {
-          rec.read(Sp, srec, C * npb / (NC - 1), (C + 1) * npb / (NC - 1), lane);
+          rec.read<WGT>(Sp, srec, C * npb / (NC - 1), (C + 1) * npb / (NC - 1), lane);
           if (wgt_m) rec.read_u(Sp, rm.uph, C * nug / (NC - 1), (C + 1) * nug / (NC - 1), lane);
         } else {
           rec.reduce(Sp, n, d, lane);
@@ -778,7 +845,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     if (n_sweeps > 0 && recorded(sweep0 + n_sweeps - 1)) {
       const uint32_t* Sl = smem + iw * (1 + ((n_sweeps - 1u) & 1u));
       rec.clear();
-      rec.read(Sl, srec, 0, npb, lane);
+      rec.read<WGT>(Sl, srec, 0, npb, lane);
       if (wgt_m) rec.read_u(Sl, rm.uph, 0, nug, lane);
       rec.reduce(Sl, n, d, lane);
       rec.bin<WGT>(rm_g, g, batch, lane, shist, n_valid, n_samples);
@@ -891,6 +958,10 @@ __global__ void init_kernel(const RunModelDev* __restrict__ rm, int n_models,
       if (e == 0xFFFFFFFFu) {
         v = philox4x32_10(make_uint4(g + r.group0, 0u, (uint32_t)p | (kTagInit << 16), 0u),
                           r.seed_lo, r.seed_hi).x;
+      } else if (e == 0xFFFFFFFEu) {  // Toffoli target: its own general link
+        const GLink* G = r.glk ? r.glk + p : nullptr;
+        if (!G || G->a[0] >= nw || G->b[0] >= nw || G->c[0] >= nw) { set_status(hdr, PB_EINVAL); v = 0u; }
+        else v = W[G->a[0]] ^ (W[G->b[0]] & W[G->c[0]]);
       } else {
         const uint32_t a = e & 0xFFFFu, b = e >> 16;
         if ((int)a >= nw || (int)b >= nw) { set_status(hdr, PB_EINVAL); v = 0u; }
@@ -951,7 +1022,8 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
   int bad = 0;
   for (int i = threadIdx.x; i < npb; i += blockDim.x) {
     const Rec R = r.rec[i];
-    bad |= (R.vd >= nw || R.va >= nw || R.vb >= nw || R.pa >= nw || R.pb >= nw) ? 1 : 0;
+    bad |= (R.vd >= nw || R.va >= nw || R.vb >= nw || R.pa >= nw || R.pb >= nw ||
+            (WGT && R.vc >= nw)) ? 1 : 0;
   }
   if (WGT && r.cpl)
     for (int i = threadIdx.x; i < md.n_ug; i += blockDim.x)
@@ -1027,6 +1099,10 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
         } else if (e == 0xFFFFFFFFu) {
           v = philox4x32_10(make_uint4(gglob, t, (uint32_t)p | (kTagElim << 16), 0u), r.seed_lo,
                             r.seed_hi).x;
+        } else if (WGT && e == 0xFFFFFFFEu) {  // Toffoli target: its own general link
+          const GLink* G = r.glk ? r.glk + p : nullptr;
+          if (!G || G->a[0] >= nw || G->b[0] >= nw || G->c[0] >= nw) { set_status(hdr, PB_EINVAL); v = 0u; }
+          else v = W[G->a[0]] ^ (W[G->b[0]] & W[G->c[0]]);
         } else {
           const uint32_t a = e & 0xFFFFu, b = e >> 16;
           if ((int)a >= nw || (int)b >= nw) { set_status(hdr, PB_EINVAL); v = 0u; }
@@ -1037,7 +1113,7 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
       __syncwarp();
     }
     rec.clear();
-    rec.read(W, r.rec, 0, npb, lane);
+    rec.read<WGT>(W, r.rec, 0, npb, lane);
     if (WGT && r.cpl) rec.read_u(W, r.uph, 0, md.n_ug, lane);
     rec.reduce(W, n, d, lane);
     rec.bin<WGT>(r, g, batch, lane, nullptr, n_valid, n_samples);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libpbits.so")
 
 PB_OK, PB_EINVAL, PB_ERANGE, PB_ENOMEM, PB_ECUDA, PB_ETIMEOUT, PB_ESTATE = 0, -1, -2, -3, -4, -5, -6
 PB_GIBBS, PB_LEARNED, PB_ELIM, PB_ELIM_CLAMP = 0, 1, 2, 3
-PB_U, PB_X, PB_U2 = 5, 6, 7
+PB_U, PB_X, PB_U2, PB_CCX = 5, 6, 7, 8
 
 _lib = None
 
@@ -206,7 +206,9 @@ class Model:
         lib = load()
         arr, ng = gate_array(gates)
         h = ctypes.c_void_p()
-        if mats is None and mats2 is None:
+        g5 = np.asarray(gates)
+        toffoli = g5.size > 0 and g5.ndim == 2 and np.any(g5[:, 0] == PB_CCX)
+        if mats is None and mats2 is None and not toffoli:
             _check(lib.pb_compile(n, d, arr, ng, ctypes.c_uint32(input_bits), ctypes.c_double(J),
                                   ctypes.byref(h)), "pb_compile")
         else:

@@ -248,3 +248,54 @@ def test_exchange_operator_circuit_converges():
     psi, se = r.amplitudes()
     assert np.all(np.abs(psi - exact) <= 5 * se + 1e-9), (psi, exact, se)
     assert np.all(se < 0.02)
+
+
+# ---- the Toffoli gate (PB_CCX)
+
+CCX_CASES = [(4, 5, 2, 256, 40), (6, 8, 3, 100, 25), (12, 20, 1000, 4096, 6), (5, 6, 7, 33, 9)]
+
+
+@pytest.mark.parametrize("n,d,seed,chains,sweeps", CCX_CASES)
+def test_toffoli_bit_exact_vs_oracle(n, d, seed, chains, sweeps):
+    g = W.random_ccx_circuit(n, d, seed, frac=0.9)
+    assert np.sum(g[:, 0] == W.CCX) > 0
+    m = pbits.Model(n, d, g, 3.0)
+    r = pbits.Run([m], [pbits.RunCfg(seed=23, chains=chains)])
+    r.sweeps(sweeps)
+    sums, cnt, valid, samples = r.phase_sums()
+    ref = oracle.u_gibbs(n, d, g, None, J=3.0, seed=23, chains=chains, sweeps=sweeps)
+    assert np.array_equal(pbits.unslice_state(r.get_state(), chains), ref["state"])
+    assert np.array_equal(cnt, ref["cnt"]) and valid == ref["valid"] and samples == ref["samples"]
+    assert np.all(np.abs(sums - ref["sum"]) <= _sum_tol(cnt, 0))
+
+
+def test_toffoli_shape_invariance_and_exact_sampler():
+    n, d = 12, 20
+    g = W.random_ccx_circuit(n, d, 1000, frac=0.7)
+    m = pbits.Model(n, d, g, 3.0)
+    r = pbits.Run([m], [pbits.RunCfg(seed=9, chains=256)])
+    r.set_shape(32, 96)  # classes beyond 32 p-bits: the out-of-line path
+    r.sweeps(9)
+    _, cnt, valid, _ = r.phase_sums()
+    ref = oracle.u_gibbs(n, d, g, None, J=3.0, seed=9, chains=256, sweeps=9)
+    assert np.array_equal(pbits.unslice_state(r.get_state(), 256), ref["state"])
+    assert np.array_equal(cnt, ref["cnt"]) and valid == ref["valid"]
+    e = pbits.Run([m], [pbits.RunCfg(seed=41, chains=300, sampler=pbits.PB_ELIM)])
+    e.sweeps(12)
+    sums, cnt, valid, samples = e.phase_sums()
+    refe = oracle.u_elim(n, d, g, None, seed=41, chains=300, sweeps=12)
+    assert np.array_equal(cnt, refe["cnt"]) and samples == valid == refe["samples"]
+    assert np.array_equal(pbits.unslice_state(e.get_state(), 300), refe["state"])
+    with pytest.raises(pbits.PbError):
+        pbits.Run([m], [pbits.RunCfg(seed=1, chains=32, alphas=np.array([0], np.uint32),
+                                     sampler=pbits.PB_ELIM_CLAMP)])
+
+
+def test_toffoli_circuit_converges():
+    g = W.random_ccx_circuit(4, 5, 2, frac=0.9)
+    exact = oracle.u_statevector(4, 5, g, None)
+    m = pbits.Model(4, 5, g, 3.0)
+    r = pbits.Run([m], [pbits.RunCfg(seed=3, chains=4096, burn_in=50, n_batches=32)])
+    r.sweeps(2000)
+    psi, se = r.amplitudes()
+    assert np.all(np.abs(psi - exact) <= 5 * se + 1e-9), (psi, exact, se)

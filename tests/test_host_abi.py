@@ -128,3 +128,12 @@ def test_compile_rejects_unrepresentable_two_qubit_gates():
         with pytest.raises(pbits.PbError):
             pbits.Model(2, 1, g, 3.0, mats2=bad[None])
     pbits.Model(2, 1, g, 3.0, mats2=W.swap_matrix()[None])
+
+
+@pytest.mark.parametrize("n,d,seed", [(4, 5, 2), (6, 8, 3), (12, 20, 1000)])
+def test_compile_toffoli_matches_oracle(n, d, seed):
+    g = W.random_ccx_circuit(n, d, seed, frac=0.9)
+    assert np.sum(g[:, 0] == W.CCX) > 0
+    m = pbits.Model(n, d, g, 3.0)
+    assert np.array_equal(m.colours(), oracle.u_colour(n, d, g))
+    assert m.info()["rank"] == -1
