@@ -578,10 +578,10 @@ def shor_measurement(dev, stream):
             M = 2 ** wl.n
             count, _, mx = sc.peaks(2.2 / M, 0)
         steps = float(M) * wl.T  # (k, sample) pairs
-        # per pair: 2 FADD (sums) + 4 (complex rotation) FP32 lane operations
+        # per pair one complex multiply-add: 4 FP32 lane operations
         out[wl.name] = {"N": wl.N, "a": wl.a, "n": wl.n, "T": wl.T, "order": wl.r,
                         "peaks_found": count, "call_s": best, "pairs_per_s": steps / best,
-                        "fp32_frac_lower_bound": steps * 6 / best / peak_fp32,
+                        "fp32_frac_lower_bound": steps * 4 / best / peak_fp32,
                         "paper_s": 5923.0 if wl.name == "shor_78" else 32 * 3600.0}
         del sc
         torch.cuda.empty_cache()

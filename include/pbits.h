@@ -442,9 +442,10 @@ PB_API int pb_gemm_bf16(const void* dA, int lda, const void* dB, int ldb, void* 
  * shows as r peaks near multiples of 2^n / r (Sec. 5.2: T = gamma r
  * samples, 2 <= gamma <= 4).
  * Device computation: modular exponentiation, a sort of the samples by
- * (y, x), then per k a walk over the sorted samples (FP32 phasors: an exact
- * integer phase k x mod 2^n per sample, re-anchored every 32 k; each term
- * within about 1e-5 of the exact one; FP64 output).
+ * (y, x), then per k a walk over the sorted samples (FP32 phasors: the
+ * exact integer phase k0 x mod 2^n of a 32-k block times the sample's table
+ * of e^{2 pi i j x / 2^n}, j < 32; each term within about 5e-7 of the exact
+ * one; FP64 output).
  *   N in [2, 2^32), n in [1, 32], 1 <= T <= 2^26, x: host array of T column
  *   indices < 2^n (caller-owned; the draws are the caller's, so that they
  *   can be shared and reproduced).  d_workspace: device, 256-byte aligned,

@@ -7,9 +7,10 @@
 // paper's 3 x 2^n) the samples are sorted by (y, x) on the device, so each
 // y's samples are contiguous, and a thread that owns 32 consecutive k walks
 // the sorted list: per sample an exact anchor e^{2 pi i k0 x / 2^n} (integer
-// phase k0 x mod 2^n, FP32 sincospif), then 31 rotations by e^{2 pi i x / 2^n}
-// (one complex multiply per k), adding into the group's 32 complex sums; at a
-// group's end the squared moduli go into P.  Memory: 2^n doubles of output
+// phase k0 x mod 2^n, FP32 sincospif) times the sample's table
+// e^{2 pi i j x / 2^n}, j = 0..31 (shared by every thread, read from shared
+// memory), one complex multiply-add per k into the group's 32 complex sums;
+// at a group's end the squared moduli go into P.  Memory: 2^n doubles of output
 // plus O(T).  The only contention is the FP64 atomic add of a block's P into
 // the output when the samples are split over several blocks (at group
 // boundaries, so that every |sum|^2 is complete in one block).
@@ -26,7 +27,7 @@ namespace {
 
 constexpr int kShorK = 32;          // k values per thread
 constexpr int kShorThreads = 256;   // threads per block
-constexpr int kShorChunk = 2048;    // samples staged in shared memory per pass
+constexpr int kShorChunk = 128;     // samples staged in shared memory per pass
 
 // Sort key of sample i: y << 32 | x (T <= i < Tpad: all ones, sorted last).
 __global__ void shor_modexp_kernel(const uint32_t* __restrict__ x, uint32_t T, uint32_t Tpad,
@@ -64,20 +65,26 @@ __global__ void bitonic_step_kernel(unsigned long long* __restrict__ keys, uint3
   }
 }
 
-// Sorted keys -> x, the rotation e^{2 pi i x / 2^n} (FP64, rounded to FP32)
-// and the group-end flag (the next sample has another y).
+// Sorted keys -> x, the group-end flag (the next sample has another y) and
+// the sample's table e^{2 pi i j x / 2^n}, j = 0 .. kShorK - 1 (exact integer
+// phase j x mod 2^n, FP64 sincospi, rounded to FP32); one thread per (i, j).
 __global__ void shor_prep_kernel(const unsigned long long* __restrict__ keys, uint32_t T, int n,
-                                 uint32_t* __restrict__ xs, float2* __restrict__ rot,
+                                 uint32_t* __restrict__ xs, float2* __restrict__ tab,
                                  uint8_t* __restrict__ gend) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= T) return;
+  const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned long long)T * kShorK) return;
+  const uint32_t i = (uint32_t)(t / kShorK), j = (uint32_t)(t % kShorK);
   const unsigned long long key = keys[i];
   const uint32_t x = (uint32_t)key;
-  xs[i] = x;
-  gend[i] = (i + 1 == T || (keys[i + 1] >> 32) != (key >> 32)) ? 1 : 0;
+  if (j == 0) {
+    xs[i] = x;
+    gend[i] = (i + 1 == T || (keys[i + 1] >> 32) != (key >> 32)) ? 1 : 0;
+  }
+  const unsigned long long mask = (n == 64) ? ~0ull : ((1ull << n) - 1ull);
+  const unsigned long long ph = ((unsigned long long)j * x) & mask;
   double s, c;
-  sincospi(ldexp((double)x, 1 - n), &s, &c);  // angle 2 pi x / 2^n
-  rot[i] = make_float2((float)c, (float)s);
+  sincospi(ldexp((double)ph, 1 - n), &s, &c);  // angle 2 pi j x / 2^n
+  tab[t] = make_float2((float)c, (float)s);
 }
 
 // Slice s of the sorted samples starts at the first group start at or after
@@ -94,11 +101,11 @@ __global__ void shor_bounds_kernel(const uint8_t* __restrict__ gend, uint32_t T,
 // P for k = k0 .. k0 + 31 of this thread over the samples of slice
 // blockIdx.y, added (times `scale`) into prob.
 __global__ void __launch_bounds__(kShorThreads) shor_columns_kernel(
-    const uint32_t* __restrict__ xs, const float2* __restrict__ rot,
+    const uint32_t* __restrict__ xs, const float2* __restrict__ tab,
     const uint8_t* __restrict__ gend, const uint32_t* __restrict__ bounds, int n, double scale,
     double* __restrict__ prob) {
   __shared__ uint32_t sx[kShorChunk];
-  __shared__ float2 sr[kShorChunk];
+  __shared__ __align__(16) float2 sr[kShorChunk * kShorK];
   __shared__ uint8_t sg[kShorChunk];
   const unsigned long long Ktot = 1ull << n;
   const unsigned long long k0 =
@@ -116,25 +123,30 @@ __global__ void __launch_bounds__(kShorThreads) shor_columns_kernel(
     __syncthreads();
     for (uint32_t t = threadIdx.x; t < cn; t += blockDim.x) {
       sx[t] = xs[c0 + t];
-      sr[t] = rot[c0 + t];
       sg[t] = gend[c0 + t];
+    }
+    {  // the chunk's tables, 16 bytes at a time
+      const float4* src = reinterpret_cast<const float4*>(tab + (size_t)c0 * kShorK);
+      float4* dst = reinterpret_cast<float4*>(sr);
+      for (uint32_t t = threadIdx.x; t < cn * (kShorK / 2); t += blockDim.x) dst[t] = src[t];
     }
     __syncthreads();
 #pragma unroll 1
     for (uint32_t t = 0; t < cn; ++t) {
       const uint32_t x = sx[t];
-      const float2 w = sr[t];
       // exact integer phase k0 x mod 2^n, centred to [-2^{n-1}, 2^{n-1})
       const int32_t ph = (int32_t)((k0w * x) << sh) >> sh;
       float pr, pi;
       sincospif((float)ph * to_half_turns, &pi, &pr);
+      const float4* w4 = reinterpret_cast<const float4*>(sr + t * kShorK);
 #pragma unroll
-      for (int j = 0; j < kShorK; ++j) {
-        ar[j] += pr;
-        ai[j] += pi;
-        const float tr = fmaf(pr, w.x, -pi * w.y);
-        pi = fmaf(pr, w.y, pi * w.x);
-        pr = tr;
+      for (int j2 = 0; j2 < kShorK / 2; ++j2) {
+        const float4 w = w4[j2];  // e^{i 2 pi (2 j2) x / 2^n}, e^{i 2 pi (2 j2 + 1) x / 2^n}
+        const int j = 2 * j2;
+        ar[j] = fmaf(pr, w.x, fmaf(-pi, w.y, ar[j]));
+        ai[j] = fmaf(pr, w.y, fmaf(pi, w.x, ai[j]));
+        ar[j + 1] = fmaf(pr, w.z, fmaf(-pi, w.w, ar[j + 1]));
+        ai[j + 1] = fmaf(pr, w.w, fmaf(pi, w.z, ai[j + 1]));
       }
       if (sg[t]) {  // end of this y's samples: |sum|^2 into P
 #pragma unroll
@@ -188,7 +200,7 @@ __global__ void peaks_kernel(const double* __restrict__ prob, unsigned long long
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct ShorLayout {
-  size_t x, keys, ys, xs, rot, gend, bounds, misc, total;
+  size_t x, keys, ys, xs, tab, gend, bounds, misc, total;
   uint32_t Tpad, S;
 };
 
@@ -214,7 +226,7 @@ ShorLayout shor_layout(int n, uint32_t T) {
   L.keys = take((size_t)Tpad * 8);
   L.ys = take((size_t)T * 8);
   L.xs = take((size_t)T * 4);
-  L.rot = take((size_t)T * 8);
+  L.tab = take((size_t)T * kShorK * 8);
   L.gend = take((size_t)T);
   L.bounds = take((size_t)(L.S + 1) * 4);
   L.misc = take(64);
@@ -260,7 +272,7 @@ PB_API int pb_shor_columns(uint64_t N, uint64_t a, int n, const uint32_t* x, uin
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + L.keys);
   unsigned long long* ys = reinterpret_cast<unsigned long long*>(ws + L.ys);
   uint32_t* xs = reinterpret_cast<uint32_t*>(ws + L.xs);
-  float2* rot = reinterpret_cast<float2*>(ws + L.rot);
+  float2* tab = reinterpret_cast<float2*>(ws + L.tab);
   uint8_t* gend = reinterpret_cast<uint8_t*>(ws + L.gend);
   uint32_t* bounds = reinterpret_cast<uint32_t*>(ws + L.bounds);
   const unsigned long long K = 1ull << n;
@@ -273,14 +285,15 @@ PB_API int pb_shor_columns(uint64_t N, uint64_t a, int n, const uint32_t* x, uin
   for (uint32_t k = 2; k <= L.Tpad; k <<= 1)
     for (uint32_t j = k >> 1; j > 0; j >>= 1)
       bitonic_step_kernel<<<(L.Tpad + tpb - 1) / tpb, tpb, 0, st>>>(keys, L.Tpad, j, k);
-  shor_prep_kernel<<<(T + tpb - 1) / tpb, tpb, 0, st>>>(keys, T, n, xs, rot, gend);
+  shor_prep_kernel<<<(unsigned)(((unsigned long long)T * kShorK + tpb - 1) / tpb), tpb, 0, st>>>(
+      keys, T, n, xs, tab, gend);
   shor_bounds_kernel<<<(L.S + 1 + tpb - 1) / tpb, tpb, 0, st>>>(gend, T, L.S, bounds);
   const unsigned long long kthreads = (K + kShorK - 1) / kShorK;
   const unsigned long long kblocks = (kthreads + kShorThreads - 1) / kShorThreads;
   if (kblocks > 0x7FFFFFFFull) return PB_ERANGE;
   // prob[k] = P[k] / T with the IQFT's 2^{-n} folded in
   const double scale = std::ldexp(1.0, -n) / (double)T;
-  shor_columns_kernel<<<dim3((unsigned)kblocks, L.S), kShorThreads, 0, st>>>(xs, rot, gend, bounds,
+  shor_columns_kernel<<<dim3((unsigned)kblocks, L.S), kShorThreads, 0, st>>>(xs, tab, gend, bounds,
                                                                             n, scale, d_prob);
   if ((e = cudaGetLastError()) != cudaSuccess) return PB_ECUDA;
   if (y_out) {

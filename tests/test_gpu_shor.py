@@ -20,10 +20,10 @@ def _lib():
 
 
 def _tol(N, a, n, x):
-    """Per k: each FP32 phasor is within about 4e-6 of e^{i angle} (an exact
-    integer phase rounded to FP32, then up to 31 FP32 rotations, each adding
-    about 1.2e-7), so |group sum|^2 moves by at most 8e-6 g^2 and prob by
-    1e-5 sum_y g_y^2 / (2^n T)."""
+    """Per k: each FP32 phasor is within about 5e-7 of e^{i angle} (an exact
+    integer phase rounded to FP32 and sincospif, times an FP32-rounded table
+    entry), so |group sum|^2 moves by at most about 1e-6 g^2; the bound used,
+    1e-5 sum_y g_y^2 / (2^n T), leaves a factor of ten."""
     y = np.array([pow(a, int(v), N) for v in x])
     _, g = np.unique(y, return_counts=True)
     return 1e-5 * float(np.sum(g.astype(np.float64) ** 2)) / (2 ** n * len(x)) + 1e-12
