@@ -48,6 +48,13 @@ def _worker(rank, world, port, q, mode):
         if mode == "leave" and rank == 1:
             q.put((rank, "left"))
             return  # leaves before the exchange
+        if mode == "phase":  # a general-gate model: FP64 phase sums + exact counters
+            gu, mu = W.random_general_circuit(n, d, 19, frac_u=0.6)
+            r = oracle.u_gibbs(n, d, gu, mu, J=3.0, seed=7, chains=c, chain0=g0 * 32, sweeps=15)
+            sums, cnt, valid, samples = D.allreduce_phase_sums(r["sum"], r["cnt"], r["valid"],
+                                                               r["samples"])
+            q.put((rank, (sums.tolist(), cnt.tolist(), valid, samples)))
+            return
         r = oracle.gibbs(n, d, g, J=3.0, seed=7, chains=c, chain0=g0 * 32, sweeps=15)
         try:
             cnt, valid, samples = D.allreduce_histogram(r["cnt"], r["valid"], r["samples"])
@@ -96,3 +103,19 @@ def test_rank_leaving_before_the_exchange_is_detected():
     out = _spawn("leave")
     assert out[1] == "left"
     assert isinstance(out[0], str) and out[0].startswith("error"), out[0]
+
+
+
+def test_two_rank_phase_sums_equal_single_run():
+    """General one-qubit gates: the counters reduce exactly and the FP64 phase
+    sums to rounding."""
+    import oracle
+    out = _spawn("phase")
+    n, d = 4, 6
+    gu, mu = W.random_general_circuit(n, d, 19, frac_u=0.6)
+    ref = oracle.u_gibbs(n, d, gu, mu, J=3.0, seed=7, chains=100, sweeps=15)
+    for rank in (0, 1):
+        sums, cnt, valid, samples = out[rank]
+        assert np.array_equal(np.array(cnt, dtype=np.uint64), ref["cnt"])
+        assert valid == ref["valid"] and samples == ref["samples"]
+        assert np.allclose(np.array(sums), ref["sum"], rtol=0, atol=1e-9)

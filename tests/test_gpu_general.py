@@ -299,3 +299,44 @@ def test_toffoli_circuit_converges():
     r.sweeps(2000)
     psi, se = r.amplitudes()
     assert np.all(np.abs(psi - exact) <= 5 * se + 1e-9), (psi, exact, se)
+
+
+def test_general_run_checkpoint_tune_and_mixed_with_toffoli():
+    """A run holding a coupled-U model, a U2 model and a Toffoli model:
+    checkpoint / restore gives the same states and counters (the FP64 sums
+    to rounding), the
+    autotuner keeps shapes of at most 512 threads and leaves the results
+    unchanged."""
+    n, d = 6, 8
+    gu, mu = W.random_general_circuit(n, d, 5, frac_u=0.5)
+    g2, m2 = W.random_two_qubit_circuit(n, d, 6, frac=0.8)
+    gc = W.random_ccx_circuit(n, d, 3, frac=0.9)
+    models = [pbits.Model(n, d, gu, 3.0, mats=mu), pbits.Model(n, d, g2, 3.0, mats2=m2),
+              pbits.Model(n, d, gc, 3.0)]
+    cfgs = [pbits.RunCfg(seed=11 + i, chains=64 + 17 * i) for i in range(3)]
+    a = pbits.Run(models, cfgs)
+    a.sweeps(7)
+    blob = a.checkpoint()
+    a.sweeps(9)
+    b = pbits.Run(models, cfgs)
+    b.restore(blob)
+    b.sweeps(9)
+    for i in range(3):
+        sa, ca, va, na = a.phase_sums(i)
+        sb, cb, vb, nb = b.phase_sums(i)
+        assert np.array_equal(ca, cb) and va == vb and na == nb
+        # FP64 atomic adds land in any order: equal to rounding
+        assert np.allclose(sa, sb, rtol=0, atol=1e-9 * max(1.0, float(np.abs(sa).max())))
+        assert np.array_equal(a.get_state(i), b.get_state(i))
+    c = pbits.Run(models, cfgs)
+    c.tune(trial_sweeps=5)
+    sh = c.shape()
+    assert sh["consumers"] + sh["producers"] + 32 <= 512
+    c.sweeps(16)
+    refs = [oracle.u_gibbs(n, d, gu, mu, J=3.0, seed=11, chains=64, sweeps=16),
+            oracle.u_gibbs(n, d, g2, None, J=3.0, seed=12, chains=81, sweeps=16, mats2=m2),
+            oracle.u_gibbs(n, d, gc, None, J=3.0, seed=13, chains=98, sweeps=16)]
+    for i, ref in enumerate(refs):
+        _, cnt, valid, _ = c.phase_sums(i)
+        assert np.array_equal(cnt, ref["cnt"]) and valid == ref["valid"]
+        assert np.array_equal(pbits.unslice_state(c.get_state(i), cfgs[i].chains), ref["state"])
