@@ -19,7 +19,13 @@
  * controlled phases, ...).  Every permutation of two bits is affine over
  * GF(2), so each output bit is a copy or an XOR of the input bits, possibly
  * complemented; an output bit that is the complement of an XOR of both
- * inputs is rejected (the J-penalty links carry at most two words).  Rows
+ * inputs is rejected (the J-penalty links carry at most two words).  A
+ * unitary U2 with a column of more than one nonzero is a "table" gate
+ * (Eq. ET2): both outputs are free and carry the real energy
+ * E(y, x) = -ln |U(y, x)| (J for a zero entry, the Appendix's e^{-J}); a
+ * path through a zero entry is invalid; with unequal column sums of |U|
+ * the estimator has no closed-form scale (log2z is NaN) and is read
+ * L2-normalised (Fig. 2 Step 4).  Rows
  * with other ops are the Clifford+T gates of oracle.c; their mats entries
  * are ignored.  op = ORC_CCX (8) is the Toffoli gate of the Appendix on
  * (q0, q1, q2), controls q0 and q1, target q2: x_{q2} XOR= x_{q0} x_{q1},
@@ -72,7 +78,7 @@ typedef struct {
 } orc_gate;
 
 enum { G_H = 0, G_S = 1, G_T = 2, G_CNOT = 3, G_CZ = 4, G_U = 5, G_X = 6, G_U2 = 7, G_CCX = 8 };
-enum { K_STD = 0, K_DIAG = 1, K_ANTI = 2, K_COUPLED = 3 };
+enum { K_STD = 0, K_DIAG = 1, K_ANTI = 2, K_COUPLED = 3, K_TABLE = 4 };
 enum { MAT = 32 }; /* doubles per gate row of mats */
 
 /* from oracle.c */
@@ -127,9 +133,10 @@ static void u2_entry(const double* m32, int y, int x, double* re, double* im) {
   *im = m32[k + 1];
 }
 
-/* A two-qubit gate: unitary within 1e-9, one nonzero per column; perm[x] =
- * the row of column x's nonzero; dmask[o] (bit u: output bit o depends on
- * input bit u) and cbit[o] of the affine map.  -1 if rejected. */
+/* A two-qubit gate, unitary within 1e-9.  One nonzero per column: perm[x] =
+ * the row of column x's nonzero, dmask[o] (bit u: output bit o depends on
+ * input bit u) and cbit[o] of the affine map; returns 0.  A column of more
+ * than one nonzero: a table gate, returns 1.  -1 if rejected. */
 static int u2_classify(const double* m, int perm[4], int dmask[2], int cbit[2]) {
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
@@ -150,7 +157,7 @@ static int u2_classify(const double* m, int perm[4], int dmask[2], int cbit[2]) 
       u2_entry(m, y, x, &r, &i);
       if (r != 0.0 || i != 0.0) { perm[x] = y; ++nz; }
     }
-    if (nz != 1) return -1;
+    if (nz != 1) return 1; /* a table gate */
   }
   for (int o = 0; o < 2; ++o) {
     const int c = (perm[0] >> o) & 1, al = ((perm[1] >> o) & 1) ^ c, be = ((perm[2] >> o) & 1) ^ c;
@@ -279,10 +286,9 @@ static int unet_init(unet* u, int n, int d, const orc_gate* g, int ng, const dou
       u->kind[i] = k;
     }
     if (G->op == G_U2) {
-      if (!mats || u2_classify(mats + (size_t)MAT * i, u->perm[i], u->dmask[i], u->cbit[i]) != 0) {
-        unet_free(u);
-        return -1;
-      }
+      const int k = mats ? u2_classify(mats + (size_t)MAT * i, u->perm[i], u->dmask[i], u->cbit[i]) : -1;
+      if (k < 0) { unet_free(u); return -1; }
+      if (k == 1) u->kind[i] = K_TABLE;
     }
   }
   return 0;
@@ -401,6 +407,7 @@ int orc_u_pathstats(int n, int d, const orc_gate* g, int ng, const double* mats,
 static double log2_scale(const unet* u) {
   double l = 0.0;
   for (int i = 0; i < u->ng; ++i) {
+    if (u->g[i].op == G_U2 && u->kind[i] == K_TABLE) return NAN; /* no closed form */
     if (u->g[i].op == G_H) l += 0.5;
     if (u->g[i].op == G_U && u->kind[i] == K_COUPLED) l += log2(u->a[i] + u->b[i]);
   }
@@ -442,6 +449,7 @@ static int layer_viol(const unet* u, int L, uint32_t x, uint32_t y) {
         else v += bitof(x, q) != bitof(y, q);
         break;
       case G_U2: {
+        if (u->kind[gi] == K_TABLE) break; /* free outputs (the table's energy) */
         const int o = (q == G->q0) ? 0 : 1;
         v += ((u->perm[gi][gidx(G, x)] >> o) & 1) != bitof(y, q);
         break;
@@ -449,6 +457,26 @@ static int layer_viol(const unet* u, int L, uint32_t x, uint32_t y) {
     }
   }
   return v;
+}
+
+/* Does the path take a zero entry of a table gate? */
+static int table_zero(const unet* u, const uint32_t* s) {
+  for (int i = 0; i < u->ng; ++i) {
+    const orc_gate* G = &u->g[i];
+    if (G->op != G_U2 || u->kind[i] != K_TABLE) continue;
+    double r, im;
+    u2_entry(u->mats + (size_t)MAT * i, gidx(G, s[G->layer + 1]), gidx(G, s[G->layer]), &r, &im);
+    if (r == 0.0 && im == 0.0) return 1;
+  }
+  return 0;
+}
+
+/* Energy of a table gate's entry: -ln |U(y, x)|, J for a zero entry. */
+static double table_energy(const unet* u, int gi, int y, int x, double J) {
+  double r, im;
+  u2_entry(u->mats + (size_t)MAT * gi, y, x, &r, &im);
+  const double m = hypot(r, im);
+  return m > 0.0 ? -log(m) : J;
 }
 
 static int path_viol(const unet* u, const uint32_t* s) {
@@ -492,7 +520,8 @@ static int det_bit(const unet* u, int L, int q, uint32_t x) {
 static int is_free(const unet* u, int L, int q) {
   const int gi = u->gate_of[L * u->n + q];
   if (gi < 0) return 0;
-  return u->g[gi].op == G_H || (u->g[gi].op == G_U && u->kind[gi] == K_COUPLED);
+  return u->g[gi].op == G_H || (u->g[gi].op == G_U && u->kind[gi] == K_COUPLED) ||
+         (u->g[gi].op == G_U2 && u->kind[gi] == K_TABLE);
 }
 
 /* Colour classes of one sweep: the rule of oracle.c's pbit_colours (DSATUR,
@@ -516,7 +545,7 @@ static int u_colours(const unet* u, int32_t* colour) {
   int over = 0;
   for (int L = 0; L < d; ++L)
     for (int q = 0; q < n; ++q) {
-      int vars[4], nv = 0, ins[3], ni = 0;
+      int vars[5], nv = 0, ins[3], ni = 0;
       vars[nv++] = L * n + q; /* p-bit (L+1, q) */
       const int gi = u->gate_of[L * n + q];
       if (gi < 0) {
@@ -527,6 +556,11 @@ static int u_colours(const unet* u, int32_t* colour) {
         if (G->op == G_CNOT) {
           ins[ni++] = q;
           if (q == G->q1) ins[ni++] = G->q0;
+        } else if (G->op == G_U2 && u->kind[gi] == K_TABLE) {
+          /* the table's factor: both outputs and both inputs */
+          vars[nv++] = L * n + (q == G->q0 ? G->q1 : G->q0);
+          ins[ni++] = G->q0;
+          ins[ni++] = G->q1;
         } else if (G->op == G_U2) {
           const int dm = u->dmask[gi][(q == G->q0) ? 0 : 1];
           if (dm & 1) ins[ni++] = G->q0;
@@ -571,7 +605,10 @@ static int u_colours(const unet* u, int32_t* colour) {
     /* the fixed classes separate at most two inputs of one factor: a
      * Toffoli's four-bit factor needs the computed colouring */
     for (int i = 0; i < u->ng; ++i)
-      if (u->g[i].op == G_CCX) { free(nb); free(deg); free(seen); return -2; }
+      if (u->g[i].op == G_CCX || (u->g[i].op == G_U2 && u->kind[i] == K_TABLE)) {
+        free(nb); free(deg); free(seen);
+        return -2;
+      }
     ncol = 4;
     for (int k = 1; k <= d; ++k)
       for (int q = 0; q < n; ++q) {
@@ -607,6 +644,44 @@ static uint32_t uniform32(uint64_t seed, uint32_t chain, uint32_t t, uint32_t p,
   return u;
 }
 
+/* The 32-bit uniform of chain c as one Philox word: word (c mod 4) of
+ * Philox(c >> 5, t, p | tag << 16, (c mod 32) / 4). */
+static uint32_t lane_uniform(uint64_t seed, uint32_t chain, uint32_t t, uint32_t p, uint32_t tag) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t ctr[4] = {chain >> 5, t, p | (tag << 16), (chain & 31u) >> 2}, out[4];
+  orc_philox4x32_10(ctr, key, out);
+  return out[chain & 3u];
+}
+
+/* Change of the table energy when p-bit (k, q) goes 0 -> 1 (path s, layers
+ * 0..d): the gate of layer k-1 on q if it is a table (the bit is one of its
+ * outputs), plus the gate of layer k if it is a table (one of its inputs). */
+static double table_delta(const unet* u, const uint32_t* s, int k, int q, double J) {
+  const int n = u->n, d = u->d;
+  double din = 0.0, dout = 0.0;
+  const int gin = u->gate_of[(k - 1) * n + q];
+  if (gin >= 0 && u->g[gin].op == G_U2 && u->kind[gin] == K_TABLE) {
+    const orc_gate* G = &u->g[gin];
+    const int o = (q == G->q0) ? 0 : 1;
+    const int xi = gidx(G, s[k - 1]);
+    const int yo = bitof(s[k], o == 0 ? G->q1 : G->q0);  /* the other output */
+    const int y1 = o == 0 ? 1 + 2 * yo : yo + 2, y0 = o == 0 ? 2 * yo : yo;
+    din = table_energy(u, gin, y1, xi, J) - table_energy(u, gin, y0, xi, J);
+  }
+  if (k < d) {
+    const int gout = u->gate_of[k * n + q];
+    if (gout >= 0 && u->g[gout].op == G_U2 && u->kind[gout] == K_TABLE) {
+      const orc_gate* G = &u->g[gout];
+      const int iu = (q == G->q0) ? 0 : 1;
+      const int yi = gidx(G, s[k + 1]);
+      const int xo = bitof(s[k], iu == 0 ? G->q1 : G->q0);  /* the other input */
+      const int x1 = iu == 0 ? 1 + 2 * xo : xo + 2, x0 = iu == 0 ? 2 * xo : xo;
+      dout = table_energy(u, gout, yi, x1, J) - table_energy(u, gout, yi, x0, J);
+    }
+  }
+  return din + dout;
+}
+
 /* Bit (c mod 32) of word 0 of Philox(c >> 5, t, p | tag << 16, 0). */
 static int coin(uint64_t seed, uint32_t chain, uint32_t t, uint32_t p, uint32_t tag) {
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -623,7 +698,7 @@ static uint32_t to_u32_threshold(double x) {
 
 static void add_sample(const unet* u, const uint32_t* s, const uint32_t* alphas, int n_alphas,
                        double* sre, double* sim, uint64_t* cnt, uint64_t* my_valid, int* err) {
-  if (path_viol(u, s) != 0) return;
+  if (path_viol(u, s) != 0 || table_zero(u, s)) return;
   double pr, pi;
   if (!path_phase_c(u, s, &pr, &pi)) { *err = 1; return; }
   ++*my_valid;
@@ -659,6 +734,10 @@ static void add_sample(const unet* u, const uint32_t* s, const uint32_t* alphas,
  *     dK = K_in (1 - 2 e_in) + K_out (1 - 2 e_out) is the change of
  *     sum K [s_out != s_in] caused by the flip.  Accept when dK <= 0, else
  *     when u' < floor(2^32 e^{-dK}) (capped at 2^32 - 1), u' = uniform32(tag 6).
+ *   Step 2b (table gates, Eq. ET2): a flip that passed is kept when the
+ *     change dE of the tables' energy (-ln|U| of the entries taken, J for a
+ *     zero entry; table_delta, sign by direction) is <= 0, else when
+ *     u'' < floor(2^32 e^{-dE}), u'' = lane_uniform(tag 7).
  *   The pair is Metropolis-Hastings with the J-part heat-bath as proposal:
  *   the chain keeps p proportional to e^{-J viol} e^{-sum K [s_out != s_in]}.
  * Initial paths: free outputs (H, coupled U) from the tag-1 coin, the others
@@ -750,6 +829,16 @@ int orc_u_gibbs(int n, int d, const orc_gate* g, int ng, const double* mats, uin
                   const uint32_t A = to_u32_threshold(exp(-dk));
                   if (!(uniform32(seed, chain, sweep, p, 6) < A)) xn = x;
                 }
+                /* Step 2b: Metropolis acceptance on the table energy (a second
+                 * factor of the acceptance: min(1, e^{-dK}) min(1, e^{-dE})) */
+                if (xn != x) {
+                  const double de = table_delta(&u, s, k, q, J);
+                  const double dt = x == 0 ? de : -de;
+                  if (dt > 0.0) {
+                    const uint32_t A = to_u32_threshold(exp(-dt));
+                    if (!(lane_uniform(seed, chain, sweep, p, 7) < A)) xn = x;
+                  }
+                }
               }
               s[k] = (keep & ~(1u << q)) | ((uint32_t)xn << q);
             }
@@ -790,6 +879,8 @@ int orc_u_elim(int n, int d, const orc_gate* g, int ng, const double* mats, uint
   if (record_every == 0) return -1;
   if (!alphas && n > 22) return -2;
   if (unet_init(&u, n, d, g, ng, mats) != 0) return -1;
+  for (int i = 0; i < ng; ++i)
+    if (g[i].op == G_U2 && u.kind[i] == K_TABLE) { unet_free(&u); return -1; } /* Gibbs only */
   if (log2z) *log2z = log2_scale(&u);
   const uint32_t nmask = (n == 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
   const uint64_t bins = alphas ? (uint64_t)n_alphas : (1ull << n);

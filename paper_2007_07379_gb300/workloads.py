@@ -194,6 +194,36 @@ def random_ccx_circuit(n: int, d: int, seed: int, frac: float = 0.5) -> np.ndarr
     return np.asarray(rows, dtype=np.int32).reshape(-1, 5)
 
 
+def random_unitary4(rng: "SplitMix64") -> np.ndarray:
+    """A 4x4 unitary with no zero entry: QR of a complex matrix of entries
+    uniform in the unit square (SplitMix64 draws), phases fixed by R's
+    diagonal."""
+    def unif() -> float:
+        return (rng.next() >> 11) * (2.0 ** -53)
+    a = np.array([[unif() - 0.5 + 1j * (unif() - 0.5) for _ in range(4)] for _ in range(4)])
+    q, r = np.linalg.qr(a)
+    return q * (np.diag(r) / np.abs(np.diag(r)))[None, :]
+
+
+def random_table_circuit(n: int, d: int, seed: int, frac: float = 0.6):
+    """random_circuit(n, d, seed) with each CNOT / CZ replaced, with
+    probability frac, by a random dense two-qubit unitary (a table gate,
+    Eq. ET2), alternating with the controlled-H (a table with zeros).
+    Returns (gates, mats2)."""
+    g = random_circuit(n, d, seed).copy()
+    rng = SplitMix64(seed ^ 0x7AB1E)
+    mats2 = np.zeros((len(g), 4, 4), dtype=np.complex128)
+    ch = np.eye(4, dtype=np.complex128)
+    ch[np.ix_([1, 3], [1, 3])] = np.array([[1, 1], [1, -1]]) / np.sqrt(2)  # H on q1 if q0 = 1
+    k = 0
+    for i in range(len(g)):
+        if g[i, 0] in (CNOT, CZ) and (rng.next() >> 11) * (2.0 ** -53) < frac:
+            mats2[i] = random_unitary4(rng) if k % 2 == 0 else ch
+            g[i, 0] = U2
+            k += 1
+    return g, mats2
+
+
 def rotated_h_chain(d: int, theta: float):
     """n = 1, d rotated Hadamards in series (Sec. 4.2, Fig. 5): (gates, mats)
     with mats complex128[d, 2, 2]."""

@@ -400,9 +400,6 @@ def test_two_qubit_circuits_converge(n, d, seed):
 def test_rejects_unrepresentable_two_qubit_gates():
     g = np.array([[W.U2, 0, 0, 1]], dtype=np.int32)
     bad = []
-    # a general (non-permutation) unitary: H on q0 as a 4x4
-    h = np.kron(np.eye(2), np.array([[1, 1], [1, -1]]) / np.sqrt(2))
-    bad.append(h)
     # output q0 = NOT(x1 XOR x2): y = (1 ^ x1 ^ x2) | x2 << 1
     m = np.zeros((4, 4), dtype=np.complex128)
     for x in range(4):
@@ -488,3 +485,79 @@ def test_ccx_circuits_converge(n, d, seed):
     Z = 2 ** e["log2z"]
     se_e = np.sqrt(np.maximum(Z * ps["zabs"] - np.abs(exact) ** 2, 0) / e["samples"])
     assert np.all(np.abs(oracle.u_estimate(e) - exact) <= 5 * se_e + 1e-12)
+
+
+
+# ---- two-qubit tables (Eq. ET2): more than one nonzero per column
+
+def _table_circuit(n, d, seed):
+    g, m2 = W.random_table_circuit(n, d, seed)
+    assert np.sum(g[:, 0] == W.U2) >= 1
+    return g, m2
+
+
+@pytest.mark.parametrize("n,d,seed", [(2, 4, 1), (3, 5, 2), (4, 5, 6)])
+def test_table_gates_against_matrix_products(n, d, seed):
+    g, m2 = _table_circuit(n, d, seed)
+    want = _kron_unitary(n, d, g, None, m2)[:, 0]
+    assert np.allclose(oracle.u_statevector(n, d, g, None, mats2=m2), want, atol=1e-12)
+    assert np.allclose(oracle.u_pathstats(n, d, g, None, mats2=m2)["U"], want, atol=1e-12)
+    assert np.isnan(oracle.u_log2z(n, d, g, None, mats2=m2))
+
+
+@pytest.mark.parametrize("n,d,seed", [(2, 4, 1), (3, 4, 2), (3, 5, 9)])
+def test_table_stationary_law_is_abs_weight(n, d, seed):
+    """The factorised Metropolis step (table energy -ln|U| per entry) keeps
+    p_C ~ |U_C| over the valid paths: chi-square of the final states."""
+    from scipy.stats import chisquare
+    g, m2 = _table_circuit(n, d, seed)
+    # |U_C| of every valid path by the layer matrices (numpy)
+    per_layer = []
+    for L in range(d):
+        gl = [(i, r) for i, r in enumerate(g) if r[1] == L]
+        sub = np.array([r for _, r in gl], dtype=np.int32).reshape(-1, 4).copy()
+        sub[:, 1] = 0
+        mm = np.stack([m2[i] for i, _ in gl]) if gl else np.zeros((0, 4, 4))
+        per_layer.append(_kron_unitary(n, 1, sub, None, mm))
+    weights = {}
+    for path in itertools.product(range(1 << n), repeat=d):
+        w, prev = 1.0 + 0j, 0
+        for L, s_ in enumerate(path):
+            w *= per_layer[L][s_, prev]
+            prev = s_
+        if abs(w) > 1e-14:
+            weights[path] = abs(w)
+    keys = sorted(weights)
+    p = np.array([weights[k] for k in keys])
+    p /= p.sum()
+    chains = 20000
+    # a table with zero entries is crossed only through penalised states:
+    # 1500 sweeps forget the initial law at J = 4
+    r = oracle.u_gibbs(n, d, g, None, J=4.0, seed=17, chains=chains, sweeps=1500, mats2=m2)
+    idx = _path_index(r["state"], n)
+    key_idx = np.array([_path_index(np.array([k]), n)[0] for k in keys])
+    counts = np.array([np.sum(idx == w) for w in key_idx])
+    assert counts.sum() > 0.3 * chains
+    assert chisquare(counts, p * counts.sum()).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("n,d,seed", [(3, 5, 2), (4, 5, 6)])
+def test_table_circuits_converge_l2(n, d, seed):
+    """No closed-form scale: the L2-normalised estimate (Fig. 2 Step 4)
+    approaches the normalised state vector."""
+    g, m2 = _table_circuit(n, d, seed)
+    exact = oracle.u_statevector(n, d, g, None, mats2=m2)
+    blocks = []
+    for b in range(16):
+        r = oracle.u_gibbs(n, d, g, None, J=4.0, seed=5, chains=128, chain0=128 * b, sweeps=600,
+                           burn_in=100, mats2=m2)
+        blocks.append(r["sum"])
+    blocks = np.array(blocks)
+    tot = blocks.sum(axis=0)
+    est = tot / np.linalg.norm(tot)
+    # batch means of the normalised estimate (normalised per block)
+    per = blocks / np.linalg.norm(blocks, axis=1, keepdims=True)
+    se = per.std(axis=0, ddof=1) / np.sqrt(len(per))
+    assert np.all(np.abs(est - exact) <= 5 * se + 1e-3), (est, exact, se)
+    with pytest.raises(ValueError):  # the exact sampler needs closed-form column sums
+        oracle.u_elim(n, d, g, None, seed=1, chains=32, sweeps=2, mats2=m2)
