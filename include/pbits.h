@@ -76,9 +76,20 @@ typedef enum { PB_H = 0, PB_S = 1, PB_T = 2, PB_CNOT = 3, PB_CZ = 4, PB_U = 5, P
  * CNOT either way).  Every such permutation is affine over GF(2), so each
  * output bit is J-linked to a copy, a complement, or the XOR of the two
  * inputs; an output equal to the complement of the XOR is rejected
- * (PB_EINVAL), as is any gate with a column of more than one nonzero
- * (general two-qubit tables, Eq. ET2, are not supported).  The phase
- * arg U(pi(x), x) of the column taken is added to the path. */
+ * (PB_EINVAL).  The phase arg U(pi(x), x) of the column taken is added to
+ * the path.
+ * A unitary PB_U2 with a column of more than one nonzero is a table gate
+ * (Eq. ET2): both outputs are free; the real energy of the entry taken,
+ * -ln |U(y, x)| (J for a zero entry, the Appendix's e^{-J}), enters through
+ * a second Metropolis factor after the heat-bath proposal (and after the
+ * coupling factor of PB_U neighbours): a flip of chain c with energy change
+ * dE > 0 is kept when u < floor(2^32 e^{-dE}), u = word (c mod 4) of
+ * Philox4x32-10 at (c / 32, t, p | 7 << 16, (c mod 32) / 4).  A path
+ * through a zero entry is invalid; the phase arg U(y, x) is recorded.  The
+ * columns of |U| need not share a sum, so the amplitude scale has no closed
+ * form: pb_model_info's log2z is NaN and pb_run_amplitudes needs
+ * l2_normalize (PB_ESTATE otherwise; Fig. 2 Step 4).  Gibbs runs only
+ * (PB_EINVAL for the exact samplers). */
 /* PB_U: a general one-qubit gate with a caller-given 2x2 complex matrix U
  * (pb_compile_u; Sec. 2 Eq. EB, e.g. the rotated Hadamard of Eq. HadT).  U
  * must be unitary within 1e-9 (max |(U^dagger U - I)_ij|).  Kinds:

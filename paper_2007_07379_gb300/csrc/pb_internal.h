@@ -25,7 +25,8 @@ struct Desc {
   uint16_t dst;   // word index of the p-bit (k*n + q)
   uint8_t mflag;  // bits 0-1: m (links), bit 2: link 0 is the p-bit's own link,
                   // bit 3: coupled (Metropolis acceptance, see Cpl),
-                  // bit 4: general links (a Toffoli's, see GLink)
+                  // bit 4: general links (a Toffoli's, see GLink),
+                  // bit 5: table acceptance (two-qubit tables, see TAcc)
   uint8_t pair;   // threshold pair: 0 (t0,t0) 1 (t1,t1) 2 (t2,t0) 3 (t3,t1)
   uint16_t a[3];
   uint16_t b[3];
@@ -72,6 +73,30 @@ struct GLink {
 };
 static_assert(sizeof(GLink) == 32, "GLink must be 32 bytes");
 
+// Metropolis acceptance of a p-bit next to two-qubit table gates (Eq. ET2),
+// 544 bytes by p: a proposed flip of a chain is kept when bit idx of amask is
+// set or the chain's tag-7 uniform is below thr[idx], idx = the bits of
+// W[w[0..5]] at the chain (the in-table's other output and inputs, the
+// out-table's other input and outputs; ZERO where absent) | old value << 6.
+struct TAcc {
+  uint16_t w[6];
+  uint16_t pad[2];
+  uint32_t amask[4];
+  uint32_t thr[128];
+};
+static_assert(sizeof(TAcc) == 544, "TAcc must be 544 bytes");
+
+// Record entry of a two-qubit table gate (80 bytes): inputs W[wx0], W[wx1],
+// outputs W[wy0], W[wy1]; entry idx = x0 + 2 x1 + 4 (y0 + 2 y1): phase
+// ph[idx] (2^-32 turn), zero entry (an invalid path) when bit idx of zmask.
+struct TRec {
+  uint16_t wx0, wx1, wy0, wy1;
+  uint32_t zmask;
+  uint32_t ph[16];
+  uint32_t pad;
+};
+static_assert(sizeof(TRec) == 80, "TRec must be 80 bytes");
+
 // Phase of one general gate (32 bytes): ph[2 y + x] = arg U_yx in units of
 // 2^-32 turn, y = bit W[wout], x = bit W[win] of the chain.
 struct UPh {
@@ -91,7 +116,7 @@ struct ModelDev {
   int32_t max_col;         // largest colour class
   int32_t wgt;             // 1: PB_U gates (complex phase sums, couplings)
   int32_t n_ug;            // PB_U gates (UPh entries)
-  int32_t pad0;
+  int32_t n_tr;            // two-qubit table gates (TRec entries)
   double log2z;            // log2 of the estimator scale
 };
 
@@ -129,6 +154,8 @@ struct RunModelDev {
   const Cpl* cpl;
   const UPh* uph;
   const GLink* glk;        // models with Toffoli gates, else nullptr
+  const TAcc* tacc;        // models with two-qubit table gates, else nullptr
+  const TRec* trec;
 };
 
 // Workspace header at offset 0.
@@ -152,6 +179,7 @@ constexpr uint32_t kTagMH = 2;
 constexpr uint32_t kTagElim = 4;  // exact sampler's H outputs (tag 3: training rows)
 constexpr uint32_t kTagClamp = 5;  // free draws of the output-clamped exact sampler
 constexpr uint32_t kTagCouple = 6;  // Metropolis acceptance of coupled p-bits
+constexpr uint32_t kTagTable = 7;   // acceptance next to two-qubit tables (per-chain words)
 
 }  // namespace pb
 
@@ -176,6 +204,9 @@ struct pb_model {
   std::vector<pb::UPh> uph;           // one per PB_U gate
   int n_ccx = 0;                      // Toffoli gates
   std::vector<pb::GLink> glk;         // by p (Toffoli models only)
+  int n_tab = 0;                      // two-qubit table gates
+  std::vector<pb::TAcc> tacc;         // by p (table models only)
+  std::vector<pb::TRec> trec;         // one per table gate
 };
 
 // Proposal network (host side of pb_mlp): fp32 master weights, Adam state,

@@ -63,10 +63,12 @@ struct U2Map {
   int dmask[2] = {0, 0}, cbit[2] = {0, 0};
 };
 
-// PB_U2 matrix (32 doubles: Re/Im of <y|U|x>, row-major 4x4): unitary within
-// 1e-9, exactly one nonzero per column, no output equal to the complement
-// of the XOR of both inputs.  false if rejected.
-bool classify_u2(const double* m, U2Map& u) {
+// PB_U2 matrix (32 doubles: Re/Im of <y|U|x>, row-major 4x4), unitary within
+// 1e-9.  Exactly one nonzero per column: an affine permutation (u filled;
+// returns 1) unless an output equals the complement of the XOR of both
+// inputs (returns 0: rejected).  More than one nonzero in some column: a
+// table gate (returns 2).  Not unitary: 0.
+int classify_u2(const double* m, U2Map& u) {
   auto re = [&](int y, int x) { return m[2 * (4 * y + x)]; };
   auto im = [&](int y, int x) { return m[2 * (4 * y + x) + 1]; };
   for (int i = 0; i < 4; ++i)
@@ -76,7 +78,7 @@ bool classify_u2(const double* m, U2Map& u) {
         sr += re(y, i) * re(y, j) + im(y, i) * im(y, j);
         si += re(y, i) * im(y, j) - im(y, i) * re(y, j);
       }
-      if (!(std::fabs(sr - (i == j ? 1.0 : 0.0)) <= 1e-9) || !(std::fabs(si) <= 1e-9)) return false;
+      if (!(std::fabs(sr - (i == j ? 1.0 : 0.0)) <= 1e-9) || !(std::fabs(si) <= 1e-9)) return 0;
     }
   for (int x = 0; x < 4; ++x) {
     int nz = 0;
@@ -85,18 +87,20 @@ bool classify_u2(const double* m, U2Map& u) {
         u.perm[x] = y;
         ++nz;
       }
-    if (nz != 1) return false;
+    if (nz != 1) return 2;
   }
   for (int o = 0; o < 2; ++o) {
     const int c = (u.perm[0] >> o) & 1;
     const int al = ((u.perm[1] >> o) & 1) ^ c, be = ((u.perm[2] >> o) & 1) ^ c;
-    if ((((u.perm[3] >> o) & 1) ^ c) != (al ^ be)) return false;
+    if ((((u.perm[3] >> o) & 1) ^ c) != (al ^ be)) return 0;
     u.dmask[o] = al | (be << 1);
     u.cbit[o] = c;
-    if (u.dmask[o] == 0 || (u.dmask[o] == 3 && c)) return false;
+    if (u.dmask[o] == 0 || (u.dmask[o] == 3 && c)) return 0;
   }
-  return true;
+  return 1;
 }
+
+constexpr int kU2Table = 4;  // Slot.ukind of a two-qubit table gate
 
 enum { kUDiag = 1, kUAnti = 2, kUCoupled = 3 };
 
@@ -228,7 +232,10 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
       if (s0.ukind < 0) return PB_EINVAL;
     }
     if (g.op == PB_U2) {
-      if (!mats || stride < 32 || !classify_u2(mats + (size_t)stride * i, u2map[i])) return PB_EINVAL;
+      if (!mats || stride < 32) return PB_EINVAL;
+      const int k = classify_u2(mats + (size_t)stride * i, u2map[i]);
+      if (k == 0) return PB_EINVAL;
+      if (k == 2) s0.ukind = kU2Table;
     }
     if (two) {
       Slot& s1 = slot[(size_t)g.layer * n + g.q1];
@@ -239,6 +246,7 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
       s1.target = (g.op == PB_CNOT);
       s1.gi = i;
       s1.u2o = 1;
+      s1.ukind = s0.ukind;
     }
   }
 
@@ -261,7 +269,10 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
   auto word = [&](int k, int q) -> uint16_t { return (uint16_t)(k * n + q); };
   // free outputs: H and coupled PB_U; the second word of a single-input
   // link: the CNOT control (target), ONES (anti-diagonal PB_U: NOT), ZERO
-  auto is_free = [](const Slot& s) { return s.op == PB_H || (s.op == PB_U && s.ukind == kUCoupled); };
+  auto table = [](const Slot& s) { return s.op == PB_U2 && s.ukind == kU2Table; };
+  auto is_free = [&](const Slot& s) {
+    return s.op == PB_H || (s.op == PB_U && s.ukind == kUCoupled) || table(s);
+  };
   auto coupled = [](const Slot& s) { return s.op == PB_U && s.ukind == kUCoupled; };
   for (int i = 0; i < n_gates; ++i) {
     if (gates[i].op == PB_U || gates[i].op == PB_U2) {
@@ -273,8 +284,16 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
       m->wgt = true;
       ++m->n_ccx;
     }
+    if (gates[i].op == PB_U2 && table(at(gates[i].layer, gates[i].q0))) ++m->n_tab;
   }
   if (m->n_ccx) m->glk.assign((size_t)n * d, GLink{});
+  if (m->n_tab) m->tacc.assign((size_t)n * d, TAcc{});
+  // energy -ln|U(y, x)| of a table gate's entry, J for a zero entry (Appendix)
+  auto tab_energy = [&](int gi, int y, int x) {
+    const double* mu = mats + (size_t)stride * gi;
+    const double mag = std::hypot(mu[2 * (4 * y + x)], mu[2 * (4 * y + x) + 1]);
+    return mag > 0.0 ? -std::log(mag) : J;
+  };
 
   const int npb = n * d;
   std::vector<Desc> by_p(npb);
@@ -299,7 +318,7 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
       };
       // qubit of input u (0: q0, 1: q1) of the PB_U2 on this slot
       auto u2q = [&](const Slot& s, int u) { return ((s.u2o == 0) == (u == 0)) ? q : s.partner; };
-      if (prod.op == PB_U2) {  // own link: this output's affine map
+      if (prod.op == PB_U2 && !table(prod)) {  // own link: this output's affine map
         const U2Map& um = u2map[prod.gi];
         const int o = prod.u2o, dm = um.dmask[o];
         own = true;
@@ -318,7 +337,7 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
         ++m_links;
       }
       bool tgt_next = false;
-      if (k < d && at(k, q).op == PB_U2) {
+      if (k < d && at(k, q).op == PB_U2 && !table(at(k, q))) {
         // the outputs of the next layer's PB_U2 whose map reads this input
         const Slot& cons = at(k, q);
         const U2Map& um = u2map[cons.gi];
@@ -407,6 +426,49 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
         if (C.flags & 1u) D.mflag |= 8;
         m->cpl.push_back(C);
       }
+      const bool tin = table(prod), tout = k < d && table(at(k, q));
+      if (tin || tout) {  // Metropolis acceptance on the tables' energy
+        TAcc A{};
+        for (int l = 0; l < 6; ++l) A.w[l] = Z;
+        int o = 0, iu = 0, gin = -1, gout = -1;
+        if (tin) {  // this bit is output o of the table of layer k-1
+          gin = prod.gi;
+          const pb_gate& tg = gates[gin];
+          o = prod.u2o;
+          A.w[0] = word(k, o == 0 ? tg.q1 : tg.q0);  // the other output
+          A.w[1] = word(k - 1, tg.q0);
+          A.w[2] = word(k - 1, tg.q1);
+        }
+        if (tout) {  // input iu of the table of layer k
+          const Slot& cs = at(k, q);
+          gout = cs.gi;
+          const pb_gate& tg = gates[gout];
+          iu = cs.u2o;
+          A.w[3] = word(k, iu == 0 ? tg.q1 : tg.q0);  // the other input
+          A.w[4] = word(k + 1, tg.q0);
+          A.w[5] = word(k + 1, tg.q1);
+        }
+        for (int idx = 0; idx < 128; ++idx) {
+          const int ci = idx & 7, co = (idx >> 3) & 7, dir = idx >> 6;
+          double din = 0.0, dout = 0.0;
+          if (tin) {
+            const int yo = ci & 1, xi = (ci >> 1) & 3;
+            const int y1 = o == 0 ? 1 + 2 * yo : yo + 2, y0 = o == 0 ? 2 * yo : yo;
+            din = tab_energy(gin, y1, xi) - tab_energy(gin, y0, xi);
+          }
+          if (tout) {
+            const int xo = co & 1, yi = (co >> 1) & 3;
+            const int x1 = iu == 0 ? 1 + 2 * xo : xo + 2, x0 = iu == 0 ? 2 * xo : xo;
+            dout = tab_energy(gout, yi, x1) - tab_energy(gout, yi, x0);
+          }
+          const double de = din + dout;
+          const double dt = dir == 0 ? de : -de;
+          if (dt <= 0.0) A.amask[idx >> 5] |= 1u << (idx & 31);
+          else A.thr[idx] = u32_threshold(std::exp(-dt));
+        }
+        m->tacc[(size_t)(k - 1) * n + q] = A;
+        D.mflag |= 0x20;
+      }
       static const uint8_t pair_of_m[4] = {0, 1, 2, 3};
       D.pair = pair_of_m[m_links];
       by_p[p] = D;
@@ -474,6 +536,19 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
           join((L - 1) * n + q, L * n + q);
           join(L * n + q, (L - 1) * n + q);
         }
+    // a two-qubit table joins its outputs and inputs pairwise
+    for (int i = 0; i < n_gates; ++i) {
+      const pb_gate& tg = gates[i];
+      if (tg.op != PB_U2 || !table(at(tg.layer, tg.q0))) continue;
+      std::vector<int> vs = {tg.layer * n + tg.q0, tg.layer * n + tg.q1};
+      if (tg.layer >= 1) {
+        vs.push_back((tg.layer - 1) * n + tg.q0);
+        vs.push_back((tg.layer - 1) * n + tg.q1);
+      }
+      for (int a : vs)
+        for (int b : vs)
+          if (a != b) join(a, b);
+    }
     std::vector<int> col(npb, -1);
     std::vector<uint32_t> seen(npb, 0u);
     int ncol = 0;
@@ -496,7 +571,7 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
     }
     if (ncol <= 4)
       for (int p = 0; p < npb; ++p) m->colour[p] = col[p];
-    else if (m->n_ccx)  // the fixed classes cannot separate a Toffoli's four-bit factor
+    else if (m->n_ccx || m->n_tab)  // the fixed classes cannot separate a four-bit factor
       return PB_ERANGE;
   }
 
@@ -514,6 +589,22 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
   for (int i = 0; i < n_gates; ++i) {
     const pb_gate& g = gates[i];
     if (g.op == PB_H) l2z += 0.5;
+    if (g.op == PB_U2 && table(at(g.layer, g.q0))) {  // a table: 16 phases, zero entries
+      TRec R{};
+      const double* mu = mats + (size_t)stride * i;
+      for (int y = 0; y < 4; ++y)
+        for (int x = 0; x < 4; ++x) {
+          const double re = mu[2 * (4 * y + x)], im = mu[2 * (4 * y + x) + 1];
+          R.ph[x + 4 * y] = fixed_turns(re, im);
+          if (re == 0.0 && im == 0.0) R.zmask |= 1u << (x + 4 * y);
+        }
+      R.wx0 = word(g.layer, g.q0);
+      R.wx1 = word(g.layer, g.q1);
+      R.wy0 = word(g.layer + 1, g.q0);
+      R.wy1 = word(g.layer + 1, g.q1);
+      m->trec.push_back(R);
+      continue;
+    }
     if (g.op == PB_U2) {  // phase of the column taken: arg U(pi(x), x), x = x_{q0} + 2 x_{q1}
       UPh P{};
       const double* mu = mats + (size_t)stride * i;
@@ -537,7 +628,9 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
     P.win = word(g.layer, g.q0);
     m->uph.push_back(P);
   }
-  m->log2z = l2z;
+  // tables: the columns of |U| need not share one sum, so sum |U_C| has no
+  // closed form; the estimate is read L2-normalised
+  m->log2z = m->n_tab ? std::nan("") : l2z;
 
   // h, M and the GF(2) rank of the free outputs (H, coupled PB_U) -> s_d
   int h = 0;
@@ -560,7 +653,7 @@ PB_API int pb_compile_g(int n, int d, const pb_gate* gates, int n_gates, const d
           ++var;
         } else if (s.op == PB_CNOT && s.target) {
           for (size_t w = 0; w < nxt[q].size(); ++w) nxt[q][w] = wire[q][w] ^ wire[s.partner][w];
-        } else if (s.op == PB_U2) {  // the linear part of this output's affine map
+        } else if (s.op == PB_U2 && !table(s)) {  // the linear part of this output's affine map
           const int dm = u2map[s.gi].dmask[s.u2o];
           const int qa = s.u2o == 0 ? q : s.partner, qb = s.u2o == 0 ? s.partner : q;  // q0, q1
           for (size_t w = 0; w < nxt[q].size(); ++w)
@@ -613,7 +706,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 
 struct ModelSlots {
   size_t model_dev, desc, rec, init, state, hist, valid, samples, alpha_sorted, alpha_slot, amp,
-      clamp, cpl, uph, glk;
+      clamp, cpl, uph, glk, tacc, trec;
   uint32_t bins, groups, n_batches;
   int clamp_mw;  // mask words per p-bit of the clamp table (0: not clamped)
 };
@@ -718,6 +811,8 @@ int check_cfg(const pb_model* m, const pb_run_cfg& c) {
   if (c.sampler == PB_ELIM_CLAMP && (c.alphas == nullptr || c.n_alphas != 1)) return PB_EINVAL;
   // clamping assumes uniform free outputs: no coupled general gate
   if (c.sampler == PB_ELIM_CLAMP && (m->n_coupled > 0 || m->n_ccx > 0)) return PB_EINVAL;
+  // tables: Gibbs only (the exact sampler would need closed-form column sums)
+  if (c.sampler != PB_GIBBS && m->n_tab > 0) return PB_EINVAL;
   if (c.alphas == nullptr) {
     if (c.n_alphas != 0) return PB_EINVAL;
     if (m->n > 22) return PB_ERANGE;
@@ -776,6 +871,8 @@ int plan(pb_model* const* models, const pb_run_cfg* cfgs, int nm, Layout& L) {
     s.cpl = take(m->wgt ? npb * sizeof(Cpl) : 0);
     s.uph = take(m->uph.size() * sizeof(UPh));
     s.glk = take(m->glk.size() * sizeof(GLink));
+    s.tacc = take(m->tacc.size() * sizeof(TAcc));
+    s.trec = take(m->trec.size() * sizeof(TRec));
   }
   L.work = take((size_t)total_groups * 4);
   L.total = align_up(off, 256);
@@ -963,7 +1060,8 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
     for (int k = 0; k < 4; ++k) md.max_col = std::max(md.max_col, m.col_off[k + 1] - m.col_off[k]);
     md.wgt = m.wgt ? 1 : 0;
     md.n_ug = (int32_t)m.uph.size();
-    md.log2z = m.log2z;
+    md.n_tr = (int32_t)m.trec.size();
+    md.log2z = m.n_tab ? 0.0 : m.log2z;  // tables: unit scale, read L2-normalised
     const size_t npb = (size_t)m.n * m.d;
     if ((e = cudaMemcpyAsync(ws + s.model_dev, &md, sizeof md, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(ws + s.desc, m.desc.data(), npb * sizeof(Desc), cudaMemcpyHostToDevice, st)) ||
@@ -975,7 +1073,11 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
          (!m.uph.empty() && (e = cudaMemcpyAsync(ws + s.uph, m.uph.data(), m.uph.size() * sizeof(UPh),
                                                  cudaMemcpyHostToDevice, st))) ||
          (!m.glk.empty() && (e = cudaMemcpyAsync(ws + s.glk, m.glk.data(), m.glk.size() * sizeof(GLink),
-                                                 cudaMemcpyHostToDevice, st)))))
+                                                 cudaMemcpyHostToDevice, st))) ||
+         (!m.tacc.empty() && (e = cudaMemcpyAsync(ws + s.tacc, m.tacc.data(), m.tacc.size() * sizeof(TAcc),
+                                                  cudaMemcpyHostToDevice, st))) ||
+         (!m.trec.empty() && (e = cudaMemcpyAsync(ws + s.trec, m.trec.data(), m.trec.size() * sizeof(TRec),
+                                                  cudaMemcpyHostToDevice, st)))))
       return PB_ECUDA;
     if (c.alphas) {
       std::vector<int32_t> idx(c.n_alphas);
@@ -1022,6 +1124,10 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
       d.cpl = reinterpret_cast<const Cpl*>(ws + s.cpl);
       d.uph = reinterpret_cast<const UPh*>(ws + s.uph);
       if (!m.glk.empty()) d.glk = reinterpret_cast<const GLink*>(ws + s.glk);
+      if (!m.tacc.empty()) {
+        d.tacc = reinterpret_cast<const TAcc*>(ws + s.tacc);
+        d.trec = reinterpret_cast<const TRec*>(ws + s.trec);
+      }
     }
     if (c.sampler == PB_ELIM_CLAMP) {
       ClampTable t = build_clamp(m, c.alphas[0], s.clamp_mw);
@@ -1205,6 +1311,7 @@ PB_API int pb_run_histogram(const pb_run* r, int model, uint64_t* counts, uint64
 PB_API int pb_run_amplitudes(const pb_run* r, int model, int l2_normalize, double* re, double* im,
                              double* se) {
   if (!r || model < 0 || model >= r->nm || !re || !im) return PB_EINVAL;
+  if (r->models[model]->n_tab && !l2_normalize) return PB_ESTATE;  // no closed-form scale
   const ModelSlots& s = r->L.ms[model];
   cudaError_t e = launch_amplitudes(r->d_rm(), model, s.bins, l2_normalize, r->st);
   if (e != cudaSuccess) return PB_ECUDA;

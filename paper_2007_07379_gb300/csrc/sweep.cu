@@ -259,6 +259,39 @@ __device__ __noinline__ uint32_t glink_heat_bath(const uint32_t* W, const GLink*
   return neg ^ lt;
 }
 
+// Metropolis acceptance of a p-bit next to two-qubit table gates (Eq. ET2),
+// one chain at a time: a lane that would flip keeps the flip when bit idx of
+// the always-mask is set or its tag-7 uniform -- word (lane mod 4) of
+// Philox(g, sweep, p | 7 << 16, lane / 4) -- is below thr[idx], idx = the
+// lane's context bits | its old value << 6 (see TAcc).  Out of line: only
+// p-bits next to a table.
+__device__ __noinline__ uint32_t table_accept(const uint32_t* W, const TAcc* tp, uint32_t old,
+                                              uint32_t prop, uint32_t g, uint32_t sweep,
+                                              uint32_t p, uint32_t k0, uint32_t k1) {
+  const uint32_t flip = old ^ prop;
+  if (flip == 0u) return old;
+  uint32_t cw[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) cw[i] = W[tp->w[i]];
+  uint32_t acc = 0u;
+#pragma unroll 1
+  for (uint32_t grp = 0; grp < 8u; ++grp) {
+    if (((flip >> (4u * grp)) & 0xFu) == 0u) continue;
+    const uint4 r = philox_cold(make_uint4(g, sweep, p | (kTagTable << 16), grp), k0, k1);
+    const uint32_t R[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (uint32_t w = 0; w < 4u; ++w) {
+      const uint32_t l = 4u * grp + w;
+      if (!((flip >> l) & 1u)) continue;
+      uint32_t idx = ((old >> l) & 1u) << 6;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) idx |= ((cw[i] >> l) & 1u) << i;
+      if (((tp->amask[idx >> 5] >> (idx & 31u)) & 1u) || R[w] < tp->thr[idx]) acc |= 1u << l;
+    }
+  }
+  return old ^ (flip & acc);
+}
+
 __device__ __forceinline__ void add3(uint32_t& f0, uint32_t& f1, uint32_t& f2, uint32_t x0,
                                      uint32_t x1, uint32_t x2) {
   const uint32_t c0 = f0 & x0;
@@ -342,6 +375,21 @@ struct Recorder {
   uint32_t phi = 0u;  // general gates: this lane's chain's phase, 2^-32 turn
 
   __device__ void clear() { viol = f0 = f1 = f2 = phi = 0u; }
+
+  // Two-qubit tables lo..hi-1: each adds its entry's phase for the lane's
+  // chain, and a zero entry marks the chain's path invalid.
+  __device__ void read_t(const uint32_t* S, const TRec* tr, int lo, int hi, int lane) {
+    bool bad = false;
+#pragma unroll 1
+    for (int i = lo; i < hi; ++i) {
+      const TRec& R = tr[i];
+      const uint32_t idx = ((S[R.wx0] >> lane) & 1u) | (((S[R.wx1] >> lane) & 1u) << 1) |
+                           (((S[R.wy0] >> lane) & 1u) << 2) | (((S[R.wy1] >> lane) & 1u) << 3);
+      phi += R.ph[idx];
+      bad = bad || ((R.zmask >> idx) & 1u);
+    }
+    viol |= __ballot_sync(0xffffffffu, bad);
+  }
 
   // Phases of general gates lo..hi-1 for the lane's own chain, eight gates
   // per batch with every load of a batch issued before the first use.
@@ -526,7 +574,7 @@ __device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc
                                             int hi, int stride, int n, FastThr fast, uint32_t thr0,
                                             uint32_t thr1, uint32_t thr2, uint32_t thr3,
                                             uint32_t g, uint32_t sweep, uint32_t k0, uint32_t k1,
-                                            const Cpl* cpl, const GLink* glk) {
+                                            const Cpl* cpl, const GLink* glk, const TAcc* tacc) {
   for (int i = lo + first; i < hi; i += stride) {
     Desc D = sdesc[i];
     if (D.mflag & 0x80) continue;
@@ -550,6 +598,10 @@ __device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc
       const uint32_t p = (uint32_t)(D.dst - n);
       v = couple_accept(W, cpl + p, W[D.dst], v, nullptr, g, sweep, p, k0, k1);
     }
+    if (tacc && (D.mflag & 0x20)) {
+      const uint32_t p = (uint32_t)(D.dst - n);
+      v = table_accept(W, tacc + p, W[D.dst], v, g, sweep, p, k0, k1);
+    }
     W[D.dst] = v;
     S[D.dst] = v;
   }
@@ -563,16 +615,17 @@ __device__ __noinline__ void redraw_extra(uint32_t* W, uint32_t* S, const Desc* 
                                           uint32_t thr2, uint32_t thr3, uint32_t g, uint32_t sweep,
                                           uint32_t k0, uint32_t k1) {
   redraw_body(W, S, sdesc, cur, lo, first, hi, stride, n, fast, thr0, thr1, thr2, thr3, g, sweep,
-              k0, k1, nullptr, nullptr);
+              k0, k1, nullptr, nullptr, nullptr);
 }
 __device__ __noinline__ void redraw_extra_coupled(uint32_t* W, uint32_t* S, const Desc* sdesc,
                                                   const uint4* cur, int lo, int first, int hi,
                                                   int stride, int n, FastThr fast, uint32_t thr0,
                                                   uint32_t thr1, uint32_t thr2, uint32_t thr3,
                                                   uint32_t g, uint32_t sweep, uint32_t k0,
-                                                  uint32_t k1, const Cpl* cpl, const GLink* glk) {
+                                                  uint32_t k1, const Cpl* cpl, const GLink* glk,
+                                                  const TAcc* tacc) {
   redraw_body(W, S, sdesc, cur, lo, first, hi, stride, n, fast, thr0, thr1, thr2, thr3, g, sweep,
-              k0, k1, cpl, glk);
+              k0, k1, cpl, glk, tacc);
 }
 
 // Runs `n_sweeps` sweeps (absolute indices sweep0...) of one chain group.
@@ -656,6 +709,15 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     for (int i = tid; i < npb; i += T) bad |= (rm.cpl[i].win >= nw || rm.cpl[i].wout >= nw) ? 1 : 0;
 #pragma unroll 1
     for (int i = tid; i < nug; i += T) bad |= (rm.uph[i].win >= nw || rm.uph[i].wout >= nw) ? 1 : 0;
+    if (rm.tacc) {
+#pragma unroll 1
+      for (int i = tid; i < npb; i += T)
+        for (int l = 0; l < 6; ++l) bad |= rm.tacc[i].w[l] >= nw ? 1 : 0;
+#pragma unroll 1
+      for (int i = tid; i < md.n_tr; i += T)
+        bad |= (rm.trec[i].wx0 >= nw || rm.trec[i].wx1 >= nw || rm.trec[i].wy0 >= nw ||
+                rm.trec[i].wy1 >= nw) ? 1 : 0;
+    }
     if (rm.glk)
 #pragma unroll 1
       for (int i = tid; i < npb; i += T)
@@ -705,6 +767,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       E.m = (uint32_t)m;
       if (WGT && (D.mflag & 8)) E.m |= 0x100u;     // coupled: Metropolis acceptance
       if (WGT && (D.mflag & 0x10)) E.m |= 0x200u;  // general links (Toffoli)
+      if (WGT && (D.mflag & 0x20)) E.m |= 0x400u;  // table acceptance
       E.M0 = m == 0 ? ~0u : 0u;
       E.M1 = m == 1 ? ~0u : 0u;
       E.M2 = m == 2 ? ~0u : 0u;
@@ -793,6 +856,10 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
             v = couple_accept_body(Cp, win_w, wout_w, old_w, v, cur + acc_off + tid * kPreC,
                                    gglob, sweep, p, k0, k1);
           }
+          if (E.m & 0x400u) {  // a second acceptance factor: the tables' energy
+            const uint32_t p = E.dst / 4u - (uint32_t)n;
+            v = table_accept(W, rm.tacc + p, word(E.dst), v, gglob, sweep, p, k0, k1);
+          }
         }
         *reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(W) + E.dst) = v;
         *reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(S) + E.dst) = v;
@@ -801,7 +868,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       if (K > sh.cons) {
         if constexpr (WGT)
           redraw_extra_coupled(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0,
-                               thr1, thr2, thr3, gglob, sweep, k0, k1, rm.cpl, rm.glk);
+                               thr1, thr2, thr3, gglob, sweep, k0, k1, rm.cpl, rm.glk, rm.tacc);
         else
           redraw_extra(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0, thr1, thr2,
                        thr3, gglob, sweep, k0, k1);
@@ -825,6 +892,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         if constexpr (C + 1 < NC) {
           rec.read<WGT>(Sp, srec, C * npb / (NC - 1), (C + 1) * npb / (NC - 1), lane);
           if (wgt_m) rec.read_u(Sp, rm.uph, C * nug / (NC - 1), (C + 1) * nug / (NC - 1), lane);
+          if (WGT && rm.trec)
+            rec.read_t(Sp, rm.trec, C * md.n_tr / (NC - 1), (C + 1) * md.n_tr / (NC - 1), lane);
         } else {
           rec.reduce(Sp, n, d, lane);
           rec.bin<WGT>(rm_g, g, batch, lane, shist, n_valid, n_samples);
@@ -847,6 +916,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       rec.clear();
       rec.read<WGT>(Sl, srec, 0, npb, lane);
       if (wgt_m) rec.read_u(Sl, rm.uph, 0, nug, lane);
+      if (WGT && rm.trec) rec.read_t(Sl, rm.trec, 0, md.n_tr, lane);
       rec.reduce(Sl, n, d, lane);
       rec.bin<WGT>(rm_g, g, batch, lane, shist, n_valid, n_samples);
     }

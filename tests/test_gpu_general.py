@@ -340,3 +340,55 @@ def test_general_run_checkpoint_tune_and_mixed_with_toffoli():
         _, cnt, valid, _ = c.phase_sums(i)
         assert np.array_equal(cnt, ref["cnt"]) and valid == ref["valid"]
         assert np.array_equal(pbits.unslice_state(c.get_state(i), cfgs[i].chains), ref["state"])
+
+
+# ---- two-qubit tables (Eq. ET2): a second Metropolis factor on -ln|U|
+
+def _table_with_u(n, d, seed):
+    """A table circuit whose one-qubit gates are partly random unitaries:
+    p-bits with both a coupling and a table factor."""
+    g, m2 = W.random_table_circuit(n, d, seed)
+    g = g.copy()
+    rng = np.random.default_rng(seed)
+    m1 = np.zeros((len(g), 2, 2), dtype=np.complex128)
+    for i in range(len(g)):
+        if g[i, 0] in (W.H, W.S, W.T) and rng.random() < 0.5:
+            g[i, 0] = W.U
+            m1[i] = W.u3(*(2 * np.pi * rng.random(3)))
+    return g, m1, m2
+
+
+TABLE_CASES = [(3, 5, 2, 256, 30, False), (6, 8, 5, 100, 25, False), (12, 20, 1000, 4096, 5, False),
+               (6, 8, 5, 96, 20, True), (12, 20, 1000, 512, 6, True)]
+
+
+@pytest.mark.parametrize("n,d,seed,chains,sweeps,with_u", TABLE_CASES)
+def test_table_gates_bit_exact_vs_oracle(n, d, seed, chains, sweeps, with_u):
+    if with_u:
+        g, m1, m2 = _table_with_u(n, d, seed)
+    else:
+        (g, m2), m1 = W.random_table_circuit(n, d, seed), None
+    m = pbits.Model(n, d, g, 4.0, mats=m1, mats2=m2)
+    r = pbits.Run([m], [pbits.RunCfg(seed=29, chains=chains)])
+    r.sweeps(sweeps)
+    sums, cnt, valid, samples = r.phase_sums()
+    ref = oracle.u_gibbs(n, d, g, m1, J=4.0, seed=29, chains=chains, sweeps=sweeps, mats2=m2)
+    assert np.array_equal(pbits.unslice_state(r.get_state(), chains), ref["state"])
+    assert np.array_equal(cnt, ref["cnt"]) and valid == ref["valid"] and samples == ref["samples"]
+    n_ph = int(np.sum(g[:, 0] == W.U2) + np.sum(g[:, 0] == W.U))
+    assert np.all(np.abs(sums - ref["sum"]) <= _sum_tol(cnt, n_ph))
+
+
+def test_table_gates_l2_amplitudes_and_rejections():
+    n, d = 3, 5
+    g, m2 = W.random_table_circuit(n, d, 2)
+    exact = oracle.u_statevector(n, d, g, None, mats2=m2)
+    m = pbits.Model(n, d, g, 4.0, mats2=m2)
+    r = pbits.Run([m], [pbits.RunCfg(seed=5, chains=4096, burn_in=100, n_batches=32)])
+    r.sweeps(1500)
+    psi, se = r.amplitudes(l2_normalize=True)
+    assert np.all(np.abs(psi - exact) <= 5 * se + 2e-3), (psi, exact, se)
+    with pytest.raises(pbits.PbError):  # no closed-form scale
+        r.amplitudes(l2_normalize=False)
+    with pytest.raises(pbits.PbError):  # the exact sampler needs closed-form column sums
+        pbits.Run([m], [pbits.RunCfg(seed=1, chains=32, sampler=pbits.PB_ELIM)])

@@ -123,11 +123,21 @@ def test_compile_rejects_unrepresentable_two_qubit_gates():
     for x in range(4):
         x1, x2 = x & 1, x >> 1
         m[(1 ^ x1 ^ x2) | (x2 << 1), x] = 1
-    h = np.kron(np.eye(2), np.array([[1, 1], [1, -1]]) / np.sqrt(2))
-    for bad in (m, h, 2 * W.swap_matrix()):
+    for bad in (m, 2 * W.swap_matrix()):
         with pytest.raises(pbits.PbError):
             pbits.Model(2, 1, g, 3.0, mats2=bad[None])
     pbits.Model(2, 1, g, 3.0, mats2=W.swap_matrix()[None])
+    # a non-permutation unitary is a table gate (Eq. ET2): no closed-form scale
+    h = np.kron(np.eye(2), np.array([[1, 1], [1, -1]]) / np.sqrt(2))
+    assert np.isnan(pbits.Model(2, 1, g, 3.0, mats2=h[None]).info()["log2z"])
+
+
+@pytest.mark.parametrize("n,d,seed", [(3, 5, 2), (6, 8, 5), (12, 20, 1000)])
+def test_compile_table_gates_matches_oracle(n, d, seed):
+    g, m2 = W.random_table_circuit(n, d, seed)
+    m = pbits.Model(n, d, g, 3.0, mats2=m2)
+    assert np.array_equal(m.colours(), oracle.u_colour(n, d, g, None, m2))
+    assert np.isnan(m.info()["log2z"])
 
 
 @pytest.mark.parametrize("n,d,seed", [(4, 5, 2), (6, 8, 3), (12, 20, 1000)])
