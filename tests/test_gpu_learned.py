@@ -112,3 +112,26 @@ def test_trained_proposal_lowers_the_error_at_equal_steps():
     err_l = np.mean(np.abs(psi_l - exact))
     assert np.all(np.abs(psi_l - exact) <= 5 * se_l + 1e-9)
     assert err_l < err_p and np.mean(se_l) < np.mean(se_p), (err_p, err_l, np.mean(se_p), np.mean(se_l))
+
+
+def test_mh_keeps_the_distribution_with_x_gates():
+    """X gates are deterministic links the proposal replays (the suffix's X
+    bits flip): with an untrained network the move still keeps the law, so
+    the amplitudes stay within 5 SE of the general oracle's state vector."""
+    n, d = 4, 6
+    g = W.random_circuit(n, d, 17).copy()
+    for i in range(0, len(g), 2):
+        if g[i, 0] in (W.S, W.T):
+            g[i, 0] = W.X
+    assert np.sum(g[:, 0] == W.X) > 0
+    m, r = _run(n, d, g, W.default_J(n, d, g), 1024, 0x5EED + 17)
+    net = pbits.Mlp(n, d, hidden=64, batch=1024, seed=12)
+    L = pbits.Learned(r, net)
+    for _ in range(2000):
+        L.step(1)
+        r.sweeps(1)
+    psi, se = r.amplitudes()
+    exact = oracle.u_statevector(n, d, g, None)
+    err = np.abs(psi - exact)
+    assert np.all(err <= 5 * se + 1e-9), (err, se)
+    assert 0 < L.accepted < L.proposed

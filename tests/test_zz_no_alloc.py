@@ -54,3 +54,17 @@ def test_noalloc_rejects_oversize():
     with pytest.raises(pbits.PbError) as e:
         pbits.gibbs_run_noalloc(m, pbits.RunCfg(seed=1, chains=1 << 20), 1, counts, totals)
     assert e.value.code == pbits.PB_ERANGE
+
+
+def test_noalloc_rejects_general_gate_models():
+    """Models with general one-qubit gates carry complex phase sums, which
+    the fixed scratch does not hold: the call is refused before any launch."""
+    import torch
+    g, mats = W.random_general_circuit(5, 8, 3, frac_u=0.5)
+    m = pbits.Model(5, 8, g, 3.0, mats=mats)
+    assert m.info()["n_u"] > 0
+    counts = torch.zeros(32 * 8, dtype=torch.int64, device="cuda")
+    totals = torch.zeros(2, dtype=torch.int64, device="cuda")
+    with pytest.raises(pbits.PbError) as e:
+        pbits.gibbs_run_noalloc(m, pbits.RunCfg(seed=1, chains=64), 1, counts, totals)
+    assert e.value.code == pbits.PB_EINVAL
