@@ -1,7 +1,7 @@
 """FP64 reference of the learned proposal network (test infrastructure only).
 
 The paper trains nothing (its weights are "one-shot", from the gate
-matrices); the proposal network is this build's addition to the sampler of
+matrices); the proposal network is an addition to the sampler of
 Fig. 2 Step 1, so its reference is the textbook definition, written plainly:
 
   q(s_j | s_{j-1}, j) = prod_q sigma(l_q)^{s_j[q]} sigma(-l_q)^{1-s_j[q]},
