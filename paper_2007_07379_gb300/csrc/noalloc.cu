@@ -20,7 +20,8 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
                         cudaStream_t st);
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
-                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt = false);
+                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt = false,
+                          bool ext = false);
 size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins,
                         bool wgt = false);
 cudaError_t sweep_prepare();

@@ -21,7 +21,8 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
                         cudaStream_t st);
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
-                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt = false);
+                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt = false,
+                          bool ext = false);
 cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
                                      uint32_t n_work, uint32_t n_sweeps, int cons, int prod,
                                      int max_col, int nc, int grid, size_t smem_bytes,
@@ -896,6 +897,7 @@ struct pb_run {
   size_t smem = 0;
   bool persistent = false;
   bool wgt = false;        // some model has PB_U gates (the general-gate kernels)
+  bool ext = false;        // some model has Toffoli links or two-qubit tables
   int nc = 2;              // colour steps per sweep (largest over the models)
   bool elim = false;       // exact-sampler run: i.i.d. paths instead of sweeps
   size_t elim_smem = 0;
@@ -1025,6 +1027,7 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
     if (exact(cfgs[i].sampler) != exact(cfgs[0].sampler)) return PB_EINVAL;
   r->elim = exact(cfgs[0].sampler);
   for (auto& m : r->models) r->wgt = r->wgt || m->wgt;
+  for (auto& m : r->models) r->ext = r->ext || m->n_ccx > 0 || m->n_tab > 0;
   for (auto& m : r->models)
     for (int c = 0; c < 4; ++c)
       if (m->col_off[c + 1] > m->col_off[c]) r->nc = std::max(r->nc, c + 1);
@@ -1202,7 +1205,7 @@ PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
                                    r->grid, r->smem, r->hdr(), r->cap_st);
     else
       e = launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->cons, r->prod, r->max_col,
-                        r->nc, r->smem, r->hdr(), r->cap_st, r->wgt);
+                        r->nc, r->smem, r->hdr(), r->cap_st, r->wgt, r->ext);
     cudaError_t e2 = cudaStreamEndCapture(r->cap_st, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);

@@ -632,8 +632,10 @@ __device__ __noinline__ void redraw_extra_coupled(uint32_t* W, uint32_t* S, cons
 // NC = colour steps per sweep (2..4; the model's classes NC.. are empty).
 // WGT: the instantiation for runs with general-gate models (coupled p-bits
 // get the Metropolis acceptance, records add FP64 phases); plain models run
-// through it unchanged.
-template <int NC, bool WGT>
+// through it unchanged.  EXT (with WGT): some model also has Toffoli links
+// or two-qubit tables; without them those paths are compiled out, so the
+// coupled-gate consumers and the recorder keep their shorter code.
+template <int NC, bool WGT, bool EXT>
 __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, uint32_t n_sweeps,
                           Shape sh, int max_col_all, uint32_t* smem, WsHeader* hdr) {
   // run and model constants held in registers for the whole launch
@@ -683,6 +685,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     bool ok = D.dst < nw;
 #pragma unroll
     for (int l = 0; l < 3; ++l) ok = ok && D.a[l] < nw && D.b[l] < nw;
+    if (!EXT && (D.mflag & 0x30)) ok = false;  // Toffoli / table p-bit: needs EXT
     if (!ok) {  // never write through a bad index: the entry is skipped
       set_status(hdr, PB_EINVAL);
       D.mflag = 0x80;
@@ -766,8 +769,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       E.dst = 4u * D.dst;
       E.m = (uint32_t)m;
       if (WGT && (D.mflag & 8)) E.m |= 0x100u;     // coupled: Metropolis acceptance
-      if (WGT && (D.mflag & 0x10)) E.m |= 0x200u;  // general links (Toffoli)
-      if (WGT && (D.mflag & 0x20)) E.m |= 0x400u;  // table acceptance
+      if (EXT && (D.mflag & 0x10)) E.m |= 0x200u;  // general links (Toffoli)
+      if (EXT && (D.mflag & 0x20)) E.m |= 0x400u;  // table acceptance
       E.M0 = m == 0 ? ~0u : 0u;
       E.M1 = m == 1 ? ~0u : 0u;
       E.M2 = m == 2 ? ~0u : 0u;
@@ -844,7 +847,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
           }
         }
         uint32_t v;
-        if (WGT && (E.m & 0x200u))
+        if (EXT && (E.m & 0x200u))
           v = glink_heat_bath(W, rm.glk + (E.dst / 4u - (uint32_t)n), rp, thr0, thr1, thr2, thr3,
                               gglob, sweep, pidx, k0, k1);
         else
@@ -856,7 +859,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
             v = couple_accept_body(Cp, win_w, wout_w, old_w, v, cur + acc_off + tid * kPreC,
                                    gglob, sweep, p, k0, k1);
           }
-          if (E.m & 0x400u) {  // a second acceptance factor: the tables' energy
+          if (EXT && (E.m & 0x400u)) {  // a second acceptance factor: the tables' energy
             const uint32_t p = E.dst / 4u - (uint32_t)n;
             v = table_accept(W, rm.tacc + p, word(E.dst), v, gglob, sweep, p, k0, k1);
           }
@@ -868,7 +871,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       if (K > sh.cons) {
         if constexpr (WGT)
           redraw_extra_coupled(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0,
-                               thr1, thr2, thr3, gglob, sweep, k0, k1, rm.cpl, rm.glk, rm.tacc);
+                               thr1, thr2, thr3, gglob, sweep, k0, k1, rm.cpl,
+                               EXT ? rm.glk : nullptr, EXT ? rm.tacc : nullptr);
         else
           redraw_extra(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0, thr1, thr2,
                        thr3, gglob, sweep, k0, k1);
@@ -890,9 +894,9 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         const uint32_t* Sp = smem + iw * (1 + ((s + 1u) & 1u));
         if constexpr (C == 0) rec.clear();
         if constexpr (C + 1 < NC) {
-          rec.read<WGT>(Sp, srec, C * npb / (NC - 1), (C + 1) * npb / (NC - 1), lane);
+          rec.read<EXT>(Sp, srec, C * npb / (NC - 1), (C + 1) * npb / (NC - 1), lane);
           if (wgt_m) rec.read_u(Sp, rm.uph, C * nug / (NC - 1), (C + 1) * nug / (NC - 1), lane);
-          if (WGT && rm.trec)
+          if (EXT && rm.trec)
             rec.read_t(Sp, rm.trec, C * md.n_tr / (NC - 1), (C + 1) * md.n_tr / (NC - 1), lane);
         } else {
           rec.reduce(Sp, n, d, lane);
@@ -914,9 +918,9 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     if (n_sweeps > 0 && recorded(sweep0 + n_sweeps - 1)) {
       const uint32_t* Sl = smem + iw * (1 + ((n_sweeps - 1u) & 1u));
       rec.clear();
-      rec.read<WGT>(Sl, srec, 0, npb, lane);
+      rec.read<EXT>(Sl, srec, 0, npb, lane);
       if (wgt_m) rec.read_u(Sl, rm.uph, 0, nug, lane);
-      if (WGT && rm.trec) rec.read_t(Sl, rm.trec, 0, md.n_tr, lane);
+      if (EXT && rm.trec) rec.read_t(Sl, rm.trec, 0, md.n_tr, lane);
       rec.reduce(Sl, n, d, lane);
       rec.bin<WGT>(rm_g, g, batch, lane, shist, n_valid, n_samples);
     }
@@ -957,7 +961,7 @@ constexpr int kMaxThreads = 608;  // 224 consumers + 352 producers + 1 recorder 
 // recorder paths get 128 registers.
 constexpr int kMaxThreadsWgt = 512;
 
-template <int NC, bool WGT>
+template <int NC, bool WGT, bool EXT>
 __global__ void __launch_bounds__(WGT ? kMaxThreadsWgt : kMaxThreads) sweep_kernel(const RunModelDev* __restrict__ rm,
                                                      int n_models, uint32_t total_groups,
                                                      uint32_t n_sweeps, Shape sh, int max_col,
@@ -970,7 +974,7 @@ __global__ void __launch_bounds__(WGT ? kMaxThreadsWgt : kMaxThreads) sweep_kern
   const RunModelDev& r = rm[mi];
   const uint32_t g = flat - r.group_base;
   if (g >= r.groups) return;
-  run_group<NC, WGT>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
+  run_group<NC, WGT, EXT>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
 }
 
 // Persistent form: a fixed grid pops (model, group) items from a
@@ -992,7 +996,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_persistent_kernel(
     const int mi = find_model(rm, n_models, flat);
     const RunModelDev& r = rm[mi];
     const uint32_t g = flat - r.group_base;
-    if (g < r.groups) run_group<NC, false>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
+    if (g < r.groups) run_group<NC, false, false>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
   }
 }
 
@@ -1351,24 +1355,29 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
 __global__ void advance_kernel(WsHeader* hdr, uint32_t n_sweeps) { hdr->sweep0 += n_sweeps; }
 
 // nc: colour steps per sweep (the largest over the launch's models; 2..4).
-// wgt: some model has general one-qubit gates (the WGT instantiation).
+// wgt: some model has general gates (the WGT instantiation); ext: some model
+// has Toffoli links or two-qubit tables (EXT).
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
-                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt) {
+                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt, bool ext) {
   const int threads = cons + prod + 32;
   const Shape sh{cons, prod};
   auto go = [&](auto kern) {
     kern<<<total_groups, threads, smem_bytes, st>>>(d_rm, n_models, total_groups, n_sweeps, sh,
                                                     max_col, hdr);
   };
-  if (wgt) {
-    if (nc <= 2) go(sweep_kernel<2, true>);
-    else if (nc == 3) go(sweep_kernel<3, true>);
-    else go(sweep_kernel<4, true>);
+  if (wgt && ext) {
+    if (nc <= 2) go(sweep_kernel<2, true, true>);
+    else if (nc == 3) go(sweep_kernel<3, true, true>);
+    else go(sweep_kernel<4, true, true>);
+  } else if (wgt) {
+    if (nc <= 2) go(sweep_kernel<2, true, false>);
+    else if (nc == 3) go(sweep_kernel<3, true, false>);
+    else go(sweep_kernel<4, true, false>);
   } else {
-    if (nc <= 2) go(sweep_kernel<2, false>);
-    else if (nc == 3) go(sweep_kernel<3, false>);
-    else go(sweep_kernel<4, false>);
+    if (nc <= 2) go(sweep_kernel<2, false, false>);
+    else if (nc == 3) go(sweep_kernel<3, false, false>);
+    else go(sweep_kernel<4, false, false>);
   }
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
@@ -1440,12 +1449,15 @@ cudaError_t sweep_prepare() {
   const int big = (int)kSweepSmemMax;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(sweep_kernel<2, false>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<3, false>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<4, false>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<2, true>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<3, true>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<4, true>, a, big)) != cudaSuccess ||
+  if ((e = cudaFuncSetAttribute(sweep_kernel<2, false, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3, false, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4, false, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<2, true, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3, true, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4, true, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<2, true, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3, true, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4, true, true>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_persistent_kernel<2>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_persistent_kernel<3>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_persistent_kernel<4>, a, big)) != cudaSuccess)
