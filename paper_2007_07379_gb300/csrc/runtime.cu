@@ -29,8 +29,8 @@ cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, cons
                                      WsHeader* hdr, cudaStream_t st);
 cudaError_t launch_elim(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                         const uint32_t* const* d_init_tabs, uint32_t n_sweeps, size_t smem_bytes,
-                        WsHeader* hdr, cudaStream_t st, bool wgt);
-size_t elim_smem_bytes(int n, int d, int zwords);
+                        WsHeader* hdr, cudaStream_t st, bool wgt, int warps);
+size_t elim_smem_bytes(int n, int d, int zwords, int warps);
 cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
                               cudaStream_t st);
 cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t count,
@@ -901,6 +901,7 @@ struct pb_run {
   int nc = 2;              // colour steps per sweep (largest over the models)
   bool elim = false;       // exact-sampler run: i.i.d. paths instead of sweeps
   size_t elim_smem = 0;
+  int elim_warps = 8;      // exact samplers: warps per CTA (8, 16 or 32)
   std::vector<std::vector<uint32_t>> clamp_keep;
   int grid = 0;
   uint64_t sweeps_done = 0;
@@ -1031,8 +1032,6 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
   for (auto& m : r->models)
     for (int c = 0; c < 4; ++c)
       if (m->col_off[c + 1] > m->col_off[c]) r->nc = std::max(r->nc, c + 1);
-  for (auto& m : r->models)
-    r->elim_smem = std::max(r->elim_smem, elim_smem_bytes(m->n, m->d, (m->h + 3) & ~3));
 
   cudaStream_t st = r->st;
   char* ws = r->ws;
@@ -1150,6 +1149,24 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
     r->flips_per_sweep += (double)c.chains * (double)npb;
   }
   r->total_groups = base;
+  // Exact samplers: warps per CTA.  Samples are independent, so a CTA with
+  // more warps hides more latency; 32 while the groups leave SMs free, 16 up
+  // to two groups per SM, else 8 (several CTAs per SM do the same), and
+  // fewer when the per-warp images do not fit.
+  if (r->elim) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int ew = r->total_groups <= (uint32_t)sms ? 32 : (r->total_groups <= 2u * (uint32_t)sms ? 16 : 8);
+    auto smem_for = [&](int w) {
+      size_t b = 0;
+      for (auto& m : r->models) b = std::max(b, elim_smem_bytes(m->n, m->d, (m->h + 3) & ~3, w));
+      return b;
+    };
+    while (ew > 8 && smem_for(ew) > kSweepSmemMax) ew /= 2;
+    r->elim_warps = ew;
+    r->elim_smem = smem_for(ew);
+  }
   // Work list for the persistent launch: longest first (LPT order).
   std::stable_sort(cost.begin(), cost.end(),
                    [](const std::pair<double, uint32_t>& a, const std::pair<double, uint32_t>& b) {
@@ -1198,7 +1215,7 @@ PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
     if (r->elim)
       e = launch_elim(r->d_rm(), r->nm, r->total_groups,
                       reinterpret_cast<const uint32_t* const*>(r->ws + r->L.init_ptrs), n_sweeps,
-                      r->elim_smem, r->hdr(), r->cap_st, r->wgt);
+                      r->elim_smem, r->hdr(), r->cap_st, r->wgt, r->elim_warps);
     else if (r->persistent)
       e = launch_sweeps_persistent(r->d_rm(), r->nm, reinterpret_cast<const uint32_t*>(r->ws + r->L.work),
                                    r->total_groups, n_sweeps, r->cons, r->prod, r->max_col, r->nc,

@@ -1057,18 +1057,18 @@ __global__ void init_kernel(const RunModelDev* __restrict__ rm, int n_models,
 // sample t is bit (c mod 32) of word 0 of Philox(c / 32, t, p | 4 << 16, 0),
 // every other bit the XOR of two words given by the init table -- and
 // records it (Fig. 2 Step 3; every path is valid).  One CTA per chain group;
-// warp w takes the launch's samples w, w + kElimWarps, ... in its own
-// shared-memory image; lane q writes word q of a layer.
+// warp w of the NW takes the launch's samples w, w + NW, ... in its own
+// shared-memory image; lane q writes word q of a layer.  The samples are
+// independent, so NW only sets how much latency a CTA can hide: the run
+// takes 32 warps when its groups do not fill the SMs, 16 or 8 when they do.
 // Output-clamped models (clamp_tab set): the sample's free draws z_b are
 // bit c % 32 of word b % 4 of Philox(c / 32, t, (b / 4) | 5 << 16, 0), and an
 // H output is its table constant XOR the z_b of its mask (GF(2) elimination
 // on the host), so every path ends at the clamped output.
-constexpr int kElimWarps = 8;
-
 // WGT: the instantiation for runs with general-gate models (coupled coins,
 // phasor records); plain runs take the plain one.
-template <bool WGT>
-__global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
+template <bool WGT, int NW>
+__global__ void __launch_bounds__(NW * 32) elim_kernel(
     const RunModelDev* __restrict__ rm, int n_models, uint32_t total_groups,
     const uint32_t* const* __restrict__ init_tabs, uint32_t n_sweeps, int wstride, WsHeader* hdr) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -1120,7 +1120,7 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
   Recorder rec;
   unsigned long long n_valid = 0ull, n_samples = 0ull;
 #pragma unroll 1
-  for (uint32_t i = (uint32_t)warp; i < n_sweeps; i += kElimWarps) {
+  for (uint32_t i = (uint32_t)warp; i < n_sweeps; i += (uint32_t)NW) {
     const uint32_t t = sweep0 + i;
     if (!recorded(t)) continue;
     if (ctab) {
@@ -1201,7 +1201,7 @@ __global__ void __launch_bounds__(kElimWarps * 32) elim_kernel(
   int last = -1;
   for (int i = (int)n_sweeps - 1; i >= 0; --i)
     if (recorded(sweep0 + (uint32_t)i)) { last = i; break; }
-  if (last >= 0 && warp == last % kElimWarps) {
+  if (last >= 0 && warp == last % NW) {
     uint32_t* out = r.state + (size_t)g * npb;
     for (int i = lane; i < npb; i += 32) out[i] = W[n + i];
   }
@@ -1404,24 +1404,33 @@ cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, cons
   return cudaGetLastError();
 }
 
-// smem_bytes from elim_smem_bytes: kElimWarps equal per-warp regions
+// smem_bytes from elim_smem_bytes(.., warps): `warps` (8, 16 or 32) equal
+// per-warp regions.
 cudaError_t launch_elim(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                         const uint32_t* const* d_init_tabs, uint32_t n_sweeps, size_t smem_bytes,
-                        WsHeader* hdr, cudaStream_t st, bool wgt) {
-  const int wstride = (int)(smem_bytes / (4 * kElimWarps));
-  if (wgt)
-    elim_kernel<true><<<total_groups, kElimWarps * 32, smem_bytes, st>>>(
-        d_rm, n_models, total_groups, d_init_tabs, n_sweeps, wstride, hdr);
-  else
-    elim_kernel<false><<<total_groups, kElimWarps * 32, smem_bytes, st>>>(
-        d_rm, n_models, total_groups, d_init_tabs, n_sweeps, wstride, hdr);
+                        WsHeader* hdr, cudaStream_t st, bool wgt, int warps) {
+  if (warps != 8 && warps != 16 && warps != 32) return cudaErrorInvalidValue;
+  const int wstride = (int)(smem_bytes / (4 * (size_t)warps));
+  auto go = [&](auto kern) {
+    kern<<<total_groups, warps * 32, smem_bytes, st>>>(d_rm, n_models, total_groups, d_init_tabs,
+                                                       n_sweeps, wstride, hdr);
+  };
+  if (wgt) {
+    if (warps == 32) go(elim_kernel<true, 32>);
+    else if (warps == 16) go(elim_kernel<true, 16>);
+    else go(elim_kernel<true, 8>);
+  } else {
+    if (warps == 32) go(elim_kernel<false, 32>);
+    else if (warps == 16) go(elim_kernel<false, 16>);
+    else go(elim_kernel<false, 8>);
+  }
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
 }
 
 // Per warp: the path image and up to `zwords` free draws (16-byte multiples).
-size_t elim_smem_bytes(int n, int d, int zwords) {
-  return (size_t)kElimWarps * (size_t)(image_words(n, d) + ((zwords + 3) & ~3)) * 4;
+size_t elim_smem_bytes(int n, int d, int zwords, int warps) {
+  return (size_t)warps * (size_t)(image_words(n, d) + ((zwords + 3) & ~3)) * 4;
 }
 
 cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
@@ -1462,8 +1471,13 @@ cudaError_t sweep_prepare() {
       (e = cudaFuncSetAttribute(sweep_persistent_kernel<3>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_persistent_kernel<4>, a, big)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(elim_kernel<false>, a, big)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(elim_kernel<true>, a, big);
+  if ((e = cudaFuncSetAttribute(elim_kernel<false, 8>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(elim_kernel<false, 16>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(elim_kernel<false, 32>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(elim_kernel<true, 8>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(elim_kernel<true, 16>, a, big)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(elim_kernel<true, 32>, a, big);
 }
 
 int sweep_max_blocks_per_sm(int threads, size_t smem) {
