@@ -28,9 +28,13 @@ def _elim_run(n, d, g, seed, chains, alphas=None, burn_in=0, record_every=1, n_b
     return m, pbits.Run([m], [cfg])
 
 
+# chain groups (chains / 32) against the SM count (152 on GB300) pick the
+# kernel's warps per CTA: up to 152 groups 32 warps, up to 304 16, else 8;
+# 9600 and 12800 chains (300, 400 groups) take the 16- and 8-warp kernels
 @pytest.mark.parametrize("n,d,cseed,chains,sweeps", [(3, 4, 0, 1024, 50), (5, 8, 21, 100, 33),
                                                      (12, 20, 1000, 4096, 6), (1, 6, -1, 64, 40),
-                                                     (32, 64, 3, 40, 3), (6, 1, 4, 33, 7)])
+                                                     (32, 64, 3, 40, 3), (6, 1, 4, 33, 7),
+                                                     (5, 8, 22, 9600, 37), (5, 8, 23, 12800, 13)])
 def test_bit_exact_vs_oracle(n, d, cseed, chains, sweeps):
     g = W.hadamard_chain(d) if cseed < 0 else W.random_circuit(n, d, cseed)
     alphas = np.arange(16, dtype=np.uint32) if n > 20 else None
@@ -112,7 +116,8 @@ def _clamp_cfg(seed, chains, alpha, n_batches=8, sampler=None):
 
 
 @pytest.mark.parametrize("n,d,cseed,chains,sweeps", [(4, 8, 17, 300, 20), (5, 6, 3, 64, 9),
-                                                     (12, 20, 1000, 4096, 4)])
+                                                     (12, 20, 1000, 4096, 4), (4, 8, 18, 9600, 19),
+                                                     (4, 8, 19, 12800, 11)])
 def test_clamped_bit_exact_vs_oracle(n, d, cseed, chains, sweeps):
     g = W.random_circuit(n, d, cseed)
     exact = oracle.statevector(n, d, g)

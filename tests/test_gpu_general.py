@@ -116,8 +116,10 @@ def test_global_histogram_path():
     assert np.all(np.abs(sums - ref["sum"]) <= _sum_tol(cnt, int(np.sum(g[:, 0] == W.U))))
 
 
+# 9600 / 12800 chains: 300 / 400 groups, the 16- and 8-warp exact-sampler kernels
 @pytest.mark.parametrize("kind,n,d,seed,chains,sweeps", [("gen", 3, 5, 7, 300, 20), ("rot", 1, 10, 1, 64, 30),
-                                                         ("gen", 12, 20, 1000, 4096, 4)])
+                                                         ("gen", 12, 20, 1000, 4096, 4),
+                                                         ("gen", 5, 8, 11, 9600, 9), ("gen", 5, 8, 12, 12800, 7)])
 def test_elim_bit_exact_vs_oracle(kind, n, d, seed, chains, sweeps):
     g, mats = _circuit(kind, n, d, seed)
     m = pbits.Model(n, d, g, 3.0, mats=mats)
