@@ -378,6 +378,23 @@ PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, voi
                          size_t workspace_bytes, uintptr_t stream, pb_mlp** out);
 /* dims[6] = n, d, hidden, k_in, batch, number of fp32 parameters. */
 PB_API int pb_mlp_info(const pb_mlp* mlp, int* dims);
+/* Failure detection of the network's kernels.  Every wait in them for the
+ * tensor cores or a bulk copy is bounded; a wait that runs out leaves the
+ * kernel (after draining what it started) and sets PB_ETIMEOUT in a status
+ * word of the network's workspace.  *status receives that word (PB_OK = 0,
+ * else PB_ETIMEOUT); clear != 0 resets it.  Synchronizes the network's
+ * stream; call it after the launches that used the network (forward,
+ * backward, training, MH moves on a run's stream) have completed.
+ * Errors: PB_EINVAL (NULL), PB_ECUDA. */
+PB_API int pb_mlp_status(pb_mlp* mlp, int clear, int* status);
+/* Self-test of that bounded wait, with nothing else in flight: one thread
+ * initialises a one-arrival mbarrier, arrives on it (arrive != 0) or not,
+ * and waits for its first phase for at most max_iters tries (1 .. 2^20).
+ * *status receives PB_OK when the wait completed, PB_ETIMEOUT when it ran
+ * out (arrive == 0).  Runs on the default stream and synchronizes the
+ * device; calls must not overlap (one status word in the library).
+ * Errors: PB_EINVAL (NULL status, max_iters out of range), PB_ECUDA. */
+PB_API int pb_selftest_wait(int arrive, uint32_t max_iters, int* status);
 /* Flat fp32 parameters W1 [h x k_in], b1, W2 [h x h], b2, W3 [npad x h]
  * (npad = n rounded up to 16; rows >= n are zero), b3 [npad].  get != 0
  * reads them to host, get == 0 loads them.  Synchronous. */

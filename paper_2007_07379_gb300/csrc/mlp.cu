@@ -168,6 +168,29 @@ cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t st) {
 
 }  // namespace pb
 
+namespace pb {
+
+// Self-test of the bounded wait every tensor-core kernel here uses: one
+// thread initialises a one-arrival mbarrier, arrives on it or not, and
+// waits for its first phase with tc::mbar_wait(max_iters).  A wait that runs
+// out records PB_ETIMEOUT in the status word the way the GEMM and fused
+// kernels do; nothing else (no MMA, no copy, no tensor memory) is in flight.
+__device__ uint32_t g_selftest_status;
+
+__global__ void selftest_wait_kernel(int arrive, uint32_t max_iters) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&mbar, 1u);
+  if (arrive) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&mbar)) : "memory");
+  }
+  const bool ok = tc::mbar_wait(&mbar, 0u, max_iters);
+  if (!ok) atomicCAS(&g_selftest_status, 0u, (uint32_t)PB_ETIMEOUT);
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(tc::smem_u32(&mbar)) : "memory");
+}
+
+}  // namespace pb
+
 using namespace pb;
 
 extern "C" PB_API int pb_gemm_bf16(const void* dA, int lda, const void* dB, int ldb, void* dD,
@@ -329,7 +352,7 @@ namespace {
 
 struct MlpLayout {
   size_t w, m, v, g, W1, W2, W3, W2t, W3t, W1p, W2p, W3p, X, Xt, H1, H1t, H2, H2t, dY, dYt, dZ2,
-      dZ2t, dZ1, dZ1t, logits, target, loss, total;
+      dZ2t, dZ1, dZ1t, logits, target, loss, status, total;
 };
 
 MlpLayout mlp_layout(int kin, int H, int npad, int B) {
@@ -369,6 +392,7 @@ MlpLayout mlp_layout(int kin, int H, int npad, int B) {
   L.logits = take((size_t)B * npad * 4);
   L.target = take((size_t)B * npad * 4);
   L.loss = take(256);
+  L.status = take(16);
   L.total = (p + 255) & ~(size_t)255;
   return L;
 }
@@ -385,7 +409,7 @@ int mlp_dims(int n, int d, int hidden, int batch, int* kin, int* npad) {
 // GEMM helper: D = epi(A[M x K] B[N x K]^T)
 cudaError_t mm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, void* D, int ldd,
                int M, int N, int K, int flags, const float* bias, const __nv_bfloat16* mask,
-               int ldm, cudaStream_t st) {
+               int ldm, cudaStream_t st, uint32_t* status) {
   pb::GemmArgs g{};
   g.A = A;
   g.B = B;
@@ -401,7 +425,7 @@ cudaError_t mm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
   g.K = K;
   g.flags = flags;
   g.alpha = 1.f;
-  g.status = nullptr;
+  g.status = status;
   return pb::launch_gemm_bf16(g, st);
 }
 
@@ -432,13 +456,13 @@ cudaError_t mlp_fwd(pb_mlp* p, int rows) {
   cudaError_t e;
   const int flags = pb::kEpiRelu | pb::kEpiOutBf16;
   if ((e = mm(p->X, p->kin, p->W1, p->kin, p->H1, p->H, rows, p->H, p->kin, flags,
-              p->w + p->off_b1, nullptr, 0, p->st)) != cudaSuccess)
+              p->w + p->off_b1, nullptr, 0, p->st, p->status)) != cudaSuccess)
     return e;
   if ((e = mm(p->H1, p->H, p->W2, p->H, p->H2, p->H, rows, p->H, p->H, flags, p->w + p->off_b2,
-              nullptr, 0, p->st)) != cudaSuccess)
+              nullptr, 0, p->st, p->status)) != cudaSuccess)
     return e;
   return mm(p->H2, p->H, p->W3, p->H, p->logits, p->npad, rows, p->npad, p->H, 0,
-            p->w + p->off_b3, nullptr, 0, p->st);
+            p->w + p->off_b3, nullptr, 0, p->st, p->status);
 }
 
 // Backward of the mean BCE over `rows` (targets in p->target): gradients
@@ -455,26 +479,26 @@ cudaError_t mlp_bwd(pb_mlp* p, int rows) {
   if ((e = pb::transpose_bf16(p->X, B, p->kin, p->Xt, p->st)) != cudaSuccess) return e;
   // gW3 = dY^T H2
   if ((e = mm(p->dYt, B, p->H2t, B, p->g + p->off_W3, H, p->npad, H, B, 0, nullptr, nullptr, 0,
-              p->st)) != cudaSuccess)
+              p->st, p->status)) != cudaSuccess)
     return e;
   // dZ2 = (dY W3) * [H2 > 0]
   if ((e = mm(p->dY, p->npad, p->W3t, p->npad, p->dZ2, H, B, H, p->npad,
-              pb::kEpiMask | pb::kEpiOutBf16, nullptr, p->H2, H, p->st)) != cudaSuccess)
+              pb::kEpiMask | pb::kEpiOutBf16, nullptr, p->H2, H, p->st, p->status)) != cudaSuccess)
     return e;
   if ((e = pb::transpose_bf16(p->dZ2, B, H, p->dZ2t, p->st)) != cudaSuccess) return e;
   // gW2 = dZ2^T H1, gb2 = column sums of dZ2
   if ((e = mm(p->dZ2t, B, p->H1t, B, p->g + p->off_W2, H, H, H, B, 0, nullptr, nullptr, 0,
-              p->st)) != cudaSuccess)
+              p->st, p->status)) != cudaSuccess)
     return e;
   pb::rowsum_bf16_kernel<<<(H + 7) / 8, 256, 0, p->st>>>(p->dZ2t, H, B, p->g + p->off_b2);
   // dZ1 = (dZ2 W2) * [H1 > 0]
   if ((e = mm(p->dZ2, H, p->W2t, H, p->dZ1, H, B, H, H, pb::kEpiMask | pb::kEpiOutBf16, nullptr,
-              p->H1, H, p->st)) != cudaSuccess)
+              p->H1, H, p->st, p->status)) != cudaSuccess)
     return e;
   if ((e = pb::transpose_bf16(p->dZ1, B, H, p->dZ1t, p->st)) != cudaSuccess) return e;
   // gW1 = dZ1^T X, gb1 = column sums of dZ1
   if ((e = mm(p->dZ1t, B, p->Xt, B, p->g + p->off_W1, p->kin, H, p->kin, B, 0, nullptr, nullptr,
-              0, p->st)) != cudaSuccess)
+              0, p->st, p->status)) != cudaSuccess)
     return e;
   pb::rowsum_bf16_kernel<<<(H + 7) / 8, 256, 0, p->st>>>(p->dZ1t, H, B, p->g + p->off_b1);
   return cudaGetLastError();
@@ -546,6 +570,7 @@ PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, voi
   p->dZ2 = (__nv_bfloat16*)(b + L.dZ2); p->dZ2t = (__nv_bfloat16*)(b + L.dZ2t);
   p->dZ1 = (__nv_bfloat16*)(b + L.dZ1); p->dZ1t = (__nv_bfloat16*)(b + L.dZ1t);
   p->logits = (float*)(b + L.logits); p->target = (float*)(b + L.target); p->loss = (float*)(b + L.loss);
+  p->status = (uint32_t*)(b + L.status);
   // Initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64(seed), biases 0.
   std::vector<float> w(p->n_params, 0.f);
   uint64_t s = seed;
@@ -567,15 +592,37 @@ PB_API int pb_mlp_create(int n, int d, int hidden, int batch, uint64_t seed, voi
   fill(p->off_W1, hidden, kin, n + d, hidden, n + d);
   fill(p->off_W2, hidden, hidden, hidden, hidden, hidden);
   fill(p->off_W3, npad, hidden, hidden, n, hidden);
-  cudaError_t e;
-  if ((e = pb::mlp_prepare()) != cudaSuccess ||
-      (e = cudaMemsetAsync(p->ws, 0, L.total, p->st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(p->w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, p->st)) != cudaSuccess ||
-      (e = refresh_bf16(p)) != cudaSuccess || (e = cudaStreamSynchronize(p->st)) != cudaSuccess) {
+  if (pb::mlp_prepare() != cudaSuccess || cudaMemsetAsync(p->ws, 0, L.total, p->st) != cudaSuccess ||
+      cudaMemcpyAsync(p->w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, p->st) != cudaSuccess ||
+      refresh_bf16(p) != cudaSuccess || cudaStreamSynchronize(p->st) != cudaSuccess) {
     delete p;
     return PB_ECUDA;
   }
   *out = p;
+  return PB_OK;
+}
+
+PB_API int pb_selftest_wait(int arrive, uint32_t max_iters, int* status) {
+  if (!status || max_iters == 0u || max_iters > (1u << 20)) return PB_EINVAL;
+  const uint32_t zero = 0u;
+  uint32_t v = 0u;
+  if (cudaMemcpyToSymbol(pb::g_selftest_status, &zero, 4) != cudaSuccess) return PB_ECUDA;
+  pb::selftest_wait_kernel<<<1, 32>>>(arrive ? 1 : 0, max_iters);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpyFromSymbol(&v, pb::g_selftest_status, 4) != cudaSuccess)
+    return PB_ECUDA;
+  *status = (int)v;
+  return PB_OK;
+}
+
+PB_API int pb_mlp_status(pb_mlp* p, int clear, int* status) {
+  if (!p || !status) return PB_EINVAL;
+  uint32_t v = 0u;
+  if (cudaStreamSynchronize(p->st) != cudaSuccess ||
+      cudaMemcpy(&v, p->status, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PB_ECUDA;
+  *status = (int)v;
+  if (clear && v != 0u && cudaMemset(p->status, 0, 4) != cudaSuccess) return PB_ECUDA;
   return PB_OK;
 }
 
@@ -1080,6 +1127,7 @@ static FusedArgs fused_args(pb_mlp* p, int rows) {
   a.npad = p->npad;
   a.n = p->n;
   a.d = p->d;
+  a.status = p->status;
   return a;
 }
 
@@ -1135,7 +1183,7 @@ cudaError_t mlp_forward_fused(pb_mlp* p, int rows) {
   a.kin = p->kin;
   a.H = p->H;
   a.npad = p->npad;
-  a.status = nullptr;
+  a.status = p->status;
   a.n = p->n;
   const size_t smem = fused_layout(a);
   if (smem == 0) return cudaErrorInvalidValue;

@@ -226,6 +226,9 @@ struct pb_mlp {
                 *H2t = nullptr, *dY = nullptr, *dYt = nullptr, *dZ2 = nullptr, *dZ2t = nullptr,
                 *dZ1 = nullptr, *dZ1t = nullptr;
   float *logits = nullptr, *target = nullptr, *loss = nullptr;
+  // PB_ETIMEOUT once a bounded wait in one of this network's kernels expired
+  // (a word of the workspace, zeroed at creation)
+  uint32_t* status = nullptr;
   int step = 0;
 };
 

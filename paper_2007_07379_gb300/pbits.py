@@ -98,6 +98,8 @@ _SIGS = {
     "pb_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                      _VP, ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(_VP)]),
     "pb_mlp_info": (ctypes.c_int, [_VP, _VP]),
+    "pb_mlp_status": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "pb_selftest_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, _VP]),
     "pb_mlp_params": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "pb_mlp_grads": (ctypes.c_int, [_VP, _VP]),
     "pb_mlp_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
@@ -149,6 +151,15 @@ def load(path: str = LIB_PATH):
 def exported_symbols(path: str = LIB_PATH) -> dict[str, bool]:
     lib = ctypes.CDLL(path)
     return {name: hasattr(lib, name) for name in _SIGS}
+
+
+def selftest_wait(arrive: bool, max_iters: int) -> int:
+    """The library's bounded mbarrier wait on its own (pb_selftest_wait):
+    PB_OK when the barrier was arrived on, PB_ETIMEOUT when it was not."""
+    v = ctypes.c_int(0)
+    _check(load().pb_selftest_wait(1 if arrive else 0, ctypes.c_uint32(max_iters), ctypes.byref(v)),
+           "pb_selftest_wait")
+    return v.value
 
 
 def strerror(code: int) -> str:
@@ -509,6 +520,13 @@ class Mlp:
 
     def set_params(self, p: dict):
         _check(load().pb_mlp_params(self._h, _ptr(self._flat(p)), 0), "pb_mlp_params")
+
+    def status(self, clear: bool = False) -> int:
+        """PB_OK, or PB_ETIMEOUT once a bounded wait in one of the network's
+        kernels ran out (pb_mlp_status; synchronizes the network's stream)."""
+        v = ctypes.c_int(0)
+        _check(load().pb_mlp_status(self._h, 1 if clear else 0, ctypes.byref(v)), "pb_mlp_status")
+        return v.value
 
     def grads(self) -> dict:
         flat = np.zeros(self.n_params, dtype=np.float32)

@@ -147,3 +147,15 @@ def test_compile_toffoli_matches_oracle(n, d, seed):
     m = pbits.Model(n, d, g, 3.0)
     assert np.array_equal(m.colours(), oracle.u_colour(n, d, g))
     assert m.info()["rank"] == -1
+
+
+def test_selftest_wait_rejects_bad_arguments_before_any_launch():
+    """Argument checks of pb_selftest_wait come before any CUDA call."""
+    import ctypes
+    lib = pbits.load()
+    v = ctypes.c_int(7)
+    assert lib.pb_selftest_wait(0, ctypes.c_uint32(0), ctypes.byref(v)) == pbits.PB_EINVAL
+    assert lib.pb_selftest_wait(0, ctypes.c_uint32((1 << 20) + 1), ctypes.byref(v)) == pbits.PB_EINVAL
+    assert lib.pb_selftest_wait(1, ctypes.c_uint32(10), None) == pbits.PB_EINVAL
+    assert lib.pb_mlp_status(None, 0, ctypes.byref(v)) == pbits.PB_EINVAL
+    assert v.value == 7
