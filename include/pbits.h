@@ -427,7 +427,9 @@ PB_API void pb_mlp_free(pb_mlp* mlp);
  * workspace of pb_mh_workspace_bytes (256-byte aligned); the run and the
  * network must outlive it.  pb_mh_moves enqueues moves on the run's stream
  * (each replayed from a CUDA graph captured once per k*); pb_mh_stats
- * returns the moves done and proposals accepted (synchronous). */
+ * returns the moves done and proposals accepted (synchronous), and returns
+ * PB_ETIMEOUT when a bounded wait in the network's kernels has run out
+ * (pb_mlp_status; the moves since then are not valid). */
 PB_API int pb_mh_workspace_bytes(const pb_run* run, int model, size_t* bytes);
 PB_API int pb_mh_create(pb_run* run, int model, pb_mlp* mlp, void* d_workspace,
                         size_t workspace_bytes, pb_mh** out);

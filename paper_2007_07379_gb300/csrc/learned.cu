@@ -476,12 +476,15 @@ PB_API int pb_mh_moves(pb_mh* h, uint32_t n_moves) {
 PB_API int pb_mh_stats(pb_mh* h, uint64_t* moves, uint64_t* accepted) {
   if (!h) return PB_EINVAL;
   unsigned long long acc = 0;
+  uint32_t st = 0u;
   if (cudaMemcpyAsync(&acc, h->ws + h->L.cnt, 8, cudaMemcpyDeviceToHost, h->v.st) != cudaSuccess ||
+      cudaMemcpyAsync(&st, h->mlp->status, 4, cudaMemcpyDeviceToHost, h->v.st) != cudaSuccess ||
       cudaStreamSynchronize(h->v.st) != cudaSuccess)
     return PB_ECUDA;
   if (moves) *moves = h->moves;
   if (accepted) *accepted = acc;
-  return PB_OK;
+  // a bounded wait of the network's kernels ran out: the moves since are not valid
+  return st != 0u ? (int)st : PB_OK;
 }
 
 PB_API void pb_mh_free(pb_mh* h) {
