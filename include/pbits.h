@@ -353,11 +353,15 @@ PB_API int pb_philox_fill(const uint32_t* d_ctr, uint32_t k0, uint32_t k1,
  * reaches them.  Returns PB_ERANGE when the run does not fit the array
  * (groups * n * d * 4 + 2^n * 64 bytes plus tables must stay below 16 MiB,
  * e.g. 4096 chains of n=12, d=20), PB_EINVAL for bad arguments.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and each leaves its contents
- * behind: every call clears what must start at zero, and calls whose work
- * overlaps on the GPU (other streams, other host threads) race on it. */
+ * The first call on a device looks up the array's device address and opts
+ * the sweep kernels into their shared memory (once per device, with that
+ * device current; the lookup assumes the device's context is not reset
+ * afterwards).  The call copies its tables from host memory, so it cannot be
+ * recorded into a CUDA graph: on a stream that is capturing it returns
+ * PB_ESTATE and enqueues nothing.  All calls share the one array and each
+ * leaves its contents behind: every call clears what must start at zero, and
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it. */
 PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* cfg, uint32_t n_sweeps,
                                 unsigned long long* d_counts, unsigned long long* d_totals,
                                 uintptr_t stream);

@@ -111,10 +111,12 @@ __global__ void __launch_bounds__(128) gemm_bf16_tn_kernel(GemmArgs g) {
       }
       tc::mma_commit(&mbar);
     }
-    ok = tc::mbar_wait(&mbar, phase);
+    // one decision for the whole CTA: a thread that gave up and one that saw
+    // the commit must take the same branch (the loop has barriers)
+    ok = __syncthreads_and(tc::mbar_wait(&mbar, phase)) != 0;
     phase ^= 1u;
     if (!ok) {
-      if (g.status) atomicCAS(g.status, 0u, (uint32_t)PB_ETIMEOUT);
+      if (tid == 0 && g.status) atomicCAS(g.status, 0u, (uint32_t)PB_ETIMEOUT);
       break;
     }
     tc::fence_after_sync();
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_tn_kernel(GemmArgs g) {
       }
     }
   }
-  if (!ok) tc::mbar_wait(&mbar, phase ^ 1u);  // let MMAs in flight drain (bounded)
+  if (!ok && tid == 0) tc::mbar_wait(&mbar, phase ^ 1u);  // let MMAs in flight drain (bounded)
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, ncols);

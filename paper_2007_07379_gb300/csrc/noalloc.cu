@@ -35,8 +35,12 @@ namespace {
 constexpr size_t kScratchBytes = 16u << 20;
 static __device__ __align__(256) unsigned char g_pb_scratch[kScratchBytes];
 
-// Device address of g_pb_scratch per device, looked up once per device with
-// that device current (the name itself is only a host-side stand-in).
+// Per device, set up once with that device current: the device address of
+// g_pb_scratch (the name itself is only a host-side stand-in) and the sweep
+// kernels' shared-memory opt-in.  The cache assumes the device's context is
+// not reset while the library is loaded (cudaDeviceReset would invalidate
+// both; a process that resets a device must not call this entry point
+// afterwards).
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mutex;
@@ -49,6 +53,7 @@ int scratch_address(void** out) {
   if (!g_scratch_addr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_pb_scratch) != cudaSuccess || p == nullptr) return PB_ECUDA;
+    if (sweep_prepare() != cudaSuccess) return PB_ECUDA;
     g_scratch_addr[dev] = p;
   }
   *out = g_scratch_addr[dev];
@@ -69,6 +74,12 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
   if (m->n > 16) return PB_ERANGE;
   if (n_sweeps > (1u << 26)) return PB_ERANGE;
   if ((uint64_t)cfg->group0 + (cfg->chains + 31) / 32 > 0xFFFFFFFFull) return PB_ERANGE;
+  // The call copies its tables from host memory: it cannot be recorded into
+  // a CUDA graph (the copies would point at this call's host buffers).
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cap) != cudaSuccess)
+    return PB_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone) return PB_ESTATE;
 
   const int n = m->n, d = m->d;
   const size_t npb = (size_t)n * d;
@@ -104,9 +115,12 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
   auto up32 = [](int x) { return ((x + 31) / 32) * 32; };
   const int cons = std::max(32, std::min(224, up32(maxcol)));
   const int prod = std::max(32, std::min(352, up32(3 * maxcol)));
+  // histogram placement: the rule of a single-model run (shared memory when
+  // its u32 counters take at most 128 KiB and the CTA still fits)
   const size_t smem0 = sweep_smem_bytes(n, d, cons, maxcol, 0);
-  const bool hist_smem = (size_t)bins * 32 <= (128u << 10) && smem0 + (size_t)bins * 32 <= (200u << 10);
+  const bool hist_smem = (size_t)bins * 32 <= (128u << 10) && smem0 + (size_t)bins * 32 <= kSweepSmemMax;
   const size_t smem = sweep_smem_bytes(n, d, cons, maxcol, hist_smem ? bins : 0);
+  if (smem > kSweepSmemMax) return PB_ERANGE;
 
   ModelDev md{};
   md.n = n;
@@ -155,7 +169,6 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
       (e = cudaMemcpyAsync(base + o_rec, m->rec.data(), npb * sizeof(Rec), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(base + o_init, m->init.data(), npb * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return PB_ECUDA;
-  if (sweep_prepare() != cudaSuccess) return PB_ECUDA;
   const RunModelDev* d_rm = reinterpret_cast<const RunModelDev*>(base + o_rm);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(base + o_hdr);
   if ((e = launch_init(d_rm, 1, groups, reinterpret_cast<const uint32_t* const*>(base + o_iptr),

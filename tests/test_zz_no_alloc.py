@@ -45,6 +45,53 @@ def test_noalloc_matches_regular_run_twice():
         assert int(tot[0]) == want_valid and int(tot[1]) == want_samples, f"call {call}"
 
 
+def test_noalloc_global_histogram_matches_regular_run():
+    """n = 14: the 2^14-bin histogram does not fit in shared memory, so the
+    recorders add every count to the array's histogram in global memory
+    (cleared by the call itself); still bit-identical to the regular run,
+    on two calls in a row."""
+    import torch
+    n, d, chains, sweeps = 14, 5, 96, 12
+    g = W.random_circuit(n, d, seed=78)
+    m = pbits.Model(n, d, g, 3.0)
+    cfg = pbits.RunCfg(seed=0x5EED + 10, chains=chains)
+    r = pbits.Run([m], [cfg])
+    r.sweeps(sweeps)
+    want_cnt, want_valid, want_samples = r.histogram()
+    assert want_valid > 0
+    for call in range(2):
+        counts = torch.full(((1 << n) * 8,), -1, dtype=torch.int64, device="cuda")
+        totals = torch.full((2,), -1, dtype=torch.int64, device="cuda")
+        pbits.gibbs_run_noalloc(m, cfg, sweeps, counts, totals)
+        torch.cuda.synchronize()
+        got = counts.cpu().numpy().view(np.uint64).reshape(-1, 8)
+        tot = totals.cpu().numpy()
+        assert np.array_equal(got, want_cnt), f"call {call}: histogram differs"
+        assert int(tot[0]) == want_valid and int(tot[1]) == want_samples, f"call {call}"
+
+
+def test_noalloc_refuses_stream_capture():
+    """The call copies host tables, so it cannot be recorded into a graph:
+    on a capturing stream it returns PB_ESTATE and enqueues nothing."""
+    import torch
+    n, d = 5, 6
+    m = pbits.Model(n, d, W.random_circuit(n, d, seed=79), 3.0)
+    cfg = pbits.RunCfg(seed=3, chains=64)
+    counts = torch.zeros((1 << n) * 8, dtype=torch.int64, device="cuda")
+    totals = torch.zeros(2, dtype=torch.int64, device="cuda")
+    pbits.gibbs_run_noalloc(m, cfg, 2, counts, totals)  # first call on the device: set-up
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    err = None
+    with torch.cuda.graph(graph, stream=s):
+        try:
+            pbits.gibbs_run_noalloc(m, cfg, 2, counts, totals, stream=s)
+        except pbits.PbError as e:
+            err = e
+    assert err is not None and err.code == pbits.PB_ESTATE
+
+
 def test_noalloc_rejects_oversize():
     import torch
     g = W.random_circuit(12, 20, seed=1)
