@@ -47,7 +47,7 @@ def _load():
             u32p = ctypes.POINTER(ctypes.c_uint32)
             lib.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
             lib.orc_philox4x32_10.restype = None
-            for name in ("orc_statevector", "orc_pathsum_exact", "orc_gf2_rank",
+            for name in ("orc_statevector", "orc_pathsum_exact", "orc_gf2_rank", "orc_reach",
                          "orc_colour", "orc_gibbs", "orc_elim", "orc_elim_clamped", "orc_violations", "orc_path_phase",
                          "orc_thresholds", "orc_u_statevector", "orc_u_pathstats", "orc_u_gibbs",
                          "orc_u_elim", "orc_u_log2z", "orc_shor_columns", "orc_shor_prob_at",
@@ -127,6 +127,33 @@ def gf2_rank(n: int, d: int, gates):
     if rc != 0:
         raise ValueError(f"orc_gf2_rank failed ({rc})")
     return h.value, r.value
+
+
+def valid_paths_per_output(n: int, d: int, gates, alphas=None, beta: int = 0) -> np.ndarray:
+    """N_alpha, the number of valid paths ending at alpha (float64; 2^{h-rank}
+    for an output in the affine image of the H outputs, else 0), for every
+    alpha in `alphas` (default: all 2^n outputs)."""
+    lib = _load()
+    g = _gates(gates)
+    h = ctypes.c_int(0)
+    r = ctypes.c_int(0)
+    c = ctypes.c_uint32(0)
+    masks = np.zeros(32, dtype=np.uint32)
+    rc = lib.orc_reach(n, d, _p(g), len(g), ctypes.c_uint32(beta), ctypes.byref(h), ctypes.byref(r),
+                       ctypes.byref(c), _p(masks))
+    if rc != 0:
+        raise ValueError(f"orc_reach failed ({rc})")
+    a = np.arange(1 << n, dtype=np.uint64) if alphas is None else np.asarray(alphas, dtype=np.uint64)
+    x = a ^ np.uint64(c.value)
+    ok = np.ones(len(a), dtype=bool)
+    for m in masks[:n - r.value]:
+        v = x & np.uint64(m)
+        par = np.zeros(len(a), dtype=np.uint64)
+        while np.any(v):
+            par ^= v & np.uint64(1)
+            v >>= np.uint64(1)
+        ok &= par == 0
+    return np.where(ok, 2.0 ** (h.value - r.value), 0.0)
 
 
 def thresholds(J: float) -> np.ndarray:

@@ -22,6 +22,8 @@
  *   orc_gf2_rank        h (number of H gates) and the GF(2) rank of the map
  *                       from H outputs to the final layer (closed-form
  *                       variance, Eqs. U26/U30 with uniform valid paths).
+ *   orc_reach           the outputs reached by valid paths, N_alpha = 2^{h-rank}
+ *                       or 0 (affine image of the H outputs).
  *   orc_thresholds      heat-bath thresholds floor(2^32 sigma(-J v)).
  *   orc_colour          the sweep's colour classes.
  *   orc_gibbs           reference Gibbs sampler of the layered J-penalty
@@ -344,6 +346,77 @@ int orc_gf2_rank(int n, int d, const orc_gate* g, int ng, int* h_out,
   free(next);
   *h_out = h;
   *rank_out = rank;
+  return 0;
+}
+
+/* The outputs reached by valid paths (closed-form variance of the estimator,
+ * Eqs. U26/U30 with uniform valid paths: E|X_alpha|^2 = N_alpha).  Each wire
+ * bit is affine over GF(2) in the H outputs x: s_d = A x + c, where c carries
+ * the input bits through the CNOTs (S, T and CZ leave bits unchanged).  The
+ * valid paths to alpha are the solutions of A x = alpha + c: 2^{h - rank} of
+ * them when alpha + c lies in the column space of A, none otherwise.  Row
+ * reduction of [A | I] leaves, for every row without a pivot in A, an output
+ * mask m with m A = 0; alpha is reached iff parity(m & (alpha ^ c)) = 0 for
+ * every such m.
+ *   c_out: the constant c (bit q = qubit q); masks: n words, the first
+ *   n - rank of them the constraint masks.  n <= 32. */
+int orc_reach(int n, int d, const orc_gate* g, int ng, uint32_t beta, int* h_out, int* rank_out,
+              uint32_t* c_out, uint32_t* masks) {
+  if (check_circuit(n, d, g, ng) != 0) return -1;
+  int h = 0;
+  for (int i = 0; i < ng; ++i) h += (g[i].op == ORC_H);
+  if (h > 64 * ORC_MAXW) return -2;
+  uint64_t(*wire)[ORC_MAXW] = calloc((size_t)n, sizeof(*wire));
+  uint64_t(*next)[ORC_MAXW] = calloc((size_t)n, sizeof(*next));
+  if (!wire || !next) { free(wire); free(next); return -3; }
+  uint32_t cst = beta, ncst;
+  int var = 0;
+  for (int L = 0; L < d; ++L) {
+    memcpy(next, wire, (size_t)n * sizeof(*wire));
+    ncst = cst;
+    for (int i = 0; i < ng; ++i) {
+      if (g[i].layer != L) continue;
+      const int a = g[i].q0, t = g[i].q1;
+      if (g[i].op == ORC_H) {
+        memset(next[a], 0, sizeof(next[0]));
+        next[a][var >> 6] |= 1ull << (var & 63);
+        ++var;
+        ncst &= ~(1u << a);
+      } else if (g[i].op == ORC_CNOT) {
+        for (int w = 0; w < ORC_MAXW; ++w) next[t][w] = wire[t][w] ^ wire[a][w];
+        ncst ^= ((cst >> a) & 1u) << t;
+      }
+    }
+    memcpy(wire, next, (size_t)n * sizeof(*wire));
+    cst = ncst;
+  }
+  /* row q of [A | I]: wire[q] | comb[q] */
+  uint32_t comb[32];
+  int pivoted[32];
+  for (int q = 0; q < n; ++q) { comb[q] = 1u << q; pivoted[q] = 0; }
+  int rank = 0;
+  for (int col = 0; col < h; ++col) {
+    int piv = -1;
+    for (int q = 0; q < n; ++q)
+      if (!pivoted[q] && ((wire[q][col >> 6] >> (col & 63)) & 1ull)) { piv = q; break; }
+    if (piv < 0) continue;
+    pivoted[piv] = 1;
+    ++rank;
+    for (int q = 0; q < n; ++q)
+      if (q != piv && ((wire[q][col >> 6] >> (col & 63)) & 1ull)) {
+        for (int w = 0; w < ORC_MAXW; ++w) wire[q][w] ^= wire[piv][w];
+        comb[q] ^= comb[piv];
+      }
+  }
+  int k = 0;
+  for (int q = 0; q < n; ++q) masks[q] = 0u;
+  for (int q = 0; q < n; ++q)
+    if (!pivoted[q]) masks[k++] = comb[q];
+  free(wire);
+  free(next);
+  *h_out = h;
+  *rank_out = rank;
+  *c_out = cst;
   return 0;
 }
 

@@ -206,6 +206,34 @@ def test_gf2_count_of_valid_paths(n, d, seed):
     assert (Na > 0).sum() == 2 ** r
 
 
+@pytest.mark.parametrize("n,d,seed,beta", [(3, 4, 0, 0), (3, 5, 7, 5), (4, 4, 3, 0), (2, 8, 11, 2),
+                                            (5, 3, 5, 0b10110), (4, 5, 21, 9), (5, 4, 7, 0)])
+def test_reached_outputs_match_brute_force(n, d, seed, beta):
+    """N_alpha of every output (which outputs the valid paths reach, and how
+    many paths each) equals the brute-force count of paths per output, with
+    and without input bits; the counts add up to the 2^h valid paths."""
+    g = W.random_circuit(n, d, seed=seed)
+    cnt, h = oracle.pathsum_exact(n, d, g, beta=beta)
+    N = oracle.valid_paths_per_output(n, d, g, beta=beta)
+    assert np.array_equal(N, cnt.sum(axis=1).astype(float))
+    assert N.sum() == 2.0 ** h
+    sub = np.array([3, 0, (1 << n) - 1], dtype=np.uint32) % (1 << n)
+    assert np.array_equal(oracle.valid_paths_per_output(n, d, g, alphas=sub, beta=beta), N[sub])
+    # E|X|^2 >= |E X|^2 for the per-sample estimator 2^{h/2} [end = a] w^phi
+    psi = oracle.statevector(n, d, g, beta=beta)
+    assert np.all(N + 1e-12 >= np.abs(psi) ** 2)
+
+
+def test_reached_outputs_of_ghz_and_hadamard_chain():
+    """GHZ-6 reaches |000000> and |111111> through one path each; the n = 1
+    Hadamard chain reaches both outputs through 2^{d-1} paths each."""
+    g = W.ghz(6)
+    N = oracle.valid_paths_per_output(6, 6, g)
+    assert N[0] == 1 and N[63] == 1 and N.sum() == 2
+    N = oracle.valid_paths_per_output(1, 6, W.hadamard_chain(6))
+    assert list(N) == [32.0, 32.0]
+
+
 # --------------------------------------------------------------------------
 def test_thresholds_high_precision():
     sympy = pytest.importorskip("sympy")
