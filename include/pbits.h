@@ -230,13 +230,33 @@ typedef struct {
   uint32_t n_batches;     /* SE batches over chain groups (0 = automatic)      */
   const uint32_t* alphas; /* bins to record; NULL = full 2^n histogram (n<=22)  */
   int32_t n_alphas;
-  int32_t sampler;        /* PB_GIBBS, PB_ELIM or PB_ELIM_CLAMP (PB_LEARNED: pb_mh_create) */
-  const pb_mlp* proposal; /* trained MLP for PB_LEARNED, else NULL             */
-  uint32_t mh_every;      /* PB_LEARNED: one suffix MH move every mh_every sweeps */
+  int32_t sampler;        /* PB_GIBBS, PB_LEARNED, PB_ELIM or PB_ELIM_CLAMP      */
+  const pb_mlp* proposal; /* PB_LEARNED: the network (must outlive the run)      */
+  uint32_t mh_every;      /* PB_LEARNED: sweeps per move period (>= 1)           */
   uint32_t group0;        /* global index of the first chain group: the chains
                              here are 32*group0 ... (multi-rank sharding; the
                              draws depend on the global index only)             */
 } pb_run_cfg;
+
+/* PB_LEARNED: Gibbs sweeps with the learned proposal as a run mode (Fig. 2
+ * Step 1 with the network q as the proposal, Steps 2-3 unchanged).  Every
+ * call pb_run_sweeps(n) runs n / mh_every periods, each one suffix move of
+ * every PB_LEARNED model of the run (the move of pb_mh_moves: k* from
+ * SplitMix64 of the seed and the model's move count, proposal drawn layer by
+ * layer from `proposal`, Metropolis-Hastings acceptance on the J energy;
+ * the move count starts at 0 with the run) followed by mh_every sweeps,
+ * then n mod mh_every sweeps without a move.  The whole sequence is one
+ * CUDA graph whose periods are counted down on the device (a while node),
+ * so no host step runs between moves.  The records of the sweeps are the
+ * samples; the moves keep the sampled law whatever the network.  The
+ * network's weights are read at every move (training between calls takes
+ * effect).  Requirements (PB_EINVAL otherwise): proposal != NULL with the
+ * model's n and d and k_in <= 96, n <= 32 (the fused inference kernel), a
+ * plain model (no PB_U, PB_U2 or PB_CCX gate), mh_every >= 1, and the same
+ * mh_every for all PB_LEARNED models of a run (which may hold PB_GIBBS models
+ * too; all draw from their own streams).  pb_run_moves reads the moves done
+ * and accepted; pb_run_wait also returns PB_ETIMEOUT from a network's
+ * status word; checkpoints hold the move counters. */
 
 /* Bytes of device workspace that pb_run_create() needs for these models. */
 PB_API int pb_workspace_bytes(pb_model* const* models, const pb_run_cfg* cfgs,
@@ -257,8 +277,14 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs,
 PB_API int pb_run_sweeps(pb_run* run, uint32_t n_sweeps);
 
 /* Waits for the run's stream; returns PB_OK, PB_ECUDA or the device status
- * word (PB_ETIMEOUT when a bounded device wait expired). */
+ * word (PB_ETIMEOUT when a bounded device wait expired, in the run's kernels
+ * or, for PB_LEARNED models, in their networks' kernels). */
 PB_API int pb_run_wait(pb_run* run);
+
+/* Moves done and proposals accepted (one per chain and move) of a
+ * PB_LEARNED model (synchronous).  PB_ESTATE for another sampler; moves /
+ * accepted may be NULL. */
+PB_API int pb_run_moves(pb_run* run, int model, uint64_t* moves, uint64_t* accepted);
 
 /* Histogram of model `model` (synchronous): counts[bin*8 + b] = valid samples
  * that ended in bin with phase w^b (w = e^{i pi/4}) summed over batches;
@@ -318,7 +344,8 @@ PB_API int pb_run_get_shape(const pb_run* run, int* consumers, int* producers, i
  * (may be NULL) receives the time of trial_sweeps sweeps with that shape. */
 PB_API int pb_run_tune(pb_run* run, uint32_t trial_sweeps, const char* cache_path, double* best_ms);
 
-/* Checkpoint: chain words, counters and the sweep index of every model.
+/* Checkpoint: chain words, counters and the sweep index of every model (and
+ * the move counters of PB_LEARNED models).
  * bytes_needed is written when host_buf is NULL.  Restore puts them back;
  * since the draws are counter-based the resumed run is bit-identical to an
  * uninterrupted one. */

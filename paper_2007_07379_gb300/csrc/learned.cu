@@ -71,14 +71,16 @@ __global__ void unslice_kernel(const uint32_t* __restrict__ state, int n, int d,
   P[(size_t)(g * 32 + lane) * d + j] = y;
 }
 
-// Per-chain words -> bit-sliced words for layers k0..d (1-based).
-__global__ void slice_kernel(const uint32_t* __restrict__ P, int n, int d, int k0, uint32_t groups,
-                             uint32_t* __restrict__ state) {
-  const int L = d - k0 + 1;
+// Per-chain words -> bit-sliced words for layers k..d (1-based), k read from
+// k_dev; one warp per (group, layer) over all d layers, the warps of layers
+// before k leave at once.
+__global__ void slice_kernel(const uint32_t* __restrict__ P, int n, int d, const int* __restrict__ k_dev,
+                             uint32_t groups, uint32_t* __restrict__ state) {
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= groups * (uint32_t)L) return;
-  const uint32_t g = w / L, j = (k0 - 1) + w % L;
+  if (w >= groups * (uint32_t)d) return;
+  const uint32_t g = w / d, j = w % d;
+  if ((int)j + 1 < *k_dev) return;  // the whole warp: layer j+1 is before the suffix
   const uint32_t x = P[(size_t)(g * 32 + lane) * d + j];
   const uint32_t y = warp_transpose(x, lane);
   if (lane < n) state[((size_t)g * d + j) * n + lane] = y;
@@ -183,13 +185,14 @@ __global__ void sample_kernel(const float* __restrict__ logits, int npad, int n,
 // Metropolis-Hastings decision, and the accepted suffix copied into P.
 __global__ void accept_kernel(uint32_t* __restrict__ P, const uint32_t* __restrict__ Pn,
                               const LayerTab* __restrict__ tab, uint32_t beta, uint32_t nmask,
-                              int d, int k, float J, const float* __restrict__ lq,
+                              int d, float J, const float* __restrict__ lq,
                               const float* __restrict__ lqf, uint32_t chains, uint32_t k0,
-                              uint32_t k1, const uint32_t* __restrict__ move_dev, uint32_t group0,
-                              unsigned long long* __restrict__ n_accept) {
+                              uint32_t k1, MhCounters* __restrict__ ctr, uint32_t group0) {
   const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= chains) return;
-  const uint32_t move = *move_dev;
+  const uint32_t move = ctr->moves;
+  const int k = ctr->k;
+  unsigned long long* n_accept = &ctr->accepted;
   const uint32_t* cur = P + (size_t)c * d;
   const uint32_t* prop = Pn + (size_t)c * d;
   const uint32_t base = k == 1 ? beta : cur[k - 2];
@@ -219,27 +222,80 @@ __global__ void accept_kernel(uint32_t* __restrict__ P, const uint32_t* __restri
     for (int j = k; j <= d; ++j) P[(size_t)c * d + (j - 1)] = prop[j - 1];
 }
 
-__global__ void mh_advance_kernel(uint32_t* move_dev) { *move_dev += 1u; }
+__global__ void mh_advance_kernel(MhCounters* ctr) { ctr->moves += 1u; }
 
-// Valid paths (no violated link) appended to out[count][d] while room is left.
-__global__ void collect_kernel(const uint32_t* __restrict__ P, const LayerTab* __restrict__ tab,
-                               uint32_t beta, uint32_t nmask, int d, uint32_t chains,
-                               uint32_t* __restrict__ out, unsigned long long capacity,
-                               unsigned long long* __restrict__ count) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= chains) return;
-  const uint32_t* s = P + (size_t)c * d;
-  uint32_t prev = beta;
-  int v = 0;
-  for (int j = 1; j <= d; ++j) {
-    const LayerTab& L = tab[j - 1];
-    v += __popc((s[j - 1] ^ layer_map(L, prev)) & ~L.hmask & nmask);
-    prev = s[j - 1];
+// SplitMix64 (Steele, Lea, Flood 2014): the suffix start of a move.
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__host__ __device__ inline int suffix_start(uint64_t seed, uint32_t move, int d) {
+  return 1 + (int)(splitmix64(seed ^ (0xA5A5ull << 40) ^ move) % (uint64_t)d);
+}
+
+// k* of the current move from the seed and the move counter (device side,
+// so one captured graph serves every move); set_k_kernel: a host-drawn k*.
+__global__ void mh_pick_kernel(MhCounters* ctr, uint64_t seed, int d) {
+  ctr->k = suffix_start(seed, ctr->moves, d);
+}
+__global__ void set_k_kernel(MhCounters* ctr, int k) { ctr->k = k; }
+
+__global__ void zero_f32_kernel(float* __restrict__ x, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = 0.f;
+}
+
+// Valid paths (no violated link) appended to out[count][d] while room is
+// left, in chain order: one CTA walks the chains in tiles of its threads; a
+// tile's valid chains take consecutive slots by a warp ballot and the
+// warps' counts (an exclusive prefix sum), so the collected data, and a
+// training run on it, are the same on every run.  *count grows by the
+// number of valid chains (also past the capacity).
+__global__ void __launch_bounds__(1024) collect_kernel(const uint32_t* __restrict__ P,
+                                                       const LayerTab* __restrict__ tab,
+                                                       uint32_t beta, uint32_t nmask, int d,
+                                                       uint32_t chains, uint32_t* __restrict__ out,
+                                                       unsigned long long capacity,
+                                                       unsigned long long* __restrict__ count) {
+  __shared__ unsigned long long base;
+  __shared__ uint32_t wcount[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (tid == 0) base = *count;
+  __syncthreads();
+  for (uint32_t c0 = 0; c0 < chains; c0 += blockDim.x) {
+    const uint32_t c = c0 + (uint32_t)tid;
+    bool valid = false;
+    if (c < chains) {
+      const uint32_t* s = P + (size_t)c * d;
+      uint32_t prev = beta;
+      int v = 0;
+      for (int j = 1; j <= d; ++j) {
+        const LayerTab& L = tab[j - 1];
+        v += __popc((s[j - 1] ^ layer_map(L, prev)) & ~L.hmask & nmask);
+        prev = s[j - 1];
+      }
+      valid = v == 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, valid);
+    if (lane == 0) wcount[warp] = (uint32_t)__popc(bal);
+    __syncthreads();
+    uint32_t off = 0, total = 0;
+    for (int w = 0; w < nwarps; ++w) {
+      if (w < warp) off += wcount[w];
+      total += wcount[w];
+    }
+    const unsigned long long slot = base + off + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+    if (valid && slot < capacity) {
+      const uint32_t* s = P + (size_t)c * d;
+      for (int j = 0; j < d; ++j) out[slot * d + j] = s[j];
+    }
+    __syncthreads();  // every thread has read base and wcount
+    if (tid == 0) base += total;
+    __syncthreads();
   }
-  if (v != 0) return;
-  const unsigned long long slot = atomicAdd(count, 1ull);
-  if (slot >= capacity) return;
-  for (int j = 0; j < d; ++j) out[slot * d + j] = s[j];
+  if (tid == 0) *count = base;
 }
 
 // Training rows from collected paths: row r takes path i and layer j drawn
@@ -284,7 +340,7 @@ std::vector<LayerTab> layer_table(const pb_model& m) {
 }
 
 struct MhLayout {
-  size_t tab, P, Pn, lq, lqf, cnt, move, total;
+  size_t ctr, tab, P, Pn, lq, lqf, total;
 };
 
 MhLayout mh_layout(int d, uint32_t groups) {
@@ -297,22 +353,143 @@ MhLayout mh_layout(int d, uint32_t groups) {
     return at;
   };
   const size_t C = (size_t)groups * 32;
+  L.ctr = take(sizeof(MhCounters));  // offset 0
   L.tab = take(sizeof(LayerTab) * 64);
   L.P = take(C * d * 4);
   L.Pn = take(C * d * 4);
   L.lq = take(C * d * 4);
   L.lqf = take(C * 4);
-  L.cnt = take(16);
-  L.move = take(16);
   L.total = (p + 255) & ~(size_t)255;
   return L;
 }
 
-uint64_t splitmix(uint64_t x) {
-  x += 0x9E3779B97F4A7C15ull;
-  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-  return x ^ (x >> 31);
+// The pieces of a move region.
+struct MhPtrs {
+  MhCounters* ctr;
+  const LayerTab* tab;
+  uint32_t *P, *Pn;
+  float *lq, *lqf;
+};
+MhPtrs mh_ptrs(const MhCtx& c) {
+  const MhLayout L = mh_layout(c.model->d, c.groups);
+  MhPtrs q;
+  q.ctr = reinterpret_cast<MhCounters*>(c.ws + L.ctr);
+  q.tab = reinterpret_cast<const LayerTab*>(c.ws + L.tab);
+  q.P = reinterpret_cast<uint32_t*>(c.ws + L.P);
+  q.Pn = reinterpret_cast<uint32_t*>(c.ws + L.Pn);
+  q.lq = reinterpret_cast<float*>(c.ws + L.lq);
+  q.lqf = reinterpret_cast<float*>(c.ws + L.lqf);
+  return q;
+}
+
+// Acceptance, slicing back and the move counter: the end of every move.
+cudaError_t finish_move(const MhCtx& c, const MhPtrs& q, cudaStream_t st) {
+  const pb_model& m = *c.model;
+  const int n = m.n, d = m.d, T = 256;
+  const uint32_t nmask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  const uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);
+  accept_kernel<<<(c.chains + T - 1) / T, T, 0, st>>>(q.P, q.Pn, q.tab, m.beta, nmask, d, (float)m.J,
+                                                      q.lq, q.lqf, c.chains, k0, k1, q.ctr, c.group0);
+  const uint32_t sw = c.groups * (uint32_t)d;
+  slice_kernel<<<(sw * 32 + T - 1) / T, T, 0, st>>>(q.P, n, d, &q.ctr->k, c.groups, c.state);
+  mh_advance_kernel<<<1, 1, 0, st>>>(q.ctr);
+  return cudaGetLastError();
+}
+
+// The kernels of one move with a host-drawn suffix start k (networks that
+// do not fit the fused kernel: rows batched through the layer-by-layer GEMMs).
+cudaError_t enqueue_move_host_k(const MhCtx& c, int k, cudaStream_t st) {
+  const pb_model& m = *c.model;
+  pb_mlp* mlp = c.mlp;
+  const MhPtrs q = mh_ptrs(c);
+  const int n = m.n, d = m.d, kin = mlp->kin, npad = mlp->npad, B = mlp->batch;
+  const uint32_t C = c.chains;
+  const uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);
+  const int T = 256;
+  const int Ls = d - k + 1;
+  cudaStream_t mst = mlp->st;
+  mlp->st = st;
+  cudaError_t e = cudaSuccess;
+  const uint32_t warps = c.groups * (uint32_t)d;
+  unslice_kernel<<<(warps * 32 + T - 1) / T, T, 0, st>>>(c.state, n, d, c.groups, q.P);
+  set_k_kernel<<<1, 1, 0, st>>>(q.ctr, k);
+  const uint64_t rows_total = (uint64_t)C * Ls;
+  for (uint64_t r0 = 0; r0 < rows_total && e == cudaSuccess; r0 += B) {
+    const int rows = (int)std::min<uint64_t>(B, rows_total - r0);
+    rows_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(q.P, m.beta, n, d, kin, k, r0, rows, mlp->X);
+    if ((e = mlp_forward_rows(mlp, rows)) != cudaSuccess) break;
+    logq_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, q.P, n, d, k, r0, rows, q.lq);
+  }
+  zero_f32_kernel<<<(C + T - 1) / T, T, 0, st>>>(q.lqf, C);
+  for (int j = k; j <= d && e == cudaSuccess; ++j) {
+    for (uint32_t c0 = 0; c0 < C && e == cudaSuccess; c0 += (uint32_t)B) {
+      const int rows = (int)std::min<uint32_t>((uint32_t)B, C - c0);
+      rows_proposal_kernel<<<(rows + T - 1) / T, T, 0, st>>>(q.P, q.Pn, m.beta, n, d, kin, k, j, c0,
+                                                             rows, mlp->X);
+      if ((e = mlp_forward_rows(mlp, rows)) != cudaSuccess) break;
+      sample_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, n, d, j, c0, rows, k0, k1,
+                                                      &q.ctr->moves, c.group0, q.Pn, q.lqf);
+    }
+  }
+  if (e == cudaSuccess) e = finish_move(c, q, st);
+  mlp->st = mst;
+  return e;
+}
+
+}  // namespace
+
+namespace pb {
+
+size_t mh_region_bytes(int d, uint32_t groups) { return mh_layout(d, groups).total; }
+
+bool mh_fused(const pb_mlp* mlp) { return mlp->kin <= 96 && mlp->npad <= 32; }
+
+cudaError_t mh_region_init(const MhCtx& c, cudaStream_t st) {
+  const MhLayout L = mh_layout(c.model->d, c.groups);
+  const std::vector<LayerTab> tab = layer_table(*c.model);
+  cudaError_t e = cudaMemsetAsync(c.ws, 0, L.total, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c.ws + L.tab, tab.data(), sizeof(LayerTab) * c.model->d, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host table is a local
+  return e;
+}
+
+// One move (fused networks): unslice, draw k*, log q of the current suffix,
+// the proposal layer by layer, acceptance, slice back; no host value depends
+// on k*, so the sequence is captured once.
+cudaError_t mh_enqueue_move_dev(const MhCtx& c, cudaStream_t st) {
+  const pb_model& m = *c.model;
+  const MhPtrs q = mh_ptrs(c);
+  const int n = m.n, d = m.d, T = 256;
+  const uint32_t C = c.chains;
+  const uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);
+  const uint32_t warps = c.groups * (uint32_t)d;
+  unslice_kernel<<<(warps * 32 + T - 1) / T, T, 0, st>>>(c.state, n, d, c.groups, q.P);
+  mh_pick_kernel<<<1, 1, 0, st>>>(q.ctr, c.seed, d);
+  cudaError_t e = mlp_fused_logq_dev(c.mlp, q.P, m.beta, (int)C, &q.ctr->k, q.lq, st);
+  if (e != cudaSuccess) return e;
+  zero_f32_kernel<<<(C + T - 1) / T, T, 0, st>>>(q.lqf, C);
+  e = mlp_fused_sample_dev(c.mlp, q.P, q.Pn, m.beta, (int)C, &q.ctr->k, q.lqf, k0, k1, &q.ctr->moves,
+                           c.group0, st);
+  if (e != cudaSuccess) return e;
+  return finish_move(c, q, st);
+}
+
+}  // namespace pb
+
+namespace {
+
+MhCtx mh_ctx(const RunView& v, pb_mlp* mlp, char* ws) {
+  MhCtx c;
+  c.model = v.model;
+  c.mlp = mlp;
+  c.state = v.state;
+  c.chains = v.chains;
+  c.groups = v.groups;
+  c.group0 = v.group0;
+  c.seed = v.seed;
+  c.ws = ws;
+  return c;
 }
 
 }  // namespace
@@ -332,83 +509,13 @@ PB_API int pb_mh_workspace_bytes(const pb_run* run, int model, size_t* bytes) {
 
 struct pb_mh {
   pb_run* run = nullptr;
-  pb_mlp* mlp = nullptr;
-  int model = 0;
   RunView v{};
-  char* ws = nullptr;
-  size_t ws_bytes = 0;
-  MhLayout L{};
+  MhCtx c{};
   uint32_t moves = 0;
   cudaStream_t cap_st = nullptr;
-  std::vector<cudaGraphExec_t> graphs;  // one per k* (1..d), built on first use
+  cudaGraphExec_t graph = nullptr;      // fused networks: one graph, k* drawn on the device
+  std::vector<cudaGraphExec_t> graphs;  // otherwise one per k* (1..d), built on first use
 };
-
-namespace {
-
-// The kernels of one move with suffix start k, in stream order.
-cudaError_t enqueue_move(pb_mh* h, int k, cudaStream_t st) {
-  const pb_model& m = *h->v.model;
-  pb_mlp* mlp = h->mlp;
-  char* ws = h->ws;
-  const MhLayout& L = h->L;
-  uint32_t* P = reinterpret_cast<uint32_t*>(ws + L.P);
-  uint32_t* Pn = reinterpret_cast<uint32_t*>(ws + L.Pn);
-  float* lq = reinterpret_cast<float*>(ws + L.lq);
-  float* lqf = reinterpret_cast<float*>(ws + L.lqf);
-  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws + L.cnt);
-  uint32_t* move_dev = reinterpret_cast<uint32_t*>(ws + L.move);
-  const LayerTab* dtab = reinterpret_cast<const LayerTab*>(ws + L.tab);
-  const int n = m.n, d = m.d, kin = mlp->kin, npad = mlp->npad, B = mlp->batch;
-  const uint32_t nmask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-  const uint32_t C = h->v.chains;
-  const uint32_t k0 = (uint32_t)h->v.seed, k1 = (uint32_t)(h->v.seed >> 32);
-  const int T = 256;
-  const int Ls = d - k + 1;
-  cudaStream_t mst = mlp->st;
-  mlp->st = st;
-  cudaError_t e = cudaSuccess;
-  const bool fused = mlp->kin <= 96 && mlp->npad <= 32;
-  const uint32_t warps = h->v.groups * (uint32_t)d;
-  unslice_kernel<<<(warps * 32 + T - 1) / T, T, 0, st>>>(h->v.state, n, d, h->v.groups, P);
-  if (fused) {
-    // one launch for log q of the current suffix, one per proposal layer
-    e = mlp_fused_logq(mlp, P, m.beta, (int)C, k, lq, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(lqf, 0, (size_t)C * 4, st);
-    if (e == cudaSuccess)
-      e = mlp_fused_sample(mlp, P, Pn, m.beta, (int)C, k, k, d, lqf, k0, k1, move_dev, h->v.group0, st);
-  } else {
-    const uint64_t rows_total = (uint64_t)C * Ls;
-    for (uint64_t r0 = 0; r0 < rows_total && e == cudaSuccess; r0 += B) {
-      const int rows = (int)std::min<uint64_t>(B, rows_total - r0);
-      rows_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(P, m.beta, n, d, kin, k, r0, rows, mlp->X);
-      if ((e = mlp_forward_rows(mlp, rows)) != cudaSuccess) break;
-      logq_current_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, P, n, d, k, r0, rows, lq);
-    }
-    if (e == cudaSuccess) e = cudaMemsetAsync(lqf, 0, (size_t)C * 4, st);
-    for (int j = k; j <= d && e == cudaSuccess; ++j) {
-      for (uint32_t c0 = 0; c0 < C && e == cudaSuccess; c0 += (uint32_t)B) {
-        const int rows = (int)std::min<uint32_t>((uint32_t)B, C - c0);
-        rows_proposal_kernel<<<(rows + T - 1) / T, T, 0, st>>>(P, Pn, m.beta, n, d, kin, k, j, c0,
-                                                               rows, mlp->X);
-        if ((e = mlp_forward_rows(mlp, rows)) != cudaSuccess) break;
-        sample_kernel<<<(rows + T - 1) / T, T, 0, st>>>(mlp->logits, npad, n, d, j, c0, rows, k0, k1,
-                                                        move_dev, h->v.group0, Pn, lqf);
-      }
-    }
-  }
-  if (e == cudaSuccess) {
-    accept_kernel<<<(C + T - 1) / T, T, 0, st>>>(P, Pn, dtab, m.beta, nmask, d, k, (float)m.J, lq,
-                                                 lqf, C, k0, k1, move_dev, h->v.group0, cnt);
-    const uint32_t sw = h->v.groups * (uint32_t)Ls;
-    slice_kernel<<<(sw * 32 + T - 1) / T, T, 0, st>>>(P, n, d, k, h->v.groups, h->v.state);
-    mh_advance_kernel<<<1, 1, 0, st>>>(move_dev);
-    e = cudaGetLastError();
-  }
-  mlp->st = mst;
-  return e;
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -422,41 +529,37 @@ PB_API int pb_mh_create(pb_run* run, int model, pb_mlp* mlp, void* d_ws, size_t 
   if (!mlp || !d_ws || ((uintptr_t)d_ws & 255)) return PB_EINVAL;
   const pb_model& m = *v.model;
   if (mlp->n != m.n || mlp->d != m.d) return PB_EINVAL;
-  const MhLayout L = mh_layout(m.d, v.groups);
-  if (ws_bytes < L.total) return PB_ERANGE;
+  if (ws_bytes < mh_layout(m.d, v.groups).total) return PB_ERANGE;
   pb_mh* h = new (std::nothrow) pb_mh;
   if (!h) return PB_ENOMEM;
-  h->run = run; h->mlp = mlp; h->model = model; h->v = v;
-  h->ws = static_cast<char*>(d_ws); h->ws_bytes = ws_bytes; h->L = L;
+  h->run = run;
+  h->v = v;
+  h->c = mh_ctx(v, mlp, static_cast<char*>(d_ws));
   h->graphs.assign(m.d + 1, nullptr);
-  const std::vector<LayerTab> tab = layer_table(m);
-  cudaError_t e = cudaMemsetAsync(h->ws, 0, L.total, v.st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->ws + L.tab, tab.data(), sizeof(LayerTab) * m.d, cudaMemcpyHostToDevice, v.st);
+  cudaError_t e = mh_region_init(h->c, v.st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(mlp->st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(v.st);
   if (e == cudaSuccess) e = mlp_prepare();
   if (e != cudaSuccess) { delete h; return PB_ECUDA; }
   *out = h;
   return PB_OK;
 }
 
-// n_moves further moves, each replayed from a CUDA graph captured for its
-// suffix start k* (asynchronous on the run's stream).
+// n_moves further moves, each a replay of a captured graph (asynchronous on
+// the run's stream).
 PB_API int pb_mh_moves(pb_mh* h, uint32_t n_moves) {
   if (!h) return PB_EINVAL;
   const int d = h->v.model->d;
+  const bool fused = mh_fused(h->c.mlp);
   for (uint32_t i = 0; i < n_moves; ++i) {
-    const uint32_t move = h->moves;
-    const int k = 1 + (int)(splitmix(h->v.seed ^ (0xA5A5ull << 40) ^ move) % (uint64_t)d);
-    cudaGraphExec_t& ex = h->graphs[k];
+    const int k = suffix_start(h->v.seed, h->moves, d);
+    cudaGraphExec_t& ex = fused ? h->graph : h->graphs[k];
     if (!ex) {
       if (!h->cap_st && cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess)
         return PB_ECUDA;
       cudaGraph_t graph = nullptr;
       if (cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return PB_ECUDA;
-      cudaError_t e = enqueue_move(h, k, h->cap_st);
+      cudaError_t e = fused ? mh_enqueue_move_dev(h->c, h->cap_st) : enqueue_move_host_k(h->c, k, h->cap_st);
       cudaError_t e2 = cudaStreamEndCapture(h->cap_st, &graph);
       if (e != cudaSuccess || e2 != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -475,14 +578,14 @@ PB_API int pb_mh_moves(pb_mh* h, uint32_t n_moves) {
 // Moves done and proposals accepted so far (synchronous).
 PB_API int pb_mh_stats(pb_mh* h, uint64_t* moves, uint64_t* accepted) {
   if (!h) return PB_EINVAL;
-  unsigned long long acc = 0;
+  MhCounters ctr{};
   uint32_t st = 0u;
-  if (cudaMemcpyAsync(&acc, h->ws + h->L.cnt, 8, cudaMemcpyDeviceToHost, h->v.st) != cudaSuccess ||
-      cudaMemcpyAsync(&st, h->mlp->status, 4, cudaMemcpyDeviceToHost, h->v.st) != cudaSuccess ||
+  if (cudaMemcpyAsync(&ctr, h->c.ws, sizeof ctr, cudaMemcpyDeviceToHost, h->v.st) != cudaSuccess ||
+      cudaMemcpyAsync(&st, h->c.mlp->status, 4, cudaMemcpyDeviceToHost, h->v.st) != cudaSuccess ||
       cudaStreamSynchronize(h->v.st) != cudaSuccess)
     return PB_ECUDA;
   if (moves) *moves = h->moves;
-  if (accepted) *accepted = acc;
+  if (accepted) *accepted = ctr.accepted;
   // a bounded wait of the network's kernels ran out: the moves since are not valid
   return st != 0u ? (int)st : PB_OK;
 }
@@ -490,6 +593,7 @@ PB_API int pb_mh_stats(pb_mh* h, uint64_t* moves, uint64_t* accepted) {
 PB_API void pb_mh_free(pb_mh* h) {
   if (!h) return;
   cudaStreamSynchronize(h->v.st);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
   for (auto& g : h->graphs)
     if (g) cudaGraphExecDestroy(g);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
@@ -514,9 +618,9 @@ PB_API int pb_run_collect_paths(pb_run* run, int model, void* d_ws, size_t ws_by
   const uint32_t warps = v.groups * (uint32_t)m.d;
   unslice_kernel<<<(warps * 32 + T - 1) / T, T, 0, v.st>>>(v.state, m.n, m.d, v.groups, P);
   const uint32_t nmask = m.n == 32 ? 0xFFFFFFFFu : ((1u << m.n) - 1u);
-  collect_kernel<<<(v.chains + T - 1) / T, T, 0, v.st>>>(
-      P, reinterpret_cast<const LayerTab*>(ws + L.tab), m.beta, nmask, m.d, v.chains, d_paths,
-      capacity, reinterpret_cast<unsigned long long*>(d_count));
+  collect_kernel<<<1, 1024, 0, v.st>>>(P, reinterpret_cast<const LayerTab*>(ws + L.tab), m.beta, nmask,
+                                       m.d, v.chains, d_paths, capacity,
+                                       reinterpret_cast<unsigned long long*>(d_count));
   if (e == cudaSuccess) e = cudaGetLastError();
   // host layer table must outlive the staged copy
   if (e == cudaSuccess) e = cudaStreamSynchronize(v.st);

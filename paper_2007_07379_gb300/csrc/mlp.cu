@@ -298,29 +298,54 @@ __global__ void pack_canonical_kernel(const __nv_bfloat16* __restrict__ src, int
 }
 
 // dY = (sigmoid(l) - t) / B for the first n columns (0 beyond), bf16, both
-// layouts; db3 += column sums (fp32); loss += BCE / B.
+// layouts.
+__device__ __forceinline__ float bce_grad(float l, float t, int B) {
+  return (1.f / (1.f + __expf(-l)) - t) / (float)B;
+}
 __global__ void bce_grad_kernel(const float* __restrict__ logits, const float* __restrict__ target,
                                 int B, int n, int npad, __nv_bfloat16* __restrict__ dY,
-                                __nv_bfloat16* __restrict__ dYt, float* __restrict__ db3,
-                                float* __restrict__ loss) {
+                                __nv_bfloat16* __restrict__ dYt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * npad) return;
   const int r = i / npad, c = i % npad;
-  float g = 0.f, l_term = 0.f;
-  if (c < n) {
-    const float l = logits[(size_t)r * npad + c];
-    const float t = target[(size_t)r * n + c];
-    const float s = 1.f / (1.f + __expf(-l));
-    g = (s - t) / (float)B;
-    // -[t log s(l) + (1-t) log s(-l)] = softplus(l) - t l, computed stably
-    const float sp = fmaxf(l, 0.f) + log1pf(__expf(-fabsf(l)));
-    l_term = (sp - t * l) / (float)B;
-    atomicAdd(&db3[c], g);
-  }
+  const float g = c < n ? bce_grad(logits[(size_t)r * npad + c], target[(size_t)r * n + c], B) : 0.f;
   const __nv_bfloat16 gb = __float2bfloat16(g);
   dY[(size_t)r * npad + c] = gb;
   dYt[(size_t)c * B + r] = gb;
-  if (loss && l_term != 0.f) atomicAdd(loss, l_term);
+}
+
+// Block c < n: db3[c] = sum over the rows of the fp32 gradient of column c;
+// block n: loss = the mean BCE, -[t log s(l) + (1-t) log s(-l)] =
+// softplus(l) - t l, computed stably.  Each sum is taken in a fixed order
+// (per-thread strided partial sums, then a tree), so that a training run is
+// reproducible bit for bit.
+__global__ void __launch_bounds__(256) bce_sums_kernel(const float* __restrict__ logits,
+                                                       const float* __restrict__ target, int B,
+                                                       int n, int npad, float* __restrict__ db3,
+                                                       float* __restrict__ loss) {
+  __shared__ float part[256];
+  const int c = blockIdx.x, tid = threadIdx.x;
+  float acc = 0.f;
+  if (c < n) {
+    for (int r = tid; r < B; r += 256)
+      acc += bce_grad(logits[(size_t)r * npad + c], target[(size_t)r * n + c], B);
+  } else {
+    for (int i = tid; i < B * n; i += 256) {
+      const int r = i / n, q = i % n;
+      const float l = logits[(size_t)r * npad + q], t = target[(size_t)r * n + q];
+      acc += (fmaxf(l, 0.f) + log1pf(__expf(-fabsf(l))) - t * l) / (float)B;
+    }
+  }
+  part[tid] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (tid < s) part[tid] += part[tid + s];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (c < n) db3[c] = part[0];
+    else if (loss) *loss = part[0];
+  }
 }
 
 // out[j] = sum_b M[j][b] (bf16 rows, fp32 sums), one warp per row.
@@ -474,8 +499,10 @@ cudaError_t mlp_bwd(pb_mlp* p, int rows) {
   const int B = rows, H = p->H, T = 256;
   cudaMemsetAsync(p->g, 0, p->n_params * 4, p->st);
   cudaMemsetAsync(p->loss, 0, 4, p->st);
-  pb::bce_grad_kernel<<<(B * p->npad + T - 1) / T, T, 0, p->st>>>(
-      p->logits, p->target, B, p->n, p->npad, p->dY, p->dYt, p->g + p->off_b3, p->loss);
+  pb::bce_grad_kernel<<<(B * p->npad + T - 1) / T, T, 0, p->st>>>(p->logits, p->target, B, p->n,
+                                                                   p->npad, p->dY, p->dYt);
+  pb::bce_sums_kernel<<<p->n + 1, 256, 0, p->st>>>(p->logits, p->target, B, p->n, p->npad,
+                                                   p->g + p->off_b3, p->loss);
   if ((e = pb::transpose_bf16(p->H2, B, H, p->H2t, p->st)) != cudaSuccess) return e;
   if ((e = pb::transpose_bf16(p->H1, B, H, p->H1t, p->st)) != cudaSuccess) return e;
   if ((e = pb::transpose_bf16(p->X, B, p->kin, p->Xt, p->st)) != cudaSuccess) return e;
@@ -725,6 +752,9 @@ struct FusedArgs {
   float* lq;
   float* lqf;
   const uint32_t* move_dev;
+  const int* k_dev;  // per-chain modes: when set, the suffix start k is read here
+                     // (kFusedLogQ: layers k + blockIdx.y; kFusedSample: j = k,
+                     // jlast = d) and CTAs past layer d leave at once
   uint32_t beta, k0, k1, group0;
   int n, d, k, j, jlast;  // kFusedSample: layers j .. jlast, one after the other
   // shared-memory layout (byte offsets; fused_layout) and W2 chunk buffers
@@ -841,8 +871,10 @@ __global__ void __launch_bounds__(kFusedThreads) mlp_fused_kernel(FusedArgs a) {
   const int H = a.H, kin = a.kin, npad = a.npad, nb = min(a.nb, kMaxNb);
   const int nchunks = (H + 63) / 64;
   auto chunk_k = [&](int c) { return (c == nchunks - 1 && (H % 64)) ? (H % 64) : 64; };
-  const int jfirst = MODE == kFusedLogQ ? a.k + (int)blockIdx.y : a.j;
-  const int jend = MODE == kFusedSample ? a.jlast : jfirst;
+  const int kk = (MODE != kFusedLogits && a.k_dev) ? *a.k_dev : a.k;
+  const int jfirst = MODE == kFusedLogQ ? kk + (int)blockIdx.y : (a.k_dev ? kk : a.j);
+  const int jend = MODE == kFusedSample ? (a.k_dev ? a.d : a.jlast) : jfirst;
+  if (MODE != kFusedLogits && (jfirst < 1 || jfirst > a.d)) return;  // whole CTA: no layer here
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
   if (tid == 0) {
@@ -1148,6 +1180,24 @@ cudaError_t mlp_fused_logq(pb_mlp* p, const uint32_t* P, uint32_t beta, int chai
   return cudaGetLastError();
 }
 
+// The same with the suffix start read from k_dev on the device (a grid over
+// all d layers; the CTAs of layers before k leave at once), so that one
+// captured graph serves every k.
+cudaError_t mlp_fused_logq_dev(pb_mlp* p, const uint32_t* P, uint32_t beta, int chains,
+                               const int* k_dev, float* lq, cudaStream_t st) {
+  FusedArgs a = fused_args(p, chains);
+  a.P = P;
+  a.beta = beta;
+  a.k = 1;
+  a.k_dev = k_dev;
+  a.lq = lq;
+  dim3 grid((chains + 127) / 128, p->d);
+  const size_t smem = fused_layout(a);
+  if (smem == 0) return cudaErrorInvalidValue;
+  mlp_fused_kernel<kFusedLogQ><<<grid, kFusedThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 // Layers j .. jlast of the proposal for all chains (one launch; each CTA
 // carries its 128 chains through the layers in turn).
 cudaError_t mlp_fused_sample(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uint32_t beta, int chains,
@@ -1160,6 +1210,29 @@ cudaError_t mlp_fused_sample(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uint32_
   a.k = k;
   a.j = j;
   a.jlast = jlast;
+  a.lqf = lqf;
+  a.k0 = k0;
+  a.k1 = k1;
+  a.move_dev = move_dev;
+  a.group0 = group0;
+  const size_t smem = fused_layout(a);
+  if (smem == 0) return cudaErrorInvalidValue;
+  mlp_fused_kernel<kFusedSample><<<(chains + 127) / 128, kFusedThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Layers k .. d of the proposal, k read from k_dev on the device.
+cudaError_t mlp_fused_sample_dev(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uint32_t beta,
+                                 int chains, const int* k_dev, float* lqf, uint32_t k0, uint32_t k1,
+                                 const uint32_t* move_dev, uint32_t group0, cudaStream_t st) {
+  FusedArgs a = fused_args(p, chains);
+  a.P = P;
+  a.Pn = Pn;
+  a.beta = beta;
+  a.k = 1;
+  a.j = 1;
+  a.jlast = p->d;
+  a.k_dev = k_dev;
   a.lqf = lqf;
   a.k0 = k0;
   a.k1 = k1;

@@ -163,7 +163,8 @@ struct WsHeader {
   uint32_t status;         // 0 = ok, else a pb_status code set by a kernel
   uint32_t work_next;      // persistent scheduler counter
   uint32_t sweep0;         // absolute index of the next sweep
-  uint32_t pad[61];
+  uint32_t periods_left;   // learned runs: move periods still to run in a launch
+  uint32_t pad[60];
 };
 
 // Dynamic shared memory the sweep and exact-sampler kernels may use per CTA
@@ -245,6 +246,39 @@ cudaError_t mlp_fused_logq(pb_mlp* p, const uint32_t* P, uint32_t beta, int chai
 cudaError_t mlp_fused_sample(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uint32_t beta, int chains,
                              int k, int j, int jlast, float* lqf, uint32_t k0, uint32_t k1,
                              const uint32_t* move_dev, uint32_t group0, cudaStream_t st);
+cudaError_t mlp_fused_logq_dev(pb_mlp* p, const uint32_t* P, uint32_t beta, int chains,
+                               const int* k_dev, float* lq, cudaStream_t st);
+cudaError_t mlp_fused_sample_dev(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uint32_t beta,
+                                 int chains, const int* k_dev, float* lqf, uint32_t k0, uint32_t k1,
+                                 const uint32_t* move_dev, uint32_t group0, cudaStream_t st);
+
+// Learned-proposal moves on one model (learned.cu): the run's chain words,
+// the network and a device region of mh_region_bytes(d, groups) bytes
+// (256-byte aligned) holding the per-chain words, log q terms, the move
+// counters and the layer table.
+struct MhCtx {
+  const pb_model* model = nullptr;
+  pb_mlp* mlp = nullptr;
+  uint32_t* state = nullptr;  // [group][k-1][q] chain words of the model
+  uint32_t chains = 0, groups = 0, group0 = 0;
+  uint64_t seed = 0;
+  char* ws = nullptr;
+};
+// Counters at the start of a move region: proposals accepted, moves done.
+struct MhCounters {
+  unsigned long long accepted;
+  uint32_t moves;
+  int32_t k;  // suffix start of the current move
+};
+size_t mh_region_bytes(int d, uint32_t groups);
+// True when the network takes the fused inference kernel (k_in <= 96,
+// n <= 32): then a move draws its suffix start on the device.
+bool mh_fused(const pb_mlp* mlp);
+// Zeroes the region and uploads the layer table (synchronous on st).
+cudaError_t mh_region_init(const MhCtx& c, cudaStream_t st);
+// Enqueues one move with its suffix start drawn on the device from the seed
+// and the move counter (fused networks; capturable, no host synchronisation).
+cudaError_t mh_enqueue_move_dev(const MhCtx& c, cudaStream_t st);
 
 // What the learned-proposal code needs to know about one model of a run.
 struct RunView {

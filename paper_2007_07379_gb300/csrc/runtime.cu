@@ -708,6 +708,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) & ~(a - 1); }
 struct ModelSlots {
   size_t model_dev, desc, rec, init, state, hist, valid, samples, alpha_sorted, alpha_slot, amp,
       clamp, cpl, uph, glk, tacc, trec;
+  size_t mh;  // PB_LEARNED: the model's move region (mh_region_bytes), else unused
   uint32_t bins, groups, n_batches;
   int clamp_mw;  // mask words per p-bit of the clamp table (0: not clamped)
 };
@@ -807,8 +808,17 @@ int check_cfg(const pb_model* m, const pb_run_cfg& c) {
   if (!m) return PB_EINVAL;
   if (c.chains == 0 || c.record_every == 0) return PB_EINVAL;
   if ((uint64_t)c.group0 + (c.chains + 31) / 32 > 0xFFFFFFFFull) return PB_ERANGE;
-  // the learned sampler has its own entry points (pb_mh_*) on a PB_GIBBS run
-  if (c.sampler != PB_GIBBS && c.sampler != PB_ELIM && c.sampler != PB_ELIM_CLAMP) return PB_EINVAL;
+  if (c.sampler != PB_GIBBS && c.sampler != PB_LEARNED && c.sampler != PB_ELIM &&
+      c.sampler != PB_ELIM_CLAMP)
+    return PB_EINVAL;
+  // the learned proposal: a network for this circuit that the fused kernel
+  // takes (its suffix start is drawn on the device), a move period, and a
+  // model whose acceptance needs the J energy only
+  if (c.sampler == PB_LEARNED) {
+    const pb_mlp* mlp = c.proposal;
+    if (!mlp || c.mh_every == 0 || m->wgt || mlp->n != m->n || mlp->d != m->d || !mh_fused(mlp))
+      return PB_EINVAL;
+  }
   if (c.sampler == PB_ELIM_CLAMP && (c.alphas == nullptr || c.n_alphas != 1)) return PB_EINVAL;
   // clamping assumes uniform free outputs: no coupled general gate
   if (c.sampler == PB_ELIM_CLAMP && (m->n_coupled > 0 || m->n_ccx > 0)) return PB_EINVAL;
@@ -874,6 +884,7 @@ int plan(pb_model* const* models, const pb_run_cfg* cfgs, int nm, Layout& L) {
     s.glk = take(m->glk.size() * sizeof(GLink));
     s.tacc = take(m->tacc.size() * sizeof(TAcc));
     s.trec = take(m->trec.size() * sizeof(TRec));
+    s.mh = take(c.sampler == PB_LEARNED ? mh_region_bytes(m->d, s.groups) : 0);
   }
   L.work = take((size_t)total_groups * 4);
   L.total = align_up(off, 256);
@@ -912,6 +923,11 @@ struct pb_run {
   bool timed = false;
   double last_flips = 0.0;
   std::map<uint32_t, cudaGraphExec_t> graphs;
+  // PB_LEARNED models: their move contexts (mlp == nullptr for the others),
+  // the common move period and a device counter of the loop's periods
+  std::vector<MhCtx> mh;
+  bool learned = false;
+  uint32_t mh_every = 0;
   WsHeader* hdr() const { return reinterpret_cast<WsHeader*>(ws + L.hdr); }
   RunModelDev* d_rm() const { return reinterpret_cast<RunModelDev*>(ws + L.rm); }
 };
@@ -919,6 +935,90 @@ struct pb_run {
 namespace {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? PB_OK : PB_ECUDA; }
+
+// The device-side loop of a learned run's launch: the count of move periods
+// is set at the start, and the last kernel of each period counts down and
+// tells the graph's while node whether to run another.
+__global__ void periods_init_kernel(WsHeader* hdr, uint32_t periods) { hdr->periods_left = periods; }
+__global__ void periods_step_kernel(WsHeader* hdr, cudaGraphConditionalHandle loop) {
+  const uint32_t left = hdr->periods_left - 1u;
+  hdr->periods_left = left;
+  cudaGraphSetConditional(loop, left > 0u ? 1u : 0u);
+}
+
+// The launches of n sweeps of every model (no moves), in stream order.
+cudaError_t enqueue_sweeps(pb_run* r, uint32_t n_sweeps, cudaStream_t st) {
+  if (r->elim)
+    return launch_elim(r->d_rm(), r->nm, r->total_groups,
+                       reinterpret_cast<const uint32_t* const*>(r->ws + r->L.init_ptrs), n_sweeps,
+                       r->elim_smem, r->hdr(), st, r->wgt, r->elim_warps);
+  if (r->persistent)
+    return launch_sweeps_persistent(r->d_rm(), r->nm, reinterpret_cast<const uint32_t*>(r->ws + r->L.work),
+                                    r->total_groups, n_sweeps, r->cons, r->prod, r->max_col, r->nc,
+                                    r->grid, r->smem, r->hdr(), st);
+  return launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->cons, r->prod, r->max_col,
+                       r->nc, r->smem, r->hdr(), st, r->wgt, r->ext);
+}
+
+// Graph of n sweeps of a learned run (Fig. 2 Step 1 with the network as the
+// proposal, interleaved with the heat-bath sweeps): n / mh_every periods of
+// [one suffix move of every PB_LEARNED model, mh_every sweeps] run by a
+// while node on the device, then n mod mh_every sweeps without a move.
+cudaError_t build_learned_graph(pb_run* r, uint32_t n_sweeps, cudaStream_t cap, cudaGraph_t* out) {
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  const uint32_t periods = n_sweeps / r->mh_every, rem = n_sweeps % r->mh_every;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  auto fail = [&](cudaError_t err) {
+    cudaGraphDestroy(g);
+    return err;
+  };
+  cudaGraphNode_t last = nullptr;
+  if (periods > 0) {
+    if ((e = cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, mode)) != cudaSuccess) return fail(e);
+    periods_init_kernel<<<1, 1, 0, cap>>>(r->hdr(), periods);
+    e = cudaGetLastError();
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) return fail(e != cudaSuccess ? e : e2);
+    size_t nn = 1;
+    cudaGraphNode_t init = nullptr;
+    if ((e = cudaGraphGetNodes(g, &init, &nn)) != cudaSuccess || nn != 1) return fail(cudaErrorUnknown);
+    cudaGraphConditionalHandle loop;
+    if ((e = cudaGraphConditionalHandleCreate(&loop, g, 1u, cudaGraphCondAssignDefault)) != cudaSuccess)
+      return fail(e);
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond = nullptr;
+    if ((e = cudaGraphAddNode(&cond, g, &init, nullptr, 1, &cp)) != cudaSuccess) return fail(e);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, mode)) != cudaSuccess)
+      return fail(e);
+    for (const MhCtx& x : r->mh)
+      if (x.mlp && e == cudaSuccess) e = mh_enqueue_move_dev(x, cap);
+    if (e == cudaSuccess) e = enqueue_sweeps(r, r->mh_every, cap);
+    if (e == cudaSuccess) {
+      periods_step_kernel<<<1, 1, 0, cap>>>(r->hdr(), loop);
+      e = cudaGetLastError();
+    }
+    e2 = cudaStreamEndCapture(cap, &body);
+    if (e != cudaSuccess || e2 != cudaSuccess) return fail(e != cudaSuccess ? e : e2);
+    last = cond;
+  }
+  if (rem > 0) {
+    if ((e = cudaStreamBeginCaptureToGraph(cap, g, last ? &last : nullptr, nullptr, last ? 1 : 0, mode)) !=
+        cudaSuccess)
+      return fail(e);
+    e = enqueue_sweeps(r, rem, cap);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) return fail(e != cudaSuccess ? e : e2);
+  }
+  *out = g;
+  return cudaSuccess;
+}
 
 // Applies a CTA shape (consumer and producer threads, multiples of 32) to
 // the run: shared-memory size, histogram placement and the persistent grid.
@@ -1149,6 +1249,24 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
     r->flips_per_sweep += (double)c.chains * (double)npb;
   }
   r->total_groups = base;
+  // Learned models: one move period for the run; their move regions.
+  r->mh.assign(n_models, MhCtx{});
+  for (int i = 0; i < n_models; ++i) {
+    const pb_run_cfg& c = r->cfgs[i];
+    if (c.sampler != PB_LEARNED) continue;
+    if (r->learned && c.mh_every != r->mh_every) return PB_EINVAL;
+    r->learned = true;
+    r->mh_every = c.mh_every;
+    MhCtx& x = r->mh[i];
+    x.model = r->models[i].get();
+    x.mlp = const_cast<pb_mlp*>(c.proposal);
+    x.state = r->rm[i].state;
+    x.chains = c.chains;
+    x.groups = r->L.ms[i].groups;
+    x.group0 = c.group0;
+    x.seed = c.seed;
+    x.ws = ws + r->L.ms[i].mh;
+  }
   // Exact samplers: warps per CTA.  Samples are independent, so a CTA with
   // more warps hides more latency; 32 while the groups leave SMs free, 16 up
   // to two groups per SM, else 8 (several CTAs per SM do the same), and
@@ -1188,6 +1306,11 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
                   reinterpret_cast<const uint32_t* const*>(ws + r->L.init_ptrs), init_smem,
                   r->hdr(), st);
   if (e != cudaSuccess) return PB_ECUDA;
+  if (r->learned) {
+    if (mlp_prepare() != cudaSuccess) return PB_ECUDA;
+    for (const MhCtx& x : r->mh)
+      if (x.mlp && mh_region_init(x, st) != cudaSuccess) return PB_ECUDA;
+  }
   // host copies must outlive the (possibly staged) async copies
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return PB_ECUDA;
@@ -1210,23 +1333,18 @@ PB_API int pb_run_sweeps(pb_run* r, uint32_t n_sweeps) {
     cudaGraph_t graph = nullptr;
     if (!r->cap_st && cudaStreamCreateWithFlags(&r->cap_st, cudaStreamNonBlocking) != cudaSuccess)
       return PB_ECUDA;
-    cudaError_t e = cudaStreamBeginCapture(r->cap_st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return PB_ECUDA;
-    if (r->elim)
-      e = launch_elim(r->d_rm(), r->nm, r->total_groups,
-                      reinterpret_cast<const uint32_t* const*>(r->ws + r->L.init_ptrs), n_sweeps,
-                      r->elim_smem, r->hdr(), r->cap_st, r->wgt, r->elim_warps);
-    else if (r->persistent)
-      e = launch_sweeps_persistent(r->d_rm(), r->nm, reinterpret_cast<const uint32_t*>(r->ws + r->L.work),
-                                   r->total_groups, n_sweeps, r->cons, r->prod, r->max_col, r->nc,
-                                   r->grid, r->smem, r->hdr(), r->cap_st);
-    else
-      e = launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->cons, r->prod, r->max_col,
-                        r->nc, r->smem, r->hdr(), r->cap_st, r->wgt, r->ext);
-    cudaError_t e2 = cudaStreamEndCapture(r->cap_st, &graph);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      return PB_ECUDA;
+    cudaError_t e;
+    if (r->learned) {
+      if (build_learned_graph(r, n_sweeps, r->cap_st, &graph) != cudaSuccess) return PB_ECUDA;
+    } else {
+      e = cudaStreamBeginCapture(r->cap_st, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return PB_ECUDA;
+      e = enqueue_sweeps(r, n_sweeps, r->cap_st);
+      cudaError_t e2 = cudaStreamEndCapture(r->cap_st, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return PB_ECUDA;
+      }
     }
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -1250,7 +1368,25 @@ PB_API int pb_run_wait(pb_run* r) {
   uint32_t status = 0;
   e = cudaMemcpy(&status, &r->hdr()->status, 4, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return PB_ECUDA;
+  // learned runs: an expired bounded wait in a network's kernels
+  for (const MhCtx& x : r->mh) {
+    if (!x.mlp || status != 0) continue;
+    if (cudaMemcpy(&status, x.mlp->status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PB_ECUDA;
+  }
   return status == 0 ? PB_OK : (int)status;
+}
+
+PB_API int pb_run_moves(pb_run* r, int model, uint64_t* moves, uint64_t* accepted) {
+  if (!r || model < 0 || model >= r->nm) return PB_EINVAL;
+  const MhCtx& x = r->mh[model];
+  if (!x.mlp) return PB_ESTATE;  // not a PB_LEARNED model
+  MhCounters c{};
+  if (cudaStreamSynchronize(r->st) != cudaSuccess ||
+      cudaMemcpy(&c, x.ws, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PB_ECUDA;
+  if (moves) *moves = c.moves;
+  if (accepted) *accepted = c.accepted;
+  return PB_OK;
 }
 
 PB_API int pb_run_phase_sums(const pb_run* r, int model, double* re, double* im, uint64_t* counts,
@@ -1498,7 +1634,8 @@ PB_API int pb_run_checkpoint(const pb_run* r, void* host_buf, size_t bytes, size
   for (int i = 0; i < r->nm; ++i) {
     const ModelSlots& s = r->L.ms[i];
     need += (size_t)s.groups * r->models[i]->n * r->models[i]->d * 4 +
-            (size_t)s.n_batches * s.bins * 64 + (size_t)s.n_batches * 16;
+            (size_t)s.n_batches * s.bins * 64 + (size_t)s.n_batches * 16 +
+            (r->mh[i].mlp ? sizeof(MhCounters) : 0);  // learned: the move counters
   }
   if (bytes_needed) *bytes_needed = need;
   if (!host_buf) return PB_OK;
@@ -1522,6 +1659,10 @@ PB_API int pb_run_checkpoint(const pb_run* r, void* host_buf, size_t bytes, size
     p += s.n_batches * 8;
     if (cudaMemcpy(p, r->ws + s.samples, s.n_batches * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return PB_ECUDA;
     p += s.n_batches * 8;
+    if (r->mh[i].mlp) {
+      if (cudaMemcpy(p, r->mh[i].ws, sizeof(MhCounters), cudaMemcpyDeviceToHost) != cudaSuccess) return PB_ECUDA;
+      p += sizeof(MhCounters);
+    }
   }
   return PB_OK;
 }
@@ -1551,6 +1692,10 @@ PB_API int pb_run_restore(pb_run* r, const void* host_buf, size_t bytes) {
     p += s.n_batches * 8;
     if (cudaMemcpy(r->ws + s.samples, p, s.n_batches * 8, cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;
     p += s.n_batches * 8;
+    if (r->mh[i].mlp) {
+      if (cudaMemcpy(r->mh[i].ws, p, sizeof(MhCounters), cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;
+      p += sizeof(MhCounters);
+    }
   }
   uint32_t sw32 = (uint32_t)sw;
   if (cudaMemcpy(&r->hdr()->sweep0, &sw32, 4, cudaMemcpyHostToDevice) != cudaSuccess) return PB_ECUDA;

@@ -1353,6 +1353,7 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
 // Sweep index advance after a launch (the sweep kernels read hdr->sweep0, so
 // one captured graph replays correctly any number of times).
 __global__ void advance_kernel(WsHeader* hdr, uint32_t n_sweeps) { hdr->sweep0 += n_sweeps; }
+__global__ void reset_work_kernel(WsHeader* hdr) { hdr->work_next = 0u; }
 
 // nc: colour steps per sweep (the largest over the launch's models; 2..4).
 // wgt: some model has general gates (the WGT instantiation); ext: some model
@@ -1388,8 +1389,9 @@ cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, cons
                                      int max_col, int nc, int grid, size_t smem_bytes,
                                      WsHeader* hdr, cudaStream_t st) {
   const int threads = cons + prod + 32;
-  cudaError_t e = cudaMemsetAsync(&hdr->work_next, 0, sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
+  // the work counter is cleared by a kernel (a graph may hold this launch
+  // inside a device-side loop, whose body takes kernels)
+  reset_work_kernel<<<1, 1, 0, st>>>(hdr);
   const Shape sh{cons, prod};
   if (nc <= 2)
     sweep_persistent_kernel<2><<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work,

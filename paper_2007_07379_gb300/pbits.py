@@ -76,6 +76,8 @@ _SIGS = {
                                      ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(_VP)]),
     "pb_run_sweeps": (ctypes.c_int, [_VP, ctypes.c_uint32]),
     "pb_run_wait": (ctypes.c_int, [_VP]),
+    "pb_run_moves": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                    ctypes.POINTER(ctypes.c_uint64)]),
     "pb_run_histogram": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     "pb_run_phase_sums": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pb_run_amplitudes": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
@@ -336,6 +338,12 @@ class Run:
 
     def wait(self):
         _check(load().pb_run_wait(self._h), "pb_run_wait")
+
+    def moves(self, model: int = 0):
+        """(moves done, proposals accepted) of a PB_LEARNED model."""
+        mv, acc = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(load().pb_run_moves(self._h, model, ctypes.byref(mv), ctypes.byref(acc)), "pb_run_moves")
+        return mv.value, acc.value
 
     def histogram(self, model: int = 0):
         cnt = np.zeros((self.bins(model), 8), dtype=np.uint64)

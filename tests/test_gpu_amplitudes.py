@@ -120,8 +120,9 @@ def _train(r, net, d, sweeps=60, steps=300):
 
 def test_learned_workload_amplitudes_plain_and_learned():
     """Learned workload (n=16, d=24, 4096 chains): plain Gibbs (2e4 sweeps)
-    and Gibbs with a suffix move per sweep from a trained network (1e4
-    moves and sweeps), each against the 65,536-amplitude state vector."""
+    and the PB_LEARNED run mode with a suffix move per sweep from a trained
+    network (1e4 moves and sweeps in one pb_run_sweeps call), each against
+    the 65,536-amplitude state vector."""
     wl = W.learned()
     exact = oracle.statevector(wl.n, wl.d, wl.gates)
     N = oracle.valid_paths_per_output(wl.n, wl.d, wl.gates)
@@ -134,14 +135,12 @@ def test_learned_workload_amplitudes_plain_and_learned():
     _, src = _run(wl, seed=wl.seed + 100)
     net = pbits.Mlp(wl.n, wl.d, hidden=256, batch=4096, seed=21)
     _train(src, net, wl.d)
-    _, r = _run(wl, seed=wl.seed + 2)
-    L = pbits.Learned(r, net)
-    for _ in range(100):
-        for _ in range(100):
-            L.step(1)
-            r.sweeps(1)
-        r.wait()
-    moves, acc = L.stats()
+    # the learned sampler as a run mode: one graph, a move before every sweep
+    r = pbits.Run([m], [pbits.RunCfg(seed=wl.seed + 2, chains=wl.chains, n_batches=32,
+                                     sampler=pbits.PB_LEARNED, proposal=net, mh_every=1)])
+    r.sweeps(10_000)
+    r.wait()
+    moves, acc = r.moves()
     assert moves == 10_000 and acc > 0
     print(f"learned move acceptance {acc / (moves * wl.chains):.4f}")
     psi, se = r.amplitudes()
