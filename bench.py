@@ -153,12 +153,22 @@ def _oracle_gibbs(oracle, wl, **kw):
     return oracle.gibbs(wl.n, wl.d, wl.gates, J=wl.J, seed=wl.seed, **kw)
 
 
-def cpu_oracle_rate(wl, budget_s: float = 12.0, chains: int | None = None):
+def cpu_oracle_rate(wl, budget_s: float = 10.0, chains: int | None = None, threads: int | None = None):
     """The oracle's reference Gibbs sampler on a bounded sample of the same
-    workload (host cores, OpenMP over chains, about `budget_s` seconds).
-    Returns (flips/s, cores, sample)."""
+    workload (host cores, OpenMP over chains, about `budget_s` seconds; all
+    the host's threads, or `threads`).  Returns (flips/s, cores, sample)."""
     import oracle
     n, d = wl.n, wl.d
+    all_threads = oracle.num_threads()
+    if threads is not None:
+        oracle.set_num_threads(threads)
+    try:
+        return _cpu_oracle_rate(oracle, wl, n, d, budget_s, chains)
+    finally:
+        oracle.set_num_threads(all_threads)
+
+
+def _cpu_oracle_rate(oracle, wl, n, d, budget_s, chains):
     c = chains or 128
     t0 = time.perf_counter()
     _oracle_gibbs(oracle, wl, chains=c, sweeps=20)
@@ -352,7 +362,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_oracle_rate(wl)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        v1, _, sample1 = cpu_oracle_rate(wl, budget_s=6.0, chains=32, threads=1)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_core": {"value": v1, "unit": UNIT, "cores": 1, "sample": sample1}}
 
     if rank == 0:
         line = {
@@ -370,21 +382,71 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+def _top16(name: str):
+    """The 16 outputs of largest |psi| of a learned workload and their exact
+    amplitudes (tests/golden/learned_top16.json, written from the FP64 state
+    vector by tests/golden/make_learned_top16.py)."""
+    with open(os.path.join(ROOT, "tests", "golden", "learned_top16.json")) as f:
+        d = json.load(f)[name]
+    return np.array(d["alphas"], dtype=np.int64), np.array(d["re"]) + 1j * np.array(d["im"])
+
+
+def _eps_curve(run, chunk: int, seconds: float, alphas, exact):
+    """Error eps(t) = max over the 16 outputs of |psi_hat - psi|, read after
+    1, 2, 4, ... pb_run_sweeps calls of `chunk` sweeps (or samples) and at
+    the end; t = the summed device time of those calls (CUDA events around
+    each graph replay), until `seconds` of device time."""
+    pts, t, k, nxt = [], 0.0, 0, 1
+    wall0 = time.perf_counter()
+    while True:
+        run.sweeps(chunk)
+        t += run.stats()["last_ms"] / 1e3
+        k += 1
+        last = t >= seconds or time.perf_counter() - wall0 > 3 * seconds + 30
+        if k == nxt or last:
+            psi, _ = run.amplitudes()
+            pts.append((t, float(np.abs(psi[alphas] - exact).max())))
+            nxt *= 2
+        if last:
+            return pts, k
+
+
+def _eps_fit(pts, eps: float):
+    """Least-squares fit of log eps = log A - log t / 2 (the 1/sqrt(T) law of
+    Eq. U26) over the points in the last 64th of the time range and on, and
+    the time to eps it gives, (A / eps)^2; the free-slope fit beside it; the
+    first measured time with eps(t) <= eps, if any."""
+    t = np.array([p[0] for p in pts])
+    e = np.array([p[1] for p in pts])
+    use = (t >= t[-1] / 64) & (e > 0)
+    A = float(np.exp(np.mean(np.log(e[use]) + 0.5 * np.log(t[use]))))
+    slope = float(np.polyfit(np.log(t[use]), np.log(e[use]), 1)[0]) if use.sum() >= 2 else None
+    hit = [float(tt) for tt, ee in pts if ee <= eps]
+    return {"A": A, "t_to_eps_s": (A / eps) ** 2, "free_slope": slope,
+            "t_first_below_eps_s": hit[0] if hit else None, "eps_final": float(e[-1]),
+            "t_final_s": float(t[-1]), "points": [[float(a), float(b)] for a, b in pts]}
+
+
 def learned_comparison(dev, stream, seconds: float = 8.0, train_paths: int = 1_000_000,
                        train_steps: int = 3000, wl=None):
-    """Wall time to an amplitude error of 1 % for plain Gibbs and for Gibbs
-    with the learned suffix move, on the learned workload (n=16, d=24, 4096
-    chains).  Both run for the same wall time; the error of each is its
-    batch-means standard error (32 batches of chain groups, Eq. U26), and the
-    time to reach eps follows from the 1/sqrt(t) law: t_eps = t (SE / eps)^2.
-    The network is trained first on valid paths collected from plain Gibbs
-    (the training time is reported separately)."""
+    """Wall time to 1 % amplitude error, learned proposal vs plain Gibbs (and
+    the exact i.i.d. sampler as the ceiling), on the learned workload (n=16,
+    d=24, 4096 chains).  The error is measured against the exact amplitudes:
+    eps(t) = max over the 16 largest |psi_alpha| of |psi_hat - psi|, read at
+    doubling intervals for `seconds` of device time per sampler; eps(t) is
+    fitted with the 1/sqrt(t) law and extrapolated to eps = 0.01.  The
+    network is trained first on valid paths of plain Gibbs (time reported
+    separately); the learned sampler is the PB_LEARNED run mode, one suffix
+    move before every sweep, all in one graph per call."""
     import torch
     from paper_2007_07379_gb300 import pbits
     wl = wl or W.learned()
     n, d = wl.n, wl.d
+    alphas, exact = _top16(wl.name)
+    eps = 0.01
     out = {"workload": f"{wl.name}: random Clifford+T n={n} d={d}, {wl.chains} chains, hidden 256",
-           "eps": 0.01}
+           "eps": eps, "error": "max |psi_hat - psi| over the 16 largest |psi| (FP64 state vector)",
+           "top16_abs_psi": float(np.abs(exact).max())}
     with torch.cuda.stream(stream):
         model = pbits.Model(n, d, wl.gates, wl.J)
         # 1. collect valid paths from plain Gibbs and train the network
@@ -408,60 +470,29 @@ def learned_comparison(dev, stream, seconds: float = 8.0, train_paths: int = 1_0
         out.update({"train_paths": cap, "train_steps": train_steps, "collect_s": t_collect,
                     "train_s": t_train, "loss_first": float(lc[:10].mean()), "loss_last": float(lc[-10:].mean()),
                     "h": model.info()["h"]})
+        del paths
 
-        def timed(learned: bool, sweeps_per_move: int = 1):
-            run = pbits.Run([model], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, n_batches=32)],
-                            stream=stream)
-            L = pbits.Learned(run, net) if learned else None
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            steps = 0
-            while time.perf_counter() - t0 < seconds:
-                if learned:
-                    for _ in range(16):  # enqueue a bounded amount of work, then wait
-                        L.step(1)
-                        run.sweeps(sweeps_per_move)
-                        steps += sweeps_per_move
-                    run.wait()
-                else:
-                    run.sweeps(200)
-                    run.wait()
-                    steps += 200
-            torch.cuda.synchronize(dev)
-            t = time.perf_counter() - t0
-            psi, se = run.amplitudes()
-            se_rms = float(np.sqrt(np.mean(se ** 2)))
-            res = {"wall_s": t, "sweeps": steps, "se_rms": se_rms, "se_psi0": float(se[0]),
-                   "t_to_eps_s": t * (se_rms / 0.01) ** 2}
-            if learned:
-                mv, acc = L.stats()
+        def arm(sampler, chunk, **kw):
+            run = pbits.Run([model], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, n_batches=32,
+                                                   sampler=sampler, **kw)], stream=stream)
+            pts, calls = _eps_curve(run, chunk, seconds, alphas, exact)
+            res = _eps_fit(pts, eps)
+            res["sweeps_or_samples"] = calls * chunk
+            if sampler == pbits.PB_LEARNED:
+                mv, acc = run.moves()
                 res["moves"] = mv
                 res["accept"] = acc / max(mv * wl.chains, 1)
-                res["ms_per_move_and_sweep"] = 1e3 * t / max(mv, 1)
+                res["ms_per_move_and_sweep"] = 1e3 * res["t_final_s"] / max(mv, 1)
             return res
 
-        def timed_elim():
-            # the i.i.d. ceiling: exact paths on the eliminated network
-            run = pbits.Run([model], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, n_batches=32,
-                                                   sampler=pbits.PB_ELIM)], stream=stream)
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            steps = 0
-            while time.perf_counter() - t0 < seconds:
-                run.sweeps(200)
-                run.wait()
-                steps += 200
-            t = time.perf_counter() - t0
-            psi, se = run.amplitudes()
-            se_rms = float(np.sqrt(np.mean(se ** 2)))
-            return {"wall_s": t, "samples_per_chain": steps, "se_rms": se_rms, "se_psi0": float(se[0]),
-                    "t_to_eps_s": t * (se_rms / 0.01) ** 2}
-
-        out["plain"] = timed(False)
-        out["learned"] = timed(True)
-        out["elim"] = timed_elim()
+        out["plain"] = arm(pbits.PB_GIBBS, 200)
+        out["learned"] = arm(pbits.PB_LEARNED, 20, proposal=net, mh_every=1)
+        out["elim"] = arm(pbits.PB_ELIM, 200)
         out["ratio_plain_over_learned"] = out["plain"]["t_to_eps_s"] / out["learned"]["t_to_eps_s"]
         out["ratio_elim_over_learned"] = out["elim"]["t_to_eps_s"] / out["learned"]["t_to_eps_s"]
+        # the learned arm's time with its training included, for the same error
+        out["ratio_plain_over_learned_with_training"] = out["plain"]["t_to_eps_s"] / (
+            out["learned"]["t_to_eps_s"] + t_collect + t_train)
     return out
 
 
@@ -613,10 +644,11 @@ def batched_measurement(dev, stream, sweeps: int = 10_000):
             "shape": run.shape()}
 
 
-def large_measurement(dev, stream, sweeps: int = 2000, moves: int = 20):
+def large_measurement(dev, stream, sweeps: int = 2000, moves: int = 40):
     """The large workload: n=24, d=32 (792 p-bits), 65536 chains, 64 output
-    amplitudes; plain sweeps and learned suffix moves (untrained network:
-    the cost of a move does not depend on the weights)."""
+    amplitudes; plain sweeps, and the PB_LEARNED run mode (a suffix move
+    before every sweep, one graph per call; untrained network: the cost of a
+    move does not depend on the weights)."""
     import torch
     from paper_2007_07379_gb300 import pbits
     wl = W.large()
@@ -629,17 +661,20 @@ def large_measurement(dev, stream, sweeps: int = 2000, moves: int = 20):
         run.wait()
         ms = run.stats()["last_ms"]
         net = pbits.Mlp(wl.n, wl.d, hidden=256, batch=4096, seed=3, stream=stream)
-        L = pbits.Learned(run, net)
-        L.step(2)
-        run.wait()
-        t0 = time.perf_counter()
-        L.step(moves)
-        run.wait()
-        t_move = (time.perf_counter() - t0) / moves
+        lr = pbits.Run([m], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, alphas=wl.alphas,
+                                          sampler=pbits.PB_LEARNED, proposal=net, mh_every=1)],
+                       stream=stream)
+        lr.sweeps(moves)
+        lr.wait()
+        lr.sweeps(moves)
+        lr.wait()
+        ms_l = lr.stats()["last_ms"]
     flips = wl.chains * wl.n * wl.d * sweeps
+    per_sweep = ms / sweeps
     return {"workload": "large: random Clifford+T n=24 d=32 (792 p-bits), 65536 chains, 64 amplitudes",
             "sweeps": sweeps, "launch_ms": ms, "flips_per_s": flips / (ms * 1e-3),
-            "ms_per_mh_move": t_move * 1e3}
+            "learned_run_ms_per_move_and_sweep": ms_l / moves,
+            "ms_per_mh_move": ms_l / moves - per_sweep}
 
 
 def kernel_rev() -> str:

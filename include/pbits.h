@@ -196,7 +196,10 @@ PB_API void pb_model_free(pb_model* m);
  * tag 1 = initial H and coupled-PB_U outputs, tag 6 = the Metropolis
  * acceptance of coupled p-bits).  A p-bit whose violation count changes by v
  * when it goes 0 -> 1 is redrawn as [v < 0] XOR [u < thr[|v|]]  (heat-bath,
- * Fig. 2 Steps 1-2).  One sweep visits the four colour classes in order. */
+ * Fig. 2 Steps 1-2).  One sweep visits the model's colour classes in
+ * increasing order (pb_model_colours: a DSATUR colouring of the p-bits'
+ * interaction graph, two to four classes; p-bits of one class share no
+ * link, so a class is redrawn in parallel). */
 enum { PB_GIBBS = 0, PB_LEARNED = 1, PB_ELIM = 2, PB_ELIM_CLAMP = 3 };
 /* PB_ELIM: the exact sampler on the eliminated network (Appendix: without
  * the link constraints every non-H bit is a function of the previous layer

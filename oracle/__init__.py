@@ -56,6 +56,8 @@ def _load():
             lib.orc_modexp.restype = ctypes.c_uint64
             lib.orc_modexp.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
             lib.orc_num_threads.restype = ctypes.c_int
+            lib.orc_set_num_threads.restype = ctypes.c_int
+            lib.orc_set_num_threads.argtypes = [ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -286,6 +288,11 @@ def path_phase(n: int, d: int, gates, path, beta: int = 0) -> int:
 
 def num_threads() -> int:
     return _load().orc_num_threads()
+
+
+def set_num_threads(t: int) -> int:
+    """Threads of the oracle's OpenMP loops from now on; returns the count."""
+    return _load().orc_set_num_threads(int(t))
 
 
 def estimate_amplitudes(cnt: np.ndarray, valid: int, h: int) -> np.ndarray:

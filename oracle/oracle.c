@@ -1055,3 +1055,15 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops that follow (at least 1); returns the count in
+ * force.  For timing the same code on one core and on all of them. */
+int orc_set_num_threads(int t) {
+#ifdef _OPENMP
+  omp_set_num_threads(t < 1 ? 1 : t);
+  return omp_get_max_threads();
+#else
+  (void)t;
+  return 1;
+#endif
+}

@@ -6,10 +6,11 @@
 // in shared memory for the whole launch; global memory sees the image only at
 // the start and the end of a launch and the histogram atomics in between.
 //
-// One sweep = four colour classes in order (Fig. 2 Steps 1-2 for every p-bit);
-// p-bits of one class share no factor (the layer parity separates adjacent
-// layers, the second bit separates the control and target of a CNOT in the
-// next layer), so the threads of the CTA redraw a whole class in parallel.
+// One sweep = the model's colour classes in order (Fig. 2 Steps 1-2 for
+// every p-bit; two to four classes, three on every workload circuit, from a
+// DSATUR colouring of the p-bits' interaction graph at compile time); p-bits
+// of one class share no link, so the threads of the CTA redraw a whole class
+// in parallel.
 // After each recorded sweep the CTA evaluates every chain's validity and path
 // phase bit-sliced and adds one count to the bin (end state, phase class)
 // (Fig. 2 Step 3).
