@@ -150,7 +150,9 @@ struct RunModelDev {
   int32_t pad2;
   // models with PB_U gates (else nullptr): couplings by p, gate phases.
   // Their histogram slots per (batch, bin) are {re (double), im (double),
-  // count (u64), unused...} instead of 8 phase-class counters.
+  // count (u64), compensation of re (double), compensation of im (double),
+  // unused...} instead of 8 phase-class counters: the phase sums are
+  // compensated (the sum is re + its compensation).
   const Cpl* cpl;
   const UPh* uph;
   const GLink* glk;        // models with Toffoli gates, else nullptr

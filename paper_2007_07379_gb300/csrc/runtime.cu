@@ -1031,16 +1031,18 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
   r->max_col = maxcol;
   r->threads = cons + prod + 32;
   // Shared-memory histograms: counted per CTA, added to the global counters
-  // once per launch.  Used when the bins fit (128 KiB for one circuit, 32 KiB
-  // per circuit in a batch so that several CTAs share an SM); otherwise the
-  // record adds to global memory directly.
-  const size_t cap = r->nm == 1 ? (128u << 10) : (32u << 10);
+  // once per launch.  Used when the bins fit (up to 4096 bins for one
+  // circuit, 1024 per circuit in a batch so that several CTAs share an SM;
+  // 32 bytes a bin, 40 with general gates); otherwise the record adds to
+  // global memory directly.
+  const size_t cap_bins = r->nm == 1 ? 4096u : 1024u;
   size_t smem = 0;
   for (int i = 0; i < r->nm; ++i) {
     const pb_model& m = *r->models[i];
     const uint32_t bins = r->L.ms[i].bins;
     const size_t base = sweep_smem_bytes(m.n, m.d, cons, maxcol, 0, r->wgt);
-    const bool use = (size_t)bins * 32 <= cap && base + (size_t)bins * 32 <= kSweepSmemMax;
+    const size_t per_bin = sweep_smem_bytes(m.n, m.d, cons, maxcol, 1, r->wgt) - base;
+    const bool use = bins <= cap_bins && base + (size_t)bins * per_bin <= kSweepSmemMax;
     r->rm[i].hist_smem = use ? 1u : 0u;
     smem = std::max(smem, sweep_smem_bytes(m.n, m.d, cons, maxcol, use ? bins : 0, r->wgt));
   }
@@ -1403,12 +1405,14 @@ PB_API int pb_run_phase_sums(const pb_run* r, int model, double* re, double* im,
     uint64_t cn = 0;
     for (uint32_t b = 0; b < s.n_batches; ++b) {
       const uint64_t* c = &h[((size_t)b * s.bins + i) * 8];
-      if (wgt) {
-        double x, y;
+      if (wgt) {  // compensated sums: slot 3 / 4 hold the compensations of re / im
+        double x, y, cx, cy;
         std::memcpy(&x, &c[0], 8);
         std::memcpy(&y, &c[1], 8);
-        sr += x;
-        si += y;
+        std::memcpy(&cx, &c[3], 8);
+        std::memcpy(&cy, &c[4], 8);
+        sr += x + cx;
+        si += y + cy;
         cn += c[2];
       } else {
         for (int k = 0; k < 8; ++k) {

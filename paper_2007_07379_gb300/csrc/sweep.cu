@@ -316,6 +316,19 @@ __device__ __forceinline__ void set_status(WsHeader* hdr, int code) {
   if (hdr) atomicCAS(&hdr->status, 0u, (uint32_t)code);
 }
 
+// Compensated FP64 accumulation of the phase sums: *s += x by an atomic add,
+// whose old value gives the exact rounding error of fl(old + x) (Knuth's
+// two-sum), and that error (plus `carry`, a compensation brought along) is
+// added to the compensation word *c.  The sum is *s + *c; the rounding of the
+// big partial sums no longer accumulates over the samples.
+__device__ __forceinline__ void atomic_add_comp(double* s, double* c, double x, double carry = 0.0) {
+  const double old = atomicAdd(s, x);
+  const double nw = old + x;
+  const double bp = nw - old;
+  const double err = (old - (nw - bp)) + (x - bp) + carry;
+  if (err != 0.0) atomicAdd(c, err);
+}
+
 // CTA roles: `cons` consumer threads redraw the p-bits of the current colour
 // class; `prod` producer threads compute the Philox planes of the next class,
 // compared group by group with each p-bit's two thresholds,
@@ -345,7 +358,7 @@ __host__ __device__ inline int image_words(int n, int d) { return (n_words(n, d)
 __host__ __device__ inline size_t group_smem_bytes(int n, int d, int cons, int max_col,
                                                    uint32_t hist_bins, bool wgt = false) {
   return (size_t)3 * image_words(n, d) * 4 + (size_t)n * d * sizeof(Desc) +
-         (size_t)n * d * sizeof(Rec) + (size_t)hist_bins * 8 * 4 +
+         (size_t)n * d * sizeof(Rec) + (size_t)hist_bins * (wgt ? 10 : 8) * 4 +
          (size_t)4 * cons * sizeof(ClassEnt) +
          (size_t)2 * ((size_t)kPre * max_col + (wgt ? (size_t)kPreC * cons : 0)) * sizeof(uint4);
 }
@@ -489,14 +502,15 @@ struct Recorder {
       }
       if (lane == leader) {
         if (shist) {
-          double* sd = reinterpret_cast<double*>(shist);
-          atomicAdd(&sd[2u * (uint32_t)b], r);
-          atomicAdd(&sd[2u * (uint32_t)b + 1u], q);
-          atomicAdd(&shist[4u * rm.bins + (uint32_t)b], (uint32_t)__popc(m));
+          double* sd = reinterpret_cast<double*>(shist) + 4u * (uint32_t)b;
+          atomic_add_comp(&sd[0], &sd[2], r);
+          atomic_add_comp(&sd[1], &sd[3], q);
+          atomicAdd(&shist[8u * rm.bins + (uint32_t)b], (uint32_t)__popc(m));
         } else {
           unsigned long long* c = rm.hist + ((size_t)batch * rm.bins + (uint32_t)b) * 8u;
-          atomicAdd(reinterpret_cast<double*>(c), r);
-          atomicAdd(reinterpret_cast<double*>(c + 1), q);
+          double* cd = reinterpret_cast<double*>(c);
+          atomic_add_comp(&cd[0], &cd[3], r);
+          atomic_add_comp(&cd[1], &cd[4], q);
           atomicAdd(c + 2, (unsigned long long)__popc(m));
         }
       }
@@ -544,14 +558,15 @@ struct Recorder {
           double cs, sn;
           phasor(phase, cs, sn);
           if (shist) {
-            double* sd = reinterpret_cast<double*>(shist);
-            atomicAdd(&sd[2u * (uint32_t)bin], cs);
-            atomicAdd(&sd[2u * (uint32_t)bin + 1u], sn);
-            atomicAdd(&shist[4u * rm.bins + (uint32_t)bin], 1u);
+            double* sd = reinterpret_cast<double*>(shist) + 4u * (uint32_t)bin;
+            atomic_add_comp(&sd[0], &sd[2], cs);
+            atomic_add_comp(&sd[1], &sd[3], sn);
+            atomicAdd(&shist[8u * rm.bins + (uint32_t)bin], 1u);
           } else {
             unsigned long long* c = rm.hist + ((size_t)batch * rm.bins + (uint32_t)bin) * 8u;
-            atomicAdd(reinterpret_cast<double*>(c), cs);
-            atomicAdd(reinterpret_cast<double*>(c + 1), sn);
+            double* cd = reinterpret_cast<double*>(c);
+            atomic_add_comp(&cd[0], &cd[3], cs);
+            atomic_add_comp(&cd[1], &cd[4], sn);
             atomicAdd(c + 2, 1ull);
           }
           done = true;
@@ -660,7 +675,9 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   Rec* srec = reinterpret_cast<Rec*>(sdesc + npb);
   uint32_t* after_rec = reinterpret_cast<uint32_t*>(srec + npb);
   uint32_t* shist = rm.hist_smem ? after_rec : nullptr;
-  const uint32_t hist_words = rm.bins * 8u;
+  // per bin: 8 u32 phase-class counters, or (general gates) 4 doubles (re,
+  // im and their compensations) and a u32 count (10 words with padding)
+  const uint32_t hist_words = rm.bins * (wgt_m ? 10u : 8u);
   ClassEnt* sclass = reinterpret_cast<ClassEnt*>(after_rec + (rm.hist_smem ? hist_words : 0u));
   // two buffers, each [max_col][kPre] sweep-draw outputs, then (general-gate
   // runs) [cons][kPreC] acceptance outputs of the class's first cons p-bits
@@ -932,15 +949,16 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   uint32_t* out = rm.state + (size_t)g * npb;
 #pragma unroll 1
   for (int i = tid; i < npb; i += T) out[i] = W[n + i];
-  if (shist && wgt_m) {  // (re, im) doubles per bin, then u32 counts
+  if (shist && wgt_m) {  // (re, im, comp re, comp im) doubles per bin, then u32 counts
     const double* sd = reinterpret_cast<const double*>(shist);
 #pragma unroll 1
     for (uint32_t i = tid; i < rm.bins; i += T) {
-      const uint32_t cn = shist[4u * rm.bins + i];
+      const uint32_t cn = shist[8u * rm.bins + i];
       if (!cn) continue;
       unsigned long long* c = rm.hist + ((size_t)batch * rm.bins + i) * 8u;
-      atomicAdd(reinterpret_cast<double*>(c), sd[2u * i]);
-      atomicAdd(reinterpret_cast<double*>(c + 1), sd[2u * i + 1u]);
+      double* cd = reinterpret_cast<double*>(c);
+      atomic_add_comp(&cd[0], &cd[3], sd[4u * i], sd[4u * i + 2u]);
+      atomic_add_comp(&cd[1], &cd[4], sd[4u * i + 1u], sd[4u * i + 3u]);
       atomicAdd(c + 2, (unsigned long long)cn);
     }
   } else if (shist) {
@@ -1239,9 +1257,9 @@ __device__ inline void phase_sum(const unsigned long long* c, double& re, double
 __device__ inline void batch_sum(const RunModelDev& rm, bool wgt, uint32_t b, uint32_t bin,
                                  double& re, double& im) {
   const unsigned long long* c = rm.hist + ((size_t)b * rm.bins + bin) * 8u;
-  if (wgt) {
-    re = __longlong_as_double((long long)c[0]);
-    im = __longlong_as_double((long long)c[1]);
+  if (wgt) {  // the compensated sums: sum + compensation
+    re = __longlong_as_double((long long)c[0]) + __longlong_as_double((long long)c[3]);
+    im = __longlong_as_double((long long)c[1]) + __longlong_as_double((long long)c[4]);
   } else {
     phase_sum(c, re, im);
   }
