@@ -71,13 +71,46 @@ __global__ void unslice_kernel(const uint32_t* __restrict__ state, int n, int d,
   P[(size_t)(g * 32 + lane) * d + j] = y;
 }
 
+// SplitMix64 (Steele, Lea, Flood 2014): the suffix start of a move.
+__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__host__ __device__ inline int suffix_start(uint64_t seed, uint32_t move, int d) {
+  return 1 + (int)(splitmix64(seed ^ (0xA5A5ull << 40) ^ move) % (uint64_t)d);
+}
+
+// The start of a move: unslice as above, and (thread 0) the suffix start k*
+// from the seed and the move count (SplitMix64, so that one captured graph
+// serves every move), and the proposal's log q sums cleared.
+__global__ void move_begin_kernel(const uint32_t* __restrict__ state, int n, int d, uint32_t groups,
+                                  uint32_t* __restrict__ P, MhCounters* __restrict__ ctr, uint64_t seed,
+                                  float* __restrict__ lqf, uint32_t chains) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) ctr->k = suffix_start(seed, ctr->moves, d);
+  if (i < chains) lqf[i] = 0.f;
+  const uint32_t w = i >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= groups * (uint32_t)d) return;
+  const uint32_t g = w / d, j = w % d;
+  const uint32_t x = lane < n ? state[((size_t)g * d + j) * n + lane] : 0u;
+  const uint32_t y = warp_transpose(x, lane);
+  P[(size_t)(g * 32 + lane) * d + j] = y;
+}
+
 // Per-chain words -> bit-sliced words for layers k..d (1-based), k read from
 // k_dev; one warp per (group, layer) over all d layers, the warps of layers
 // before k leave at once.
-__global__ void slice_kernel(const uint32_t* __restrict__ P, int n, int d, const int* __restrict__ k_dev,
+__global__ void slice_kernel(const uint32_t* __restrict__ P, int n, int d, MhCounters* __restrict__ ctr,
                              uint32_t groups, uint32_t* __restrict__ state) {
   const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  const int* k_dev = &ctr->k;
+  // the end of the move: its count (read by no kernel of this move after
+  // the acceptance, which ran before)
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->moves += 1u;
   if (w >= groups * (uint32_t)d) return;
   const uint32_t g = w / d, j = w % d;
   if ((int)j + 1 < *k_dev) return;  // the whole warp: layer j+1 is before the suffix
@@ -182,64 +215,60 @@ __global__ void sample_kernel(const float* __restrict__ logits, int npad, int n,
 }
 
 // Violation counts of layers k..d for the current and proposed suffix, the
-// Metropolis-Hastings decision, and the accepted suffix copied into P.
+// Metropolis-Hastings decision, and the accepted suffix copied into P.  One
+// warp per chain: lane l takes layers k + l, k + l + 32, ...; the warp sums
+// the counts and the log q terms (a fixed tree), lane 0 decides.
 __global__ void accept_kernel(uint32_t* __restrict__ P, const uint32_t* __restrict__ Pn,
                               const LayerTab* __restrict__ tab, uint32_t beta, uint32_t nmask,
                               int d, float J, const float* __restrict__ lq,
                               const float* __restrict__ lqf, uint32_t chains, uint32_t k0,
                               uint32_t k1, MhCounters* __restrict__ ctr, uint32_t group0) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= chains) return;
+  __shared__ uint32_t n_acc;
+  if (threadIdx.x == 0) n_acc = 0u;
+  __syncthreads();
+  const uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const bool in = c < chains;  // warp-uniform
   const uint32_t move = ctr->moves;
   const int k = ctr->k;
-  unsigned long long* n_accept = &ctr->accepted;
-  const uint32_t* cur = P + (size_t)c * d;
-  const uint32_t* prop = Pn + (size_t)c * d;
-  const uint32_t base = k == 1 ? beta : cur[k - 2];
-  int v = 0, vn = 0;
-  uint32_t pc = base, pn = base;
-  float lrev = 0.f;
-  for (int j = k; j <= d; ++j) {
-    const LayerTab& L = tab[j - 1];
-    const uint32_t link = ~L.hmask & nmask;
-    v += __popc((cur[j - 1] ^ layer_map(L, pc)) & link);
-    vn += __popc((prop[j - 1] ^ layer_map(L, pn)) & link);
-    pc = cur[j - 1];
-    pn = prop[j - 1];
-    lrev += lq[(size_t)c * d + (j - 1)];
+  bool acc = false;
+  if (in) {
+    const uint32_t* cur = P + (size_t)c * d;
+    const uint32_t* prop = Pn + (size_t)c * d;
+    int v = 0, vn = 0;
+    float lrev = 0.f;
+    for (int j = k + lane; j <= d; j += 32) {
+      const LayerTab& L = tab[j - 1];
+      const uint32_t link = ~L.hmask & nmask;
+      const uint32_t pc = j == 1 ? beta : cur[j - 2];   // s_{j-1}
+      const uint32_t pn = j == k ? pc : prop[j - 2];    // s'_{j-1}, s'_{k-1} = s_{k-1}
+      v += __popc((cur[j - 1] ^ layer_map(L, pc)) & link);
+      vn += __popc((prop[j - 1] ^ layer_map(L, pn)) & link);
+      lrev += lq[(size_t)c * d + (j - 1)];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      v += __shfl_xor_sync(0xffffffffu, v, off);
+      vn += __shfl_xor_sync(0xffffffffu, vn, off);
+      lrev += __shfl_xor_sync(0xffffffffu, lrev, off);
+    }
+    if (lane == 0) {
+      const float logA = -J * (float)(vn - v) + lrev - lqf[c];
+      const uint32_t gc = group0 * 32u + c;
+      const uint32_t u = philox4x32_10(make_uint4(gc, move, 0xFFFFu | (kTagMH << 16), 0u), k0, k1).x;
+      const float uf = ((float)(u >> 8) + 0.5f) * (1.f / 16777216.f);
+      acc = logf(uf) < logA;
+      if (acc) atomicAdd(&n_acc, 1u);
+    }
+    acc = __shfl_sync(0xffffffffu, acc, 0);
+    if (acc)
+      for (int j = k + lane; j <= d; j += 32) P[(size_t)c * d + (j - 1)] = prop[j - 1];
   }
-  const float logA = -J * (float)(vn - v) + lrev - lqf[c];
-  const uint32_t gc = group0 * 32u + c;
-  const uint32_t u = philox4x32_10(make_uint4(gc, move, 0xFFFFu | (kTagMH << 16), 0u), k0, k1).x;
-  const float uf = ((float)(u >> 8) + 0.5f) * (1.f / 16777216.f);
-  const bool acc = logf(uf) < logA;
-  // one counter update per warp (the accepted lanes' count)
-  const unsigned act = __activemask();
-  const unsigned accm = __ballot_sync(act, acc);
-  if (accm != 0u && (int)(threadIdx.x & 31u) == __ffs((int)act) - 1)
-    atomicAdd(n_accept, (unsigned long long)__popc(accm));
-  if (acc)
-    for (int j = k; j <= d; ++j) P[(size_t)c * d + (j - 1)] = prop[j - 1];
+  __syncthreads();
+  if (threadIdx.x == 0 && n_acc) atomicAdd(&ctr->accepted, (unsigned long long)n_acc);
 }
 
-__global__ void mh_advance_kernel(MhCounters* ctr) { ctr->moves += 1u; }
-
-// SplitMix64 (Steele, Lea, Flood 2014): the suffix start of a move.
-__host__ __device__ inline uint64_t splitmix64(uint64_t x) {
-  x += 0x9E3779B97F4A7C15ull;
-  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-  return x ^ (x >> 31);
-}
-__host__ __device__ inline int suffix_start(uint64_t seed, uint32_t move, int d) {
-  return 1 + (int)(splitmix64(seed ^ (0xA5A5ull << 40) ^ move) % (uint64_t)d);
-}
-
-// k* of the current move from the seed and the move counter (device side,
-// so one captured graph serves every move); set_k_kernel: a host-drawn k*.
-__global__ void mh_pick_kernel(MhCounters* ctr, uint64_t seed, int d) {
-  ctr->k = suffix_start(seed, ctr->moves, d);
-}
+// A host-drawn k* (networks that do not fit the fused kernel).
 __global__ void set_k_kernel(MhCounters* ctr, int k) { ctr->k = k; }
 
 __global__ void zero_f32_kernel(float* __restrict__ x, uint32_t n) {
@@ -388,11 +417,11 @@ cudaError_t finish_move(const MhCtx& c, const MhPtrs& q, cudaStream_t st) {
   const int n = m.n, d = m.d, T = 256;
   const uint32_t nmask = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
   const uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);
-  accept_kernel<<<(c.chains + T - 1) / T, T, 0, st>>>(q.P, q.Pn, q.tab, m.beta, nmask, d, (float)m.J,
-                                                      q.lq, q.lqf, c.chains, k0, k1, q.ctr, c.group0);
+  accept_kernel<<<(c.chains * 32 + T - 1) / T, T, 0, st>>>(q.P, q.Pn, q.tab, m.beta, nmask, d, (float)m.J,
+                                                           q.lq, q.lqf, c.chains, k0, k1, q.ctr, c.group0);
+  // slicing back also counts the move
   const uint32_t sw = c.groups * (uint32_t)d;
-  slice_kernel<<<(sw * 32 + T - 1) / T, T, 0, st>>>(q.P, n, d, &q.ctr->k, c.groups, c.state);
-  mh_advance_kernel<<<1, 1, 0, st>>>(q.ctr);
+  slice_kernel<<<(sw * 32 + T - 1) / T, T, 0, st>>>(q.P, n, d, q.ctr, c.groups, c.state);
   return cudaGetLastError();
 }
 
@@ -464,15 +493,41 @@ cudaError_t mh_enqueue_move_dev(const MhCtx& c, cudaStream_t st) {
   const uint32_t C = c.chains;
   const uint32_t k0 = (uint32_t)c.seed, k1 = (uint32_t)(c.seed >> 32);
   const uint32_t warps = c.groups * (uint32_t)d;
-  unslice_kernel<<<(warps * 32 + T - 1) / T, T, 0, st>>>(c.state, n, d, c.groups, q.P);
-  mh_pick_kernel<<<1, 1, 0, st>>>(q.ctr, c.seed, d);
-  cudaError_t e = mlp_fused_logq_dev(c.mlp, q.P, m.beta, (int)C, &q.ctr->k, q.lq, st);
-  if (e != cudaSuccess) return e;
-  zero_f32_kernel<<<(C + T - 1) / T, T, 0, st>>>(q.lqf, C);
+  move_begin_kernel<<<(warps * 32 + T - 1) / T, T, 0, st>>>(c.state, n, d, c.groups, q.P, q.ctr, c.seed,
+                                                            q.lqf, C);
+  // the proposal (sequential over the suffix layers, one CTA per 128
+  // chains) first on st; log q of the current suffix (one CTA per tile and
+  // layer) beside it on the side stream; both read P and k only
+  cudaError_t e = cudaSuccess;
+  if (c.side) {
+    if ((e = cudaEventRecord(c.fork, st)) != cudaSuccess || (e = cudaStreamWaitEvent(c.side, c.fork, 0)) != cudaSuccess)
+      return e;
+  }
   e = mlp_fused_sample_dev(c.mlp, q.P, q.Pn, m.beta, (int)C, &q.ctr->k, q.lqf, k0, k1, &q.ctr->moves,
                            c.group0, st);
   if (e != cudaSuccess) return e;
+  e = mlp_fused_logq_dev(c.mlp, q.P, m.beta, (int)C, &q.ctr->k, q.lq, c.side ? c.side : st);
+  if (e != cudaSuccess) return e;
+  if (c.side) {
+    if ((e = cudaEventRecord(c.join, c.side)) != cudaSuccess || (e = cudaStreamWaitEvent(st, c.join, 0)) != cudaSuccess)
+      return e;
+  }
   return finish_move(c, q, st);
+}
+
+cudaError_t mh_ctx_open(MhCtx& c) {
+  cudaError_t e = cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming);
+  return e;
+}
+
+void mh_ctx_close(MhCtx& c) {
+  if (c.fork) cudaEventDestroy(c.fork);
+  if (c.join) cudaEventDestroy(c.join);
+  if (c.side) cudaStreamDestroy(c.side);
+  c.fork = c.join = nullptr;
+  c.side = nullptr;
 }
 
 }  // namespace pb
@@ -536,10 +591,15 @@ PB_API int pb_mh_create(pb_run* run, int model, pb_mlp* mlp, void* d_ws, size_t 
   h->v = v;
   h->c = mh_ctx(v, mlp, static_cast<char*>(d_ws));
   h->graphs.assign(m.d + 1, nullptr);
-  cudaError_t e = mh_region_init(h->c, v.st);
+  cudaError_t e = mh_ctx_open(h->c);
+  if (e == cudaSuccess) e = mh_region_init(h->c, v.st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(mlp->st);
   if (e == cudaSuccess) e = mlp_prepare();
-  if (e != cudaSuccess) { delete h; return PB_ECUDA; }
+  if (e != cudaSuccess) {
+    mh_ctx_close(h->c);
+    delete h;
+    return PB_ECUDA;
+  }
   *out = h;
   return PB_OK;
 }
@@ -597,6 +657,7 @@ PB_API void pb_mh_free(pb_mh* h) {
   for (auto& g : h->graphs)
     if (g) cudaGraphExecDestroy(g);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  mh_ctx_close(h->c);
   delete h;
 }
 

@@ -1146,6 +1146,299 @@ template __global__ void mlp_fused_kernel<kFusedLogits>(FusedArgs);
 template __global__ void mlp_fused_kernel<kFusedLogQ>(FusedArgs);
 template __global__ void mlp_fused_kernel<kFusedSample>(FusedArgs);
 
+// ===========================================================================
+// The per-chain modes with 64-row tiles: twice the CTAs of the 128-row
+// kernel, and with half the rows the x and h tiles shrink enough that W1,
+// W2 and W3 all stay in shared memory for the whole launch (one bulk copy
+// each at the start; no W2 chunks streamed per layer).  MMAs are M = 64
+// (idesc M field 4): row r of an accumulator sits in TMEM lane
+// 32 (r / 16) + r % 16, so warp w (lane quadrant q = w % 4) holds rows
+// 16 q .. 16 q + 15; its epilogue reads them with the 16x256b shape (thread
+// t: rows t / 4 and 8 + t / 4 of the 16, columns 2 (t % 4) and the next, of
+// each 8-column block), and the four warps of a quadrant split the hidden
+// columns.  The logits of row 16 q + i are read by lane i < 16 of warp q
+// (32x32b shape), which draws or scores the row's bits as the 128-row
+// kernel does.  Same modes, arguments and results (the accumulation order
+// of the tensor cores may differ in the last bit).
+// ===========================================================================
+constexpr int kTile64 = 64;
+
+// Dynamic shared memory of the 64-row kernel: x (64 x kin), h (64 x H),
+// W1, the whole W2 image, W3 and the biases; 0 when they do not fit.
+inline size_t fused64_layout(FusedArgs& a) {
+  const size_t X = round_kb((size_t)kTile64 * a.kin * 2), Hs = round_kb((size_t)kTile64 * a.H * 2);
+  const size_t W1 = round_kb((size_t)a.H * a.kin * 2), W2 = round_kb((size_t)a.H * a.H * 2);
+  const size_t W3 = round_kb((size_t)a.npad * a.H * 2);
+  const size_t B = round_kb((size_t)(2 * a.H + a.npad) * 4);
+  a.offH = (uint32_t)X;
+  a.offW1 = (uint32_t)(X + Hs);
+  a.offWb = (uint32_t)(X + Hs + W1);  // W2, chunk c at + c * H * 64 * 2
+  a.offW3 = (uint32_t)(X + Hs + W1 + W2);
+  a.offB = (uint32_t)(X + Hs + W1 + W2 + W3);
+  a.chunk_bytes = (uint32_t)(a.H * 64 * 2);
+  a.nb = 0;
+  const size_t total = X + Hs + W1 + W2 + W3 + B;
+  if (a.H % 64 != 0 || total > kFusedSmemMax) return 0;
+  return total;
+}
+
+// 16 lanes x 256 bits (8 fp32 columns) of the warp's TMEM lane quadrant, 8
+// blocks of 8 columns (addresses taddr + 8 j), one completion wait: v[4 j +
+// 0, 1] = rows t / 4, columns 8 j + 2 (t % 4) + {0, 1}; v[4 j + 2, 3] = row
+// 8 + t / 4, the same columns.
+__device__ __forceinline__ void tmem_ld_16x256b_x8(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[4 * j]), "=r"(r[4 * j + 1]), "=r"(r[4 * j + 2]), "=r"(r[4 * j + 3])
+                 : "r"(taddr + 8u * (uint32_t)j)
+                 : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kFusedThreads) mlp_move64_kernel(FusedArgs a) {
+  static_assert(MODE == kFusedLogQ || MODE == kFusedSample, "per-chain modes only");
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ uint64_t bars[3];  // weights delivered, MMAs of a GEMM done, drain
+  __shared__ uint32_t tmem_base;
+  __shared__ uint32_t wrd[kTile64];  // drawn words of the layer, by row
+  // the four parts of a row exchange their bits and log q terms here
+  __shared__ uint32_t xw[kFusedParts][kTile64];
+  __shared__ float xq[kFusedParts][kTile64];
+  uint64_t* wbar = &bars[0];
+  uint64_t* done = &bars[1];
+  uint64_t* drain = &bars[2];
+  uint8_t* sX = sm;
+  uint8_t* sH = sm + a.offH;
+  uint8_t* sW1 = sm + a.offW1;
+  uint8_t* sW2 = sm + a.offWb;
+  uint8_t* sW3 = sm + a.offW3;
+  float* sB = reinterpret_cast<float*>(sm + a.offB);  // b1 [H], b2 [H], b3 [npad]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, part = warp >> 2;
+  const int H = a.H, kin = a.kin, npad = a.npad;
+  const int r0 = blockIdx.x * kTile64;
+  const int kk = a.k_dev ? *a.k_dev : a.k;
+  // kFusedLogQ: layers kk + y L .. kk + y L + L - 1 (L = a.jlast layers per
+  // CTA, so the weights are loaded once for several layers); kFusedSample:
+  // the suffix, layer after layer
+  const int jfirst = MODE == kFusedLogQ ? kk + (int)blockIdx.y * a.jlast : (a.k_dev ? kk : a.j);
+  const int jend = MODE == kFusedSample ? (a.k_dev ? a.d : a.jlast) : min(jfirst + a.jlast - 1, a.d);
+  if (jfirst < 1 || jfirst > a.d) return;  // whole CTA: no layer here
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 256);
+  if (tid == 0) {
+    for (int i = 0; i < 3; ++i) tc::mbar_init(&bars[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < H; i += kFusedThreads) {
+    sB[i] = a.b1[i];
+    sB[H + i] = a.b2[i];
+  }
+  for (int i = tid; i < npad; i += kFusedThreads) sB[2 * H + i] = a.b3[i];
+  __syncthreads();  // TMEM address, barriers and biases visible
+  const uint32_t tb = tmem_base;
+  if (tid == 0) {
+    const uint32_t w1 = (uint32_t)(H * kin * 2), w2 = (uint32_t)(H * H * 2), w3 = (uint32_t)(npad * H * 2);
+    tc::mbar_expect_tx(wbar, w1 + w2 + w3);
+    tc::bulk_load(sW1, a.W1p, w1, wbar);
+    tc::bulk_load(sW2, a.W2p, w2, wbar);
+    tc::bulk_load(sW3, a.W3p, w3, wbar);
+  }
+  bool ok = true, weights = false;
+  uint32_t dph = 0u;
+  // A wait whose outcome the whole CTA shares (every thread takes the same
+  // branches and barriers after it).
+  auto wait_all = [&](uint64_t* bar, uint32_t ph) {
+    const bool w = ok && tc::mbar_wait(bar, ph);
+    ok = __syncthreads_and(w) != 0;
+    tc::fence_after_sync();
+  };
+  auto publish = [&]() {
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+  // h = relu(D + bias) in bf16 into sH (canonical, K = H): warp (quad,
+  // part) converts rows 16 quad .. + 15, columns 64 part .. + 63
+  const uint32_t tq = tb + ((uint32_t)(quad * 32) << 16);
+  auto epilogue = [&](const float* bias) {
+    const int ra = 16 * quad + (lane >> 2), rb = ra + 8;
+    uint8_t* ha = sH + (ra >> 3) * (H * 16) + (ra & 7) * 16;
+    uint8_t* hb = sH + (rb >> 3) * (H * 16) + (rb & 7) * 16;
+    for (int c0 = 64 * part; c0 < H; c0 += 256) {
+      float v[32];
+      tmem_ld_16x256b_x8(tq + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = c0 + 8 * j + 2 * (lane & 3);
+        const float b0 = bias[c], b1 = bias[c + 1];
+        const __nv_bfloat162 xa = __floats2bfloat162_rn(fmaxf(v[4 * j] + b0, 0.f), fmaxf(v[4 * j + 1] + b1, 0.f));
+        const __nv_bfloat162 xb = __floats2bfloat162_rn(fmaxf(v[4 * j + 2] + b0, 0.f), fmaxf(v[4 * j + 3] + b1, 0.f));
+        const int off = (c >> 3) * 128 + (c & 7) * 2;
+        *reinterpret_cast<__nv_bfloat162*>(ha + off) = xa;
+        *reinterpret_cast<__nv_bfloat162*>(hb + off) = xb;
+      }
+    }
+  };
+
+  // this thread's row for the logits: lanes < 16 of every warp
+  const int srow = 16 * quad + lane;  // row within the tile (lanes < 16)
+  const int chain = r0 + srow;
+  const bool live = lane < 16 && chain < a.rows;
+  float lq_acc = 0.f;
+  // the previous-layer word of every row of the tile, for the x builders
+  for (int r = tid; r < kTile64; r += kFusedThreads) {
+    const int c = r0 + r;
+    wrd[r] = (c < a.rows && jfirst > 1) ? a.P[(size_t)c * a.d + (jfirst - 2)] : a.beta;
+  }
+  __syncthreads();
+
+  for (int jl = jfirst; jl <= jend; ++jl) {
+    // ---- x tile: 64 rows x kin, 16-byte pieces of 8 elements
+    const int pieces = kin / 8;
+    for (int v = tid; v < kTile64 * pieces; v += kFusedThreads) {
+      const int r = v / pieces, c = v % pieces;
+      build_x_part(sX, kin, a.n, r, wrd[r], jl, c, c + 1);
+    }
+    publish();
+    // ---- layer 1: D = x W1^T
+    if (tid == 0 && ok) {
+      if (!weights) {
+        weights = tc::mbar_wait(wbar, 0u);
+        if (!weights) ok = false;
+      }
+      if (ok) {
+        const uint32_t ax = tc::smem_u32(sX), bw = tc::smem_u32(sW1);
+        const uint32_t idesc = tc::idesc_bf16_f32(kTile64, H);
+        for (int s = 0; s < kin / 16; ++s)
+          tc::mma_bf16(tb, tc::smem_desc(ax + s * 256, 128, kin * 16),
+                       tc::smem_desc(bw + s * 256, 128, kin * 16), idesc, s > 0);
+        tc::mma_commit(done);
+      }
+    }
+    ok = __syncthreads_and(ok) != 0;  // thread 0's weight wait, shared
+    wait_all(done, dph);
+    dph ^= 1u;
+    if (ok) epilogue(sB);
+    publish();
+    // ---- layer 2: D = h W2^T, W2 resident (K-chunk c of 64 at c H 128 bytes)
+    if (tid == 0 && ok) {
+      const uint32_t idesc = tc::idesc_bf16_f32(kTile64, H);
+      const uint32_t ah = tc::smem_u32(sH), bw = tc::smem_u32(sW2);
+      for (int c = 0; c < H / 64; ++c)
+        for (int s = 0; s < 4; ++s)
+          tc::mma_bf16(tb, tc::smem_desc(ah + c * 8 * 128 + s * 256, 128, H * 16),
+                       tc::smem_desc(bw + c * a.chunk_bytes + s * 256, 128, 64 * 16), idesc,
+                       (c > 0) || (s > 0));
+      tc::mma_commit(done);
+    }
+    wait_all(done, dph);
+    dph ^= 1u;
+    if (ok) epilogue(sB + H);
+    publish();
+    // ---- layer 3: D = h W3^T
+    if (tid == 0 && ok) {
+      const uint32_t ah = tc::smem_u32(sH), bw = tc::smem_u32(sW3);
+      const uint32_t idesc = tc::idesc_bf16_f32(kTile64, npad);
+      for (int s = 0; s < H / 16; ++s)
+        tc::mma_bf16(tb, tc::smem_desc(ah + s * 256, 128, H * 16),
+                     tc::smem_desc(bw + s * 256, 128, H * 16), idesc, s > 0);
+      tc::mma_commit(done);
+    }
+    wait_all(done, dph);
+    dph ^= 1u;
+    // ---- logits: the four parts of a quadrant split each row's bits by
+    // Philox output (part p takes the 4-bit groups g = p, p + 4, ...): lane
+    // i < 16 of warp (quad, part) scores row 16 quad + i, logit columns
+    // 4 g .. 4 g + 3; log q of the current word, or the draw
+    uint32_t wpart = 0u;
+    float qpart = 0.f;
+    if (ok) {
+      const float* b3 = sB + 2 * H;
+      const int groups = (a.n + 3) / 4;
+      const uint32_t move = MODE == kFusedSample ? *a.move_dev : 0u;
+      const uint32_t gc = a.group0 * 32u + (uint32_t)chain;
+      const uint32_t bits = (MODE == kFusedLogQ && live) ? a.P[(size_t)chain * a.d + (jl - 1)] : 0u;
+      for (int g = part; g < groups; g += kFusedParts) {  // warp-uniform
+        float la[4];
+        tc::tmem_ld4(tq + 4u * (uint32_t)g, la);
+        if (!live) continue;
+        uint4 u4 = make_uint4(0u, 0u, 0u, 0u);
+        if (MODE == kFusedSample)
+          u4 = philox4x32_10(make_uint4(gc, move, (uint32_t)(jl - 1) | (kTagMH << 16), (uint32_t)g), a.k0, a.k1);
+        const uint32_t U[4] = {u4.x, u4.y, u4.z, u4.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int qb = 4 * g + i;
+          if (qb >= a.n) break;
+          const float l = la[i] + b3[qb];
+          uint32_t bit;
+          if (MODE == kFusedLogQ) {
+            bit = (bits >> qb) & 1u;
+          } else {
+            const float e = __expf(-fabsf(l));
+            const float r = __fdividef(1.f, 1.f + e);
+            const float p1 = l >= 0.f ? r : e * r;  // sigma(l)
+            const float uf = ((float)(U[i] >> 8) + 0.5f) * (1.f / 16777216.f);
+            bit = uf < p1 ? 1u : 0u;
+          }
+          wpart |= bit << qb;
+          const float z = bit ? -l : l;
+          qpart -= fmaxf(z, 0.f) + softplus_tail(l);
+        }
+      }
+    }
+    if (live) {
+      xw[part][srow] = wpart;
+      xq[part][srow] = qpart;
+    }
+    // the TMEM reads of this layer are complete before the next layer's
+    // MMAs; the parts' bits and log q terms are exchanged
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (ok && live && part == 0) {
+      uint32_t word = 0u;
+      float sq = 0.f;
+#pragma unroll
+      for (int q = 0; q < kFusedParts; ++q) {
+        word |= xw[q][srow];
+        sq += xq[q][srow];
+      }
+      if (MODE == kFusedLogQ) {
+        a.lq[(size_t)chain * a.d + (jl - 1)] = sq;
+        wrd[srow] = word;  // the current word: the next layer's input
+      } else {
+        wrd[srow] = word;
+        a.Pn[(size_t)chain * a.d + (jl - 1)] = word;
+        lq_acc += sq;
+      }
+    }
+    __syncthreads();  // the drawn words are visible to the next x tile
+  }  // layers
+  if (MODE == kFusedSample && ok && live && part == 0) a.lqf[chain] += lq_acc;
+  if (!ok && tid == 0) {
+    if (a.status) atomicCAS(a.status, 0u, (uint32_t)PB_ETIMEOUT);
+    // let MMAs and copies in flight drain (bounded) before TMEM and shared
+    // memory are given up
+    tc::mma_commit(drain);
+    tc::mbar_wait(drain, 0u);
+    if (!weights) tc::mbar_wait(wbar, 0u);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tb, 256);
+}
+
+template __global__ void mlp_move64_kernel<kFusedLogQ>(FusedArgs);
+template __global__ void mlp_move64_kernel<kFusedSample>(FusedArgs);
+
 static FusedArgs fused_args(pb_mlp* p, int rows) {
   FusedArgs a{};
   a.jlast = 0;
@@ -1191,6 +1484,15 @@ cudaError_t mlp_fused_logq_dev(pb_mlp* p, const uint32_t* P, uint32_t beta, int 
   a.k = 1;
   a.k_dev = k_dev;
   a.lq = lq;
+  if (const size_t smem64 = fused64_layout(a)) {  // 64-row tiles, weights resident
+    // layers per CTA: one while the (tile, layer) pairs are few, more as the
+    // chains grow, so that the weights are loaded once for several layers
+    const int tiles = (chains + kTile64 - 1) / kTile64;
+    a.jlast = std::max(1, std::min(p->d, tiles * p->d / 4096));
+    dim3 grid(tiles, (p->d + a.jlast - 1) / a.jlast);
+    mlp_move64_kernel<kFusedLogQ><<<grid, kFusedThreads, smem64, st>>>(a);
+    return cudaGetLastError();
+  }
   dim3 grid((chains + 127) / 128, p->d);
   const size_t smem = fused_layout(a);
   if (smem == 0) return cudaErrorInvalidValue;
@@ -1238,6 +1540,10 @@ cudaError_t mlp_fused_sample_dev(pb_mlp* p, const uint32_t* P, uint32_t* Pn, uin
   a.k1 = k1;
   a.move_dev = move_dev;
   a.group0 = group0;
+  if (const size_t smem64 = fused64_layout(a)) {  // 64-row tiles, weights resident
+    mlp_move64_kernel<kFusedSample><<<(chains + kTile64 - 1) / kTile64, kFusedThreads, smem64, st>>>(a);
+    return cudaGetLastError();
+  }
   const size_t smem = fused_layout(a);
   if (smem == 0) return cudaErrorInvalidValue;
   mlp_fused_kernel<kFusedSample><<<(chains + 127) / 128, kFusedThreads, smem, st>>>(a);
@@ -1274,6 +1580,12 @@ cudaError_t mlp_fused_prepare() {
                              (int)kFusedSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_fused_kernel<kFusedSample>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_move64_kernel<kFusedLogQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFusedSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_move64_kernel<kFusedSample>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemMax);
   return e;
 }

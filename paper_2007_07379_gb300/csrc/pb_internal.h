@@ -265,6 +265,10 @@ struct MhCtx {
   uint32_t chains = 0, groups = 0, group0 = 0;
   uint64_t seed = 0;
   char* ws = nullptr;
+  // a second stream and two events: the log q of the current suffix runs
+  // beside the proposal draw (mh_ctx_open / mh_ctx_close)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 // Counters at the start of a move region: proposals accepted, moves done.
 struct MhCounters {
@@ -273,6 +277,8 @@ struct MhCounters {
   int32_t k;  // suffix start of the current move
 };
 size_t mh_region_bytes(int d, uint32_t groups);
+cudaError_t mh_ctx_open(MhCtx& c);
+void mh_ctx_close(MhCtx& c);
 // True when the network takes the fused inference kernel (k_in <= 96,
 // n <= 32): then a move draws its suffix start on the device.
 bool mh_fused(const pb_mlp* mlp);

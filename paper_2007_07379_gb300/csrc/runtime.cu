@@ -928,6 +928,9 @@ struct pb_run {
   std::vector<MhCtx> mh;
   bool learned = false;
   uint32_t mh_every = 0;
+  ~pb_run() {
+    for (MhCtx& x : mh) mh_ctx_close(x);
+  }
   WsHeader* hdr() const { return reinterpret_cast<WsHeader*>(ws + L.hdr); }
   RunModelDev* d_rm() const { return reinterpret_cast<RunModelDev*>(ws + L.rm); }
 };
@@ -1310,8 +1313,9 @@ PB_API int pb_run_create(pb_model* const* models, const pb_run_cfg* cfgs, int n_
   if (e != cudaSuccess) return PB_ECUDA;
   if (r->learned) {
     if (mlp_prepare() != cudaSuccess) return PB_ECUDA;
-    for (const MhCtx& x : r->mh)
-      if (x.mlp && mh_region_init(x, st) != cudaSuccess) return PB_ECUDA;
+    for (MhCtx& x : r->mh)
+      if (x.mlp && (mh_ctx_open(x) != cudaSuccess || mh_region_init(x, st) != cudaSuccess))
+        return PB_ECUDA;  // the run's destructor closes what was opened
   }
   // host copies must outlive the (possibly staged) async copies
   e = cudaStreamSynchronize(st);
