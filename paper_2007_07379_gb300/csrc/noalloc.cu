@@ -21,9 +21,9 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
                           size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt = false,
-                          bool ext = false);
+                          bool ext = false, bool bal = false);
 size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins,
-                        bool wgt = false);
+                        bool wgt = false, bool bal = false);
 cudaError_t sweep_prepare();
 }  // namespace pb
 
@@ -114,12 +114,19 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
   }
   auto up32 = [](int x) { return ((x + 31) / 32) * 32; };
   const int cons = std::max(32, std::min(224, up32(maxcol)));
-  const int prod = std::max(32, std::min(352, up32(3 * maxcol)));
-  // histogram placement: the rule of a single-model run (shared memory when
-  // its u32 counters take at most 128 KiB and the CTA still fits)
-  const size_t smem0 = sweep_smem_bytes(n, d, cons, maxcol, 0);
-  const bool hist_smem = (size_t)bins * 32 <= (128u << 10) && smem0 + (size_t)bins * 32 <= kSweepSmemMax;
-  const size_t smem = sweep_smem_bytes(n, d, cons, maxcol, hist_smem ? bins : 0);
+  const int prod = std::max(32, std::min(352, up32(sweep_producers_wanted(*m, nc, false))));
+  // histogram placement and plane buffers: the rules of a single-model run
+  // (shared memory when its u32 counters take at most 128 KiB and the CTA
+  // still fits; 16 planes ahead in three buffers when that fits with the
+  // same placement)
+  auto hist_fits = [&](bool bal) {
+    const size_t smem0 = sweep_smem_bytes(n, d, cons, maxcol, 0, false, bal);
+    return (size_t)bins * 32 <= (128u << 10) && smem0 + (size_t)bins * 32 <= kSweepSmemMax;
+  };
+  const bool hist_smem = hist_fits(false);
+  const bool bal = hist_fits(true) == hist_smem &&
+                   sweep_smem_bytes(n, d, cons, maxcol, hist_smem ? bins : 0, false, true) <= kSweepSmemMax;
+  const size_t smem = sweep_smem_bytes(n, d, cons, maxcol, hist_smem ? bins : 0, false, bal);
   if (smem > kSweepSmemMax) return PB_ERANGE;
 
   ModelDev md{};
@@ -175,7 +182,8 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
                        (size_t)n_words(n, d) * 4, hdr, st)) != cudaSuccess)
     return PB_ECUDA;
   if (n_sweeps > 0 &&
-      (e = launch_sweeps(d_rm, 1, groups, n_sweeps, cons, prod, maxcol, nc, smem, hdr, st)) != cudaSuccess)
+      (e = launch_sweeps(d_rm, 1, groups, n_sweeps, cons, prod, maxcol, nc, smem, hdr, st, false,
+                         false, bal)) != cudaSuccess)
     return PB_ECUDA;
   if ((e = cudaMemcpyAsync(d_counts, base + o_hist, (size_t)bins * 8 * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_totals, base + o_cnt, 2 * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)

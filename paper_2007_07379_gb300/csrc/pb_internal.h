@@ -1,6 +1,7 @@
 // Internal layout shared by the host compiler, the runtime and the kernels.
 #pragma once
 #include <cstddef>
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -211,6 +212,27 @@ struct pb_model {
   std::vector<pb::TAcc> tacc;         // by p (table models only)
   std::vector<pb::TRec> trec;         // one per table gate
 };
+
+namespace pb {
+// Philox calls the producers of a sweep launch make in one colour step for
+// model m, nc colour steps per sweep: 3 per p-bit of the next class in one
+// step (12 planes ahead, two buffers: general-gate runs, and plain runs
+// whose tables leave no room for more), or 4 per p-bit spread evenly over
+// the steps (16 planes ahead, three buffers: other plain runs); the larger
+// of the two for plain runs, which take either.
+inline int sweep_producers_wanted(const pb_model& m, int nc, bool wgt) {
+  int maxcol = 1;
+  for (int c = 0; c < 4; ++c) maxcol = std::max(maxcol, m.col_off[c + 1] - m.col_off[c]);
+  if (wgt) return 3 * maxcol;
+  return std::max(3 * maxcol, (4 * m.col_off[4] + nc - 1) / std::max(1, nc));
+}
+template <class Models>  // a container of pointers to models
+inline int sweep_producers_wanted(const Models& ms, int nc, bool wgt) {
+  int p = 32;
+  for (auto& m : ms) p = std::max(p, sweep_producers_wanted(*m, nc, wgt));
+  return p;
+}
+}  // namespace pb
 
 // Proposal network (host side of pb_mlp): fp32 master weights, Adam state,
 // bf16 copies for the tensor cores and the batch buffers of one call.

@@ -22,11 +22,11 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
                           size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt = false,
-                          bool ext = false);
+                          bool ext = false, bool bal = false);
 cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
                                      uint32_t n_work, uint32_t n_sweeps, int cons, int prod,
                                      int max_col, int nc, int grid, size_t smem_bytes,
-                                     WsHeader* hdr, cudaStream_t st);
+                                     WsHeader* hdr, cudaStream_t st, bool bal);
 cudaError_t launch_elim(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                         const uint32_t* const* d_init_tabs, uint32_t n_sweeps, size_t smem_bytes,
                         WsHeader* hdr, cudaStream_t st, bool wgt, int warps);
@@ -36,7 +36,7 @@ cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins,
 cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t count,
                                uint32_t* out, cudaStream_t st);
 size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins,
-                        bool wgt = false);
+                        bool wgt = false, bool bal = false);
 cudaError_t sweep_prepare();
 int sweep_max_blocks_per_sm(int threads, size_t smem);
 }  // namespace pb
@@ -909,6 +909,7 @@ struct pb_run {
   bool persistent = false;
   bool wgt = false;        // some model has PB_U gates (the general-gate kernels)
   bool ext = false;        // some model has Toffoli links or two-qubit tables
+  bool bal = false;        // plain run with 16 planes ahead, produced evenly over the steps
   int nc = 2;              // colour steps per sweep (largest over the models)
   bool elim = false;       // exact-sampler run: i.i.d. paths instead of sweeps
   size_t elim_smem = 0;
@@ -958,9 +959,9 @@ cudaError_t enqueue_sweeps(pb_run* r, uint32_t n_sweeps, cudaStream_t st) {
   if (r->persistent)
     return launch_sweeps_persistent(r->d_rm(), r->nm, reinterpret_cast<const uint32_t*>(r->ws + r->L.work),
                                     r->total_groups, n_sweeps, r->cons, r->prod, r->max_col, r->nc,
-                                    r->grid, r->smem, r->hdr(), st);
+                                    r->grid, r->smem, r->hdr(), st, r->bal);
   return launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->cons, r->prod, r->max_col,
-                       r->nc, r->smem, r->hdr(), st, r->wgt, r->ext);
+                       r->nc, r->smem, r->hdr(), st, r->wgt, r->ext, r->bal);
 }
 
 // Graph of n sweeps of a learned run (Fig. 2 Step 1 with the network as the
@@ -1039,20 +1040,41 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
   // 32 bytes a bin, 40 with general gates); otherwise the record adds to
   // global memory directly.
   const size_t cap_bins = r->nm == 1 ? 4096u : 1024u;
-  size_t smem = 0;
-  for (int i = 0; i < r->nm; ++i) {
-    const pb_model& m = *r->models[i];
-    const uint32_t bins = r->L.ms[i].bins;
-    const size_t base = sweep_smem_bytes(m.n, m.d, cons, maxcol, 0, r->wgt);
-    const size_t per_bin = sweep_smem_bytes(m.n, m.d, cons, maxcol, 1, r->wgt) - base;
-    const bool use = bins <= cap_bins && base + (size_t)bins * per_bin <= kSweepSmemMax;
-    r->rm[i].hist_smem = use ? 1u : 0u;
-    smem = std::max(smem, sweep_smem_bytes(m.n, m.d, cons, maxcol, use ? bins : 0, r->wgt));
-  }
-  r->smem = smem;
+  auto layout = [&](bool bal, std::vector<char>& use) {
+    size_t smem = 0;
+    use.assign(r->nm, 0);
+    for (int i = 0; i < r->nm; ++i) {
+      const pb_model& m = *r->models[i];
+      const uint32_t bins = r->L.ms[i].bins;
+      const size_t base = sweep_smem_bytes(m.n, m.d, cons, maxcol, 0, r->wgt, bal);
+      const size_t per_bin = sweep_smem_bytes(m.n, m.d, cons, maxcol, 1, r->wgt, bal) - base;
+      use[i] = bins <= cap_bins && base + (size_t)bins * per_bin <= kSweepSmemMax;
+      smem = std::max(smem, sweep_smem_bytes(m.n, m.d, cons, maxcol, use[i] ? bins : 0, r->wgt, bal));
+    }
+    return smem;
+  };
   r->persistent = r->nm > 1;
   if (const char* e = std::getenv("PB_PERSISTENT")) r->persistent = std::atoi(e) != 0;
   if (r->wgt) r->persistent = false;  // general-gate sweeps: one CTA per group
+  // Plain runs take the balanced production (16 planes ahead, three plane
+  // buffers) when its tables fit with the same histogram placement and, on
+  // a persistent grid, the same CTAs per SM; otherwise 12 planes in two.
+  std::vector<char> use_s, use_b;
+  const size_t smem_s = layout(false, use_s);
+  bool bal = false;
+  size_t smem_b = 0;
+  if (!r->wgt) {
+    smem_b = layout(true, use_b);
+    bal = smem_b <= kSweepSmemMax && use_b == use_s;
+    if (bal && r->persistent)
+      bal = sweep_max_blocks_per_sm(r->threads, smem_b) >= sweep_max_blocks_per_sm(r->threads, smem_s);
+    if (const char* e = std::getenv("PB_BALANCED")) bal = bal && std::atoi(e) != 0;
+  }
+  const std::vector<char>& use = bal ? use_b : use_s;
+  for (int i = 0; i < r->nm; ++i) r->rm[i].hist_smem = use[i] ? 1u : 0u;
+  const size_t smem = bal ? smem_b : smem_s;
+  r->bal = bal;
+  r->smem = smem;
   r->grid = 0;
   if (r->persistent) {
     int dev = 0, sms = 1;
@@ -1068,15 +1090,16 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
 
 // Default launch shape: consumers = the largest colour class rounded up to
 // a warp (one p-bit per consumer per class), capped at 224; producers = one
-// per Philox call of that class (kPre = 3 per p-bit), capped at 352; plus one
-// recorder warp.  Environment overrides PB_CONS, PB_PROD (multiples of 32).
+// per Philox call of a colour step (sweep_producers_wanted), capped at 352;
+// plus one recorder warp.  Environment overrides PB_CONS, PB_PROD
+// (multiples of 32).
 void choose_shape(pb_run* r) {
   int maxcol = 1;
   for (auto& m : r->models)
     for (int c = 0; c < 4; ++c) maxcol = std::max(maxcol, m->col_off[c + 1] - m->col_off[c]);
   auto up32 = [](int x) { return ((x + 31) / 32) * 32; };
   int cons = std::max(32, std::min(224, up32(maxcol)));
-  int prod = std::max(32, std::min(352, up32(3 * maxcol)));
+  int prod = std::max(32, std::min(352, up32(sweep_producers_wanted(r->models, r->nc, r->wgt))));
   if (const char* e = std::getenv("PB_CONS")) {
     int v = std::atoi(e);
     if (v >= 32 && v <= 224 && v % 32 == 0) cons = v;
@@ -1588,8 +1611,9 @@ PB_API int pb_run_tune(pb_run* r, uint32_t trial_sweeps, const char* cache_path,
   std::vector<int> cons_c, prod_c, bpsm_c = {0};
   for (int c : {64, 128, 224})
     if (c <= std::max(64, up)) cons_c.push_back(c);
+  const int pw = sweep_producers_wanted(r->models, r->nc, r->wgt);
   for (int p : {96, 192, 352})
-    if (p <= std::max(96, ((3 * maxcol + 31) / 32) * 32)) prod_c.push_back(p);
+    if (p <= std::max(96, ((pw + 31) / 32) * 32)) prod_c.push_back(p);
   if (r->nm > 1) bpsm_c = {1, 2, 0};
   double best = 1e30;
   int bc = r->cons, bp = r->prod, bb = r->blocks_per_sm;

@@ -64,8 +64,11 @@ __device__ __forceinline__ void compare_tail(uint32_t& lt, uint32_t& eq, const H
     compare4(lt, eq, k, philox_cold(make_uint4(g, sweep, p, grp), k0, k1), grp);
 }
 
-// Number of Philox calls computed ahead of a colour class (12 planes).
+// Number of Philox calls computed ahead of a colour class: 12 planes for
+// general-gate runs, 16 for plain runs (whose producers spread the work over
+// the colour steps and have room for the fourth).
 constexpr int kPre = 3;
+constexpr int kPrePlain = 4;
 // General-gate runs: Philox calls of the Metropolis acceptance draw (tag 6)
 // computed ahead (12 planes) for the coupled p-bits among the first
 // `consumers` of a class (the rest draw their own, out of line).
@@ -82,11 +85,11 @@ __device__ __forceinline__ uint32_t thr_b(int m, uint32_t t0, uint32_t t1) {
 
 // Comparison of the precomputed planes for any thresholds (small J), and
 // the planes beyond them; out of line: taken rarely.
+// np: the precomputed outputs R0 .. R{np-1} (3 or 4; R3 unused when 3).
 __device__ __noinline__ uint32_t heat_bath_general(const HbClass k, uint4 R0, uint4 R1, uint4 R2,
-                                                   uint32_t lt, uint32_t eq, bool pre, uint32_t g,
-                                                   uint32_t sweep, uint32_t pidx, uint32_t k0,
-                                                   uint32_t k1) {
-  static_assert(kPre == 3, "heat_bath_general takes three Philox outputs");
+                                                   uint4 R3, int np, uint32_t lt, uint32_t eq,
+                                                   bool pre, uint32_t g, uint32_t sweep,
+                                                   uint32_t pidx, uint32_t k0, uint32_t k1) {
   if (pre) {
     lt = 0u;
     eq = ~0u;
@@ -94,13 +97,14 @@ __device__ __noinline__ uint32_t heat_bath_general(const HbClass k, uint4 R0, ui
     eq &= ~k.tail0;
     compare4(lt, eq, k, R1, 1u);
     compare4(lt, eq, k, R2, 2u);
+    if (np > 3) compare4(lt, eq, k, R3, 3u);
   }
-  compare_tail(lt, eq, k, (uint32_t)kPre, g, sweep, pidx, k0, k1);
+  compare_tail(lt, eq, k, (uint32_t)np, g, sweep, pidx, k0, k1);
   return lt;
 }
 
 // Thresholds for which the consumers take the short comparison below:
-// thr1 < 2^24 and thr2 < 2^20 (thr3 <= thr2), i.e. on the 4 kPre = 12
+// thr1 < 2^24 and thr2 < 2^20 (thr3 <= thr2), i.e. on the first 12
 // precomputed planes every threshold bit is 0 except the top bit of
 // t0 = 2^31 and bits 23..20 of thr1 (planes 8..11).
 struct FastThr {
@@ -108,7 +112,6 @@ struct FastThr {
   uint32_t U[4];  // ~0 where thr1 has a one bit on plane 8 + w, else 0
 };
 __device__ __forceinline__ FastThr fast_thresholds(uint32_t thr1, uint32_t thr2) {
-  static_assert(kPre == 3, "the short comparison assumes 12 precomputed planes");
   FastThr f;
   f.on = thr1 < (1u << 24) && thr2 < (1u << 20);
 #pragma unroll
@@ -118,16 +121,20 @@ __device__ __forceinline__ FastThr fast_thresholds(uint32_t thr1, uint32_t thr2)
 
 // New value of the 32 chains of one p-bit (Fig. 2 Steps 1-2) from its link
 // demands r0..r2 (three-link form: m=0: 0,0,0  m=1: r0,r0,0  m=2: r0,r1,0
-// m=3: r0,r1,r2), its masks Mk = [m == k] and its kPre precomputed Philox
+// m=3: r0,r1,r2), its masks Mk = [m == k] and its NP precomputed Philox
 // outputs R.  Short form (F.on): plane 0 decides the t0 lanes (u < 2^31 iff
 // its top bit is 0); on planes 1..7 every other threshold bit is 0, so a
 // lane stays equal only while it draws zeros; on planes 8..11 the lanes
 // compared with thr1 (L1) meet thr1's bits and the thr2 / thr3 lanes zeros.
-// Lanes still equal after the precomputed planes, and every lane when the
-// thresholds do not have that form, go to heat_bath_general.
+// A lane is still equal after plane 11 with probability 2^-12, so about one
+// p-bit in 128 (32 lanes) needs more: with NP = 4 the fourth output gives
+// planes 12..15 inline (general comparison, no Philox call).  Lanes still
+// equal after the precomputed planes, and every lane when the thresholds do
+// not have that form, go to heat_bath_general.
+template <int NP>
 __device__ __forceinline__ uint32_t heat_bath_links(uint32_t r0, uint32_t r1, uint32_t r2, int m,
                                                     uint32_t M0, uint32_t M1, uint32_t M2,
-                                                    uint32_t M3, const uint4 (&R)[kPre],
+                                                    uint32_t M3, const uint4 (&R)[NP],
                                                     const FastThr& F, uint32_t thr0,
                                                     uint32_t thr1, uint32_t thr2, uint32_t thr3,
                                                     uint32_t g, uint32_t sweep, uint32_t pidx,
@@ -149,12 +156,20 @@ __device__ __forceinline__ uint32_t heat_bath_links(uint32_t r0, uint32_t r1, ui
       lt |= eq & ~P[w] & A;
       eq &= ~(P[w] ^ A);
     }
+    if constexpr (NP > 3) {
+      if (eq != 0u) {
+        k.tA = thr_a(m, thr0, thr1, thr2, thr3);
+        k.tB = thr_b(m, thr0, thr1);
+        compare4(lt, eq, k, R[3], 3u);
+      }
+    }
     general = eq != 0u;
   }
   if (general) {
     k.tA = thr_a(m, thr0, thr1, thr2, thr3);
     k.tB = thr_b(m, thr0, thr1);
-    lt = heat_bath_general(k, R[0], R[1], R[2], lt, eq, !F.on, g, sweep, pidx, k0, k1);
+    lt = heat_bath_general(k, R[0], R[1], R[2], R[NP > 3 ? 3 : 2], NP, lt, eq, !F.on, g, sweep,
+                           pidx, k0, k1);
   }
   return k.neg ^ lt;
 }
@@ -216,8 +231,9 @@ __device__ __noinline__ uint32_t couple_accept(const uint32_t* W, const Cpl* cpl
 // lane the active links that demand 0 (z) and 1 (o) are counted in two-bit
 // bit-sliced counters, v = z - o, and the new value is [v < 0] XOR
 // [u < thr[|v|]] -- the plain rule with the link count varying by lane --
-// from the same planes (the kPre precomputed Philox outputs, then further
-// ones of the same counter).  Out of line: only Toffoli-adjacent p-bits.
+// from the same planes (the kPre precomputed Philox outputs of a general-
+// gate run, then further ones of the same counter).  Out of line: only
+// Toffoli-adjacent p-bits, which only general-gate runs have.
 __device__ __noinline__ uint32_t glink_heat_bath(const uint32_t* W, const GLink* gp,
                                                  const uint4* rp, uint32_t thr0, uint32_t thr1,
                                                  uint32_t thr2, uint32_t thr3, uint32_t g,
@@ -349,18 +365,21 @@ static_assert(sizeof(ClassEnt) == 48, "ClassEnt must be 48 bytes");
 
 // Shared-memory image of one group: words (image_words) and two snapshots,
 // descriptors, record terms, an optional histogram of hist_bins x 8 u32
-// counters, the consumers' class table and two buffers of kPre x max_col
-// group comparisons (one per Philox output).  The image holds the (d+1) n layer words,
+// counters, the consumers' class table and the plane buffers: three of
+// kPrePlain x max_col Philox outputs (plain runs), or two of kPre x max_col
+// plus kPreC x cons acceptance outputs (general-gate runs).  The image holds the (d+1) n layer words,
 // ZERO, ONES and one scratch word (the store target of consumers without a
 // p-bit in a colour class), rounded up to 16 bytes.
 __host__ __device__ inline int image_words(int n, int d) { return (n_words(n, d) + 1 + 3) & ~3; }
 
 __host__ __device__ inline size_t group_smem_bytes(int n, int d, int cons, int max_col,
-                                                   uint32_t hist_bins, bool wgt = false) {
+                                                   uint32_t hist_bins, bool wgt = false,
+                                                   bool bal = false) {
   return (size_t)3 * image_words(n, d) * 4 + (size_t)n * d * sizeof(Desc) +
          (size_t)n * d * sizeof(Rec) + (size_t)hist_bins * (wgt ? 10 : 8) * 4 +
          (size_t)4 * cons * sizeof(ClassEnt) +
-         (size_t)2 * ((size_t)kPre * max_col + (wgt ? (size_t)kPreC * cons : 0)) * sizeof(uint4);
+         (wgt ? (size_t)2 * ((size_t)kPre * max_col + (size_t)kPreC * cons)
+              : bal ? (size_t)3 * kPrePlain * max_col : (size_t)2 * kPre * max_col) * sizeof(uint4);
 }
 
 // 32 x 32 bit transpose across a warp: on entry lane r holds row r; on
@@ -584,9 +603,12 @@ struct Recorder {
 
 // p-bits lo + first, lo + first + stride, ... < hi of a colour class from
 // their descriptors (a class larger than the consumers; rare).  cpl: the
-// coupling table of a general-gate model, else nullptr.
+// coupling table of a general-gate model, else nullptr.  Output j of the
+// class's k-th p-bit is cur[k NP + j] (pst = 1) or cur[j pst + k] (pst > 1:
+// plane-major buffers).
+template <int NP>
 __device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc* sdesc,
-                                            const uint4* cur, int lo, int first,
+                                            const uint4* cur, int pst, int lo, int first,
                                             int hi, int stride, int n, FastThr fast, uint32_t thr0,
                                             uint32_t thr1, uint32_t thr2, uint32_t thr3,
                                             uint32_t g, uint32_t sweep, uint32_t k0, uint32_t k1,
@@ -596,10 +618,10 @@ __device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc
     if (D.mflag & 0x80) continue;
     const int m = D.mflag & 3;
     if (m == 1) { D.a[1] = D.a[0]; D.b[1] = D.b[0]; }
-    const uint4* rp = cur + (i - lo) * kPre;
-    uint4 R[kPre];
+    const uint4* rp = cur + (i - lo) * (pst == 1 ? NP : 1);
+    uint4 R[NP];
 #pragma unroll
-    for (int j = 0; j < kPre; ++j) R[j] = rp[j];
+    for (int j = 0; j < NP; ++j) R[j] = rp[j * pst];
     const uint32_t r0 = W[D.a[0]] ^ W[D.b[0]];
     const uint32_t r1 = W[D.a[1]] ^ W[D.b[1]];
     const uint32_t r2 = W[D.a[2]] ^ W[D.b[2]];
@@ -607,7 +629,7 @@ __device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc
     uint32_t v = (glk && (D.mflag & 0x10))
                      ? glink_heat_bath(W, glk + (D.dst - n), rp, thr0, thr1, thr2, thr3, g, sweep,
                                        pidx, k0, k1)
-                     : heat_bath_links(r0, r1, r2, m, m == 0 ? ~0u : 0u, m == 1 ? ~0u : 0u,
+                     : heat_bath_links<NP>(r0, r1, r2, m, m == 0 ? ~0u : 0u, m == 1 ? ~0u : 0u,
                                        m == 2 ? ~0u : 0u, m == 3 ? ~0u : 0u, R, fast, thr0, thr1,
                                        thr2, thr3, g, sweep, pidx, k0, k1);
     if (cpl && (D.mflag & 8)) {
@@ -624,14 +646,16 @@ __device__ __forceinline__ void redraw_body(uint32_t* W, uint32_t* S, const Desc
 }
 
 // Out-of-line entries (the plain one keeps the hot kernel's call site small:
-// one argument more there costs register spills).
+// one argument more there costs register spills).  NP: Philox outputs
+// computed ahead per p-bit.
+template <int NP>
 __device__ __noinline__ void redraw_extra(uint32_t* W, uint32_t* S, const Desc* sdesc,
-                                          const uint4* cur, int lo, int first, int hi, int stride,
-                                          int n, FastThr fast, uint32_t thr0, uint32_t thr1,
-                                          uint32_t thr2, uint32_t thr3, uint32_t g, uint32_t sweep,
-                                          uint32_t k0, uint32_t k1) {
-  redraw_body(W, S, sdesc, cur, lo, first, hi, stride, n, fast, thr0, thr1, thr2, thr3, g, sweep,
-              k0, k1, nullptr, nullptr, nullptr);
+                                          const uint4* cur, int pst, int lo, int first, int hi,
+                                          int stride, int n, FastThr fast, uint32_t thr0,
+                                          uint32_t thr1, uint32_t thr2, uint32_t thr3, uint32_t g,
+                                          uint32_t sweep, uint32_t k0, uint32_t k1) {
+  redraw_body<NP>(W, S, sdesc, cur, pst, lo, first, hi, stride, n, fast, thr0, thr1, thr2, thr3,
+                  g, sweep, k0, k1, nullptr, nullptr, nullptr);
 }
 __device__ __noinline__ void redraw_extra_coupled(uint32_t* W, uint32_t* S, const Desc* sdesc,
                                                   const uint4* cur, int lo, int first, int hi,
@@ -640,8 +664,8 @@ __device__ __noinline__ void redraw_extra_coupled(uint32_t* W, uint32_t* S, cons
                                                   uint32_t g, uint32_t sweep, uint32_t k0,
                                                   uint32_t k1, const Cpl* cpl, const GLink* glk,
                                                   const TAcc* tacc) {
-  redraw_body(W, S, sdesc, cur, lo, first, hi, stride, n, fast, thr0, thr1, thr2, thr3, g, sweep,
-              k0, k1, cpl, glk, tacc);
+  redraw_body<kPre>(W, S, sdesc, cur, 1, lo, first, hi, stride, n, fast, thr0, thr1, thr2, thr3,
+                    g, sweep, k0, k1, cpl, glk, tacc);
 }
 
 // Runs `n_sweeps` sweeps (absolute indices sweep0...) of one chain group.
@@ -650,8 +674,11 @@ __device__ __noinline__ void redraw_extra_coupled(uint32_t* W, uint32_t* S, cons
 // get the Metropolis acceptance, records add FP64 phases); plain models run
 // through it unchanged.  EXT (with WGT): some model also has Toffoli links
 // or two-qubit tables; without them those paths are compiled out, so the
-// coupled-gate consumers and the recorder keep their shorter code.
-template <int NC, bool WGT, bool EXT>
+// coupled-gate consumers and the recorder keep their shorter code.  BAL
+// (plain runs whose tables leave room): 16 planes computed ahead per p-bit
+// in three buffers, produced evenly over the colour steps; otherwise 12
+// planes in two buffers, each class's produced during the step before.
+template <int NC, bool WGT, bool EXT, bool BAL>
 __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, uint32_t n_sweeps,
                           Shape sh, int max_col_all, uint32_t* smem, WsHeader* hdr) {
   // run and model constants held in registers for the whole launch
@@ -679,10 +706,19 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   // im and their compensations) and a u32 count (10 words with padding)
   const uint32_t hist_words = rm.bins * (wgt_m ? 10u : 8u);
   ClassEnt* sclass = reinterpret_cast<ClassEnt*>(after_rec + (rm.hist_smem ? hist_words : 0u));
-  // two buffers, each [max_col][kPre] sweep-draw outputs, then (general-gate
-  // runs) [cons][kPreC] acceptance outputs of the class's first cons p-bits
+  // plane buffers, each [max_col][KP] sweep-draw outputs, then (general-
+  // gate runs) [cons][kPreC] acceptance outputs of the class's first cons
+  // p-bits: three with BAL (producers up to two steps ahead), else two (one
+  // step ahead)
   uint4* planes = reinterpret_cast<uint4*>(sclass + 4 * sh.cons);
-  const int acc_off = max_col_all * kPre;
+  static_assert(!(WGT && BAL), "balanced production: plain runs only");
+  constexpr int KP = BAL ? kPrePlain : kPre;  // Philox outputs computed ahead per p-bit
+  // Output j of a class's k-th p-bit: [k KP + j] (48-byte rows, conflict-free
+  // for 16-byte loads across a warp), or with BAL [j max_col + k] (plane-
+  // major: 64-byte rows would put 16 lanes on the same four banks).
+  const int pst = BAL ? max_col_all : 1;
+  auto pidx_of = [&](int k, int j) { return BAL ? j * max_col_all + k : k * KP + j; };
+  const int acc_off = max_col_all * KP;
   const int pbuf = acc_off + (WGT ? sh.cons * kPreC : 0);
 
   // ---- load the group image and the tables
@@ -800,14 +836,14 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   auto produce = [&](auto cc, uint32_t sw, uint4* buf) {
     constexpr int C = decltype(cc)::value;
     const int lo = col_lo[C], K = col_hi[C] - lo;
-    const int nsw = K * kPre;
+    const int nsw = K * KP;
     const int nacc = WGT ? (K < sh.cons ? K : sh.cons) * kPreC : 0;
 #pragma unroll 1
     for (int u = ptid; u < nsw + nacc; u += sh.prod) {
       if (!WGT || u < nsw) {
-        const int i = u / kPre, j = u - i * kPre;
+        const int i = u / KP, j = u - i * KP;
         const uint32_t p = (uint32_t)(sdesc[lo + i].dst - n) | (kTagSweep << 16);
-        buf[u] = philox4x32_10(make_uint4(gglob, sw, p, (uint32_t)j), k0, k1);
+        buf[pidx_of(i, j)] = philox4x32_10(make_uint4(gglob, sw, p, (uint32_t)j), k0, k1);
       } else {  // acceptance draws: coupled p-bits only
         const int a = u - nsw, i = a / kPreC, j = a - i * kPreC;
         const Desc& D = sdesc[lo + i];
@@ -819,6 +855,19 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   };
   if (producer && n_sweeps > 0u) produce(std::integral_constant<int, 0>{}, sweep0, planes);
   __syncthreads();
+
+  // BAL: production spread evenly over the colour steps.  The units
+  // of a sweep are its U Philox outputs (KP a p-bit) in step order; step t
+  // needs its own before it starts, and the three buffers hold steps t (being
+  // read), t + 1 and t + 2.  During step t the producers take the next units
+  // of the stream up to max(D(t + 2), pp + B) and at most D(t + 3), B = U /
+  // NC a step (D(t): units of the steps before t; pp: units produced so
+  // far, kept relative to the current sweep's first unit).  With classes of
+  // 116, 91 and 33 p-bits this is 336 outputs a step instead of 364, 132 and
+  // 464 for the next step alone.
+  [[maybe_unused]] const uint32_t U = (uint32_t)(KP * col_hi[NC - 1]);  // every p-bit is in one class
+  [[maybe_unused]] const uint32_t B = (U + NC - 1) / NC;
+  [[maybe_unused]] uint32_t pp = (uint32_t)(KP * col_hi[0]);  // units of step 0, produced above
 
   const FastThr fast = fast_thresholds(thr1, thr2);
   Recorder rec;
@@ -835,17 +884,18 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     const uint32_t sweep = sweep0 + s;
     uint32_t* S = smem + iw * (1 + (s & 1u));
     // plane buffer of global step s NC + C
-    const uint4* cur = planes + ((s * (uint32_t)NC + (uint32_t)C) & 1u) * pbuf;
+    const uint32_t gstep = s * (uint32_t)NC + (uint32_t)C;
+    const uint4* cur = planes + (BAL ? (gstep % 3u) : (gstep & 1u)) * pbuf;
     if (consumer) {
       const int lo = col_lo[C], hi = col_hi[C], K = hi - lo;
       // the first p-bit of every consumer from its table entry; warps with no
       // p-bit in this class skip it (their entries are dummies)
       if (warp * 32 < K) {
         const ClassEnt E = sclass[C * sh.cons + tid];
-        const uint4* rp = cur + (tid < K ? tid : 0) * kPre;  // dummies: any planes
-        uint4 R[kPre];
+        const uint4* rp = cur + pidx_of(tid < K ? tid : 0, 0);  // dummies: any planes
+        uint4 R[KP];
 #pragma unroll
-        for (int j = 0; j < kPre; ++j) R[j] = rp[j];
+        for (int j = 0; j < KP; ++j) R[j] = rp[j * pst];
         const char* Wb = reinterpret_cast<const char*>(W);
         auto word = [&](uint32_t off) { return *reinterpret_cast<const uint32_t*>(Wb + off); };
         const uint32_t r0 = word(E.la[0]) ^ word(E.lb[0]);
@@ -869,7 +919,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
           v = glink_heat_bath(W, rm.glk + (E.dst / 4u - (uint32_t)n), rp, thr0, thr1, thr2, thr3,
                               gglob, sweep, pidx, k0, k1);
         else
-          v = heat_bath_links(r0, r1, r2, (int)(WGT ? (E.m & 3u) : E.m), E.M0, E.M1, E.M2, E.M3, R,
+          v = heat_bath_links<KP>(r0, r1, r2, (int)(WGT ? (E.m & 3u) : E.m), E.M0, E.M1, E.M2, E.M3, R,
                               fast, thr0, thr1, thr2, thr3, gglob, sweep, pidx, k0, k1);
         if constexpr (WGT) {
           if (E.m & 0x100u) {
@@ -892,17 +942,42 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
                                thr1, thr2, thr3, gglob, sweep, k0, k1, rm.cpl,
                                EXT ? rm.glk : nullptr, EXT ? rm.tacc : nullptr);
         else
-          redraw_extra(W, S, sdesc, cur, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0, thr1, thr2,
+          redraw_extra<KP>(W, S, sdesc, cur, pst, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0, thr1, thr2,
                        thr3, gglob, sweep, k0, k1);
       }
     } else if (producer) {
-      // the next step: class C + 1 of this sweep, or class 0 of the next one
-      const uint32_t nxt = s * (uint32_t)NC + (uint32_t)C + 1u;
-      if constexpr (C + 1 < NC) {
-        produce(std::integral_constant<int, C + 1>{}, sweep, planes + (nxt & 1u) * pbuf);
+      if constexpr (!BAL) {
+        // the next step: class C + 1 of this sweep, or class 0 of the next one
+        const uint32_t nxt = gstep + 1u;
+        if constexpr (C + 1 < NC) {
+          produce(std::integral_constant<int, C + 1>{}, sweep, planes + (nxt & 1u) * pbuf);
+        } else {
+          if (s + 1u < n_sweeps)
+            produce(std::integral_constant<int, 0>{}, sweep + 1u, planes + (nxt & 1u) * pbuf);
+        }
       } else {
-        if (s + 1u < n_sweeps)
-          produce(std::integral_constant<int, 0>{}, sweep + 1u, planes + (nxt & 1u) * pbuf);
+        // steps gstep + 1 and gstep + 2: classes C1, C2 of sweeps s + c1, s + c2
+        constexpr int C1 = (C + 1) % NC, C2 = (C + 2) % NC, C3 = (C + 3) % NC;
+        constexpr uint32_t c1 = (C + 1) / NC, c2 = (C + 2) / NC, c3 = (C + 3) / NC;
+        const uint32_t d1 = c1 * U + (uint32_t)(KP * col_lo[C1]);  // D(t + k) - D(sweep s)
+        const uint32_t d2 = c2 * U + (uint32_t)(KP * col_lo[C2]);
+        uint32_t lim = c3 * U + (uint32_t)(KP * col_lo[C3]);
+        if (s + 1u >= n_sweeps && lim > U) lim = U;  // no unit past the launch
+        uint32_t tgt = pp + B > d2 ? pp + B : d2;
+        if (tgt > lim) tgt = lim;
+#pragma unroll 1
+        for (uint32_t u = pp + (uint32_t)ptid; u < tgt; u += (uint32_t)sh.prod) {
+          const bool second = u >= d2;
+          const uint32_t r = u - (second ? d2 : d1);  // unit within its step
+          const uint32_t i = r / (uint32_t)KP, j = r - i * (uint32_t)KP;
+          const int lo = second ? col_lo[C2] : col_lo[C1];
+          const uint32_t sw = sweep + (second ? c2 : c1);
+          const uint32_t slot = (gstep + (second ? 2u : 1u)) % 3u;
+          const uint32_t p = (uint32_t)(sdesc[lo + (int)i].dst - n) | (kTagSweep << 16);
+          planes[slot * (uint32_t)pbuf + j * (uint32_t)max_col_all + i] =
+              philox4x32_10(make_uint4(gglob, sw, p, j), k0, k1);
+        }
+        pp = tgt;
       }
     } else {
       // records run one sweep behind: the record of sweep s-1 reads its
@@ -930,6 +1005,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     step(std::integral_constant<int, 1>{}, s);
     if constexpr (NC > 2) step(std::integral_constant<int, 2>{}, s);
     if constexpr (NC > 3) step(std::integral_constant<int, 3>{}, s);
+    if constexpr (BAL) pp -= U;  // production pointer relative to the next sweep
   }
   // the record still in flight: the last sweep's
   if (recorder) {
@@ -980,7 +1056,7 @@ constexpr int kMaxThreads = 608;  // 224 consumers + 352 producers + 1 recorder 
 // recorder paths get 128 registers.
 constexpr int kMaxThreadsWgt = 512;
 
-template <int NC, bool WGT, bool EXT>
+template <int NC, bool WGT, bool EXT, bool BAL>
 __global__ void __launch_bounds__(WGT ? kMaxThreadsWgt : kMaxThreads) sweep_kernel(const RunModelDev* __restrict__ rm,
                                                      int n_models, uint32_t total_groups,
                                                      uint32_t n_sweeps, Shape sh, int max_col,
@@ -993,12 +1069,12 @@ __global__ void __launch_bounds__(WGT ? kMaxThreadsWgt : kMaxThreads) sweep_kern
   const RunModelDev& r = rm[mi];
   const uint32_t g = flat - r.group_base;
   if (g >= r.groups) return;
-  run_group<NC, WGT, EXT>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
+  run_group<NC, WGT, EXT, BAL>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
 }
 
 // Persistent form: a fixed grid pops (model, group) items from a
 // cost-ordered work list with one atomic counter.  No CTA waits on another.
-template <int NC>
+template <int NC, bool BAL>
 __global__ void __launch_bounds__(kMaxThreads) sweep_persistent_kernel(
     const RunModelDev* __restrict__ rm, int n_models, const uint32_t* __restrict__ work,
     uint32_t n_work, uint32_t n_sweeps, Shape sh, int max_col, WsHeader* hdr) {
@@ -1015,7 +1091,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_persistent_kernel(
     const int mi = find_model(rm, n_models, flat);
     const RunModelDev& r = rm[mi];
     const uint32_t g = flat - r.group_base;
-    if (g < r.groups) run_group<NC, false, false>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
+    if (g < r.groups) run_group<NC, false, false, BAL>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
   }
 }
 
@@ -1379,7 +1455,8 @@ __global__ void reset_work_kernel(WsHeader* hdr) { hdr->work_next = 0u; }
 // has Toffoli links or two-qubit tables (EXT).
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
-                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt, bool ext) {
+                          size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt, bool ext,
+                          bool bal) {
   const int threads = cons + prod + 32;
   const Shape sh{cons, prod};
   auto go = [&](auto kern) {
@@ -1387,17 +1464,21 @@ cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_
                                                     max_col, hdr);
   };
   if (wgt && ext) {
-    if (nc <= 2) go(sweep_kernel<2, true, true>);
-    else if (nc == 3) go(sweep_kernel<3, true, true>);
-    else go(sweep_kernel<4, true, true>);
+    if (nc <= 2) go(sweep_kernel<2, true, true, false>);
+    else if (nc == 3) go(sweep_kernel<3, true, true, false>);
+    else go(sweep_kernel<4, true, true, false>);
   } else if (wgt) {
-    if (nc <= 2) go(sweep_kernel<2, true, false>);
-    else if (nc == 3) go(sweep_kernel<3, true, false>);
-    else go(sweep_kernel<4, true, false>);
+    if (nc <= 2) go(sweep_kernel<2, true, false, false>);
+    else if (nc == 3) go(sweep_kernel<3, true, false, false>);
+    else go(sweep_kernel<4, true, false, false>);
+  } else if (bal) {
+    if (nc <= 2) go(sweep_kernel<2, false, false, true>);
+    else if (nc == 3) go(sweep_kernel<3, false, false, true>);
+    else go(sweep_kernel<4, false, false, true>);
   } else {
-    if (nc <= 2) go(sweep_kernel<2, false, false>);
-    else if (nc == 3) go(sweep_kernel<3, false, false>);
-    else go(sweep_kernel<4, false, false>);
+    if (nc <= 2) go(sweep_kernel<2, false, false, false>);
+    else if (nc == 3) go(sweep_kernel<3, false, false, false>);
+    else go(sweep_kernel<4, false, false, false>);
   }
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
@@ -1406,21 +1487,25 @@ cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_
 cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
                                      uint32_t n_work, uint32_t n_sweeps, int cons, int prod,
                                      int max_col, int nc, int grid, size_t smem_bytes,
-                                     WsHeader* hdr, cudaStream_t st) {
+                                     WsHeader* hdr, cudaStream_t st, bool bal) {
   const int threads = cons + prod + 32;
   // the work counter is cleared by a kernel (a graph may hold this launch
   // inside a device-side loop, whose body takes kernels)
   reset_work_kernel<<<1, 1, 0, st>>>(hdr);
   const Shape sh{cons, prod};
-  if (nc <= 2)
-    sweep_persistent_kernel<2><<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work,
-                                                                  n_sweeps, sh, max_col, hdr);
-  else if (nc == 3)
-    sweep_persistent_kernel<3><<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work,
-                                                                  n_sweeps, sh, max_col, hdr);
-  else
-    sweep_persistent_kernel<4><<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work,
-                                                                  n_sweeps, sh, max_col, hdr);
+  auto go = [&](auto kern) {
+    kern<<<grid, threads, smem_bytes, st>>>(d_rm, n_models, d_work, n_work, n_sweeps, sh, max_col,
+                                            hdr);
+  };
+  if (bal) {
+    if (nc <= 2) go(sweep_persistent_kernel<2, true>);
+    else if (nc == 3) go(sweep_persistent_kernel<3, true>);
+    else go(sweep_persistent_kernel<4, true>);
+  } else {
+    if (nc <= 2) go(sweep_persistent_kernel<2, false>);
+    else if (nc == 3) go(sweep_persistent_kernel<3, false>);
+    else go(sweep_persistent_kernel<4, false>);
+  }
   advance_kernel<<<1, 1, 0, st>>>(hdr, n_sweeps);
   return cudaGetLastError();
 }
@@ -1469,8 +1554,9 @@ cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, ui
   return cudaGetLastError();
 }
 
-size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins, bool wgt) {
-  return group_smem_bytes(n, d, cons, max_col, hist_bins, wgt);
+size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins, bool wgt,
+                        bool bal) {
+  return group_smem_bytes(n, d, cons, max_col, hist_bins, wgt && !bal, bal && !wgt);
 }
 
 // Opt the sweep kernels into large dynamic shared memory (called once per
@@ -1479,18 +1565,24 @@ cudaError_t sweep_prepare() {
   const int big = (int)kSweepSmemMax;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(sweep_kernel<2, false, false>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<3, false, false>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<4, false, false>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<2, true, false>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<3, true, false>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<4, true, false>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<2, true, true>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<3, true, true>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_kernel<4, true, true>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_persistent_kernel<2>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_persistent_kernel<3>, a, big)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(sweep_persistent_kernel<4>, a, big)) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(sweep_kernel<2, false, false, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3, false, false, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4, false, false, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<2, false, false, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3, false, false, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4, false, false, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<2, true, false, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3, true, false, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4, true, false, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<2, true, true, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3, true, true, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4, true, true, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_persistent_kernel<2, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_persistent_kernel<3, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_persistent_kernel<4, false>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_persistent_kernel<2, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_persistent_kernel<3, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_persistent_kernel<4, true>, a, big)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(elim_kernel<false, 8>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(elim_kernel<false, 16>, a, big)) != cudaSuccess ||
@@ -1503,7 +1595,7 @@ cudaError_t sweep_prepare() {
 
 int sweep_max_blocks_per_sm(int threads, size_t smem) {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_persistent_kernel<4>, threads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_persistent_kernel<4, false>, threads,
                                                     smem) != cudaSuccess)
     return 1;
   return blocks;

@@ -101,6 +101,27 @@ def test_init_and_sweeps_bit_exact(case):
     assert np.array_equal(cnt, ref["cnt"])
 
 
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] in ("tiny", "ragged", "mid_shape", "one_chain")],
+                         ids=lambda c: c[0])
+def test_two_buffer_production_bit_exact(case, monkeypatch):
+    """Plain runs whose tables fit take 16 planes ahead per p-bit, produced
+    evenly over the colour steps in three buffers; the others (the largest
+    models) 12 planes in two buffers, made one step ahead.  The second form
+    is forced here (PB_BALANCED=0) on models that would take the first: both
+    must give the oracle's chains and histogram (the planes are the same
+    Philox outputs, only computed at another time)."""
+    monkeypatch.setenv("PB_BALANCED", "0")
+    name, n, d, seed, chains, J, beta = case
+    g = _circuit(name, n, d, seed)
+    J = W.default_J(n, d, g) if J is None else J
+    key = 0x5EED + 8
+    m, r = _gpu_run(n, d, g, J, key, chains, sweeps=(9,), beta=beta)
+    ref = oracle.gibbs(n, d, g, J=J, seed=key, chains=chains, sweeps=9, beta=beta)
+    assert np.array_equal(pbits.unslice_state(r.get_state(), chains), ref["state"])
+    cnt, valid, _ = r.histogram()
+    assert np.array_equal(cnt, ref["cnt"]) and valid == ref["valid"]
+
+
 def test_graph_replays_continue_the_stream():
     """sweeps(7) + sweeps(11) + sweeps(7) == the oracle's 25 sweeps."""
     n, d = 6, 9
