@@ -376,7 +376,7 @@ __host__ __device__ inline size_t group_smem_bytes(int n, int d, int cons, int m
                                                    uint32_t hist_bins, bool wgt = false,
                                                    bool bal = false) {
   return (size_t)3 * image_words(n, d) * 4 + (size_t)n * d * sizeof(Desc) +
-         (size_t)n * d * sizeof(Rec) + (size_t)hist_bins * (wgt ? 10 : 8) * 4 +
+         (size_t)n * d * sizeof(Rec) + (((size_t)hist_bins * (wgt ? 10 : 8) + 3) & ~(size_t)3) * 4 +
          (size_t)4 * cons * sizeof(ClassEnt) +
          (wgt ? (size_t)2 * ((size_t)kPre * max_col + (size_t)kPreC * cons)
               : bal ? (size_t)3 * kPrePlain * max_col : (size_t)2 * kPre * max_col) * sizeof(uint4);
@@ -704,7 +704,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   uint32_t* shist = rm.hist_smem ? after_rec : nullptr;
   // per bin: 8 u32 phase-class counters, or (general gates) 4 doubles (re,
   // im and their compensations) and a u32 count (10 words with padding)
-  const uint32_t hist_words = rm.bins * (wgt_m ? 10u : 8u);
+  // (rounded up to 16 bytes: the class table and the plane buffers follow)
+  const uint32_t hist_words = (rm.bins * (wgt_m ? 10u : 8u) + 3u) & ~3u;
   ClassEnt* sclass = reinterpret_cast<ClassEnt*>(after_rec + (rm.hist_smem ? hist_words : 0u));
   // plane buffers, each [max_col][KP] sweep-draw outputs, then (general-
   // gate runs) [cons][kPreC] acceptance outputs of the class's first cons
@@ -1040,7 +1041,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   } else if (shist) {
     unsigned long long* gh = rm.hist + (size_t)batch * rm.bins * 8u;
 #pragma unroll 1
-    for (uint32_t i = tid; i < hist_words; i += T)
+    for (uint32_t i = tid; i < rm.bins * 8u; i += T)
       if (shist[i]) atomicAdd(&gh[i], (unsigned long long)shist[i]);
   }
   if (recorder && lane == 0) {

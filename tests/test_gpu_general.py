@@ -64,6 +64,26 @@ def test_gibbs_bit_exact_vs_oracle(kind, n, d, seed, chains, sweeps):
     assert np.all(np.abs(psi - want) <= scale * _sum_tol(cnt, inf["n_u"]) + 1e-12)
 
 
+@pytest.mark.parametrize("n_alphas", [1, 3, 5])
+def test_odd_output_lists_bit_exact(n_alphas):
+    """An output list of odd length: the shared histogram holds 40 bytes a
+    bin, so the tables after it start at a 16-byte boundary only because
+    the histogram is rounded up to one; results as the oracle's."""
+    n, d, chains, sweeps = 5, 8, 100, 21
+    g, mats = _circuit("gen", n, d, 21)
+    alphas = np.array([3, 17, 30, 8, 21][:n_alphas], dtype=np.uint32)
+    m = pbits.Model(n, d, g, 3.0, mats=mats)
+    r = pbits.Run([m], [pbits.RunCfg(seed=78, chains=chains, alphas=alphas)])
+    r.sweeps(sweeps)
+    r.wait()
+    sums, cnt, valid, samples = r.phase_sums()
+    ref = oracle.u_gibbs(n, d, g, mats, J=3.0, seed=78, chains=chains, sweeps=sweeps, alphas=alphas)
+    assert np.array_equal(pbits.unslice_state(r.get_state(), chains), ref["state"])
+    assert samples == ref["samples"] and valid == ref["valid"]
+    assert np.array_equal(cnt, ref["cnt"])
+    assert np.all(np.abs(sums - ref["sum"]) <= _sum_tol(cnt, m.info()["n_u"]))
+
+
 def test_plain_and_general_models_share_a_run():
     """The general-gate kernel runs plain models unchanged (8 exact phase
     classes), and both match their oracles bit-exactly."""
