@@ -1292,6 +1292,9 @@ __global__ void __launch_bounds__(kFusedThreads) mlp_move64_kernel(FusedArgs a) 
   const int chain = r0 + srow;
   const bool live = lane < 16 && chain < a.rows;
   float lq_acc = 0.f;
+  const int groups = (a.n + 3) / 4;  // 4-bit groups of a layer's bits (n <= 32: at most 8)
+  const uint32_t move = MODE == kFusedSample ? *a.move_dev : 0u;
+  const uint32_t gc = a.group0 * 32u + (uint32_t)chain;
   // the previous-layer word of every row of the tile, for the x builders
   for (int r = tid; r < kTile64; r += kFusedThreads) {
     const int c = r0 + r;
@@ -1338,6 +1341,24 @@ __global__ void __launch_bounds__(kFusedThreads) mlp_move64_kernel(FusedArgs a) 
                        (c > 0) || (s > 0));
       tc::mma_commit(done);
     }
+    // while the tensor cores run layer 2: this thread's inputs to the logits
+    // step (the draw's Philox outputs for groups part and part + 4, or the
+    // current word), which depend on nothing the MMAs produce
+    uint4 upre[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+    uint32_t bits = 0u;
+    if (live) {
+      if (MODE == kFusedSample) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int g = part + kFusedParts * t;
+          if (g < groups)
+            upre[t] = philox4x32_10(make_uint4(gc, move, (uint32_t)(jl - 1) | (kTagMH << 16), (uint32_t)g),
+                                    a.k0, a.k1);
+        }
+      } else {
+        bits = a.P[(size_t)chain * a.d + (jl - 1)];
+      }
+    }
     wait_all(done, dph);
     dph ^= 1u;
     if (ok) epilogue(sB + H);
@@ -1361,17 +1382,14 @@ __global__ void __launch_bounds__(kFusedThreads) mlp_move64_kernel(FusedArgs a) 
     float qpart = 0.f;
     if (ok) {
       const float* b3 = sB + 2 * H;
-      const int groups = (a.n + 3) / 4;
-      const uint32_t move = MODE == kFusedSample ? *a.move_dev : 0u;
-      const uint32_t gc = a.group0 * 32u + (uint32_t)chain;
-      const uint32_t bits = (MODE == kFusedLogQ && live) ? a.P[(size_t)chain * a.d + (jl - 1)] : 0u;
-      for (int g = part; g < groups; g += kFusedParts) {  // warp-uniform
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {  // groups part, part + 4 (warp-uniform)
+        const int g = part + kFusedParts * t;
+        if (g >= groups) break;
         float la[4];
         tc::tmem_ld4(tq + 4u * (uint32_t)g, la);
         if (!live) continue;
-        uint4 u4 = make_uint4(0u, 0u, 0u, 0u);
-        if (MODE == kFusedSample)
-          u4 = philox4x32_10(make_uint4(gc, move, (uint32_t)(jl - 1) | (kTagMH << 16), (uint32_t)g), a.k0, a.k1);
+        const uint4 u4 = upre[t];
         const uint32_t U[4] = {u4.x, u4.y, u4.z, u4.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
