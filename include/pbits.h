@@ -331,8 +331,9 @@ typedef struct {
 PB_API int pb_run_stats(pb_run* run, pb_run_stats_t* stats);
 
 /* CTA shape of the sweep launches: consumer threads (redraw one colour
- * class, 32..224), producer threads (Philox planes of the next class,
- * 32..352), both multiples of 32, plus one recorder warp; blocks_per_sm
+ * class, 32..224), producer threads (the Philox planes the consumers
+ * compare against, made one or two colour steps ahead, 32..352), both
+ * multiples of 32, plus one recorder warp; blocks_per_sm
  * caps the persistent grid of batched runs (0 = as many as fit).  A run
  * with PB_U models takes at most 512 threads (consumers + producers + 32;
  * PB_ERANGE otherwise).  The results do not depend on the shape. */
