@@ -247,6 +247,8 @@ def main():
     ap.add_argument("--moves-only", type=int, default=0, metavar="K",
                     help="run K learned suffix moves (pb_mh_moves, one plain graph per move) on the "
                          "learned workload with an untrained network and exit: a profiling target")
+    ap.add_argument("--moves-workload", default="learned", choices=["learned", "large"],
+                    help="workload of --moves-only")
     ap.add_argument("--workload", default="mid", choices=["mid", "general_mid"],
                     help="headline circuit: mid (Clifford+T) or general_mid (30%% of the "
                          "one-qubit gates random unitaries)")
@@ -255,7 +257,7 @@ def main():
         args.warmup = 3
 
     if args.moves_only:
-        moves_only(args.moves_only)
+        moves_only(args.moves_only, args.moves_workload)
         return
     wl = W.mid() if args.workload == "mid" else W.general_mid()
     if args.impl == "reference":
@@ -433,24 +435,26 @@ def _eps_fit(pts, eps: float):
             "t_final_s": float(t[-1]), "points": [[float(a), float(b)] for a, b in pts]}
 
 
-def moves_only(k: int):
-    """K learned suffix moves on the learned workload (4096 chains, hidden
-    256, untrained network: the cost of a move does not depend on the
-    weights), each a replay of the move graph; prints the mean time."""
+def moves_only(k: int, workload: str = "learned"):
+    """K learned suffix moves on the learned workload (4096 chains) or the
+    large one (65536 chains), hidden 256, untrained network (the cost of a
+    move does not depend on the weights), each a replay of the move graph;
+    prints the mean time."""
     import torch
     from paper_2007_07379_gb300 import pbits
-    wl = W.learned()
+    wl = W.large() if workload == "large" else W.learned()
     pbits.load()
     m = pbits.Model(wl.n, wl.d, wl.gates, wl.J)
     net = pbits.Mlp(wl.n, wl.d, hidden=256, batch=4096, seed=3)
-    run = pbits.Run([m], [pbits.RunCfg(seed=wl.seed, chains=wl.chains)])
+    run = pbits.Run([m], [pbits.RunCfg(seed=wl.seed, chains=wl.chains, alphas=wl.alphas)])
     mh = pbits.Learned(run, net)
     mh.step(2)
     run.wait()
     t0 = time.perf_counter()
     mh.step(k)
     run.wait()
-    print(json.dumps({"moves": k, "ms_per_move": 1e3 * (time.perf_counter() - t0) / k}), flush=True)
+    print(json.dumps({"workload": workload, "moves": k,
+                      "ms_per_move": 1e3 * (time.perf_counter() - t0) / k}), flush=True)
 
 
 def learned_comparison(dev, stream, seconds: float = 8.0, train_paths: int = 1_000_000,
