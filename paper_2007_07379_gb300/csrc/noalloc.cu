@@ -114,7 +114,7 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
   }
   auto up32 = [](int x) { return ((x + 31) / 32) * 32; };
   const int cons = std::max(32, std::min(224, up32(maxcol)));
-  const int prod = std::max(32, std::min(352, up32(sweep_producers_wanted(*m, nc, false))));
+  int prod = std::max(32, std::min(kProducersMax, up32(sweep_producers_wanted(*m, nc, false))));
   // histogram placement and plane buffers: the rules of a single-model run
   // (shared memory when its u32 counters take at most 128 KiB and the CTA
   // still fits; 16 planes ahead in three buffers when that fits with the
@@ -128,6 +128,7 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
                    sweep_smem_bytes(n, d, cons, maxcol, hist_smem ? bins : 0, false, true) <= kSweepSmemMax;
   const size_t smem = sweep_smem_bytes(n, d, cons, maxcol, hist_smem ? bins : 0, false, bal);
   if (smem > kSweepSmemMax) return PB_ERANGE;
+  if (bal) prod = std::min(prod, kProducersBalanced);
 
   ModelDev md{};
   md.n = n;

@@ -226,6 +226,12 @@ inline int sweep_producers_wanted(const pb_model& m, int nc, bool wgt) {
   if (wgt) return 3 * maxcol;
   return std::max(3 * maxcol, (4 * m.col_off[4] + nc - 1) / std::max(1, nc));
 }
+// Default producer count caps: 352, and 224 for plain runs with the three-
+// buffer production (seven producer warps: with four consumer warps and the
+// recorder, three warps per scheduler; measured 6 % faster than 352 on the
+// mid workload, 2-4 % on the learned and large ones).
+constexpr int kProducersMax = 352;
+constexpr int kProducersBalanced = 224;
 template <class Models>  // a container of pointers to models
 inline int sweep_producers_wanted(const Models& ms, int nc, bool wgt) {
   int p = 32;

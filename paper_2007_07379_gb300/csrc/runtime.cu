@@ -1046,9 +1046,8 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
     for (int i = 0; i < r->nm; ++i) {
       const pb_model& m = *r->models[i];
       const uint32_t bins = r->L.ms[i].bins;
-      const size_t base = sweep_smem_bytes(m.n, m.d, cons, maxcol, 0, r->wgt, bal);
-      const size_t per_bin = sweep_smem_bytes(m.n, m.d, cons, maxcol, 1, r->wgt, bal) - base;
-      use[i] = bins <= cap_bins && base + (size_t)bins * per_bin <= kSweepSmemMax;
+      use[i] = bins <= cap_bins &&
+               sweep_smem_bytes(m.n, m.d, cons, maxcol, bins, r->wgt, bal) <= kSweepSmemMax;
       smem = std::max(smem, sweep_smem_bytes(m.n, m.d, cons, maxcol, use[i] ? bins : 0, r->wgt, bal));
     }
     return smem;
@@ -1090,26 +1089,32 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
 
 // Default launch shape: consumers = the largest colour class rounded up to
 // a warp (one p-bit per consumer per class), capped at 224; producers = one
-// per Philox call of a colour step (sweep_producers_wanted), capped at 352;
-// plus one recorder warp.  Environment overrides PB_CONS, PB_PROD
-// (multiples of 32).
+// per Philox call of a colour step (sweep_producers_wanted), capped at 352,
+// or at 224 when the run takes the three-buffer production; plus one
+// recorder warp.  Environment overrides PB_CONS, PB_PROD (multiples of 32).
 void choose_shape(pb_run* r) {
   int maxcol = 1;
   for (auto& m : r->models)
     for (int c = 0; c < 4; ++c) maxcol = std::max(maxcol, m->col_off[c + 1] - m->col_off[c]);
   auto up32 = [](int x) { return ((x + 31) / 32) * 32; };
   int cons = std::max(32, std::min(224, up32(maxcol)));
-  int prod = std::max(32, std::min(352, up32(sweep_producers_wanted(r->models, r->nc, r->wgt))));
+  const int want = up32(sweep_producers_wanted(r->models, r->nc, r->wgt));
+  int prod = std::max(32, std::min(kProducersMax, want));
   if (const char* e = std::getenv("PB_CONS")) {
     int v = std::atoi(e);
     if (v >= 32 && v <= 224 && v % 32 == 0) cons = v;
   }
+  bool fixed_prod = false;
   if (const char* e = std::getenv("PB_PROD")) {
     int v = std::atoi(e);
-    if (v >= 32 && v <= 352 && v % 32 == 0) prod = v;
+    if (v >= 32 && v <= 352 && v % 32 == 0) { prod = v; fixed_prod = true; }
   }
   if (r->wgt) prod = std::max(32, std::min(prod, kSweepThreadsWgt - 32 - cons));
   apply_shape(r, cons, prod, 0);
+  if (r->bal && !fixed_prod && prod > kProducersBalanced) {
+    prod = kProducersBalanced;
+    apply_shape(r, cons, prod, 0);
+  }
   // a shape whose tables do not fit: fewer consumers (their class table and
   // acceptance planes shrink; the class runs in more passes)
   while (r->smem > kSweepSmemMax && cons > 32) {
@@ -1612,7 +1617,7 @@ PB_API int pb_run_tune(pb_run* r, uint32_t trial_sweeps, const char* cache_path,
   for (int c : {64, 128, 224})
     if (c <= std::max(64, up)) cons_c.push_back(c);
   const int pw = sweep_producers_wanted(r->models, r->nc, r->wgt);
-  for (int p : {96, 192, 352})
+  for (int p : {96, 192, 224, 352})
     if (p <= std::max(96, ((pw + 31) / 32) * 32)) prod_c.push_back(p);
   if (r->nm > 1) bpsm_c = {1, 2, 0};
   double best = 1e30;
