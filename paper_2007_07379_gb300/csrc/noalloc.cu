@@ -128,7 +128,7 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
                    sweep_smem_bytes(n, d, cons, maxcol, hist_smem ? bins : 0, false, true) <= kSweepSmemMax;
   const size_t smem = sweep_smem_bytes(n, d, cons, maxcol, hist_smem ? bins : 0, false, bal);
   if (smem > kSweepSmemMax) return PB_ERANGE;
-  if (bal) prod = std::min(prod, kProducersBalanced);
+  if (bal) prod = std::min(prod, kProducersBalanced);  // cons + prod + 32 <= kSweepThreadsBal
 
   ModelDev md{};
   md.n = n;

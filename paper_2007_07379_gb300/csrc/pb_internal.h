@@ -176,6 +176,10 @@ constexpr size_t kSweepSmemMax = 226 * 1024;
 // Threads per sweep CTA in a run with general one-qubit gates (the general
 // instantiation is compiled for at most this many).
 constexpr int kSweepThreadsWgt = 512;
+// Plain runs with the three-buffer production: at most 512 threads a CTA,
+// so that the kernel gets up to 128 registers a thread (larger shapes take
+// the two-buffer form, 608 threads and 96 registers).
+constexpr int kSweepThreadsBal = 512;
 
 constexpr uint32_t kTagSweep = 0;
 constexpr uint32_t kTagInit = 1;

@@ -38,7 +38,7 @@ cudaError_t launch_philox_fill(const uint32_t* ctr, uint32_t k0, uint32_t k1, ui
 size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins,
                         bool wgt = false, bool bal = false);
 cudaError_t sweep_prepare();
-int sweep_max_blocks_per_sm(int threads, size_t smem);
+int sweep_max_blocks_per_sm(int threads, size_t smem, bool bal);
 }  // namespace pb
 
 using namespace pb;
@@ -1064,9 +1064,10 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
   size_t smem_b = 0;
   if (!r->wgt) {
     smem_b = layout(true, use_b);
-    bal = smem_b <= kSweepSmemMax && use_b == use_s;
+    bal = smem_b <= kSweepSmemMax && use_b == use_s && r->threads <= kSweepThreadsBal;
     if (bal && r->persistent)
-      bal = sweep_max_blocks_per_sm(r->threads, smem_b) >= sweep_max_blocks_per_sm(r->threads, smem_s);
+      bal = sweep_max_blocks_per_sm(r->threads, smem_b, true) >=
+            sweep_max_blocks_per_sm(r->threads, smem_s, false);
     if (const char* e = std::getenv("PB_BALANCED")) bal = bal && std::atoi(e) != 0;
   }
   const std::vector<char>& use = bal ? use_b : use_s;
@@ -1079,7 +1080,7 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = sweep_max_blocks_per_sm(r->threads, smem);
+    int per_sm = sweep_max_blocks_per_sm(r->threads, smem, r->bal);
     if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
     r->grid = std::max(1, sms * std::max(1, per_sm));
     r->grid = (int)std::min<uint32_t>((uint32_t)r->grid, r->total_groups);
@@ -1110,9 +1111,13 @@ void choose_shape(pb_run* r) {
     if (v >= 32 && v <= 352 && v % 32 == 0) { prod = v; fixed_prod = true; }
   }
   if (r->wgt) prod = std::max(32, std::min(prod, kSweepThreadsWgt - 32 - cons));
-  apply_shape(r, cons, prod, 0);
-  if (r->bal && !fixed_prod && prod > kProducersBalanced) {
-    prod = kProducersBalanced;
+  if (!r->wgt && !fixed_prod && prod > kProducersBalanced) {
+    // the three-buffer form with its producer count where it applies, else
+    // the two-buffer form with the larger one
+    apply_shape(r, cons, kProducersBalanced, 0);
+    if (r->bal) prod = kProducersBalanced;
+    else apply_shape(r, cons, prod, 0);
+  } else {
     apply_shape(r, cons, prod, 0);
   }
   // a shape whose tables do not fit: fewer consumers (their class table and

@@ -819,8 +819,10 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       const int m = D.mflag & 3;
       if (m == 1) { D.a[1] = D.a[0]; D.b[1] = D.b[0]; }
       ClassEnt E;
+      // plain runs: link words as shared-window addresses (no add per load)
+      const uint32_t lbase = WGT ? 0u : (uint32_t)__cvta_generic_to_shared(W);
 #pragma unroll
-      for (int l = 0; l < 3; ++l) { E.la[l] = 4u * D.a[l]; E.lb[l] = 4u * D.b[l]; }
+      for (int l = 0; l < 3; ++l) { E.la[l] = lbase + 4u * D.a[l]; E.lb[l] = lbase + 4u * D.b[l]; }
       E.dst = 4u * D.dst;
       E.m = (uint32_t)m;
       if (WGT && (D.mflag & 8)) E.m |= 0x100u;     // coupled: Metropolis acceptance
@@ -886,7 +888,9 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     uint32_t* S = smem + iw * (1 + (s & 1u));
     // plane buffer of global step s NC + C
     const uint32_t gstep = s * (uint32_t)NC + (uint32_t)C;
-    const uint4* cur = planes + (BAL ? (gstep % 3u) : (gstep & 1u)) * pbuf;
+    // (with three colour steps a sweep, step C's buffer is C)
+    const uint32_t cslot = BAL ? (NC == 3 ? (uint32_t)C : gstep % 3u) : (gstep & 1u);
+    const uint4* cur = planes + cslot * pbuf;
     if (consumer) {
       const int lo = col_lo[C], hi = col_hi[C], K = hi - lo;
       // the first p-bit of every consumer from its table entry; warps with no
@@ -899,9 +903,15 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         for (int j = 0; j < KP; ++j) R[j] = rp[j * pst];
         const char* Wb = reinterpret_cast<const char*>(W);
         auto word = [&](uint32_t off) { return *reinterpret_cast<const uint32_t*>(Wb + off); };
-        const uint32_t r0 = word(E.la[0]) ^ word(E.lb[0]);
-        const uint32_t r1 = word(E.la[1]) ^ word(E.lb[1]);
-        const uint32_t r2 = word(E.la[2]) ^ word(E.lb[2]);
+        auto link = [&](uint32_t a) {  // plain runs: a is a shared-window address
+          if constexpr (WGT) return word(a);
+          uint32_t x;
+          asm volatile("ld.shared.u32 %0, [%1];" : "=r"(x) : "r"(a));
+          return x;
+        };
+        const uint32_t r0 = link(E.la[0]) ^ link(E.lb[0]);
+        const uint32_t r1 = link(E.la[1]) ^ link(E.lb[1]);
+        const uint32_t r2 = link(E.la[2]) ^ link(E.lb[2]);
         const uint32_t pidx = (E.dst / 4u - (uint32_t)n) | (kTagSweep << 16);
         // coupled p-bit: its coupling entry and neighbour words, loaded
         // ahead so that their latency overlaps the heat-bath draw
@@ -973,7 +983,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
           const uint32_t i = r / (uint32_t)KP, j = r - i * (uint32_t)KP;
           const int lo = second ? col_lo[C2] : col_lo[C1];
           const uint32_t sw = sweep + (second ? c2 : c1);
-          const uint32_t slot = (gstep + (second ? 2u : 1u)) % 3u;
+          const uint32_t slot = NC == 3 ? (second ? (uint32_t)((C + 2) % 3) : (uint32_t)((C + 1) % 3))
+                                        : (gstep + (second ? 2u : 1u)) % 3u;
           const uint32_t p = (uint32_t)(sdesc[lo + (int)i].dst - n) | (kTagSweep << 16);
           planes[slot * (uint32_t)pbuf + j * (uint32_t)max_col_all + i] =
               philox4x32_10(make_uint4(gglob, sw, p, j), k0, k1);
@@ -1058,7 +1069,7 @@ constexpr int kMaxThreads = 608;  // 224 consumers + 352 producers + 1 recorder 
 constexpr int kMaxThreadsWgt = 512;
 
 template <int NC, bool WGT, bool EXT, bool BAL>
-__global__ void __launch_bounds__(WGT ? kMaxThreadsWgt : kMaxThreads) sweep_kernel(const RunModelDev* __restrict__ rm,
+__global__ void __launch_bounds__(WGT ? kMaxThreadsWgt : (BAL ? kSweepThreadsBal : kMaxThreads)) sweep_kernel(const RunModelDev* __restrict__ rm,
                                                      int n_models, uint32_t total_groups,
                                                      uint32_t n_sweeps, Shape sh, int max_col,
                                                      WsHeader* hdr) {
@@ -1076,7 +1087,7 @@ __global__ void __launch_bounds__(WGT ? kMaxThreadsWgt : kMaxThreads) sweep_kern
 // Persistent form: a fixed grid pops (model, group) items from a
 // cost-ordered work list with one atomic counter.  No CTA waits on another.
 template <int NC, bool BAL>
-__global__ void __launch_bounds__(kMaxThreads) sweep_persistent_kernel(
+__global__ void __launch_bounds__(BAL ? kSweepThreadsBal : kMaxThreads) sweep_persistent_kernel(
     const RunModelDev* __restrict__ rm, int n_models, const uint32_t* __restrict__ work,
     uint32_t n_work, uint32_t n_sweeps, Shape sh, int max_col, WsHeader* hdr) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -1594,12 +1605,14 @@ cudaError_t sweep_prepare() {
   return cudaFuncSetAttribute(elim_kernel<true, 32>, a, big);
 }
 
-int sweep_max_blocks_per_sm(int threads, size_t smem) {
+int sweep_max_blocks_per_sm(int threads, size_t smem, bool bal) {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_persistent_kernel<4, false>, threads,
-                                                    smem) != cudaSuccess)
-    return 1;
-  return blocks;
+  const cudaError_t e =
+      bal ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_persistent_kernel<4, true>,
+                                                          threads, smem)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_persistent_kernel<4, false>,
+                                                          threads, smem);
+  return e == cudaSuccess ? blocks : 1;
 }
 
 }  // namespace pb
