@@ -835,7 +835,10 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       sclass[c * sh.cons + tid] = E;
     }
   }
-  // Producers: the Philox outputs of class C at sweep `sw` into `buf`.
+  // Producers: the Philox outputs of class C at sweep `sw` into `buf`
+  // (three-buffer runs: with the group's round keys computed once).
+  [[maybe_unused]] PhiloxGroup pg;
+  if constexpr (BAL) pg = philox_group(gglob, k0, k1);
   auto produce = [&](auto cc, uint32_t sw, uint4* buf) {
     constexpr int C = decltype(cc)::value;
     const int lo = col_lo[C], K = col_hi[C] - lo;
@@ -987,7 +990,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
                                         : (gstep + (second ? 2u : 1u)) % 3u;
           const uint32_t p = (uint32_t)(sdesc[lo + (int)i].dst - n) | (kTagSweep << 16);
           planes[slot * (uint32_t)pbuf + j * (uint32_t)max_col_all + i] =
-              philox4x32_10(make_uint4(gglob, sw, p, j), k0, k1);
+              philox4x32_10_group(pg, sw, p, j);
         }
         pp = tgt;
       }
