@@ -1002,10 +1002,12 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         const uint32_t* Sp = smem + iw * (1 + ((s + 1u) & 1u));
         if constexpr (C == 0) rec.clear();
         if constexpr (C + 1 < NC) {
-          rec.read<EXT>(Sp, srec, C * npb / (NC - 1), (C + 1) * npb / (NC - 1), lane);
-          if (wgt_m) rec.read_u(Sp, rm.uph, C * nug / (NC - 1), (C + 1) * nug / (NC - 1), lane);
-          if (EXT && rm.trec)
-            rec.read_t(Sp, rm.trec, C * md.n_tr / (NC - 1), (C + 1) * md.n_tr / (NC - 1), lane);
+          // part C of the records: one share in step 0 (the largest class,
+          // the most consumer warps), two in each later step
+          constexpr int D = 2 * (NC - 1) - 1, B0 = C == 0 ? 0 : 2 * C - 1, B1 = 2 * C + 1;
+          rec.read<EXT>(Sp, srec, B0 * npb / D, B1 * npb / D, lane);
+          if (wgt_m) rec.read_u(Sp, rm.uph, B0 * nug / D, B1 * nug / D, lane);
+          if (EXT && rm.trec) rec.read_t(Sp, rm.trec, B0 * md.n_tr / D, B1 * md.n_tr / D, lane);
         } else {
           rec.reduce(Sp, n, d, lane);
           rec.bin<WGT>(rm_g, g, batch, lane, shist, n_valid, n_samples);
