@@ -1358,31 +1358,52 @@ __device__ inline void batch_sum(const RunModelDev& rm, bool wgt, uint32_t b, ui
   }
 }
 
+// One warp per bin, the lanes over the batches (lane b takes batches b,
+// b + 32, ...): the counts (or phase sums) and valid totals of every batch
+// are summed by warp reductions, then each lane adds its batches' terms of
+// the batch-means variance (one FP64 division a batch, the terms summed by
+// a compensated add per lane and a warp reduction).
 __global__ void amplitude_kernel(const RunModelDev* __restrict__ rm_all, int model) {
   const RunModelDev& rm = rm_all[model];
-  const uint32_t bin = blockIdx.x * blockDim.x + threadIdx.x;
-  if (bin >= rm.bins) return;
+  const uint32_t bin = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (bin >= rm.bins) return;  // whole warp
   const int h = rm.model->h;
   const bool wgt = rm.model->wgt != 0;
   // 2^{h/2} (Clifford+T: every valid path has |U_C| = 2^{-h/2}); general
-  // gates: 2^{log2z}, the sum of |U_C| over all paths
-  const double scale_h = wgt ? exp2(rm.model->log2z + (double)rm.amp_shift)
-                             : exp2(0.5 * (double)h + (double)rm.amp_shift);
+  // gates: 2^{log2z}, the sum of |U_C| over all paths (FP64 issues slowly on
+  // this part: one lane evaluates the warp-uniform factors)
+  double scale_h = 0.0;
+  if (lane == 0)
+    scale_h = wgt ? exp2(rm.model->log2z + (double)rm.amp_shift)
+                  : exp2(0.5 * (double)h + (double)rm.amp_shift);
+  scale_h = __shfl_sync(0xffffffffu, scale_h, 0);
   unsigned long long tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   double wre = 0.0, wim = 0.0;
   unsigned long long vtot = 0;
-  for (uint32_t b = 0; b < rm.n_batches; ++b) {
-    const unsigned long long* c = rm.hist + ((size_t)b * rm.bins + bin) * 8u;
+  for (uint32_t b = (uint32_t)lane; b < rm.n_batches; b += 32u) {
     if (wgt) {
       double x, y;
       batch_sum(rm, true, b, bin, x, y);
       wre += x;
       wim += y;
     } else {
+      const unsigned long long* c = rm.hist + ((size_t)b * rm.bins + bin) * 8u;
 #pragma unroll
       for (int k = 0; k < 8; ++k) tot[k] += c[k];
     }
     vtot += rm.valid[b];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    vtot += __shfl_xor_sync(0xffffffffu, vtot, off);
+    if (wgt) {
+      wre += __shfl_xor_sync(0xffffffffu, wre, off);
+      wim += __shfl_xor_sync(0xffffffffu, wim, off);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], off);
+    }
   }
   double re = 0.0, im = 0.0, se = 0.0;
   if (vtot > 0) {
@@ -1392,27 +1413,43 @@ __global__ void amplitude_kernel(const RunModelDev* __restrict__ rm_all, int mod
     } else {
       phase_sum(tot, re, im);
     }
-    re *= scale_h / (double)vtot;
-    im *= scale_h / (double)vtot;
+    double f = 0.0, inv_vtot = 0.0;
+    if (lane == 0) {
+      f = scale_h / (double)vtot;
+      inv_vtot = 1.0 / (double)vtot;
+    }
+    f = __shfl_sync(0xffffffffu, f, 0);
+    inv_vtot = __shfl_sync(0xffffffffu, inv_vtot, 0);
+    re *= f;
+    im *= f;
     uint32_t nb = 0;
     Kahan acc;
-    for (uint32_t b = 0; b < rm.n_batches; ++b) {
+    for (uint32_t b = (uint32_t)lane; b < rm.n_batches; b += 32u) {
       const unsigned long long vb = rm.valid[b];
       if (vb == 0) continue;
       ++nb;
       double br, bi;
       batch_sum(rm, wgt, b, bin, br, bi);
-      br = br * scale_h / (double)vb - re;
-      bi = bi * scale_h / (double)vb - im;
-      const double w = (double)vb / (double)vtot;
+      const double fb = scale_h / (double)vb;
+      br = br * fb - re;
+      bi = bi * fb - im;
+      const double w = (double)vb * inv_vtot;
       acc.add(w * w * (br * br + bi * bi));
     }
-    se = nb > 1 ? sqrt(acc.s * (double)nb / (double)(nb - 1)) : 0.0;
+    double var = acc.s - acc.c;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      var += __shfl_xor_sync(0xffffffffu, var, off);
+      nb += __shfl_xor_sync(0xffffffffu, nb, off);
+    }
+    if (lane == 0) se = nb > 1 ? sqrt(var * (double)nb / (double)(nb - 1)) : 0.0;
   }
-  double* out = rm.amp + (size_t)bin * 3u;
-  out[0] = re;
-  out[1] = im;
-  out[2] = se;
+  if (lane == 0) {
+    double* out = rm.amp + (size_t)bin * 3u;
+    out[0] = re;
+    out[1] = im;
+    out[2] = se;
+  }
 }
 
 // L2 normalisation over the recorded bins (Fig. 2 Step 4), one CTA.
@@ -1558,8 +1595,9 @@ size_t elim_smem_bytes(int n, int d, int zwords, int warps) {
 
 cudaError_t launch_amplitudes(const RunModelDev* d_rm, int model, uint32_t bins, int l2,
                               cudaStream_t st) {
-  const int tpb = 256;
-  amplitude_kernel<<<(bins + tpb - 1) / tpb, tpb, 0, st>>>(d_rm, model);
+  // one warp a bin, eight bins a CTA
+  const uint32_t per_cta = 8;
+  amplitude_kernel<<<(bins + per_cta - 1) / per_cta, 32 * per_cta, 0, st>>>(d_rm, model);
   if (l2) normalize_kernel<<<1, 1024, 0, st>>>(d_rm, model);
   return cudaGetLastError();
 }
