@@ -77,3 +77,20 @@ def test_shape_does_not_change_results(cons, prod):
     ref = oracle.gibbs(n, d, g, J=3.0, seed=4, chains=256, sweeps=12)
     assert np.array_equal(pbits.unslice_state(r.get_state(), 256), ref["state"])
     assert np.array_equal(r.histogram()[0], ref["cnt"])
+
+
+def test_two_buffer_persistent_launch_matches(monkeypatch):
+    """The persistent launch in both plane-buffer forms (three buffers with
+    16 planes ahead, the default; two with 12, forced by PB_BALANCED=0):
+    identical chains and histograms for 16 uneven circuits."""
+    wls = W.batched()[:16]
+    _, a = _batched_run(wls)
+    a.sweeps(9)
+    a.wait()
+    monkeypatch.setenv("PB_BALANCED", "0")
+    _, b = _batched_run(wls)
+    b.sweeps(9)
+    b.wait()
+    for i in range(len(wls)):
+        assert np.array_equal(a.get_state(i), b.get_state(i)), i
+        assert np.array_equal(a.histogram(i)[0], b.histogram(i)[0]), i
