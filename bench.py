@@ -676,9 +676,10 @@ def batched_measurement(dev, stream, sweeps: int = 10_000):
 
 def large_measurement(dev, stream, sweeps: int = 2000, moves: int = 40):
     """The large workload: n=24, d=32 (792 p-bits), 65536 chains, 64 output
-    amplitudes; plain sweeps, and the PB_LEARNED run mode (a suffix move
-    before every sweep, one graph per call; untrained network: the cost of a
-    move does not depend on the weights)."""
+    amplitudes; plain sweeps, the PB_LEARNED run mode (a suffix move before
+    every sweep, one graph per call) and the moves alone (pb_mh_moves, one
+    graph per move, CUDA events); untrained network: the cost of a move does
+    not depend on the weights."""
     import torch
     from paper_2007_07379_gb300 import pbits
     wl = W.large()
@@ -699,12 +700,24 @@ def large_measurement(dev, stream, sweeps: int = 2000, moves: int = 40):
         lr.sweeps(moves)
         lr.wait()
         ms_l = lr.stats()["last_ms"]
+        run.sweeps(1)
+        run.wait()
+        one = run.stats()["last_ms"]
+        mh = pbits.Learned(run, net)
+        mh.step(2)
+        run.wait()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mh.step(moves)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_mv = e0.elapsed_time(e1) / moves
     flips = wl.chains * wl.n * wl.d * sweeps
-    per_sweep = ms / sweeps
     return {"workload": "large: random Clifford+T n=24 d=32 (792 p-bits), 65536 chains, 64 amplitudes",
             "sweeps": sweeps, "launch_ms": ms, "flips_per_s": flips / (ms * 1e-3),
+            "ms_per_mh_move": ms_mv,
             "learned_run_ms_per_move_and_sweep": ms_l / moves,
-            "ms_per_mh_move": ms_l / moves - per_sweep}
+            "one_sweep_launch_ms": one}
 
 
 def kernel_rev() -> str:
