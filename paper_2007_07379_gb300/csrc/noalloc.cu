@@ -21,7 +21,7 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
                           size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt = false,
-                          bool ext = false, bool bal = false);
+                          bool ext = false, bool bal = false, bool dec = false);
 size_t sweep_smem_bytes(int n, int d, int cons, int max_col, uint32_t hist_bins,
                         bool wgt = false, bool bal = false);
 cudaError_t sweep_prepare();
@@ -184,7 +184,7 @@ extern "C" PB_API int pb_gibbs_run_noalloc(const pb_model* m, const pb_run_cfg* 
     return PB_ECUDA;
   if (n_sweeps > 0 &&
       (e = launch_sweeps(d_rm, 1, groups, n_sweeps, cons, prod, maxcol, nc, smem, hdr, st, false,
-                         false, bal)) != cudaSuccess)
+                         false, bal, bal && maxcol > cons)) != cudaSuccess)
     return PB_ECUDA;
   if ((e = cudaMemcpyAsync(d_counts, base + o_hist, (size_t)bins * 8 * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(d_totals, base + o_cnt, 2 * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)

@@ -22,7 +22,7 @@ cudaError_t launch_init(const RunModelDev* d_rm, int n_models, uint32_t total_gr
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
                           size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt = false,
-                          bool ext = false, bool bal = false);
+                          bool ext = false, bool bal = false, bool dec = false);
 cudaError_t launch_sweeps_persistent(const RunModelDev* d_rm, int n_models, const uint32_t* d_work,
                                      uint32_t n_work, uint32_t n_sweeps, int cons, int prod,
                                      int max_col, int nc, int grid, size_t smem_bytes,
@@ -910,6 +910,7 @@ struct pb_run {
   bool wgt = false;        // some model has PB_U gates (the general-gate kernels)
   bool ext = false;        // some model has Toffoli links or two-qubit tables
   bool bal = false;        // plain run with 16 planes ahead, produced evenly over the steps
+  bool dec = false;        // (with bal) the recorder outside the colour steps' barriers
   int nc = 2;              // colour steps per sweep (largest over the models)
   bool elim = false;       // exact-sampler run: i.i.d. paths instead of sweeps
   size_t elim_smem = 0;
@@ -961,7 +962,7 @@ cudaError_t enqueue_sweeps(pb_run* r, uint32_t n_sweeps, cudaStream_t st) {
                                     r->total_groups, n_sweeps, r->cons, r->prod, r->max_col, r->nc,
                                     r->grid, r->smem, r->hdr(), st, r->bal);
   return launch_sweeps(r->d_rm(), r->nm, r->total_groups, n_sweeps, r->cons, r->prod, r->max_col,
-                       r->nc, r->smem, r->hdr(), st, r->wgt, r->ext, r->bal);
+                       r->nc, r->smem, r->hdr(), st, r->wgt, r->ext, r->bal, r->dec);
 }
 
 // Graph of n sweeps of a learned run (Fig. 2 Step 1 with the network as the
@@ -1074,6 +1075,9 @@ void apply_shape(pb_run* r, int cons, int prod, int blocks_per_sm) {
   for (int i = 0; i < r->nm; ++i) r->rm[i].hist_smem = use[i] ? 1u : 0u;
   const size_t smem = bal ? smem_b : smem_s;
   r->bal = bal;
+  // the recorder outside the colour steps' barriers where some class takes
+  // more than one consumer pass (single-grid plain runs)
+  r->dec = bal && !r->wgt && !r->persistent && maxcol > cons;
   r->smem = smem;
   r->grid = 0;
   if (r->persistent) {

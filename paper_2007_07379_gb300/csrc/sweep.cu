@@ -683,7 +683,7 @@ __device__ __noinline__ void redraw_extra_coupled(uint32_t* W, uint32_t* S, cons
 // (plain runs whose tables leave room): 16 planes computed ahead per p-bit
 // in three buffers, produced evenly over the colour steps; otherwise 12
 // planes in two buffers, each class's produced during the step before.
-template <int NC, bool WGT, bool EXT, bool BAL>
+template <int NC, bool WGT, bool EXT, bool BAL, bool DEC = false>
 __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, uint32_t n_sweeps,
                           Shape sh, int max_col_all, uint32_t* smem, WsHeader* hdr) {
   // run and model constants held in registers for the whole launch
@@ -1002,11 +1002,13 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
     } else {
       // records run one sweep behind: the record of sweep s-1 reads its
       // snapshot in NC-1 parts (steps 0..NC-2 of sweep s), then reduces and
-      // bins (step NC-1).  General-gate runs: the recorder takes no part in
-      // the colour steps' barriers, only in the sweep's last one (it reads
-      // the previous sweep's snapshot, which no consumer writes during this
-      // sweep, at its own pace; measured 3.6 % faster there, and slower on
-      // the plain mid circuit, whose steps it then crowds).
+      // bins (step NC-1).  General-gate runs, and plain runs with DEC: the
+      // recorder takes no part in the colour steps' barriers, only in the
+      // sweep's last one (it reads the previous sweep's snapshot, which no
+      // consumer writes during this sweep, at its own pace; measured 3-4 %
+      // faster on general_mid and on the large workload, whose classes take
+      // two consumer passes, and slower on the plain mid circuit, whose
+      // steps it then crowds).
       if (s > 0u && recorded(sweep - 1u)) {
         const uint32_t* Sp = smem + iw * (1 + ((s + 1u) & 1u));
         if constexpr (C == 0) rec.clear();
@@ -1023,7 +1025,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
         }
       }
     }
-    if constexpr (WGT && C + 1 < NC) {
+    if constexpr ((WGT || DEC) && C + 1 < NC) {
       if (!recorder) bar_sync_first(1u, (uint32_t)(sh.cons + sh.prod));
     } else {
       __syncthreads();  // (the sweep's end: snapshots change parity)
@@ -1086,7 +1088,7 @@ constexpr int kMaxThreads = 608;  // 224 consumers + 352 producers + 1 recorder 
 // recorder paths get 128 registers.
 constexpr int kMaxThreadsWgt = 512;
 
-template <int NC, bool WGT, bool EXT, bool BAL>
+template <int NC, bool WGT, bool EXT, bool BAL, bool DEC = false>
 __global__ void __launch_bounds__(WGT ? kMaxThreadsWgt : (BAL ? kSweepThreadsBal : kMaxThreads)) sweep_kernel(const RunModelDev* __restrict__ rm,
                                                      int n_models, uint32_t total_groups,
                                                      uint32_t n_sweeps, Shape sh, int max_col,
@@ -1099,7 +1101,7 @@ __global__ void __launch_bounds__(WGT ? kMaxThreadsWgt : (BAL ? kSweepThreadsBal
   const RunModelDev& r = rm[mi];
   const uint32_t g = flat - r.group_base;
   if (g >= r.groups) return;
-  run_group<NC, WGT, EXT, BAL>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
+  run_group<NC, WGT, EXT, BAL, DEC>(r, g, sweep0, n_sweeps, sh, max_col, smem, hdr);
 }
 
 // Persistent form: a fixed grid pops (model, group) items from a
@@ -1523,7 +1525,7 @@ __global__ void reset_work_kernel(WsHeader* hdr) { hdr->work_next = 0u; }
 cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_groups,
                           uint32_t n_sweeps, int cons, int prod, int max_col, int nc,
                           size_t smem_bytes, WsHeader* hdr, cudaStream_t st, bool wgt, bool ext,
-                          bool bal) {
+                          bool bal, bool dec) {
   const int threads = cons + prod + 32;
   const Shape sh{cons, prod};
   auto go = [&](auto kern) {
@@ -1538,6 +1540,10 @@ cudaError_t launch_sweeps(const RunModelDev* d_rm, int n_models, uint32_t total_
     if (nc <= 2) go(sweep_kernel<2, true, false, false>);
     else if (nc == 3) go(sweep_kernel<3, true, false, false>);
     else go(sweep_kernel<4, true, false, false>);
+  } else if (bal && dec) {
+    if (nc <= 2) go(sweep_kernel<2, false, false, true, true>);
+    else if (nc == 3) go(sweep_kernel<3, false, false, true, true>);
+    else go(sweep_kernel<4, false, false, true, true>);
   } else if (bal) {
     if (nc <= 2) go(sweep_kernel<2, false, false, true>);
     else if (nc == 3) go(sweep_kernel<3, false, false, true>);
@@ -1639,6 +1645,9 @@ cudaError_t sweep_prepare() {
       (e = cudaFuncSetAttribute(sweep_kernel<2, false, false, true>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_kernel<3, false, false, true>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_kernel<4, false, false, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<2, false, false, true, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<3, false, false, true, true>, a, big)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(sweep_kernel<4, false, false, true, true>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_kernel<2, true, false, false>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_kernel<3, true, false, false>, a, big)) != cudaSuccess ||
       (e = cudaFuncSetAttribute(sweep_kernel<4, true, false, false>, a, big)) != cudaSuccess ||
