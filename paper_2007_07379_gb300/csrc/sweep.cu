@@ -874,7 +874,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   // of the stream up to max(D(t + 2), pp + B) and at most D(t + 3), B = U /
   // NC a step (D(t): units of the steps before t; pp: units produced so
   // far, kept relative to the current sweep's first unit).  With classes of
-  // 116, 91 and 33 p-bits this is 336 outputs a step instead of 364, 132 and
+  // 116, 91 and 33 p-bits this is 320 outputs a step instead of 364, 132 and
   // 464 for the next step alone.
   [[maybe_unused]] const uint32_t U = (uint32_t)(KP * col_hi[NC - 1]);  // every p-bit is in one class
   [[maybe_unused]] const uint32_t B = (U + NC - 1) / NC;
