@@ -203,6 +203,22 @@ def test_amplitude_kernel_matches_counts():
     assert np.allclose(psin, want / np.sqrt(np.sum(np.abs(want) ** 2)), rtol=1e-12, atol=1e-14)
 
 
+def test_amplitude_kernel_many_batches():
+    """More batches than a warp has lanes (the amplitude kernel's lanes take
+    batches b, b + 32, ...): amplitudes equal the oracle's estimate of the
+    same counts."""
+    n, d = 4, 5
+    g = W.random_circuit(n, d, 22)
+    m, r = _gpu_run(n, d, g, 3.0, 3, 45 * 32, sweeps=(60,), n_batches=45)
+    cnt, valid, _ = r.histogram()
+    psi, se = r.amplitudes()
+    want = oracle.estimate_amplitudes(cnt, valid, m.info()["h"])
+    assert np.allclose(psi, want, rtol=1e-12, atol=1e-14)
+    assert np.all(se >= 0) and np.all(np.isfinite(se))
+    reached = cnt.sum(axis=1) > 0
+    assert np.all(se[reached] > 0)
+
+
 def test_tiny_workload_amplitudes():
     """Tiny workload at its budget (1024 chains x 1e4 sweeps): every amplitude
     within 5 batch-means standard errors of the FP64 state vector."""
