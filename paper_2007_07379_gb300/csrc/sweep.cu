@@ -890,6 +890,8 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
   // One colour class C of sweep sweep0 + s: consumers redraw it from plane
   // buffer C & 1, producers fill the other buffer for the next class, the
   // recorder works on the previous sweep's snapshot; then one barrier.
+  [[maybe_unused]] ClassEnt En{};  // DEC consumers: the coming step's table entry
+  if (DEC && consumer) En = sclass[tid];
   auto step = [&](auto cc, uint32_t s) {
     constexpr int C = decltype(cc)::value;
     const uint32_t sweep = sweep0 + s;
@@ -904,7 +906,7 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
       // the first p-bit of every consumer from its table entry; warps with no
       // p-bit in this class skip it (their entries are dummies)
       if (warp * 32 < K) {
-        const ClassEnt E = sclass[C * sh.cons + tid];
+        const ClassEnt E = DEC ? En : sclass[C * sh.cons + tid];
         const uint4* rp = cur + pidx_of(tid < K ? tid : 0, 0);  // dummies: any planes
         uint4 R[KP];
 #pragma unroll
@@ -964,6 +966,9 @@ __device__ void run_group(const RunModelDev& rm_g, uint32_t g, uint32_t sweep0, 
           redraw_extra<KP>(W, S, sdesc, cur, pst, lo, tid + sh.cons, hi, sh.cons, n, fast, thr0, thr1, thr2,
                        thr3, gglob, sweep, k0, k1);
       }
+      // DEC: the next step's table entry, loaded before the barrier so that
+      // the step after it starts with the link loads
+      if constexpr (DEC) En = sclass[((C + 1) % NC) * sh.cons + tid];
     } else if (producer) {
       if constexpr (!BAL) {
         // the next step: class C + 1 of this sweep, or class 0 of the next one
